@@ -1,0 +1,293 @@
+"""Throughput benchmark of the one-GPU NeRF-XL hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+A step renders one batch of the grid8 workload (K=8 regions, 2x2x2 over
+[-1,1]^3, L=16 F=2 T=2^19 levels 16->2048, 2^18 rays from 64 pinhole cameras,
+128 samples per ray) through the C ABI, FP32 plain path. Under torchrun each
+rank renders its own batch on its own GPU (rays are independent: weak
+scaling, no data-path collective). Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s (render fwd; train fwd+bwd) vs FP32 plain at stated error; p50/p99 serve ms"
+WORKLOAD = "grid8"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-rays", type=int, default=1 << 14, help="oracle sample size for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def setup_workload(seed_offset: int = 0):
+    from paper_2404_16221_b300 import api, native as N, synthetic as sy
+
+    w = sy.workload(WORKLOAD)
+    E = N.table_entries(w.level_res, w.log2_T)
+    P = N.mlp_params(w.mlp_in, w.W)
+    tables, mlp = sy.field_params(w, E, P)
+    o, d = sy.workload_rays(w)
+    if seed_offset:
+        # another rank: the same scene seen by a rotated camera ring
+        ang = 0.37 * seed_offset
+        Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]], np.float32)
+        o, d = (o @ Rz.T).astype(np.float32), (d @ Rz.T).astype(np.float32)
+    return w, tables, mlp, o, d
+
+
+def cpu_baseline(w, tables, mlp, o, d, n_rays: int):
+    import oracle
+
+    from paper_2404_16221_b300 import synthetic as sy
+
+    f = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, tables.astype(np.float64),
+                     mlp.astype(np.float64))
+    sel = sy.subset(len(o), min(n_rays, len(o)), 1234)
+    t0 = time.perf_counter()
+    oracle.render(f, w.S, o[sel], d[sel], 1)
+    dt = time.perf_counter() - t0
+    return {"value": len(sel) / dt, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d seeded rays of the %s workload, FP64 partitioned render (Algorithm 1/2), %.1f s"
+                      % (len(sel), w.name, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w, tables, mlp, o, d = setup_workload()
+    for _ in range(max(0, args.warmup)):
+        cpu_baseline(w, tables, mlp, o, d, 256)
+    times = []
+    vals = []
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, tables, mlp, o, d, max(256, args.cpu_rays // 8))
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * (w.n_rays / v),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid8: K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 (16->2048), 2^18 rays from 64 "
+                                   "cameras, S=128; per step a bounded ray sample, rays/s extrapolated"},
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_16221_b300 import api, build, native as N
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    w, tables, mlp, o, d = setup_workload(rank)
+    field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(tables), torch.from_numpy(mlp),
+                                 device=dev)
+    samp = api.Sampling(w.S, w.max_segments)
+    R = len(o)
+    o_dev = torch.from_numpy(o).to(dev)
+    d_dev = torch.from_numpy(d).to(dev)
+    ws = api.alloc_workspace(field, samp, R)
+    out = {"rgb": torch.empty(R, 3, device=dev), "depth": torch.empty(R, device=dev),
+           "opacity": torch.empty(R, device=dev), "dist": torch.empty(R, device=dev)}
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        api.render_fwd(field, samp, o_dev, d_dev, workspace=ws, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    api.check(ws)
+    n_samples = C_int64()
+    n_chunks = C_int64()
+    N.check(N.lib().nerfxl_workspace_stats(N._ptr(ws), ws.numel(), n_samples, n_chunks,
+                                           N._stream(None)), "stats")
+    torch.cuda.synchronize()
+
+    # Device-timed steps: L2 flushed before each step (outside the events),
+    # the dominant kernel bracketed by the library's profile events.
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            N.check(N.lib().nerfxl_set_profile_events(C_void(kev[i][0].cuda_event), C_void(kev[i][1].cuda_event)),
+                    "profile events")
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        N.lib().nerfxl_set_profile_events(None, None)
+        # end to end through host buffers: H2D of the rays, D2H of the image
+        o_h = torch.from_numpy(o).pin_memory()
+        d_h = torch.from_numpy(d).pin_memory()
+        out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            o_dev.copy_(o_h, non_blocking=True)
+            d_dev.copy_(d_h, non_blocking=True)
+            step()
+            for k in out:
+                out_h[k].copy_(out[k], non_blocking=True)
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+    t_step = sum(step_ms) / 1000.0
+    t_e2e = sum(e2e_ms) / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(tt[0]), float(tt[1])
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return
+    hbm, bf16, src = peaks()
+    kern_s = statistics.mean(kern_ms) / 1000.0
+    bytes_per_sample = 8 * w.F * 4 * w.L  # 8 corners x F features x 4 B x L levels
+    achieved = n_samples.value * bytes_per_sample / kern_s / 1e9
+    rays_total = R * world * args.steps
+    line = {
+        "metric": METRIC, "value": rays_total / t_step, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": 1000.0 * t_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "grid8 render fwd: K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 (16->2048), FP32 tables "
+                               "and MLP 32-64-64-4, 2^18 rays from 64 pinhole cameras, S=128",
+                   "rays_per_gpu": R, "samples_per_step": int(n_samples.value), "chunks_per_step": int(n_chunks.value),
+                   "l2": "flushed before every timed step (252 MB write, outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(2 * R * 12),
+                "d2h_bytes_per_step": int(R * (12 + 4 + 4 + 4))},
+        "gpu_launches": 5 * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_field_fwd_f32", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "basis": "%d B/sample algorithmic gather bytes x %d samples / mean kernel time %.3f ms (%s peak)"
+                              % (bytes_per_sample, n_samples.value, 1000 * kern_s, src)},
+        "kernel_ms": statistics.mean(kern_ms), "wall_s": wall,
+    }
+    line["clocks"] = clk.summary()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, tables, mlp, o, d, args.cpu_rays)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def C_int64():
+    import ctypes
+
+    return ctypes.c_int64(0)
+
+
+def C_void(x):
+    import ctypes
+
+    return ctypes.c_void_p(x)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * nerfxl.h -- C ABI of the one-GPU NeRF-XL hot path (arXiv 2404.16221).
+ *
+ * The scene is split into K disjoint axis-aligned regions (Sec. 4.2). Each
+ * region owns its own multiresolution hash grid and small MLP (App. A.1).
+ * Every ray is (a) cut into per-region segments and sampled without any
+ * interval crossing a region face (Sec. 4.2), (b) evaluated through each
+ * region's hash grid and MLP, (c) rendered region-locally into per-segment
+ * partials (transmittance, colour, opacity, depth, distortion; Eq. 3-8), and
+ * (d) composited across regions by an exclusive prefix product in ray order
+ * (Algorithm 1, Algorithm 2), which equals single-pass rendering.
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE memory owned by the caller unless a
+ *    comment says "host". The library never allocates device memory: scratch
+ *    comes from a caller-provided workspace sized by nerfxl_workspace_bytes().
+ *  - Calls are asynchronous on the given stream. Arguments are validated on
+ *    the host before anything is launched; a bad argument returns
+ *    NERFXL_E_INVALID / NERFXL_E_UNSUPPORTED / NERFXL_E_WORKSPACE and launches
+ *    nothing. A launch failure returns NERFXL_E_CUDA. Conditions only the
+ *    device can see (more segments on a ray than max_segments) set a flag in
+ *    the workspace that nerfxl_check() reports.
+ *  - No C++ exception crosses this boundary. nerfxl_last_error() returns a
+ *    thread-local description of the last non-OK status.
+ *  - Rays: rays_o, rays_d are [R][3] float32, d of unit length. A ray that
+ *    misses every region renders rgb = 0, depth = 0, opacity = 0, dist = 0
+ *    (black background).
+ *  - Geometry and hash indices are computed in FP32 with a fixed operation
+ *    order (IEEE division, no fused multiply-add), so region assignment,
+ *    interval edges and hash indices are reproducible bit for bit.
+ */
+#ifndef NERFXL_H_
+#define NERFXL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NERFXL_MAX_LEVELS 32
+#define NERFXL_MAX_SEGMENTS 32
+#define NERFXL_MAX_REGIONS 1024
+
+typedef enum {
+  NERFXL_OK = 0,
+  NERFXL_E_INVALID = 1,     /* malformed argument */
+  NERFXL_E_WORKSPACE = 2,   /* workspace missing or too small */
+  NERFXL_E_CUDA = 3,        /* a CUDA call or launch failed */
+  NERFXL_E_TIMEOUT = 4,     /* a bounded device wait gave up */
+  NERFXL_E_UNSUPPORTED = 5, /* valid but not implemented (sizes, dtypes) */
+  NERFXL_E_OVERFLOW = 6     /* a ray crossed more regions than max_segments */
+} nerfxl_status;
+
+typedef enum { NERFXL_F32 = 0, NERFXL_F16 = 1, NERFXL_BF16 = 2, NERFXL_E4M3 = 3 } nerfxl_dtype;
+
+/*
+ * The partitioned field: K regions, each with a hash grid of L levels of F
+ * features and an MLP mlp_in -> W -> W -> 4 (ReLU, no biases; density =
+ * exp(o0), colour = sigmoid(o1..o3)).
+ *
+ * Level l has resolution level_res[l] (N_l cells per axis, (N_l+1)^3
+ * vertices). It is stored densely when (N_l+1)^3 <= 2^log2_T (the vertex
+ * count rounded up to a multiple of 8 entries), else as 2^log2_T hashed
+ * entries with the Instant-NGP spatial hash. E = nerfxl_table_entries() is the
+ * sum of the level sizes; a region's table is [E][F], levels back to back.
+ *
+ * tables: [K][E][F] of table_dtype (F32 or F16).
+ * mlp:    [K][P] of mlp_dtype, P = nerfxl_mlp_params(); each block is
+ *         W1 [mlp_in][W], W2 [W][W], W3 [W][4], row-major. Features beyond L*F
+ *         are zero, so only the first L*F rows of W1 matter.
+ * Currently supported: F = 2, mlp_in = 32, W = 64, L*F <= 32.
+ */
+typedef struct nerfxl_field {
+  int32_t K, L, F, log2_T, mlp_in, mlp_width;
+  int32_t level_res[NERFXL_MAX_LEVELS]; /* host values, copied into launches */
+  const float* boxes;                   /* [K][6]: min xyz, max xyz; disjoint */
+  const void* tables;                   /* [K][E][F] of table_dtype */
+  const void* mlp;                      /* [K][P] of mlp_dtype */
+  int32_t table_dtype, mlp_dtype;       /* nerfxl_dtype */
+  const float* mlp_scales;              /* [K][3] dequantisation scales for E4M3, else NULL */
+} nerfxl_field;
+
+/*
+ * Sampling (Sec. 4.2): the ray's segments [t0_k, t1_k] are sorted by t0; a
+ * uniform grid of n_samples intervals is laid over [first t0, last t1]
+ * (edges e_j = tn + j * ((tf - tn) / n_samples)), and each segment is cut at
+ * its own ends: segment k owns {t0_k} U {e_j : t0_k < e_j < t1_k} U {t1_k}.
+ * A ray therefore has at most n_samples + max_segments - 1 intervals.
+ * max_segments bounds the segments of one ray (0 means min(K, 32)).
+ */
+typedef struct nerfxl_sampling {
+  int32_t n_samples;
+  int32_t max_segments;
+  float t_min; /* near clamp of every t0 (0 for cameras outside the scene) */
+  int32_t flags; /* reserved, 0 */
+} nerfxl_sampling;
+
+/* Entries per region table (sum of level sizes), or -1 on bad input. */
+int64_t nerfxl_table_entries(const int32_t* level_res /* host [L] */, int32_t L, int32_t log2_T);
+/* Parameters per region MLP block: mlp_in*W + W*W + 4*W. */
+int64_t nerfxl_mlp_params(int32_t mlp_in, int32_t width);
+/* Largest number of 32-sample chunks one ray can produce. */
+int32_t nerfxl_max_chunks(const nerfxl_sampling* s, int32_t K);
+
+/*
+ * Workspace for R rays. With for_backward != 0 it also holds what
+ * nerfxl_render_bwd needs; a forward call on such a workspace keeps the
+ * per-chunk partials for the backward call that follows.
+ */
+size_t nerfxl_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, int32_t for_backward);
+
+/*
+ * Forward render (steps a-d above). Outputs: rgb [R][3], depth [R]
+ * (unnormalised expected distance, Eq. 6), opacity [R] (accumulated weight,
+ * Eq. 5), dist [R] (distortion loss of the ray, Eq. 7; may be NULL).
+ */
+nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                const float* rays_o, const float* rays_d, float* rgb, float* depth, float* opacity,
+                                float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Status of device-side checks of the last call made with this workspace
+ * (synchronises the stream): NERFXL_OK or NERFXL_E_OVERFLOW.
+ */
+nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Counters of the last call made with this workspace (synchronises the
+ * stream): total intervals (samples) and non-empty 32-sample chunks.
+ */
+nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int64_t* n_samples, int64_t* n_chunks,
+                                     cudaStream_t stream);
+
+/*
+ * Instrumentation: while set (non-NULL), every following call records
+ * `start` right before and `stop` right after its dominant kernel (the fused
+ * field kernel of the forward or backward pass), on the call's stream, so a
+ * caller can time that kernel with CUDA events. Pass NULL, NULL to stop.
+ * Process-wide setting; not for concurrent use from several threads.
+ */
+nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
+
+/* Thread-local text for the last non-OK status. */
+const char* nerfxl_last_error(void);
+
+/*
+ * Debug views of the forward pass, computed by the same device functions as
+ * nerfxl_render_fwd, for bit-exact checks.
+ *
+ * nerfxl_debug_segments: nseg [R]; region, t0, t1, n_intervals [R][max_seg].
+ * nerfxl_debug_samples: per ray count [R]; per interval a, b [R][max_int]
+ *   (float32) and region [R][max_int]; optionally hash indices within the
+ *   level idx [R][max_int][L][8] (uint32, may be NULL), features
+ *   feat [R][max_int][mlp_in] (float32, may be NULL) and raw MLP outputs
+ *   raw [R][max_int][4] (float32, may be NULL). Slots past count are untouched.
+ */
+nerfxl_status nerfxl_debug_segments(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                    const float* rays_o, const float* rays_d, int32_t max_seg, int32_t* nseg,
+                                    int32_t* region, float* t0, float* t1, int32_t* n_intervals, void* workspace,
+                                    size_t ws_bytes, cudaStream_t stream);
+nerfxl_status nerfxl_debug_samples(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                   const float* rays_o, const float* rays_d, int32_t max_int, int32_t* count,
+                                   float* a, float* b, int32_t* region, uint32_t* idx, float* feat, float* raw,
+                                   cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NERFXL_H_ */

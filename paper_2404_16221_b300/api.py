@@ -1,0 +1,150 @@
+"""Python front end of the NeRF-XL C ABI: field blocks on the GPU and calls.
+
+A ``PartitionedField`` holds the K region parameter blocks (boxes, hash
+tables, MLPs) as device tensors; ``Sampling`` holds the per-ray sampling
+settings. The functions below only marshal arguments into the C ABI
+(``native.py``); all work happens in libnerfxl's CUDA kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import native as N
+
+_DTYPE_CODE = {torch.float32: N.F32, torch.float16: N.F16, torch.bfloat16: N.BF16, torch.uint8: N.E4M3}
+
+
+@dataclasses.dataclass
+class Sampling:
+    n_samples: int
+    max_segments: int = 0
+    t_min: float = 0.0
+
+    def desc(self) -> N.SamplingDesc:
+        return N.SamplingDesc(int(self.n_samples), int(self.max_segments), float(self.t_min), 0)
+
+
+class PartitionedField:
+    """K disjoint regions, each with its own hash grid and MLP (App. A.1).
+
+    boxes [K][6] float32; tables [K][E][F] float32 (or float16);
+    mlp [K][P] float32 (or bf16/fp16; uint8 holding e4m3 with mlp_scales).
+    """
+
+    def __init__(self, boxes, level_res, log2_T: int, tables, mlp, F: int = 2, mlp_in: int = 32, width: int = 64,
+                 mlp_scales=None, device="cuda"):
+        self.device = torch.device(device)
+        self.boxes = torch.as_tensor(boxes, dtype=torch.float32).reshape(-1, 6).contiguous().to(self.device)
+        self.level_res = [int(v) for v in level_res]
+        self.K = int(self.boxes.shape[0])
+        self.L = len(self.level_res)
+        self.F, self.log2_T, self.mlp_in, self.width = int(F), int(log2_T), int(mlp_in), int(width)
+        self.E = N.table_entries(self.level_res, self.log2_T)
+        self.P = N.mlp_params(self.mlp_in, self.width)
+        self.tables = torch.as_tensor(tables).to(self.device).reshape(self.K, self.E, self.F).contiguous()
+        self.mlp = torch.as_tensor(mlp).to(self.device).reshape(self.K, self.P).contiguous()
+        self.mlp_scales = None if mlp_scales is None else torch.as_tensor(
+            mlp_scales, dtype=torch.float32).to(self.device).reshape(self.K, 3).contiguous()
+
+    def desc(self) -> N.FieldDesc:
+        d = N.FieldDesc()
+        d.K, d.L, d.F, d.log2_T, d.mlp_in, d.mlp_width = self.K, self.L, self.F, self.log2_T, self.mlp_in, self.width
+        for i, v in enumerate(self.level_res):
+            d.level_res[i] = v
+        d.boxes = self.boxes.data_ptr()
+        d.tables = self.tables.data_ptr()
+        d.mlp = self.mlp.data_ptr()
+        d.table_dtype = _DTYPE_CODE[self.tables.dtype]
+        d.mlp_dtype = _DTYPE_CODE[self.mlp.dtype]
+        d.mlp_scales = None if self.mlp_scales is None else self.mlp_scales.data_ptr()
+        return d
+
+
+def _rays(rays_o, rays_d, device):
+    o = torch.as_tensor(rays_o, dtype=torch.float32).reshape(-1, 3).to(device).contiguous()
+    d = torch.as_tensor(rays_d, dtype=torch.float32).reshape(-1, 3).to(device).contiguous()
+    if o.shape != d.shape:
+        raise ValueError("rays_o and rays_d differ in shape")
+    return o, d
+
+
+def workspace_bytes(field: PartitionedField, samp: Sampling, n_rays: int, for_backward: bool = False) -> int:
+    fd, sd = field.desc(), samp.desc()
+    n = int(N.lib().nerfxl_workspace_bytes(C_ref(fd), C_ref(sd), int(n_rays), int(for_backward)))
+    if n == 0:
+        N.check(N.E_INVALID, "nerfxl_workspace_bytes")
+    return n
+
+
+def C_ref(x):
+    import ctypes
+
+    return ctypes.byref(x)
+
+
+def alloc_workspace(field, samp, n_rays, for_backward=False):
+    return torch.empty(workspace_bytes(field, samp, n_rays, for_backward), dtype=torch.uint8, device=field.device)
+
+
+def render_fwd(field: PartitionedField, samp: Sampling, rays_o, rays_d, workspace=None, want_dist: bool = True,
+               stream=None, out=None):
+    """Forward render: returns dict rgb [R][3], depth, opacity, dist [R]."""
+    o, d = _rays(rays_o, rays_d, field.device)
+    R = o.shape[0]
+    if workspace is None:
+        workspace = alloc_workspace(field, samp, R)
+    if out is None:
+        out = {"rgb": torch.empty(R, 3, device=field.device), "depth": torch.empty(R, device=field.device),
+               "opacity": torch.empty(R, device=field.device),
+               "dist": torch.empty(R, device=field.device) if want_dist else None}
+    fd, sd = field.desc(), samp.desc()
+    st = N.lib().nerfxl_render_fwd(C_ref(fd), C_ref(sd), R, N._ptr(o), N._ptr(d), N._ptr(out["rgb"]),
+                                   N._ptr(out["depth"]), N._ptr(out["opacity"]), N._ptr(out.get("dist")),
+                                   N._ptr(workspace), workspace.numel(), N._stream(stream))
+    N.check(st, "nerfxl_render_fwd")
+    return out
+
+
+def check(workspace, stream=None):
+    """Report device-side flags of the last call on this workspace (syncs)."""
+    N.check(N.lib().nerfxl_check(N._ptr(workspace), workspace.numel(), N._stream(stream)), "nerfxl_check")
+
+
+def debug_segments(field: PartitionedField, samp: Sampling, rays_o, rays_d, max_seg: int):
+    o, d = _rays(rays_o, rays_d, field.device)
+    R = o.shape[0]
+    dev = field.device
+    nseg = torch.zeros(R, dtype=torch.int32, device=dev)
+    region = torch.full((R, max_seg), -1, dtype=torch.int32, device=dev)
+    t0 = torch.zeros(R, max_seg, device=dev)
+    t1 = torch.zeros(R, max_seg, device=dev)
+    nint = torch.zeros(R, max_seg, dtype=torch.int32, device=dev)
+    ws = alloc_workspace(field, samp, R)
+    fd, sd = field.desc(), samp.desc()
+    st = N.lib().nerfxl_debug_segments(C_ref(fd), C_ref(sd), R, N._ptr(o), N._ptr(d), int(max_seg), N._ptr(nseg),
+                                       N._ptr(region), N._ptr(t0), N._ptr(t1), N._ptr(nint), N._ptr(ws), ws.numel(),
+                                       N._stream(None))
+    N.check(st, "nerfxl_debug_segments")
+    return nseg, region, t0, t1, nint
+
+
+def debug_samples(field: PartitionedField, samp: Sampling, rays_o, rays_d, max_int: int, want_idx=False,
+                  want_feat=False, want_raw=False):
+    o, d = _rays(rays_o, rays_d, field.device)
+    R = o.shape[0]
+    dev = field.device
+    count = torch.zeros(R, dtype=torch.int32, device=dev)
+    a = torch.zeros(R, max_int, device=dev)
+    b = torch.zeros(R, max_int, device=dev)
+    region = torch.full((R, max_int), -1, dtype=torch.int32, device=dev)
+    idx = torch.zeros(R, max_int, field.L, 8, dtype=torch.int32, device=dev) if want_idx else None
+    feat = torch.zeros(R, max_int, field.mlp_in, device=dev) if want_feat else None
+    raw = torch.zeros(R, max_int, 4, device=dev) if want_raw else None
+    fd, sd = field.desc(), samp.desc()
+    st = N.lib().nerfxl_debug_samples(C_ref(fd), C_ref(sd), R, N._ptr(o), N._ptr(d), int(max_int), N._ptr(count),
+                                      N._ptr(a), N._ptr(b), N._ptr(region), N._ptr(idx), N._ptr(feat), N._ptr(raw),
+                                      N._stream(None))
+    N.check(st, "nerfxl_debug_samples")
+    return count, a, b, region, idx, feat, raw

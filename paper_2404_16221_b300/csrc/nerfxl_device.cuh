@@ -1,0 +1,226 @@
+// Device-side building blocks of the NeRF-XL hot path (arXiv 2404.16221).
+//
+// Geometry (Sec. 4.2) and the hash index (App. A.1, Instant-NGP encoding)
+// are written with explicit round-to-nearest intrinsics so that nvcc cannot
+// contract them into fused multiply-adds: region assignment, interval edges
+// and table indices are then identical to any IEEE FP32 evaluation in the
+// same operation order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nerfxl.h"
+
+namespace nerfxl {
+
+constexpr int kWarp = 32;
+constexpr int kMaxSeg = NERFXL_MAX_SEGMENTS;
+constexpr int kMaxLevels = NERFXL_MAX_LEVELS;
+constexpr uint32_t kEmptyChunk = 0xFFFFFFFFu;
+constexpr uint32_t kHashPrime2 = 2654435761u;  // Instant-NGP spatial hash primes (pi_1 = 1)
+constexpr uint32_t kHashPrime3 = 805459861u;
+
+// Fixed-size MLP the kernels are specialised for: 32 -> 64 -> 64 -> 4.
+constexpr int kIn = 32;
+constexpr int kWidth = 64;
+constexpr int kOut = 4;
+constexpr int kMlpParams = kIn * kWidth + kWidth * kWidth + kWidth * kOut;
+
+// Error flags written into the workspace header.
+constexpr int kErrOverflow = 1;
+
+// Per-level layout of a region table, passed by value in kernel parameters.
+struct LevelParams {
+  int32_t N[kMaxLevels];       // cells per axis
+  uint32_t off[kMaxLevels];    // first entry of the level
+  uint32_t dense_mask;         // bit l set: level l stored densely
+  uint32_t hash_mask;          // 2^log2_T - 1
+  int32_t L;
+  uint32_t E;                  // entries per region
+};
+
+// Sampling description shared by the kernels.
+struct SampParams {
+  int32_t S;          // grid intervals over [tn, tf]
+  int32_t max_seg;    // segments per ray bound (<= kMaxSeg)
+  int32_t max_chunk;  // chunks per ray bound
+  float t_min;
+};
+
+// One ray's sampling header.
+struct __align__(16) RayHdr {
+  float tn;       // first segment start
+  float delta;    // (tf - tn) / S
+  int32_t nseg;
+  int32_t nchunk;
+};
+
+// One segment: [t0, t1] inside region; first interior grid edge j_lo and
+// interval count n; chunk_base = index of its first chunk within the ray.
+struct __align__(16) SegDesc {
+  float t0, t1;
+  int32_t jlo_n;      // j_lo (low 16 bits) | n (high 16 bits)
+  int32_t reg_cb;     // region (low 16 bits) | chunk_base (high 16 bits)
+};
+
+__device__ __forceinline__ int seg_jlo(const SegDesc& s) { return s.jlo_n & 0xFFFF; }
+__device__ __forceinline__ int seg_n(const SegDesc& s) { return (s.jlo_n >> 16) & 0xFFFF; }
+__device__ __forceinline__ int seg_region(const SegDesc& s) { return s.reg_cb & 0xFFFF; }
+__device__ __forceinline__ int seg_chunk_base(const SegDesc& s) { return (s.reg_cb >> 16) & 0xFFFF; }
+
+// ---------------------------------------------------------------------------
+// Geometry (Sec. 4.2).
+
+// Slab test: t0 = max(t_min, max_axis min(ta, tb)), t1 = min_axis max(ta, tb),
+// ta = (bmin - o) * (1/d), tb = (bmax - o) * (1/d); fminf/fmaxf ignore NaN.
+__device__ __forceinline__ bool slab(const float o[3], const float inv_d[3], const float* box, float t_min,
+                                     float& t0, float& t1) {
+  float tn = -INFINITY, tf = INFINITY;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float ta = __fmul_rn(__fsub_rn(box[ax], o[ax]), inv_d[ax]);
+    const float tb = __fmul_rn(__fsub_rn(box[3 + ax], o[ax]), inv_d[ax]);
+    tn = fmaxf(tn, fminf(ta, tb));
+    tf = fminf(tf, fmaxf(ta, tb));
+  }
+  tn = fmaxf(tn, t_min);
+  t0 = tn;
+  t1 = tf;
+  return tf > tn;
+}
+
+// Grid edge e_j = tn + j * delta, two roundings.
+__device__ __forceinline__ float grid_edge(float tn, float delta, int j) {
+  return __fadd_rn(tn, __fmul_rn((float)j, delta));
+}
+
+// First j in [1, S] with e_j > t (S if none): estimate, then walk to the exact
+// boundary of the monotone sequence e_j (each walk is bounded by S steps).
+__device__ __forceinline__ int first_edge_above(float tn, float delta, int S, float t) {
+  float est = __fdiv_rn(__fsub_rn(t, tn), delta);
+  est = fminf(fmaxf(est, 0.0f), (float)S);
+  int j = max(1, (int)est);
+  for (int it = 0; it <= S && j > 1 && grid_edge(tn, delta, j - 1) > t; ++it) --j;
+  for (int it = 0; it <= S && j < S && !(grid_edge(tn, delta, j) > t); ++it) ++j;
+  return j;
+}
+
+// First j in [1, S] with e_j >= t (S if none).
+__device__ __forceinline__ int first_edge_at_or_above(float tn, float delta, int S, float t) {
+  float est = __fdiv_rn(__fsub_rn(t, tn), delta);
+  est = fminf(fmaxf(est, 0.0f), (float)S);
+  int j = max(1, (int)est);
+  for (int it = 0; it <= S && j > 1 && grid_edge(tn, delta, j - 1) >= t; ++it) --j;
+  for (int it = 0; it <= S && j < S && !(grid_edge(tn, delta, j) >= t); ++it) ++j;
+  return j;
+}
+
+// Segments of one ray, sorted by (t0, region). Returns the number of hits
+// (possibly > max_seg: only the first max_seg in sort order are kept and the
+// caller flags an overflow).
+__device__ __forceinline__ int ray_segments(const float o[3], const float d[3], const float* boxes, int K,
+                                            float t_min, int max_seg, float* st0, float* st1, int* sreg) {
+  float inv_d[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) inv_d[ax] = __fdiv_rn(1.0f, d[ax]);
+  int n = 0, hits = 0;
+  for (int k = 0; k < K; ++k) {
+    float t0, t1;
+    if (!slab(o, inv_d, boxes + 6 * k, t_min, t0, t1)) continue;
+    ++hits;
+    // insertion into the sorted prefix (K is scanned in increasing order, so
+    // equal t0 keeps the lower region id first)
+    int pos = n;
+    while (pos > 0 && st0[pos - 1] > t0) --pos;
+    if (pos >= max_seg) continue;
+    const int last = min(n, max_seg - 1);
+    for (int q = last; q > pos; --q) {
+      st0[q] = st0[q - 1];
+      st1[q] = st1[q - 1];
+      sreg[q] = sreg[q - 1];
+    }
+    st0[pos] = t0;
+    st1[pos] = t1;
+    sreg[pos] = k;
+    n = min(n + 1, max_seg);
+  }
+  return hits;
+}
+
+// Interval i of a segment: [a, b].
+__device__ __forceinline__ void segment_interval(const SegDesc& sd, float tn, float delta, int i, float& a,
+                                                 float& b) {
+  const int jlo = seg_jlo(sd), n = seg_n(sd);
+  a = (i == 0) ? sd.t0 : grid_edge(tn, delta, jlo + i - 1);
+  b = (i == n - 1) ? sd.t1 : grid_edge(tn, delta, jlo + i);
+}
+
+// Sample point x = o + tbar * d, two roundings per axis.
+__device__ __forceinline__ void sample_point(const float o[3], const float d[3], float tbar, float x[3]) {
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) x[ax] = __fadd_rn(o[ax], __fmul_rn(tbar, d[ax]));
+}
+
+// Region-local coordinate u = clamp((x - bmin) * (1 / (bmax - bmin)), 0, 1).
+__device__ __forceinline__ void region_coord(const float* box, const float x[3], float u[3]) {
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float inv_ext = __fdiv_rn(1.0f, __fsub_rn(box[3 + ax], box[ax]));
+    const float v = __fmul_rn(__fsub_rn(x[ax], box[ax]), inv_ext);
+    u[ax] = fminf(fmaxf(v, 0.0f), 1.0f);
+  }
+}
+
+// Cell of level resolution N: c = min(floor(u * N), N - 1), f = u * N - c.
+__device__ __forceinline__ void level_cell(float u, int N, int& c, float& f) {
+  const float p = __fmul_rn(u, (float)N);
+  int ci = (int)floorf(p);
+  ci = min(max(ci, 0), N - 1);
+  c = ci;
+  f = __fsub_rn(p, (float)ci);
+}
+
+// Index within level l of vertex (x, y, z).
+__device__ __forceinline__ uint32_t vertex_index(const LevelParams& lp, int l, uint32_t x, uint32_t y, uint32_t z) {
+  if ((lp.dense_mask >> l) & 1u) {
+    const uint32_t side = (uint32_t)lp.N[l] + 1u;
+    return x + y * side + z * side * side;
+  }
+  return (x ^ (y * kHashPrime2) ^ (z * kHashPrime3)) & lp.hash_mask;
+}
+
+// ---------------------------------------------------------------------------
+// Warp scans and reductions.
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ float warp_exclusive_from_inclusive(float incl, int lane) {
+  const float t = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  return lane == 0 ? 0.0f : t;
+}
+
+// Suffix sum (sum over lanes >= lane).
+__device__ __forceinline__ float warp_suffix_scan(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if (lane + o < 32) v += t;
+  }
+  return v;
+}
+
+}  // namespace nerfxl

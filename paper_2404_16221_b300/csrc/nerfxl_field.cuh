@@ -1,0 +1,163 @@
+// Per-sample field evaluation and chunk rendering shared by the forward,
+// backward and debug kernels (FP32 plain path).
+#pragma once
+
+#include "nerfxl_device.cuh"
+
+namespace nerfxl {
+
+// ---------------------------------------------------------------------------
+// Field evaluation of one sample, FP32 plain path.
+
+struct FieldPtrs {
+  const float* boxes;
+  const float* tables;  // [K][E][2]
+  const float* mlp;     // [K][kMlpParams]
+};
+
+// Hash-grid encoding (F = 2): feat[2l + j] = sum_corners w * table[l][idx][j].
+__device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* __restrict__ table, const float u[3],
+                                           float feat[kIn]) {
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) feat[i] = 0.0f;
+#pragma unroll
+  for (int l = 0; l < kIn / 2; ++l) {
+    if (l >= lp.L) break;
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t idx = vertex_index(lp, l, c[0] + (e & 1), c[1] + ((e >> 1) & 1), c[2] + ((e >> 2) & 1));
+      v[e] = __ldg(table + lp.off[l] + idx);
+    }
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float w = ((e & 1) ? f[0] : 1.0f - f[0]) * (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) *
+                      (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+      s0 = fmaf(w, v[e].x, s0);
+      s1 = fmaf(w, v[e].y, s1);
+    }
+    feat[2 * l] = s0;
+    feat[2 * l + 1] = s1;
+  }
+}
+
+// MLP with weights staged in shared memory as W1t [64][32] (row n holds
+// column n of W1), W2t [64][64], W3 [64][4]. Layer 2 and 3 are fused per
+// hidden unit so that only h1 stays live.
+__device__ __forceinline__ void mlp_f32_smem(const float* __restrict__ s_w, const float feat[kIn], float out[kOut]) {
+  const float4* W1t = reinterpret_cast<const float4*>(s_w);
+  const float4* W2t = reinterpret_cast<const float4*>(s_w + kIn * kWidth);
+  const float4* W3 = reinterpret_cast<const float4*>(s_w + kIn * kWidth + kWidth * kWidth);
+  float h1[kWidth];
+#pragma unroll
+  for (int n = 0; n < kWidth; ++n) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i4 = 0; i4 < kIn / 4; ++i4) {
+      const float4 w = W1t[n * (kIn / 4) + i4];
+      acc = fmaf(feat[4 * i4 + 0], w.x, acc);
+      acc = fmaf(feat[4 * i4 + 1], w.y, acc);
+      acc = fmaf(feat[4 * i4 + 2], w.z, acc);
+      acc = fmaf(feat[4 * i4 + 3], w.w, acc);
+    }
+    h1[n] = fmaxf(acc, 0.0f);
+  }
+  float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, o3 = 0.0f;
+#pragma unroll 2
+  for (int n = 0; n < kWidth; ++n) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i4 = 0; i4 < kWidth / 4; ++i4) {
+      const float4 w = W2t[n * (kWidth / 4) + i4];
+      acc = fmaf(h1[4 * i4 + 0], w.x, acc);
+      acc = fmaf(h1[4 * i4 + 1], w.y, acc);
+      acc = fmaf(h1[4 * i4 + 2], w.z, acc);
+      acc = fmaf(h1[4 * i4 + 3], w.w, acc);
+    }
+    const float h2 = fmaxf(acc, 0.0f);
+    const float4 w3 = W3[n];
+    o0 = fmaf(h2, w3.x, o0);
+    o1 = fmaf(h2, w3.y, o1);
+    o2 = fmaf(h2, w3.z, o2);
+    o3 = fmaf(h2, w3.w, o3);
+  }
+  out[0] = o0;
+  out[1] = o1;
+  out[2] = o2;
+  out[3] = o3;
+}
+
+// Stage region k's FP32 MLP block into shared memory (transposed layout).
+__device__ __forceinline__ void load_mlp_f32(const float* __restrict__ blk, float* __restrict__ s_w) {
+  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+    const int row = i / kWidth, col = i % kWidth;  // W1[row][col]
+    s_w[col * kIn + row] = blk[i];
+  }
+  const float* W2 = blk + kIn * kWidth;
+  float* s2 = s_w + kIn * kWidth;
+  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+    const int row = i / kWidth, col = i % kWidth;
+    s2[col * kWidth + row] = W2[i];
+  }
+  const float* W3 = W2 + kWidth * kWidth;
+  float* s3 = s2 + kWidth * kWidth;
+  for (int i = threadIdx.x; i < kWidth * kOut; i += blockDim.x) s3[i] = W3[i];
+}
+
+// Chunk partial: {tau, C[3], A, D', L, 0}; D' and L use t' = tbar - tn.
+struct Partial {
+  float tau, c0, c1, c2, A, D, L;
+};
+
+// Region-local volume rendering of one 32-sample chunk by one warp
+// (Eq. 1-2 restricted to the chunk, transmittance restarting at 1).
+__device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3], float tr, float dl, int lane) {
+  const float tau = sigma * dl;
+  const float incl = warp_inclusive_scan(tau, lane);
+  const float excl = warp_exclusive_from_inclusive(incl, lane);
+  const float T = expf(-excl);
+  const float alpha = -expm1f(-tau);
+  const float w = T * alpha;
+  const float wt = w * tr;
+  const float Wx = warp_exclusive_from_inclusive(warp_inclusive_scan(w, lane), lane);
+  const float WTx = warp_exclusive_from_inclusive(warp_inclusive_scan(wt, lane), lane);
+  const float l = 2.0f * w * (tr * Wx - WTx) + w * w * dl * (1.0f / 3.0f);
+  Partial p;
+  p.tau = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  p.c0 = warp_sum(w * rgb[0]);
+  p.c1 = warp_sum(w * rgb[1]);
+  p.c2 = warp_sum(w * rgb[2]);
+  p.A = warp_sum(w);
+  p.D = warp_sum(wt);
+  p.L = warp_sum(l);
+  return p;
+}
+
+
+// MLP reading the row-major block W1 [32][64], W2 [64][64], W3 [64][4]
+// straight from global memory (debug views only).
+__device__ __forceinline__ void mlp_f32_global(const float* __restrict__ blk, const float feat[kIn], float out[kOut]) {
+  const float* W1 = blk;
+  const float* W2 = blk + kIn * kWidth;
+  const float* W3 = W2 + kWidth * kWidth;
+  float h1[kWidth];
+  for (int n = 0; n < kWidth; ++n) {
+    float acc = 0.0f;
+    for (int i = 0; i < kIn; ++i) acc = fmaf(feat[i], W1[i * kWidth + n], acc);
+    h1[n] = fmaxf(acc, 0.0f);
+  }
+  for (int m = 0; m < kOut; ++m) out[m] = 0.0f;
+  for (int n = 0; n < kWidth; ++n) {
+    float acc = 0.0f;
+    for (int i = 0; i < kWidth; ++i) acc = fmaf(h1[i], W2[i * kWidth + n], acc);
+    const float h2 = fmaxf(acc, 0.0f);
+    for (int m = 0; m < kOut; ++m) out[m] = fmaf(h2, W3[n * kOut + m], out[m]);
+  }
+}
+
+}  // namespace nerfxl

@@ -1,0 +1,570 @@
+// Forward pass of the one-GPU NeRF-XL hot path (arXiv 2404.16221) and the
+// C-ABI entry points declared in include/nerfxl.h.
+//
+// Work decomposition. A ray's samples are grouped into CHUNKS of at most 32
+// consecutive intervals that all lie in one region segment. Each chunk is
+// reduced by one warp to a 7-float partial (optical depth, colour, opacity,
+// depth, distortion), exactly the per-segment partial of Sec. 4.3: because
+// the composition of Eq. 3-8 is associative, chunks are just finer segments,
+// so chunks never need each other's state. Chunks are bucketed by region
+// (padded to whole tiles of kChunksPerTile) so that every CTA tile evaluates a
+// single region's MLP and can keep its weights in shared memory. A final
+// per-ray kernel composites the chunk partials in ray order (Algorithm 1, 2).
+//
+// Kernels (one forward call):
+//   k_segments     per ray: slab tests, sorted segments, interval counts;
+//                  per-region chunk histogram (block-aggregated atomics)
+//   k_region_scan  1 thread: padded exclusive scan of the histogram -> bases
+//   k_fill_chunks  per ray: chunk references into the region buckets
+//   k_field_fwd    persistent CTAs over tiles: hash gather + MLP + local render
+//   k_composite    per ray: exclusive prefix product over chunk partials
+
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "nerfxl_device.cuh"
+#include "nerfxl_field.cuh"
+#include "nerfxl_host.h"
+
+namespace nerfxl {
+
+// ---------------------------------------------------------------------------
+// k_segments
+
+__global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays_o, const float* __restrict__ rays_d,
+                                                  int64_t R, const float* __restrict__ boxes, int K, SampParams sp,
+                                                  RayHdr* __restrict__ hdr, SegDesc* __restrict__ segs,
+                                                  int32_t* __restrict__ counts, int32_t* __restrict__ err) {
+  extern __shared__ float s_mem[];
+  float* s_boxes = s_mem;                                 // [K][6]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [K]
+  __shared__ unsigned long long s_samples, s_chunks;
+  for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
+  __syncthreads();
+
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R) {
+    float o[3], d[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      o[ax] = rays_o[3 * r + ax];
+      d[ax] = rays_d[3 * r + ax];
+    }
+    float st0[kMaxSeg], st1[kMaxSeg];
+    int sreg[kMaxSeg];
+    const int hits = ray_segments(o, d, s_boxes, K, sp.t_min, sp.max_seg, st0, st1, sreg);
+    if (hits > sp.max_seg) atomicOr(err, kErrOverflow);
+    const int nseg = min(hits, sp.max_seg);
+    RayHdr h;
+    h.nseg = nseg;
+    h.tn = nseg ? st0[0] : 0.0f;
+    h.delta = nseg ? __fdiv_rn(__fsub_rn(st1[nseg - 1], st0[0]), (float)sp.S) : 0.0f;
+    int cbase = 0, n_samples = 0;
+    for (int k = 0; k < nseg; ++k) {
+      const int jlo = first_edge_above(h.tn, h.delta, sp.S, st0[k]);
+      const int jend = first_edge_at_or_above(h.tn, h.delta, sp.S, st1[k]);
+      const int n = 1 + max(0, jend - jlo);
+      SegDesc s;
+      s.t0 = st0[k];
+      s.t1 = st1[k];
+      s.jlo_n = (jlo & 0xFFFF) | (n << 16);
+      s.reg_cb = (sreg[k] & 0xFFFF) | (cbase << 16);
+      segs[r * sp.max_seg + k] = s;
+      const int nch = (n + kWarp - 1) / kWarp;
+      atomicAdd(&s_cnt[sreg[k]], nch);
+      cbase += nch;
+      n_samples += n;
+    }
+    h.nchunk = cbase;
+    hdr[r] = h;
+    atomicAdd(&s_samples, (unsigned long long)n_samples);
+    atomicAdd(&s_chunks, (unsigned long long)cbase);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
+  if (threadIdx.x == 0) {
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
+    atomicAdd(stats + 0, s_samples);
+    atomicAdd(stats + 1, s_chunks);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_region_scan: base[k] = sum_{k' < k} round_up(count[k'], tile); padding
+// slots get the empty marker; header word 1 = total tiles.
+
+__global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chunks_per_tile,
+                              int32_t* __restrict__ base, uint2* __restrict__ chunks, int32_t* __restrict__ n_tiles) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int32_t acc = 0;
+  for (int k = 0; k < K; ++k) {
+    base[k] = acc;
+    const int c = counts[k];
+    const int padded = (c + chunks_per_tile - 1) / chunks_per_tile * chunks_per_tile;
+    for (int i = c; i < padded; ++i) chunks[acc + i] = make_uint2(kEmptyChunk, 0u);
+    acc += padded;
+  }
+  base[K] = acc;
+  *n_tiles = acc / chunks_per_tile;
+}
+
+// ---------------------------------------------------------------------------
+// k_fill_chunks: chunk references {ray, seg << 16 | chunk-in-segment}.
+
+__global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParams sp, const RayHdr* __restrict__ hdr,
+                                                     const SegDesc* __restrict__ segs,
+                                                     const int32_t* __restrict__ base, int32_t* __restrict__ cursor,
+                                                     uint2* __restrict__ chunks) {
+  extern __shared__ int32_t s_i[];
+  int32_t* s_cnt = s_i;       // [K]
+  int32_t* s_base = s_i + K;  // [K]
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int nseg = 0;
+  int off[kMaxSeg];
+  if (r < R) {
+    nseg = hdr[r].nseg;
+    for (int k = 0; k < nseg; ++k) {
+      const SegDesc s = segs[r * sp.max_seg + k];
+      off[k] = atomicAdd(&s_cnt[seg_region(s)], (seg_n(s) + kWarp - 1) / kWarp);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_base[i] = s_cnt[i] ? atomicAdd(&cursor[i], s_cnt[i]) : 0;
+  __syncthreads();
+  for (int k = 0; k < nseg; ++k) {
+    const SegDesc s = segs[r * sp.max_seg + k];
+    const int reg = seg_region(s);
+    const int nch = (seg_n(s) + kWarp - 1) / kWarp;
+    const int dst = base[reg] + s_base[reg] + off[k];
+    for (int c = 0; c < nch; ++c) chunks[dst + c] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_field_fwd (FP32): persistent CTAs, contiguous tile ranges; warp w of a
+// tile handles chunk 4 * tile + w. Weights are reloaded only when the tile's
+// region changes.
+
+constexpr int kChunksPerTile = 4;
+constexpr int kFwdThreads = kChunksPerTile * kWarp;
+
+struct FwdParams {
+  const float* rays_o;
+  const float* rays_d;
+  FieldPtrs fp;
+  LevelParams lp;
+  SampParams sp;
+  int K;
+  const RayHdr* hdr;
+  const SegDesc* segs;
+  const int32_t* base;     // [K+1]
+  const uint2* chunks;
+  const int32_t* n_tiles;
+  float4* partials;        // [R][max_chunk][2]
+};
+
+__device__ __forceinline__ int region_of_chunk(const int32_t* s_base, int K, int chunk) {
+  int lo = 0, hi = K - 1;  // largest k with base[k] <= chunk
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_base[mid] <= chunk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 4) k_field_fwd_f32(FwdParams p) {
+  extern __shared__ __align__(16) float s_dyn[];
+  float* s_w = s_dyn;                                            // kMlpParams floats
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kMlpParams);  // [K+1]
+  for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  __syncthreads();
+  const int n_tiles = *p.n_tiles;
+  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int t_begin = blockIdx.x * per;
+  const int t_end = min(n_tiles, t_begin + per);
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  int region = -1;
+  const float2* table = nullptr;
+  for (int t = t_begin; t < t_end; ++t) {
+    const int chunk = t * kChunksPerTile + warp;
+    const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
+    if (k != region) {
+      __syncthreads();
+      load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
+      __syncthreads();
+      region = k;
+      table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
+    }
+    const uint2 ref = p.chunks[chunk];
+    if (ref.x == kEmptyChunk) continue;  // warp-uniform
+    const uint32_t ray = ref.x;
+    const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+    const RayHdr h = p.hdr[ray];
+    const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+    float o[3], d[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      o[ax] = p.rays_o[3 * (size_t)ray + ax];
+      d[ax] = p.rays_d[3 * (size_t)ray + ax];
+    }
+    const int i = c * kWarp + lane;
+    const bool valid = i < seg_n(sd);
+    float feat[kIn];
+    float tbar = 0.0f, dl = 0.0f;
+    if (valid) {
+      float a, b;
+      segment_interval(sd, h.tn, h.delta, i, a, b);
+      tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+      dl = __fsub_rn(b, a);
+      float x[3], u[3];
+      sample_point(o, d, tbar, x);
+      region_coord(p.fp.boxes + 6 * k, x, u);
+      encode_f32(p.lp, table, u, feat);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+    }
+    float raw[kOut];
+    mlp_f32_smem(s_w, feat, raw);
+    float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+      sigma = expf(raw[0]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) rgb[q] = 1.0f / (1.0f + expf(-raw[1 + q]));
+    }
+    const float tr = valid ? __fsub_rn(tbar, h.tn) : 0.0f;
+    const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
+    if (lane == 0) {
+      float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
+      dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
+      dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_composite: Algorithm 1 + 2 over the chunk partials of one ray, with the
+// prefix optical depth accumulated in log space (Kahan-compensated):
+//   L += T^2 L_c + 2 T (D_c A - A_c D);  C += T C_c;  A += T A_c;  D += T D_c;
+//   tau += tau_c;  T = exp(-tau).
+
+__global__ void __launch_bounds__(256) k_composite(int64_t R, SampParams sp, const RayHdr* __restrict__ hdr,
+                                                   const float4* __restrict__ partials, float* __restrict__ rgb,
+                                                   float* __restrict__ depth, float* __restrict__ opacity,
+                                                   float* __restrict__ dist) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const RayHdr h = hdr[r];
+  float T = 1.0f, tau = 0.0f, comp = 0.0f;
+  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f, D = 0.0f, L = 0.0f;
+  const float4* src = partials + 2 * (size_t)r * sp.max_chunk;
+  for (int c = 0; c < h.nchunk; ++c) {
+    const float4 q0 = src[2 * c], q1 = src[2 * c + 1];
+    const float S = q1.y * A - q1.x * D;
+    L += T * T * q1.z + 2.0f * T * S;
+    C0 += T * q0.y;
+    C1 += T * q0.z;
+    C2 += T * q0.w;
+    A += T * q1.x;
+    D += T * q1.y;
+    const float y = q0.x - comp;
+    const float s = tau + y;
+    comp = (s - tau) - y;
+    tau = s;
+    T = expf(-tau);
+  }
+  rgb[3 * r + 0] = C0;
+  rgb[3 * r + 1] = C1;
+  rgb[3 * r + 2] = C2;
+  depth[r] = D + A * h.tn;
+  opacity[r] = A;
+  if (dist) dist[r] = L;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+namespace {
+
+thread_local std::string g_last_error;
+
+nerfxl_status fail(nerfxl_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    g_num_sms = n;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+const char* last_error() { return g_last_error.c_str(); }
+nerfxl_status set_error(nerfxl_status st, const std::string& msg) { return fail(st, msg); }
+
+int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s) {
+  int ms = s->max_segments > 0 ? s->max_segments : std::min(f->K, (int)kMaxSeg);
+  return ms;
+}
+
+int max_chunks(int S, int max_seg) { return max_seg + (S - 1) / kWarp; }
+
+Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int for_backward) {
+  Layout L;
+  const int ms = effective_max_seg(f, s);
+  const int mc = max_chunks(s->n_samples, ms);
+  const int K = f->K;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  L.hdr = take(sizeof(int32_t) * 16);
+  L.counts = take(sizeof(int32_t) * K);
+  L.cursor = take(sizeof(int32_t) * K);
+  L.zero_end = off;
+  L.base = take(sizeof(int32_t) * (K + 1));
+  L.ray_hdr = take(sizeof(RayHdr) * R);
+  L.segs = take(sizeof(SegDesc) * R * ms);
+  L.chunk_cap = (int64_t)R * mc + (int64_t)kChunksPerTile * K;
+  L.chunks = take(sizeof(uint2) * L.chunk_cap);
+  L.partials = take(sizeof(float4) * 2 * R * mc);
+  L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
+  L.total = off;
+  L.max_seg = ms;
+  L.max_chunk = mc;
+  return L;
+}
+
+nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R) {
+  if (!f || !s) return fail(NERFXL_E_INVALID, "null field or sampling");
+  if (f->K < 1 || f->K > NERFXL_MAX_REGIONS) return fail(NERFXL_E_INVALID, "K out of range");
+  if (f->L < 1 || f->L > NERFXL_MAX_LEVELS) return fail(NERFXL_E_INVALID, "L out of range");
+  if (f->log2_T < 1 || f->log2_T > 24) return fail(NERFXL_E_INVALID, "log2_T out of range");
+  if (f->F != 2 || f->mlp_in != kIn || f->mlp_width != kWidth || f->L * f->F > kIn)
+    return fail(NERFXL_E_UNSUPPORTED, "only F=2, mlp_in=32, width=64, L*F<=32 are built");
+  for (int l = 0; l < f->L; ++l)
+    if (f->level_res[l] < 1 || f->level_res[l] > (1 << 20)) return fail(NERFXL_E_INVALID, "level_res out of range");
+  if (s->n_samples < 1 || s->n_samples > 16384) return fail(NERFXL_E_INVALID, "n_samples out of range");
+  const int ms = effective_max_seg(f, s);
+  if (ms < 1 || ms > kMaxSeg) return fail(NERFXL_E_UNSUPPORTED, "max_segments must be in [1, 32]");
+  if (max_chunks(s->n_samples, ms) > 0xFFFF) return fail(NERFXL_E_UNSUPPORTED, "too many chunks per ray");
+  if (R < 0 || R > (int64_t)0x7FFFFFFF) return fail(NERFXL_E_INVALID, "n_rays out of range");
+  if (!f->boxes || !f->tables || !f->mlp) return fail(NERFXL_E_INVALID, "null field pointer");
+  return NERFXL_OK;
+}
+
+LevelParams level_params(const nerfxl_field* f) {
+  LevelParams lp;
+  const int64_t T = int64_t(1) << f->log2_T;
+  int64_t off = 0;
+  lp.dense_mask = 0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    lp.N[l] = 1;
+    lp.off[l] = 0;
+  }
+  for (int l = 0; l < f->L; ++l) {
+    const int64_t side = (int64_t)f->level_res[l] + 1;
+    const int64_t verts = side * side * side;
+    const bool dense = verts <= T;
+    lp.N[l] = f->level_res[l];
+    lp.off[l] = (uint32_t)off;
+    if (dense) lp.dense_mask |= 1u << l;
+    off += dense ? (verts + 7) / 8 * 8 : T;
+  }
+  lp.hash_mask = (uint32_t)(T - 1);
+  lp.L = f->L;
+  lp.E = (uint32_t)off;
+  return lp;
+}
+
+SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s) {
+  SampParams sp;
+  sp.S = s->n_samples;
+  sp.max_seg = effective_max_seg(f, s);
+  sp.max_chunk = max_chunks(s->n_samples, sp.max_seg);
+  sp.t_min = s->t_min;
+  return sp;
+}
+
+nerfxl_status launch_check(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(NERFXL_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return NERFXL_OK;
+}
+
+// Steps (a) and bucketing, shared by forward, backward and debug calls.
+nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t R, const float* rays_o,
+                           const float* rays_d, char* ws, const Layout& L, cudaStream_t stream) {
+  const int K = f->K;
+  if (cudaMemsetAsync(ws, 0, L.zero_end, stream) != cudaSuccess) return launch_check("workspace clear");
+  int32_t* hdr_words = reinterpret_cast<int32_t*>(ws + L.hdr);
+  const int threads = 256;
+  const int blocks = (int)((R + threads - 1) / threads);
+  if (R > 0) {
+    const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * K;
+    k_segments<<<blocks, threads, smem, stream>>>(rays_o, rays_d, R, f->boxes, K, sp,
+                                                  reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
+                                                  reinterpret_cast<SegDesc*>(ws + L.segs),
+                                                  reinterpret_cast<int32_t*>(ws + L.counts), hdr_words + 0);
+    nerfxl_status st = launch_check("k_segments");
+    if (st != NERFXL_OK) return st;
+  }
+  k_region_scan<<<1, 32, 0, stream>>>(reinterpret_cast<int32_t*>(ws + L.counts), K, kChunksPerTile,
+                                      reinterpret_cast<int32_t*>(ws + L.base), reinterpret_cast<uint2*>(ws + L.chunks),
+                                      hdr_words + 1);
+  nerfxl_status st = launch_check("k_region_scan");
+  if (st != NERFXL_OK) return st;
+  if (R > 0) {
+    k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 2 * K, stream>>>(
+        R, K, sp, reinterpret_cast<RayHdr*>(ws + L.ray_hdr), reinterpret_cast<SegDesc*>(ws + L.segs),
+        reinterpret_cast<int32_t*>(ws + L.base), reinterpret_cast<int32_t*>(ws + L.cursor),
+        reinterpret_cast<uint2*>(ws + L.chunks));
+    st = launch_check("k_fill_chunks");
+    if (st != NERFXL_OK) return st;
+  }
+  return NERFXL_OK;
+}
+
+cudaEvent_t g_prof[2] = {nullptr, nullptr};
+
+void profile_mark(int which, cudaStream_t stream) {
+  if (g_prof[which]) cudaEventRecord(g_prof[which], stream);
+}
+
+int fwd_grid(int64_t max_tiles, int ctas_per_sm) {
+  const int64_t g = (int64_t)num_sms() * ctas_per_sm;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, max_tiles));
+}
+
+}  // namespace nerfxl
+
+using namespace nerfxl;
+
+extern "C" {
+
+int64_t nerfxl_table_entries(const int32_t* level_res, int32_t L, int32_t log2_T) {
+  if (!level_res || L < 1 || L > NERFXL_MAX_LEVELS || log2_T < 1 || log2_T > 24) return -1;
+  const int64_t T = int64_t(1) << log2_T;
+  int64_t off = 0;
+  for (int l = 0; l < L; ++l) {
+    if (level_res[l] < 1) return -1;
+    const int64_t side = (int64_t)level_res[l] + 1;
+    const int64_t verts = side * side * side;
+    off += verts <= T ? (verts + 7) / 8 * 8 : T;
+  }
+  return off;
+}
+
+int64_t nerfxl_mlp_params(int32_t mlp_in, int32_t width) {
+  return (int64_t)mlp_in * width + (int64_t)width * width + (int64_t)width * 4;
+}
+
+int32_t nerfxl_max_chunks(const nerfxl_sampling* s, int32_t K) {
+  if (!s) return -1;
+  const int ms = s->max_segments > 0 ? s->max_segments : std::min<int>(K, kMaxSeg);
+  return max_chunks(s->n_samples, ms);
+}
+
+size_t nerfxl_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, int32_t for_backward) {
+  if (validate(f, s, n_rays) != NERFXL_OK) return 0;
+  return layout(f, s, n_rays, for_backward).total;
+}
+
+nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                const float* rays_o, const float* rays_d, float* rgb, float* depth, float* opacity,
+                                float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  nerfxl_status st = validate(f, s, n_rays);
+  if (st != NERFXL_OK) return st;
+  if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
+    return set_error(NERFXL_E_UNSUPPORTED, "this build renders FP32 tables with an FP32 MLP");
+  if (n_rays > 0 && (!rays_o || !rays_d || !rgb || !depth || !opacity))
+    return set_error(NERFXL_E_INVALID, "null ray or output pointer");
+  const Layout L = layout(f, s, n_rays, 0);
+  if (!workspace || ws_bytes < L.total) return set_error(NERFXL_E_WORKSPACE, "workspace too small");
+  char* ws = static_cast<char*>(workspace);
+  const SampParams sp = samp_params(f, s);
+  st = run_sampling(f, sp, n_rays, rays_o, rays_d, ws, L, stream);
+  if (st != NERFXL_OK) return st;
+  if (n_rays == 0) return NERFXL_OK;
+
+  FwdParams p;
+  p.rays_o = rays_o;
+  p.rays_d = rays_d;
+  p.fp.boxes = f->boxes;
+  p.fp.tables = static_cast<const float*>(f->tables);
+  p.fp.mlp = static_cast<const float*>(f->mlp);
+  p.lp = level_params(f);
+  p.sp = sp;
+  p.K = f->K;
+  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
+  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
+  p.base = reinterpret_cast<const int32_t*>(ws + L.base);
+  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
+  p.partials = reinterpret_cast<float4*>(ws + L.partials);
+  const size_t smem = sizeof(float) * kMlpParams + sizeof(int32_t) * (f->K + 1);
+  const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 4);
+  profile_mark(0, stream);
+  k_field_fwd_f32<<<grid, kFwdThreads, smem, stream>>>(p);
+  profile_mark(1, stream);
+  st = launch_check("k_field_fwd_f32");
+  if (st != NERFXL_OK) return st;
+  k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.partials, rgb, depth, opacity,
+                                                                dist);
+  return launch_check("k_composite");
+}
+
+nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!workspace || ws_bytes < 64) return set_error(NERFXL_E_WORKSPACE, "no workspace");
+  int32_t flags = 0;
+  if (cudaMemcpyAsync(&flags, workspace, sizeof(flags), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return launch_check("nerfxl_check");
+  if (flags & kErrOverflow) return set_error(NERFXL_E_OVERFLOW, "a ray crossed more regions than max_segments");
+  return NERFXL_OK;
+}
+
+nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int64_t* n_samples, int64_t* n_chunks,
+                                     cudaStream_t stream) {
+  if (!workspace || ws_bytes < 64) return set_error(NERFXL_E_WORKSPACE, "no workspace");
+  int64_t v[2] = {0, 0};
+  if (cudaMemcpyAsync(v, static_cast<const char*>(workspace) + 8, sizeof(v), cudaMemcpyDeviceToHost, stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return launch_check("nerfxl_workspace_stats");
+  if (n_samples) *n_samples = v[0];
+  if (n_chunks) *n_chunks = v[1];
+  return NERFXL_OK;
+}
+
+nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop) {
+  if ((start == nullptr) != (stop == nullptr)) return set_error(NERFXL_E_INVALID, "give both events or neither");
+  g_prof[0] = start;
+  g_prof[1] = stop;
+  return NERFXL_OK;
+}
+
+const char* nerfxl_last_error(void) { return last_error(); }
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// Host-side helpers shared by the translation units of libnerfxl.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+
+#include "nerfxl_device.cuh"
+
+namespace nerfxl {
+
+// Byte offsets of the workspace regions (each 256-byte aligned).
+struct Layout {
+  size_t hdr;        // int32[16]: [0] error flags, [1] tile count, [2..5] int64 samples, chunks
+  size_t counts;     // int32[K] chunks per region
+  size_t cursor;     // int32[K] fill cursors
+  size_t zero_end;   // [0, zero_end) is cleared at the start of each call
+  size_t base;       // int32[K+1] first chunk slot of each region bucket
+  size_t ray_hdr;    // RayHdr[R]
+  size_t segs;       // SegDesc[R][max_seg]
+  size_t chunks;     // uint2[chunk_cap]
+  size_t partials;   // float4[R][max_chunk][2]
+  size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
+  size_t total;
+  int64_t chunk_cap;
+  int max_seg, max_chunk;
+};
+
+const char* last_error();
+nerfxl_status set_error(nerfxl_status st, const std::string& msg);
+nerfxl_status launch_check(const char* what);
+nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R);
+int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s);
+int max_chunks(int S, int max_seg);
+Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int for_backward);
+LevelParams level_params(const nerfxl_field* f);
+SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s);
+nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t R, const float* rays_o,
+                           const float* rays_d, char* ws, const Layout& L, cudaStream_t stream);
+// Records the instrumentation event `which` (0 = before, 1 = after the
+// dominant kernel) if the caller installed one.
+void profile_mark(int which, cudaStream_t stream);
+int fwd_grid(int64_t max_tiles, int ctas_per_sm);
+
+}  // namespace nerfxl

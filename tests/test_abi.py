@@ -1,0 +1,70 @@
+"""The C-ABI library loads, exports every declared symbol, and validates its
+arguments on the host (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16221_b300 import build, native as N
+from paper_2404_16221_b300 import synthetic as sy
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return N.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = N.header_functions()
+    assert "nerfxl_render_fwd" in names and len(names) >= 8
+    raw = ctypes.CDLL(N.LIB_PATH)
+    for name in names:
+        assert hasattr(raw, name), name
+        assert name in N.SIGNATURES, "binding misses " + name
+
+
+@pytest.mark.parametrize("name", ["unit", "grid8", "city32"])
+def test_table_layout_agrees_with_oracle(lib, name):
+    # Two independent implementations of the level layout must agree.
+    w = sy.workload(name)
+    assert N.table_entries(w.level_res, w.log2_T) == oracle.table_entries(w.level_res, w.log2_T)
+    assert N.mlp_params(32, 64) == oracle.mlp_params(32, 64)
+
+
+def _desc(K=8, F=2, mlp_in=32, width=64, L=16):
+    d = N.FieldDesc()
+    d.K, d.L, d.F, d.log2_T, d.mlp_in, d.mlp_width = K, L, F, 19, mlp_in, width
+    for i in range(L):
+        d.level_res[i] = 16 + 8 * i
+    d.boxes = d.tables = d.mlp = 1  # never dereferenced: validation fails or no launch happens
+    return d
+
+
+def test_host_validation_rejects_bad_arguments(lib):
+    s = N.SamplingDesc(128, 4, 0.0, 0)
+    for kw, want in ((dict(K=0), N.E_INVALID), (dict(F=4), N.E_UNSUPPORTED), (dict(width=128), N.E_UNSUPPORTED),
+                     (dict(L=0), N.E_INVALID)):
+        d = _desc(**kw)
+        st = lib.nerfxl_render_fwd(ctypes.byref(d), ctypes.byref(s), 16, None, None, None, None, None, None, None, 0,
+                                   None)
+        assert st == want, (kw, st)
+        assert lib.nerfxl_last_error()
+    bad_s = N.SamplingDesc(0, 4, 0.0, 0)
+    d = _desc()
+    assert lib.nerfxl_render_fwd(ctypes.byref(d), ctypes.byref(bad_s), 16, None, None, None, None, None, None, None,
+                                 0, None) == N.E_INVALID
+    # workspace too small is refused before any launch
+    st = lib.nerfxl_render_fwd(ctypes.byref(d), ctypes.byref(s), 16, 1, 1, 1, 1, 1, 1, 1, 16, None)
+    assert st == N.E_WORKSPACE
+
+
+def test_workspace_size_grows_with_rays(lib):
+    d = _desc()
+    s = N.SamplingDesc(128, 4, 0.0, 0)
+    a = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0)
+    b = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 2000, 0)
+    c = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 2000, 1)
+    assert 0 < a < b < c
+    assert lib.nerfxl_max_chunks(ctypes.byref(s), 8) == 4 + 127 // 32

@@ -1,0 +1,176 @@
+"""Forward parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer decisions (segments, interval edges, hash indices) must match bit for
+bit; floating outputs within the FP32 tolerance |gpu - ref| <= 1e-5 (|ref| + s).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16221_b300 import synthetic as sy
+
+import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_16221_b300 import build
+
+    build.build()
+
+
+def _edge_rays(w, n):
+    """Workload rays plus ragged cases: misses, rays starting inside a box,
+    axis-parallel rays, and rays along shared faces."""
+    o, d = sy.workload_rays(w, n)
+    lo, hi = w.boxes[:, :3].min(0), w.boxes[:, 3:].max(0)
+    c = 0.5 * (lo + hi)
+    extra_o = [c + 3 * (hi - lo), c, c - np.array([0, 0, 2 * (hi[2] - lo[2])], np.float32),
+               np.array([lo[0] - 1, c[1], c[2]], np.float32), np.array([lo[0] - 1, lo[1] + 1e-3, c[2]], np.float32)]
+    extra_d = [np.array([1, 0, 0], np.float32), np.array([0.3, 0.5, 0.8], np.float32),
+               np.array([0, 0, 1], np.float32), np.array([1, 0, 0], np.float32), np.array([1, 0, 0], np.float32)]
+    extra_d = [v / np.linalg.norm(v) for v in extra_d]
+    return (np.concatenate([o, np.array(extra_o, np.float32)]),
+            np.concatenate([d, np.array(extra_d, np.float32)]))
+
+
+@pytest.mark.parametrize("name", ["unit", "grid8", "city32"])
+def test_segments_bit_exact(name):
+    w = H.workload(name, L=4, log2_T=12)
+    t, m = H.params(w)
+    of = H.oracle_field(w, t, m)
+    gf = H.gpu_field(w, t, m)
+    o, d = _edge_rays(w, 3000)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    from paper_2404_16221_b300 import api
+
+    gn, gr, g0, g1, gi = [x.cpu().numpy() for x in api.debug_segments(gf, H.sampling(w), o, d, w.K)]
+    np.testing.assert_array_equal(gn, nseg)
+    for r in range(len(o)):
+        k = nseg[r]
+        np.testing.assert_array_equal(gr[r, :k], region[r, :k])
+        np.testing.assert_array_equal(g0[r, :k].view(np.uint32), t0[r, :k].view(np.uint32))
+        np.testing.assert_array_equal(g1[r, :k].view(np.uint32), t1[r, :k].view(np.uint32))
+        np.testing.assert_array_equal(gi[r, :k], nint[r, :k])
+
+
+@pytest.mark.parametrize("name", ["unit", "grid8", "city32"])
+def test_intervals_and_hash_indices_bit_exact(name):
+    w = H.workload(name)
+    t, m = H.params(w)
+    of = H.oracle_field(w, t, m)
+    gf = H.gpu_field(w, t, m)
+    o, d = _edge_rays(w, 96)
+    max_int = w.S + w.max_segments - 1
+    from paper_2404_16221_b300 import api
+
+    cnt, a, b, reg = oracle.intervals(of, w.S, o, d, max_int)
+    idx = oracle.hash_indices(of, w.S, o, d, max_int)
+    gc, ga, gb, gr, gidx, gfeat, graw = api.debug_samples(gf, H.sampling(w), o, d, max_int, True, True, True)
+    gc, ga, gb, gr = gc.cpu().numpy(), ga.cpu().numpy(), gb.cpu().numpy(), gr.cpu().numpy()
+    gidx = gidx.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(gc, cnt)
+    mask = np.arange(max_int)[None, :] < cnt[:, None]
+    np.testing.assert_array_equal(ga[mask].view(np.uint32), a[mask].view(np.uint32))
+    np.testing.assert_array_equal(gb[mask].view(np.uint32), b[mask].view(np.uint32))
+    np.testing.assert_array_equal(gr[mask], reg[mask])
+    np.testing.assert_array_equal(gidx[mask], idx[mask])
+    # features and raw MLP outputs (FP32 vs FP64)
+    tb = 0.5 * (a + b)
+    x = (o[:, None, :] + tb[..., None].astype(np.float32) * d[:, None, :]).astype(np.float32)
+    feat = oracle.encode_points(of, reg[mask], x[mask])
+    gfe = gfeat.cpu().numpy()[mask]
+    assert H.rel_err(gfe, feat, 1.0) < 1e-5
+    raw = oracle.mlp(of, reg[mask], feat)
+    assert H.rel_err(graw.cpu().numpy()[mask], raw, 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("name,n", [("unit", 4096), ("grid8", 2048), ("city32", 1024)])
+def test_forward_matches_oracle(name, n):
+    w = H.workload(name, L=None if name != "city32" else 16, log2_T=None if name != "city32" else 16)
+    t, m = H.params(w)
+    of = H.oracle_field(w, t, m)
+    gf = H.gpu_field(w, t, m)
+    o, d = _edge_rays(w, n)
+    from paper_2404_16221_b300 import api
+
+    ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+    out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+    api.check(ws)
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = oracle.render(of, w.S, o, d, 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(o))])
+    errs = H.assert_forward_close(out, ref, t_far)
+    # misses are exactly black
+    miss = nseg == 0
+    assert miss.any()
+    assert np.all(out["rgb"][miss] == 0) and np.all(out["opacity"][miss] == 0) and np.all(out["depth"][miss] == 0)
+    print(name, errs)
+
+
+def test_forward_is_deterministic():
+    w = H.workload("grid8", L=8)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    o, d = sy.workload_rays(w, 8192)
+    from paper_2404_16221_b300 import api
+
+    a = api.render_fwd(gf, H.sampling(w), o, d)
+    b = api.render_fwd(gf, H.sampling(w), o, d)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_empty_batch():
+    w = H.workload("unit")
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    from paper_2404_16221_b300 import api
+
+    out = api.render_fwd(gf, H.sampling(w), np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    assert out["rgb"].shape == (0, 3)
+
+
+def test_overflow_is_reported():
+    """A ray crossing more regions than max_segments sets the device flag."""
+    w = H.workload("grid8", L=4, log2_T=12)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    from paper_2404_16221_b300 import api, native as N
+
+    samp = api.Sampling(w.S, 1)
+    o = np.array([[-2.0, -0.5, -0.5]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0]], np.float32)  # crosses two boxes
+    ws = api.alloc_workspace(gf, samp, 1)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    with pytest.raises(N.NerfxlError) as e:
+        api.check(ws)
+    assert e.value.status == N.E_OVERFLOW
+
+
+@pytest.mark.parametrize("name", ["grid8"])
+def test_full_size_forward_sampled_rays(name):
+    """The full workload (2^18 rays) in one launch; a seeded sample of rays
+    is checked against the oracle ray by ray."""
+    w = H.workload(name)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    o, d = sy.workload_rays(w)
+    from paper_2404_16221_b300 import api
+
+    ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+    out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+    api.check(ws)
+    sel = sy.subset(len(o), 2048, 99)
+    of = H.oracle_field(w, t, m)
+    ref = oracle.render(of, w.S, o[sel], d[sel], 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o[sel], d[sel])
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sel))])
+    got = {k: v.cpu().numpy()[sel] for k, v in out.items()}
+    H.assert_forward_close(got, ref, t_far)

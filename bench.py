@@ -203,6 +203,10 @@ def main():
     # the dominant kernel bracketed by the library's profile events.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for pair in kev:  # torch creates the CUDA event on first record
+        for e in pair:
+            e.record(stream)
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()

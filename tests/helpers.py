@@ -62,10 +62,11 @@ def assert_forward_close(out, ref, t_far, tol=1e-5):
     errs = {
         "rgb": rel_err(out["rgb"], ref["rgb"], 1.0),
         "opacity": rel_err(out["opacity"], ref["opacity"], 1.0),
+        # a missed ray has t_far = 0 and must render depth 0 exactly
         "depth": float(np.max(np.abs(np.asarray(out["depth"], np.float64) - ref["depth"]) /
-                              (np.abs(ref["depth"]) + t_far))) if len(t_far) else 0.0,
+                              (np.abs(ref["depth"]) + np.where(t_far > 0, t_far, 1.0)))) if len(t_far) else 0.0,
         "dist": rel_err(out["dist"], ref["dist"], max(float(np.max(np.abs(ref["dist"]))), 1e-30)),
     }
-    bad = {k: v for k, v in errs.items() if v > tol}
+    bad = {k: v for k, v in errs.items() if not v <= tol}  # NaN counts as a failure
     assert not bad, errs
     return errs

@@ -123,6 +123,23 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
                                 float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream);
 
 /*
+ * Forward render without a caller workspace (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory, such as plain C
+ * programs or plug-ins without an allocator, hosts that own the whole device
+ * memory pool, or frame loops where cudaMalloc would stall). Same inputs,
+ * outputs and results as nerfxl_render_fwd; the scratch comes from a fixed
+ * 32 MiB array in the library's device image, reserved on every GPU that
+ * loads the library until exit. Batches needing more scratch are refused
+ * with NERFXL_E_WORKSPACE (grid8-sized rays: roughly 90 thousand per call).
+ * The first call on a device looks up the array's address; make it before
+ * any stream capture. Calls share the array: calls that overlap on the GPU
+ * race, so order them on one stream. Allocates nothing.
+ */
+nerfxl_status nerfxl_render_fwd_static(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                       const float* rays_o, const float* rays_d, float* rgb, float* depth,
+                                       float* opacity, float* dist, cudaStream_t stream);
+
+/*
  * Status of device-side checks of the last call made with this workspace
  * (synchronises the stream): NERFXL_OK or NERFXL_E_OVERFLOW.
  */

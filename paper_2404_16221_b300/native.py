@@ -53,6 +53,7 @@ SIGNATURES = {
     "nerfxl_workspace_bytes": (_sz, [_FP, _SP, _i64, _i32]),
     "nerfxl_render_fwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_check": (C.c_int, [_vp, _sz, _vp]),
+    "nerfxl_render_fwd_static": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nerfxl_last_error": (C.c_char_p, []),
     "nerfxl_workspace_stats": (C.c_int, [_vp, _sz, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]),
     "nerfxl_set_profile_events": (C.c_int, [_vp, _vp]),

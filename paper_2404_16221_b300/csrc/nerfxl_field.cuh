@@ -28,10 +28,20 @@ __device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* 
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
     float2 v[8];
+    const float2* tl = table + lp.off[l];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const uint32_t idx = vertex_index(lp, l, c[0] + (e & 1), c[1] + ((e >> 1) & 1), c[2] + ((e >> 2) & 1));
-      v[e] = __ldg(table + lp.off[l] + idx);
+    for (int e = 0; e < 8; e += 2) {
+      // x-neighbour pair: one aligned 16-byte load covers both corners when
+      // their indices differ only in bit 0 (even x for hashed levels, even
+      // index for dense ones); otherwise a second 8-byte load.
+      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+      const float4 q = __ldg(reinterpret_cast<const float4*>(tl + (i0 & ~1u)));
+      const bool odd = i0 & 1u;
+      v[e] = odd ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+      if ((i0 ^ i1) == 1u) v[e + 1] = odd ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+      else v[e + 1] = __ldg(tl + i1);
     }
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll

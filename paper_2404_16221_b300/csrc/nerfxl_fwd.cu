@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
 }
 
 // ---------------------------------------------------------------------------
-// k_field_fwd (FP32): persistent CTAs, contiguous tile ranges; warp w of a
+// k_field_fwd (FP32): persistent CTAs over interleaved tiles; warp w of a
 // tile handles chunk 4 * tile + w. Weights are reloaded only when the tile's
 // region changes.
 
@@ -188,13 +188,13 @@ __global__ void __launch_bounds__(kFwdThreads, 4) k_field_fwd_f32(FwdParams p) {
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   __syncthreads();
   const int n_tiles = *p.n_tiles;
-  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const int t_begin = blockIdx.x * per;
-  const int t_end = min(n_tiles, t_begin + per);
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   int region = -1;
   const float2* table = nullptr;
-  for (int t = t_begin; t < t_end; ++t) {
+  // Interleaved tiles: at any moment the whole GPU works on neighbouring
+  // tiles of the region-major list, i.e. on one region whose tables then stay
+  // resident in L2; a CTA switches region (and reloads weights) about K times.
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int chunk = t * kChunksPerTile + warp;
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     if (k != region) {

@@ -123,6 +123,75 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
                                 float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream);
 
 /*
+ * Backward (adjoint) render. Given dL/d(output) per ray (any of d_rgb [R][3],
+ * d_depth, d_opacity, d_dist [R] may be NULL, meaning zero), ACCUMULATES the
+ * gradient into grad_tables [K][E][F] and grad_mlp [K][P] (FP32, caller
+ * zeroes them). The workspace must be the one of the immediately preceding
+ * nerfxl_render_fwd on the same field and rays, sized with for_backward=1 and
+ * unmodified since. Per-sample activations are recomputed, not stored.
+ * Gradient accumulation order is unspecified (FP32 atomics), so results vary
+ * in the last bits between runs. Loss gradients reach each region's
+ * parameters only through that region's own samples (Sec. 4.2).
+ */
+nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                const float* rays_o, const float* rays_d, const float* d_rgb, const float* d_depth,
+                                const float* d_opacity, const float* d_dist, float* grad_tables, float* grad_mlp,
+                                void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Loss L = mean_{r,c} (rgb - target)^2 + lambda * mean_r dist (Sec. 4.1:
+ * photometric L2 plus the distortion regulariser of Eq. 2). Writes
+ * loss_out[3] = {L, photometric term, mean distortion} and, where non-NULL,
+ * the output adjoints d_rgb [R][3] and d_dist [R]. scratch holds
+ * ceil(R/256) float2 block sums. Deterministic (fixed reduction order).
+ */
+nerfxl_status nerfxl_loss(int64_t n_rays, const float* rgb, const float* dist, const float* target_rgb,
+                          float lambda_dist, float* d_rgb, float* d_dist, float* loss_out, void* scratch,
+                          size_t scratch_bytes, cudaStream_t stream);
+
+/* Adam hyper-parameters of one update; step is 1-based. */
+typedef struct nerfxl_adam {
+  float lr, beta1, beta2, eps;
+  int64_t step;
+} nerfxl_adam;
+
+/*
+ * One Adam step (Kingma & Ba, bias-corrected) over n FP32 parameters, in
+ * place. If copy_dtype is NERFXL_F16 or NERFXL_BF16 the updated values are
+ * also written, rounded, to compute_copy (the reduced-precision parameters
+ * the render kernels read).
+ */
+nerfxl_status nerfxl_adam_update(int64_t n, float* params, const float* grads, float* m, float* v,
+                                 const nerfxl_adam* opt, void* compute_copy, int32_t copy_dtype, cudaStream_t stream);
+
+/* FP32 master parameters, their gradients and Adam moments (all [K][E][F] / [K][P]). */
+typedef struct nerfxl_train_state {
+  float* tables;
+  float* mlp;
+  float* grad_tables;
+  float* grad_mlp;
+  float* m_tables;
+  float* v_tables;
+  float* m_mlp;
+  float* v_mlp;
+} nerfxl_train_state;
+
+/* Workspace of nerfxl_step for R rays. */
+size_t nerfxl_step_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays);
+
+/*
+ * One training step: clear gradients, forward render, loss (lambda_dist
+ * weighs the distortion term), backward, Adam on tables and MLP. loss_out[3]
+ * as nerfxl_loss (the loss of the parameters before the update). For the FP32
+ * path the field must point at the masters (f->tables == st->tables,
+ * f->mlp == st->mlp).
+ */
+nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
+                          const float* rays_d, const float* target_rgb, float lambda_dist,
+                          const nerfxl_train_state* st, const nerfxl_adam* opt, float* loss_out, void* workspace,
+                          size_t ws_bytes, cudaStream_t stream);
+
+/*
  * Forward render without a caller workspace (the paper has no counterpart:
  * this serves callers that cannot allocate device memory, such as plain C
  * programs or plug-ins without an allocator, hosts that own the whole device

@@ -148,3 +148,103 @@ def debug_samples(field: PartitionedField, samp: Sampling, rays_o, rays_d, max_i
                                       N._stream(None))
     N.check(st, "nerfxl_debug_samples")
     return count, a, b, region, idx, feat, raw
+
+
+def render_bwd(field: PartitionedField, samp: Sampling, rays_o, rays_d, workspace, d_rgb=None, d_depth=None,
+               d_opacity=None, d_dist=None, grad_tables=None, grad_mlp=None, stream=None):
+    """Adjoint render. ``workspace`` must come from the matching render_fwd
+    (allocated with for_backward=True). Gradients are accumulated into
+    grad_tables [K][E][F] and grad_mlp [K][P] (FP32; zero-filled if None)."""
+    o, d = _rays(rays_o, rays_d, field.device)
+    R = o.shape[0]
+    if grad_tables is None:
+        grad_tables = torch.zeros(field.K, field.E, field.F, dtype=torch.float32, device=field.device)
+    if grad_mlp is None:
+        grad_mlp = torch.zeros(field.K, field.P, dtype=torch.float32, device=field.device)
+
+    def c(t):
+        return None if t is None else t.contiguous()
+
+    d_rgb, d_depth, d_opacity, d_dist = c(d_rgb), c(d_depth), c(d_opacity), c(d_dist)
+    fd, sd = field.desc(), samp.desc()
+    st = N.lib().nerfxl_render_bwd(C_ref(fd), C_ref(sd), R, N._ptr(o), N._ptr(d), N._ptr(d_rgb), N._ptr(d_depth),
+                                   N._ptr(d_opacity), N._ptr(d_dist), N._ptr(grad_tables), N._ptr(grad_mlp),
+                                   N._ptr(workspace), workspace.numel(), N._stream(stream))
+    N.check(st, "nerfxl_render_bwd")
+    return grad_tables, grad_mlp
+
+
+def loss(rgb, dist, target, lam: float, want_grads: bool = True, stream=None):
+    """Returns (loss[3] device tensor, d_rgb, d_dist)."""
+    R = rgb.shape[0]
+    dev = rgb.device
+    out = torch.empty(3, dtype=torch.float32, device=dev)
+    d_rgb = torch.empty_like(rgb) if want_grads else None
+    d_dist = torch.empty(R, dtype=torch.float32, device=dev) if want_grads else None
+    scratch = torch.empty(max(1, (R + 255) // 256) * 8, dtype=torch.uint8, device=dev)
+    tgt = torch.as_tensor(target, dtype=torch.float32).to(dev).contiguous()
+    st = N.lib().nerfxl_loss(R, N._ptr(rgb.contiguous()), N._ptr(None if dist is None else dist.contiguous()),
+                             N._ptr(tgt), float(lam), N._ptr(d_rgb), N._ptr(d_dist), N._ptr(out), N._ptr(scratch),
+                             scratch.numel(), N._stream(stream))
+    N.check(st, "nerfxl_loss")
+    return out, d_rgb, d_dist
+
+
+def adam_update(params, grads, m, v, step: int, lr: float, beta1=0.9, beta2=0.99, eps=1e-15, compute_copy=None,
+                stream=None):
+    """In-place Adam on FP32 tensors; refreshes an fp16/bf16 compute copy if given."""
+    opt = N.AdamDesc(float(lr), float(beta1), float(beta2), float(eps), int(step))
+    code = N.F32 if compute_copy is None else _DTYPE_CODE[compute_copy.dtype]
+    st = N.lib().nerfxl_adam_update(params.numel(), N._ptr(params), N._ptr(grads), N._ptr(m), N._ptr(v),
+                                    ctypes_addr(opt), N._ptr(compute_copy), code, N._stream(stream))
+    N.check(st, "nerfxl_adam_update")
+
+
+def ctypes_addr(x):
+    import ctypes
+
+    return ctypes.cast(ctypes.pointer(x), ctypes.c_void_p)
+
+
+class Trainer:
+    """FP32 master parameters + Adam moments; nerfxl_step does fwd, loss, bwd
+    and the update in one call."""
+
+    def __init__(self, field: PartitionedField, samp: Sampling, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
+                 lambda_dist=0.01):
+        if field.tables.dtype != torch.float32 or field.mlp.dtype != torch.float32:
+            raise ValueError("the FP32 trainer renders from FP32 masters")
+        self.field, self.samp = field, samp
+        self.lr, self.beta1, self.beta2, self.eps, self.lambda_dist = lr, beta1, beta2, eps, lambda_dist
+        z = torch.zeros_like
+        self.grad_tables, self.grad_mlp = z(field.tables), z(field.mlp)
+        self.m_tables, self.v_tables = z(field.tables), z(field.tables)
+        self.m_mlp, self.v_mlp = z(field.mlp), z(field.mlp)
+        self.step_count = 0
+        self._ws = None
+        self.loss = torch.zeros(3, dtype=torch.float32, device=field.device)
+
+    def state_desc(self) -> N.TrainStateDesc:
+        f = self.field
+        return N.TrainStateDesc(f.tables.data_ptr(), f.mlp.data_ptr(), self.grad_tables.data_ptr(),
+                                self.grad_mlp.data_ptr(), self.m_tables.data_ptr(), self.v_tables.data_ptr(),
+                                self.m_mlp.data_ptr(), self.v_mlp.data_ptr())
+
+    def step(self, rays_o, rays_d, target, stream=None):
+        o, d = _rays(rays_o, rays_d, self.field.device)
+        tgt = torch.as_tensor(target, dtype=torch.float32).to(self.field.device).reshape(-1, 3).contiguous()
+        R = o.shape[0]
+        fd, sd = self.field.desc(), self.samp.desc()
+        need = int(N.lib().nerfxl_step_workspace_bytes(C_ref(fd), C_ref(sd), R))
+        if need == 0:
+            N.check(N.E_INVALID, "nerfxl_step_workspace_bytes")
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.field.device)
+        self.step_count += 1
+        opt = N.AdamDesc(float(self.lr), float(self.beta1), float(self.beta2), float(self.eps), self.step_count)
+        stt = self.state_desc()
+        st = N.lib().nerfxl_step(C_ref(fd), C_ref(sd), R, N._ptr(o), N._ptr(d), N._ptr(tgt), float(self.lambda_dist),
+                                 ctypes_addr(stt), ctypes_addr(opt), N._ptr(self.loss), N._ptr(self._ws),
+                                 self._ws.numel(), N._stream(stream))
+        N.check(st, "nerfxl_step")
+        return self.loss

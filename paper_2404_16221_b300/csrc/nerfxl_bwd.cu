@@ -1,0 +1,484 @@
+// Backward (adjoint) pass of the one-GPU NeRF-XL hot path (arXiv 2404.16221).
+//
+// The forward keeps only per-ray headers, segments, the region buckets and
+// the chunk partials; per-sample activations are recomputed here, never
+// stored. Gradients of the loss reach a region's parameters only through
+// that region's own samples (Sec. 4.2: each loss lives in a graph that only
+// differentiates its local parameters), which on one GPU simply means the
+// scatter targets the sample's own region block.
+//
+//   k_composite_bwd  per ray: reverse of Algorithm 1+2 over the chunk partials
+//                    -> adjoints of every chunk partial (tau, C, A, D', L)
+//   k_field_bwd_f32  persistent CTAs over the same tiles as the forward:
+//                    recompute gather + MLP, chunk-local render adjoint (warp
+//                    scans), MLP backward, weight gradients as CTA GEMMs over
+//                    the tile's 256 samples (accumulated in shared memory per
+//                    region), table gradients by vector atomics.
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "nerfxl_field.cuh"
+#include "nerfxl_host.h"
+
+namespace nerfxl {
+
+// ---------------------------------------------------------------------------
+// k_composite_bwd. Forward step c (state before it: P_c, A_<c, D_<c):
+//   L += P_c^2 L_c + 2 P_c (D_c A_<c - A_c D_<c);  C += P_c C_c;
+//   A += P_c A_c;  D += P_c D_c;  P_{c+1} = P_c exp(-tau_c).
+// Reverse, with adjoints gC, gA, gD, gL of the accumulators and gP of P_{c+1}:
+//   g tau_c = -gP P_{c+1};  gP <- gP exp(-tau_c) + gC.C_c + gA A_c + gD D_c
+//                                 + gL (2 P_c L_c + 2 S_c);
+//   gC_c = P_c gC;  gA_c = P_c gA - 2 gL P_c D_<c;  gD_c = P_c gD + 2 gL P_c A_<c;
+//   gL_c = P_c^2 gL;  then gA += 2 gL P_c D_c, gD -= 2 gL P_c A_c for earlier steps.
+// depth = D' + A tn (D' relative to tn), so gA gets gdepth * tn.
+
+__global__ void __launch_bounds__(256) k_composite_bwd(int64_t R, SampParams sp, const RayHdr* __restrict__ hdr,
+                                                       const float4* __restrict__ partials,
+                                                       const float* __restrict__ d_rgb,
+                                                       const float* __restrict__ d_depth,
+                                                       const float* __restrict__ d_opacity,
+                                                       const float* __restrict__ d_dist, float4* __restrict__ dpart) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const RayHdr h = hdr[r];
+  const float4* src = partials + 2 * (size_t)r * sp.max_chunk;
+  float4* dst = dpart + 2 * (size_t)r * sp.max_chunk;
+  // forward sweep: remember P_c, A_<c, D_<c of every chunk (in the adjoint slots)
+  float P = 1.0f, tau = 0.0f, comp = 0.0f, A = 0.0f, D = 0.0f;
+  for (int c = 0; c < h.nchunk; ++c) {
+    const float4 q0 = src[2 * c], q1 = src[2 * c + 1];
+    dst[2 * c] = make_float4(P, A, D, 0.0f);
+    A += P * q1.x;
+    D += P * q1.y;
+    const float y = q0.x - comp;
+    const float s = tau + y;
+    comp = (s - tau) - y;
+    tau = s;
+    P = expf(-tau);
+  }
+  float gC0 = d_rgb ? d_rgb[3 * r + 0] : 0.0f;
+  float gC1 = d_rgb ? d_rgb[3 * r + 1] : 0.0f;
+  float gC2 = d_rgb ? d_rgb[3 * r + 2] : 0.0f;
+  const float gdep = d_depth ? d_depth[r] : 0.0f;
+  float gA = (d_opacity ? d_opacity[r] : 0.0f) + gdep * h.tn;
+  float gD = gdep;
+  const float gL = d_dist ? d_dist[r] : 0.0f;
+  float gP = 0.0f;        // adjoint of P_{c+1}
+  float P_next = P;       // P_{c+1}
+  for (int c = h.nchunk - 1; c >= 0; --c) {
+    const float4 st = dst[2 * c];
+    const float Pc = st.x, Ab = st.y, Db = st.z;
+    const float4 q0 = src[2 * c], q1 = src[2 * c + 1];
+    const float tc = q0.x, Ac = q1.x, Dc = q1.y, Lc = q1.z;
+    const float g_tau = -gP * P_next;
+    const float S = Dc * Ab - Ac * Db;
+    const float gPc = gP * expf(-tc) + gC0 * q0.y + gC1 * q0.z + gC2 * q0.w + gA * Ac + gD * Dc +
+                      gL * (2.0f * Pc * Lc + 2.0f * S);
+    const float gAc = Pc * gA - 2.0f * gL * Pc * Db;
+    const float gDc = Pc * gD + 2.0f * gL * Pc * Ab;
+    dst[2 * c] = make_float4(g_tau, Pc * gC0, Pc * gC1, Pc * gC2);
+    dst[2 * c + 1] = make_float4(gAc, gDc, Pc * Pc * gL, 0.0f);
+    gA += 2.0f * gL * Pc * Dc;
+    gD -= 2.0f * gL * Pc * Ac;
+    gP = gPc;
+    P_next = Pc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_field_bwd_f32
+
+constexpr int kBwdThreads = kChunksPerTile * kWarp;  // 256 samples per tile
+constexpr int kFeatPitch = 36;                        // cols 32..35 hold dL/d(raw outputs)
+constexpr int kActPitch = 68;
+
+struct BwdParams {
+  const float* rays_o;
+  const float* rays_d;
+  FieldPtrs fp;
+  LevelParams lp;
+  SampParams sp;
+  int K;
+  const RayHdr* hdr;
+  const SegDesc* segs;
+  const int32_t* base;
+  const uint2* chunks;
+  const int32_t* n_tiles;
+  const float4* dpart;   // chunk partial adjoints
+  float* grad_tables;    // [K][E][2] accumulated
+  float* grad_mlp;       // [K][kMlpParams] accumulated
+};
+
+constexpr size_t kBwdSmemFloats =
+    2 * kMlpParams + (size_t)kBwdThreads * kFeatPitch + 2 * (size_t)kBwdThreads * kActPitch;
+
+// Adjoint of the chunk-local render for one warp (one chunk). Inputs per lane:
+// sigma, rgb, t' (tbar - tn), delta; chunk adjoints gtc, gC, gA, gD, gL.
+// Returns dL/d(sigma), dL/d(rgb).
+__device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rgb[3], float tr, float dl, int lane,
+                                                     float gtc, const float gC[3], float gA, float gD, float gL,
+                                                     float& g_sigma, float g_rgb[3]) {
+  const float tau = sigma * dl;
+  const float incl = warp_inclusive_scan(tau, lane);
+  const float excl = warp_exclusive_from_inclusive(incl, lane);
+  const float T = expf(-excl);
+  const float Tn = expf(-incl);
+  const float w = T * -expm1f(-tau);
+  const float wt = w * tr;
+  const float W_in = warp_inclusive_scan(w, lane);
+  const float WT_in = warp_inclusive_scan(wt, lane);
+  const float W_lt = warp_exclusive_from_inclusive(W_in, lane);
+  const float WT_lt = warp_exclusive_from_inclusive(WT_in, lane);
+  const float W_gt = warp_suffix_scan(w, lane) - w;
+  const float WT_gt = warp_suffix_scan(wt, lane) - wt;
+  // sum_j w_j |t_i - t_j| over the chunk
+  const float pair = (tr * W_lt - WT_lt) + (WT_gt - tr * W_gt);
+  const float gw = gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2] + gA + gD * tr +
+                   gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
+  const float gww = gw * w;
+  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
+  const float g_tau = gtc + gw * Tn - later;
+  g_sigma = g_tau * dl;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g_rgb[q] = w * gC[q];
+}
+
+// Scatter dL/dfeat into the region table: entry += corner weight * gfeat.
+__device__ __forceinline__ void scatter_table_grad(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
+                                                   const float gfeat[kIn]) {
+#pragma unroll
+  for (int l = 0; l < kIn / 2; ++l) {
+    if (l >= lp.L) break;
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+    float2* gl = gtab + lp.off[l];
+    const float g0 = gfeat[2 * l], g1 = gfeat[2 * l + 1];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+      const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+      const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+      if ((i0 ^ i1) == 1u) {
+        // both corners in one aligned pair: one 16-byte atomic
+        const bool odd = i0 & 1u;
+        const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
+                             : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
+        atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
+      } else {
+        atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
+        atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, float* __restrict__ g) {
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+    const float v = s_acc[i];
+    if (v != 0.0f) atomicAdd(g + i, v);
+  }
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
+  extern __shared__ __align__(16) float sm[];
+  float* s_w = sm;                                       // W1t [64][32], W2t [64][64], W3 [64][4]
+  float* s_acc = s_w + kMlpParams;                       // gW1 [32][64], gW2 [64][64], gW3 [64][4]
+  float* s_feat = s_acc + kMlpParams;                    // [256][36]
+  float* s_P = s_feat + kBwdThreads * kFeatPitch;        // [256][68]
+  float* s_Q = s_P + kBwdThreads * kActPitch;            // [256][68]
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_Q + kBwdThreads * kActPitch);
+  for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  __syncthreads();
+  const int n_tiles = *p.n_tiles;
+  const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+  const float4* W1t4 = reinterpret_cast<const float4*>(s_w);
+  const float4* W2t4 = reinterpret_cast<const float4*>(s_w + kIn * kWidth);
+  const float4* W34 = reinterpret_cast<const float4*>(s_w + kIn * kWidth + kWidth * kWidth);
+  float* gW1 = s_acc;
+  float* gW2 = s_acc + kIn * kWidth;
+  float* gW3 = gW2 + kWidth * kWidth;
+  int region = -1;
+  const float2* table = nullptr;
+  float2* gtab = nullptr;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
+    __syncthreads();  // previous tile's shared buffers fully consumed
+    if (k != region) {
+      if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
+      __syncthreads();
+      load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
+      for (int i = tid; i < kMlpParams; i += blockDim.x) s_acc[i] = 0.0f;
+      __syncthreads();
+      region = k;
+      table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
+      gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+    }
+    const uint2 ref = p.chunks[t * kChunksPerTile + warp];
+    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
+    bool valid = false;
+    float feat[kIn], u[3];
+    float tr = 0.0f, dl = 0.0f;
+    float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+    if (chunk_ok) {
+      const uint32_t ray = ref.x;
+      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+      const RayHdr h = p.hdr[ray];
+      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+      const float4 g0 = p.dpart[2 * slot], g1 = p.dpart[2 * slot + 1];
+      gtc = g0.x;
+      gC[0] = g0.y;
+      gC[1] = g0.z;
+      gC[2] = g0.w;
+      gA = g1.x;
+      gD = g1.y;
+      gL = g1.z;
+      const int i = c * kWarp + lane;
+      valid = i < seg_n(sd);
+      if (valid) {
+        float o[3], d[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          o[ax] = p.rays_o[3 * (size_t)ray + ax];
+          d[ax] = p.rays_d[3 * (size_t)ray + ax];
+        }
+        float a, b;
+        segment_interval(sd, h.tn, h.delta, i, a, b);
+        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        dl = __fsub_rn(b, a);
+        tr = __fsub_rn(tbar, h.tn);
+        float x[3];
+        sample_point(o, d, tbar, x);
+        region_coord(p.fp.boxes + 6 * k, x, u);
+        encode_f32(p.lp, table, u, feat);
+      }
+    }
+    // ---- forward recompute: feat -> h1 (s_P) -> h2 (s_Q) -> raw outputs
+    float* my_feat = s_feat + tid * kFeatPitch;
+    float* my_P = s_P + tid * kActPitch;
+    float* my_Q = s_Q + tid * kActPitch;
+#pragma unroll
+    for (int q = 0; q < kIn; q += 4)
+      *reinterpret_cast<float4*>(my_feat + q) = make_float4(feat[q], feat[q + 1], feat[q + 2], feat[q + 3]);
+    float h1[kWidth];
+#pragma unroll
+    for (int n = 0; n < kWidth; ++n) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i4 = 0; i4 < kIn / 4; ++i4) {
+        const float4 wv = W1t4[n * (kIn / 4) + i4];
+        acc = fmaf(feat[4 * i4], wv.x, acc);
+        acc = fmaf(feat[4 * i4 + 1], wv.y, acc);
+        acc = fmaf(feat[4 * i4 + 2], wv.z, acc);
+        acc = fmaf(feat[4 * i4 + 3], wv.w, acc);
+      }
+      h1[n] = fmaxf(acc, 0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_P + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
+    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, o3 = 0.0f;
+#pragma unroll 2
+    for (int n = 0; n < kWidth; ++n) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
+        const float4 wv = W2t4[n * (kWidth / 4) + i4];
+        acc = fmaf(h1[4 * i4], wv.x, acc);
+        acc = fmaf(h1[4 * i4 + 1], wv.y, acc);
+        acc = fmaf(h1[4 * i4 + 2], wv.z, acc);
+        acc = fmaf(h1[4 * i4 + 3], wv.w, acc);
+      }
+      const float h2 = fmaxf(acc, 0.0f);
+      my_Q[n] = h2;
+      const float4 w3 = W34[n];
+      o0 = fmaf(h2, w3.x, o0);
+      o1 = fmaf(h2, w3.y, o1);
+      o2 = fmaf(h2, w3.z, o2);
+      o3 = fmaf(h2, w3.w, o3);
+    }
+    // ---- chunk-local render adjoint -> dL/d(raw outputs)
+    float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+      sigma = expf(o0);
+      rgb[0] = 1.0f / (1.0f + expf(-o1));
+      rgb[1] = 1.0f / (1.0f + expf(-o2));
+      rgb[2] = 1.0f / (1.0f + expf(-o3));
+    }
+    float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+    float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (valid) {
+      go[0] = g_sigma * sigma;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) go[1 + q] = g_rgb[q] * rgb[q] * (1.0f - rgb[q]);
+    }
+    *reinterpret_cast<float4*>(my_feat + kIn) = make_float4(go[0], go[1], go[2], go[3]);
+    __syncthreads();
+    // ---- gW3[n][m] += sum_s h2[s][n] go[s][m]   (one output per thread)
+    {
+      const int n = tid >> 2, m = tid & 3;
+      float acc = 0.0f;
+      for (int s = 0; s < kBwdThreads; ++s) acc = fmaf(s_Q[s * kActPitch + n], s_feat[s * kFeatPitch + kIn + m], acc);
+      gW3[n * kOut + m] += acc;
+    }
+    __syncthreads();
+    // ---- dL/dz2 (into s_Q) and dL/dh1 = W2 dz2
+    float gh1[kWidth];
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) gh1[i] = 0.0f;
+#pragma unroll 2
+    for (int n = 0; n < kWidth; ++n) {
+      const float4 w3 = W34[n];
+      const float gz2 = my_Q[n] > 0.0f ? w3.x * go[0] + w3.y * go[1] + w3.z * go[2] + w3.w * go[3] : 0.0f;
+      my_Q[n] = gz2;
+#pragma unroll
+      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
+        const float4 wv = W2t4[n * (kWidth / 4) + i4];  // W2[4 i4 + j][n]
+        gh1[4 * i4] = fmaf(wv.x, gz2, gh1[4 * i4]);
+        gh1[4 * i4 + 1] = fmaf(wv.y, gz2, gh1[4 * i4 + 1]);
+        gh1[4 * i4 + 2] = fmaf(wv.z, gz2, gh1[4 * i4 + 2]);
+        gh1[4 * i4 + 3] = fmaf(wv.w, gz2, gh1[4 * i4 + 3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) gh1[i] = my_P[i] > 0.0f ? gh1[i] : 0.0f;  // dL/dz1
+    __syncthreads();
+    // ---- gW2[i][n] += sum_s h1[s][i] dz2[s][n]   (16 outputs per thread)
+    {
+      const int i = tid >> 2, n0 = (tid & 3) * 16;
+      float acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float hv = s_P[s * kActPitch + i];
+        const float4* qr = reinterpret_cast<const float4*>(s_Q + s * kActPitch + n0);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 v = qr[q4];
+          acc[4 * q4] = fmaf(hv, v.x, acc[4 * q4]);
+          acc[4 * q4 + 1] = fmaf(hv, v.y, acc[4 * q4 + 1]);
+          acc[4 * q4 + 2] = fmaf(hv, v.z, acc[4 * q4 + 2]);
+          acc[4 * q4 + 3] = fmaf(hv, v.w, acc[4 * q4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) gW2[i * kWidth + n0 + q] += acc[q];
+    }
+    __syncthreads();
+    // ---- dz1 into s_P; dL/dfeat = W1 dz1
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_P + q) = make_float4(gh1[q], gh1[q + 1], gh1[q + 2], gh1[q + 3]);
+    float gfeat[kIn];
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) gfeat[j] = 0.0f;
+#pragma unroll
+    for (int n = 0; n < kWidth; ++n) {
+#pragma unroll
+      for (int i4 = 0; i4 < kIn / 4; ++i4) {
+        const float4 wv = W1t4[n * (kIn / 4) + i4];  // W1[4 i4 + j][n]
+        gfeat[4 * i4] = fmaf(wv.x, gh1[n], gfeat[4 * i4]);
+        gfeat[4 * i4 + 1] = fmaf(wv.y, gh1[n], gfeat[4 * i4 + 1]);
+        gfeat[4 * i4 + 2] = fmaf(wv.z, gh1[n], gfeat[4 * i4 + 2]);
+        gfeat[4 * i4 + 3] = fmaf(wv.w, gh1[n], gfeat[4 * i4 + 3]);
+      }
+    }
+    __syncthreads();
+    // ---- gW1[j][n] += sum_s feat[s][j] dz1[s][n]   (8 outputs per thread)
+    {
+      const int j = tid >> 3, n0 = (tid & 7) * 8;
+      float acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float fv = s_feat[s * kFeatPitch + j];
+        const float4* qr = reinterpret_cast<const float4*>(s_P + s * kActPitch + n0);
+#pragma unroll
+        for (int q4 = 0; q4 < 2; ++q4) {
+          const float4 v = qr[q4];
+          acc[4 * q4] = fmaf(fv, v.x, acc[4 * q4]);
+          acc[4 * q4 + 1] = fmaf(fv, v.y, acc[4 * q4 + 1]);
+          acc[4 * q4 + 2] = fmaf(fv, v.z, acc[4 * q4 + 2]);
+          acc[4 * q4 + 3] = fmaf(fv, v.w, acc[4 * q4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) gW1[j * kWidth + n0 + q] += acc[q];
+    }
+    // ---- table gradients
+    if (valid) scatter_table_grad(p.lp, gtab, u, gfeat);
+  }
+  __syncthreads();
+  if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
+}
+
+}  // namespace nerfxl
+
+using namespace nerfxl;
+
+extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
+                                           const float* rays_o, const float* rays_d, const float* d_rgb,
+                                           const float* d_depth, const float* d_opacity, const float* d_dist,
+                                           float* grad_tables, float* grad_mlp, void* workspace, size_t ws_bytes,
+                                           cudaStream_t stream) {
+  nerfxl_status st = validate(f, s, n_rays);
+  if (st != NERFXL_OK) return st;
+  if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
+    return set_error(NERFXL_E_UNSUPPORTED, "the FP32 backward reads FP32 parameters");
+  if (n_rays > 0 && (!rays_o || !rays_d || !grad_tables || !grad_mlp))
+    return set_error(NERFXL_E_INVALID, "null ray or gradient pointer");
+  const Layout L = layout(f, s, n_rays, 1);
+  if (!workspace || ws_bytes < L.total)
+    return set_error(NERFXL_E_WORKSPACE, "backward needs the forward's workspace sized with for_backward=1");
+  if (n_rays == 0) return NERFXL_OK;
+  char* ws = static_cast<char*>(workspace);
+  const SampParams sp = samp_params(f, s);
+  float4* dpart = reinterpret_cast<float4*>(ws + L.dpartials);
+  k_composite_bwd<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
+      n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
+      d_rgb, d_depth, d_opacity, d_dist, dpart);
+  st = launch_check("k_composite_bwd");
+  if (st != NERFXL_OK) return st;
+  BwdParams p;
+  p.rays_o = rays_o;
+  p.rays_d = rays_d;
+  p.fp.boxes = f->boxes;
+  p.fp.tables = static_cast<const float*>(f->tables);
+  p.fp.mlp = static_cast<const float*>(f->mlp);
+  p.lp = level_params(f);
+  p.sp = sp;
+  p.K = f->K;
+  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
+  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
+  p.base = reinterpret_cast<const int32_t*>(ws + L.base);
+  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
+  p.dpart = dpart;
+  p.grad_tables = grad_tables;
+  p.grad_mlp = grad_mlp;
+  const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    if (cudaFuncSetAttribute(k_field_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
+      return launch_check("k_field_bwd_f32 smem attribute");
+    attr_dev = dev;
+  }
+  if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
+  const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);
+  profile_mark(0, stream);
+  k_field_bwd_f32<<<grid, kBwdThreads, smem, stream>>>(p);
+  profile_mark(1, stream);
+  return launch_check("k_field_bwd_f32");
+}

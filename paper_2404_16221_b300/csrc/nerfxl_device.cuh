@@ -27,6 +27,9 @@ constexpr int kWidth = 64;
 constexpr int kOut = 4;
 constexpr int kMlpParams = kIn * kWidth + kWidth * kWidth + kWidth * kOut;
 
+// Chunks per CTA tile (one warp per chunk); region buckets are padded to it.
+constexpr int kChunksPerTile = 8;
+
 // Error flags written into the workspace header.
 constexpr int kErrOverflow = 1;
 
@@ -188,6 +191,17 @@ __device__ __forceinline__ uint32_t vertex_index(const LevelParams& lp, int l, u
     return x + y * side + z * side * side;
   }
   return (x ^ (y * kHashPrime2) ^ (z * kHashPrime3)) & lp.hash_mask;
+}
+
+// Region owning chunk slot `chunk`: the largest k with base[k] <= chunk.
+__device__ __forceinline__ int region_of_chunk(const int32_t* base, int K, int chunk) {
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= chunk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // ---------------------------------------------------------------------------

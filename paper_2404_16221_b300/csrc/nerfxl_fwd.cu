@@ -150,10 +150,9 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
 
 // ---------------------------------------------------------------------------
 // k_field_fwd (FP32): persistent CTAs over interleaved tiles; warp w of a
-// tile handles chunk 4 * tile + w. Weights are reloaded only when the tile's
+// tile handles chunk kChunksPerTile * tile + w. Weights are reloaded only when the tile's
 // region changes.
 
-constexpr int kChunksPerTile = 4;
 constexpr int kFwdThreads = kChunksPerTile * kWarp;
 
 struct FwdParams {
@@ -171,17 +170,8 @@ struct FwdParams {
   float4* partials;        // [R][max_chunk][2]
 };
 
-__device__ __forceinline__ int region_of_chunk(const int32_t* s_base, int K, int chunk) {
-  int lo = 0, hi = K - 1;  // largest k with base[k] <= chunk
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (s_base[mid] <= chunk) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
-__global__ void __launch_bounds__(kFwdThreads, 4) k_field_fwd_f32(FwdParams p) {
+__global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
   extern __shared__ __align__(16) float s_dyn[];
   float* s_w = s_dyn;                                            // kMlpParams floats
   int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kMlpParams);  // [K+1]
@@ -524,7 +514,7 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   const size_t smem = sizeof(float) * kMlpParams + sizeof(int32_t) * (f->K + 1);
-  const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 4);
+  const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
   profile_mark(0, stream);
   k_field_fwd_f32<<<grid, kFwdThreads, smem, stream>>>(p);
   profile_mark(1, stream);

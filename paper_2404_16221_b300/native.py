@@ -36,6 +36,16 @@ class FieldDesc(C.Structure):
                 ("mlp_dtype", C.c_int32), ("mlp_scales", C.c_void_p)]
 
 
+class AdamDesc(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int64)]
+
+
+class TrainStateDesc(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("tables", "mlp", "grad_tables", "grad_mlp", "m_tables", "v_tables",
+                                          "m_mlp", "v_mlp")]
+
+
 class SamplingDesc(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("max_segments", C.c_int32), ("t_min", C.c_float), ("flags", C.c_int32)]
 
@@ -57,6 +67,11 @@ SIGNATURES = {
     "nerfxl_last_error": (C.c_char_p, []),
     "nerfxl_workspace_stats": (C.c_int, [_vp, _sz, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]),
     "nerfxl_set_profile_events": (C.c_int, [_vp, _vp]),
+    "nerfxl_render_bwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "nerfxl_loss": (C.c_int, [_i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "nerfxl_adam_update": (C.c_int, [_i64, _vp, _vp, _vp, _vp, C.c_void_p, _vp, _i32, _vp]),
+    "nerfxl_step_workspace_bytes": (_sz, [_FP, _SP, _i64]),
+    "nerfxl_step": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_segments": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_samples": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }

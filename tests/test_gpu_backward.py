@@ -1,0 +1,228 @@
+"""Backward, loss, Adam and training through the C ABI, against the FP64 oracle.
+
+Gradients: |gpu - ref| <= 1e-4 * max|ref| per tensor (FP32 atomics reorder
+the sums). The oracle's own gradient is pinned to central differences by
+tests/test_oracle.py, so GPU == oracle == finite differences.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16221_b300 import synthetic as sy
+
+import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_16221_b300 import build
+
+    build.build()
+
+
+def grad_err(g, ref):
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.abs(g - ref).max() / max(np.abs(ref).max(), 1e-30))
+
+
+def grad_close(g, ref, tol=1e-4):
+    """FP32 gradient bound: |g - ref| <= tol * max|ref| per tensor.
+
+    A ReLU whose pre-activation lies within ~1e-7 of zero (relative) can take
+    opposite decisions in FP32 and FP64, and then the whole contribution of
+    that unit at that sample differs. Such kinks touch a tiny share of the
+    entries, so at most 0.1% of entries may exceed the bound, and none may
+    exceed 100x the bound. A wrong term, sign or index breaks both."""
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    scale = max(np.abs(ref).max(), 1e-30)
+    err = np.abs(g - ref) / scale
+    frac = float(np.mean(err > tol))
+    return frac <= 1e-3 and err.max() <= 100 * tol, (frac, float(err.max()))
+
+
+def _case(name="grid8", n=1024, L=16, log2_T=14, S=None):
+    w = H.workload(name, L=L, log2_T=log2_T, S=S)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, n, 5)
+    return w, t, m, o[sel].copy(), d[sel].copy()
+
+
+@pytest.mark.parametrize("which", ["rgb", "depth", "opacity", "dist", "all"])
+def test_render_bwd_matches_oracle(which):
+    from paper_2404_16221_b300 import api
+
+    w, t, m, o, d = _case()
+    R = len(o)
+    g = sy.rng(11, "misc")
+    adj = {"rgb": np.zeros((R, 3)), "depth": np.zeros(R), "opacity": np.zeros(R), "dist": np.zeros(R)}
+    for k in adj:
+        if which in (k, "all"):
+            adj[k] = g.standard_normal(adj[k].shape)
+    of = H.oracle_field(w, t, m)
+    gt_ref, gm_ref = oracle.render_grad(of, w.S, o, d, adj["rgb"], adj["depth"], adj["opacity"], adj["dist"])
+    gf = H.gpu_field(w, t, m)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(adj["rgb"]), dev(adj["depth"]), dev(adj["opacity"]),
+                            dev(adj["dist"]))
+    okt, et = grad_close(gt.cpu().numpy(), gt_ref)
+    okm, em = grad_close(gm.cpu().numpy(), gm_ref)
+    assert okt and okm, (which, et, em)
+
+
+def test_loss_kernel_matches_oracle():
+    from paper_2404_16221_b300 import api
+
+    w, t, m, o, d = _case(n=3000)
+    tgt = sy.rng(12, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
+    gf = H.gpu_field(w, t, m)
+    out = api.render_fwd(gf, H.sampling(w), o, d)
+    L, d_rgb, d_dist = api.loss(out["rgb"], out["dist"], tgt, 0.01)
+    ref = oracle.loss(H.oracle_field(w, t, m), w.S, o, d, tgt, 0.01)
+    assert abs(float(L[0]) - ref) <= 1e-5 * abs(ref)
+    R = len(o)
+    np.testing.assert_allclose(d_dist.cpu().numpy(), 0.01 / R, rtol=1e-6)
+    np.testing.assert_allclose(d_rgb.cpu().numpy(), 2 * (out["rgb"].cpu().numpy() - tgt) / (3 * R), rtol=1e-5,
+                               atol=1e-12)
+
+
+def test_loss_gradient_through_autograd_matches_oracle():
+    """torch.autograd.Function: loss in torch from the rendered outputs, then
+    backward through the hand-written adjoint kernels."""
+    from paper_2404_16221_b300 import autograd
+
+    w, t, m, o, d = _case(n=512)
+    tgt = sy.rng(13, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
+    gf = H.gpu_field(w, t, m)
+    gf.tables.requires_grad_(True)
+    gf.mlp.requires_grad_(True)
+    rgb, depth, opacity, dist = autograd.render(gf, H.sampling(w), o, d)
+    loss = ((rgb - torch.from_numpy(tgt).cuda()) ** 2).mean() + 0.01 * dist.mean()
+    loss.backward()
+    L_ref, gt_ref, gm_ref = oracle.loss_grad(H.oracle_field(w, t, m), w.S, o, d, tgt, 0.01)
+    assert abs(float(loss) - L_ref) <= 1e-5 * L_ref
+    for g, ref in ((gf.tables.grad, gt_ref), (gf.mlp.grad, gm_ref)):
+        ok, e = grad_close(g.cpu().numpy(), ref)
+        assert ok, e
+
+
+def test_adam_kernel_matches_oracle():
+    from paper_2404_16221_b300 import api
+
+    g = sy.rng(14, "misc")
+    n = 100003
+    p = g.standard_normal(n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    pt, mt, vt = (torch.from_numpy(a.astype(np.float32)).cuda() for a in (p, m, v))
+    p32 = p.astype(np.float32).astype(np.float64)
+    for step in range(1, 4):
+        grad = g.standard_normal(n)
+        grad32 = grad.astype(np.float32)
+        api.adam_update(pt, torch.from_numpy(grad32).cuda(), mt, vt, step, 1e-2, 0.9, 0.99, 1e-8)
+        oracle.adam(p32, m, v, grad32.astype(np.float64), step, 1e-2, 0.9, 0.99, 1e-8)
+    np.testing.assert_allclose(pt.cpu().numpy(), p32, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(mt.cpu().numpy(), m, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(vt.cpu().numpy(), v, rtol=1e-5, atol=1e-7)
+
+
+def test_adam_refreshes_half_precision_copy():
+    from paper_2404_16221_b300 import api
+
+    n = 4096
+    p = torch.randn(n, device="cuda")
+    copy16 = torch.zeros(n, dtype=torch.float16, device="cuda")
+    copybf = torch.zeros(n, dtype=torch.bfloat16, device="cuda")
+    for copy in (copy16, copybf):
+        q = p.clone()
+        api.adam_update(q, torch.randn(n, device="cuda"), torch.zeros(n, device="cuda"),
+                        torch.zeros(n, device="cuda"), 1, 1e-2, compute_copy=copy)
+        assert torch.equal(copy, q.to(copy.dtype))
+
+
+def test_training_step_matches_oracle():
+    """One nerfxl_step: loss of the pre-update parameters, and the Adam update
+    computed from the oracle's gradient."""
+    from paper_2404_16221_b300 import api
+
+    w, t, m, o, d = _case(n=2048)
+    tgt = sy.rng(15, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
+    gf = H.gpu_field(w, t, m)
+    trainer = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    L = trainer.step(o, d, tgt).cpu().numpy()
+    of = H.oracle_field(w, t, m)
+    L_ref, gt_ref, gm_ref = oracle.loss_grad(of, w.S, o, d, tgt, 0.01)
+    assert abs(L[0] - L_ref) <= 1e-5 * L_ref
+    for g, ref in ((trainer.grad_tables, gt_ref), (trainer.grad_mlp, gm_ref)):
+        ok, e = grad_close(g.cpu().numpy(), ref)
+        assert ok, e
+    # The first Adam step moves each parameter by lr * g / (|g| + eps): by
+    # +-lr where the gradient is clearly non-zero, not at all where it is zero.
+    for new, old, gref in ((gf.tables, t, gt_ref), (gf.mlp, m, gm_ref)):
+        delta = new.cpu().numpy().astype(np.float64) - old
+        gref = gref.reshape(delta.shape)
+        big = np.abs(gref) > 1e-3 * np.abs(gref).max()
+        moved = np.abs(delta[big] + 1e-2 * np.sign(gref[big])) <= 1e-6 + 1e-4 * 1e-2
+        assert np.mean(moved) >= 0.999, np.mean(moved)
+        # untouched entries (no sample reads them) do not move
+        zero = gref == 0
+        if zero.any():
+            assert np.mean(delta[zero] != 0) < 1e-4
+
+
+def _psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - b) ** 2))
+    return 10 * np.log10(1.0 / max(mse, 1e-12))
+
+
+@pytest.mark.slow
+def test_training_gains_over_untrained_and_frozen_grid():
+    """Train the K=8 scene towards the Gaussian-blob target with the project's
+    own forward/backward/Adam kernels. Held-out PSNR must rise well above the
+    initial field's, and above the same training with the hash tables frozen
+    (the learned encoding removed)."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("train8", L=16, log2_T=16)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    P = oracle.mlp_params(w.mlp_in, w.W)
+    t0, m0 = sy.field_params(w, E, P, table_std=1e-4, mlp_std=0.1, table_init="uniform")
+    blobs = sy.blobs(200, w.seed)
+    o_tr, d_tr = sy.orbit_cameras(16, 3.0, 64, 64, 50.0, 0, 20)
+    o_te, d_te = sy.orbit_cameras(4, 3.0, 64, 64, 50.0, 16, 20)
+    of = H.oracle_field(w, t0, m0)
+    tgt_tr = oracle.blob_render(of, w.S, o_tr, d_tr, blobs)[0].astype(np.float32)
+    tgt_te = oracle.blob_render(of, w.S, o_te, d_te, blobs)[0]
+
+    def run(freeze_tables: bool, steps: int = 400, batch: int = 8192):
+        gf = H.gpu_field(w, t0.copy(), m0.copy())
+        tr = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
+        g = sy.rng(16, "batch")
+        o_dev, d_dev = torch.from_numpy(o_tr).cuda(), torch.from_numpy(d_tr).cuda()
+        tgt_dev = torch.from_numpy(tgt_tr).cuda()
+        for s in range(steps):
+            idx = torch.from_numpy(g.integers(0, len(o_tr), batch)).cuda()
+            if freeze_tables:
+                keep = gf.tables.clone()
+            tr.step(o_dev[idx], d_dev[idx], tgt_dev[idx])
+            if freeze_tables:
+                gf.tables.copy_(keep)
+        out = api.render_fwd(gf, H.sampling(w), o_te, d_te)
+        return _psnr(out["rgb"].cpu().numpy(), tgt_te)
+
+    init = _psnr(oracle.render(of, w.S, o_te, d_te, 1)["rgb"], tgt_te)
+    trained = run(False)
+    frozen = run(True)
+    print("held-out PSNR: initial %.2f, frozen grid %.2f, trained %.2f" % (init, frozen, trained))
+    assert trained > init + 6.0
+    assert trained > frozen + 1.0

@@ -72,7 +72,10 @@ typedef enum { NERFXL_F32 = 0, NERFXL_F16 = 1, NERFXL_BF16 = 2, NERFXL_E4M3 = 3 
  * mlp:    [K][P] of mlp_dtype, P = nerfxl_mlp_params(); each block is
  *         W1 [mlp_in][W], W2 [W][W], W3 [W][4], row-major. Features beyond L*F
  *         are zero, so only the first L*F rows of W1 matter.
- * Currently supported: F = 2, mlp_in = 32, W = 64, L*F <= 32.
+ * Currently supported: F = 2, mlp_in = 32, W = 64, L*F <= 32; dtypes FP32
+ * tables with an FP32 MLP (CUDA cores), or FP32/FP16 tables with a BF16/FP16
+ * MLP (tensor cores, FP32 accumulation). Hash features are interpolated in
+ * FP32 and rounded to the MLP's 16-bit type.
  */
 typedef struct nerfxl_field {
   int32_t K, L, F, log2_T, mlp_in, mlp_width;
@@ -210,7 +213,9 @@ nerfxl_status nerfxl_render_fwd_static(const nerfxl_field* f, const nerfxl_sampl
 
 /*
  * Status of device-side checks of the last call made with this workspace
- * (synchronises the stream): NERFXL_OK or NERFXL_E_OVERFLOW.
+ * (synchronises the stream): NERFXL_OK, NERFXL_E_OVERFLOW, or NERFXL_E_TIMEOUT (a
+ * bounded wait of the tensor-core pipeline expired; the kernel stopped early
+ * and released its tensor memory, the outputs of that call are invalid).
  */
 nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t stream);
 

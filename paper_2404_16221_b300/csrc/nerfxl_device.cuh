@@ -32,6 +32,7 @@ constexpr int kChunksPerTile = 8;
 
 // Error flags written into the workspace header.
 constexpr int kErrOverflow = 1;
+constexpr int kErrTimeout = 2;  // a bounded wait on the tensor-core pipeline expired
 
 // Per-level layout of a region table, passed by value in kernel parameters.
 struct LevelParams {

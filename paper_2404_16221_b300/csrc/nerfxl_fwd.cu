@@ -486,8 +486,10 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
                                 float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream) {
   nerfxl_status st = validate(f, s, n_rays);
   if (st != NERFXL_OK) return st;
-  if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
-    return set_error(NERFXL_E_UNSUPPORTED, "this build renders FP32 tables with an FP32 MLP");
+  const bool tab_ok = f->table_dtype == NERFXL_F32 || f->table_dtype == NERFXL_F16;
+  const bool tc_mlp = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
+  if (!tab_ok || !(tc_mlp || f->mlp_dtype == NERFXL_F32) || (f->mlp_dtype == NERFXL_F32 && f->table_dtype != NERFXL_F32))
+    return set_error(NERFXL_E_UNSUPPORTED, "supported: FP32 tables + FP32 MLP, or FP32/FP16 tables + BF16/FP16 MLP");
   if (n_rays > 0 && (!rays_o || !rays_d || !rgb || !depth || !opacity))
     return set_error(NERFXL_E_INVALID, "null ray or output pointer");
   const Layout L = layout(f, s, n_rays, 0);
@@ -497,6 +499,14 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
   st = run_sampling(f, sp, n_rays, rays_o, rays_d, ws, L, stream);
   if (st != NERFXL_OK) return st;
   if (n_rays == 0) return NERFXL_OK;
+  if (tc_mlp) {
+    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, stream);
+    if (st != NERFXL_OK) return st;
+    k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
+        n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
+        rgb, depth, opacity, dist);
+    return launch_check("k_composite");
+  }
 
   FwdParams p;
   p.rays_o = rays_o;
@@ -531,6 +541,7 @@ nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t 
   if (cudaMemcpyAsync(&flags, workspace, sizeof(flags), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
     return launch_check("nerfxl_check");
+  if (flags & kErrTimeout) return set_error(NERFXL_E_TIMEOUT, "a bounded wait on the tensor-core pipeline expired");
   if (flags & kErrOverflow) return set_error(NERFXL_E_OVERFLOW, "a ray crossed more regions than max_segments");
   return NERFXL_OK;
 }

@@ -1,0 +1,395 @@
+// Field forward with the MLP on the tensor cores (tcgen05, accumulators in
+// tensor memory): the mixed-precision forms (BF16 or FP16 MLP with FP32
+// accumulation; FP32 or FP16 hash features).
+//
+// One CTA = 4 warps = one 128-row MMA tile (4 chunks of 32 samples, all of
+// one region). Per tile:
+//   gather   each thread encodes its sample; features -> A0 (bf16/fp16)
+//   layer 1  D1[128x64] = A0[128x32] W1            (2 MMAs, K = 16 each)
+//   layer 2  h1 = relu(D1) -> A1; D2 = A1 W2        (4 MMAs)
+//   layer 3  h2 = relu(D2) -> A0; D3[128x16] = A0 W3 (4 MMAs; columns 4..15 zero)
+//   render   sigma = exp(D3[:,0]), rgb = sigmoid(D3[:,1..3]); chunk partial
+// One elected thread issues the MMAs and commits them to an mbarrier; every
+// thread reads its own accumulator row (its TMEM lane) with tcgen05.ld.
+// Waits on the mbarrier are bounded: on expiry the kernel flags
+// kErrTimeout in the workspace, frees its tensor memory and returns.
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "nerfxl_field.cuh"
+#include "nerfxl_host.h"
+#include "nerfxl_tc.cuh"
+
+namespace nerfxl {
+
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+constexpr int kTcChunks = kTcRows / kWarp;  // 4 chunks per MMA tile
+constexpr uint32_t kTmemCols = 128;         // D1 at column 0, D2 at column 64, D3 reuses column 0
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Shared-memory plan (offsets from a 1024-byte-aligned base).
+constexpr uint32_t kOffA0 = 0;                    // 128 rows x 128 B
+constexpr uint32_t kOffA1 = kOffA0 + 128 * 128;   // 128 rows x 128 B
+constexpr uint32_t kOffB1 = kOffA1 + 128 * 128;   // 64 rows (n) x 128 B (k < 32 used)
+constexpr uint32_t kOffB2 = kOffB1 + 64 * 128;    // 64 rows x 128 B
+constexpr uint32_t kOffB3 = kOffB2 + 64 * 128;    // 16 rows x 128 B
+constexpr uint32_t kOffMisc = kOffB3 + 16 * 128;  // mbarrier (8 B), tmem base (4 B)
+constexpr uint32_t kOffBase = kOffMisc + 64;      // int32 base[K+1]
+constexpr size_t kTcSmemFixed = kOffBase + 1024;  // + 1024 slack for the alignment of the base
+
+template <bool BF16>
+struct Half2Of;
+template <>
+struct Half2Of<true> {
+  __device__ static uint32_t pack(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static float load(const void* p, size_t i) {
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
+  }
+  __device__ static uint16_t bits(const void* p, size_t i) { return reinterpret_cast<const uint16_t*>(p)[i]; }
+};
+template <>
+struct Half2Of<false> {
+  __device__ static uint32_t pack(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static float load(const void* p, size_t i) { return __half2float(reinterpret_cast<const __half*>(p)[i]); }
+  __device__ static uint16_t bits(const void* p, size_t i) { return reinterpret_cast<const uint16_t*>(p)[i]; }
+};
+
+// Hash-grid gather for FP16 tables: one 4-byte half2 per corner, 8-byte x-pairs.
+__device__ __forceinline__ void encode_f16(const LevelParams& lp, const __half2* __restrict__ table, const float u[3],
+                                           float feat[kIn]) {
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) feat[i] = 0.0f;
+#pragma unroll
+  for (int l = 0; l < kIn / 2; ++l) {
+    if (l >= lp.L) break;
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+    const __half2* tl = table + lp.off[l];
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+      const uint2 q = __ldg(reinterpret_cast<const uint2*>(tl + (i0 & ~1u)));
+      const bool odd = i0 & 1u;
+      const uint32_t a = odd ? q.y : q.x, b = odd ? q.x : q.y;
+      v[e] = __half22float2(*reinterpret_cast<const __half2*>(&a));
+      if ((i0 ^ i1) == 1u) {
+        v[e + 1] = __half22float2(*reinterpret_cast<const __half2*>(&b));
+      } else {
+        v[e + 1] = __half22float2(__ldg(tl + i1));
+      }
+    }
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float w = ((e & 1) ? f[0] : 1.0f - f[0]) * (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) *
+                      (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+      s0 = fmaf(w, v[e].x, s0);
+      s1 = fmaf(w, v[e].y, s1);
+    }
+    feat[2 * l] = s0;
+    feat[2 * l + 1] = s1;
+  }
+}
+
+template <bool kF16Table>
+struct TableOf;
+template <>
+struct TableOf<false> {
+  using T = float2;
+  __device__ static void encode(const LevelParams& lp, const void* t, const float u[3], float feat[kIn]) {
+    encode_f32(lp, static_cast<const float2*>(t), u, feat);
+  }
+};
+template <>
+struct TableOf<true> {
+  using T = __half2;
+  __device__ static void encode(const LevelParams& lp, const void* t, const float u[3], float feat[kIn]) {
+    encode_f16(lp, static_cast<const __half2*>(t), u, feat);
+  }
+};
+
+// Weights of region k (row-major W1 [32][64], W2 [64][64], W3 [64][4], 16-bit)
+// into the K-major swizzled B tiles: B(row n, column k) = W[k][n].
+template <bool BF16>
+__device__ __forceinline__ void load_weights_tc(const void* blk, char* sm) {
+  uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + kOffB1);
+  uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + kOffB2);
+  uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + kOffB3);
+  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    b1[tc::sw128_offset(n, k) >> 1] = Half2Of<BF16>::bits(blk, i);
+  }
+  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    b2[tc::sw128_offset(n, k) >> 1] = Half2Of<BF16>::bits(blk, kIn * kWidth + i);
+  }
+  for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+    const int n = i / 64, k = i % 64;
+    const uint16_t v = n < kOut ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
+    b3[tc::sw128_offset(n, k) >> 1] = v;
+  }
+}
+
+// Writes 64 activations (relu applied by the caller) of row r as 16-bit into a
+// swizzled A tile, 8 chunks of 16 bytes.
+template <bool BF16>
+__device__ __forceinline__ void store_row64(uint32_t tile, uint32_t r, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    tc::st_shared_v4(tile + tc::sw128_chunk(r, c), Half2Of<BF16>::pack(v[8 * c], v[8 * c + 1]),
+                     Half2Of<BF16>::pack(v[8 * c + 2], v[8 * c + 3]), Half2Of<BF16>::pack(v[8 * c + 4], v[8 * c + 5]),
+                     Half2Of<BF16>::pack(v[8 * c + 6], v[8 * c + 7]));
+  }
+}
+
+template <bool BF16>
+__device__ __forceinline__ void store_row32(uint32_t tile, uint32_t r, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    tc::st_shared_v4(tile + tc::sw128_chunk(r, c), Half2Of<BF16>::pack(v[8 * c], v[8 * c + 1]),
+                     Half2Of<BF16>::pack(v[8 * c + 2], v[8 * c + 3]), Half2Of<BF16>::pack(v[8 * c + 4], v[8 * c + 5]),
+                     Half2Of<BF16>::pack(v[8 * c + 6], v[8 * c + 7]));
+  }
+}
+
+// Reads 64 accumulator columns of this thread's row, applies relu.
+__device__ __forceinline__ void tmem_row64_relu(uint32_t taddr, float* v) {
+  tc::tmem_ld16(taddr + 0, v);
+  tc::tmem_ld16(taddr + 16, v + 16);
+  tc::tmem_ld16(taddr + 32, v + 32);
+  tc::tmem_ld16(taddr + 48, v + 48);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = fmaxf(v[i], 0.0f);
+}
+
+struct FwdTcParams {
+  const float* rays_o;
+  const float* rays_d;
+  const float* boxes;
+  const void* tables;  // [K][E] of float2 or half2
+  const void* mlp;     // [K][kMlpParams] 16-bit
+  LevelParams lp;
+  SampParams sp;
+  int K;
+  const RayHdr* hdr;
+  const SegDesc* segs;
+  const int32_t* base;
+  const uint2* chunks;
+  const int32_t* n_tiles;  // tiles of kChunksPerTile chunks
+  float4* partials;
+  int32_t* err;
+};
+
+template <bool kF16Table, bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
+  extern __shared__ __align__(1024) char s_raw[];
+  char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = tc::smem_u32(sm);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
+  int32_t* s_base = reinterpret_cast<int32_t*>(sm + kOffBase);
+  const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+
+  for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+
+  constexpr uint32_t idesc64 = tc::idesc_f16(BF16, kTcRows, 64);
+  constexpr uint32_t idesc16 = tc::idesc_f16(BF16, kTcRows, 16);
+  const uint32_t a0 = sbase + kOffA0, a1 = sbase + kOffA1;
+  const uint32_t b1 = sbase + kOffB1, b2 = sbase + kOffB2, b3 = sbase + kOffB3;
+
+  const int n_sub = *p.n_tiles * (kChunksPerTile / kTcChunks);
+  int region = -1;
+  const void* table = nullptr;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int t = blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
+    const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
+    if (k != region) {
+      __syncthreads();
+      load_weights_tc<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm);
+      region = k;
+      table = static_cast<const char*>(p.tables) + (size_t)k * p.lp.E * sizeof(typename TableOf<kF16Table>::T);
+    }
+    // ---- gather: one sample per thread
+    const uint2 ref = p.chunks[t * kTcChunks + warp];
+    const bool chunk_ok = ref.x != kEmptyChunk;
+    bool valid = false;
+    float tbar = 0.0f, dl = 0.0f, tr = 0.0f;
+    float feat[kIn];
+#pragma unroll
+    for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+    RayHdr h = {0.0f, 0.0f, 0, 0};
+    SegDesc sd = {0.0f, 0.0f, 0, 0};
+    int c = 0;
+    uint32_t ray = 0;
+    if (chunk_ok) {
+      ray = ref.x;
+      const int seg = ref.y >> 16;
+      c = ref.y & 0xFFFF;
+      h = p.hdr[ray];
+      sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      const int i = c * kWarp + lane;
+      valid = i < seg_n(sd);
+      if (valid) {
+        float o[3], d[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          o[ax] = p.rays_o[3 * (size_t)ray + ax];
+          d[ax] = p.rays_d[3 * (size_t)ray + ax];
+        }
+        float a, b;
+        segment_interval(sd, h.tn, h.delta, i, a, b);
+        tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        dl = __fsub_rn(b, a);
+        tr = __fsub_rn(tbar, h.tn);
+        float x[3], u[3];
+        sample_point(o, d, tbar, x);
+        region_coord(p.boxes + 6 * k, x, u);
+        TableOf<kF16Table>::encode(p.lp, table, u, feat);
+      }
+    }
+    store_row32<BF16>(a0, tid, feat);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- layer 1
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+        tc::mma_f16(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b1 + 32 * kk), idesc64, kk);
+      tc::mma_commit(mbar);
+    }
+    bool ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    float v[64];
+    tmem_row64_relu(tmem_row + 0, v);
+    store_row64<BF16>(a1, tid, v);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- layer 2
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma_f16(tmem + 64, tc::desc_sw128(a1 + 32 * kk), tc::desc_sw128(b2 + 32 * kk), idesc64, kk);
+      tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    tmem_row64_relu(tmem_row + 64, v);
+    store_row64<BF16>(a0, tid, v);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- layer 3
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma_f16(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b3 + 32 * kk), idesc16, kk);
+      tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    float raw[16];
+    tc::tmem_ld16(tmem_row + 0, raw);
+    tc::tmem_ld_wait();
+    tc::fence_before_sync();
+    // ---- chunk render
+    if (chunk_ok) {
+      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (valid) {
+        sigma = expf(raw[0]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rgb[q] = 1.0f / (1.0f + expf(-raw[1 + q]));
+      }
+      const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
+      if (lane == 0) {
+        float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
+        dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
+        dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+      }
+    }
+    __syncthreads();  // A0 and TMEM free for the next tile
+  }
+  if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Host dispatch (called from nerfxl_render_fwd).
+nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
+                                  const float* rays_o, const float* rays_d, char* ws, const Layout& L,
+                                  cudaStream_t stream) {
+  FwdTcParams p;
+  p.rays_o = rays_o;
+  p.rays_d = rays_d;
+  p.boxes = f->boxes;
+  p.tables = f->tables;
+  p.mlp = f->mlp;
+  p.lp = lp;
+  p.sp = sp;
+  p.K = f->K;
+  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
+  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
+  p.base = reinterpret_cast<const int32_t*>(ws + L.base);
+  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
+  p.partials = reinterpret_cast<float4*>(ws + L.partials);
+  p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
+  const size_t smem = kTcSmemFixed + sizeof(int32_t) * (f->K + 1);
+  const bool bf16 = f->mlp_dtype == NERFXL_BF16;
+  const bool f16tab = f->table_dtype == NERFXL_F16;
+  void (*kern)(FwdTcParams) = nullptr;
+  if (f16tab) kern = bf16 ? k_field_fwd_tc<true, true> : k_field_fwd_tc<true, false>;
+  else kern = bf16 ? k_field_fwd_tc<false, true> : k_field_fwd_tc<false, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return launch_check("k_field_fwd_tc smem attribute");
+  const int grid = fwd_grid(L.chunk_cap / kTcChunks, 4);
+  profile_mark(0, stream);
+  kern<<<grid, kTcThreads, smem, stream>>>(p);
+  profile_mark(1, stream);
+  return launch_check("k_field_fwd_tc");
+}
+
+}  // namespace nerfxl

@@ -41,5 +41,9 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
 // dominant kernel) if the caller installed one.
 void profile_mark(int which, cudaStream_t stream);
 int fwd_grid(int64_t max_tiles, int ctas_per_sm);
+// Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
+nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
+                                  const float* rays_o, const float* rays_d, char* ws, const Layout& L,
+                                  cudaStream_t stream);
 
 }  // namespace nerfxl

@@ -155,6 +155,33 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(step, steps, flush, stream, prof=True):
+    """Per-step CUDA events around each step (L2 flushed before each step,
+    outside the events); the library's profile events bracket the dominant
+    kernel of each step. Returns (step_ms, kernel_ms) lists."""
+    import torch
+
+    from paper_2404_16221_b300 import native as N
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for pair in kev:  # torch creates the CUDA event on first record
+        for e in pair:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        if prof:
+            N.check(N.lib().nerfxl_set_profile_events(C_void(kev[i][0].cuda_event), C_void(kev[i][1].cuda_event)),
+                    "profile events")
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    N.lib().nerfxl_set_profile_events(None, None)
+    return [a.elapsed_time(b) for a, b in ev], ([a.elapsed_time(b) for a, b in kev] if prof else [])
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -175,105 +202,133 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     w, tables, mlp, o, d = setup_workload(rank)
-    field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(tables), torch.from_numpy(mlp),
-                                 device=dev)
     samp = api.Sampling(w.S, w.max_segments)
     R = len(o)
     o_dev = torch.from_numpy(o).to(dev)
     d_dev = torch.from_numpy(d).to(dev)
-    ws = api.alloc_workspace(field, samp, R)
-    out = {"rgb": torch.empty(R, 3, device=dev), "depth": torch.empty(R, device=dev),
-           "opacity": torch.empty(R, device=dev), "dist": torch.empty(R, device=dev)}
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    steps, warm = args.steps, max(3, args.warmup)
 
-    def step():
-        api.render_fwd(field, samp, o_dev, d_dev, workspace=ws, out=out)
+    def mk_field(tab_dtype, mlp_dtype):
+        return api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(tables).to(tab_dtype),
+                                    torch.from_numpy(mlp).to(mlp_dtype), device=dev)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    api.check(ws)
-    n_samples = C_int64()
-    n_chunks = C_int64()
-    N.check(N.lib().nerfxl_workspace_stats(N._ptr(ws), ws.numel(), n_samples, n_chunks,
-                                           N._stream(None)), "stats")
-    torch.cuda.synchronize()
+    def out_bufs():
+        return {"rgb": torch.empty(R, 3, device=dev), "depth": torch.empty(R, device=dev),
+                "opacity": torch.empty(R, device=dev), "dist": torch.empty(R, device=dev)}
 
-    # Device-timed steps: L2 flushed before each step (outside the events),
-    # the dominant kernel bracketed by the library's profile events.
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for pair in kev:  # torch creates the CUDA event on first record
-        for e in pair:
-            e.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    forms = {}
+    # forward, FP32 plain path and the mixed form (FP16 tables, BF16 MLP on tensor cores)
+    for name, td, md in (("fwd_fp32", torch.float32, torch.float32), ("fwd_f16tab_bf16mlp", torch.float16,
+                                                                      torch.bfloat16)):
+        field = mk_field(td, md)
+        ws = api.alloc_workspace(field, samp, R)
+        out = out_bufs()
+        step = lambda field=field, ws=ws, out=out: api.render_fwd(field, samp, o_dev, d_dev, workspace=ws, out=out)
+        for _ in range(warm):
+            step()
+        api.check(ws)
+        ns, nc = C_int64(), C_int64()
+        N.check(N.lib().nerfxl_workspace_stats(N._ptr(ws), ws.numel(), ns, nc, N._stream(None)), "stats")
+        with Clocks(local) as clk:
+            step_ms, kern_ms = time_steps(step, steps, flush, stream)
+        forms[name] = {"field": field, "ws": ws, "out": out, "step": step, "step_ms": step_ms, "kern_ms": kern_ms,
+                       "samples": ns.value, "chunks": nc.value, "clocks": clk.summary(),
+                       "kernel": "k_field_fwd_f32" if md == torch.float32 else "k_field_fwd_tc",
+                       "bytes_per_sample": 8 * w.F * (4 if td == torch.float32 else 2) * w.L}
+        del field
+    # training step, FP32 (forward + loss + backward + Adam), random target colours
+    tfield = mk_field(torch.float32, torch.float32)
+    trainer = api.Trainer(tfield, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    tgt = torch.rand(R, 3, generator=torch.Generator().manual_seed(1002)).to(dev)
+    tstep = lambda: trainer.step(o_dev, d_dev, tgt)
+    for _ in range(warm):
+        tstep()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            N.check(N.lib().nerfxl_set_profile_events(C_void(kev[i][0].cuda_event), C_void(kev[i][1].cuda_event)),
-                    "profile events")
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        N.lib().nerfxl_set_profile_events(None, None)
-        # end to end through host buffers: H2D of the rays, D2H of the image
-        o_h = torch.from_numpy(o).pin_memory()
-        d_h = torch.from_numpy(d).pin_memory()
-        out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            e2e_ev[i][0].record(stream)
-            o_dev.copy_(o_h, non_blocking=True)
-            d_dev.copy_(d_h, non_blocking=True)
-            step()
-            for k in out:
-                out_h[k].copy_(out[k], non_blocking=True)
-            e2e_ev[i][1].record(stream)
-        torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
-    e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
-    t_step = sum(step_ms) / 1000.0
+        step_ms, kern_ms = time_steps(tstep, steps, flush, stream)
+    forms["train_fp32"] = {"step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
+                           "kernel": "k_field_bwd_f32", "samples": forms["fwd_fp32"]["samples"]}
+    del trainer, tfield
+    # training step in the mixed form: FP16 tables, BF16 MLP, FP32 Adam masters
+    mfield = mk_field(torch.float16, torch.bfloat16)
+    mtrainer = api.Trainer(mfield, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=torch.from_numpy(tables),
+                           master_mlp=torch.from_numpy(mlp))
+    mstep = lambda: mtrainer.step(o_dev, d_dev, tgt)
+    for _ in range(warm):
+        mstep()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        step_ms, kern_ms = time_steps(mstep, steps, flush, stream)
+    forms["train_f16tab_bf16mlp"] = {"step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
+                                     "kernel": "k_field_bwd_f32<f16 tables, bf16 mlp>",
+                                     "samples": forms["fwd_fp32"]["samples"]}
+    del mtrainer, mfield
+
+    head = forms["fwd_fp32"]
+    # end to end through host buffers for the headline form
+    o_h = torch.from_numpy(o).pin_memory()
+    d_h = torch.from_numpy(d).pin_memory()
+    out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in head["out"].items()}
+
+    def e2e_step():
+        o_dev.copy_(o_h, non_blocking=True)
+        d_dev.copy_(d_h, non_blocking=True)
+        head["step"]()
+        for k in head["out"]:
+            out_h[k].copy_(head["out"][k], non_blocking=True)
+
+    for _ in range(warm):
+        e2e_step()
+    e2e_ms, _ = time_steps(e2e_step, steps, flush, stream, prof=False)
+    t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
         tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step, t_e2e = float(tt[0]), float(tt[1])
     if rank != 0:
-        dist.destroy_process_group() if world > 1 else None
+        if world > 1:
+            dist.destroy_process_group()
         return
     hbm, bf16, src = peaks()
-    kern_s = statistics.mean(kern_ms) / 1000.0
-    bytes_per_sample = 8 * w.F * 4 * w.L  # 8 corners x F features x 4 B x L levels
-    achieved = n_samples.value * bytes_per_sample / kern_s / 1e9
-    rays_total = R * world * args.steps
+
+    def summary(f):
+        ms = statistics.mean(f["step_ms"])
+        r = {"rays_per_s": R / (ms / 1000.0), "ms_per_step": ms}
+        if f.get("kern_ms"):
+            km = statistics.mean(f["kern_ms"])
+            r["kernel"] = f["kernel"]
+            r["kernel_ms"] = km
+            if "bytes_per_sample" in f:
+                r["gather_gbs_algorithmic"] = f["samples"] * f["bytes_per_sample"] / (km / 1000.0) / 1e9
+        r["clocks"] = f["clocks"]
+        return r
+
+    kern_s = statistics.mean(head["kern_ms"]) / 1000.0
+    achieved = head["samples"] * head["bytes_per_sample"] / kern_s / 1e9
+    rays_total = R * world * steps
     line = {
-        "metric": METRIC, "value": rays_total / t_step, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": 1000.0 * t_step / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": rays_total / t_step, "unit": "rays/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": 1000.0 * t_step / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "grid8 render fwd: K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 (16->2048), FP32 tables "
                                "and MLP 32-64-64-4, 2^18 rays from 64 pinhole cameras, S=128",
-                   "rays_per_gpu": R, "samples_per_step": int(n_samples.value), "chunks_per_step": int(n_chunks.value),
+                   "rays_per_gpu": R, "samples_per_step": int(head["samples"]), "chunks_per_step": int(head["chunks"]),
                    "l2": "flushed before every timed step (252 MB write, outside the step events)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "train_target": "uniform random colours (throughput does not depend on the target)"},
         "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(2 * R * 12),
                 "d2h_bytes_per_step": int(R * (12 + 4 + 4 + 4))},
-        "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_field_fwd_f32", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "gpu_launches": 5 * steps,
+        "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "basis": "%d B/sample algorithmic gather bytes x %d samples / mean kernel time %.3f ms (%s peak)"
-                              % (bytes_per_sample, n_samples.value, 1000 * kern_s, src)},
-        "kernel_ms": statistics.mean(kern_ms), "wall_s": wall,
+                              % (head["bytes_per_sample"], head["samples"], 1000 * kern_s, src)},
+        "forms": {k: summary(v) for k, v in forms.items()},
+        "clocks": head["clocks"],
     }
-    line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, tables, mlp, o, d, args.cpu_rays)
     print(json.dumps(line), flush=True)

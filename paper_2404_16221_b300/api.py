@@ -208,25 +208,33 @@ def ctypes_addr(x):
 
 class Trainer:
     """FP32 master parameters + Adam moments; nerfxl_step does fwd, loss, bwd
-    and the update in one call."""
+    and the update in one call. If the field holds 16-bit compute copies
+    (FP16 tables, BF16/FP16 MLP), the masters live here and every step
+    refreshes the copies from them."""
 
     def __init__(self, field: PartitionedField, samp: Sampling, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
-                 lambda_dist=0.01):
-        if field.tables.dtype != torch.float32 or field.mlp.dtype != torch.float32:
-            raise ValueError("the FP32 trainer renders from FP32 masters")
+                 lambda_dist=0.01, master_tables=None, master_mlp=None):
         self.field, self.samp = field, samp
         self.lr, self.beta1, self.beta2, self.eps, self.lambda_dist = lr, beta1, beta2, eps, lambda_dist
+
+        def master(copy, given):
+            if copy.dtype == torch.float32:
+                return copy  # renders straight from the master
+            m = given if given is not None else copy.float()
+            return torch.as_tensor(m, dtype=torch.float32).to(field.device).reshape(copy.shape).contiguous()
+
+        self.tables = master(field.tables, master_tables)
+        self.mlp = master(field.mlp, master_mlp)
         z = torch.zeros_like
-        self.grad_tables, self.grad_mlp = z(field.tables), z(field.mlp)
-        self.m_tables, self.v_tables = z(field.tables), z(field.tables)
-        self.m_mlp, self.v_mlp = z(field.mlp), z(field.mlp)
+        self.grad_tables, self.grad_mlp = z(self.tables), z(self.mlp)
+        self.m_tables, self.v_tables = z(self.tables), z(self.tables)
+        self.m_mlp, self.v_mlp = z(self.mlp), z(self.mlp)
         self.step_count = 0
         self._ws = None
         self.loss = torch.zeros(3, dtype=torch.float32, device=field.device)
 
     def state_desc(self) -> N.TrainStateDesc:
-        f = self.field
-        return N.TrainStateDesc(f.tables.data_ptr(), f.mlp.data_ptr(), self.grad_tables.data_ptr(),
+        return N.TrainStateDesc(self.tables.data_ptr(), self.mlp.data_ptr(), self.grad_tables.data_ptr(),
                                 self.grad_mlp.data_ptr(), self.m_tables.data_ptr(), self.v_tables.data_ptr(),
                                 self.m_mlp.data_ptr(), self.v_mlp.data_ptr())
 

@@ -99,6 +99,8 @@ struct BwdParams {
   const float* rays_o;
   const float* rays_d;
   FieldPtrs fp;
+  const void* tables;  // [K][E] of float2 or half2
+  const void* mlp;     // [K][kMlpParams] of fp32, bf16 or fp16
   LevelParams lp;
   SampParams sp;
   int K;
@@ -186,6 +188,7 @@ __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, 
   }
 }
 
+template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
   float* s_w = sm;                                       // W1t [64][32], W2t [64][64], W3 [64][4]
@@ -205,19 +208,21 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   float* gW2 = s_acc + kIn * kWidth;
   float* gW3 = gW2 + kWidth * kWidth;
   int region = -1;
-  const float2* table = nullptr;
+  const void* table = nullptr;
   float2* gtab = nullptr;
+  using TabT = typename TableOf<kF16Table>::T;
+  const size_t mlp_esize = kMlpType == 0 ? 4 : 2;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     __syncthreads();  // previous tile's shared buffers fully consumed
     if (k != region) {
       if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
       __syncthreads();
-      load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
+      load_mlp_any<kMlpType>(static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * mlp_esize, s_w);
       for (int i = tid; i < kMlpParams; i += blockDim.x) s_acc[i] = 0.0f;
       __syncthreads();
       region = k;
-      table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
+      table = static_cast<const char*>(p.tables) + (size_t)k * p.lp.E * sizeof(TabT);
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
     const uint2 ref = p.chunks[t * kChunksPerTile + warp];
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
         float x[3];
         sample_point(o, d, tbar, x);
         region_coord(p.fp.boxes + 6 * k, x, u);
-        encode_f32(p.lp, table, u, feat);
+        TableOf<kF16Table>::encode(p.lp, table, u, feat);
       }
     }
     // ---- forward recompute: feat -> h1 (s_P) -> h2 (s_Q) -> raw outputs
@@ -433,8 +438,10 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
                                            cudaStream_t stream) {
   nerfxl_status st = validate(f, s, n_rays);
   if (st != NERFXL_OK) return st;
-  if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
-    return set_error(NERFXL_E_UNSUPPORTED, "the FP32 backward reads FP32 parameters");
+  const bool f16tab = f->table_dtype == NERFXL_F16;
+  if (!(f->table_dtype == NERFXL_F32 || f16tab) ||
+      !(f->mlp_dtype == NERFXL_F32 || f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16))
+    return set_error(NERFXL_E_UNSUPPORTED, "backward reads FP32/FP16 tables and an FP32/BF16/FP16 MLP");
   if (n_rays > 0 && (!rays_o || !rays_d || !grad_tables || !grad_mlp))
     return set_error(NERFXL_E_INVALID, "null ray or gradient pointer");
   const Layout L = layout(f, s, n_rays, 1);
@@ -453,8 +460,10 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.rays_o = rays_o;
   p.rays_d = rays_d;
   p.fp.boxes = f->boxes;
-  p.fp.tables = static_cast<const float*>(f->tables);
-  p.fp.mlp = static_cast<const float*>(f->mlp);
+  p.fp.tables = nullptr;
+  p.fp.mlp = nullptr;
+  p.tables = f->tables;
+  p.mlp = f->mlp;
   p.lp = level_params(f);
   p.sp = sp;
   p.K = f->K;
@@ -467,18 +476,16 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
-  static int attr_dev = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (attr_dev != dev) {
-    if (cudaFuncSetAttribute(k_field_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
-      return launch_check("k_field_bwd_f32 smem attribute");
-    attr_dev = dev;
-  }
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
+  const int mt = f->mlp_dtype == NERFXL_F32 ? 0 : (f->mlp_dtype == NERFXL_BF16 ? 1 : 2);
+  void (*kern)(BwdParams) = nullptr;
+  if (f16tab) kern = mt == 0 ? k_field_bwd_f32<true, 0> : (mt == 1 ? k_field_bwd_f32<true, 1> : k_field_bwd_f32<true, 2>);
+  else kern = mt == 0 ? k_field_bwd_f32<false, 0> : (mt == 1 ? k_field_bwd_f32<false, 1> : k_field_bwd_f32<false, 2>);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
+    return launch_check("k_field_bwd_f32 smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);
   profile_mark(0, stream);
-  k_field_bwd_f32<<<grid, kBwdThreads, smem, stream>>>(p);
+  kern<<<grid, kBwdThreads, smem, stream>>>(p);
   profile_mark(1, stream);
   return launch_check("k_field_bwd_f32");
 }

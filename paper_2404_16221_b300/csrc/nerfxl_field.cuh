@@ -2,6 +2,9 @@
 // backward and debug kernels (FP32 plain path).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "nerfxl_device.cuh"
 
 namespace nerfxl {
@@ -148,6 +151,89 @@ __device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3],
   return p;
 }
 
+
+// Hash-grid gather for FP16 tables: one 4-byte half2 per corner, 8-byte x-pairs.
+__device__ __forceinline__ void encode_f16(const LevelParams& lp, const __half2* __restrict__ table, const float u[3],
+                                           float feat[kIn]) {
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) feat[i] = 0.0f;
+#pragma unroll
+  for (int l = 0; l < kIn / 2; ++l) {
+    if (l >= lp.L) break;
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+    const __half2* tl = table + lp.off[l];
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+      const uint2 q = __ldg(reinterpret_cast<const uint2*>(tl + (i0 & ~1u)));
+      const bool odd = i0 & 1u;
+      const uint32_t a = odd ? q.y : q.x, b = odd ? q.x : q.y;
+      v[e] = __half22float2(*reinterpret_cast<const __half2*>(&a));
+      if ((i0 ^ i1) == 1u) {
+        v[e + 1] = __half22float2(*reinterpret_cast<const __half2*>(&b));
+      } else {
+        v[e + 1] = __half22float2(__ldg(tl + i1));
+      }
+    }
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float w = ((e & 1) ? f[0] : 1.0f - f[0]) * (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) *
+                      (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+      s0 = fmaf(w, v[e].x, s0);
+      s1 = fmaf(w, v[e].y, s1);
+    }
+    feat[2 * l] = s0;
+    feat[2 * l + 1] = s1;
+  }
+}
+
+template <bool kF16Table>
+struct TableOf;
+template <>
+struct TableOf<false> {
+  using T = float2;
+  __device__ static void encode(const LevelParams& lp, const void* t, const float u[3], float feat[kIn]) {
+    encode_f32(lp, static_cast<const float2*>(t), u, feat);
+  }
+};
+template <>
+struct TableOf<true> {
+  using T = __half2;
+  __device__ static void encode(const LevelParams& lp, const void* t, const float u[3], float feat[kIn]) {
+    encode_f16(lp, static_cast<const __half2*>(t), u, feat);
+  }
+};
+
+// Stage region k's 16-bit MLP block into shared memory as FP32 (same
+// transposed layout as load_mlp_f32).
+template <int kMlpType>  // 1 = bf16, 2 = fp16
+__device__ __forceinline__ float mlp_elem(const void* blk, int i) {
+  if (kMlpType == 1) return __bfloat162float(static_cast<const __nv_bfloat16*>(blk)[i]);
+  if (kMlpType == 2) return __half2float(static_cast<const __half*>(blk)[i]);
+  return static_cast<const float*>(blk)[i];
+}
+
+template <int kMlpType>
+__device__ __forceinline__ void load_mlp_any(const void* blk, float* __restrict__ s_w) {
+  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+    const int row = i / kWidth, col = i % kWidth;
+    s_w[col * kIn + row] = mlp_elem<kMlpType>(blk, i);
+  }
+  float* s2 = s_w + kIn * kWidth;
+  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+    const int row = i / kWidth, col = i % kWidth;
+    s2[col * kWidth + row] = mlp_elem<kMlpType>(blk, kIn * kWidth + i);
+  }
+  float* s3 = s2 + kWidth * kWidth;
+  for (int i = threadIdx.x; i < kWidth * kOut; i += blockDim.x) s3[i] = mlp_elem<kMlpType>(blk, kIn * kWidth + kWidth * kWidth + i);
+}
 
 // MLP reading the row-major block W1 [32][64], W2 [64][64], W3 [64][4]
 // straight from global memory (debug views only).

@@ -155,13 +155,14 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
   nerfxl_status rc = validate(f, s, n_rays);
   if (rc != NERFXL_OK) return rc;
   if (!st || !opt || !loss_out) return set_error(NERFXL_E_INVALID, "null train state, optimiser or loss output");
-  if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
-    return set_error(NERFXL_E_UNSUPPORTED, "this training step runs the FP32 path");
   if (!st->tables || !st->mlp || !st->grad_tables || !st->grad_mlp || !st->m_tables || !st->v_tables ||
       !st->m_mlp || !st->v_mlp)
     return set_error(NERFXL_E_INVALID, "null train-state pointer");
-  if (st->tables != f->tables || st->mlp != f->mlp)
-    return set_error(NERFXL_E_INVALID, "FP32 path: the field must render from the master parameters");
+  const bool tab32 = f->table_dtype == NERFXL_F32, mlp32 = f->mlp_dtype == NERFXL_F32;
+  if ((tab32 && st->tables != f->tables) || (mlp32 && st->mlp != f->mlp))
+    return set_error(NERFXL_E_INVALID, "an FP32 field block must be the master itself");
+  if ((!tab32 && f->table_dtype != NERFXL_F16) || (!mlp32 && f->mlp_dtype != NERFXL_BF16 && f->mlp_dtype != NERFXL_F16))
+    return set_error(NERFXL_E_UNSUPPORTED, "compute copies must be FP16 tables and BF16/FP16 MLP");
   const size_t need = nerfxl_step_workspace_bytes(f, s, n_rays);
   if (!workspace || ws_bytes < need) return set_error(NERFXL_E_WORKSPACE, "step workspace too small");
   const Layout L = layout(f, s, n_rays, 1);
@@ -189,9 +190,12 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
   rc = nerfxl_render_bwd(f, s, n_rays, rays_o, rays_d, d_rgb, nullptr, nullptr, d_dist, st->grad_tables,
                          st->grad_mlp, workspace, L.total, stream);
   if (rc != NERFXL_OK) return rc;
-  rc = launch_adam(n_tab, st->tables, st->grad_tables, st->m_tables, st->v_tables, opt, nullptr, 0, stream);
+  // masters updated in FP32; 16-bit compute copies refreshed from them
+  rc = launch_adam(n_tab, st->tables, st->grad_tables, st->m_tables, st->v_tables, opt,
+                   tab32 ? nullptr : const_cast<void*>(f->tables), tab32 ? 0 : 1, stream);
   if (rc != NERFXL_OK) return rc;
-  return launch_adam(n_mlp, st->mlp, st->grad_mlp, st->m_mlp, st->v_mlp, opt, nullptr, 0, stream);
+  return launch_adam(n_mlp, st->mlp, st->grad_mlp, st->m_mlp, st->v_mlp, opt, mlp32 ? nullptr : const_cast<void*>(f->mlp),
+                     mlp32 ? 0 : (f->mlp_dtype == NERFXL_BF16 ? 2 : 1), stream);
 }
 
 }  // extern "C"

@@ -84,3 +84,78 @@ def test_mixed_forward_deterministic():
     b = api.render_fwd(gf, H.sampling(w), o, d)
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+def _grad_close(g, ref, tol):
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    err = np.abs(g - ref) / max(np.abs(ref).max(), 1e-30)
+    return float(np.mean(err > tol)), float(err.max())
+
+
+@pytest.mark.parametrize("tab,mlp", [(torch.float16, torch.bfloat16), (torch.float32, torch.float16)])
+def test_mixed_backward_matches_oracle(tab, mlp):
+    """Gradients of the mixed form against the oracle run on the rounded
+    parameters. The backward recomputes activations in FP32 from the 16-bit
+    parameters, while the chunk adjoints come from the tensor-core forward
+    (16-bit activations), so the bound is the forward's relative error
+    (~1e-4 for BF16) scaled by the adjoint chain: 2e-3 of max|g|, with the
+    ReLU-kink allowance of the FP32 test (0.1% of entries, 100x)."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 1024, 5)
+    o, d = o[sel].copy(), d[sel].copy()
+    R = len(o)
+    g = sy.rng(21, "misc")
+    gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
+    gf = H.gpu_field(w, t, m, table_dtype=tab, mlp_dtype=mlp)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(gC), dev(gD), dev(gA), dev(gL))
+    tq = _rounded(t, tab) if tab != torch.float32 else t
+    gt_ref, gm_ref = oracle.render_grad(H.oracle_field(w, tq, _rounded(m, mlp)), w.S, o, d, gC, gD, gA, gL)
+    ft, et = _grad_close(gt.cpu().numpy(), gt_ref, 2e-3)
+    fm, em = _grad_close(gm.cpu().numpy(), gm_ref, 2e-3)
+    print("mixed backward tables=%s mlp=%s: tables frac>bound %.1e max %.2e; mlp frac %.1e max %.2e"
+          % (tab, mlp, ft, et, fm, em))
+    assert ft <= 1e-3 and et <= 0.2 and fm <= 1e-3 and em <= 0.2
+
+
+@pytest.mark.slow
+def test_mixed_training_gains():
+    """Training with FP16 tables, BF16 MLP and FP32 Adam masters (the c3 form)
+    on the Gaussian-blob target: held-out PSNR rises well above the initial
+    field's."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("train8", L=16, log2_T=16)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    P = oracle.mlp_params(w.mlp_in, w.W)
+    t0, m0 = sy.field_params(w, E, P, table_std=1e-4, mlp_std=0.1, table_init="uniform")
+    blobs = sy.blobs(200, w.seed)
+    o_tr, d_tr = sy.orbit_cameras(16, 3.0, 64, 64, 50.0, 0, 20)
+    o_te, d_te = sy.orbit_cameras(4, 3.0, 64, 64, 50.0, 16, 20)
+    of = H.oracle_field(w, t0, m0)
+    tgt_tr = oracle.blob_render(of, w.S, o_tr, d_tr, blobs)[0].astype(np.float32)
+    tgt_te = oracle.blob_render(of, w.S, o_te, d_te, blobs)[0]
+    gf = H.gpu_field(w, t0, m0, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+    tr = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=t0, master_mlp=m0)
+    g = sy.rng(16, "batch")
+    o_dev, d_dev, tgt_dev = (torch.from_numpy(a).cuda() for a in (o_tr, d_tr, tgt_tr))
+    for s in range(400):
+        idx = torch.from_numpy(g.integers(0, len(o_tr), 8192)).cuda()
+        tr.step(o_dev[idx], d_dev[idx], tgt_dev[idx])
+    out = api.render_fwd(gf, H.sampling(w), o_te, d_te)
+    mse = float(np.mean((out["rgb"].cpu().numpy() - tgt_te) ** 2))
+    psnr = 10 * np.log10(1 / mse)
+    init = 10 * np.log10(1 / float(np.mean((oracle.render(of, w.S, o_te, d_te, 1)["rgb"] - tgt_te) ** 2)))
+    print("mixed training held-out PSNR: initial %.2f, trained %.2f" % (init, psnr))
+    assert psnr > init + 6.0
+    # the compute copies track the FP32 masters
+    assert torch.equal(gf.tables, tr.tables.to(torch.float16))
+    assert torch.equal(gf.mlp, tr.mlp.to(torch.bfloat16))

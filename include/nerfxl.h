@@ -194,6 +194,42 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
                           const nerfxl_train_state* st, const nerfxl_adam* opt, float* loss_out, void* workspace,
                           size_t ws_bytes, cudaStream_t stream);
 
+/* A pinhole camera (row-major pixels, pixel centres, vertical field of view). */
+typedef struct nerfxl_camera {
+  float origin[3];
+  float right[3], up[3], forward[3]; /* orthonormal camera frame */
+  float tan_half_fov;                /* tan of half the vertical field of view */
+  int32_t width, height;
+  int32_t reserved;
+} nerfxl_camera;
+
+/* One contiguous range of one camera's pixels inside a rendering batch. */
+typedef struct nerfxl_ray_item {
+  int64_t batch_offset; /* first ray of the item in the batch (items sorted, contiguous from 0) */
+  int64_t first_pixel;  /* row-major index of its first pixel in the camera image */
+  int64_t out_offset;   /* output slot of its first pixel */
+  int32_t camera;       /* index into cams */
+  int32_t count;        /* number of pixels */
+} nerfxl_ray_item;
+
+/* Workspace of nerfxl_render_cameras for batches of up to max_rays rays. */
+size_t nerfxl_render_cameras_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t max_rays);
+
+/*
+ * Render a batch of pixel ranges from many cameras in one pass (the device
+ * side of the serving loop). items [n_items] and cams [n_cams] are DEVICE arrays; the
+ * batch has n_rays = sum of item counts rays, generated on the device from
+ * the cameras. Pixel p of item it is written to rgb [(out_offset + p) * 3],
+ * depth and opacity [out_offset + p]. A ray's result does not depend on the
+ * rest of the batch, so a request renders identically alone or mixed. A ray
+ * that falls outside its item, its image or the camera list is skipped (no
+ * output written).
+ */
+nerfxl_status nerfxl_render_cameras(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, int32_t n_items,
+                                    const nerfxl_ray_item* items, const nerfxl_camera* cams, int32_t n_cams,
+                                    float* rgb, float* depth, float* opacity, void* workspace, size_t ws_bytes,
+                                    cudaStream_t stream);
+
 /*
  * Forward render without a caller workspace (the paper has no counterpart:
  * this serves callers that cannot allocate device memory, such as plain C

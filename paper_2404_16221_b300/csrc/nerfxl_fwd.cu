@@ -250,9 +250,11 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
 __global__ void __launch_bounds__(256) k_composite(int64_t R, SampParams sp, const RayHdr* __restrict__ hdr,
                                                    const float4* __restrict__ partials, float* __restrict__ rgb,
                                                    float* __restrict__ depth, float* __restrict__ opacity,
-                                                   float* __restrict__ dist) {
+                                                   float* __restrict__ dist, const int64_t* __restrict__ out_index) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
+  const int64_t o = out_index ? out_index[r] : r;  // output slot of this ray
+  if (o < 0) return;
   const RayHdr h = hdr[r];
   float T = 1.0f, tau = 0.0f, comp = 0.0f;
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f, D = 0.0f, L = 0.0f;
@@ -272,12 +274,12 @@ __global__ void __launch_bounds__(256) k_composite(int64_t R, SampParams sp, con
     tau = s;
     T = expf(-tau);
   }
-  rgb[3 * r + 0] = C0;
-  rgb[3 * r + 1] = C1;
-  rgb[3 * r + 2] = C2;
-  depth[r] = D + A * h.tn;
-  opacity[r] = A;
-  if (dist) dist[r] = L;
+  rgb[3 * o + 0] = C0;
+  rgb[3 * o + 1] = C1;
+  rgb[3 * o + 2] = C2;
+  depth[o] = D + A * h.tn;
+  opacity[o] = A;
+  if (dist) dist[o] = L;
 }
 
 // ---------------------------------------------------------------------------
@@ -484,6 +486,17 @@ size_t nerfxl_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, i
 nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
                                 const float* rays_o, const float* rays_d, float* rgb, float* depth, float* opacity,
                                 float* dist, void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  return render_fwd_impl(f, s, n_rays, rays_o, rays_d, rgb, depth, opacity, dist, nullptr, workspace, ws_bytes,
+                         stream);
+}
+
+}  // extern "C"
+
+namespace nerfxl {
+
+nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
+                              const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,
+                              const int64_t* out_index, void* workspace, size_t ws_bytes, cudaStream_t stream) {
   nerfxl_status st = validate(f, s, n_rays);
   if (st != NERFXL_OK) return st;
   const bool tab_ok = f->table_dtype == NERFXL_F32 || f->table_dtype == NERFXL_F16;
@@ -504,7 +517,7 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
     if (st != NERFXL_OK) return st;
     k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
         n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
-        rgb, depth, opacity, dist);
+        rgb, depth, opacity, dist, out_index);
     return launch_check("k_composite");
   }
 
@@ -531,9 +544,13 @@ nerfxl_status nerfxl_render_fwd(const nerfxl_field* f, const nerfxl_sampling* s,
   st = launch_check("k_field_fwd_f32");
   if (st != NERFXL_OK) return st;
   k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.partials, rgb, depth, opacity,
-                                                                dist);
+                                                                dist, out_index);
   return launch_check("k_composite");
 }
+
+}  // namespace nerfxl
+
+extern "C" {
 
 nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!workspace || ws_bytes < 64) return set_error(NERFXL_E_WORKSPACE, "no workspace");

@@ -41,6 +41,10 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
 // dominant kernel) if the caller installed one.
 void profile_mark(int which, cudaStream_t stream);
 int fwd_grid(int64_t max_tiles, int ctas_per_sm);
+// Forward render; out_index (device [R], may be NULL) gives each ray's output slot.
+nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
+                              const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,
+                              const int64_t* out_index, void* workspace, size_t ws_bytes, cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,

@@ -46,6 +46,16 @@ class TrainStateDesc(C.Structure):
                                           "m_mlp", "v_mlp")]
 
 
+class CameraDesc(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3), ("forward", C.c_float * 3),
+                ("tan_half_fov", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("reserved", C.c_int32)]
+
+
+class RayItemDesc(C.Structure):
+    _fields_ = [("batch_offset", C.c_int64), ("first_pixel", C.c_int64), ("out_offset", C.c_int64),
+                ("camera", C.c_int32), ("count", C.c_int32)]
+
+
 class SamplingDesc(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("max_segments", C.c_int32), ("t_min", C.c_float), ("flags", C.c_int32)]
 
@@ -72,6 +82,8 @@ SIGNATURES = {
     "nerfxl_adam_update": (C.c_int, [_i64, _vp, _vp, _vp, _vp, C.c_void_p, _vp, _i32, _vp]),
     "nerfxl_step_workspace_bytes": (_sz, [_FP, _SP, _i64]),
     "nerfxl_step": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "nerfxl_render_cameras_workspace_bytes": (_sz, [_FP, _SP, _i64]),
+    "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_segments": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_samples": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }

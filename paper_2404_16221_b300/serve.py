@@ -1,0 +1,265 @@
+"""Continuous-batching render server over the C ABI (nerfxl_render_cameras).
+
+Requests (a pinhole camera and an image size) arrive over time. The engine
+keeps the field and every admitted request's state on the device: its camera
+in a device camera table and its output image in a fixed-capacity device
+arena. A request is admitted when its image fits in the arena (admission by
+memory). Each iteration forms a batch of up to ``max_batch_rays`` pixels taken
+first-in-first-out from the admitted requests (a large request spans several
+batches; small ones share a batch with others) and renders it with one call,
+whose field kernel is a persistent launch over the whole batch. At most two
+batches are in flight, so requests that arrive while the GPU works are
+admitted into the next batch. Completion times are device times (CUDA events
+aligned to the host clock at start), so latency = device completion - arrival.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import time
+from collections import deque
+
+import numpy as np
+import torch
+
+from . import api
+from . import native as N
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    height: int
+    width: int
+    eye: tuple
+    target: tuple
+    fov_deg: float = 60.0
+    # filled by the engine
+    slot: int = -1          # first pixel slot in the arena
+    cam: int = -1           # camera table entry
+    next_pixel: int = 0
+    done_s: float = math.nan
+    result: dict | None = None
+
+    @property
+    def pixels(self) -> int:
+        return int(self.height) * int(self.width)
+
+
+class Arena:
+    """First-fit allocator of pixel slots (the device image memory)."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        self.free = [(0, self.capacity)]  # sorted (start, length)
+
+    def alloc(self, n: int) -> int:
+        for i, (s, l) in enumerate(self.free):
+            if l >= n:
+                if l == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (s + n, l - n)
+                return s
+        return -1
+
+    def release(self, s: int, n: int):
+        self.free.append((s, n))
+        self.free.sort()
+        merged = []
+        for a, l in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == a:
+                merged[-1] = (merged[-1][0], merged[-1][1] + l)
+            else:
+                merged.append((a, l))
+        self.free = merged
+
+    @property
+    def used(self) -> int:
+        return self.capacity - sum(l for _, l in self.free)
+
+
+def camera_desc(req: Request) -> N.CameraDesc:
+    eye = np.asarray(req.eye, np.float64)
+    f = np.asarray(req.target, np.float64) - eye
+    f /= np.linalg.norm(f)
+    up = np.array([0.0, 0.0, 1.0])
+    if abs(float(f @ up)) > 0.999:
+        up = np.array([0.0, 1.0, 0.0])
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    c = N.CameraDesc()
+    for i in range(3):
+        c.origin[i], c.right[i], c.up[i], c.forward[i] = eye[i], r[i], u[i], f[i]
+    c.tan_half_fov = math.tan(math.radians(req.fov_deg) / 2.0)
+    c.width, c.height, c.reserved = int(req.width), int(req.height), 0
+    return c
+
+
+def camera_rays(req: Request):
+    """Host copy of the rays nerfxl_render_cameras generates for a request
+    (same formula; used to check a served image against a plain render)."""
+    c = camera_desc(req)
+    r, u, f = (np.array(list(v), np.float32) for v in (c.right, c.up, c.forward))
+    js, is_ = np.meshgrid(np.arange(req.width, dtype=np.float32), np.arange(req.height, dtype=np.float32))
+    x = ((js + 0.5) / req.width * 2 - 1) * np.float32(c.tan_half_fov) * np.float32(req.width / req.height)
+    y = (1 - (is_ + 0.5) / req.height * 2) * np.float32(c.tan_half_fov)
+    d = x[..., None] * r + y[..., None] * u + f
+    d = (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3).astype(np.float32)
+    o = np.broadcast_to(np.array(list(c.origin), np.float32), d.shape).copy()
+    return o, d
+
+
+class ServeEngine:
+    def __init__(self, field: api.PartitionedField, samp: api.Sampling, max_batch_rays: int = 1 << 20,
+                 arena_pixels: int = 1 << 26, max_cameras: int = 4096, max_inflight: int = 2,
+                 one_at_a_time: bool = False, keep_results: bool = False):
+        self.field, self.samp = field, samp
+        self.dev = field.device
+        self.max_batch = int(max_batch_rays)
+        self.one_at_a_time = one_at_a_time
+        self.max_inflight = 1 if one_at_a_time else int(max_inflight)
+        self.keep_results = keep_results
+        self.arena = Arena(arena_pixels)
+        self.rgb = torch.empty(arena_pixels, 3, device=self.dev)
+        self.depth = torch.empty(arena_pixels, device=self.dev)
+        self.opacity = torch.empty(arena_pixels, device=self.dev)
+        self.max_cameras = max_cameras
+        self.cams_host = (N.CameraDesc * max_cameras)()
+        self.cams_dev = torch.empty(max_cameras * ctypes.sizeof(N.CameraDesc), dtype=torch.uint8, device=self.dev)
+        self.free_cams = deque(range(max_cameras))
+        fd, sd = field.desc(), samp.desc()
+        wsb = int(N.lib().nerfxl_render_cameras_workspace_bytes(ctypes.byref(fd), ctypes.byref(sd), self.max_batch))
+        if wsb == 0:
+            N.check(N.E_INVALID, "nerfxl_render_cameras_workspace_bytes")
+        nbuf = self.max_inflight
+        self.ws = [torch.empty(wsb, dtype=torch.uint8, device=self.dev) for _ in range(nbuf)]
+        self.max_items = 4096
+        isz = ctypes.sizeof(N.RayItemDesc)
+        self.items_host = [torch.empty(self.max_items * isz, dtype=torch.uint8).pin_memory() for _ in range(nbuf)]
+        self.items_dev = [torch.empty(self.max_items * isz, dtype=torch.uint8, device=self.dev) for _ in range(nbuf)]
+        self.stream = torch.cuda.current_stream(self.dev)
+
+    # -- device state of a request
+    def _admit(self, req: Request) -> bool:
+        if req.pixels > self.arena.capacity:
+            raise ValueError("request %d needs %d pixel slots, the arena holds %d" % (req.rid, req.pixels,
+                                                                                      self.arena.capacity))
+        if not self.free_cams:
+            return False
+        s = self.arena.alloc(req.pixels)
+        if s < 0:
+            return False
+        req.slot = s
+        req.cam = self.free_cams.popleft()
+        self.cams_host[req.cam] = camera_desc(req)
+        csz = ctypes.sizeof(N.CameraDesc)
+        src = torch.frombuffer(bytearray(bytes(self.cams_host[req.cam])), dtype=torch.uint8)
+        self.cams_dev[req.cam * csz:(req.cam + 1) * csz].copy_(src, non_blocking=False)
+        req.next_pixel = 0
+        return True
+
+    def _release(self, req: Request):
+        if self.keep_results:
+            s, n = req.slot, req.pixels
+            req.result = {"rgb": self.rgb[s:s + n].clone(), "depth": self.depth[s:s + n].clone(),
+                          "opacity": self.opacity[s:s + n].clone()}
+        self.arena.release(req.slot, req.pixels)
+        self.free_cams.append(req.cam)
+
+    def _launch(self, active: deque, buf: int):
+        """One batch: FIFO pixel ranges from the admitted requests."""
+        items = (N.RayItemDesc * self.max_items).from_buffer(self.items_host[buf].numpy())
+        n_items = 0
+        n_rays = 0
+        finished = []
+        while active and n_rays < self.max_batch and n_items < self.max_items:
+            req = active[0]
+            take = min(req.pixels - req.next_pixel, self.max_batch - n_rays)
+            it = items[n_items]
+            it.batch_offset, it.first_pixel, it.out_offset = n_rays, req.next_pixel, req.slot + req.next_pixel
+            it.camera, it.count = req.cam, take
+            n_items += 1
+            n_rays += take
+            req.next_pixel += take
+            if req.next_pixel == req.pixels:
+                finished.append(active.popleft())
+            if self.one_at_a_time:
+                break
+        nbytes = n_items * ctypes.sizeof(N.RayItemDesc)
+        self.items_dev[buf][:nbytes].copy_(self.items_host[buf][:nbytes], non_blocking=True)
+        fd, sd = self.field.desc(), self.samp.desc()
+        st = N.lib().nerfxl_render_cameras(ctypes.byref(fd), ctypes.byref(sd), n_rays, n_items,
+                                           N._ptr(self.items_dev[buf]), N._ptr(self.cams_dev), self.max_cameras,
+                                           N._ptr(self.rgb), N._ptr(self.depth), N._ptr(self.opacity),
+                                           N._ptr(self.ws[buf]), self.ws[buf].numel(), N._stream(self.stream))
+        N.check(st, "nerfxl_render_cameras")
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(self.stream)
+        return ev, finished, n_rays
+
+    def run(self, requests, realtime: bool = True):
+        """Serve the requests (sorted by arrival). Returns metrics; fills
+        each request's done_s (and result if keep_results)."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival_s))
+        active = deque()
+        inflight = deque()
+        torch.cuda.synchronize()
+        t0_ev = torch.cuda.Event(enable_timing=True)
+        t0_ev.record(self.stream)
+        t0_ev.synchronize()
+        t0 = time.perf_counter()
+        done = []
+        total_rays = 0
+        n_batches = 0
+        buf = 0
+        peak_arena = 0
+        while pending or active or inflight:
+            now = time.perf_counter() - t0
+            # admission by memory (FIFO: a request waits until it fits)
+            while pending and (not realtime or pending[0].arrival_s <= now):
+                if not self._admit(pending[0]):
+                    break
+                active.append(pending.popleft())
+            peak_arena = max(peak_arena, self.arena.used)
+            progressed = False
+            if active and len(inflight) < self.max_inflight:
+                ev, fin, nr = self._launch(active, buf)
+                inflight.append((ev, fin))
+                buf = (buf + 1) % len(self.ws)
+                total_rays += nr
+                n_batches += 1
+                progressed = True
+            while inflight and (inflight[0][0].query() or (len(inflight) >= self.max_inflight and not active
+                                                          and not pending)):
+                ev, fin = inflight.popleft()
+                ev.synchronize()
+                t_dev = t0_ev.elapsed_time(ev) / 1000.0
+                for r in fin:
+                    r.done_s = t_dev
+                    self._release(r)
+                    done.append(r)
+                progressed = True
+            if not progressed:
+                if inflight:
+                    time.sleep(20e-6)
+                elif pending and realtime:
+                    time.sleep(max(0.0, min(1e-3, pending[0].arrival_s - (time.perf_counter() - t0))))
+        lat = np.array([r.done_s - r.arrival_s for r in done]) * 1000.0
+        span = max(r.done_s for r in done) - min(r.arrival_s for r in done) if done else 0.0
+        return {"requests": len(done), "rays": int(total_rays), "batches": n_batches,
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "mean_ms": float(lat.mean()) if len(lat) else None,
+                "rays_per_s": total_rays / span if span > 0 else None, "span_s": span,
+                "peak_arena_pixels": int(peak_arena)}
+
+
+def requests_from_stream(n: int, rate_hz: float, seed: int, **kw):
+    from . import synthetic as sy
+
+    t, H, W, eye, tgt = sy.request_stream(n, rate_hz, seed, **kw)
+    return [Request(i, float(t[i]), int(H[i]), int(W[i]), tuple(eye[i]), tuple(tgt[i])) for i in range(n)]

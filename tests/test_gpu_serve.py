@@ -1,0 +1,93 @@
+"""Serving loop on the GPU: continuous batching of uneven render requests."""
+import numpy as np
+import pytest
+
+from paper_2404_16221_b300 import synthetic as sy
+
+import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_16221_b300 import build
+
+    build.build()
+
+
+def _city(table_dtype=torch.float16, mlp_dtype=torch.bfloat16):
+    w = H.workload("serve32", L=16, log2_T=16)
+    t, m = H.params(w, table_std=1.0, mlp_std=0.1)
+    return w, H.gpu_field(w, t, m, table_dtype=table_dtype, mlp_dtype=mlp_dtype)
+
+
+def _requests(n, seed, h_max=200):
+    from paper_2404_16221_b300 import serve
+
+    return serve.requests_from_stream(n, 200.0, seed, h_min=16, h_max=h_max, w_min=16, w_max=356)
+
+
+def test_served_image_matches_plain_render():
+    from paper_2404_16221_b300 import api, serve
+
+    w, field = _city()
+    req = serve.Request(0, 0.0, 48, 80, (0.3, -1.5, 2.5), (0.5, 0.5, 0.1))
+    eng = serve.ServeEngine(field, H.sampling(w), max_batch_rays=1000, arena_pixels=1 << 16, keep_results=True)
+    eng.run([req], realtime=False)
+    o, d = serve.camera_rays(req)
+    ref = api.render_fwd(field, H.sampling(w), o, d)
+    for k in ("rgb", "opacity"):
+        err = (req.result[k] - ref[k]).abs()
+        # device and host ray generation round differently in the last bits
+        assert float(err.max()) < 1e-3 and float(err.mean()) < 1e-5, (k, float(err.max()))
+
+
+def test_each_request_identical_alone_and_in_the_mix():
+    from paper_2404_16221_b300 import serve
+
+    w, field = _city()
+    samp = H.sampling(w)
+    reqs = _requests(12, 7)
+    alone = {}
+    for r in reqs:
+        rr = serve.Request(r.rid, 0.0, r.height, r.width, r.eye, r.target)
+        serve.ServeEngine(field, samp, max_batch_rays=1 << 16, arena_pixels=1 << 18, keep_results=True).run(
+            [rr], realtime=False)
+        alone[r.rid] = rr.result
+    # in the mix: small batches so that requests share batches and split across them
+    eng = serve.ServeEngine(field, samp, max_batch_rays=7777, arena_pixels=1 << 18, keep_results=True)
+    m = eng.run(reqs, realtime=False)
+    assert m["requests"] == len(reqs) and m["batches"] > len(reqs) // 2
+    for r in reqs:
+        for k in ("rgb", "depth", "opacity"):
+            assert torch.equal(r.result[k], alone[r.rid][k]), (r.rid, k)
+
+
+def test_admission_by_memory():
+    from paper_2404_16221_b300 import serve
+
+    w, field = _city()
+    reqs = _requests(20, 9, h_max=120)
+    cap = max(r.pixels for r in reqs) * 2  # only a couple fit at once
+    eng = serve.ServeEngine(field, H.sampling(w), max_batch_rays=20000, arena_pixels=cap)
+    m = eng.run(reqs, realtime=False)
+    assert m["requests"] == 20 and m["peak_arena_pixels"] <= cap
+    big = serve.Request(99, 0.0, 1000, 1000, (0, -2, 2), (0, 0, 0))
+    with pytest.raises(ValueError):
+        serve.ServeEngine(field, H.sampling(w), arena_pixels=1 << 16).run([big], realtime=False)
+
+
+def test_poisson_stream_reports_latency():
+    from paper_2404_16221_b300 import serve
+
+    w, field = _city()
+    reqs = _requests(40, 11)
+    m = serve.ServeEngine(field, H.sampling(w), max_batch_rays=1 << 18, arena_pixels=1 << 22).run(reqs)
+    print("poisson 200 req/s:", m)
+    assert m["requests"] == 40 and m["p50_ms"] > 0 and m["p99_ms"] >= m["p50_ms"]
+    for r in reqs:
+        assert r.done_s >= r.arrival_s

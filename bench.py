@@ -2,11 +2,16 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-A step renders one batch of the grid8 workload (K=8 regions, 2x2x2 over
-[-1,1]^3, L=16 F=2 T=2^19 levels 16->2048, 2^18 rays from 64 pinhole cameras,
-128 samples per ray) through the C ABI, FP32 plain path. Under torchrun each
-rank renders its own batch on its own GPU (rays are independent: weak
-scaling, no data-path collective). Prints one JSON line on rank 0.
+The headline step is one training step of the grid8 workload (K=8 regions,
+2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 levels 16->2048, 2^18 rays from 64
+pinhole cameras, 128 samples per ray) through the C ABI on the FP32 plain
+path: sampling, gather, MLP, local render, composite, loss, backward, Adam.
+Beside it, under "forms": forward renders (FP32 and FP16 tables + BF16 MLP),
+the mixed-precision training step, the city32 MLP precision variants (K=32,
+2^20 rays, 256 samples) and the serving loop (Poisson 200 req/s) next to
+one-request-at-a-time FP32 rendering. Under torchrun each rank works on its
+own batch on its own GPU (rays are independent: weak scaling, no data-path
+collective). Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -37,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-rays", type=int, default=1 << 14, help="oracle sample size for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-city", action="store_true", help="skip the city32 precision and serving forms")
+    ap.add_argument("--serve-requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -182,6 +189,18 @@ def time_steps(step, steps, flush, stream, prof=True):
     return [a.elapsed_time(b) for a, b in ev], ([a.elapsed_time(b) for a, b in kev] if prof else [])
 
 
+def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
+    """CUDA-core FP32 peak: SMs x 128 FMA lanes x 2 FLOP x max SM clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# Algorithmic FLOPs of the MLP per sample (32-64-64-4, multiply-add = 2 FLOP):
+# forward 2 (32*64 + 64*64 + 64*4) = 12,800; the backward recomputes the
+# forward, then dX (12,800) and dW (12,800): 38,400 per sample.
+MLP_FWD_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 4)
+BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -194,7 +213,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2404_16221_b300 import api, build, native as N
+    from paper_2404_16221_b300 import api, build, native as N, serve, synthetic as sy
 
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -210,22 +229,19 @@ def main():
     stream = torch.cuda.current_stream()
     steps, warm = args.steps, max(3, args.warmup)
 
-    def mk_field(tab_dtype, mlp_dtype):
-        return api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(tables).to(tab_dtype),
-                                    torch.from_numpy(mlp).to(mlp_dtype), device=dev)
+    def mk_field(wl, t, m, tab_dtype, mlp_dtype):
+        return api.PartitionedField(wl.boxes, wl.level_res, wl.log2_T, torch.as_tensor(t).to(dev, tab_dtype),
+                                    torch.as_tensor(m).to(dev, mlp_dtype), device=dev)
 
-    def out_bufs():
-        return {"rgb": torch.empty(R, 3, device=dev), "depth": torch.empty(R, device=dev),
-                "opacity": torch.empty(R, device=dev), "dist": torch.empty(R, device=dev)}
+    def out_bufs(n):
+        return {"rgb": torch.empty(n, 3, device=dev), "depth": torch.empty(n, device=dev),
+                "opacity": torch.empty(n, device=dev), "dist": torch.empty(n, device=dev)}
 
-    forms = {}
-    # forward, FP32 plain path and the mixed form (FP16 tables, BF16 MLP on tensor cores)
-    for name, td, md in (("fwd_fp32", torch.float32, torch.float32), ("fwd_f16tab_bf16mlp", torch.float16,
-                                                                      torch.bfloat16)):
-        field = mk_field(td, md)
-        ws = api.alloc_workspace(field, samp, R)
-        out = out_bufs()
-        step = lambda field=field, ws=ws, out=out: api.render_fwd(field, samp, o_dev, d_dev, workspace=ws, out=out)
+    def fwd_form(wl, field, sp, ro, rd, kernel, bytes_per_sample):
+        n = ro.shape[0]
+        ws = api.alloc_workspace(field, sp, n)
+        out = out_bufs(n)
+        step = lambda: api.render_fwd(field, sp, ro, rd, workspace=ws, out=out)
         for _ in range(warm):
             step()
         api.check(ws)
@@ -233,26 +249,48 @@ def main():
         N.check(N.lib().nerfxl_workspace_stats(N._ptr(ws), ws.numel(), ns, nc, N._stream(None)), "stats")
         with Clocks(local) as clk:
             step_ms, kern_ms = time_steps(step, steps, flush, stream)
-        forms[name] = {"field": field, "ws": ws, "out": out, "step": step, "step_ms": step_ms, "kern_ms": kern_ms,
-                       "samples": ns.value, "chunks": nc.value, "clocks": clk.summary(),
-                       "kernel": "k_field_fwd_f32" if md == torch.float32 else "k_field_fwd_tc",
-                       "bytes_per_sample": 8 * w.F * (4 if td == torch.float32 else 2) * w.L}
-        del field
-    # training step, FP32 (forward + loss + backward + Adam), random target colours
-    tfield = mk_field(torch.float32, torch.float32)
-    trainer = api.Trainer(tfield, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
+        return {"rays": n, "step_ms": step_ms, "kern_ms": kern_ms, "samples": ns.value, "chunks": nc.value,
+                "clocks": clk.summary(), "kernel": kernel, "bytes_per_sample": bytes_per_sample,
+                "field": field, "ws": ws, "out": out, "step": step}
+
+    forms = {}
+    # ---- grid8 (K=8): forward forms
+    f32 = mk_field(w, tables, mlp, torch.float32, torch.float32)
+    forms["grid8_fwd_fp32"] = fwd_form(w, f32, samp, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
+    fmix = mk_field(w, tables, mlp, torch.float16, torch.bfloat16)
+    forms["grid8_fwd_f16tab_bf16mlp"] = fwd_form(w, fmix, samp, o_dev, d_dev, "k_field_fwd_tc", 8 * w.F * 2 * w.L)
+    for k in ("grid8_fwd_fp32", "grid8_fwd_f16tab_bf16mlp"):
+        forms[k].pop("field"), forms[k].pop("ws"), forms[k].pop("out"), forms[k].pop("step")
+    del fmix
+    # ---- grid8 training steps: FP32 (the headline) and FP16 tables + BF16 MLP + FP32 Adam
     tgt = torch.rand(R, 3, generator=torch.Generator().manual_seed(1002)).to(dev)
+    trainer = api.Trainer(f32, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
     tstep = lambda: trainer.step(o_dev, d_dev, tgt)
     for _ in range(warm):
         tstep()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         step_ms, kern_ms = time_steps(tstep, steps, flush, stream)
-    forms["train_fp32"] = {"step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
-                           "kernel": "k_field_bwd_f32", "samples": forms["fwd_fp32"]["samples"]}
-    del trainer, tfield
-    # training step in the mixed form: FP16 tables, BF16 MLP, FP32 Adam masters
-    mfield = mk_field(torch.float16, torch.bfloat16)
+    forms["grid8_train_fp32"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
+                                 "kernel": "k_field_bwd_f32", "samples": forms["grid8_fwd_fp32"]["samples"],
+                                 "flop_per_sample": BWD_FLOP_PER_SAMPLE}
+    # end to end through host buffers: rays and targets in, the loss out
+    o_h, d_h = torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()
+    t_h = tgt.cpu().pin_memory()
+    loss_h = torch.empty(3).pin_memory()
+
+    def e2e_step():
+        o_dev.copy_(o_h, non_blocking=True)
+        d_dev.copy_(d_h, non_blocking=True)
+        tgt.copy_(t_h, non_blocking=True)
+        loss = trainer.step(o_dev, d_dev, tgt)
+        loss_h.copy_(loss, non_blocking=True)
+
+    for _ in range(warm):
+        e2e_step()
+    e2e_ms, _ = time_steps(e2e_step, steps, flush, stream, prof=False)
+    del trainer, f32
+    mfield = mk_field(w, tables, mlp, torch.float16, torch.bfloat16)
     mtrainer = api.Trainer(mfield, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=torch.from_numpy(tables),
                            master_mlp=torch.from_numpy(mlp))
     mstep = lambda: mtrainer.step(o_dev, d_dev, tgt)
@@ -261,27 +299,54 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         step_ms, kern_ms = time_steps(mstep, steps, flush, stream)
-    forms["train_f16tab_bf16mlp"] = {"step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
-                                     "kernel": "k_field_bwd_f32<f16 tables, bf16 mlp>",
-                                     "samples": forms["fwd_fp32"]["samples"]}
+    forms["grid8_train_f16tab_bf16mlp"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms,
+                                           "clocks": clk.summary(), "kernel": "k_field_bwd_f32<f16 tab, bf16 mlp>",
+                                           "samples": forms["grid8_fwd_fp32"]["samples"],
+                                           "flop_per_sample": BWD_FLOP_PER_SAMPLE}
     del mtrainer, mfield
+    # ---- city32 (K=32, 8x4x1 slabs, 2^20 rays, S=256): MLP precision variants
+    if not args.skip_city:
+        wc = sy.workload("city32")
+        Ec = N.table_entries(wc.level_res, wc.log2_T)
+        tc_, mc_ = sy.field_params_device(wc, Ec, N.mlp_params(wc.mlp_in, wc.W), dev)
+        oc, dc = sy.workload_rays(wc)
+        oc_d, dc_d = torch.from_numpy(oc).to(dev), torch.from_numpy(dc).to(dev)
+        sc = api.Sampling(wc.S, wc.max_segments)
+        for name, td, md, kern in (("city32_fwd_fp32", torch.float32, torch.float32, "k_field_fwd_f32"),
+                                   ("city32_fwd_bf16mlp", torch.float32, torch.bfloat16, "k_field_fwd_tc"),
+                                   ("city32_fwd_fp16mlp", torch.float32, torch.float16, "k_field_fwd_tc"),
+                                   ("city32_fwd_f16tab_bf16mlp", torch.float16, torch.bfloat16, "k_field_fwd_tc")):
+            fc = mk_field(wc, tc_, mc_, td, md)
+            forms[name] = fwd_form(wc, fc, sc, oc_d, dc_d, kern, 8 * wc.F * (4 if td == torch.float32 else 2) * wc.L)
+            for k in ("field", "ws", "out", "step"):
+                forms[name].pop(k)
+            del fc
+            torch.cuda.empty_cache()
+        # ---- serving (K=32 field resident, FP16 tables + BF16 MLP), Poisson arrivals at 200 req/s
+        ws_ = sy.workload("serve32")
+        reqs = serve.requests_from_stream(args.serve_requests, 200.0, ws_.seed)
+        sfield = mk_field(ws_, tc_, mc_, torch.float16, torch.bfloat16)
+        ss = api.Sampling(ws_.S, ws_.max_segments)
+        warm_reqs = serve.requests_from_stream(4, 200.0, ws_.seed + 17)
+        serve.ServeEngine(sfield, ss, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(warm_reqs, realtime=False)
+        with Clocks(local) as clk:
+            m = serve.ServeEngine(sfield, ss, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(reqs)
+        m["clocks"] = clk.summary()
+        forms["serve32_poisson200"] = {"serve": m, "requests": len(reqs),
+                                       "note": "FP16 tables + BF16 MLP, batches of up to 2^20 rays, 2 in flight, "
+                                               "arena 2^26 pixel slots; latency = arrival to device completion"}
+        del sfield
+        torch.cuda.empty_cache()
+        ffield = mk_field(ws_, tc_, mc_, torch.float32, torch.float32)
+        reqs1 = serve.requests_from_stream(args.serve_requests, 200.0, ws_.seed)
+        serve.ServeEngine(ffield, ss, max_batch_rays=1 << 20, one_at_a_time=True).run(warm_reqs[:2], realtime=False)
+        m1 = serve.ServeEngine(ffield, ss, max_batch_rays=1 << 20, arena_pixels=1 << 26, one_at_a_time=True).run(reqs1)
+        forms["serve32_one_at_a_time_fp32"] = {"serve": m1, "requests": len(reqs1),
+                                               "note": "FP32 field, one request per launch, FIFO"}
+        del ffield, tc_, mc_
+        torch.cuda.empty_cache()
 
-    head = forms["fwd_fp32"]
-    # end to end through host buffers for the headline form
-    o_h = torch.from_numpy(o).pin_memory()
-    d_h = torch.from_numpy(d).pin_memory()
-    out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in head["out"].items()}
-
-    def e2e_step():
-        o_dev.copy_(o_h, non_blocking=True)
-        d_dev.copy_(d_h, non_blocking=True)
-        head["step"]()
-        for k in head["out"]:
-            out_h[k].copy_(head["out"][k], non_blocking=True)
-
-    for _ in range(warm):
-        e2e_step()
-    e2e_ms, _ = time_steps(e2e_step, steps, flush, stream, prof=False)
+    head = forms["grid8_train_fp32"]
     t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
@@ -293,39 +358,48 @@ def main():
             dist.destroy_process_group()
         return
     hbm, bf16, src = peaks()
+    alu_peak = fp32_alu_peak_tflops()
 
     def summary(f):
+        if "serve" in f:
+            return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
-        r = {"rays_per_s": R / (ms / 1000.0), "ms_per_step": ms}
+        r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}
         if f.get("kern_ms"):
             km = statistics.mean(f["kern_ms"])
             r["kernel"] = f["kernel"]
             r["kernel_ms"] = km
             if "bytes_per_sample" in f:
                 r["gather_gbs_algorithmic"] = f["samples"] * f["bytes_per_sample"] / (km / 1000.0) / 1e9
+                r["gather_frac_of_hbm"] = r["gather_gbs_algorithmic"] / hbm
+            if "flop_per_sample" in f:
+                r["mlp_tflops_algorithmic"] = f["samples"] * f["flop_per_sample"] / (km / 1000.0) / 1e12
+        r["samples_per_step"] = f.get("samples")
         r["clocks"] = f["clocks"]
         return r
 
     kern_s = statistics.mean(head["kern_ms"]) / 1000.0
-    achieved = head["samples"] * head["bytes_per_sample"] / kern_s / 1e9
+    achieved = head["samples"] * BWD_FLOP_PER_SAMPLE / kern_s / 1e12
     rays_total = R * world * steps
     line = {
         "metric": METRIC, "value": rays_total / t_step, "unit": "rays/s", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": 1000.0 * t_step / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "grid8 render fwd: K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 (16->2048), FP32 tables "
-                               "and MLP 32-64-64-4, 2^18 rays from 64 pinhole cameras, S=128",
-                   "rays_per_gpu": R, "samples_per_step": int(head["samples"]), "chunks_per_step": int(head["chunks"]),
+        "config": {"workload": "grid8 training step (sampling, gather, MLP, local render, composite, loss "
+                               "L2 + 0.01 distortion, backward, Adam): K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 "
+                               "(16->2048), FP32 tables and MLP 32-64-64-4, 2^18 rays from 64 pinhole cameras, S=128",
+                   "rays_per_gpu": R, "samples_per_step": int(head["samples"]),
                    "l2": "flushed before every timed step (252 MB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "train_target": "uniform random colours (throughput does not depend on the target)"},
-        "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(2 * R * 12),
-                "d2h_bytes_per_step": int(R * (12 + 4 + 4 + 4))},
-        "gpu_launches": 5 * steps,
-        "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "basis": "%d B/sample algorithmic gather bytes x %d samples / mean kernel time %.3f ms (%s peak)"
-                              % (head["bytes_per_sample"], head["samples"], 1000 * kern_s, src)},
+        "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(3 * R * 12),
+                "d2h_bytes_per_step": 12},
+        "gpu_launches": 11 * steps,
+        "roofline": {"bound": "alu", "kernel": head["kernel"], "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "basis": "%d FLOP/sample (MLP forward recompute + dX + dW, FP32 CUDA cores) x %d samples / mean "
+                              "kernel time %.3f ms; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz (derived)"
+                              % (BWD_FLOP_PER_SAMPLE, head["samples"], 1000 * kern_s)},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }

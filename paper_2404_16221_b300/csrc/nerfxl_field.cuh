@@ -59,6 +59,87 @@ __device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* 
   }
 }
 
+// Gather of four consecutive levels l0..l0+3 (F = 2) of one sample: out[8]
+// holds their features in level order; levels >= L give zeros.
+template <typename TabT>
+__device__ __forceinline__ void gather4(const LevelParams& lp, const TabT* __restrict__ table, const float u[3], int l0,
+                                        float out[8]);
+
+template <>
+__device__ __forceinline__ void gather4<float2>(const LevelParams& lp, const float2* __restrict__ table,
+                                                const float u[3], int l0, float out[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int l = l0 + q;
+    float s0 = 0.0f, s1 = 0.0f;
+    if (l < lp.L) {
+      int c[3];
+      float f[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+      const float2* tl = table + lp.off[l];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+        const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+        const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+        const float4 qv = __ldg(reinterpret_cast<const float4*>(tl + (i0 & ~1u)));
+        const bool odd = i0 & 1u;
+        const float2 v0 = odd ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
+        float2 v1;
+        if ((i0 ^ i1) == 1u) v1 = odd ? make_float2(qv.x, qv.y) : make_float2(qv.z, qv.w);
+        else v1 = __ldg(tl + i1);
+        const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+        const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+        s0 = fmaf(w0, v0.x, s0);
+        s1 = fmaf(w0, v0.y, s1);
+        s0 = fmaf(w1, v1.x, s0);
+        s1 = fmaf(w1, v1.y, s1);
+      }
+    }
+    out[2 * q] = s0;
+    out[2 * q + 1] = s1;
+  }
+}
+
+template <>
+__device__ __forceinline__ void gather4<__half2>(const LevelParams& lp, const __half2* __restrict__ table,
+                                                 const float u[3], int l0, float out[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int l = l0 + q;
+    float s0 = 0.0f, s1 = 0.0f;
+    if (l < lp.L) {
+      int c[3];
+      float f[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+      const __half2* tl = table + lp.off[l];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+        const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+        const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+        const uint2 qv = __ldg(reinterpret_cast<const uint2*>(tl + (i0 & ~1u)));
+        const bool odd = i0 & 1u;
+        const uint32_t a = odd ? qv.y : qv.x, b = odd ? qv.x : qv.y;
+        const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&a));
+        float2 v1;
+        if ((i0 ^ i1) == 1u) v1 = __half22float2(*reinterpret_cast<const __half2*>(&b));
+        else v1 = __half22float2(__ldg(tl + i1));
+        const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+        const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+        s0 = fmaf(w0, v0.x, s0);
+        s1 = fmaf(w0, v0.y, s1);
+        s0 = fmaf(w1, v1.x, s0);
+        s1 = fmaf(w1, v1.y, s1);
+      }
+    }
+    out[2 * q] = s0;
+    out[2 * q + 1] = s1;
+  }
+}
+
 // MLP with weights staged in shared memory as W1t [64][32] (row n holds
 // column n of W1), W2t [64][64], W3 [64][4]. Layer 2 and 3 are fused per
 // hidden unit so that only h1 stays live.

@@ -2,15 +2,18 @@
 // tensor memory): the mixed-precision forms (BF16 or FP16 MLP with FP32
 // accumulation; FP32 or FP16 hash features).
 //
-// One CTA = 4 warps = one 128-row MMA tile (4 chunks of 32 samples, all of
-// one region). Per tile:
-//   gather   each thread encodes its sample; features -> A0 (bf16/fp16)
+// One CTA = 16 warps on one 128-row MMA tile (4 chunks of 32 samples, all of
+// one region). Warp w serves rows 32 (w % 4) .. + 31 (its TMEM lane quarter)
+// and level group / column block w / 4, so each sample's 16-level gather is
+// spread over four threads that run concurrently. Per tile:
+//   gather   thread (row, g) encodes levels 4g..4g+3 and writes their eight
+//            features as one 16-byte chunk of row `row` of A0 (bf16/fp16)
 //   layer 1  D1[128x64] = A0[128x32] W1            (2 MMAs, K = 16 each)
 //   layer 2  h1 = relu(D1) -> A1; D2 = A1 W2        (4 MMAs)
 //   layer 3  h2 = relu(D2) -> A0; D3[128x16] = A0 W3 (4 MMAs; columns 4..15 zero)
 //   render   sigma = exp(D3[:,0]), rgb = sigmoid(D3[:,1..3]); chunk partial
-// One elected thread issues the MMAs and commits them to an mbarrier; every
-// thread reads its own accumulator row (its TMEM lane) with tcgen05.ld.
+// One elected thread issues the MMAs and commits them to an mbarrier; each
+// warp reads 16 accumulator columns of its lane quarter with tcgen05.ld.
 // Waits on the mbarrier are bounded: on expiry the kernel flags
 // kErrTimeout in the workspace, frees its tensor memory and returns.
 
@@ -25,7 +28,7 @@
 namespace nerfxl {
 
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;  // 16 warps: 4 per TMEM lane quarter
 constexpr int kTcChunks = kTcRows / kWarp;  // 4 chunks per MMA tile
 constexpr uint32_t kTmemCols = 128;         // D1 at column 0, D2 at column 64, D3 reuses column 0
 constexpr uint32_t kSpinLimit = 1u << 24;
@@ -137,7 +140,7 @@ struct FwdTcParams {
 };
 
 template <bool kF16Table, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = tc::smem_u32(sm);
@@ -145,6 +148,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
   int32_t* s_base = reinterpret_cast<int32_t*>(sm + kOffBase);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+  // Warp w owns TMEM lane quarter q = w % 4 (rows 32q..32q+31, i.e. chunk q of
+  // the tile) and level group / column block g = w / 4.
+  const int q = warp & 3, g = warp >> 2;
+  const uint32_t row = (uint32_t)(q * kWarp + lane);
 
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -153,16 +160,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tmem_q = tmem + ((uint32_t)(q * 32) << 16);
 
   constexpr uint32_t idesc64 = tc::idesc_f16(BF16, kTcRows, 64);
   constexpr uint32_t idesc16 = tc::idesc_f16(BF16, kTcRows, 16);
   const uint32_t a0 = sbase + kOffA0, a1 = sbase + kOffA1;
   const uint32_t b1 = sbase + kOffB1, b2 = sbase + kOffB2, b3 = sbase + kOffB3;
+  using TabT = typename TableOf<kF16Table>::T;
 
   const int n_sub = *p.n_tiles * (kChunksPerTile / kTcChunks);
   int region = -1;
-  const void* table = nullptr;
+  const TabT* table = nullptr;
   uint32_t phase = 0;
   bool failed = false;
   for (int t = blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
@@ -171,17 +179,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
       __syncthreads();
       load_weights_tc<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm);
       region = k;
-      table = static_cast<const char*>(p.tables) + (size_t)k * p.lp.E * sizeof(typename TableOf<kF16Table>::T);
+      table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
     }
-    // ---- gather: one sample per thread
-    const uint2 ref = p.chunks[t * kTcChunks + warp];
+    // ---- gather: the four threads of a row each gather four levels
+    const uint2 ref = p.chunks[t * kTcChunks + q];
     const bool chunk_ok = ref.x != kEmptyChunk;
     bool valid = false;
-    float tbar = 0.0f, dl = 0.0f, tr = 0.0f;
-    float feat[kIn];
+    float tr = 0.0f, dl = 0.0f;
+    float f8[8];
 #pragma unroll
-    for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
-    RayHdr h = {0.0f, 0.0f, 0, 0};
+    for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
     SegDesc sd = {0.0f, 0.0f, 0, 0};
     int c = 0;
     uint32_t ray = 0;
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
       ray = ref.x;
       const int seg = ref.y >> 16;
       c = ref.y & 0xFFFF;
-      h = p.hdr[ray];
+      const RayHdr h = p.hdr[ray];
       sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
       const int i = c * kWarp + lane;
       valid = i < seg_n(sd);
@@ -202,16 +209,18 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
         }
         float a, b;
         segment_interval(sd, h.tn, h.delta, i, a, b);
-        tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
         dl = __fsub_rn(b, a);
         tr = __fsub_rn(tbar, h.tn);
         float x[3], u[3];
         sample_point(o, d, tbar, x);
         region_coord(p.boxes + 6 * k, x, u);
-        TableOf<kF16Table>::encode(p.lp, table, u, feat);
+        gather4<TabT>(p.lp, table, u, 4 * g, f8);
       }
     }
-    store_row32<BF16>(a0, tid, feat);
+    tc::st_shared_v4(a0 + tc::sw128_chunk(row, g), Half2Of<BF16>::pack(f8[0], f8[1]),
+                     Half2Of<BF16>::pack(f8[2], f8[3]), Half2Of<BF16>::pack(f8[4], f8[5]),
+                     Half2Of<BF16>::pack(f8[6], f8[7]));
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -230,9 +239,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
       break;
     }
     tc::fence_after_sync();
-    float v[64];
-    tmem_row64_relu(tmem_row + 0, v);
-    store_row64<BF16>(a1, tid, v);
+    float v[16];
+    tc::tmem_ld16(tmem_q + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+    tc::st_shared_v4(a1 + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(v[0], v[1]), Half2Of<BF16>::pack(v[2], v[3]),
+                     Half2Of<BF16>::pack(v[4], v[5]), Half2Of<BF16>::pack(v[6], v[7]));
+    tc::st_shared_v4(a1 + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(v[8], v[9]),
+                     Half2Of<BF16>::pack(v[10], v[11]), Half2Of<BF16>::pack(v[12], v[13]),
+                     Half2Of<BF16>::pack(v[14], v[15]));
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -251,8 +267,15 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
       break;
     }
     tc::fence_after_sync();
-    tmem_row64_relu(tmem_row + 64, v);
-    store_row64<BF16>(a0, tid, v);
+    tc::tmem_ld16(tmem_q + 64 + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+    tc::st_shared_v4(a0 + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(v[0], v[1]), Half2Of<BF16>::pack(v[2], v[3]),
+                     Half2Of<BF16>::pack(v[4], v[5]), Half2Of<BF16>::pack(v[6], v[7]));
+    tc::st_shared_v4(a0 + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(v[8], v[9]),
+                     Half2Of<BF16>::pack(v[10], v[11]), Half2Of<BF16>::pack(v[12], v[13]),
+                     Half2Of<BF16>::pack(v[14], v[15]));
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -271,26 +294,27 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_field_fwd_tc(FwdTcParams p) {
       break;
     }
     tc::fence_after_sync();
-    float raw[16];
-    tc::tmem_ld16(tmem_row + 0, raw);
-    tc::tmem_ld_wait();
-    tc::fence_before_sync();
-    // ---- chunk render
-    if (chunk_ok) {
-      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
-      if (valid) {
-        sigma = expf(raw[0]);
+    // ---- chunk render by the warps of level group 0 (one chunk per warp)
+    if (g == 0) {
+      tc::tmem_ld16(tmem_q, v);
+      tc::tmem_ld_wait();
+      if (chunk_ok) {
+        float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+          sigma = expf(v[0]);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) rgb[q] = 1.0f / (1.0f + expf(-raw[1 + q]));
-      }
-      const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
-      if (lane == 0) {
-        float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
-        dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
-        dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+          for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
+        }
+        const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
+        if (lane == 0) {
+          float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
+          dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
+          dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+        }
       }
     }
-    __syncthreads();  // A0 and TMEM free for the next tile
+    tc::fence_before_sync();
+    __syncthreads();  // A tiles and TMEM free for the next tile
   }
   if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
   tc::fence_before_sync();
@@ -326,7 +350,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   else kern = bf16 ? k_field_fwd_tc<false, true> : k_field_fwd_tc<false, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_fwd_tc smem attribute");
-  const int grid = fwd_grid(L.chunk_cap / kTcChunks, 4);
+  const int grid = fwd_grid(L.chunk_cap / kTcChunks, 2);
   profile_mark(0, stream);
   kern<<<grid, kTcThreads, smem, stream>>>(p);
   profile_mark(1, stream);

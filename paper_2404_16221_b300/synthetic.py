@@ -257,3 +257,16 @@ def request_stream(n_requests: int, rate_hz: float, seed: int, h_min=64, h_max=1
     eye = np.where(aerial[:, None], eye_a, eye_s)
     tgt = np.stack([g.uniform(-4, 4, n_requests), g.uniform(-2, 2, n_requests), g.uniform(0.0, 0.3, n_requests)], -1)
     return t, H, Wd, eye, tgt
+
+
+def field_params_device(w: Workload, E: int, P: int, device, table_std: float = 1.0, mlp_std: float = 0.1):
+    """Large parameter blocks drawn directly on the GPU (seeded torch Philox),
+    for full-size throughput runs; tables [K][E][F] and MLP [K][P] float32."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(w.seed) * 7919 + _STREAMS["tables"])
+    tables = torch.randn((w.K, E, w.F), generator=g, device=device) * table_std
+    g.manual_seed(int(w.seed) * 7919 + _STREAMS["mlp"])
+    mlp = torch.randn((w.K, P), generator=g, device=device) * mlp_std
+    return tables, mlp

@@ -117,37 +117,6 @@ struct BwdParams {
 constexpr size_t kBwdSmemFloats =
     2 * kMlpParams + (size_t)kBwdThreads * kFeatPitch + 2 * (size_t)kBwdThreads * kActPitch;
 
-// Adjoint of the chunk-local render for one warp (one chunk). Inputs per lane:
-// sigma, rgb, t' (tbar - tn), delta; chunk adjoints gtc, gC, gA, gD, gL.
-// Returns dL/d(sigma), dL/d(rgb).
-__device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rgb[3], float tr, float dl, int lane,
-                                                     float gtc, const float gC[3], float gA, float gD, float gL,
-                                                     float& g_sigma, float g_rgb[3]) {
-  const float tau = sigma * dl;
-  const float incl = warp_inclusive_scan(tau, lane);
-  const float excl = warp_exclusive_from_inclusive(incl, lane);
-  const float T = expf(-excl);
-  const float Tn = expf(-incl);
-  const float w = T * -expm1f(-tau);
-  const float wt = w * tr;
-  const float W_in = warp_inclusive_scan(w, lane);
-  const float WT_in = warp_inclusive_scan(wt, lane);
-  const float W_lt = warp_exclusive_from_inclusive(W_in, lane);
-  const float WT_lt = warp_exclusive_from_inclusive(WT_in, lane);
-  const float W_gt = warp_suffix_scan(w, lane) - w;
-  const float WT_gt = warp_suffix_scan(wt, lane) - wt;
-  // sum_j w_j |t_i - t_j| over the chunk
-  const float pair = (tr * W_lt - WT_lt) + (WT_gt - tr * W_gt);
-  const float gw = gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2] + gA + gD * tr +
-                   gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
-  const float gww = gw * w;
-  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
-  const float g_tau = gtc + gw * Tn - later;
-  g_sigma = g_tau * dl;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) g_rgb[q] = w * gC[q];
-}
-
 // Scatter dL/dfeat into the region table: entry += corner weight * gfeat.
 __device__ __forceinline__ void scatter_table_grad(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
                                                    const float gfeat[kIn]) {
@@ -476,11 +445,11 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
+  if (f->mlp_dtype != NERFXL_F32)  // 16-bit MLP: tensor-core backward
+    return launch_field_bwd_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart, grad_tables, grad_mlp, stream);
+  if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-  const int mt = f->mlp_dtype == NERFXL_F32 ? 0 : (f->mlp_dtype == NERFXL_BF16 ? 1 : 2);
-  void (*kern)(BwdParams) = nullptr;
-  if (f16tab) kern = mt == 0 ? k_field_bwd_f32<true, 0> : (mt == 1 ? k_field_bwd_f32<true, 1> : k_field_bwd_f32<true, 2>);
-  else kern = mt == 0 ? k_field_bwd_f32<false, 0> : (mt == 1 ? k_field_bwd_f32<false, 1> : k_field_bwd_f32<false, 2>);
+  void (*kern)(BwdParams) = k_field_bwd_f32<false, 0>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
     return launch_check("k_field_bwd_f32 smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);

@@ -292,6 +292,37 @@ struct TableOf<true> {
   }
 };
 
+// Adjoint of the chunk-local render for one warp (one chunk). Inputs per lane:
+// sigma, rgb, t' (tbar - tn), delta; chunk adjoints gtc, gC, gA, gD, gL.
+// Returns dL/d(sigma), dL/d(rgb).
+__device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rgb[3], float tr, float dl, int lane,
+                                                     float gtc, const float gC[3], float gA, float gD, float gL,
+                                                     float& g_sigma, float g_rgb[3]) {
+  const float tau = sigma * dl;
+  const float incl = warp_inclusive_scan(tau, lane);
+  const float excl = warp_exclusive_from_inclusive(incl, lane);
+  const float T = expf(-excl);
+  const float Tn = expf(-incl);
+  const float w = T * -expm1f(-tau);
+  const float wt = w * tr;
+  const float W_in = warp_inclusive_scan(w, lane);
+  const float WT_in = warp_inclusive_scan(wt, lane);
+  const float W_lt = warp_exclusive_from_inclusive(W_in, lane);
+  const float WT_lt = warp_exclusive_from_inclusive(WT_in, lane);
+  const float W_gt = warp_suffix_scan(w, lane) - w;
+  const float WT_gt = warp_suffix_scan(wt, lane) - wt;
+  // sum_j w_j |t_i - t_j| over the chunk
+  const float pair = (tr * W_lt - WT_lt) + (WT_gt - tr * W_gt);
+  const float gw = gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2] + gA + gD * tr +
+                   gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
+  const float gww = gw * w;
+  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
+  const float g_tau = gtc + gw * Tn - later;
+  g_sigma = g_tau * dl;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g_rgb[q] = w * gC[q];
+}
+
 // Stage region k's 16-bit MLP block into shared memory as FP32 (same
 // transposed layout as load_mlp_f32).
 template <int kMlpType>  // 1 = bf16, 2 = fp16

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "nerfxl_field.cuh"
+#include "nerfxl_half.cuh"
 #include "nerfxl_host.h"
 #include "nerfxl_tc.cuh"
 
@@ -42,29 +43,6 @@ constexpr uint32_t kOffB3 = kOffB2 + 64 * 128;    // 16 rows x 128 B
 constexpr uint32_t kOffMisc = kOffB3 + 16 * 128;  // mbarrier (8 B), tmem base (4 B)
 constexpr uint32_t kOffBase = kOffMisc + 64;      // int32 base[K+1]
 constexpr size_t kTcSmemFixed = kOffBase + 1024;  // + 1024 slack for the alignment of the base
-
-template <bool BF16>
-struct Half2Of;
-template <>
-struct Half2Of<true> {
-  __device__ static uint32_t pack(float a, float b) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
-  }
-  __device__ static float load(const void* p, size_t i) {
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
-  }
-  __device__ static uint16_t bits(const void* p, size_t i) { return reinterpret_cast<const uint16_t*>(p)[i]; }
-};
-template <>
-struct Half2Of<false> {
-  __device__ static uint32_t pack(float a, float b) {
-    const __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
-  }
-  __device__ static float load(const void* p, size_t i) { return __half2float(reinterpret_cast<const __half*>(p)[i]); }
-  __device__ static uint16_t bits(const void* p, size_t i) { return reinterpret_cast<const uint16_t*>(p)[i]; }
-};
 
 // Weights of region k (row-major W1 [32][64], W2 [64][64], W3 [64][4], 16-bit)
 // into the K-major swizzled B tiles: B(row n, column k) = W[k][n].

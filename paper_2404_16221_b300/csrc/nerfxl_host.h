@@ -45,6 +45,10 @@ int fwd_grid(int64_t max_tiles, int ctas_per_sm);
 nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
                               const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,
                               const int64_t* out_index, void* workspace, size_t ws_bytes, cudaStream_t stream);
+// Tensor-core field backward (16-bit MLP).
+nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
+                                  const float* rays_o, const float* rays_d, char* ws, const Layout& L,
+                                  const float4* dpart, float* grad_tables, float* grad_mlp, cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,

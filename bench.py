@@ -4,10 +4,11 @@
 
 The headline step is one training step of the grid8 workload (K=8 regions,
 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 levels 16->2048, 2^18 rays from 64
-pinhole cameras, 128 samples per ray) through the C ABI on the FP32 plain
-path: sampling, gather, MLP, local render, composite, loss, backward, Adam.
+pinhole cameras, 128 samples per ray) through the C ABI, in the training
+configuration: FP16 hash tables, BF16 MLP on the tensor cores, FP32 Adam
+masters: sampling, gather, MLP, local render, composite, loss, backward, Adam.
 Beside it, under "forms": forward renders (FP32 and FP16 tables + BF16 MLP),
-the mixed-precision training step, the city32 MLP precision variants (K=32,
+the FP32 plain training step, the city32 MLP precision variants (K=32,
 2^20 rays, 256 samples) and the serving loop (Poisson 200 req/s) next to
 one-request-at-a-time FP32 rendering. Under torchrun each rank works on its
 own batch on its own GPU (rays are independent: weak scaling, no data-path
@@ -199,6 +200,10 @@ def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
 # forward, then dX (12,800) and dW (12,800): 38,400 per sample.
 MLP_FWD_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 4)
 BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
+# Algorithmic bytes of the backward field kernel per sample (L=16 levels, F=2,
+# 8 corners): the FP16 table gather (8 x 2 x 2 B x 16 = 512 B) and the
+# read-modify-write of the FP32 gradient entries (2 x 8 x 2 x 4 B x 16 = 2048 B).
+TRAIN_BYTES_PER_SAMPLE_F16 = 8 * 2 * 2 * 16 + 2 * 8 * 2 * 4 * 16
 
 
 def main():
@@ -262,34 +267,8 @@ def main():
     for k in ("grid8_fwd_fp32", "grid8_fwd_f16tab_bf16mlp"):
         forms[k].pop("field"), forms[k].pop("ws"), forms[k].pop("out"), forms[k].pop("step")
     del fmix
-    # ---- grid8 training steps: FP32 (the headline) and FP16 tables + BF16 MLP + FP32 Adam
+    # ---- grid8 training steps: FP16 tables + BF16 MLP + FP32 Adam (the headline, configs c3) and FP32 plain
     tgt = torch.rand(R, 3, generator=torch.Generator().manual_seed(1002)).to(dev)
-    trainer = api.Trainer(f32, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
-    tstep = lambda: trainer.step(o_dev, d_dev, tgt)
-    for _ in range(warm):
-        tstep()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        step_ms, kern_ms = time_steps(tstep, steps, flush, stream)
-    forms["grid8_train_fp32"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
-                                 "kernel": "k_field_bwd_f32", "samples": forms["grid8_fwd_fp32"]["samples"],
-                                 "flop_per_sample": BWD_FLOP_PER_SAMPLE}
-    # end to end through host buffers: rays and targets in, the loss out
-    o_h, d_h = torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()
-    t_h = tgt.cpu().pin_memory()
-    loss_h = torch.empty(3).pin_memory()
-
-    def e2e_step():
-        o_dev.copy_(o_h, non_blocking=True)
-        d_dev.copy_(d_h, non_blocking=True)
-        tgt.copy_(t_h, non_blocking=True)
-        loss = trainer.step(o_dev, d_dev, tgt)
-        loss_h.copy_(loss, non_blocking=True)
-
-    for _ in range(warm):
-        e2e_step()
-    e2e_ms, _ = time_steps(e2e_step, steps, flush, stream, prof=False)
-    del trainer, f32
     mfield = mk_field(w, tables, mlp, torch.float16, torch.bfloat16)
     mtrainer = api.Trainer(mfield, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=torch.from_numpy(tables),
                            master_mlp=torch.from_numpy(mlp))
@@ -300,10 +279,36 @@ def main():
     with Clocks(local) as clk:
         step_ms, kern_ms = time_steps(mstep, steps, flush, stream)
     forms["grid8_train_f16tab_bf16mlp"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms,
-                                           "clocks": clk.summary(), "kernel": "k_field_bwd_f32<f16 tab, bf16 mlp>",
+                                           "clocks": clk.summary(), "kernel": "k_field_bwd_tc",
                                            "samples": forms["grid8_fwd_fp32"]["samples"],
-                                           "flop_per_sample": BWD_FLOP_PER_SAMPLE}
+                                           "bytes_per_sample": TRAIN_BYTES_PER_SAMPLE_F16}
+    # end to end through host buffers: rays and targets in, the loss out
+    o_h, d_h = torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()
+    t_h = tgt.cpu().pin_memory()
+    loss_h = torch.empty(3).pin_memory()
+
+    def e2e_step():
+        o_dev.copy_(o_h, non_blocking=True)
+        d_dev.copy_(d_h, non_blocking=True)
+        tgt.copy_(t_h, non_blocking=True)
+        loss = mtrainer.step(o_dev, d_dev, tgt)
+        loss_h.copy_(loss, non_blocking=True)
+
+    for _ in range(warm):
+        e2e_step()
+    e2e_ms, _ = time_steps(e2e_step, steps, flush, stream, prof=False)
     del mtrainer, mfield
+    trainer = api.Trainer(f32, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    tstep = lambda: trainer.step(o_dev, d_dev, tgt)
+    for _ in range(warm):
+        tstep()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        step_ms, kern_ms = time_steps(tstep, steps, flush, stream)
+    forms["grid8_train_fp32"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
+                                 "kernel": "k_field_bwd_f32", "samples": forms["grid8_fwd_fp32"]["samples"],
+                                 "flop_per_sample": BWD_FLOP_PER_SAMPLE}
+    del trainer, f32
     # ---- city32 (K=32, 8x4x1 slabs, 2^20 rays, S=256): MLP precision variants
     if not args.skip_city:
         wc = sy.workload("city32")
@@ -346,7 +351,7 @@ def main():
         del ffield, tc_, mc_
         torch.cuda.empty_cache()
 
-    head = forms["grid8_train_fp32"]
+    head = forms["grid8_train_f16tab_bf16mlp"]
     t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
@@ -370,8 +375,8 @@ def main():
             r["kernel"] = f["kernel"]
             r["kernel_ms"] = km
             if "bytes_per_sample" in f:
-                r["gather_gbs_algorithmic"] = f["samples"] * f["bytes_per_sample"] / (km / 1000.0) / 1e9
-                r["gather_frac_of_hbm"] = r["gather_gbs_algorithmic"] / hbm
+                r["gbs_algorithmic"] = f["samples"] * f["bytes_per_sample"] / (km / 1000.0) / 1e9
+                r["frac_of_hbm"] = r["gbs_algorithmic"] / hbm
             if "flop_per_sample" in f:
                 r["mlp_tflops_algorithmic"] = f["samples"] * f["flop_per_sample"] / (km / 1000.0) / 1e12
         r["samples_per_step"] = f.get("samples")
@@ -379,27 +384,29 @@ def main():
         return r
 
     kern_s = statistics.mean(head["kern_ms"]) / 1000.0
-    achieved = head["samples"] * BWD_FLOP_PER_SAMPLE / kern_s / 1e12
+    achieved = head["samples"] * TRAIN_BYTES_PER_SAMPLE_F16 / kern_s / 1e9
     rays_total = R * world * steps
     line = {
         "metric": METRIC, "value": rays_total / t_step, "unit": "rays/s", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": 1000.0 * t_step / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "grid8 training step (sampling, gather, MLP, local render, composite, loss "
                                "L2 + 0.01 distortion, backward, Adam): K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 "
-                               "(16->2048), FP32 tables and MLP 32-64-64-4, 2^18 rays from 64 pinhole cameras, S=128",
+                               "(16->2048), FP16 hash tables, BF16 MLP 32-64-64-4 with FP32 accumulation on the "
+                               "tensor cores, FP32 Adam masters, 2^18 rays from 64 pinhole cameras, S=128",
                    "rays_per_gpu": R, "samples_per_step": int(head["samples"]),
                    "l2": "flushed before every timed step (252 MB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "train_target": "uniform random colours (throughput does not depend on the target)"},
+                   "train_target": "uniform random colours (throughput does not depend on the target)",
+                   "precision": "FP16 tables, BF16 MLP operands, FP32 accumulation, gradients and Adam"},
         "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(3 * R * 12),
                 "d2h_bytes_per_step": 12},
         "gpu_launches": 11 * steps,
-        "roofline": {"bound": "alu", "kernel": head["kernel"], "achieved": achieved, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
-                     "basis": "%d FLOP/sample (MLP forward recompute + dX + dW, FP32 CUDA cores) x %d samples / mean "
-                              "kernel time %.3f ms; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz (derived)"
-                              % (BWD_FLOP_PER_SAMPLE, head["samples"], 1000 * kern_s)},
+        "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "basis": "%d B/sample algorithmic (FP16 gather 512 B + FP32 gradient read-modify-write 2048 B) "
+                              "x %d samples / mean kernel time %.3f ms (%s peak)"
+                              % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src)},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }

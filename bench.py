@@ -108,19 +108,38 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def setup_workload(seed_offset: int = 0):
-    from paper_2404_16221_b300 import api, native as N, synthetic as sy
+def rank_rays(w, rank: int):
+    """Rays of one rank: rank 0 gets the workload's own rays; rank r > 0 the
+    same camera ring rotated by 0.37 r rad about z (same size and
+    distribution, different rays: each replica renders its own batch)."""
+    from paper_2404_16221_b300 import synthetic as sy
+
+    o, d = sy.workload_rays(w)
+    if rank:
+        ang = 0.37 * rank
+        Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]], np.float32)
+        o, d = (o @ Rz.T).astype(np.float32), (d @ Rz.T).astype(np.float32)
+    return o, d
+
+
+def max_over_ranks(values, device=None):
+    """Timing reduction across replicas: the slowest rank sets the job time."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def setup_workload(rank: int = 0):
+    from paper_2404_16221_b300 import native as N, synthetic as sy
 
     w = sy.workload(WORKLOAD)
     E = N.table_entries(w.level_res, w.log2_T)
     P = N.mlp_params(w.mlp_in, w.W)
     tables, mlp = sy.field_params(w, E, P)
-    o, d = sy.workload_rays(w)
-    if seed_offset:
-        # another rank: the same scene seen by a rotated camera ring
-        ang = 0.37 * seed_offset
-        Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]], np.float32)
-        o, d = (o @ Rz.T).astype(np.float32), (d @ Rz.T).astype(np.float32)
+    o, d = rank_rays(w, rank)
     return w, tables, mlp, o, d
 
 
@@ -355,9 +374,8 @@ def main():
     t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
-        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(tt[0]), float(tt[1])
+        dist.barrier()
+        t_step, t_e2e = max_over_ranks([t_step, t_e2e], dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

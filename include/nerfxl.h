@@ -271,6 +271,16 @@ nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int
  */
 nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
 
+/*
+ * Failure-path probe: one thread waits on an mbarrier with the same bounded
+ * poll loop the tensor-core kernels use (at most `spins` polls; <= 2^26).
+ * With arrive != 0 the barrier completes and the call returns NERFXL_OK;
+ * with arrive == 0 nothing ever arrives, the wait gives up, and the call
+ * returns NERFXL_E_TIMEOUT with the context still usable. status is one
+ * device int32 (1 = completed, 0 = timed out). Synchronises the stream.
+ */
+nerfxl_status nerfxl_debug_wait_probe(int32_t* status, uint32_t spins, int32_t arrive, cudaStream_t stream);
+
 /* Thread-local text for the last non-OK status. */
 const char* nerfxl_last_error(void);
 

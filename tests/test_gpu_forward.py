@@ -174,3 +174,37 @@ def test_full_size_forward_sampled_rays(name):
     t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sel))])
     got = {k: v.cpu().numpy()[sel] for k, v in out.items()}
     H.assert_forward_close(got, ref, t_far)
+
+
+@pytest.mark.slow
+def test_full_size_city32_sampled_rays():
+    """The full street/city workload (K=32, T=2^21, 2^20 rays, S=256) in the
+    launch configuration the bench times; 512 seeded rays checked against the
+    oracle, for the FP32 path (1e-5) and for FP16 tables + BF16 MLP (2e-3
+    absolute, against the oracle on the rounded parameters)."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("city32")
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w)
+    sel = sy.subset(len(o), 512, 101)
+    for tab, mlp in ((torch.float32, torch.float32), (torch.float16, torch.bfloat16)):
+        gf = H.gpu_field(w, t, m, table_dtype=tab, mlp_dtype=mlp)
+        ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+        out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+        api.check(ws)
+        got = {k: v.cpu().numpy()[sel] for k, v in out.items()}
+        del gf, ws, out
+        torch.cuda.empty_cache()
+        tq = t if tab == torch.float32 else torch.from_numpy(t).to(tab).float().numpy()
+        mq = m if mlp == torch.float32 else torch.from_numpy(m).to(mlp).float().numpy()
+        of = H.oracle_field(w, tq, mq)
+        ref = oracle.render(of, w.S, o[sel], d[sel], 1)
+        nseg, region, t0, t1, nint = oracle.segments(of, w.S, o[sel], d[sel])
+        t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sel))])
+        del of
+        if tab == torch.float32:
+            H.assert_forward_close(got, ref, t_far)
+        else:
+            assert np.abs(got["rgb"] - ref["rgb"]).max() <= 2e-3
+            assert np.abs(got["opacity"] - ref["opacity"]).max() <= 2e-3

@@ -256,3 +256,36 @@ class Trainer:
                                  self._ws.numel(), N._stream(stream))
         N.check(st, "nerfxl_step")
         return self.loss
+
+
+MLP_LAYER_SIZES = (32 * 64, 64 * 64, 64 * 4)  # W1, W2, W3 of one region block
+
+
+def quantize_mlp_e4m3(mlp):
+    """FP32 MLP blocks [K][P] -> (E4M3 bytes [K][P] uint8, scales [K][3]).
+
+    Per region and per layer: scale = max|W| / 448 (the largest finite E4M3
+    value), W_q = e4m3(W / scale), so W ~= scale * W_q."""
+    m = torch.as_tensor(mlp, dtype=torch.float32)
+    K = m.shape[0]
+    q = torch.empty(m.shape, dtype=torch.uint8, device=m.device)
+    scales = torch.empty(K, 3, dtype=torch.float32, device=m.device)
+    off = 0
+    for li, n in enumerate(MLP_LAYER_SIZES):
+        blk = m[:, off:off + n]
+        s = blk.abs().amax(dim=1).clamp_min(1e-30) / 448.0
+        q[:, off:off + n] = (blk / s[:, None]).to(torch.float8_e4m3fn).view(torch.uint8)
+        scales[:, li] = s
+        off += n
+    return q, scales
+
+
+def dequantize_mlp_e4m3(q, scales):
+    """Inverse of quantize_mlp_e4m3 (FP32), for references."""
+    q = torch.as_tensor(q)
+    out = q.view(torch.float8_e4m3fn).float()
+    off = 0
+    for li, n in enumerate(MLP_LAYER_SIZES):
+        out[:, off:off + n] *= torch.as_tensor(scales)[:, li:li + 1]
+        off += n
+    return out

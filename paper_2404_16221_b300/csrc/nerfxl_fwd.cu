@@ -500,9 +500,9 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   nerfxl_status st = validate(f, s, n_rays);
   if (st != NERFXL_OK) return st;
   const bool tab_ok = f->table_dtype == NERFXL_F32 || f->table_dtype == NERFXL_F16;
-  const bool tc_mlp = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
+  const bool tc_mlp = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16 || f->mlp_dtype == NERFXL_E4M3;
   if (!tab_ok || !(tc_mlp || f->mlp_dtype == NERFXL_F32) || (f->mlp_dtype == NERFXL_F32 && f->table_dtype != NERFXL_F32))
-    return set_error(NERFXL_E_UNSUPPORTED, "supported: FP32 tables + FP32 MLP, or FP32/FP16 tables + BF16/FP16 MLP");
+    return set_error(NERFXL_E_UNSUPPORTED, "supported: FP32 tables + FP32 MLP, or FP32/FP16 tables + BF16/FP16/E4M3 MLP");
   if (n_rays > 0 && (!rays_o || !rays_d || !rgb || !depth || !opacity))
     return set_error(NERFXL_E_INVALID, "null ray or output pointer");
   const Layout L = layout(f, s, n_rays, 0);

@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "nerfxl_field.cuh"
@@ -44,49 +45,102 @@ constexpr uint32_t kOffMisc = kOffB3 + 16 * 128;  // mbarrier (8 B), tmem base (
 constexpr uint32_t kOffBase = kOffMisc + 64;      // int32 base[K+1]
 constexpr size_t kTcSmemFixed = kOffBase + 1024;  // + 1024 slack for the alignment of the base
 
-// Weights of region k (row-major W1 [32][64], W2 [64][64], W3 [64][4], 16-bit)
-// into the K-major swizzled B tiles: B(row n, column k) = W[k][n].
-template <bool BF16>
-__device__ __forceinline__ void load_weights_tc(const void* blk, char* sm) {
-  uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + kOffB1);
-  uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + kOffB2);
-  uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + kOffB3);
-  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
-    const int k = i / kWidth, n = i % kWidth;
-    b1[tc::sw128_offset(n, k) >> 1] = Half2Of<BF16>::bits(blk, i);
+// Operand kinds of the MLP MMAs: 0 = BF16, 1 = FP16 (kind::f16, 16 elements
+// per 32-byte K step), 2 = E4M3 (kind::f8f6f4, 32 elements per K step, with a
+// per-layer weight scale applied to the FP32 accumulator). In every kind a
+// tile row is 128 bytes of the 128-byte swizzle and a K step is 32 bytes.
+constexpr int kKindBF16 = 0, kKindF16 = 1, kKindE4M3 = 2;
+
+template <int kKind>
+struct MlpOp {
+  static constexpr bool kBF16 = kKind == kKindBF16;
+  static constexpr uint32_t idesc(int M, int N) { return tc::idesc_f16(kBF16, M, N); }
+  static constexpr int steps(int K) { return K / 16; }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    tc::mma_f16(d, a, b, id, acc);
   }
-  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
-    const int k = i / kWidth, n = i % kWidth;
-    b2[tc::sw128_offset(n, k) >> 1] = Half2Of<BF16>::bits(blk, kIn * kWidth + i);
+  // eight features (levels 4g..4g+3) -> 16-byte chunk g of the row
+  __device__ static void store8(uint32_t tile, uint32_t row, int g, const float* f) {
+    tc::st_shared_v4(tile + tc::sw128_chunk(row, g), Half2Of<kBF16>::pack(f[0], f[1]), Half2Of<kBF16>::pack(f[2], f[3]),
+                     Half2Of<kBF16>::pack(f[4], f[5]), Half2Of<kBF16>::pack(f[6], f[7]));
   }
-  for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
-    const int n = i / 64, k = i % 64;
-    const uint16_t v = n < kOut ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
-    b3[tc::sw128_offset(n, k) >> 1] = v;
+  // sixteen activations (columns 16g..16g+15) -> chunks 2g, 2g+1 of the row
+  __device__ static void store16(uint32_t tile, uint32_t row, int g, const float* v) {
+    tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g), Half2Of<kBF16>::pack(v[0], v[1]),
+                     Half2Of<kBF16>::pack(v[2], v[3]), Half2Of<kBF16>::pack(v[4], v[5]),
+                     Half2Of<kBF16>::pack(v[6], v[7]));
+    tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g + 1), Half2Of<kBF16>::pack(v[8], v[9]),
+                     Half2Of<kBF16>::pack(v[10], v[11]), Half2Of<kBF16>::pack(v[12], v[13]),
+                     Half2Of<kBF16>::pack(v[14], v[15]));
   }
+  // B(row n, column k) = W[k][n] for the three layers (row-major 16-bit block)
+  __device__ static void load_weights(const void* blk, char* sm) {
+    uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + kOffB1);
+    uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + kOffB2);
+    uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + kOffB3);
+    for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+      const int k = i / kWidth, n = i % kWidth;
+      b1[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, i);
+    }
+    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+      const int k = i / kWidth, n = i % kWidth;
+      b2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kIn * kWidth + i);
+    }
+    for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+      const int n = i / 64, k = i % 64;
+      b3[tc::sw128_offset(n, k) >> 1] =
+          n < kOut ? Half2Of<kBF16>::bits(blk, kIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
+    }
+  }
+};
+
+// E4M3: byte (row, k) of a swizzled tile sits at row*128 + ((k/16 ^ row%8) * 16) + k%16.
+__device__ __forceinline__ uint32_t sw128_byte(uint32_t row, uint32_t k) {
+  return row * 128u + ((((k >> 4) ^ (row & 7u)) & 7u) << 4) + (k & 15u);
 }
 
-// Writes 64 activations (relu applied by the caller) of row r as 16-bit into a
-// swizzled A tile, 8 chunks of 16 bytes.
-template <bool BF16>
-__device__ __forceinline__ void store_row64(uint32_t tile, uint32_t r, const float* v) {
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    tc::st_shared_v4(tile + tc::sw128_chunk(r, c), Half2Of<BF16>::pack(v[8 * c], v[8 * c + 1]),
-                     Half2Of<BF16>::pack(v[8 * c + 2], v[8 * c + 3]), Half2Of<BF16>::pack(v[8 * c + 4], v[8 * c + 5]),
-                     Half2Of<BF16>::pack(v[8 * c + 6], v[8 * c + 7]));
-  }
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
 }
 
-template <bool BF16>
-__device__ __forceinline__ void store_row32(uint32_t tile, uint32_t r, const float* v) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    tc::st_shared_v4(tile + tc::sw128_chunk(r, c), Half2Of<BF16>::pack(v[8 * c], v[8 * c + 1]),
-                     Half2Of<BF16>::pack(v[8 * c + 2], v[8 * c + 3]), Half2Of<BF16>::pack(v[8 * c + 4], v[8 * c + 5]),
-                     Half2Of<BF16>::pack(v[8 * c + 6], v[8 * c + 7]));
+template <>
+struct MlpOp<kKindE4M3> {
+  static constexpr uint32_t idesc(int M, int N) { return tc::idesc_e4m3(M, N); }
+  static constexpr int steps(int K) { return K / 32; }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    tc::mma_f8(d, a, b, id, acc);
   }
-}
+  __device__ static void store8(uint32_t tile, uint32_t row, int g, const float* f) {
+    const uint32_t addr = tile + tc::sw128_chunk(row, g >> 1) + (uint32_t)(g & 1) * 8u;
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(e4m3x4(f[0], f[1], f[2], f[3])),
+                 "r"(e4m3x4(f[4], f[5], f[6], f[7]))
+                 : "memory");
+  }
+  __device__ static void store16(uint32_t tile, uint32_t row, int g, const float* v) {
+    tc::st_shared_v4(tile + tc::sw128_chunk(row, g), e4m3x4(v[0], v[1], v[2], v[3]), e4m3x4(v[4], v[5], v[6], v[7]),
+                     e4m3x4(v[8], v[9], v[10], v[11]), e4m3x4(v[12], v[13], v[14], v[15]));
+  }
+  __device__ static void load_weights(const void* blk, char* sm) {
+    const uint8_t* w = static_cast<const uint8_t*>(blk);
+    uint8_t* b1 = reinterpret_cast<uint8_t*>(sm + kOffB1);
+    uint8_t* b2 = reinterpret_cast<uint8_t*>(sm + kOffB2);
+    uint8_t* b3 = reinterpret_cast<uint8_t*>(sm + kOffB3);
+    for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+      const int k = i / kWidth, n = i % kWidth;
+      b1[sw128_byte(n, k)] = w[i];
+    }
+    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+      const int k = i / kWidth, n = i % kWidth;
+      b2[sw128_byte(n, k)] = w[kIn * kWidth + i];
+    }
+    for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+      const int n = i / 64, k = i % 64;
+      b3[sw128_byte(n, k)] = n < kOut ? w[kIn * kWidth + kWidth * kWidth + k * kOut + n] : 0;
+    }
+  }
+};
 
 // Reads 64 accumulator columns of this thread's row, applies relu.
 __device__ __forceinline__ void tmem_row64_relu(uint32_t taddr, float* v) {
@@ -104,7 +158,8 @@ struct FwdTcParams {
   const float* rays_d;
   const float* boxes;
   const void* tables;  // [K][E] of float2 or half2
-  const void* mlp;     // [K][kMlpParams] 16-bit
+  const void* mlp;     // [K][kMlpParams] 16-bit, or E4M3 bytes
+  const float* mlp_scales;  // [K][3] per-layer weight scales (E4M3 only)
   LevelParams lp;
   SampParams sp;
   int K;
@@ -117,8 +172,9 @@ struct FwdTcParams {
   int32_t* err;
 };
 
-template <bool kF16Table, bool BF16>
+template <bool kF16Table, int kKind>
 __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
+  using Op = MlpOp<kKind>;
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = tc::smem_u32(sm);
@@ -140,8 +196,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_q = tmem + ((uint32_t)(q * 32) << 16);
 
-  constexpr uint32_t idesc64 = tc::idesc_f16(BF16, kTcRows, 64);
-  constexpr uint32_t idesc16 = tc::idesc_f16(BF16, kTcRows, 16);
+  constexpr uint32_t idesc64 = Op::idesc(kTcRows, 64);
+  constexpr uint32_t idesc16 = Op::idesc(kTcRows, 16);
+  constexpr int kSteps32 = Op::steps(32), kSteps64 = Op::steps(64);
+  constexpr size_t kElem = kKind == kKindE4M3 ? 1 : 2;
+  float scale[3] = {1.0f, 1.0f, 1.0f};
   const uint32_t a0 = sbase + kOffA0, a1 = sbase + kOffA1;
   const uint32_t b1 = sbase + kOffB1, b2 = sbase + kOffB2, b3 = sbase + kOffB3;
   using TabT = typename TableOf<kF16Table>::T;
@@ -155,7 +214,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
     if (k != region) {
       __syncthreads();
-      load_weights_tc<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm);
+      Op::load_weights(static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * kElem, sm);
+      if (kKind == kKindE4M3) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) scale[l] = p.mlp_scales[3 * k + l];
+      }
       region = k;
       table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
     }
@@ -196,9 +259,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         gather4<TabT>(p.lp, table, u, 4 * g, f8);
       }
     }
-    tc::st_shared_v4(a0 + tc::sw128_chunk(row, g), Half2Of<BF16>::pack(f8[0], f8[1]),
-                     Half2Of<BF16>::pack(f8[2], f8[3]), Half2Of<BF16>::pack(f8[4], f8[5]),
-                     Half2Of<BF16>::pack(f8[6], f8[7]));
+    Op::store8(a0, row, g, f8);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -206,8 +267,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b1 + 32 * kk), idesc64, kk);
+      for (int kk = 0; kk < kSteps32; ++kk)
+        Op::mma(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b1 + 32 * kk), idesc64, kk);
       tc::mma_commit(mbar);
     }
     bool ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
@@ -221,12 +282,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     tc::tmem_ld16(tmem_q + 16 * g, v);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-    tc::st_shared_v4(a1 + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(v[0], v[1]), Half2Of<BF16>::pack(v[2], v[3]),
-                     Half2Of<BF16>::pack(v[4], v[5]), Half2Of<BF16>::pack(v[6], v[7]));
-    tc::st_shared_v4(a1 + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(v[8], v[9]),
-                     Half2Of<BF16>::pack(v[10], v[11]), Half2Of<BF16>::pack(v[12], v[13]),
-                     Half2Of<BF16>::pack(v[14], v[15]));
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * scale[0], 0.0f);
+    Op::store16(a1, row, g, v);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -234,8 +291,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem + 64, tc::desc_sw128(a1 + 32 * kk), tc::desc_sw128(b2 + 32 * kk), idesc64, kk);
+      for (int kk = 0; kk < kSteps64; ++kk)
+        Op::mma(tmem + 64, tc::desc_sw128(a1 + 32 * kk), tc::desc_sw128(b2 + 32 * kk), idesc64, kk);
       tc::mma_commit(mbar);
     }
     ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
@@ -248,12 +305,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     tc::tmem_ld16(tmem_q + 64 + 16 * g, v);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-    tc::st_shared_v4(a0 + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(v[0], v[1]), Half2Of<BF16>::pack(v[2], v[3]),
-                     Half2Of<BF16>::pack(v[4], v[5]), Half2Of<BF16>::pack(v[6], v[7]));
-    tc::st_shared_v4(a0 + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(v[8], v[9]),
-                     Half2Of<BF16>::pack(v[10], v[11]), Half2Of<BF16>::pack(v[12], v[13]),
-                     Half2Of<BF16>::pack(v[14], v[15]));
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * scale[1], 0.0f);
+    Op::store16(a0, row, g, v);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -261,8 +314,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b3 + 32 * kk), idesc16, kk);
+      for (int kk = 0; kk < kSteps64; ++kk)
+        Op::mma(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b3 + 32 * kk), idesc16, kk);
       tc::mma_commit(mbar);
     }
     ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
@@ -279,9 +332,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       if (chunk_ok) {
         float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
-          sigma = expf(v[0]);
+          sigma = expf(v[0] * scale[2]);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
+          for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j] * scale[2]));
         }
         const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
         if (lane == 0) {
@@ -310,6 +363,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.boxes = f->boxes;
   p.tables = f->tables;
   p.mlp = f->mlp;
+  p.mlp_scales = f->mlp_scales;
   p.lp = lp;
   p.sp = sp;
   p.K = f->K;
@@ -321,11 +375,16 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
   const size_t smem = kTcSmemFixed + sizeof(int32_t) * (f->K + 1);
-  const bool bf16 = f->mlp_dtype == NERFXL_BF16;
+  const int kind = f->mlp_dtype == NERFXL_BF16 ? kKindBF16 : (f->mlp_dtype == NERFXL_F16 ? kKindF16 : kKindE4M3);
+  if (kind == kKindE4M3 && !f->mlp_scales) return set_error(NERFXL_E_INVALID, "E4M3 MLP needs mlp_scales");
   const bool f16tab = f->table_dtype == NERFXL_F16;
   void (*kern)(FwdTcParams) = nullptr;
-  if (f16tab) kern = bf16 ? k_field_fwd_tc<true, true> : k_field_fwd_tc<true, false>;
-  else kern = bf16 ? k_field_fwd_tc<false, true> : k_field_fwd_tc<false, false>;
+  if (f16tab)
+    kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16>
+                             : (kind == kKindF16 ? k_field_fwd_tc<true, kKindF16> : k_field_fwd_tc<true, kKindE4M3>);
+  else
+    kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16>
+                             : (kind == kKindF16 ? k_field_fwd_tc<false, kKindF16> : k_field_fwd_tc<false, kKindE4M3>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_fwd_tc smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kTcChunks, 2);

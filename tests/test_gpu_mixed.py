@@ -187,3 +187,56 @@ def test_mixed_training_gains():
     # the compute copies track the FP32 masters
     assert torch.equal(gf.tables, tr.tables.to(torch.float16))
     assert torch.equal(gf.mlp, tr.mlp.to(torch.bfloat16))
+
+
+def test_precision_sweep_city32():
+    """Street/city precision sweep: the MLP in FP32 (CUDA cores), BF16, FP16
+    and E4M3 with per-layer scales (tensor cores), tables FP32. Each variant's
+    RGB and depth error against the FP64 oracle of the unrounded FP32 field is
+    reported; FP32 must meet 1e-5, BF16/FP16 the 2e-3 RGB bound; E4M3 (3-bit
+    mantissa activations) is an experiment and only sanity-bounded."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("city32", L=16, log2_T=16)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 2048)
+    of = H.oracle_field(w, t, m)
+    ref = oracle.render(of, w.S, o, d, 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 1.0 for r in range(len(o))])
+    rows = {}
+    for name in ("fp32", "bf16", "fp16", "e4m3"):
+        if name == "e4m3":
+            q, sc = api.quantize_mlp_e4m3(torch.from_numpy(m))
+            gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), q, mlp_scales=sc)
+        else:
+            md = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[name]
+            gf = H.gpu_field(w, t, m, mlp_dtype=md)
+        ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+        out = {k: v.cpu().numpy() for k, v in api.render_fwd(gf, H.sampling(w), o, d, workspace=ws).items()}
+        api.check(ws)
+        rows[name] = (np.abs(out["rgb"] - ref["rgb"]).max(), np.abs(out["rgb"] - ref["rgb"]).mean(),
+                      (np.abs(out["depth"] - ref["depth"]) / t_far).max())
+        print("precision sweep city32 mlp=%s: RGB max %.2e mean %.2e, depth/t_far max %.2e" % ((name,) + rows[name]))
+    assert rows["fp32"][0] <= 1e-5 * 2 and rows["bf16"][0] <= 2e-3 and rows["fp16"][0] <= 2e-3
+    assert rows["e4m3"][0] <= 0.1 and rows["e4m3"][1] <= 0.02
+
+
+def test_e4m3_matches_oracle_on_dequantized_weights():
+    """E4M3 forward against the oracle run on the dequantized weights: what
+    is left is the E4M3 rounding of activations (3 mantissa bits)."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    q, sc = api.quantize_mlp_e4m3(torch.from_numpy(m))
+    mq = api.dequantize_mlp_e4m3(q, sc).numpy()
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), q, mlp_scales=sc)
+    o, d = sy.workload_rays(w, 2048)
+    ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+    out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+    api.check(ws)
+    ref = oracle.render(H.oracle_field(w, t, mq), w.S, o, d, 1)
+    e = np.abs(out["rgb"].cpu().numpy() - ref["rgb"])
+    print("e4m3 vs dequantized-weight oracle: RGB max %.2e mean %.2e" % (e.max(), e.mean()))
+    assert e.max() <= 0.05 and e.mean() <= 0.01

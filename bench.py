@@ -220,9 +220,10 @@ def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
 MLP_FWD_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 4)
 BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
 # Algorithmic bytes of the backward field kernel per sample (L=16 levels, F=2,
-# 8 corners): the FP16 table gather (8 x 2 x 2 B x 16 = 512 B) and the
-# read-modify-write of the FP32 gradient entries (2 x 8 x 2 x 4 B x 16 = 2048 B).
-TRAIN_BYTES_PER_SAMPLE_F16 = 8 * 2 * 2 * 16 + 2 * 8 * 2 * 4 * 16
+# 8 corners) in the training mode that keeps the forward's features: the saved
+# 16-bit features (32 x 2 B = 64 B) and the read-modify-write of the FP32
+# gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
+TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 2 * 8 * 2 * 4 * 16
 
 
 def main():
@@ -422,8 +423,8 @@ def main():
         "gpu_launches": 11 * steps,
         "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "basis": "%d B/sample algorithmic (FP16 gather 512 B + FP32 gradient read-modify-write 2048 B) "
-                              "x %d samples / mean kernel time %.3f ms (%s peak)"
+                     "basis": "%d B/sample algorithmic (saved 16-bit features 64 B + FP32 gradient read-modify-write "
+                              "2048 B) x %d samples / mean kernel time %.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src)},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],

@@ -98,9 +98,17 @@ typedef struct nerfxl_field {
 typedef struct nerfxl_sampling {
   int32_t n_samples;
   int32_t max_segments;
-  float t_min; /* near clamp of every t0 (0 for cameras outside the scene) */
-  int32_t flags; /* reserved, 0 */
+  float t_min;   /* near clamp of every t0 (0 for cameras outside the scene) */
+  int32_t flags; /* NERFXL_SAVE_FEATURES or 0 */
 } nerfxl_sampling;
+
+/*
+ * Training with a 16-bit MLP: the forward stores each sample's encoded
+ * features (32 x 16 bit) in a backward-sized workspace and the backward reads
+ * them instead of gathering the hash tables again (64 bytes per sample of
+ * extra workspace). Without the flag the backward recomputes everything.
+ */
+#define NERFXL_SAVE_FEATURES 1
 
 /* Entries per region table (sum of level sizes), or -1 on bad input. */
 int64_t nerfxl_table_entries(const int32_t* level_res /* host [L] */, int32_t L, int32_t log2_T);

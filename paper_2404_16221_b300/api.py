@@ -16,14 +16,18 @@ from . import native as N
 _DTYPE_CODE = {torch.float32: N.F32, torch.float16: N.F16, torch.bfloat16: N.BF16, torch.uint8: N.E4M3}
 
 
+SAVE_FEATURES = 1  # forward stores 16-bit features for the backward (NERFXL_SAVE_FEATURES)
+
+
 @dataclasses.dataclass
 class Sampling:
     n_samples: int
     max_segments: int = 0
     t_min: float = 0.0
+    flags: int = 0
 
     def desc(self) -> N.SamplingDesc:
-        return N.SamplingDesc(int(self.n_samples), int(self.max_segments), float(self.t_min), 0)
+        return N.SamplingDesc(int(self.n_samples), int(self.max_segments), float(self.t_min), int(self.flags))
 
 
 class PartitionedField:
@@ -213,8 +217,12 @@ class Trainer:
     refreshes the copies from them."""
 
     def __init__(self, field: PartitionedField, samp: Sampling, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
-                 lambda_dist=0.01, master_tables=None, master_mlp=None):
-        self.field, self.samp = field, samp
+                 lambda_dist=0.01, master_tables=None, master_mlp=None, save_features: bool = True):
+        self.field = field
+        if save_features and field.mlp.dtype in (torch.bfloat16, torch.float16):
+            # 16-bit MLP: keep the forward's features for the backward
+            samp = dataclasses.replace(samp, flags=samp.flags | SAVE_FEATURES)
+        self.samp = samp
         self.lr, self.beta1, self.beta2, self.eps, self.lambda_dist = lr, beta1, beta2, eps, lambda_dist
 
         def master(copy, given):

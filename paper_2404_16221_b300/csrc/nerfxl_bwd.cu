@@ -447,7 +447,9 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
   if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");
   if (f->mlp_dtype != NERFXL_F32)  // 16-bit MLP: tensor-core backward
-    return launch_field_bwd_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart, grad_tables, grad_mlp, stream);
+    return launch_field_bwd_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart,
+                               L.features ? reinterpret_cast<const uint4*>(ws + L.features) : nullptr, grad_tables,
+                               grad_mlp, stream);
   if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
   void (*kern)(BwdParams) = k_field_bwd_f32<false, 0>;

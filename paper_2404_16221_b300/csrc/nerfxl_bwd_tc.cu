@@ -73,6 +73,7 @@ struct BwdTcParams {
   const uint2* chunks;
   const int32_t* n_tiles;
   const float4* dpart;
+  const uint4* feat_in;  // features saved by the forward, or NULL (gather again)
   float* grad_tables;  // FP32 [K][E][2]
   float* grad_mlp;     // FP32 [K][kMlpParams]
   int32_t* err;
@@ -305,7 +306,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         float x[3];
         sample_point(o, d, tbar, x);
         region_coord(p.boxes + 6 * k, x, u);
-        gather4<TabT>(p.lp, table, u, 4 * g, f8);
+        if (p.feat_in) {
+          const uint4 pk = p.feat_in[((size_t)(t * kTileChunks + q) * 4 + g) * kWarp + lane];
+          const uint32_t wv[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float2 fv = Half2Of<BF16>::unpack(wv[j]);
+            f8[2 * j] = fv.x;
+            f8[2 * j + 1] = fv.y;
+          }
+        } else {
+          gather4<TabT>(p.lp, table, u, 4 * g, f8);
+        }
       }
     }
     {
@@ -507,8 +519,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
 
 nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  const float4* dpart, float* grad_tables, float* grad_mlp, cudaStream_t stream) {
+                                  const float4* dpart, const uint4* feat_in, float* grad_tables, float* grad_mlp,
+                                  cudaStream_t stream) {
   BwdTcParams p;
+  p.feat_in = feat_in;
   p.rays_o = rays_o;
   p.rays_d = rays_d;
   p.boxes = f->boxes;

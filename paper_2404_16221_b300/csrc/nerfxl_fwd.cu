@@ -342,6 +342,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   L.chunks = take(sizeof(uint2) * L.chunk_cap);
   L.partials = take(sizeof(float4) * 2 * R * mc);
   L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
+  L.features = (for_backward && (s->flags & NERFXL_SAVE_FEATURES)) ? take((size_t)L.chunk_cap * 4 * 32 * 16) : 0;
   L.total = off;
   L.max_seg = ms;
   L.max_chunk = mc;
@@ -513,7 +514,14 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   if (st != NERFXL_OK) return st;
   if (n_rays == 0) return NERFXL_OK;
   if (tc_mlp) {
-    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, stream);
+    uint4* feat_out = nullptr;
+    if (s->flags & NERFXL_SAVE_FEATURES) {
+      if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
+      const Layout LB = layout(f, s, n_rays, 1);
+      if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
+      feat_out = reinterpret_cast<uint4*>(ws + LB.features);
+    }
+    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, feat_out, stream);
     if (st != NERFXL_OK) return st;
     k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
         n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),

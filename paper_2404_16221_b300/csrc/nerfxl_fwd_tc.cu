@@ -169,6 +169,7 @@ struct FwdTcParams {
   const uint2* chunks;
   const int32_t* n_tiles;  // tiles of kChunksPerTile chunks
   float4* partials;
+  uint4* feat_out;  // saved 16-bit features [chunk slot][group][lane] or NULL
   int32_t* err;
 };
 
@@ -260,6 +261,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       }
     }
     Op::store8(a0, row, g, f8);
+    if (kKind != kKindE4M3 && p.feat_out) {
+      const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
+                                  Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
+                                  Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
+                                  Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
+      p.feat_out[((size_t)(t * kTcChunks + q) * 4 + g) * kWarp + lane] = pk;
+    }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -356,8 +364,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 // Host dispatch (called from nerfxl_render_fwd).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  cudaStream_t stream) {
+                                  uint4* feat_out, cudaStream_t stream) {
   FwdTcParams p;
+  p.feat_out = feat_out;
   p.rays_o = rays_o;
   p.rays_d = rays_d;
   p.boxes = f->boxes;

@@ -21,6 +21,7 @@ struct Layout {
   size_t chunks;     // uint2[chunk_cap]
   size_t partials;   // float4[R][max_chunk][2]
   size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
+  size_t features;   // uint4[chunk_cap][4][32]: 16-bit features (backward + NERFXL_SAVE_FEATURES)
   size_t total;
   int64_t chunk_cap;
   int max_seg, max_chunk;
@@ -48,10 +49,11 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
 // Tensor-core field backward (16-bit MLP).
 nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  const float4* dpart, float* grad_tables, float* grad_mlp, cudaStream_t stream);
+                                  const float4* dpart, const uint4* feat_in, float* grad_tables, float* grad_mlp,
+                                  cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  cudaStream_t stream);
+                                  uint4* feat_out, cudaStream_t stream);
 
 }  // namespace nerfxl

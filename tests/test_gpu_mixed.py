@@ -240,3 +240,31 @@ def test_e4m3_matches_oracle_on_dequantized_weights():
     e = np.abs(out["rgb"].cpu().numpy() - ref["rgb"])
     print("e4m3 vs dequantized-weight oracle: RGB max %.2e mean %.2e" % (e.max(), e.mean()))
     assert e.max() <= 0.05 and e.mean() <= 0.01
+
+
+def test_saved_features_backward_equals_recompute():
+    """With NERFXL_SAVE_FEATURES the backward reads the features the forward
+    fed its first MMA instead of gathering again; the gradient is the same
+    (up to the order of the FP32 atomic sums)."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 2048)
+    R = len(o)
+    g = sy.rng(23, "misc")
+    adj = [torch.from_numpy(a.astype(np.float32)).cuda() for a in
+           (g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R))]
+    grads = []
+    for flags in (0, api.SAVE_FEATURES):
+        gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+        samp = dataclasses.replace(H.sampling(w), flags=flags)
+        ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+        api.render_fwd(gf, samp, o, d, workspace=ws)
+        gt, gm = api.render_bwd(gf, samp, o, d, ws, *adj)
+        api.check(ws)
+        grads.append((gt.cpu().numpy(), gm.cpu().numpy()))
+    for a, b in zip(grads[0], grads[1]):
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-city", action="store_true", help="skip the city32 precision and serving forms")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-sweep", type=str, default="",
+                    help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
     return ap.parse_args()
 
 
@@ -226,6 +228,34 @@ BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
 TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 2 * 8 * 2 * 4 * 16
 
 
+def serve_sweep(args, dev, rates):
+    """p50/p99 latency and served rays/s of the city32 serving loop (FP16
+    tables + BF16 MLP) at several Poisson arrival rates, args.serve_requests
+    requests each; prints one JSON line."""
+    import torch
+
+    from paper_2404_16221_b300 import api, native as N, serve, synthetic as sy
+
+    ws_ = sy.workload("serve32")
+    E = N.table_entries(ws_.level_res, ws_.log2_T)
+    t, m = sy.field_params_device(ws_, E, N.mlp_params(ws_.mlp_in, ws_.W), dev)
+    field = api.PartitionedField(ws_.boxes, ws_.level_res, ws_.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
+                                 device=dev)
+    del t, m
+    samp = api.Sampling(ws_.S, ws_.max_segments)
+    serve.ServeEngine(field, samp).run(serve.requests_from_stream(4, 100.0, ws_.seed + 17), realtime=False)
+    rows = []
+    for rate in rates:
+        reqs = serve.requests_from_stream(args.serve_requests, rate, ws_.seed)
+        px = sum(r.pixels for r in reqs)
+        m_ = serve.ServeEngine(field, samp, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(reqs)
+        m_.update({"rate_req_s": rate, "offered_rays_per_s": px / max(reqs[-1].arrival_s, 1e-9)})
+        rows.append(m_)
+    print(json.dumps({"serve_sweep": rows, "workload": "serve32: K=32 city field, FP16 tables + BF16 MLP, "
+                      "log-uniform 64x64..1920x1080 requests, Poisson arrivals, %d requests per rate"
+                      % args.serve_requests}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -245,6 +275,9 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     dev = torch.device("cuda", local)
+    if args.serve_sweep:
+        serve_sweep(args, dev, [float(r) for r in args.serve_sweep.split(",")])
+        return
     w, tables, mlp, o, d = setup_workload(rank)
     samp = api.Sampling(w.S, w.max_segments)
     R = len(o)

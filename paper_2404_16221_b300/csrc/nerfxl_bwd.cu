@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t R, SampParams sp,
                                                        const float* __restrict__ d_rgb,
                                                        const float* __restrict__ d_depth,
                                                        const float* __restrict__ d_opacity,
-                                                       const float* __restrict__ d_dist, float4* __restrict__ dpart) {
+                                                       const float* __restrict__ d_dist, float4* __restrict__ dpart,
+                                                       const int32_t* __restrict__ pos,
+                                                       float4* __restrict__ dpart_tile) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   const RayHdr h = hdr[r];
@@ -79,8 +81,15 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t R, SampParams sp,
                       gL * (2.0f * Pc * Lc + 2.0f * S);
     const float gAc = Pc * gA - 2.0f * gL * Pc * Db;
     const float gDc = Pc * gD + 2.0f * gL * Pc * Ab;
-    dst[2 * c] = make_float4(g_tau, Pc * gC0, Pc * gC1, Pc * gC2);
-    dst[2 * c + 1] = make_float4(gAc, gDc, Pc * Pc * gL, 0.0f);
+    const float4 a0 = make_float4(g_tau, Pc * gC0, Pc * gC1, Pc * gC2);
+    const float4 a1 = make_float4(gAc, gDc, Pc * Pc * gL, 0.0f);
+    dst[2 * c] = a0;
+    dst[2 * c + 1] = a1;
+    if (dpart_tile) {  // also in the tile order of the tensor-core backward's records
+      const size_t at = 2 * (size_t)pos[(size_t)r * sp.max_chunk + c];
+      dpart_tile[at] = a0;
+      dpart_tile[at + 1] = a1;
+    }
     gA += 2.0f * gL * Pc * Dc;
     gD -= 2.0f * gL * Pc * Ac;
     gP = gPc;
@@ -420,11 +429,21 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   char* ws = static_cast<char*>(workspace);
   const SampParams sp = samp_params(f, s);
   float4* dpart = reinterpret_cast<float4*>(ws + L.dpartials);
+  const bool tc = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
+  if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");
+  if (tc && !(s->flags & NERFXL_SAVE_FEATURES)) {
+    // The forward did not keep the records: rebuild them (the forward's
+    // partials are rewritten with identical values).
+    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, record_out(ws, L), stream);
+    if (st != NERFXL_OK) return st;
+  }
   k_composite_bwd<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
       n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
-      d_rgb, d_depth, d_opacity, d_dist, dpart);
+      d_rgb, d_depth, d_opacity, d_dist, dpart, tc ? reinterpret_cast<const int32_t*>(ws + L.rec_pos) : nullptr,
+      tc ? reinterpret_cast<float4*>(ws + L.rec_dpart) : nullptr);
   st = launch_check("k_composite_bwd");
   if (st != NERFXL_OK) return st;
+  if (tc) return launch_field_bwd_tc(f, level_params(f), ws, L, grad_tables, grad_mlp, stream);
   BwdParams p;
   p.rays_o = rays_o;
   p.rays_d = rays_d;
@@ -445,11 +464,6 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
-  if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");
-  if (f->mlp_dtype != NERFXL_F32)  // 16-bit MLP: tensor-core backward
-    return launch_field_bwd_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart,
-                               L.features ? reinterpret_cast<const uint4*>(ws + L.features) : nullptr, grad_tables,
-                               grad_mlp, stream);
   if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
   void (*kern)(BwdParams) = k_field_bwd_f32<false, 0>;

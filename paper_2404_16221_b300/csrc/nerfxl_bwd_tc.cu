@@ -1,23 +1,44 @@
 // Backward (adjoint) of the field with the MLP on the tensor cores: the
 // mixed-precision forms (BF16/FP16 MLP, FP32 or FP16 tables; FP32 gradients).
 //
-// One CTA = 16 warps on one 128-row tile (4 chunks of one region), the same
-// row / lane-quarter / level-group mapping as the tensor-core forward. Per
-// tile (all products K-major, 128-byte swizzled, FP32 accumulation in TMEM):
-//   recompute  X (features) -> D1 = X W1 -> H1 = relu -> D2 = H1 W2 -> H2 = relu
-//              -> D3 = H2 W3 -> sigma, rgb
-//   adjoint    chunk-local render adjoint (warp scans) -> g_o [128 x 4]
-//              G2 = (H2 > 0) * (g_o W3^T)                    (CUDA cores)
-//              D4 = G2 W2^T, G1 = (H1 > 0) * D4             (tensor cores)
-//              D5 = G1 W1^T = dL/dfeatures -> table scatter-add (vector atomics)
-//              G2 and G1 enter these products as hi + lo pairs of 16-bit values
-//              (two MMAs each), so the upstream gradient keeps ~16 mantissa
-//              bits; the weights are exact in their 16-bit compute copy.
-//   weights    DW += [G2^T ; G1^T] [H1 | X]  (M = 128, N = 96, K = 128 samples),
-//              accumulated in TMEM over every tile of the region; its diagonal
-//              blocks are dW2^T and dW1^T and are flushed once per region.
-//              dW3 = H2^T g_o on CUDA cores (256 outputs).
-// Bounded mbarrier waits flag kErrTimeout, free tensor memory and return.
+// The kernel works from per-tile records in tile order, written by the
+// tensor-core forward: every row's 16-bit features exactly as the forward's
+// first MMA read them, its region coordinates u, position tr and length dl,
+// each chunk's sample count, and (written by the composite backward) each
+// chunk's partial adjoints. One thread copies the next tile's records into a
+// second shared-memory stage with bulk asynchronous copies while the CTA works
+// on the current tile, so no ray, segment or hash-table read sits between
+// tiles.
+//
+// One CTA per SM, 16 warps in two roles. The table-gradient scatter is bound
+// by the SM's throughput for scattered vector atomics (about one address per
+// clock), so it runs concurrently with the MMA pipeline instead of after it:
+//   compute warps 0-7   one 128-row tile (4 chunks of one region) at a time;
+//                       warp w serves TMEM lane quarter q = w % 4 (rows
+//                       32q..32q+31) and column half / level half g = w / 4
+//   scatter warps 8-15  scatter the previous tile's dL/dfeatures, handed over
+//                       through a double-buffered shared-memory slot guarded
+//                       by full / empty mbarriers
+// Per tile, on the compute warps (FP32 accumulation in TMEM):
+//   recompute  D1 = X W1 -> H1 = relu -> D2 = H1 W2 -> H2 = relu -> D3 = H2 W3
+//   adjoint    chunk-local render adjoint (warp scans) -> g_o [128 x 4], stored
+//              as one 16-bit tile row [g_o hi | g_o lo | 0]
+//              G2 = (H2 > 0) * ([g_o hi | g_o lo] [W3 | W3]^T)  (one K = 16 MMA)
+//              D4 = G2 W2^T, G1 = (H1 > 0) * D4
+//              D5 = G1 W1^T = dL/dfeatures -> hand-off slot -> table
+//              scatter-add by the scatter warps (vector atomics)
+//              G2 and G1 enter these products as hi + lo pairs of 16-bit
+//              values (two MMAs each), keeping ~16 mantissa bits of the
+//              upstream gradient; the weights are exact in their 16-bit copy.
+//   weights    DW  += [G2 | G1]^T [H1 | X]        (M = 128, N = 96, K = 128 samples)
+//              DW3 += [H2 | H1]^T [g_o hi | g_o lo]  (M = 128, N = 16;
+//                                                     dW3 = columns 0-3 + 4-7)
+//              Both read the row-major activation tiles as MN-major operands
+//              (the samples are the contraction), accumulate in TMEM over all
+//              of a region's tiles and are flushed once per region: DW's
+//              diagonal blocks are dW2 and dW1, DW3's first 64 rows are dW3.
+// Bounded waits flag kErrTimeout, wait (bounded) for copies still in flight,
+// free tensor memory and return.
 
 #include <cuda_runtime.h>
 
@@ -29,83 +50,89 @@
 namespace nerfxl {
 namespace {
 
-constexpr int kRows = 128;
+constexpr int kRows = kRecRows;
 constexpr int kThreads = 512;
+constexpr int kGroup = 256;  // threads per role
+constexpr int kBarCompute = 1, kBarScatter = 2;
 constexpr int kTileChunks = kRows / kWarp;
-constexpr uint32_t kCols = 256;  // 0-63 D1/D3/D4, 64-127 D2/D5, 128-223 DW
-constexpr uint32_t kDwCol = 128;
+constexpr uint32_t kCols = 256;  // 0-63 D1/D3/D5, 64-127 D2/D4, 128-223 DW, 224-239 DW3
+constexpr uint32_t kDwCol = 128, kDw3Col = 224;
 constexpr uint32_t kSpin = 1u << 24;
 
-// Shared-memory plan (bytes from a 1024-aligned base).
-constexpr uint32_t oX = 0;              // X  [128][64] (k < 32 used)
-constexpr uint32_t oH1 = oX + 16384;    // H1 [128][64]
-constexpr uint32_t oH2 = oH1 + 16384;   // H2 [128][64]
-constexpr uint32_t oG2 = oH2 + 16384;   // G2 [128][64], 16-bit rounding (hi part)
-constexpr uint32_t oG2l = oG2 + 16384;  // G2 - hi (lo part)
-constexpr uint32_t oG1 = oG2l + 16384;  // G1 [128][64] hi
-constexpr uint32_t oG1l = oG1 + 16384;  // G1 lo
-constexpr uint32_t oAT = oG1l + 16384;  // [G2^T ; G1^T] (hi): 2 sub-tiles of [128 rows][64 samples]
-constexpr uint32_t oBT = oAT + 32768;   // [H1^T ; X^T]: 2 sub-tiles of [96 rows][64 samples]
-constexpr uint32_t kBTSub = 96 * 128;
-constexpr uint32_t oB1 = oBT + 2 * kBTSub;  // W1^T [64][32]   (forward layer 1)
-constexpr uint32_t oB2 = oB1 + 8192;        // W2^T [64][64]
-constexpr uint32_t oB3 = oB2 + 8192;        // W3^T [16][64]
-constexpr uint32_t oB4 = oB3 + 2048;        // W2 [64][64] (rows = h1 index)
-constexpr uint32_t oB5 = oB4 + 8192;        // W1 [32][64] (rows = feature index)
-constexpr uint32_t oW3f = oB5 + 4096;       // W3 fp32 [64][4]
-constexpr uint32_t oGo = oW3f + 1024;       // g_o fp32 [128][4]
-constexpr uint32_t oMisc = oGo + 2048;      // mbarrier, TMEM base
-constexpr uint32_t oBase = oMisc + 64;      // int32 base[K+1]
+// Shared-memory plan (bytes from a 1024-aligned base). Activation tiles are
+// 128 rows x 128 B (128-byte swizzle); pairs read as one MN-major operand of
+// M or N = 128 (or 96) sit one tile apart: (H2, H1), (H1, X), (G2, G1).
+constexpr uint32_t kTileBytes = 16384;
+constexpr uint32_t oH2 = 0;
+constexpr uint32_t oH1 = oH2 + kTileBytes;
+constexpr uint32_t oX = oH1 + kTileBytes;     // k < 32 used
+constexpr uint32_t oG2 = oX + kTileBytes;     // G2, 16-bit rounding (hi part)
+constexpr uint32_t oG1 = oG2 + kTileBytes;    // G1 hi
+constexpr uint32_t oG2l = oG1 + kTileBytes;   // G2 - hi (lo part)
+constexpr uint32_t oG1l = oG2l + kTileBytes;  // G1 lo
+constexpr uint32_t oB1 = oG1l + kTileBytes;   // W1^T [64 rows z1][k = feature < 32]  (layer 1)
+constexpr uint32_t oB2 = oB1 + 8192;          // W2^T [64 rows z2][k = h1] (layer 2; MN-major W2 for D4)
+constexpr uint32_t oB3 = oB2 + 8192;          // W3^T [16 rows][k = h2], rows >= 4 zero
+constexpr uint32_t oB5 = oB3 + 2048;          // W1 [32 rows feature][k = z1]
+constexpr uint32_t oB6 = oB5 + 4096;          // [W3 | W3] [64 rows n][k: 0-3, 4-7 = W3[n][0..3], 8-15 zero]
+constexpr uint32_t oGO = oB6 + 8192;          // g_o tile [128 rows][k: 0-3 hi, 4-7 lo, 8-15 zero]
+constexpr uint32_t oStage = oGO + kTileBytes; // two record stages
+constexpr uint32_t kStFeat = 0;
+constexpr uint32_t kStGeom = kStFeat + (uint32_t)kRecFeatBytes;
+constexpr uint32_t kStDpart = kStGeom + 4 * kGeomFloats;
+constexpr uint32_t kStageBytes = kStDpart + 2 * 4 * 16;
+// Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][128 rows]
+// (row-contiguous, so both roles access it without bank conflicts), u as
+// float [3][128], then int32 n_valid[4] and the region.
+constexpr uint32_t oHand = oStage + 2 * kStageBytes;
+constexpr uint32_t kHdDf = 0, kHdU = 16384, kHdNv = kHdU + 3 * 4 * kRows, kHdRegion = kHdNv + 16;
+constexpr uint32_t kHandBytes = kHdRegion + 16;
+constexpr uint32_t oMisc = oHand + 2 * kHandBytes;  // 7 mbarriers, TMEM base, abort flag
+constexpr uint32_t oBase = oMisc + 64;              // int32 base[K+1]
 constexpr size_t kSmemFixed = oBase + 1024;
+static_assert(kStGeom % 16 == 0 && kStDpart % 16 == 0 && kStageBytes % 16 == 0, "bulk copies need 16 B");
+static_assert(oStage % 1024 == 0 && oHand % 16 == 0 && kHandBytes % 16 == 0 && oMisc % 8 == 0, "alignment");
 
 struct BwdTcParams {
-  const float* rays_o;
-  const float* rays_d;
-  const float* boxes;
-  const void* tables;
   const void* mlp;  // 16-bit [K][kMlpParams]
   LevelParams lp;
-  SampParams sp;
   int K;
-  const RayHdr* hdr;
-  const SegDesc* segs;
   const int32_t* base;
-  const uint2* chunks;
   const int32_t* n_tiles;
-  const float4* dpart;
-  const uint4* feat_in;  // features saved by the forward, or NULL (gather again)
-  float* grad_tables;  // FP32 [K][E][2]
-  float* grad_mlp;     // FP32 [K][kMlpParams]
+  const char* rec_feat;   // kRecFeatBytes per tile
+  const char* rec_geom;   // kGeomFloats floats per tile
+  const char* rec_dpart;  // 4 chunks x 2 float4 per tile
+  float* grad_tables;     // FP32 [K][E][2]
+  float* grad_mlp;        // FP32 [K][kMlpParams]
   int32_t* err;
 };
 
 template <bool BF16>
-__device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm) {
+__device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int tid, int nthreads) {
   uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + oB1);
   uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + oB2);
   uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + oB3);
-  uint16_t* b4 = reinterpret_cast<uint16_t*>(sm + oB4);
   uint16_t* b5 = reinterpret_cast<uint16_t*>(sm + oB5);
-  float* w3f = reinterpret_cast<float*>(sm + oW3f);
-  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+  uint16_t* b6 = reinterpret_cast<uint16_t*>(sm + oB6);
+  for (int i = tid; i < kIn * kWidth; i += nthreads) {
     const int f = i / kWidth, n = i % kWidth;  // W1[f][n]
     const uint16_t v = Half2Of<BF16>::bits(blk, i);
     b1[tc::sw128_offset(n, f) >> 1] = v;  // forward: row n, k = f
     b5[tc::sw128_offset(f, n) >> 1] = v;  // backward: row f, k = n
   }
-  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+  for (int i = tid; i < kWidth * kWidth; i += nthreads) {
     const int a = i / kWidth, b = i % kWidth;  // W2[a][b]: h1 index a, z2 index b
-    const uint16_t v = Half2Of<BF16>::bits(blk, kIn * kWidth + i);
-    b2[tc::sw128_offset(b, a) >> 1] = v;  // forward: row b, k = a
-    b4[tc::sw128_offset(a, b) >> 1] = v;  // backward: row a, k = b
+    b2[tc::sw128_offset(b, a) >> 1] = Half2Of<BF16>::bits(blk, kIn * kWidth + i);
   }
-  for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+  for (int i = tid; i < 16 * 64; i += nthreads) {
     const int n = i / 64, k = i % 64;
     b3[tc::sw128_offset(n, k) >> 1] =
         n < kOut ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
   }
-  for (int i = threadIdx.x; i < kWidth * kOut; i += blockDim.x)
-    w3f[i] = Half2Of<BF16>::load(blk, kIn * kWidth + kWidth * kWidth + i);
+  for (int i = tid; i < kWidth * 16; i += nthreads) {
+    const int n = i / 16, k = i % 16;  // W3[n][k % 4] for k < 8
+    b6[tc::sw128_offset(n, k) >> 1] = k < 8 ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + n * kOut + (k & 3)) : 0;
+  }
 }
 
 // Scatter dL/dfeat of levels l0..l0+3 (g8, level order) into the region's
@@ -142,374 +169,418 @@ __device__ __forceinline__ void scatter4(const LevelParams& lp, float2* __restri
   }
 }
 
-// Writes 16 values of row `row` as chunks 2g, 2g+1 of a normal tile and as
-// column `row` of rows r0..r0+15 of a transposed (samples-contiguous) tile.
+// 16-bit value > 0 (sign clear, not zero).
+__device__ __forceinline__ uint32_t positive16(uint32_t bits16) { return (uint32_t)((bits16 - 1u) & 0xFFFFu) < 0x7FFFu; }
+
+// relu of 16 accumulator values -> chunks 2g, 2g+1 of row `row` of a tile;
+// returns the mask of stored values that are > 0.
 template <bool BF16>
-__device__ __forceinline__ void store16(uint32_t tile, uint32_t row, int g, const float* v, uint32_t tt, uint32_t sub,
-                                        uint32_t r0) {
-  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(v[0], v[1]), Half2Of<BF16>::pack(v[2], v[3]),
-                   Half2Of<BF16>::pack(v[4], v[5]), Half2Of<BF16>::pack(v[6], v[7]));
-  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(v[8], v[9]),
-                   Half2Of<BF16>::pack(v[10], v[11]), Half2Of<BF16>::pack(v[12], v[13]),
-                   Half2Of<BF16>::pack(v[14], v[15]));
-  if (tt) {
-    const uint32_t st = tt + (row >> 6) * sub;
+__device__ __forceinline__ uint32_t store16_relu(uint32_t tile, uint32_t row, int g, const float* v) {
+  uint32_t w[8], mask = 0;
 #pragma unroll
-    for (int i = 0; i < 16; i += 2) {
-      const uint32_t pk = Half2Of<BF16>::pack(v[i], v[i + 1]);
-      tc::st_shared_u16(st + tc::sw128_offset(r0 + i, row & 63), (uint16_t)(pk & 0xFFFF));
-      tc::st_shared_u16(st + tc::sw128_offset(r0 + i + 1, row & 63), (uint16_t)(pk >> 16));
-    }
+  for (int i = 0; i < 8; ++i) {
+    w[i] = Half2Of<BF16>::pack(fmaxf(v[2 * i], 0.0f), fmaxf(v[2 * i + 1], 0.0f));
+    mask |= positive16(w[i] & 0xFFFFu) << (2 * i);
+    mask |= positive16(w[i] >> 16) << (2 * i + 1);
   }
+  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g), w[0], w[1], w[2], w[3]);
+  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g + 1), w[4], w[5], w[6], w[7]);
+  return mask;
 }
 
-// Writes 16 values of row `row` as a hi/lo pair of normal tiles (chunks 2g,
-// 2g+1): hi = 16-bit rounding of v, lo = 16-bit rounding of v - hi.
+// 16 values -> chunks 2g, 2g+1 of row `row` as a hi/lo pair of tiles:
+// hi = 16-bit rounding of v, lo = 16-bit rounding of v - hi.
 template <bool BF16>
-__device__ __forceinline__ void store16_lo(uint32_t tile_lo, uint32_t row, int g, const float* v) {
-  float lo[16];
+__device__ __forceinline__ void store16_hilo(uint32_t tile, uint32_t tile_lo, uint32_t row, int g, const float* v) {
+  uint32_t hi[8], lo[8];
 #pragma unroll
-  for (int i = 0; i < 16; i += 2) {
-    const float2 hv = Half2Of<BF16>::unpack(Half2Of<BF16>::pack(v[i], v[i + 1]));
-    lo[i] = v[i] - hv.x;
-    lo[i + 1] = v[i + 1] - hv.y;
+  for (int i = 0; i < 8; ++i) {
+    hi[i] = Half2Of<BF16>::pack(v[2 * i], v[2 * i + 1]);
+    const float2 h = Half2Of<BF16>::unpack(hi[i]);
+    lo[i] = Half2Of<BF16>::pack(v[2 * i] - h.x, v[2 * i + 1] - h.y);
   }
-  tc::st_shared_v4(tile_lo + tc::sw128_chunk(row, 2 * g), Half2Of<BF16>::pack(lo[0], lo[1]),
-                   Half2Of<BF16>::pack(lo[2], lo[3]), Half2Of<BF16>::pack(lo[4], lo[5]),
-                   Half2Of<BF16>::pack(lo[6], lo[7]));
-  tc::st_shared_v4(tile_lo + tc::sw128_chunk(row, 2 * g + 1), Half2Of<BF16>::pack(lo[8], lo[9]),
-                   Half2Of<BF16>::pack(lo[10], lo[11]), Half2Of<BF16>::pack(lo[12], lo[13]),
-                   Half2Of<BF16>::pack(lo[14], lo[15]));
+  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g), hi[0], hi[1], hi[2], hi[3]);
+  tc::st_shared_v4(tile + tc::sw128_chunk(row, 2 * g + 1), hi[4], hi[5], hi[6], hi[7]);
+  tc::st_shared_v4(tile_lo + tc::sw128_chunk(row, 2 * g), lo[0], lo[1], lo[2], lo[3]);
+  tc::st_shared_v4(tile_lo + tc::sw128_chunk(row, 2 * g + 1), lo[4], lo[5], lo[6], lo[7]);
 }
 
-// Bounded wait for the MMAs committed so far; false on timeout (all threads agree).
+// Bounded wait of the compute warps for the MMAs committed so far; false on
+// timeout (all compute threads agree).
 __device__ __forceinline__ bool mma_wait(uint64_t* mbar, uint32_t& phase) {
   const bool ok = tc::mbar_wait_bounded(mbar, phase, kSpin);
   phase ^= 1;
-  return !__syncthreads_or(!ok);
+  return !tc::bar_or(kBarCompute, kGroup, !ok);
 }
+__device__ __forceinline__ void compute_sync() { tc::bar_sync(kBarCompute, kGroup); }
 
-template <bool kF16Table, bool BF16>
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = tc::smem_u32(sm);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMisc);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMisc + 8);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMisc);  // MMA completion
+  uint64_t* full = mbar + 1;                                  // record stages 0, 1
+  uint64_t* hfull = mbar + 3;                                 // hand-off slots 0, 1 written
+  uint64_t* hempty = mbar + 5;                                // hand-off slots 0, 1 read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMisc + 56);
+  volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(sm + oMisc + 60);
   int32_t* s_base = reinterpret_cast<int32_t*>(sm + oBase);
-  const float* w3f = reinterpret_cast<const float*>(sm + oW3f);
-  float* s_go = reinterpret_cast<float*>(sm + oGo);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
-  const int q = warp & 3, g = warp >> 2;
-  const uint32_t row = (uint32_t)(q * kWarp + lane);
 
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  for (int i = tid; i < (int)(kTileBytes / 16); i += blockDim.x) tc::st_shared_v4(sb + oGO + 16 * i, 0u, 0u, 0u, 0u);
   if (warp == 0) tc::tmem_alloc(tmem_slot, kCols);
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (tid == 0) {
+    for (int i = 0; i < 7; ++i) tc::mbar_init(mbar + i, 1);
+    *s_abort = 0;
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-
-  constexpr uint32_t id64 = tc::idesc_f16(BF16, kRows, 64);
-  constexpr uint32_t id32 = tc::idesc_f16(BF16, kRows, 32);
-  constexpr uint32_t id16 = tc::idesc_f16(BF16, kRows, 16);
-  constexpr uint32_t id96 = tc::idesc_f16(BF16, kRows, 96);
-  using TabT = typename TableOf<kF16Table>::T;
-
   const int n_sub = *p.n_tiles * (kChunksPerTile / kTileChunks);
-  int region = -1;
-  const TabT* table = nullptr;
-  float2* gtab = nullptr;
-  uint32_t phase = 0;
-  bool failed = false, dw_started = false;
-  float acc3 = 0.0f;  // dW3 entry (tid < 256): row tid / 4, column tid % 4
+  const int G = (int)gridDim.x;
 
-  auto flush = [&]() {
-    // dW accumulator -> global (diagonal blocks only); needs all MMAs complete.
-    if (dw_started) {
+  if (warp >= kGroup / kWarp) {
+    // ===================== scatter warps =====================
+    const int sw = warp - kGroup / kWarp, q = sw & 3, g = sw >> 2;
+    const uint32_t row = (uint32_t)(q * kWarp + lane);
+    int it = 0;
+    for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
+      const int b = it & 1;
+      const bool ok = tc::mbar_wait_bounded(hfull + b, (uint32_t)(it >> 1) & 1u, kSpin);
+      if (tc::bar_or(kBarScatter, kGroup, !ok || *s_abort != 0)) {
+        if (!ok && tid == kGroup) atomicOr(p.err, kErrTimeout);
+        break;
+      }
+      const char* hd = sm + oHand + (uint32_t)b * kHandBytes;
+      const int n_valid = reinterpret_cast<const int32_t*>(hd + kHdNv)[q];
+      const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegion);
+      const float* hu = reinterpret_cast<const float*>(hd + kHdU);
+      const float u[3] = {hu[row], hu[kRows + row], hu[2 * kRows + row]};
+      const float4* df = reinterpret_cast<const float4*>(hd + kHdDf);
+      float g16[16];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 x = df[(g * 4 + j) * kRows + row];
+        g16[4 * j] = x.x;
+        g16[4 * j + 1] = x.y;
+        g16[4 * j + 2] = x.z;
+        g16[4 * j + 3] = x.w;
+      }
+      tc::bar_sync(kBarScatter, kGroup);  // slot read by every scatter thread
+      if (tid == kGroup) tc::mbar_arrive(hempty + b);
+      if (lane < n_valid) {
+        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+        scatter4(p.lp, gtab, u, 8 * g, g16);
+        scatter4(p.lp, gtab, u, 8 * g + 4, g16 + 8);
+      }
+    }
+  } else {
+    // ===================== compute warps =====================
+    const int q = warp & 3, g = warp >> 2;
+    const uint32_t row = (uint32_t)(q * kWarp + lane);
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    constexpr uint32_t id32 = tc::idesc_f16(BF16, kRows, 32);
+    constexpr uint32_t id64 = tc::idesc_f16(BF16, kRows, 64);
+    constexpr uint32_t id16 = tc::idesc_f16(BF16, kRows, 16);
+    constexpr uint32_t id64_bt = tc::idesc_f16(BF16, kRows, 64) | tc::kMnMajorB;
+    constexpr uint32_t id16_abt = tc::idesc_f16(BF16, kRows, 16) | tc::kMnMajorA | tc::kMnMajorB;
+    constexpr uint32_t id96_abt = tc::idesc_f16(BF16, kRows, 96) | tc::kMnMajorA | tc::kMnMajorB;
+
+    // Thread 0 issues the record copies; pend[s] = iteration whose records
+    // are in flight into stage s (-1: none).
+    int pend[2] = {-1, -1};
+    auto issue = [&](int it, int t) {
+      const int s = it & 1;
+      tc::fence_proxy_async();  // order earlier generic reads of the stage before the overwrite
+      tc::mbar_expect_tx(full + s, kStageBytes);
+      const uint32_t dst = sb + oStage + (uint32_t)s * kStageBytes;
+      tc::bulk_g2s(dst + kStFeat, p.rec_feat + (size_t)t * kRecFeatBytes, (uint32_t)kRecFeatBytes, full + s);
+      tc::bulk_g2s(dst + kStGeom, p.rec_geom + (size_t)t * 4 * kGeomFloats, 4 * kGeomFloats, full + s);
+      tc::bulk_g2s(dst + kStDpart, p.rec_dpart + (size_t)t * 128, 128, full + s);
+      pend[s] = it;
+    };
+    if (tid == 0 && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
+
+    int region = -1;
+    uint32_t phase = 0;
+    bool failed = false, dw_started = false;
+
+    auto flush = [&]() {
+      // DW / DW3 accumulators -> global (needs all MMAs complete).
+      if (!dw_started) return;
       tc::fence_after_sync();
-      float v[24];
-      tc::tmem_ld16(tq + kDwCol + 24 * g, v);
-      tc::tmem_ld8(tq + kDwCol + 24 * g + 16, v + 16);
-      tc::tmem_ld_wait();
       float* gm = p.grad_mlp + (size_t)region * kMlpParams;
+      float v[16];
 #pragma unroll
-      for (int i = 0; i < 24; ++i) {
-        const int c = 24 * g + i, r = (int)row;
-        if (r < 64 && c < 64) {
-          atomicAdd(gm + kIn * kWidth + c * kWidth + r, v[i]);  // dW2[h1 = c][z2 = r]
-        } else if (r >= 64 && c >= 64 && c < 96) {
-          atomicAdd(gm + (c - 64) * kWidth + (r - 64), v[i]);  // dW1[feat = c - 64][z1 = r - 64]
-        }
-      }
-    }
-    if (tid < kWidth * kOut && region >= 0 && acc3 != 0.0f)
-      atomicAdd(p.grad_mlp + (size_t)region * kMlpParams + kIn * kWidth + kWidth * kWidth + tid, acc3);
-    acc3 = 0.0f;
-    dw_started = false;
-  };
-
-  for (int t = blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
-    const int k = region_of_chunk(s_base, p.K, t * kTileChunks);
-    if (k != region) {
-      tc::fence_before_sync();
-      __syncthreads();
-      if (region >= 0) flush();
-      tc::fence_before_sync();
-      __syncthreads();
-      load_weights_bwd<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm);
-      region = k;
-      table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
-      gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-    }
-    // ---- gather (four threads per row, four levels each)
-    const uint2 ref = p.chunks[t * kTileChunks + q];
-    const bool chunk_ok = ref.x != kEmptyChunk;
-    bool valid = false;
-    float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f};
-    float f8[8];
+      for (int h = 0; h < 3; ++h) {
+        tc::tmem_ld16(tq + kDwCol + 48 * g + 16 * h, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
-    float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
-    if (chunk_ok) {
-      const uint32_t ray = ref.x;
-      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
-      const RayHdr h = p.hdr[ray];
-      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
-      const int i = c * kWarp + lane;
-      valid = i < seg_n(sd);
-      if (g == 0) {
-        const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
-        const float4 a0 = p.dpart[2 * slot], a1 = p.dpart[2 * slot + 1];
-        gtc = a0.x;
-        gC[0] = a0.y;
-        gC[1] = a0.z;
-        gC[2] = a0.w;
-        gA = a1.x;
-        gD = a1.y;
-        gL = a1.z;
-      }
-      if (valid) {
-        float o[3], d[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          o[ax] = p.rays_o[3 * (size_t)ray + ax];
-          d[ax] = p.rays_d[3 * (size_t)ray + ax];
-        }
-        float a, b;
-        segment_interval(sd, h.tn, h.delta, i, a, b);
-        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
-        dl = __fsub_rn(b, a);
-        tr = __fsub_rn(tbar, h.tn);
-        float x[3];
-        sample_point(o, d, tbar, x);
-        region_coord(p.boxes + 6 * k, x, u);
-        if (p.feat_in) {
-          const uint4 pk = p.feat_in[((size_t)(t * kTileChunks + q) * 4 + g) * kWarp + lane];
-          const uint32_t wv[4] = {pk.x, pk.y, pk.z, pk.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float2 fv = Half2Of<BF16>::unpack(wv[j]);
-            f8[2 * j] = fv.x;
-            f8[2 * j + 1] = fv.y;
+        for (int i = 0; i < 16; ++i) {
+          const int c = 48 * g + 16 * h + i, r = (int)row;
+          if (r < 64 && c < 64) {
+            atomicAdd(gm + kIn * kWidth + c * kWidth + r, v[i]);  // dW2[h1 = c][z2 = r]
+          } else if (r >= 64 && c >= 64 && c < 96) {
+            atomicAdd(gm + (c - 64) * kWidth + (r - 64), v[i]);  // dW1[feat = c - 64][z1 = r - 64]
           }
-        } else {
-          gather4<TabT>(p.lp, table, u, 4 * g, f8);
         }
       }
-    }
-    {
-      // X (normal, chunk g) and X^T (rows 64 + 8g .. 64 + 8g + 7 of the B^T tile)
-      tc::st_shared_v4(sb + oX + tc::sw128_chunk(row, g), Half2Of<BF16>::pack(f8[0], f8[1]),
-                       Half2Of<BF16>::pack(f8[2], f8[3]), Half2Of<BF16>::pack(f8[4], f8[5]),
-                       Half2Of<BF16>::pack(f8[6], f8[7]));
-      const uint32_t st = sb + oBT + (row >> 6) * kBTSub;
+      if (g == 0 && q < 2) {  // rows 0..63: dW3[h2 = row][m] = hi column m + lo column 4 + m
+        tc::tmem_ld8(tq + kDw3Col, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 8; i += 2) {
-        const uint32_t pk = Half2Of<BF16>::pack(f8[i], f8[i + 1]);
-        tc::st_shared_u16(st + tc::sw128_offset(64 + 8 * g + i, row & 63), (uint16_t)(pk & 0xFFFF));
-        tc::st_shared_u16(st + tc::sw128_offset(64 + 8 * g + i + 1, row & 63), (uint16_t)(pk >> 16));
+        for (int m = 0; m < kOut; ++m)
+          atomicAdd(gm + kIn * kWidth + kWidth * kWidth + row * kOut + m, v[m] + v[kOut + m]);
       }
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- forward recompute: D1 = X W1
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int kk = 0; kk < 2; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(sb + oX + 32 * kk), tc::desc_sw128(sb + oB1 + 32 * kk), id64, kk);
-      tc::mma_commit(mbar);
-    }
-    if (!mma_wait(mbar, phase)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    float v[16];
-    tc::tmem_ld16(tq + 16 * g, v);
-    tc::tmem_ld_wait();
+      dw_started = false;
+    };
+
+    int it = 0;
+    for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
+      const int s = it & 1;
+      const int k = region_of_chunk(s_base, p.K, t * kTileChunks);
+      if (k != region) {
+        tc::fence_before_sync();
+        compute_sync();
+        if (region >= 0) flush();
+        tc::fence_before_sync();
+        compute_sync();
+        load_weights_bwd<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm, tid, kGroup);
+        region = k;
+      }
+      if (tid == 0 && t + G < n_sub) issue(it + 1, t + G);
+      {
+        const bool ok = tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpin);
+        if (tc::bar_or(kBarCompute, kGroup, !ok)) {
+          failed = true;
+          break;
+        }
+        if (tid == 0) pend[s] = -1;
+      }
+      // ---- this tile's records
+      const char* st = sm + oStage + (uint32_t)s * kStageBytes;
+      const float* geo = reinterpret_cast<const float*>(st + kStGeom);
+      const int n_valid = reinterpret_cast<const int32_t*>(geo)[5 * kRows + q];
+      const bool valid = lane < n_valid;
+      const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-    store16<BF16>(sb + oH1, row, g, v, sb + oBT, kBTSub, 16 * g);  // H1 and H1^T (B^T rows 0..63)
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // D2 = H1 W2
-    if (tid == 0) {
+      for (int h = 0; h < 2; ++h) {  // X chunks 2g, 2g+1 (levels 8g..8g+7)
+        const uint32_t c = (uint32_t)(2 * g + h);
+        const uint4 fx = tc::ld_shared_v4(tc::smem_u32(st + kStFeat) + (((uint32_t)q * 4 + c) * kWarp + lane) * 16);
+        tc::st_shared_v4(sb + oX + tc::sw128_chunk(row, c), fx.x, fx.y, fx.z, fx.w);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      // ---- forward recompute: D1 = X W1
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tmem, tc::desc_sw128(sb + oX + 32 * kk), tc::desc_sw128(sb + oB1 + 32 * kk), id64, kk);
+        tc::mma_commit(mbar);
+      }
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
       tc::fence_after_sync();
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oH1 + 32 * kk), tc::desc_sw128(sb + oB2 + 32 * kk), id64, kk);
-      tc::mma_commit(mbar);
-    }
-    if (!mma_wait(mbar, phase)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    tc::tmem_ld16(tq + 64 + 16 * g, v);
-    tc::tmem_ld_wait();
+      float v[16];
+      uint32_t mask1 = 0, mask2 = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-    store16<BF16>(sb + oH2, row, g, v, 0, 0, 0);
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // D3 = H2 W3
-    if (tid == 0) {
+      for (int h = 0; h < 2; ++h) {
+        tc::tmem_ld16(tq + 32 * g + 16 * h, v);
+        tc::tmem_ld_wait();
+        mask1 |= store16_relu<BF16>(sb + oH1, row, 2 * g + h, v) << (16 * h);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      // D2 = H1 W2
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oH1 + 32 * kk), tc::desc_sw128(sb + oB2 + 32 * kk), id64, kk);
+        tc::mma_commit(mbar);
+      }
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
       tc::fence_after_sync();
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(sb + oH2 + 32 * kk), tc::desc_sw128(sb + oB3 + 32 * kk), id16, kk);
-      tc::mma_commit(mbar);
-    }
-    if (!mma_wait(mbar, phase)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    // ---- chunk-local render adjoint -> g_o (warps of level group 0)
-    if (g == 0) {
-      tc::tmem_ld16(tq, v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tc::tmem_ld16(tq + 64 + 32 * g + 16 * h, v);
+        tc::tmem_ld_wait();
+        mask2 |= store16_relu<BF16>(sb + oH2, row, 2 * g + h, v) << (16 * h);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      // D3 = H2 W3
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem, tc::desc_sw128(sb + oH2 + 32 * kk), tc::desc_sw128(sb + oB3 + 32 * kk), id16, kk);
+        tc::mma_commit(mbar);
+      }
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      // ---- chunk-local render adjoint -> g_o tile row (warps of level half 0)
+      if (g == 0) {
+        tc::tmem_ld8(tq, v);
+        tc::tmem_ld_wait();
+        float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (n_valid > 0) {
+          const float4 a0 = *reinterpret_cast<const float4*>(st + kStDpart + 32 * q);
+          const float4 a1 = *reinterpret_cast<const float4*>(st + kStDpart + 32 * q + 16);
+          const float gC[3] = {a0.y, a0.z, a0.w};
+          float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+          if (valid) {
+            sigma = expf(v[0]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
+          }
+          float g_sigma, g_rgb[3];
+          render_chunk_adjoint(sigma, rgb, tr, dl, lane, a0.x, gC, a1.x, a1.y, a1.z, g_sigma, g_rgb);
+          if (valid) {
+            go[0] = g_sigma * sigma;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) go[1 + j] = g_rgb[j] * rgb[j] * (1.0f - rgb[j]);
+          }
+        }
+        const uint32_t h01 = Half2Of<BF16>::pack(go[0], go[1]), h23 = Half2Of<BF16>::pack(go[2], go[3]);
+        const float2 f01 = Half2Of<BF16>::unpack(h01), f23 = Half2Of<BF16>::unpack(h23);
+        tc::st_shared_v4(sb + oGO + tc::sw128_chunk(row, 0), h01, h23,
+                         Half2Of<BF16>::pack(go[0] - f01.x, go[1] - f01.y),
+                         Half2Of<BF16>::pack(go[2] - f23.x, go[3] - f23.y));
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      const bool acc_on = dw_started;
+      // ---- G2 before the mask: [g_o hi | g_o lo] [W3 | W3]^T (columns 64..127);
+      //      DW3 += [H2 | H1]^T [g_o hi | g_o lo] (16 samples per K step = two
+      //      8-row groups of both MN-major operands)
+      if (tid == 0) {
+        tc::fence_after_sync();
+        tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oGO), tc::desc_sw128(sb + oB6), id64, 0u);
+        for (int kk = 0; kk < 8; ++kk)
+          tc::mma_f16(tmem + kDw3Col, tc::desc_sw128_mn(sb + oH2 + 2048 * kk, kTileBytes),
+                      tc::desc_sw128_mn(sb + oGO + 2048 * kk, 1024), id16_abt, (acc_on || kk > 0) ? 1u : 0u);
+        tc::mma_commit(mbar);
+      }
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      // ---- G2 = (H2 > 0) * G2 before the mask, columns 32g..32g+31 of this row
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tc::tmem_ld16(tq + 64 + 32 * g + 16 * h, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (!((mask2 >> (16 * h + i)) & 1u)) v[i] = 0.0f;
+        store16_hilo<BF16>(sb + oG2, sb + oG2l, row, 2 * g + h, v);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      // ---- D4 = G2 W2^T (dL/dh1; W2 read MN-major from the layer-2 tile)
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oG2 + 32 * kk), tc::desc_sw128_mn(sb + oB2 + 2048 * kk, 1024),
+                      id64_bt, kk);
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oG2l + 32 * kk), tc::desc_sw128_mn(sb + oB2 + 2048 * kk, 1024),
+                      id64_bt, 1);
+        tc::mma_commit(mbar);
+      }
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tc::tmem_ld16(tq + 64 + 32 * g + 16 * h, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (!((mask1 >> (16 * h + i)) & 1u)) v[i] = 0.0f;  // G1 = (H1 > 0) * D4
+        store16_hilo<BF16>(sb + oG1, sb + oG1l, row, 2 * g + h, v);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      compute_sync();
+      // ---- D5 = G1 W1^T (dL/dfeatures); DW += [G2 | G1]^T [H1 | X]
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem, tc::desc_sw128(sb + oG1 + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, kk);
+        for (int kk = 0; kk < 4; ++kk)
+          tc::mma_f16(tmem, tc::desc_sw128(sb + oG1l + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, 1);
+        for (int kk = 0; kk < 8; ++kk)
+          tc::mma_f16(tmem + kDwCol, tc::desc_sw128_mn(sb + oG2 + 2048 * kk, kTileBytes),
+                      tc::desc_sw128_mn(sb + oH1 + 2048 * kk, kTileBytes), id96_abt, (acc_on || kk > 0) ? 1u : 0u);
+        tc::mma_commit(mbar);
+      }
+      dw_started = true;
+      if (!mma_wait(mbar, phase)) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      tc::tmem_ld16(tq + 16 * g, v);  // dL/dfeatures of levels 8g..8g+7
       tc::tmem_ld_wait();
-      float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (chunk_ok) {
-        float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
-        if (valid) {
-          sigma = expf(v[0]);
-#pragma unroll
-          for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
-        }
-        float g_sigma, g_rgb[3];
-        render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
-        if (valid) {
-          go[0] = g_sigma * sigma;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) go[1 + j] = g_rgb[j] * rgb[j] * (1.0f - rgb[j]);
+      // ---- hand the tile's dL/dfeatures to the scatter warps
+      const int b = it & 1;
+      if (it >= 2) {
+        const bool ok = tc::mbar_wait_bounded(hempty + b, (uint32_t)((it >> 1) + 1) & 1u, kSpin);
+        if (tc::bar_or(kBarCompute, kGroup, !ok)) {
+          failed = true;
+          break;
         }
       }
-      *reinterpret_cast<float4*>(s_go + 4 * row) = make_float4(go[0], go[1], go[2], go[3]);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- G2 = (H2 > 0) * (g_o W3^T), columns 16g..16g+15 of this row; G2^T rows 0..63 of A^T
-    {
-      const float4 go = *reinterpret_cast<const float4*>(s_go + 4 * row);
-      const uint4 h0 = tc::ld_shared_v4(sb + oH2 + tc::sw128_chunk(row, 2 * g));
-      const uint4 h1 = tc::ld_shared_v4(sb + oH2 + tc::sw128_chunk(row, 2 * g + 1));
-      const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+      char* hd = sm + oHand + (uint32_t)b * kHandBytes;
+      float4* df = reinterpret_cast<float4*>(hd + kHdDf);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float2 hv = Half2Of<BF16>::unpack(hw[i]);
+      for (int j = 0; j < 4; ++j) df[(g * 4 + j) * kRows + row] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      if (g == 0) {
+        float* hu = reinterpret_cast<float*>(hd + kHdU);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int n = 16 * g + 2 * i + hh;
-          const float4 w3 = *reinterpret_cast<const float4*>(w3f + 4 * n);
-          const float s = w3.x * go.x + w3.y * go.y + w3.z * go.z + w3.w * go.w;
-          v[2 * i + hh] = (hh ? hv.y : hv.x) > 0.0f ? s : 0.0f;
-        }
+        for (int a = 0; a < 3; ++a) hu[a * kRows + row] = geo[a * kRows + row];
+        if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNv)[q] = n_valid;
+        if (tid == 0) *reinterpret_cast<int32_t*>(hd + kHdRegion) = k;
       }
-      store16<BF16>(sb + oG2, row, g, v, sb + oAT, 16384, 16 * g);
-      store16_lo<BF16>(sb + oG2l, row, g, v);
+      tc::fence_before_sync();
+      compute_sync();  // slot written; tiles, stage and TMEM free for the next tile
+      if (tid == 0) tc::mbar_arrive(hfull + b);
     }
-    // dW3[n][m] += sum_rows H2[row][n] g_o[row][m]
-    if (tid < kWidth * kOut) {
-      const int n = tid >> 2, m = tid & 3;
-      float s = 0.0f;
-      for (int r = 0; r < kRows; ++r)
-        s = fmaf(Half2Of<BF16>::from_bits(tc::ld_shared_u16(sb + oH2 + tc::sw128_offset(r, n))), s_go[4 * r + m], s);
-      acc3 += s;
+    if (!failed && region >= 0) {
+      tc::fence_before_sync();
+      compute_sync();
+      flush();
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- D4 = G2 W2^T (dL/dh1)
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(sb + oG2 + 32 * kk), tc::desc_sw128(sb + oB4 + 32 * kk), id64, kk);
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem, tc::desc_sw128(sb + oG2l + 32 * kk), tc::desc_sw128(sb + oB4 + 32 * kk), id64, 1);
-      tc::mma_commit(mbar);
+    if (failed && tid == 0) {
+      atomicOr(p.err, kErrTimeout);
+      *s_abort = 1;  // wake the scatter warps; they see the flag and stop
+      tc::mbar_arrive(hfull);
+      tc::mbar_arrive(hfull + 1);
+      // let MMAs and record copies still in flight land before the CTA exits
+      tc::mbar_wait_bounded(mbar, phase ^ 1u, kSpin);  // the phase a timed-out MMA wait was on
+      for (int s = 0; s < 2; ++s)
+        if (pend[s] >= 0) tc::mbar_wait_bounded(full + s, (uint32_t)(pend[s] >> 1) & 1u, kSpin);
     }
-    if (!mma_wait(mbar, phase)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    tc::tmem_ld16(tq + 16 * g, v);
-    tc::tmem_ld_wait();
-    {
-      // G1 = (H1 > 0) * D4; G1^T rows 64..127 of A^T
-      const uint4 h0 = tc::ld_shared_v4(sb + oH1 + tc::sw128_chunk(row, 2 * g));
-      const uint4 h1 = tc::ld_shared_v4(sb + oH1 + tc::sw128_chunk(row, 2 * g + 1));
-      const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float2 hv = Half2Of<BF16>::unpack(hw[i]);
-        if (!(hv.x > 0.0f)) v[2 * i] = 0.0f;
-        if (!(hv.y > 0.0f)) v[2 * i + 1] = 0.0f;
-      }
-      store16<BF16>(sb + oG1, row, g, v, sb + oAT, 16384, 64 + 16 * g);
-      store16_lo<BF16>(sb + oG1l, row, g, v);
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- D5 = G1 W1^T (dL/dfeatures); DW += [G2^T; G1^T] [H1 | X]
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oG1 + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, kk);
-      for (int kk = 0; kk < 4; ++kk)
-        tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oG1l + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, 1);
-      for (int kk = 0; kk < 8; ++kk) {
-        const uint32_t off = (uint32_t)(kk & 3) * 32;  // 16 samples per K step, 4 steps per sub-tile
-        tc::mma_f16(tmem + kDwCol, tc::desc_sw128(sb + oAT + (kk >> 2) * 16384 + off),
-                    tc::desc_sw128(sb + oBT + (kk >> 2) * kBTSub + off), id96, (dw_started || kk > 0) ? 1u : 0u);
-      }
-      tc::mma_commit(mbar);
-    }
-    dw_started = true;
-    if (!mma_wait(mbar, phase)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    float g8[8];
-    tc::tmem_ld8(tq + 64 + 8 * g, g8);
-    tc::tmem_ld_wait();
-    if (valid) scatter4(p.lp, gtab, u, 4 * g, g8);
-    tc::fence_before_sync();
-    __syncthreads();  // tiles and TMEM free for the next tile
   }
-  if (!failed && region >= 0) {
-    tc::fence_before_sync();
-    __syncthreads();
-    flush();
-  }
-  if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kCols);
@@ -517,36 +588,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
 
 }  // namespace
 
-nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                  const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  const float4* dpart, const uint4* feat_in, float* grad_tables, float* grad_mlp,
-                                  cudaStream_t stream) {
+nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,
+                                  float* grad_tables, float* grad_mlp, cudaStream_t stream) {
+  if (L.rec_tiles == 0) return set_error(NERFXL_E_WORKSPACE, "workspace has no tensor-core backward records");
   BwdTcParams p;
-  p.feat_in = feat_in;
-  p.rays_o = rays_o;
-  p.rays_d = rays_d;
-  p.boxes = f->boxes;
-  p.tables = f->tables;
   p.mlp = f->mlp;
   p.lp = lp;
-  p.sp = sp;
   p.K = f->K;
-  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
-  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
-  p.dpart = dpart;
+  p.rec_feat = ws + L.rec_feat;
+  p.rec_geom = ws + L.rec_geom;
+  p.rec_dpart = ws + L.rec_dpart;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
   const size_t smem = kSmemFixed + sizeof(int32_t) * (f->K + 1);
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-  const bool bf16 = f->mlp_dtype == NERFXL_BF16;
-  const bool f16tab = f->table_dtype == NERFXL_F16;
-  void (*kern)(BwdTcParams) = nullptr;
-  if (f16tab) kern = bf16 ? k_field_bwd_tc<true, true> : k_field_bwd_tc<true, false>;
-  else kern = bf16 ? k_field_bwd_tc<false, true> : k_field_bwd_tc<false, false>;
+  void (*kern)(BwdTcParams) = f->mlp_dtype == NERFXL_BF16 ? k_field_bwd_tc<true> : k_field_bwd_tc<false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_bwd_tc smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kTileChunks, 1);

@@ -320,6 +320,15 @@ int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s) {
 
 int max_chunks(int S, int max_seg) { return max_seg + (S - 1) / kWarp; }
 
+RecordOut record_out(char* ws, const Layout& L) {
+  RecordOut r = {nullptr, nullptr, nullptr};
+  if (L.rec_tiles == 0) return r;
+  r.feat = reinterpret_cast<uint4*>(ws + L.rec_feat);
+  r.geom = reinterpret_cast<float*>(ws + L.rec_geom);
+  r.pos = reinterpret_cast<int32_t*>(ws + L.rec_pos);
+  return r;
+}
+
 Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int for_backward) {
   Layout L;
   const int ms = effective_max_seg(f, s);
@@ -342,7 +351,15 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   L.chunks = take(sizeof(uint2) * L.chunk_cap);
   L.partials = take(sizeof(float4) * 2 * R * mc);
   L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
-  L.features = (for_backward && (s->flags & NERFXL_SAVE_FEATURES)) ? take((size_t)L.chunk_cap * 4 * 32 * 16) : 0;
+  L.rec_feat = L.rec_geom = L.rec_dpart = L.rec_pos = 0;
+  L.rec_tiles = 0;
+  if (for_backward && (f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16)) {
+    L.rec_tiles = (L.chunk_cap + 3) / 4;
+    L.rec_feat = take(kRecFeatBytes * L.rec_tiles);
+    L.rec_geom = take(sizeof(float) * kGeomFloats * L.rec_tiles);
+    L.rec_dpart = take(sizeof(float4) * 2 * 4 * L.rec_tiles);
+    L.rec_pos = take(sizeof(int32_t) * R * mc);
+  }
   L.total = off;
   L.max_seg = ms;
   L.max_chunk = mc;
@@ -514,14 +531,14 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   if (st != NERFXL_OK) return st;
   if (n_rays == 0) return NERFXL_OK;
   if (tc_mlp) {
-    uint4* feat_out = nullptr;
+    RecordOut rec = {nullptr, nullptr, nullptr};
     if (s->flags & NERFXL_SAVE_FEATURES) {
       if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
       const Layout LB = layout(f, s, n_rays, 1);
       if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
-      feat_out = reinterpret_cast<uint4*>(ws + LB.features);
+      rec = record_out(ws, LB);
     }
-    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, feat_out, stream);
+    st = launch_field_fwd_tc(f, sp, level_params(f), rays_o, rays_d, ws, L, rec, stream);
     if (st != NERFXL_OK) return st;
     k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
         n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),

@@ -169,7 +169,7 @@ struct FwdTcParams {
   const uint2* chunks;
   const int32_t* n_tiles;  // tiles of kChunksPerTile chunks
   float4* partials;
-  uint4* feat_out;  // saved 16-bit features [chunk slot][group][lane] or NULL
+  RecordOut rec;  // the backward's per-tile records, or all NULL
   int32_t* err;
 };
 
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     const uint2 ref = p.chunks[t * kTcChunks + q];
     const bool chunk_ok = ref.x != kEmptyChunk;
     bool valid = false;
-    float tr = 0.0f, dl = 0.0f;
+    float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f};
     float f8[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
@@ -254,19 +254,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
         dl = __fsub_rn(b, a);
         tr = __fsub_rn(tbar, h.tn);
-        float x[3], u[3];
+        float x[3];
         sample_point(o, d, tbar, x);
         region_coord(p.boxes + 6 * k, x, u);
         gather4<TabT>(p.lp, table, u, 4 * g, f8);
       }
     }
     Op::store8(a0, row, g, f8);
-    if (kKind != kKindE4M3 && p.feat_out) {
+    if (kKind != kKindE4M3 && p.rec.feat) {
+      // Records for the backward: the features exactly as the first MMA reads
+      // them, the sample's region coordinates / position / length (thread g
+      // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
+      // count, and the chunk's tile-order position for the composite adjoint.
       const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      p.feat_out[((size_t)(t * kTcChunks + q) * 4 + g) * kWarp + lane] = pk;
+      p.rec.feat[((size_t)(t * kTcChunks + q) * 4 + g) * kWarp + lane] = pk;
+      float* geo = p.rec.geom + (size_t)t * kGeomFloats;
+      geo[g * kTcRows + row] = g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr));
+      if (g == 0) {
+        geo[4 * kTcRows + row] = dl;
+        if (lane == 0) {
+          const int n_valid = chunk_ok ? min(kWarp, seg_n(sd) - c * kWarp) : 0;
+          reinterpret_cast<int32_t*>(geo)[5 * kTcRows + q] = n_valid;
+          if (chunk_ok) p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = t * kTcChunks + q;
+        }
+      }
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -364,9 +378,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 // Host dispatch (called from nerfxl_render_fwd).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  uint4* feat_out, cudaStream_t stream) {
+                                  const RecordOut& rec, cudaStream_t stream) {
   FwdTcParams p;
-  p.feat_out = feat_out;
+  p.rec = rec;
   p.rays_o = rays_o;
   p.rays_d = rays_d;
   p.boxes = f->boxes;

@@ -21,8 +21,14 @@ struct Layout {
   size_t chunks;     // uint2[chunk_cap]
   size_t partials;   // float4[R][max_chunk][2]
   size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
-  size_t features;   // uint4[chunk_cap][4][32]: 16-bit features (backward + NERFXL_SAVE_FEATURES)
+  // Per-tile records of the tensor-core backward (backward workspaces with a
+  // 16-bit MLP only; 0 otherwise). A tile is 4 chunks = 128 sample rows.
+  size_t rec_feat;   // uint4[tiles][4 chunks][4 level groups][32 lanes]: 16-bit features
+  size_t rec_geom;   // float[tiles][kGeomFloats]: u0, u1, u2, tr, dl per row; samples per chunk
+  size_t rec_dpart;  // float4[tiles * 4][2]: chunk adjoints in tile order
+  size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
   size_t total;
+  int64_t rec_tiles; // tiles the record regions hold
   int64_t chunk_cap;
   int max_seg, max_chunk;
 };
@@ -46,14 +52,27 @@ int fwd_grid(int64_t max_tiles, int ctas_per_sm);
 nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
                               const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,
                               const int64_t* out_index, void* workspace, size_t ws_bytes, cudaStream_t stream);
-// Tensor-core field backward (16-bit MLP).
-nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                  const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  const float4* dpart, const uint4* feat_in, float* grad_tables, float* grad_mlp,
-                                  cudaStream_t stream);
+// Record geometry block of one tile: rows' u0, u1, u2, tr, dl (128 floats
+// each), then the valid-sample count of each of the 4 chunks (int32).
+constexpr int kRecRows = 128;
+constexpr int kGeomFloats = 5 * kRecRows + 4;  // 2576 bytes, a multiple of 16
+constexpr size_t kRecFeatBytes = (size_t)kRecRows * 64;  // 8192 bytes per tile
+
+// Where the tensor-core forward writes the backward's records (all NULL for a
+// plain forward).
+struct RecordOut {
+  uint4* feat;
+  float* geom;
+  int32_t* pos;
+};
+RecordOut record_out(char* ws, const Layout& L);
+
+// Tensor-core field backward (16-bit MLP), from the per-tile records.
+nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,
+                                  float* grad_tables, float* grad_mlp, cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                  uint4* feat_out, cudaStream_t stream);
+                                  const RecordOut& rec, cudaStream_t stream);
 
 }  // namespace nerfxl

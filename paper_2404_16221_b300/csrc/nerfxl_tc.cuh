@@ -43,6 +43,25 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_addr) {
   return d;
 }
 
+// Descriptor of an MN-major operand in the same 128-byte-swizzled tiles: a
+// tile whose rows are the contraction index (K) and whose 64 row elements are
+// the M (or N) index. Atoms are 8 K-rows x 64 elements (1024 bytes, K-groups
+// 1024 bytes apart: the stride byte offset); `atom_stride` is the leading
+// byte offset, the distance to the tile holding elements 64..127 of M or N.
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t smem_addr, uint32_t atom_stride) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((atom_stride >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// Instruction-descriptor bits selecting MN-major ("transposed") A and B.
+constexpr uint32_t kMnMajorA = 1u << 15;
+constexpr uint32_t kMnMajorB = 1u << 16;
+
 // Instruction descriptor, kind::f16: D format F32 (bits 4-5 = 1), A/B format
 // (bits 7-9, 10-12: 0 = F16, 1 = BF16), both K-major, N >> 3 (bits 17-22),
 // M >> 4 (bits 24-28).
@@ -141,6 +160,42 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parit
   for (uint32_t i = 0; i < max_spins; ++i)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
+}
+
+// Arms the mbarrier's current phase for `bytes` of asynchronous copies (and
+// counts this thread's arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// Plain arrival (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Named barrier `id` over `n` threads (a multiple of 32), and its OR-vote form.
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ bool bar_or(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// Bulk asynchronous copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16); completion is counted on the mbarrier's transaction bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_smem),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {

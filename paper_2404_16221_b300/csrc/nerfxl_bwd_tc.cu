@@ -3,12 +3,13 @@
 //
 // The kernel works from per-tile records in tile order, written by the
 // tensor-core forward: every row's 16-bit features exactly as the forward's
-// first MMA read them, its region coordinates u, position tr and length dl,
-// each chunk's sample count, and (written by the composite backward) each
-// chunk's partial adjoints. One thread copies the next tile's records into a
-// second shared-memory stage with bulk asynchronous copies while the CTA works
-// on the current tile, so no ray, segment or hash-table read sits between
-// tiles.
+// first MMA read them (already laid out as that MMA's 64-byte-swizzled A
+// tile), its region coordinates u, position tr and length dl, the chunk-local
+// Tn, w and distortion pair sum of the forward's render, each chunk's sample
+// count, and (written by the composite backward) each chunk's partial
+// adjoints. One thread copies the next tile's records into a second
+// shared-memory stage with bulk asynchronous copies while the CTA works on the
+// current tile, so no ray, segment or hash-table read sits between tiles.
 //
 // One CTA per SM, 16 warps in two roles. The table-gradient scatter is bound
 // by the SM's throughput for scattered vector atomics (about one address per
@@ -21,7 +22,8 @@
 //                       by full / empty mbarriers
 // Per tile, on the compute warps (FP32 accumulation in TMEM):
 //   recompute  D1 = X W1 -> H1 = relu -> D2 = H1 W2 -> H2 = relu -> D3 = H2 W3
-//   adjoint    chunk-local render adjoint (warp scans) -> g_o [128 x 4], stored
+//   adjoint    chunk-local render adjoint from the kept Tn, w, pair (one warp
+//              suffix scan) -> g_o [128 x 4], stored
 //              as one 16-bit tile row [g_o hi | g_o lo | 0]
 //              G2 = (H2 > 0) * ([g_o hi | g_o lo] [W3 | W3]^T)  (one K = 16 MMA)
 //              D4 = G2 W2^T, G1 = (H1 > 0) * D4
@@ -30,7 +32,7 @@
 //              G2 and G1 enter these products as hi + lo pairs of 16-bit
 //              values (two MMAs each), keeping ~16 mantissa bits of the
 //              upstream gradient; the weights are exact in their 16-bit copy.
-//   weights    DW  += [G2 | G1]^T [H1 | X]        (M = 128, N = 96, K = 128 samples)
+//   weights    DW  += [G2 | G1]^T [H1 | X]        (M = 128, N = 64 + 32, K = 128 samples)
 //              DW3 += [H2 | H1]^T [g_o hi | g_o lo]  (M = 128, N = 16;
 //                                                     dW3 = columns 0-3 + 4-7)
 //              Both read the row-major activation tiles as MN-major operands
@@ -61,12 +63,11 @@ constexpr uint32_t kSpin = 1u << 24;
 
 // Shared-memory plan (bytes from a 1024-aligned base). Activation tiles are
 // 128 rows x 128 B (128-byte swizzle); pairs read as one MN-major operand of
-// M or N = 128 (or 96) sit one tile apart: (H2, H1), (H1, X), (G2, G1).
+// M = 128 sit one tile apart: (H2, H1) and (G2, G1).
 constexpr uint32_t kTileBytes = 16384;
 constexpr uint32_t oH2 = 0;
 constexpr uint32_t oH1 = oH2 + kTileBytes;
-constexpr uint32_t oX = oH1 + kTileBytes;     // k < 32 used
-constexpr uint32_t oG2 = oX + kTileBytes;     // G2, 16-bit rounding (hi part)
+constexpr uint32_t oG2 = oH1 + kTileBytes;    // G2, 16-bit rounding (hi part)
 constexpr uint32_t oG1 = oG2 + kTileBytes;    // G1 hi
 constexpr uint32_t oG2l = oG1 + kTileBytes;   // G2 - hi (lo part)
 constexpr uint32_t oG1l = oG2l + kTileBytes;  // G1 lo
@@ -76,22 +77,26 @@ constexpr uint32_t oB3 = oB2 + 8192;          // W3^T [16 rows][k = h2], rows >=
 constexpr uint32_t oB5 = oB3 + 2048;          // W1 [32 rows feature][k = z1]
 constexpr uint32_t oB6 = oB5 + 4096;          // [W3 | W3] [64 rows n][k: 0-3, 4-7 = W3[n][0..3], 8-15 zero]
 constexpr uint32_t oGO = oB6 + 8192;          // g_o tile [128 rows][k: 0-3 hi, 4-7 lo, 8-15 zero]
-constexpr uint32_t oStage = oGO + kTileBytes; // two record stages
-constexpr uint32_t kStFeat = 0;
-constexpr uint32_t kStGeom = kStFeat + (uint32_t)kRecFeatBytes;
-constexpr uint32_t kStDpart = kStGeom + 4 * kGeomFloats;
-constexpr uint32_t kStageBytes = kStDpart + 2 * 4 * 16;
+// Record stages 0, 1: the feature tile X (64-byte swizzle, the A operand of
+// layer 1 and the MN-major B operand of dW1), then geometry + chunk adjoints.
+constexpr uint32_t oXs = oGO + kTileBytes;
+constexpr uint32_t kXBytes = (uint32_t)kRecFeatBytes;
+constexpr uint32_t oGeo = oXs + 2 * kXBytes;
+constexpr uint32_t kGeoBytes = 4 * kGeomFloats;
+constexpr uint32_t kGeoStage = kGeoBytes + 2 * 4 * 16;  // + 4 chunks x 2 float4
+constexpr uint32_t kStageTx = kXBytes + kGeoStage;      // bytes per stage fill
 // Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][128 rows]
 // (row-contiguous, so both roles access it without bank conflicts), u as
 // float [3][128], then int32 n_valid[4] and the region.
-constexpr uint32_t oHand = oStage + 2 * kStageBytes;
+constexpr uint32_t oHand = oGeo + 2 * kGeoStage;
 constexpr uint32_t kHdDf = 0, kHdU = 16384, kHdNv = kHdU + 3 * 4 * kRows, kHdRegion = kHdNv + 16;
 constexpr uint32_t kHandBytes = kHdRegion + 16;
-constexpr uint32_t oMisc = oHand + 2 * kHandBytes;  // 7 mbarriers, TMEM base, abort flag
-constexpr uint32_t oBase = oMisc + 64;              // int32 base[K+1]
+constexpr uint32_t oMisc = oHand + 2 * kHandBytes;  // 8 mbarriers, TMEM base, abort flag
+constexpr uint32_t oBase = oMisc + 128;             // int32 base[K+1]
 constexpr size_t kSmemFixed = oBase + 1024;
-static_assert(kStGeom % 16 == 0 && kStDpart % 16 == 0 && kStageBytes % 16 == 0, "bulk copies need 16 B");
-static_assert(oStage % 1024 == 0 && oHand % 16 == 0 && kHandBytes % 16 == 0 && oMisc % 8 == 0, "alignment");
+static_assert(oXs % 1024 == 0 && kXBytes % 1024 == 0, "X tiles must keep the swizzle phase");
+static_assert(kGeoBytes % 16 == 0 && kGeoStage % 16 == 0 && oGeo % 16 == 0, "bulk copies need 16 B");
+static_assert(oHand % 16 == 0 && kHandBytes % 16 == 0 && oMisc % 8 == 0, "alignment");
 
 struct BwdTcParams {
   const void* mlp;  // 16-bit [K][kMlpParams]
@@ -135,37 +140,53 @@ __device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int 
   }
 }
 
-// Scatter dL/dfeat of levels l0..l0+3 (g8, level order) into the region's
-// FP32 gradient table.
-__device__ __forceinline__ void scatter4(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l0,
-                                         const float g8[8]) {
+// Scatter dL/dfeat of level l (g0, g1: its two features) into the region's
+// FP32 gradient table: the sample's 8 corners with trilinear weights (the
+// cells and weights of the forward's gather, same arithmetic). The corners of
+// an x-pair (x, x+1) go out as one 16-byte atomic on the aligned entry pair
+// holding the first corner (zero in the other half unless the second corner
+// is that pair's other entry) plus, when it is not, one 8-byte atomic.
+__device__ __forceinline__ void scatter_level(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
+                                              int l, float g0, float g1) {
+  int c[3];
+  float f[3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int l = l0 + q;
-    if (l >= lp.L) break;
-    int c[3];
-    float f[3];
+  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  float2* gl = gtab + lp.off[l];
+  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+  const float wx0 = 1.0f - f[0], wx1 = f[0];
+  // index of corner (x, y + dy, z + dz) = x + yz[dy + 2 dz] (dense), x ^ yz[..] (hashed)
+  uint32_t yz[4];
+  const bool dense = (lp.dense_mask >> l) & 1u;
+  if (dense) {
+    const uint32_t side = (uint32_t)lp.N[l] + 1u;
+    const uint32_t b = (uint32_t)c[1] * side + (uint32_t)c[2] * side * side;
+    yz[0] = b;
+    yz[1] = b + side;
+    yz[2] = b + side * side;
+    yz[3] = b + side + side * side;
+  } else {
+    const uint32_t hy0 = (uint32_t)c[1] * kHashPrime2, hy1 = hy0 + kHashPrime2;
+    const uint32_t hz0 = (uint32_t)c[2] * kHashPrime3, hz1 = hz0 + kHashPrime3;
+    yz[0] = hy0 ^ hz0;
+    yz[1] = hy1 ^ hz0;
+    yz[2] = hy0 ^ hz1;
+    yz[3] = hy1 ^ hz1;
+  }
+  const uint32_t x0 = (uint32_t)c[0];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-    float2* gl = gtab + lp.off[l];
-    const float g0 = g8[2 * q], g1 = g8[2 * q + 1];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-      const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-      const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
-      if ((i0 ^ i1) == 1u) {
-        const bool odd = i0 & 1u;
-        const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
-                             : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
-        atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
-      } else {
-        atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
-        atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
-      }
-    }
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t i0 = dense ? x0 + yz[e] : ((x0 ^ yz[e]) & lp.hash_mask);
+    const uint32_t i1 = dense ? i0 + 1u : (((x0 + 1u) ^ yz[e]) & lp.hash_mask);
+    const float wyz = wy[e & 1] * wz[e >> 1];
+    const float w0 = wx0 * wyz, w1 = wx1 * wyz;
+    const float a0 = w0 * g0, a1 = w0 * g1, b0 = w1 * g0, b1 = w1 * g1;
+    const bool pair = (i0 ^ i1) == 1u;  // both corners in the aligned pair of i0
+    const bool odd = i0 & 1u;
+    const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
+    atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
+              odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1));
+    if (!pair) atomicAdd(gl + i1, make_float2(b0, b1));
   }
 }
 
@@ -207,10 +228,10 @@ __device__ __forceinline__ void store16_hilo(uint32_t tile, uint32_t tile_lo, ui
 
 // Bounded wait of the compute warps for the MMAs committed so far; false on
 // timeout (all compute threads agree).
-__device__ __forceinline__ bool mma_wait(uint64_t* mbar, uint32_t& phase) {
+__device__ __forceinline__ bool mma_wait(uint64_t* mbar, uint32_t& phase, bool ok_before = true) {
   const bool ok = tc::mbar_wait_bounded(mbar, phase, kSpin);
   phase ^= 1;
-  return !tc::bar_or(kBarCompute, kGroup, !ok);
+  return !tc::bar_or(kBarCompute, kGroup, !ok || !ok_before);
 }
 __device__ __forceinline__ void compute_sync() { tc::bar_sync(kBarCompute, kGroup); }
 
@@ -223,8 +244,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
   uint64_t* full = mbar + 1;                                  // record stages 0, 1
   uint64_t* hfull = mbar + 3;                                 // hand-off slots 0, 1 written
   uint64_t* hempty = mbar + 5;                                // hand-off slots 0, 1 read
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMisc + 56);
-  volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(sm + oMisc + 60);
+  uint64_t* drain = mbar + 7;                                 // error path: all MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMisc + 64);
+  volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(sm + oMisc + 68);
   int32_t* s_base = reinterpret_cast<int32_t*>(sm + oBase);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
 
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
   for (int i = tid; i < (int)(kTileBytes / 16); i += blockDim.x) tc::st_shared_v4(sb + oGO + 16 * i, 0u, 0u, 0u, 0u);
   if (warp == 0) tc::tmem_alloc(tmem_slot, kCols);
   if (tid == 0) {
-    for (int i = 0; i < 7; ++i) tc::mbar_init(mbar + i, 1);
+    for (int i = 0; i < 8; ++i) tc::mbar_init(mbar + i, 1);
     *s_abort = 0;
   }
   tc::fence_before_sync();
@@ -273,8 +295,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       if (tid == kGroup) tc::mbar_arrive(hempty + b);
       if (lane < n_valid) {
         float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-        scatter4(p.lp, gtab, u, 8 * g, g16);
-        scatter4(p.lp, gtab, u, 8 * g + 4, g16 + 8);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (8 * g + j < p.lp.L) scatter_level(p.lp, gtab, u, 8 * g + j, g16[2 * j], g16[2 * j + 1]);
       }
     }
   } else {
@@ -287,22 +310,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
     constexpr uint32_t id16 = tc::idesc_f16(BF16, kRows, 16);
     constexpr uint32_t id64_bt = tc::idesc_f16(BF16, kRows, 64) | tc::kMnMajorB;
     constexpr uint32_t id16_abt = tc::idesc_f16(BF16, kRows, 16) | tc::kMnMajorA | tc::kMnMajorB;
-    constexpr uint32_t id96_abt = tc::idesc_f16(BF16, kRows, 96) | tc::kMnMajorA | tc::kMnMajorB;
+    constexpr uint32_t id64_abt = tc::idesc_f16(BF16, kRows, 64) | tc::kMnMajorA | tc::kMnMajorB;
+    constexpr uint32_t id32_abt = tc::idesc_f16(BF16, kRows, 32) | tc::kMnMajorA | tc::kMnMajorB;
 
-    // Thread 0 issues the record copies; pend[s] = iteration whose records
-    // are in flight into stage s (-1: none).
+    // Thread kCopier issues the record copies (thread 0 issues the MMAs);
+    // pend[s] = iteration whose records are in flight into stage s (-1: none).
+    constexpr int kCopier = kWarp;
     int pend[2] = {-1, -1};
     auto issue = [&](int it, int t) {
       const int s = it & 1;
       tc::fence_proxy_async();  // order earlier generic reads of the stage before the overwrite
-      tc::mbar_expect_tx(full + s, kStageBytes);
-      const uint32_t dst = sb + oStage + (uint32_t)s * kStageBytes;
-      tc::bulk_g2s(dst + kStFeat, p.rec_feat + (size_t)t * kRecFeatBytes, (uint32_t)kRecFeatBytes, full + s);
-      tc::bulk_g2s(dst + kStGeom, p.rec_geom + (size_t)t * 4 * kGeomFloats, 4 * kGeomFloats, full + s);
-      tc::bulk_g2s(dst + kStDpart, p.rec_dpart + (size_t)t * 128, 128, full + s);
+      tc::mbar_expect_tx(full + s, kStageTx);
+      const uint32_t geo = sb + oGeo + (uint32_t)s * kGeoStage;
+      tc::bulk_g2s(sb + oXs + (uint32_t)s * kXBytes, p.rec_feat + (size_t)t * kXBytes, kXBytes, full + s);
+      tc::bulk_g2s(geo, p.rec_geom + (size_t)t * kGeoBytes, kGeoBytes, full + s);
+      tc::bulk_g2s(geo + kGeoBytes, p.rec_dpart + (size_t)t * 128, 128, full + s);
       pend[s] = it;
     };
-    if (tid == 0 && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
+    if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
 
     int region = -1;
     uint32_t phase = 0;
@@ -343,48 +368,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       const int s = it & 1;
       const int k = region_of_chunk(s_base, p.K, t * kTileChunks);
       if (k != region) {
-        tc::fence_before_sync();
-        compute_sync();
-        if (region >= 0) flush();
+        if (dw_started) {  // the last tile's weight-gradient MMAs are not waited on per tile
+          if (tid == 0) tc::mma_commit(mbar);
+          if (!mma_wait(mbar, phase)) {
+            failed = true;
+            break;
+          }
+          flush();
+        }
         tc::fence_before_sync();
         compute_sync();
         load_weights_bwd<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm, tid, kGroup);
         region = k;
       }
-      if (tid == 0 && t + G < n_sub) issue(it + 1, t + G);
-      {
-        const bool ok = tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpin);
-        if (tc::bar_or(kBarCompute, kGroup, !ok)) {
-          failed = true;
-          break;
-        }
-        if (tid == 0) pend[s] = -1;
-      }
+      const bool staged = tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpin);
       // ---- this tile's records
-      const char* st = sm + oStage + (uint32_t)s * kStageBytes;
-      const float* geo = reinterpret_cast<const float*>(st + kStGeom);
-      const int n_valid = reinterpret_cast<const int32_t*>(geo)[5 * kRows + q];
+      const uint32_t xs = sb + oXs + (uint32_t)s * kXBytes;
+      const char* gst = sm + oGeo + (uint32_t)s * kGeoStage;
+      const float* geo = reinterpret_cast<const float*>(gst);
+      const int n_valid = reinterpret_cast<const int32_t*>(geo)[kGeomRowFields * kRows + q];
       const bool valid = lane < n_valid;
-      const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {  // X chunks 2g, 2g+1 (levels 8g..8g+7)
-        const uint32_t c = (uint32_t)(2 * g + h);
-        const uint4 fx = tc::ld_shared_v4(tc::smem_u32(st + kStFeat) + (((uint32_t)q * 4 + c) * kWarp + lane) * 16);
-        tc::st_shared_v4(sb + oX + tc::sw128_chunk(row, c), fx.x, fx.y, fx.z, fx.w);
-      }
-      tc::fence_proxy_async();
-      tc::fence_before_sync();
-      compute_sync();
       // ---- forward recompute: D1 = X W1
-      if (tid == 0) {
+      if (tid == 0 && staged) {
         tc::fence_after_sync();
         for (int kk = 0; kk < 2; ++kk)
-          tc::mma_f16(tmem, tc::desc_sw128(sb + oX + 32 * kk), tc::desc_sw128(sb + oB1 + 32 * kk), id64, kk);
-        tc::mma_commit(mbar);
+          tc::mma_f16(tmem, tc::desc_sw64(xs + 32 * kk, 16), tc::desc_sw128(sb + oB1 + 32 * kk), id64, kk);
+        tc::mma_commit(mbar);  // also tracks the previous tile's weight-gradient MMAs
       }
-      if (!mma_wait(mbar, phase)) {
+      if (!mma_wait(mbar, phase, staged)) {
         failed = true;
         break;
+      }
+      if (tid == kCopier) {
+        pend[s] = -1;
+        // stage s ^ 1 held the previous tile, whose MMAs have all completed
+        if (t + G < n_sub) issue(it + 1, t + G);
       }
       tc::fence_after_sync();
       float v[16];
@@ -437,21 +455,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         tc::tmem_ld_wait();
         float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (n_valid > 0) {
-          const float4 a0 = *reinterpret_cast<const float4*>(st + kStDpart + 32 * q);
-          const float4 a1 = *reinterpret_cast<const float4*>(st + kStDpart + 32 * q + 16);
+          const float4 a0 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q);
+          const float4 a1 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q + 16);
           const float gC[3] = {a0.y, a0.z, a0.w};
+          const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
+          const float Tn = geo[5 * kRows + row], w = geo[6 * kRows + row], pair = geo[7 * kRows + row];
           float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
           if (valid) {
             sigma = expf(v[0]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
           }
-          float g_sigma, g_rgb[3];
-          render_chunk_adjoint(sigma, rgb, tr, dl, lane, a0.x, gC, a1.x, a1.y, a1.z, g_sigma, g_rgb);
+          float g_tau;
+          render_chunk_adjoint_kept(gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2], tr, dl, Tn, w, pair, lane, a0.x,
+                                    a1.x, a1.y, a1.z, g_tau);
           if (valid) {
-            go[0] = g_sigma * sigma;
+            go[0] = g_tau * dl * sigma;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) go[1 + j] = g_rgb[j] * rgb[j] * (1.0f - rgb[j]);
+            for (int j = 0; j < 3; ++j) go[1 + j] = w * gC[j] * rgb[j] * (1.0f - rgb[j]);
           }
         }
         const uint32_t h01 = Half2Of<BF16>::pack(go[0], go[1]), h23 = Half2Of<BF16>::pack(go[2], go[3]);
@@ -470,10 +491,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       if (tid == 0) {
         tc::fence_after_sync();
         tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oGO), tc::desc_sw128(sb + oB6), id64, 0u);
+        tc::mma_commit(mbar);
+        // DW3 is only read at the region flush: not waited on here (H2 and
+        // the g_o tile are next written after later commits have completed)
         for (int kk = 0; kk < 8; ++kk)
           tc::mma_f16(tmem + kDw3Col, tc::desc_sw128_mn(sb + oH2 + 2048 * kk, kTileBytes),
                       tc::desc_sw128_mn(sb + oGO + 2048 * kk, 1024), id16_abt, (acc_on || kk > 0) ? 1u : 0u);
-        tc::mma_commit(mbar);
       }
       if (!mma_wait(mbar, phase)) {
         failed = true;
@@ -528,10 +551,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
           tc::mma_f16(tmem, tc::desc_sw128(sb + oG1 + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, kk);
         for (int kk = 0; kk < 4; ++kk)
           tc::mma_f16(tmem, tc::desc_sw128(sb + oG1l + 32 * kk), tc::desc_sw128(sb + oB5 + 32 * kk), id32, 1);
-        for (int kk = 0; kk < 8; ++kk)
-          tc::mma_f16(tmem + kDwCol, tc::desc_sw128_mn(sb + oG2 + 2048 * kk, kTileBytes),
-                      tc::desc_sw128_mn(sb + oH1 + 2048 * kk, kTileBytes), id96_abt, (acc_on || kk > 0) ? 1u : 0u);
         tc::mma_commit(mbar);
+        // DW likewise runs behind the next tile: its operands (G2, G1, H1 and
+        // this stage's X) are next overwritten only after the next tile's
+        // first commit, which tracks these MMAs, has completed.
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint64_t a = tc::desc_sw128_mn(sb + oG2 + 2048 * kk, kTileBytes);
+          const uint32_t acc = (acc_on || kk > 0) ? 1u : 0u;
+          tc::mma_f16(tmem + kDwCol, a, tc::desc_sw128_mn(sb + oH1 + 2048 * kk, 1024), id64_abt, acc);
+          tc::mma_f16(tmem + kDwCol + 64, a, tc::desc_sw64(xs + 1024 * kk, 512), id32_abt, acc);
+        }
       }
       dw_started = true;
       if (!mma_wait(mbar, phase)) {
@@ -565,18 +594,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       compute_sync();  // slot written; tiles, stage and TMEM free for the next tile
       if (tid == 0) tc::mbar_arrive(hfull + b);
     }
-    if (!failed && region >= 0) {
-      tc::fence_before_sync();
-      compute_sync();
-      flush();
+    if (!failed && dw_started) {
+      if (tid == 0) tc::mma_commit(mbar);  // drain the last weight-gradient MMAs
+      if (mma_wait(mbar, phase)) flush();
+      else failed = true;
     }
     if (failed && tid == 0) {
       atomicOr(p.err, kErrTimeout);
       *s_abort = 1;  // wake the scatter warps; they see the flag and stop
       tc::mbar_arrive(hfull);
       tc::mbar_arrive(hfull + 1);
-      // let MMAs and record copies still in flight land before the CTA exits
-      tc::mbar_wait_bounded(mbar, phase ^ 1u, kSpin);  // the phase a timed-out MMA wait was on
+      // let MMAs still in flight land before the CTA exits
+      tc::mma_commit(drain);
+      tc::mbar_wait_bounded(drain, 0u, kSpin);
+    }
+    if (failed && tid == kCopier) {  // and the record copies
       for (int s = 0; s < 2; ++s)
         if (pend[s] >= 0) tc::mbar_wait_bounded(full + s, (uint32_t)(pend[s] >> 1) & 1u, kSpin);
     }

@@ -209,8 +209,12 @@ struct Partial {
 };
 
 // Region-local volume rendering of one 32-sample chunk by one warp
-// (Eq. 1-2 restricted to the chunk, transmittance restarting at 1).
-__device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3], float tr, float dl, int lane) {
+// (Eq. 1-2 restricted to the chunk, transmittance restarting at 1). If `keep`
+// is given, the lane also stores the quantities its adjoint reuses:
+// keep[0] = Tn (transmittance after the sample), keep[stride] = w,
+// keep[2 stride] = sum_j w_j |tr - tr_j| over the chunk.
+__device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3], float tr, float dl, int lane,
+                                                float* keep = nullptr, int stride = 0) {
   const float tau = sigma * dl;
   const float incl = warp_inclusive_scan(tau, lane);
   const float excl = warp_exclusive_from_inclusive(incl, lane);
@@ -221,6 +225,13 @@ __device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3],
   const float Wx = warp_exclusive_from_inclusive(warp_inclusive_scan(w, lane), lane);
   const float WTx = warp_exclusive_from_inclusive(warp_inclusive_scan(wt, lane), lane);
   const float l = 2.0f * w * (tr * Wx - WTx) + w * w * dl * (1.0f / 3.0f);
+  if (keep) {
+    const float W_gt = warp_suffix_scan(w, lane) - w;
+    const float WT_gt = warp_suffix_scan(wt, lane) - wt;
+    keep[0] = expf(-incl);
+    keep[stride] = w;
+    keep[2 * stride] = (tr * Wx - WTx) + (WT_gt - tr * W_gt);
+  }
   Partial p;
   p.tau = __shfl_sync(0xFFFFFFFFu, incl, 31);
   p.c0 = warp_sum(w * rgb[0]);
@@ -321,6 +332,17 @@ __device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rg
   g_sigma = g_tau * dl;
 #pragma unroll
   for (int q = 0; q < 3; ++q) g_rgb[q] = w * gC[q];
+}
+
+// Adjoint of the chunk-local render from the forward's kept Tn, w and pair
+// (see render_chunk): one suffix scan instead of the recomputed prefix sums.
+__device__ __forceinline__ void render_chunk_adjoint_kept(float rgb_dot_gC, float tr, float dl, float Tn, float w,
+                                                          float pair, int lane, float gtc, float gA, float gD, float gL,
+                                                          float& g_tau) {
+  const float gw = rgb_dot_gC + gA + gD * tr + gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
+  const float gww = gw * w;
+  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
+  g_tau = gtc + gw * Tn - later;
 }
 
 // Stage region k's 16-bit MLP block into shared memory as FP32 (same

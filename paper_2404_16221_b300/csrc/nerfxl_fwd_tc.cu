@@ -265,19 +265,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       // Records for the backward: the features exactly as the first MMA reads
       // them, the sample's region coordinates / position / length (thread g
       // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
-      // count, and the chunk's tile-order position for the composite adjoint.
+      // count, and the chunk's tile-order position for the composite adjoint
+      // (Tn, w and pair follow from the chunk render below).
       const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      p.rec.feat[((size_t)(t * kTcChunks + q) * 4 + g) * kWarp + lane] = pk;
+      p.rec.feat[(size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u))] = pk;
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
       geo[g * kTcRows + row] = g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr));
       if (g == 0) {
         geo[4 * kTcRows + row] = dl;
         if (lane == 0) {
           const int n_valid = chunk_ok ? min(kWarp, seg_n(sd) - c * kWarp) : 0;
-          reinterpret_cast<int32_t*>(geo)[5 * kTcRows + q] = n_valid;
+          reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] = n_valid;
           if (chunk_ok) p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = t * kTcChunks + q;
         }
       }
@@ -358,7 +359,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 #pragma unroll
           for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j] * scale[2]));
         }
-        const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
+        const Partial pt = render_chunk(sigma, rgb, tr, dl, lane,
+                                        p.rec.geom ? p.rec.geom + (size_t)t * kGeomFloats + 5 * kTcRows + row : nullptr,
+                                        kTcRows);
         if (lane == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
           dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);

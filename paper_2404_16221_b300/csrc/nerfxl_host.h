@@ -23,8 +23,8 @@ struct Layout {
   size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
   // Per-tile records of the tensor-core backward (backward workspaces with a
   // 16-bit MLP only; 0 otherwise). A tile is 4 chunks = 128 sample rows.
-  size_t rec_feat;   // uint4[tiles][4 chunks][4 level groups][32 lanes]: 16-bit features
-  size_t rec_geom;   // float[tiles][kGeomFloats]: u0, u1, u2, tr, dl per row; samples per chunk
+  size_t rec_feat;   // [tiles][128 rows][64 B]: 16-bit features, 64-byte-swizzled MMA tile
+  size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl Tn w pair; samples per chunk
   size_t rec_dpart;  // float4[tiles * 4][2]: chunk adjoints in tile order
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
   size_t total;
@@ -52,11 +52,18 @@ int fwd_grid(int64_t max_tiles, int ctas_per_sm);
 nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
                               const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,
                               const int64_t* out_index, void* workspace, size_t ws_bytes, cudaStream_t stream);
-// Record geometry block of one tile: rows' u0, u1, u2, tr, dl (128 floats
-// each), then the valid-sample count of each of the 4 chunks (int32).
+// Records of one 128-row tile for the tensor-core backward.
+//   features  row r's 32 16-bit features as the K-major A operand of the first
+//             MMA in the 64-byte swizzle: 16-byte chunk c of row r at byte
+//             64 r + 16 (c ^ ((r / 2) % 4)).
+//   geometry  128 floats each of u0, u1, u2 (region coordinates), tr (tbar - tn),
+//             dl (interval length), Tn (transmittance after the sample within its
+//             chunk), w (chunk-local weight), pair (sum over the chunk of
+//             w_j |tr_i - tr_j|); then the valid-sample count of each chunk (int32).
 constexpr int kRecRows = 128;
-constexpr int kGeomFloats = 5 * kRecRows + 4;  // 2576 bytes, a multiple of 16
-constexpr size_t kRecFeatBytes = (size_t)kRecRows * 64;  // 8192 bytes per tile
+constexpr int kGeomRowFields = 8;
+constexpr int kGeomFloats = kGeomRowFields * kRecRows + 4;  // 4112 bytes, a multiple of 16
+constexpr size_t kRecFeatBytes = (size_t)kRecRows * 64;     // 8192 bytes per tile
 
 // Where the tensor-core forward writes the backward's records (all NULL for a
 // plain forward).

@@ -58,6 +58,21 @@ __device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t smem_addr, uint32_t a
   return d;
 }
 
+// Descriptor of a 64-byte-swizzled operand: rows of 64 bytes (32 16-bit
+// elements), 16-byte chunk c of row r stored at chunk slot c ^ ((r / 2) % 4),
+// 8-row groups 512 bytes apart. K-major: rows are M (or N) and the K step
+// advances the start by 32 bytes; MN-major: rows are K and `atom_stride` is
+// the distance to elements 32..63 of M or N.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t smem_addr, uint32_t atom_stride) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((atom_stride >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
 // Instruction-descriptor bits selecting MN-major ("transposed") A and B.
 constexpr uint32_t kMnMajorA = 1u << 15;
 constexpr uint32_t kMnMajorB = 1u << 16;

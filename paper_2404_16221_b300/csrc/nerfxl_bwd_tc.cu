@@ -155,29 +155,16 @@ __device__ __forceinline__ void scatter_level(const LevelParams& lp, float2* __r
   float2* gl = gtab + lp.off[l];
   const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
   const float wx0 = 1.0f - f[0], wx1 = f[0];
-  // index of corner (x, y + dy, z + dz) = x + yz[dy + 2 dz] (dense), x ^ yz[..] (hashed)
-  uint32_t yz[4];
+  // Both index forms are formed and selected per corner (measured faster here
+  // than branching per level).
   const bool dense = (lp.dense_mask >> l) & 1u;
-  if (dense) {
-    const uint32_t side = (uint32_t)lp.N[l] + 1u;
-    const uint32_t b = (uint32_t)c[1] * side + (uint32_t)c[2] * side * side;
-    yz[0] = b;
-    yz[1] = b + side;
-    yz[2] = b + side * side;
-    yz[3] = b + side + side * side;
-  } else {
-    const uint32_t hy0 = (uint32_t)c[1] * kHashPrime2, hy1 = hy0 + kHashPrime2;
-    const uint32_t hz0 = (uint32_t)c[2] * kHashPrime3, hz1 = hz0 + kHashPrime3;
-    yz[0] = hy0 ^ hz0;
-    yz[1] = hy1 ^ hz0;
-    yz[2] = hy0 ^ hz1;
-    yz[3] = hy1 ^ hz1;
-  }
+  const LevelIndex<true> dix(lp, l, c[1], c[2]);
+  const LevelIndex<false> hix(lp, l, c[1], c[2]);
   const uint32_t x0 = (uint32_t)c[0];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const uint32_t i0 = dense ? x0 + yz[e] : ((x0 ^ yz[e]) & lp.hash_mask);
-    const uint32_t i1 = dense ? i0 + 1u : (((x0 + 1u) ^ yz[e]) & lp.hash_mask);
+    const uint32_t i0 = dense ? dix(x0, e) : hix(x0, e);
+    const uint32_t i1 = dense ? i0 + 1u : hix(x0 + 1u, e);
     const float wyz = wy[e & 1] * wz[e >> 1];
     const float w0 = wx0 * wyz, w1 = wx1 * wyz;
     const float a0 = w0 * g0, a1 = w0 * g1, b0 = w1 * g0, b1 = w1 * g1;
@@ -379,6 +366,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         tc::fence_before_sync();
         compute_sync();
         load_weights_bwd<BF16>(static_cast<const uint16_t*>(p.mlp) + (size_t)k * kMlpParams, sm, tid, kGroup);
+        // the weight tiles are complete and visible to the tensor core before
+        // this tile's first MMA
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        compute_sync();
         region = k;
       }
       const bool staged = tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpin);

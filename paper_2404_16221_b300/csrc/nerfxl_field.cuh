@@ -59,49 +59,111 @@ __device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* 
   }
 }
 
+// Corner indices of one level, set up once per cell and shared by its four
+// x-pairs: corner (x, y + dy, z + dz) has index x + yz[dy + 2 dz] on a dense
+// level and (x ^ yz[dy + 2 dz]) & mask on a hashed one.
+template <bool kDense>
+struct LevelIndex {
+  uint32_t yz[4];
+  uint32_t mask;
+  __device__ LevelIndex(const LevelParams& lp, int l, int cy, int cz) {
+    if (kDense) {
+      const uint32_t side = (uint32_t)lp.N[l] + 1u;
+      const uint32_t b = (uint32_t)cy * side + (uint32_t)cz * side * side;
+      yz[0] = b;
+      yz[1] = b + side;
+      yz[2] = b + side * side;
+      yz[3] = b + side + side * side;
+    } else {
+      const uint32_t hy0 = (uint32_t)cy * kHashPrime2, hy1 = hy0 + kHashPrime2;
+      const uint32_t hz0 = (uint32_t)cz * kHashPrime3, hz1 = hz0 + kHashPrime3;
+      yz[0] = hy0 ^ hz0;
+      yz[1] = hy1 ^ hz0;
+      yz[2] = hy0 ^ hz1;
+      yz[3] = hy1 ^ hz1;
+    }
+    mask = lp.hash_mask;
+  }
+  __device__ uint32_t operator()(uint32_t x, int e) const { return kDense ? x + yz[e] : ((x ^ yz[e]) & mask); }
+};
+
+// Pair loads of the gather: the aligned entry pair holding a corner (first =
+// the corner's own entry, second = the other entry of the pair), and one
+// entry, as float2 features. The 16-bit form picks the 32-bit word before
+// converting it.
+template <typename TabT>
+struct PairLoad;
+template <>
+struct PairLoad<float2> {
+  using P = float4;
+  __device__ static P pair(const float2* t, uint32_t i) { return __ldg(reinterpret_cast<const float4*>(t + (i & ~1u))); }
+  __device__ static float2 first(const P& v, bool odd) { return odd ? make_float2(v.z, v.w) : make_float2(v.x, v.y); }
+  __device__ static float2 second(const P& v, bool odd) { return odd ? make_float2(v.x, v.y) : make_float2(v.z, v.w); }
+  __device__ static float2 one(const float2* t, uint32_t i) { return __ldg(t + i); }
+};
+template <>
+struct PairLoad<__half2> {
+  using P = uint2;
+  __device__ static P pair(const __half2* t, uint32_t i) { return __ldg(reinterpret_cast<const uint2*>(t + (i & ~1u))); }
+  __device__ static float2 cvt(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
+  __device__ static float2 first(const P& v, bool odd) { return cvt(odd ? v.y : v.x); }
+  __device__ static float2 second(const P& v, bool odd) { return cvt(odd ? v.x : v.y); }
+  __device__ static float2 one(const __half2* t, uint32_t i) { return __half22float2(__ldg(t + i)); }
+};
+
+// One level's trilinear gather (F = 2) at cell c, fractions f.
+template <bool kDense, typename TabT>
+__device__ __forceinline__ float2 gather_level(const LevelParams& lp, const TabT* __restrict__ tl, int l, const int c[3],
+                                               const float f[3]) {
+  using LD = PairLoad<TabT>;
+  const LevelIndex<kDense> ix(lp, l, c[1], c[2]);
+  const uint32_t x0 = (uint32_t)c[0];
+  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+  float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t i0 = ix(x0, e), i1 = ix(x0 + 1u, e);
+    const typename LD::P pv = LD::pair(tl, i0);
+    const bool odd = i0 & 1u;
+    const float2 v0 = LD::first(pv, odd);
+    float2 v1;
+    if ((i0 ^ i1) == 1u) v1 = LD::second(pv, odd);
+    else v1 = LD::one(tl, i1);
+    const float wyz = wy[e & 1] * wz[e >> 1];
+    const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+    s0 = fmaf(w0, v0.x, s0);
+    s1 = fmaf(w0, v0.y, s1);
+    s0 = fmaf(w1, v1.x, s0);
+    s1 = fmaf(w1, v1.y, s1);
+  }
+  return make_float2(s0, s1);
+}
+
 // Gather of four consecutive levels l0..l0+3 (F = 2) of one sample: out[8]
 // holds their features in level order; levels >= L give zeros.
 template <typename TabT>
 __device__ __forceinline__ void gather4(const LevelParams& lp, const TabT* __restrict__ table, const float u[3], int l0,
-                                        float out[8]);
-
-template <>
-__device__ __forceinline__ void gather4<float2>(const LevelParams& lp, const float2* __restrict__ table,
-                                                const float u[3], int l0, float out[8]) {
+                                        float out[8]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int l = l0 + q;
-    float s0 = 0.0f, s1 = 0.0f;
+    float2 s = make_float2(0.0f, 0.0f);
     if (l < lp.L) {
       int c[3];
       float f[3];
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-      const float2* tl = table + lp.off[l];
-#pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-        const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-        const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-        const float4 qv = __ldg(reinterpret_cast<const float4*>(tl + (i0 & ~1u)));
-        const bool odd = i0 & 1u;
-        const float2 v0 = odd ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
-        float2 v1;
-        if ((i0 ^ i1) == 1u) v1 = odd ? make_float2(qv.x, qv.y) : make_float2(qv.z, qv.w);
-        else v1 = __ldg(tl + i1);
-        const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-        const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
-        s0 = fmaf(w0, v0.x, s0);
-        s1 = fmaf(w0, v0.y, s1);
-        s0 = fmaf(w1, v1.x, s0);
-        s1 = fmaf(w1, v1.y, s1);
-      }
+      const TabT* tl = table + lp.off[l];
+      if ((lp.dense_mask >> l) & 1u) s = gather_level<true>(lp, tl, l, c, f);
+      else s = gather_level<false>(lp, tl, l, c, f);
     }
-    out[2 * q] = s0;
-    out[2 * q + 1] = s1;
+    out[2 * q] = s.x;
+    out[2 * q + 1] = s.y;
   }
 }
 
+// FP16 tables: per-corner index arithmetic, which schedules better than the
+// per-cell form above for 4-byte entries.
 template <>
 __device__ __forceinline__ void gather4<__half2>(const LevelParams& lp, const __half2* __restrict__ table,
                                                  const float u[3], int l0, float out[8]) {
@@ -139,6 +201,7 @@ __device__ __forceinline__ void gather4<__half2>(const LevelParams& lp, const __
     out[2 * q + 1] = s1;
   }
 }
+
 
 // MLP with weights staged in shared memory as W1t [64][32] (row n holds
 // column n of W1), W2t [64][64], W3 [64][4]. Layer 2 and 3 are fused per

@@ -173,7 +173,7 @@ struct FwdTcParams {
   int32_t* err;
 };
 
-template <bool kF16Table, int kKind>
+template <bool kF16Table, int kKind, bool kRec>
 __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   using Op = MlpOp<kKind>;
   extern __shared__ __align__(1024) char s_raw[];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       }
     }
     Op::store8(a0, row, g, f8);
-    if (kKind != kKindE4M3 && p.rec.feat) {
+    if (kRec) {
       // Records for the backward: the features exactly as the first MMA reads
       // them, the sample's region coordinates / position / length (thread g
       // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
           for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j] * scale[2]));
         }
         const Partial pt = render_chunk(sigma, rgb, tr, dl, lane,
-                                        p.rec.geom ? p.rec.geom + (size_t)t * kGeomFloats + 5 * kTcRows + row : nullptr,
+                                        kRec ? p.rec.geom + (size_t)t * kGeomFloats + 5 * kTcRows + row : nullptr,
                                         kTcRows);
         if (lane == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
@@ -404,13 +404,22 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   const int kind = f->mlp_dtype == NERFXL_BF16 ? kKindBF16 : (f->mlp_dtype == NERFXL_F16 ? kKindF16 : kKindE4M3);
   if (kind == kKindE4M3 && !f->mlp_scales) return set_error(NERFXL_E_INVALID, "E4M3 MLP needs mlp_scales");
   const bool f16tab = f->table_dtype == NERFXL_F16;
+  const bool recs = rec.feat != nullptr;
+  if (recs && kind == kKindE4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
   void (*kern)(FwdTcParams) = nullptr;
-  if (f16tab)
-    kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16>
-                             : (kind == kKindF16 ? k_field_fwd_tc<true, kKindF16> : k_field_fwd_tc<true, kKindE4M3>);
-  else
-    kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16>
-                             : (kind == kKindF16 ? k_field_fwd_tc<false, kKindF16> : k_field_fwd_tc<false, kKindE4M3>);
+  if (f16tab) {
+    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, true> : k_field_fwd_tc<true, kKindF16, true>;
+    else
+      kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, false>
+                               : (kind == kKindF16 ? k_field_fwd_tc<true, kKindF16, false>
+                                                   : k_field_fwd_tc<true, kKindE4M3, false>);
+  } else {
+    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, true> : k_field_fwd_tc<false, kKindF16, true>;
+    else
+      kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, false>
+                               : (kind == kKindF16 ? k_field_fwd_tc<false, kKindF16, false>
+                                                   : k_field_fwd_tc<false, kKindE4M3, false>);
+  }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_fwd_tc smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kTcChunks, 2);

@@ -268,3 +268,33 @@ def test_saved_features_backward_equals_recompute():
         grads.append((gt.cpu().numpy(), gm.cpu().numpy()))
     for a, b in zip(grads[0], grads[1]):
         assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+
+
+def test_mixed_backward_repeatable():
+    """Four mixed backward passes (fresh workspaces, with and without the
+    forward's records) agree up to the order of the FP32 atomic sums. A tile
+    whose MMA read a half-written weight tile or stage shows up here as a
+    percent-level difference."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 2048)
+    R = len(o)
+    g = sy.rng(29, "misc")
+    adj = [torch.from_numpy(a.astype(np.float32)).cuda() for a in
+           (g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R))]
+    runs = []
+    for flags in (0, api.SAVE_FEATURES, 0, api.SAVE_FEATURES):
+        gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+        samp = dataclasses.replace(H.sampling(w), flags=flags)
+        ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+        api.render_fwd(gf, samp, o, d, workspace=ws)
+        gt, gm = api.render_bwd(gf, samp, o, d, ws, *adj)
+        api.check(ws)
+        runs.append((gt.cpu().numpy(), gm.cpu().numpy()))
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()

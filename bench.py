@@ -221,11 +221,11 @@ def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
 # forward, then dX (12,800) and dW (12,800): 38,400 per sample.
 MLP_FWD_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 4)
 BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
-# Algorithmic bytes of the backward field kernel per sample (L=16 levels, F=2,
-# 8 corners) in the training mode that keeps the forward's features: the saved
-# 16-bit features (32 x 2 B = 64 B) and the read-modify-write of the FP32
-# gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
-TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 2 * 8 * 2 * 4 * 16
+# Algorithmic bytes of the tensor-core backward field kernel per sample (L=16
+# levels, F=2, 8 corners): its per-tile records (16-bit features 32 x 2 B,
+# geometry 8 x 4 B, chunk adjoints 32 B per 32 samples) and the read-modify-write
+# of the FP32 gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
+TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 8 * 4 + 1 + 2 * 8 * 2 * 4 * 16
 
 
 def serve_sweep(args, dev, rates):
@@ -456,8 +456,9 @@ def main():
         "gpu_launches": 11 * steps,
         "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "basis": "%d B/sample algorithmic (saved 16-bit features 64 B + FP32 gradient read-modify-write "
-                              "2048 B) x %d samples / mean kernel time %.3f ms (%s peak)"
+                     "basis": "%d B/sample algorithmic (records: 16-bit features 64 B + geometry 32 B + chunk "
+                              "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
+                              "%.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src)},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],

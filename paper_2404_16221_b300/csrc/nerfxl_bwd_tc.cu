@@ -5,7 +5,7 @@
 // tensor-core forward: every row's 16-bit features exactly as the forward's
 // first MMA read them (already laid out as that MMA's 64-byte-swizzled A
 // tile), its region coordinates u, position tr and length dl, the chunk-local
-// Tn, w and distortion pair sum of the forward's render, each chunk's sample
+// Tn, w, distortion pair sum, sigma and rgb of the forward's render, each chunk's sample
 // count, and (written by the composite backward) each chunk's partial
 // adjoints. One thread copies the next tile's records into a second
 // shared-memory stage with bulk asynchronous copies while the CTA works on the
@@ -20,25 +20,28 @@
 //   scatter warps 8-15  scatter the previous tile's dL/dfeatures, handed over
 //                       through a double-buffered shared-memory slot guarded
 //                       by full / empty mbarriers
-// Per tile, on the compute warps (FP32 accumulation in TMEM):
-//   recompute  D1 = X W1 -> H1 = relu -> D2 = H1 W2 -> H2 = relu -> D3 = H2 W3
-//   adjoint    chunk-local render adjoint from the kept Tn, w, pair (one warp
-//              suffix scan) -> g_o [128 x 4], stored
-//              as one 16-bit tile row [g_o hi | g_o lo | 0]
-//              G2 = (H2 > 0) * ([g_o hi | g_o lo] [W3 | W3]^T)  (one K = 16 MMA)
-//              D4 = G2 W2^T, G1 = (H1 > 0) * D4
-//              D5 = G1 W1^T = dL/dfeatures -> hand-off slot -> table
-//              scatter-add by the scatter warps (vector atomics)
-//              G2 and G1 enter these products as hi + lo pairs of 16-bit
-//              values (two MMAs each), keeping ~16 mantissa bits of the
-//              upstream gradient; the weights are exact in their 16-bit copy.
+// Per tile, on the compute warps (FP32 accumulation in TMEM, four MMA round
+// trips):
+//   1  D1 = X W1 (X straight from the record stage); meanwhile the chunk-local
+//      render adjoint from the kept Tn, w, pair, sigma, rgb (one warp suffix
+//      scan) -> g_o [128 x 4], stored as a 16-bit tile row [g_o hi | g_o lo | 0]
+//   2  H1 = relu(D1); [g_o hi | g_o lo] [W3 | W3]^T (one K = 16 MMA, the G2 of
+//      the next step before its mask); D2 = H1 W2
+//   3  H2 = relu(D2), G2 = (H2 > 0) * that product; D4 = G2 W2^T, G1 = (H1 > 0) * D4
+//   4  D5 = G1 W1^T = dL/dfeatures -> hand-off slot -> table scatter-add by the
+//      scatter warps (vector atomics)
+//   G2 and G1 enter the products as hi + lo pairs of 16-bit values (two MMAs
+//   each), keeping ~16 mantissa bits of the upstream gradient; the weights are
+//   exact in their 16-bit copy.
 //   weights    DW  += [G2 | G1]^T [H1 | X]        (M = 128, N = 64 + 32, K = 128 samples)
 //              DW3 += [H2 | H1]^T [g_o hi | g_o lo]  (M = 128, N = 16;
 //                                                     dW3 = columns 0-3 + 4-7)
 //              Both read the row-major activation tiles as MN-major operands
-//              (the samples are the contraction), accumulate in TMEM over all
-//              of a region's tiles and are flushed once per region: DW's
-//              diagonal blocks are dW2 and dW1, DW3's first 64 rows are dW3.
+//              (the samples are the contraction), run behind the next step
+//              (no wait: a later commit covers them before their operands are
+//              overwritten), accumulate in TMEM over all of a region's tiles
+//              and are flushed once per region: DW's diagonal blocks are dW2
+//              and dW1, DW3's first 64 rows are dW3.
 // Bounded waits flag kErrTimeout, wait (bounded) for copies still in flight,
 // free tensor memory and return.
 
@@ -57,8 +60,8 @@ constexpr int kThreads = 512;
 constexpr int kGroup = 256;  // threads per role
 constexpr int kBarCompute = 1, kBarScatter = 2;
 constexpr int kTileChunks = kRows / kWarp;
-constexpr uint32_t kCols = 256;  // 0-63 D1/D3/D5, 64-127 D2/D4, 128-223 DW, 224-239 DW3
-constexpr uint32_t kDwCol = 128, kDw3Col = 224;
+constexpr uint32_t kCols = 512;  // 0-63 D1/D5, 64-127 D2/D4, 128-223 DW, 224-239 DW3, 256-319 G2 before the mask
+constexpr uint32_t kDwCol = 128, kDw3Col = 224, kG2Col = 256;
 constexpr uint32_t kSpin = 1u << 24;
 
 // Shared-memory plan (bytes from a 1024-aligned base). Activation tiles are
@@ -73,8 +76,7 @@ constexpr uint32_t oG2l = oG1 + kTileBytes;   // G2 - hi (lo part)
 constexpr uint32_t oG1l = oG2l + kTileBytes;  // G1 lo
 constexpr uint32_t oB1 = oG1l + kTileBytes;   // W1^T [64 rows z1][k = feature < 32]  (layer 1)
 constexpr uint32_t oB2 = oB1 + 8192;          // W2^T [64 rows z2][k = h1] (layer 2; MN-major W2 for D4)
-constexpr uint32_t oB3 = oB2 + 8192;          // W3^T [16 rows][k = h2], rows >= 4 zero
-constexpr uint32_t oB5 = oB3 + 2048;          // W1 [32 rows feature][k = z1]
+constexpr uint32_t oB5 = oB2 + 8192;          // W1 [32 rows feature][k = z1]
 constexpr uint32_t oB6 = oB5 + 4096;          // [W3 | W3] [64 rows n][k: 0-3, 4-7 = W3[n][0..3], 8-15 zero]
 constexpr uint32_t oGO = oB6 + 8192;          // g_o tile [128 rows][k: 0-3 hi, 4-7 lo, 8-15 zero]
 // Record stages 0, 1: the feature tile X (64-byte swizzle, the A operand of
@@ -116,7 +118,6 @@ template <bool BF16>
 __device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int tid, int nthreads) {
   uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + oB1);
   uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + oB2);
-  uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + oB3);
   uint16_t* b5 = reinterpret_cast<uint16_t*>(sm + oB5);
   uint16_t* b6 = reinterpret_cast<uint16_t*>(sm + oB6);
   for (int i = tid; i < kIn * kWidth; i += nthreads) {
@@ -128,11 +129,6 @@ __device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int 
   for (int i = tid; i < kWidth * kWidth; i += nthreads) {
     const int a = i / kWidth, b = i % kWidth;  // W2[a][b]: h1 index a, z2 index b
     b2[tc::sw128_offset(b, a) >> 1] = Half2Of<BF16>::bits(blk, kIn * kWidth + i);
-  }
-  for (int i = tid; i < 16 * 64; i += nthreads) {
-    const int n = i / 64, k = i % 64;
-    b3[tc::sw128_offset(n, k) >> 1] =
-        n < kOut ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
   }
   for (int i = tid; i < kWidth * 16; i += nthreads) {
     const int n = i / 16, k = i % 16;  // W3[n][k % 4] for k < 8
@@ -171,9 +167,11 @@ __device__ __forceinline__ void scatter_level(const LevelParams& lp, float2* __r
     const bool pair = (i0 ^ i1) == 1u;  // both corners in the aligned pair of i0
     const bool odd = i0 & 1u;
     const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
-    atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
-              odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1));
-    if (!pair) atomicAdd(gl + i1, make_float2(b0, b1));
+    // evict-last: the region's gradient lines stay in L2 while its tiles run
+    const uint64_t pol = tc::policy_evict_last();
+    tc::red_add_v4(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
+                   odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1), pol);
+    if (!pair) tc::red_add_v2(gl + i1, make_float2(b0, b1), pol);
   }
 }
 
@@ -294,7 +292,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
     constexpr uint32_t id32 = tc::idesc_f16(BF16, kRows, 32);
     constexpr uint32_t id64 = tc::idesc_f16(BF16, kRows, 64);
-    constexpr uint32_t id16 = tc::idesc_f16(BF16, kRows, 16);
     constexpr uint32_t id64_bt = tc::idesc_f16(BF16, kRows, 64) | tc::kMnMajorB;
     constexpr uint32_t id16_abt = tc::idesc_f16(BF16, kRows, 16) | tc::kMnMajorA | tc::kMnMajorB;
     constexpr uint32_t id64_abt = tc::idesc_f16(BF16, kRows, 64) | tc::kMnMajorA | tc::kMnMajorB;
@@ -309,9 +306,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       tc::fence_proxy_async();  // order earlier generic reads of the stage before the overwrite
       tc::mbar_expect_tx(full + s, kStageTx);
       const uint32_t geo = sb + oGeo + (uint32_t)s * kGeoStage;
-      tc::bulk_g2s(sb + oXs + (uint32_t)s * kXBytes, p.rec_feat + (size_t)t * kXBytes, kXBytes, full + s);
-      tc::bulk_g2s(geo, p.rec_geom + (size_t)t * kGeoBytes, kGeoBytes, full + s);
-      tc::bulk_g2s(geo + kGeoBytes, p.rec_dpart + (size_t)t * 128, 128, full + s);
+      // records are read once: evict-first, so they do not push the region's
+      // gradient lines (the scatter's atomics) out of L2
+      const uint64_t pol = tc::policy_evict_first();
+      tc::bulk_g2s_hint(sb + oXs + (uint32_t)s * kXBytes, p.rec_feat + (size_t)t * kXBytes, kXBytes, full + s, pol);
+      tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeoBytes, kGeoBytes, full + s, pol);
+      tc::bulk_g2s_hint(geo + kGeoBytes, p.rec_dpart + (size_t)t * 128, 128, full + s, pol);
       pend[s] = it;
     };
     if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
@@ -387,6 +387,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
           tc::mma_f16(tmem, tc::desc_sw64(xs + 32 * kk, 16), tc::desc_sw128(sb + oB1 + 32 * kk), id64, kk);
         tc::mma_commit(mbar);  // also tracks the previous tile's weight-gradient MMAs
       }
+      // ---- meanwhile: chunk-local render adjoint from the records -> g_o tile
+      //      row (warps of level half 0); every row is rewritten, zeros for
+      //      samples outside the chunks
+      if (g == 0 && staged) {
+        float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (n_valid > 0) {
+          const float4 a0 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q);
+          const float4 a1 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q + 16);
+          const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
+          const float Tn = geo[5 * kRows + row], w = geo[6 * kRows + row], pair = geo[7 * kRows + row];
+          const float sigma = geo[8 * kRows + row];
+          const float rgb[3] = {geo[9 * kRows + row], geo[10 * kRows + row], geo[11 * kRows + row]};
+          float g_tau;
+          render_chunk_adjoint_kept(a0.y * rgb[0] + a0.z * rgb[1] + a0.w * rgb[2], tr, dl, Tn, w, pair, lane, a0.x,
+                                    a1.x, a1.y, a1.z, g_tau);
+          if (valid) {
+            const float gC[3] = {a0.y, a0.z, a0.w};
+            go[0] = g_tau * dl * sigma;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) go[1 + j] = w * gC[j] * rgb[j] * (1.0f - rgb[j]);
+          }
+        }
+        const uint32_t h01 = Half2Of<BF16>::pack(go[0], go[1]), h23 = Half2Of<BF16>::pack(go[2], go[3]);
+        const float2 f01 = Half2Of<BF16>::unpack(h01), f23 = Half2Of<BF16>::unpack(h23);
+        tc::st_shared_v4(sb + oGO + tc::sw128_chunk(row, 0), h01, h23,
+                         Half2Of<BF16>::pack(go[0] - f01.x, go[1] - f01.y),
+                         Half2Of<BF16>::pack(go[2] - f23.x, go[3] - f23.y));
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
       if (!mma_wait(mbar, phase, staged)) {
         failed = true;
         break;
@@ -395,6 +425,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         pend[s] = -1;
         // stage s ^ 1 held the previous tile, whose MMAs have all completed
         if (t + G < n_sub) issue(it + 1, t + G);
+      }
+      // G2 before the mask: [g_o hi | g_o lo] [W3 | W3]^T (one K = 16 MMA),
+      // completed by the next commit
+      if (tid == 0) {
+        tc::fence_after_sync();
+        tc::mma_f16(tmem + kG2Col, tc::desc_sw128(sb + oGO), tc::desc_sw128(sb + oB6), id64, 0u);
       }
       tc::fence_after_sync();
       float v[16];
@@ -420,94 +456,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         break;
       }
       tc::fence_after_sync();
+      // ---- H2 = relu(D2) and G2 = (H2 > 0) * (G2 before the mask), columns 32g..32g+31
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         tc::tmem_ld16(tq + 64 + 32 * g + 16 * h, v);
         tc::tmem_ld_wait();
-        mask2 |= store16_relu<BF16>(sb + oH2, row, 2 * g + h, v) << (16 * h);
-      }
-      tc::fence_proxy_async();
-      tc::fence_before_sync();
-      compute_sync();
-      // D3 = H2 W3
-      if (tid == 0) {
-        tc::fence_after_sync();
-        for (int kk = 0; kk < 4; ++kk)
-          tc::mma_f16(tmem, tc::desc_sw128(sb + oH2 + 32 * kk), tc::desc_sw128(sb + oB3 + 32 * kk), id16, kk);
-        tc::mma_commit(mbar);
-      }
-      if (!mma_wait(mbar, phase)) {
-        failed = true;
-        break;
-      }
-      tc::fence_after_sync();
-      // ---- chunk-local render adjoint -> g_o tile row (warps of level half 0)
-      if (g == 0) {
-        tc::tmem_ld8(tq, v);
-        tc::tmem_ld_wait();
-        float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (n_valid > 0) {
-          const float4 a0 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q);
-          const float4 a1 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q + 16);
-          const float gC[3] = {a0.y, a0.z, a0.w};
-          const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
-          const float Tn = geo[5 * kRows + row], w = geo[6 * kRows + row], pair = geo[7 * kRows + row];
-          float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
-          if (valid) {
-            sigma = expf(v[0]);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j]));
-          }
-          float g_tau;
-          render_chunk_adjoint_kept(gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2], tr, dl, Tn, w, pair, lane, a0.x,
-                                    a1.x, a1.y, a1.z, g_tau);
-          if (valid) {
-            go[0] = g_tau * dl * sigma;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) go[1 + j] = w * gC[j] * rgb[j] * (1.0f - rgb[j]);
-          }
-        }
-        const uint32_t h01 = Half2Of<BF16>::pack(go[0], go[1]), h23 = Half2Of<BF16>::pack(go[2], go[3]);
-        const float2 f01 = Half2Of<BF16>::unpack(h01), f23 = Half2Of<BF16>::unpack(h23);
-        tc::st_shared_v4(sb + oGO + tc::sw128_chunk(row, 0), h01, h23,
-                         Half2Of<BF16>::pack(go[0] - f01.x, go[1] - f01.y),
-                         Half2Of<BF16>::pack(go[2] - f23.x, go[3] - f23.y));
-      }
-      tc::fence_proxy_async();
-      tc::fence_before_sync();
-      compute_sync();
-      const bool acc_on = dw_started;
-      // ---- G2 before the mask: [g_o hi | g_o lo] [W3 | W3]^T (columns 64..127);
-      //      DW3 += [H2 | H1]^T [g_o hi | g_o lo] (16 samples per K step = two
-      //      8-row groups of both MN-major operands)
-      if (tid == 0) {
-        tc::fence_after_sync();
-        tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oGO), tc::desc_sw128(sb + oB6), id64, 0u);
-        tc::mma_commit(mbar);
-        // DW3 is only read at the region flush: not waited on here (H2 and
-        // the g_o tile are next written after later commits have completed)
-        for (int kk = 0; kk < 8; ++kk)
-          tc::mma_f16(tmem + kDw3Col, tc::desc_sw128_mn(sb + oH2 + 2048 * kk, kTileBytes),
-                      tc::desc_sw128_mn(sb + oGO + 2048 * kk, 1024), id16_abt, (acc_on || kk > 0) ? 1u : 0u);
-      }
-      if (!mma_wait(mbar, phase)) {
-        failed = true;
-        break;
-      }
-      tc::fence_after_sync();
-      // ---- G2 = (H2 > 0) * G2 before the mask, columns 32g..32g+31 of this row
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        tc::tmem_ld16(tq + 64 + 32 * g + 16 * h, v);
+        const uint32_t m2 = store16_relu<BF16>(sb + oH2, row, 2 * g + h, v);
+        mask2 |= m2 << (16 * h);
+        tc::tmem_ld16(tq + kG2Col + 32 * g + 16 * h, v);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          if (!((mask2 >> (16 * h + i)) & 1u)) v[i] = 0.0f;
+          if (!((m2 >> i) & 1u)) v[i] = 0.0f;
         store16_hilo<BF16>(sb + oG2, sb + oG2l, row, 2 * g + h, v);
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
       compute_sync();
+      const bool acc_on = dw_started;
       // ---- D4 = G2 W2^T (dL/dh1; W2 read MN-major from the layer-2 tile)
       if (tid == 0) {
         tc::fence_after_sync();
@@ -518,6 +484,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
           tc::mma_f16(tmem + 64, tc::desc_sw128(sb + oG2l + 32 * kk), tc::desc_sw128_mn(sb + oB2 + 2048 * kk, 1024),
                       id64_bt, 1);
         tc::mma_commit(mbar);
+        // DW3 += [H2 | H1]^T [g_o hi | g_o lo] (16 samples per K step = two
+        // 8-row groups of both MN-major operands); only read at the region
+        // flush, so not waited on here: H2 and the g_o tile are next written
+        // after the following commit has completed
+        for (int kk = 0; kk < 8; ++kk)
+          tc::mma_f16(tmem + kDw3Col, tc::desc_sw128_mn(sb + oH2 + 2048 * kk, kTileBytes),
+                      tc::desc_sw128_mn(sb + oGO + 2048 * kk, 1024), id16_abt, (acc_on || kk > 0) ? 1u : 0u);
       }
       if (!mma_wait(mbar, phase)) {
         failed = true;

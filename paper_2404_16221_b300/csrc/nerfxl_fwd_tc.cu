@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       // them, the sample's region coordinates / position / length (thread g
       // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
       // count, and the chunk's tile-order position for the composite adjoint
-      // (Tn, w and pair follow from the chunk render below).
+      // (Tn, w, pair, sigma and rgb follow from the chunk render below).
       const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
@@ -362,6 +362,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         const Partial pt = render_chunk(sigma, rgb, tr, dl, lane,
                                         kRec ? p.rec.geom + (size_t)t * kGeomFloats + 5 * kTcRows + row : nullptr,
                                         kTcRows);
+        if (kRec) {
+          float* geo = p.rec.geom + (size_t)t * kGeomFloats;
+          geo[8 * kTcRows + row] = sigma;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) geo[(9 + j) * kTcRows + row] = rgb[j];
+        }
         if (lane == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
           dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);

@@ -24,7 +24,7 @@ struct Layout {
   // Per-tile records of the tensor-core backward (backward workspaces with a
   // 16-bit MLP only; 0 otherwise). A tile is 4 chunks = 128 sample rows.
   size_t rec_feat;   // [tiles][128 rows][64 B]: 16-bit features, 64-byte-swizzled MMA tile
-  size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl Tn w pair; samples per chunk
+  size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl Tn w pair sigma rgb; chunk counts
   size_t rec_dpart;  // float4[tiles * 4][2]: chunk adjoints in tile order
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
   size_t total;
@@ -59,10 +59,11 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
 //   geometry  128 floats each of u0, u1, u2 (region coordinates), tr (tbar - tn),
 //             dl (interval length), Tn (transmittance after the sample within its
 //             chunk), w (chunk-local weight), pair (sum over the chunk of
-//             w_j |tr_i - tr_j|); then the valid-sample count of each chunk (int32).
+//             w_j |tr_i - tr_j|), sigma, r, g, b (the MLP outputs after exp /
+//             sigmoid); then the valid-sample count of each chunk (int32).
 constexpr int kRecRows = 128;
-constexpr int kGeomRowFields = 8;
-constexpr int kGeomFloats = kGeomRowFields * kRecRows + 4;  // 4112 bytes, a multiple of 16
+constexpr int kGeomRowFields = 12;
+constexpr int kGeomFloats = kGeomRowFields * kRecRows + 4;  // 6160 bytes, a multiple of 16
 constexpr size_t kRecFeatBytes = (size_t)kRecRows * 64;     // 8192 bytes per tile
 
 // Where the tensor-core forward writes the backward's records (all NULL for a

@@ -226,6 +226,10 @@ BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
 # geometry 8 x 4 B, chunk adjoints 32 B per 32 samples) and the read-modify-write
 # of the FP32 gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
 TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 8 * 4 + 1 + 2 * 8 * 2 * 4 * 16
+# DRAM bytes (read + write) of one k_field_bwd_tc launch on this workload, from
+# one ncu capture of the kernel as it stands (dram__bytes_read.sum 4.888 GB +
+# dram__bytes_write.sum 2.448 GB); re-capture when the kernel changes.
+BWD_TC_DRAM_BYTES = 4.888215e9 + 2.447699e9
 
 
 def serve_sweep(args, dev, rates):
@@ -455,7 +459,7 @@ def main():
                 "d2h_bytes_per_step": 12},
         "gpu_launches": 11 * steps,
         "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": BWD_TC_DRAM_BYTES,
                      "basis": "%d B/sample algorithmic (records: 16-bit features 64 B + geometry 32 B + chunk "
                               "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
                               "%.3f ms (%s peak)"

@@ -291,9 +291,9 @@ __device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3],
   if (keep) {
     const float W_gt = warp_suffix_scan(w, lane) - w;
     const float WT_gt = warp_suffix_scan(wt, lane) - wt;
-    keep[0] = expf(-incl);
-    keep[stride] = w;
-    keep[2 * stride] = (tr * Wx - WTx) + (WT_gt - tr * W_gt);
+    __stcs(keep, expf(-incl));
+    __stcs(keep + stride, w);
+    __stcs(keep + 2 * stride, (tr * Wx - WTx) + (WT_gt - tr * W_gt));
   }
   Partial p;
   p.tau = __shfl_sync(0xFFFFFFFFu, incl, 31);

@@ -267,15 +267,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
       // count, and the chunk's tile-order position for the composite adjoint
       // (Tn, w, pair, sigma and rgb follow from the chunk render below).
+      // Streaming stores: the records are read once, by the backward, and
+      // should not push the region's tables out of L2 meanwhile.
       const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      p.rec.feat[(size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u))] = pk;
+      __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
-      geo[g * kTcRows + row] = g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr));
+      __stcs(geo + g * kTcRows + row, g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr)));
       if (g == 0) {
-        geo[4 * kTcRows + row] = dl;
+        __stcs(geo + 4 * kTcRows + row, dl);
         if (lane == 0) {
           const int n_valid = chunk_ok ? min(kWarp, seg_n(sd) - c * kWarp) : 0;
           reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] = n_valid;
@@ -364,9 +366,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
                                         kTcRows);
         if (kRec) {
           float* geo = p.rec.geom + (size_t)t * kGeomFloats;
-          geo[8 * kTcRows + row] = sigma;
+          __stcs(geo + 8 * kTcRows + row, sigma);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) geo[(9 + j) * kTcRows + row] = rgb[j];
+          for (int j = 0; j < 3; ++j) __stcs(geo + (9 + j) * kTcRows + row, rgb[j]);
         }
         if (lane == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);

@@ -53,22 +53,31 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int64_t R, const float* _
 }
 
 // Sums the block partials in a fixed order (Kahan) -> loss_out = {total, photo, dist}.
-__global__ void k_loss_final(const float2* __restrict__ block_sums, int nb, int64_t R, float lambda,
-                             float* __restrict__ loss_out) {
-  if (threadIdx.x != 0) return;
-  float sp = 0.0f, cp = 0.0f, sd = 0.0f, cd = 0.0f;
-  for (int b = 0; b < nb; ++b) {
+// Final reduction of the per-block sums: FP64 partial sums per thread, then a
+// fixed-order tree in shared memory (deterministic, error far below FP32).
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) k_loss_final(const float2* __restrict__ block_sums, int nb, int64_t R,
+                                                              float lambda, float* __restrict__ loss_out) {
+  __shared__ double s_p[kFinalThreads], s_d[kFinalThreads];
+  double sp = 0.0, sd = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kFinalThreads) {
     const float2 v = block_sums[b];
-    float y = v.x - cp, s = sp + y;
-    cp = (s - sp) - y;
-    sp = s;
-    y = v.y - cd;
-    s = sd + y;
-    cd = (s - sd) - y;
-    sd = s;
+    sp += (double)v.x;
+    sd += (double)v.y;
   }
-  const float photo = R > 0 ? sp / (3.0f * (float)R) : 0.0f;
-  const float dmean = R > 0 ? sd / (float)R : 0.0f;
+  s_p[threadIdx.x] = sp;
+  s_d[threadIdx.x] = sd;
+  __syncthreads();
+  for (int o = kFinalThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_p[threadIdx.x] += s_p[threadIdx.x + o];
+      s_d[threadIdx.x] += s_d[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const float photo = R > 0 ? (float)(s_p[0] / (3.0 * (double)R)) : 0.0f;
+  const float dmean = R > 0 ? (float)(s_d[0] / (double)R) : 0.0f;
   loss_out[0] = photo + lambda * dmean;
   loss_out[1] = photo;
   loss_out[2] = dmean;
@@ -125,7 +134,7 @@ nerfxl_status nerfxl_loss(int64_t n_rays, const float* rgb, const float* dist, c
     nerfxl_status st = launch_check("k_loss");
     if (st != NERFXL_OK) return st;
   }
-  k_loss_final<<<1, 32, 0, stream>>>(sums, nb, n_rays, lambda_dist, loss_out);
+  k_loss_final<<<1, kFinalThreads, 0, stream>>>(sums, nb, n_rays, lambda_dist, loss_out);
   return launch_check("k_loss_final");
 }
 

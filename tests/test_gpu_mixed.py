@@ -298,3 +298,22 @@ def test_mixed_backward_repeatable():
     for other in runs[1:]:
         for a, b in zip(runs[0], other):
             assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("n", [1, 3, 37])
+def test_mixed_backward_small_batches(n):
+    """Batches with far fewer tiles than CTAs (most CTAs get no tile; a
+    region may hold a single padded tile) against the oracle, on the
+    kink-free network of the structure test."""
+    w = H.workload("grid8", L=16, log2_T=14)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    P = oracle.mlp_params(w.mlp_in, w.W)
+    g = sy.rng(22, "misc")
+    t = g.uniform(0.1, 1.0, (w.K, E, 2)).astype(np.float32)
+    m = np.concatenate([g.uniform(0.0, 0.05, (w.K, 32 * 64)), g.uniform(0.0, 0.05, (w.K, 64 * 64)),
+                        g.normal(0.0, 0.1, (w.K, 64 * 4))], 1).astype(np.float32)
+    gt, gm, gt_ref, gm_ref = _mixed_backward(w, t, m, torch.float16, torch.bfloat16, n=n, seed=30 + n)
+    ft, et = _grad_close(gt, gt_ref, 1e-2)
+    fm, em = _grad_close(gm, gm_ref, 1e-2)
+    print("mixed backward, %d rays: tables frac>1e-2 %.1e max %.2e; mlp frac %.1e max %.2e" % (n, ft, et, fm, em))
+    assert ft == 0.0 and fm == 0.0

@@ -384,6 +384,29 @@ def main():
                 forms[name].pop(k)
             del fc
             torch.cuda.empty_cache()
+        # ---- spatial partitioning (Sec. 3.4) on an uneven trajectory: 32 regions from the CDF splits of
+        #      training-ray samples vs the uniform 8x4x1 slabs, held-out rays of the same trajectory
+        root = sy.scene_root(wc)
+        o_tr, d_tr = sy.one_sided_rays(wc, 1 << 14, 61)
+        cdf_boxes, _ = api.partition_boxes(sy.ray_sample_points(o_tr, d_tr, root, 64, 62), root, 5)
+        o1, d1 = sy.one_sided_rays(wc, 1 << 18, 63)
+        o1_d, d1_d = torch.from_numpy(o1).to(dev), torch.from_numpy(d1).to(dev)
+        part = {}
+        for label, boxes in (("uniform_grid", wc.boxes), ("cdf_partition", cdf_boxes)):
+            fc = api.PartitionedField(boxes, wc.level_res, wc.log2_T, tc_.to(torch.float16), mc_.to(torch.bfloat16),
+                                      device=dev)
+            sp1 = api.Sampling(wc.S, 32)
+            r = fwd_form(wc, fc, sp1, o1_d, d1_d, "k_field_fwd_tc", 8 * wc.F * 2 * wc.L)
+            chunks = api.region_chunks(r["ws"], wc.K)
+            part[label] = {"rays_per_s": r["rays"] / (statistics.mean(r["step_ms"]) / 1000.0),
+                           "chunks_max_over_min": float(chunks.max() / max(int(chunks.min()), 1)),
+                           "chunks_max_over_mean": float(chunks.max() / chunks.mean())}
+            del fc, r
+            torch.cuda.empty_cache()
+        forms["city32_partition_balance"] = {
+            "partition": part,
+            "note": "FP16 tables + BF16 MLP; 2^18 held-out rays of a trajectory covering x < -1 only; 32 boxes "
+                    "from recursive CDF = 0.5 splits of samples of 2^14 training rays of the same trajectory"}
         # ---- serving (K=32 field resident, FP16 tables + BF16 MLP), Poisson arrivals at 200 req/s
         ws_ = sy.workload("serve32")
         reqs = serve.requests_from_stream(args.serve_requests, 200.0, ws_.seed)
@@ -422,7 +445,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops()
 
     def summary(f):
-        if "serve" in f:
+        if "serve" in f or "partition" in f:
             return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
         r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}

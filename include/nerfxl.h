@@ -239,6 +239,35 @@ nerfxl_status nerfxl_render_cameras(const nerfxl_field* f, const nerfxl_sampling
                                     cudaStream_t stream);
 
 /*
+ * Spatial partitioning (Sec. 3.4 "Spatial Partitioning" and its appendix
+ * figure): split the root box [6] (min xyz, max xyz) recursively, `levels`
+ * times, at the plane where the CDF of the points inside the box along one
+ * axis is 0.5, choosing the axis whose two halves are closest to cubic; the
+ * result is 2^levels disjoint boxes with balanced point counts, written to
+ * boxes [2^levels][6] in depth-first order (lower half first), and the number
+ * of points in each to counts [2^levels] (may be NULL). points [n_points][3]
+ * is the scene content: an SfM point cloud, or samples of training rays when
+ * there is none. Readings where the paper is silent: the CDF = 0.5 plane of
+ * m points is their median 0.5 (s[(m-1)/2] + s[m/2]) along the axis (FP32); a
+ * point goes below the plane if its coordinate < plane; a plane that is not
+ * strictly inside the box falls back to the midplane; aspect ratio = longest
+ * side / shortest side, a split scored by the worse of its two boxes, ties to
+ * the lowest axis; points outside the root are ignored. HOST pointers; runs
+ * on the CPU (once per scene). levels in 0..10; E_INVALID on bad arguments.
+ */
+nerfxl_status nerfxl_partition(const float* points, int64_t n_points, const float* root, int32_t levels, float* boxes,
+                               int64_t* counts);
+
+/*
+ * Per-region chunk counts of the last sampling in a workspace (a chunk is up
+ * to 32 samples of one ray segment): copies K int32 to the HOST array counts
+ * (synchronises the stream). The measure of how evenly a partition spreads
+ * the samples over the regions. The paper has no counterpart.
+ */
+nerfxl_status nerfxl_region_chunks(const void* workspace, size_t ws_bytes, int32_t K, int32_t* counts,
+                                   cudaStream_t stream);
+
+/*
  * Forward render without a caller workspace (the paper has no counterpart:
  * this serves callers that cannot allocate device memory, such as plain C
  * programs or plug-ins without an allocator, hosts that own the whole device

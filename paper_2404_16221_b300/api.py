@@ -9,6 +9,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import numpy as np
+
 import torch
 
 from . import native as N
@@ -297,3 +299,35 @@ def dequantize_mlp_e4m3(q, scales):
         out[:, off:off + n] *= torch.as_tensor(scales)[:, li:li + 1]
         off += n
     return out
+
+
+def partition_boxes(points, root, levels: int):
+    """Spatial partitioning (Sec. 3.4): 2^levels disjoint boxes [K][6] with
+    balanced point counts, and the counts (host numpy arrays)."""
+    pts = np.ascontiguousarray(np.asarray(points, np.float32).reshape(-1, 3))
+    root = np.ascontiguousarray(np.asarray(root, np.float32).reshape(6))
+    K = 1 << min(max(int(levels), 0), 10)  # out-of-range levels are refused by the library
+    boxes = np.zeros((K, 6), np.float32)
+    counts = np.zeros(K, np.int64)
+    st = N.lib().nerfxl_partition(pts.ctypes.data, len(pts), root.ctypes.data, int(levels), boxes.ctypes.data,
+                                  counts.ctypes.data)
+    N.check(st, "nerfxl_partition")
+    return boxes, counts
+
+
+def region_chunks(workspace, K: int, stream=None):
+    """Per-region chunk counts of the last sampling in a workspace (syncs)."""
+    out = np.zeros(int(K), np.int32)
+    N.check(N.lib().nerfxl_region_chunks(N._ptr(workspace), workspace.numel(), int(K), out.ctypes.data,
+                                         N._stream(stream)), "nerfxl_region_chunks")
+    return out
+
+
+def workspace_stats(workspace, stream=None):
+    """(samples, chunks) of the last sampling in a workspace (syncs)."""
+    import ctypes
+
+    ns, nc = ctypes.c_int64(0), ctypes.c_int64(0)
+    N.check(N.lib().nerfxl_workspace_stats(N._ptr(workspace), workspace.numel(), ctypes.byref(ns), ctypes.byref(nc),
+                                           N._stream(stream)), "nerfxl_workspace_stats")
+    return int(ns.value), int(nc.value)

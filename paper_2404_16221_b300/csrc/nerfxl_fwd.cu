@@ -601,6 +601,19 @@ nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int
   return NERFXL_OK;
 }
 
+nerfxl_status nerfxl_region_chunks(const void* workspace, size_t ws_bytes, int32_t K, int32_t* counts,
+                                   cudaStream_t stream) {
+  if (!workspace || !counts || K < 1 || K > NERFXL_MAX_REGIONS) return set_error(NERFXL_E_INVALID, "bad arguments");
+  // the counts follow the 256-byte header block (see layout())
+  const size_t off = align_up(sizeof(int32_t) * 16, 256);
+  if (ws_bytes < off + sizeof(int32_t) * (size_t)K) return set_error(NERFXL_E_WORKSPACE, "workspace too small");
+  if (cudaMemcpyAsync(counts, static_cast<const char*>(workspace) + off, sizeof(int32_t) * (size_t)K,
+                      cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return launch_check("nerfxl_region_chunks");
+  return NERFXL_OK;
+}
+
 nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop) {
   if ((start == nullptr) != (stop == nullptr)) return set_error(NERFXL_E_INVALID, "give both events or neither");
   g_prof[0] = start;

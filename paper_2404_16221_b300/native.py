@@ -85,6 +85,8 @@ SIGNATURES = {
     "nerfxl_render_cameras_workspace_bytes": (_sz, [_FP, _SP, _i64]),
     "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_wait_probe": (C.c_int, [_vp, C.c_uint32, _i32, _vp]),
+    "nerfxl_partition": (C.c_int, [_vp, _i64, _vp, _i32, _vp, _vp]),
+    "nerfxl_region_chunks": (C.c_int, [_vp, _sz, _i32, _vp, _vp]),
     "nerfxl_debug_segments": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_samples": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }

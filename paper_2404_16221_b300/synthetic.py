@@ -24,7 +24,8 @@ import math
 
 import numpy as np
 
-_STREAMS = {"rays": 1, "tables": 2, "mlp": 3, "blobs": 4, "batch": 5, "requests": 6, "subset": 7, "misc": 8}
+_STREAMS = {"rays": 1, "tables": 2, "mlp": 3, "blobs": 4, "batch": 5, "requests": 6, "subset": 7, "misc": 8,
+            "content": 9, "ray_samples": 10}
 
 
 def rng(seed: int, purpose: str) -> np.random.Generator:
@@ -270,3 +271,63 @@ def field_params_device(w: Workload, E: int, P: int, device, table_std: float = 
     g.manual_seed(int(w.seed) * 7919 + _STREAMS["mlp"])
     mlp = torch.randn((w.K, P), generator=g, device=device) * mlp_std
     return tables, mlp
+
+
+# ---------------------------------------------------------------------------
+# Scene content for the spatial partitioning (Sec. 3.4): an SfM-like point
+# cloud, or samples of training rays when no point cloud is available.
+
+def scene_root(w: Workload) -> np.ndarray:
+    """The scene's bounding box [6] (min xyz, max xyz): the union of the
+    workload's grid boxes."""
+    b = np.asarray(w.boxes, np.float32)
+    return np.concatenate([b[:, :3].min(0), b[:, 3:].max(0)]).astype(np.float32)
+
+
+def content_points(w: Workload, n: int, seed: int | None = None, clusters: int = 24) -> np.ndarray:
+    """SfM-like point cloud [n][3] float32: a mixture of anisotropic Gaussian
+    clusters (centres uniform in the scene box, per-axis sizes log-uniform in
+    2%..20% of the box extent, weights uniform in [0.2, 1]) clipped to the
+    box, so content is uneven across space as in real captures."""
+    g = rng(w.seed if seed is None else seed, "content")
+    root = scene_root(w)
+    lo, hi = root[:3].astype(np.float64), root[3:].astype(np.float64)
+    ext = hi - lo
+    centres = lo + g.uniform(0.0, 1.0, (clusters, 3)) * ext
+    sizes = np.exp(g.uniform(np.log(0.02), np.log(0.2), (clusters, 3))) * ext
+    weights = g.uniform(0.2, 1.0, clusters)
+    which = g.choice(clusters, size=n, p=weights / weights.sum())
+    pts = centres[which] + g.standard_normal((n, 3)) * sizes[which]
+    return np.clip(pts, lo, hi).astype(np.float32)
+
+
+def ray_sample_points(rays_o, rays_d, root, n_per_ray: int, seed: int) -> np.ndarray:
+    """Samples of training rays inside the scene box: per ray, n_per_ray
+    stratified samples (one uniform draw per stratum) of the ray's overlap
+    [t0, t1] with the box; rays that miss the box give none."""
+    o = np.asarray(rays_o, np.float64)
+    d = np.asarray(rays_d, np.float64)
+    root = np.asarray(root, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        ta = (root[:3] - o) * inv
+        tb = (root[3:] - o) * inv
+    t0 = np.nanmax(np.minimum(ta, tb), axis=1)
+    t1 = np.nanmin(np.maximum(ta, tb), axis=1)
+    t0 = np.maximum(t0, 0.0)
+    hit = t1 > t0
+    o, d, t0, t1 = o[hit], d[hit], t0[hit], t1[hit]
+    g = rng(seed, "ray_samples")
+    j = (np.arange(n_per_ray)[None, :] + g.uniform(0.0, 1.0, (len(o), n_per_ray))) / n_per_ray
+    t = t0[:, None] + j * (t1 - t0)[:, None]
+    pts = o[:, None, :] + t[..., None] * d[:, None, :]
+    return np.clip(pts.reshape(-1, 3), root[:3], root[3:]).astype(np.float32)
+
+
+def one_sided_rays(w: Workload, n: int, seed: int, x_max: float = -1.0):
+    """Rays of a trajectory that covers one side of the scene: the workload's
+    rays whose origin has x < x_max (uneven training-view coverage, the case
+    the spatial partitioning balances)."""
+    o, d = workload_rays(w, 4 * n, seed=seed)
+    keep = np.nonzero(o[:, 0] < x_max)[0][:n]
+    return o[keep].copy(), d[keep].copy()

@@ -17,6 +17,7 @@ collective). Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -321,6 +322,24 @@ def main():
     forms["grid8_fwd_fp32"] = fwd_form(w, f32, samp, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
     fmix = mk_field(w, tables, mlp, torch.float16, torch.bfloat16)
     forms["grid8_fwd_f16tab_bf16mlp"] = fwd_form(w, fmix, samp, o_dev, d_dev, "k_field_fwd_tc", 8 * w.F * 2 * w.L)
+    # sample-level composition (the naive scheme of Sec. 4.2) vs the segment-level one, FP32 forward:
+    # bytes between the field kernel and the composite (written once, read once) and rays/s
+    samp_s = dataclasses.replace(samp, flags=api.SAMPLE_COMPOSITE)
+    fs = fwd_form(w, f32, samp_s, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
+    seg = forms["grid8_fwd_fp32"]
+    seg_bytes = 2 * 32 * seg["chunks"] / R          # one 32-byte partial per 32-sample chunk
+    smp_bytes = 2 * 24 * 32 * fs["chunks"] / R      # 24 bytes per sample slot
+    forms["grid8_composition"] = {
+        "composition": {
+            "segment_level": {"rays_per_s": R / (statistics.mean(seg["step_ms"]) / 1000.0),
+                              "bytes_per_ray": seg_bytes},
+            "sample_level": {"rays_per_s": R / (statistics.mean(fs["step_ms"]) / 1000.0),
+                             "bytes_per_ray": smp_bytes},
+            "bytes_ratio": smp_bytes / seg_bytes},
+        "note": "FP32 field; bytes written by the field kernel and read by the composite, per ray "
+                "(the one-GPU analogue of the paper's per-sample vs per-tile exchange)"}
+    for k in ("field", "ws", "out", "step"):
+        fs.pop(k)
     for k in ("grid8_fwd_fp32", "grid8_fwd_f16tab_bf16mlp"):
         forms[k].pop("field"), forms[k].pop("ws"), forms[k].pop("out"), forms[k].pop("step")
     del fmix
@@ -445,7 +464,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops()
 
     def summary(f):
-        if "serve" in f or "partition" in f:
+        if "serve" in f or "partition" in f or "composition" in f:
             return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
         r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}

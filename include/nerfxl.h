@@ -99,16 +99,29 @@ typedef struct nerfxl_sampling {
   int32_t n_samples;
   int32_t max_segments;
   float t_min;   /* near clamp of every t0 (0 for cameras outside the scene) */
-  int32_t flags; /* NERFXL_SAVE_FEATURES or 0 */
+  int32_t flags; /* NERFXL_SAVE_FEATURES | NERFXL_SAMPLE_COMPOSITE, or 0 */
 } nerfxl_sampling;
 
 /*
- * Training with a 16-bit MLP: the forward stores each sample's encoded
- * features (32 x 16 bit) in a backward-sized workspace and the backward reads
- * them instead of gathering the hash tables again (64 bytes per sample of
- * extra workspace). Without the flag the backward recomputes everything.
+ * Training with a 16-bit MLP: the forward writes the tensor-core backward's
+ * per-tile records (the 16-bit encoded features, sample geometry and the
+ * chunk-render values its adjoint reuses: 97 bytes per sample slot) into a
+ * backward-sized workspace. Without the flag nerfxl_render_bwd rebuilds them
+ * with one more forward pass first.
  */
 #define NERFXL_SAVE_FEATURES 1
+
+/*
+ * Sample-level composition (the naive scheme of Sec. 4.2 that the paper's
+ * segment-level composition replaces): the FP32 forward writes every sample's
+ * sigma, rgb, tbar - tn and delta (24 bytes per sample slot) instead of one
+ * partial per 32-sample chunk, and the composite renders each ray in a single
+ * pass over its samples (Eq. 1-2, 5-6 and the distortion loss directly). Same
+ * outputs within FP32 rounding; kept to measure what the segment-level scheme
+ * saves (bytes between the field kernel and the composite). FP32 MLP only
+ * (E_UNSUPPORTED otherwise); forward only.
+ */
+#define NERFXL_SAMPLE_COMPOSITE 2
 
 /* Entries per region table (sum of level sizes), or -1 on bad input. */
 int64_t nerfxl_table_entries(const int32_t* level_res /* host [L] */, int32_t L, int32_t log2_T);

@@ -18,7 +18,8 @@ from . import native as N
 _DTYPE_CODE = {torch.float32: N.F32, torch.float16: N.F16, torch.bfloat16: N.BF16, torch.uint8: N.E4M3}
 
 
-SAVE_FEATURES = 1  # forward stores 16-bit features for the backward (NERFXL_SAVE_FEATURES)
+SAVE_FEATURES = 1  # forward writes the tensor-core backward's records (NERFXL_SAVE_FEATURES)
+SAMPLE_COMPOSITE = 2  # sample-level composition, FP32 forward only (NERFXL_SAMPLE_COMPOSITE)
 
 
 @dataclasses.dataclass

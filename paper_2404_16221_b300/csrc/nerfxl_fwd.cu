@@ -168,6 +168,8 @@ struct FwdParams {
   const uint2* chunks;
   const int32_t* n_tiles;
   float4* partials;        // [R][max_chunk][2]
+  float4* smp4;            // per sample slot: sigma, rgb (sample-level composition), or NULL
+  float2* smp2;            // per sample slot: tbar - tn, delta
 };
 
 
@@ -232,12 +234,78 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       for (int q = 0; q < 3; ++q) rgb[q] = 1.0f / (1.0f + expf(-raw[1 + q]));
     }
     const float tr = valid ? __fsub_rn(tbar, h.tn) : 0.0f;
+    const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+    if (p.smp4) {  // sample-level composition: every sample leaves the kernel
+      p.smp4[slot * kWarp + lane] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+      p.smp2[slot * kWarp + lane] = make_float2(tr, dl);
+      continue;
+    }
     const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
     if (lane == 0) {
-      float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
+      float4* dst = p.partials + 2 * slot;
       dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
       dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_composite_samples: sample-level composition, one warp per ray. The ray's
+// sample slots are visited in ray order (chunks of segments sorted along the
+// ray), 32 at a time; within a step the lanes scan their optical depth and
+// weights, across steps the prefix optical depth (log space, compensated), the
+// accumulated C, A, D and the weight sums W, WT of the distortion's prefix form
+// carry over:
+//   T_i = exp(-sum_{j<i} tau_j), w_i = T_i (1 - exp(-tau_i)),
+//   L = sum_i 2 w_i (t_i W_<i - WT_<i) + w_i^2 delta_i / 3.
+
+__global__ void __launch_bounds__(256) k_composite_samples(int64_t R, SampParams sp, const RayHdr* __restrict__ hdr,
+                                                           const float4* __restrict__ smp4,
+                                                           const float2* __restrict__ smp2, float* __restrict__ rgb,
+                                                           float* __restrict__ depth, float* __restrict__ opacity,
+                                                           float* __restrict__ dist, const int64_t* __restrict__ out_index) {
+  const int lane = threadIdx.x % kWarp;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  if (r >= R) return;  // warp-uniform
+  const int64_t o = out_index ? out_index[r] : r;
+  if (o < 0) return;
+  const RayHdr h = hdr[r];
+  float tau = 0.0f, comp = 0.0f;  // prefix optical depth before this step
+  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f, D = 0.0f, L = 0.0f, W = 0.0f, WT = 0.0f;
+  for (int c = 0; c < h.nchunk; ++c) {
+    const size_t at = ((size_t)r * sp.max_chunk + c) * kWarp + lane;
+    const float4 a = smp4[at];
+    const float2 b = smp2[at];
+    const float t_i = a.x * b.y;  // optical depth of the sample
+    const float incl = warp_inclusive_scan(t_i, lane);
+    const float excl = warp_exclusive_from_inclusive(incl, lane);
+    const float T = expf(-(tau + excl));
+    const float w = T * -expm1f(-t_i);
+    const float wt = w * b.x;
+    const float W_lt = W + warp_exclusive_from_inclusive(warp_inclusive_scan(w, lane), lane);
+    const float WT_lt = WT + warp_exclusive_from_inclusive(warp_inclusive_scan(wt, lane), lane);
+    const float l = 2.0f * w * (b.x * W_lt - WT_lt) + w * w * b.y * (1.0f / 3.0f);
+    C0 += warp_sum(w * a.y);
+    C1 += warp_sum(w * a.z);
+    C2 += warp_sum(w * a.w);
+    const float ws = warp_sum(w), wts = warp_sum(wt);
+    A += ws;
+    D += wts;
+    W += ws;
+    WT += wts;
+    L += warp_sum(l);
+    const float y = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1) - comp;
+    const float s = tau + y;
+    comp = (s - tau) - y;
+    tau = s;
+  }
+  if (lane == 0) {
+    rgb[3 * o + 0] = C0;
+    rgb[3 * o + 1] = C1;
+    rgb[3 * o + 2] = C2;
+    depth[o] = D + A * h.tn;
+    opacity[o] = A;
+    if (dist) dist[o] = L;
   }
 }
 
@@ -359,6 +427,11 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.rec_geom = take(sizeof(float) * kGeomFloats * L.rec_tiles);
     L.rec_dpart = take(sizeof(float4) * 2 * 4 * L.rec_tiles);
     L.rec_pos = take(sizeof(int32_t) * R * mc);
+  }
+  L.smp4 = L.smp2 = 0;
+  if (s->flags & NERFXL_SAMPLE_COMPOSITE) {
+    L.smp4 = take(sizeof(float4) * (size_t)R * mc * kWarp);
+    L.smp2 = take(sizeof(float2) * (size_t)R * mc * kWarp);
   }
   L.total = off;
   L.max_seg = ms;
@@ -530,6 +603,8 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   st = run_sampling(f, sp, n_rays, rays_o, rays_d, ws, L, stream);
   if (st != NERFXL_OK) return st;
   if (n_rays == 0) return NERFXL_OK;
+  if (tc_mlp && (s->flags & NERFXL_SAMPLE_COMPOSITE))
+    return set_error(NERFXL_E_UNSUPPORTED, "sample-level composition is built for the FP32 MLP only");
   if (tc_mlp) {
     RecordOut rec = {nullptr, nullptr, nullptr};
     if (s->flags & NERFXL_SAVE_FEATURES) {
@@ -561,6 +636,9 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
+  const bool per_sample = (s->flags & NERFXL_SAMPLE_COMPOSITE) != 0;
+  p.smp4 = per_sample ? reinterpret_cast<float4*>(ws + L.smp4) : nullptr;
+  p.smp2 = per_sample ? reinterpret_cast<float2*>(ws + L.smp2) : nullptr;
   const size_t smem = sizeof(float) * kMlpParams + sizeof(int32_t) * (f->K + 1);
   const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
   profile_mark(0, stream);
@@ -568,6 +646,12 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   profile_mark(1, stream);
   st = launch_check("k_field_fwd_f32");
   if (st != NERFXL_OK) return st;
+  if (per_sample) {
+    const int64_t threads = n_rays * kWarp;
+    k_composite_samples<<<(int)((threads + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.smp4, p.smp2, rgb,
+                                                                           depth, opacity, dist, out_index);
+    return launch_check("k_composite_samples");
+  }
   k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.partials, rgb, depth, opacity,
                                                                 dist, out_index);
   return launch_check("k_composite");

@@ -27,6 +27,9 @@ struct Layout {
   size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl Tn w pair sigma rgb; chunk counts
   size_t rec_dpart;  // float4[tiles * 4][2]: chunk adjoints in tile order
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
+  // Sample-level composition (NERFXL_SAMPLE_COMPOSITE; 0 otherwise):
+  size_t smp4;       // float4[R][max_chunk][32]: sigma, r, g, b per sample slot
+  size_t smp2;       // float2[R][max_chunk][32]: tbar - tn, delta per sample slot
   size_t total;
   int64_t rec_tiles; // tiles the record regions hold
   int64_t chunk_cap;

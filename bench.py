@@ -384,7 +384,46 @@ def main():
     forms["grid8_train_fp32"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk.summary(),
                                  "kernel": "k_field_bwd_f32", "samples": forms["grid8_fwd_fp32"]["samples"],
                                  "flop_per_sample": BWD_FLOP_PER_SAMPLE}
-    del trainer, f32
+    del trainer
+    # ---- occupancy-grid skipping (the spatial-skipping structure of Sec. 5.1) on the grid8 shapes: the
+    #      grid a field trained on the sparse blob scene would hold (11% of cells), throughput with and
+    #      without it, and the cost of one full refresh of a 128^3-per-region grid
+    G_occ = 64
+    occ_bits = sy.blob_occupancy(w.boxes, sy.sparse_blobs(w.seed), G_occ, 0.4)
+    occ = {"grid": "%d^3 cells per region, %.1f%% occupied" % (G_occ, 100.0 * float(
+        np.unpackbits(occ_bits.view(np.uint8)).sum()) / (w.K * G_occ ** 3))}
+    fmix = mk_field(w, tables, mlp, torch.float16, torch.bfloat16)
+    for label, bits in (("no_grid", None), ("grid", occ_bits)):
+        fmix.set_occupancy(bits, G_occ)
+        r = fwd_form(w, fmix, samp, o_dev, d_dev, "k_field_fwd_tc", 8 * w.F * 2 * w.L)
+        occ["fwd_f16tab_bf16mlp_" + label] = {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0),
+                                             "samples_per_ray": r["samples"] / R}
+        del r
+        otrainer = api.Trainer(fmix, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01,
+                               master_tables=torch.from_numpy(tables), master_mlp=torch.from_numpy(mlp))
+        ostep = lambda: otrainer.step(o_dev, d_dev, tgt)
+        for _ in range(warm):
+            ostep()
+        o_ms, _ = time_steps(ostep, steps, flush, stream, prof=False)
+        occ["train_f16tab_bf16mlp_" + label] = {"rays_per_s": R / (statistics.mean(o_ms) / 1000.0)}
+        del otrainer
+    del fmix
+    grid = api.OccupancyGrid(w.K, 128, decay=0.95, threshold=0.4)
+    grid.update(f32)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(3):
+        grid.update(f32)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    occ["refresh_ms_128cubed_per_region"] = ev0.elapsed_time(ev1) / 3
+    forms["grid8_occupancy"] = {
+        "occupancy": occ,
+        "note": "FP16 tables + BF16 MLP, random-init grid8 field; the bits are those of the sparse blob scene's "
+                "density > 0.4 at cell centres (a trained field's grid stand-in); the refresh evaluates the FP32 "
+                "field at one Philox point per cell"}
+    del grid, f32
+    torch.cuda.empty_cache()
     # ---- city32 (K=32, 8x4x1 slabs, 2^20 rays, S=256): MLP precision variants
     if not args.skip_city:
         wc = sy.workload("city32")
@@ -403,7 +442,7 @@ def main():
                 forms[name].pop(k)
             del fc
             torch.cuda.empty_cache()
-        # ---- spatial partitioning (Sec. 3.4) on an uneven trajectory: 32 regions from the CDF splits of
+        # ---- spatial partitioning (Sec. 4.4) on an uneven trajectory: 32 regions from the CDF splits of
         #      training-ray samples vs the uniform 8x4x1 slabs, held-out rays of the same trajectory
         root = sy.scene_root(wc)
         o_tr, d_tr = sy.one_sided_rays(wc, 1 << 14, 61)
@@ -464,7 +503,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops()
 
     def summary(f):
-        if "serve" in f or "partition" in f or "composition" in f:
+        if "serve" in f or "partition" in f or "composition" in f or "occupancy" in f:
             return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
         r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}

@@ -85,6 +85,18 @@ typedef struct nerfxl_field {
   const void* mlp;                      /* [K][P] of mlp_dtype */
   int32_t table_dtype, mlp_dtype;       /* nerfxl_dtype */
   const float* mlp_scales;              /* [K][3] dequantisation scales for E4M3, else NULL */
+  /*
+   * Occupancy grid (optional; NULL = every sample is evaluated). The
+   * spatial-skipping structure of the paper's experimental system (Sec. 5.1,
+   * the grid of the cited Instant-NGP paper): per region G^3 cells over the
+   * region box (G = occ_res), cell (x, y, z) = x + G (y + G z) holding bit
+   * c % 32 of word c / 32 of the region's ceil(G^3 / 32) words. A sample whose
+   * point lies in a region-coordinate cell min(floor(u G), G - 1) with a clear
+   * bit is empty space: it is not evaluated and renders with density 0, so
+   * the result equals rendering it with sigma = 0 (no gradient reaches it).
+   */
+  const uint32_t* occupancy;            /* [K][ceil(G^3/32)], or NULL */
+  int32_t occ_res;                      /* G in [1, 1024] when occupancy is set */
 } nerfxl_field;
 
 /*
@@ -252,7 +264,28 @@ nerfxl_status nerfxl_render_cameras(const nerfxl_field* f, const nerfxl_sampling
                                     cudaStream_t stream);
 
 /*
- * Spatial partitioning (Sec. 3.4 "Spatial Partitioning" and its appendix
+ * Occupancy-grid refresh (keeps the grid of nerfxl_field.occupancy current
+ * during training; Sec. 5.1 with the cited Instant-NGP grid). For every cell c
+ * = (cx, cy, cz) of every region k, one point is drawn in the cell in region
+ * coordinates, u = ((float)c + xi) / G (FP32), with xi_axis = (word_axis >> 8)
+ * * 2^-24 from the first three words of Philox4x32-10 (Salmon et al., SC 2011)
+ * at counter {c, k, step lo, step hi} and key {seed lo, seed hi}; then
+ *   density[k][c] = max(decay * density[k][c], sigma_k(u)),
+ *   bit c of bits[k] = density[k][c] > threshold   (unused tail bits 0).
+ * Readings where the paper is silent: every cell is refreshed on each call
+ * (the caller chooses how often), the threshold is fixed (no mean-density
+ * rule), and a grid starts with density 0 and every bit set.
+ * The field must have FP32 tables and an FP32 MLP (pass the training
+ * masters); its own occupancy pointer is not read. density [K][G^3] float
+ * (device, in/out), bits [K][ceil(G^3/32)] uint32 (device, out; may be the
+ * grid the field renders with, not while a render on it is in flight).
+ * G in [1, 1024] with K * G^3 < 2^31; decay in [0, 1]; E_INVALID otherwise.
+ */
+nerfxl_status nerfxl_occupancy_update(const nerfxl_field* f, int32_t G, int64_t step, uint64_t seed, float decay,
+                                      float threshold, float* density, uint32_t* bits, cudaStream_t stream);
+
+/*
+ * Spatial partitioning (Sec. 4.4 "Spatial Partitioning" and its appendix
  * figure): split the root box [6] (min xyz, max xyz) recursively, `levels`
  * times, at the plane where the CDF of the points inside the box along one
  * axis is 0.5, choosing the axis whose two halves are closest to cubic; the
@@ -307,7 +340,8 @@ nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t 
 
 /*
  * Counters of the last call made with this workspace (synchronises the
- * stream): total intervals (samples) and non-empty 32-sample chunks.
+ * stream): samples evaluated (all intervals, or those in occupied cells when
+ * the field has an occupancy grid) and non-empty 32-sample chunks.
  */
 nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int64_t* n_samples, int64_t* n_chunks,
                                      cudaStream_t stream);

@@ -31,7 +31,8 @@ _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 class _Field(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("F", C.c_int32), ("log2_T", C.c_int32),
                 ("mlp_in", C.c_int32), ("W", C.c_int32), ("level_res", C.c_void_p),
-                ("boxes", C.c_void_p), ("tables", C.c_void_p), ("mlp", C.c_void_p)]
+                ("boxes", C.c_void_p), ("tables", C.c_void_p), ("mlp", C.c_void_p),
+                ("occupancy", C.c_void_p), ("occ_res", C.c_int32)]
 
 
 class _Sampling(C.Structure):
@@ -91,6 +92,9 @@ def lib():
         L.oracle_adam.argtypes = [C.c_int64, _f64p, _f64p, _f64p, _f64p, C.c_int64, C.c_double, C.c_double,
                                   C.c_double, C.c_double]
         L.oracle_blob_render.argtypes = [fp, sp, C.c_int64, _f32p, _f32p, C.c_int64, _f64p, _f64p, _f64p, _f64p]
+        L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.oracle_occupancy_update.argtypes = [fp, C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_double, _f64p,
+                                              _u32p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -128,7 +132,7 @@ class Field:
     boxes [K][6] float32; tables [K][E][F] and mlp [K][P] promoted to float64.
     """
 
-    def __init__(self, boxes, level_res, log2_T, F, mlp_in, W, tables, mlp):
+    def __init__(self, boxes, level_res, log2_T, F, mlp_in, W, tables, mlp, occupancy=None, occ_res: int = 0):
         self.boxes = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 6)
         self.level_res = np.ascontiguousarray(level_res, dtype=np.int32)
         self.K = self.boxes.shape[0]
@@ -138,15 +142,31 @@ class Field:
         self.P = mlp_params(self.mlp_in, self.W)
         self.tables = np.ascontiguousarray(tables, dtype=np.float64).reshape(self.K, self.E, self.F)
         self.mlp = np.ascontiguousarray(mlp, dtype=np.float64).reshape(self.K, self.P)
+        # optional occupancy grid: [K][ceil(G^3/32)] uint32 cell bits, G = occ_res
+        self.occ_res = int(occ_res)
+        self.occupancy = None
+        if occupancy is not None:
+            self.occupancy = np.ascontiguousarray(occupancy, dtype=np.uint32).reshape(self.K, occupancy_words(occ_res))
 
     def with_params(self, tables, mlp) -> "Field":
-        return Field(self.boxes, self.level_res, self.log2_T, self.F, self.mlp_in, self.W, tables, mlp)
+        return Field(self.boxes, self.level_res, self.log2_T, self.F, self.mlp_in, self.W, tables, mlp,
+                     self.occupancy, self.occ_res)
+
+    def with_occupancy(self, occupancy, occ_res: int) -> "Field":
+        return Field(self.boxes, self.level_res, self.log2_T, self.F, self.mlp_in, self.W, self.tables, self.mlp,
+                     occupancy, occ_res)
 
     def struct(self, tables=None, mlp=None) -> _Field:
         t = self.tables if tables is None else tables
         m = self.mlp if mlp is None else mlp
+        occ = None if self.occupancy is None else self.occupancy.ctypes.data
         return _Field(self.K, self.L, self.F, self.log2_T, self.mlp_in, self.W, self.level_res.ctypes.data,
-                      self.boxes.ctypes.data, t.ctypes.data, m.ctypes.data)
+                      self.boxes.ctypes.data, t.ctypes.data, m.ctypes.data, occ, self.occ_res)
+
+
+def occupancy_words(G: int) -> int:
+    """32-bit words of one region's G^3-cell occupancy bitfield."""
+    return (int(G) ** 3 + 31) // 32
 
 
 def _samp(S: int, t_min: float = 0.0) -> _Sampling:
@@ -332,3 +352,28 @@ def blob_render(field: Field, S: int, o, d, blobs):
     fs = field.struct()
     lib().oracle_blob_render(C.byref(fs), C.byref(_samp(S)), R, o, d, blobs.shape[0], blobs, rgb, depth, op)
     return rgb, depth, op
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of one 128-bit counter and 64-bit key (4 and 2 uint32 words)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    out = np.zeros(4, np.uint32)
+    lib().oracle_philox4x32_10(c, k, out)
+    return out
+
+
+def occupancy_update(field: Field, G: int, step: int, seed: int, decay: float, threshold: float, density,
+                     want_points: bool = False):
+    """One refresh of every region's G^3 occupancy grid from the field.
+
+    density [K][G^3] float64 is updated in place to max(decay * density,
+    sigma(point)); returns the new bits [K][words] (and the drawn region
+    coordinates [K][G^3][3] if asked)."""
+    assert density.dtype == np.float64 and density.flags.c_contiguous and density.size == field.K * G ** 3
+    bits = np.zeros((field.K, occupancy_words(G)), np.uint32)
+    pts = np.zeros((field.K, G ** 3, 3), np.float32) if want_points else None
+    fs = field.struct()
+    lib().oracle_occupancy_update(C.byref(fs), int(G), int(step), int(seed), float(decay), float(threshold), density,
+                                  bits, None if pts is None else pts.ctypes.data)
+    return (bits, pts) if want_points else bits

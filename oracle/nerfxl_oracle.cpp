@@ -27,6 +27,16 @@
 //     colour = sigmoid(o1..o3).
 //   * Loss: mean squared RGB error + lambda * mean distortion; Adam (Kingma &
 //     Ba) with bias correction.
+//   * Occupancy grid (the spatial-skipping structure every compared method
+//     uses, Sec. 5.1; the grid is the one of the cited Instant-NGP paper): per
+//     region a G^3 grid of cells over the region box, one bit each. A sample
+//     whose point falls in a cell with a clear bit is rendered with density 0
+//     (it is not evaluated, and no gradient flows through it). The grid is
+//     refreshed from the field: each cell's density estimate becomes
+//     max(decay * old, sigma(p)) at one point p drawn uniformly in the cell,
+//     and its bit is set where the estimate exceeds a threshold. The points
+//     come from Philox4x32-10 (Salmon et al., SC 2011), written out below from
+//     its published definition.
 //
 // Parity status: every function here is pinned by CPU tests (closed forms,
 // brute force, library GEMMs, finite differences); none is "parity unpinned".
@@ -49,6 +59,8 @@ typedef struct {
   const float* boxes;        // [K][6] min xyz, max xyz (disjoint)
   const double* tables;      // [K][E][F]  E = sum of level sizes
   const double* mlp;         // [K][P]  W1[mlp_in][W] W2[W][W] W3[W][4]
+  const uint32_t* occupancy; // [K][ceil(G^3/32)] cell bits, or NULL (no skipping)
+  int32_t occ_res;           // G: cells per axis of each region's grid
 } oracle_field;
 
 typedef struct {
@@ -196,8 +208,36 @@ struct Encoded {
   std::vector<uint32_t> index;     // [L][8] index within the level
 };
 
+// Region-local coordinate u = clamp((x - bmin) / (bmax - bmin), 0, 1), with
+// the reciprocal of the extent taken first (FP32).
+void region_u(const float* box, const float* x, float* u) {
+  for (int ax = 0; ax < 3; ++ax) {
+    const float inv_ext = 1.0f / (box[3 + ax] - box[ax]);
+    float v = (x[ax] - box[ax]) * inv_ext;
+    v = std::fmin(std::fmax(v, 0.0f), 1.0f);
+    u[ax] = v;
+  }
+}
+
+// Cell of region coordinate u in a grid of N cells per axis: min(floor(u N), N - 1).
+int32_t grid_cell(float u, int32_t N) {
+  const float p = u * (float)N;
+  int32_t c = (int32_t)std::floor(p);
+  if (c > N - 1) c = N - 1;
+  if (c < 0) c = 0;
+  return c;
+}
+
+void encode_u(const oracle_field& f, const std::vector<Level>& lv, int region, const float* u, Encoded* out);
+
 void encode(const oracle_field& f, const std::vector<Level>& lv, int region, const float* x, Encoded* out) {
-  const float* box = f.boxes + 6 * region;
+  float u[3];
+  region_u(f.boxes + 6 * region, x, u);
+  encode_u(f, lv, region, u, out);
+}
+
+// Encoding at region coordinate u.
+void encode_u(const oracle_field& f, const std::vector<Level>& lv, int region, const float* u, Encoded* out) {
   const int64_t E = lv.back().offset + lv.back().size;
   const double* table = f.tables + int64_t(region) * E * f.F;
   const uint32_t T = uint32_t(1) << f.log2_T;
@@ -205,13 +245,6 @@ void encode(const oracle_field& f, const std::vector<Level>& lv, int region, con
   out->entry.assign(f.L * 8, 0);
   out->weight.assign(f.L * 8, 0.0);
   out->index.assign(f.L * 8, 0);
-  float u[3];
-  for (int ax = 0; ax < 3; ++ax) {
-    const float inv_ext = 1.0f / (box[3 + ax] - box[ax]);
-    float v = (x[ax] - box[ax]) * inv_ext;
-    v = std::fmin(std::fmax(v, 0.0f), 1.0f);
-    u[ax] = v;
-  }
   for (int l = 0; l < f.L; ++l) {
     const int32_t N = lv[l].N;
     int32_t c[3];
@@ -295,7 +328,17 @@ struct RayEval {
   std::vector<double> rgb;  // [n][3]
   std::vector<Encoded> enc;
   std::vector<MlpAct> act;
+  std::vector<char> skip;   // 1: the sample's occupancy cell is empty (density 0, not evaluated)
 };
+
+// Occupancy bit of the cell holding region coordinate u (1 without a grid).
+bool occupied(const oracle_field& f, int region, const float* u) {
+  if (!f.occupancy) return true;
+  const int64_t G = f.occ_res;
+  const int64_t words = (G * G * G + 31) / 32;
+  const int64_t cell = grid_cell(u[0], f.occ_res) + G * (grid_cell(u[1], f.occ_res) + G * grid_cell(u[2], f.occ_res));
+  return ((f.occupancy[int64_t(region) * words + cell / 32] >> (cell % 32)) & 1u) != 0;
+}
 
 void eval_ray(const oracle_field& f, const oracle_sampling& s, const std::vector<Level>& lv, const float* o,
               const float* d, bool keep, RayEval* re) {
@@ -305,6 +348,7 @@ void eval_ray(const oracle_field& f, const oracle_sampling& s, const std::vector
   re->delta.resize(n);
   re->sigma.resize(n);
   re->rgb.resize(3 * n);
+  re->skip.assign(n, 0);
   if (keep) {
     re->enc.resize(n);
     re->act.resize(n);
@@ -317,10 +361,18 @@ void eval_ray(const oracle_field& f, const oracle_sampling& s, const std::vector
     const float dl = q.b - q.a;
     float x[3];
     for (int ax = 0; ax < 3; ++ax) x[ax] = o[ax] + tb * d[ax];
-    encode(f, lv, q.region, x, &enc);
-    mlp_forward(f, q.region, enc.feat.data(), &act);
     re->tbar[i] = tb;
     re->delta[i] = dl;
+    float u[3];
+    region_u(f.boxes + 6 * q.region, x, u);
+    if (!occupied(f, q.region, u)) {
+      re->skip[i] = 1;
+      re->sigma[i] = 0.0;
+      for (int c = 0; c < 3; ++c) re->rgb[3 * i + c] = 0.0;
+      continue;
+    }
+    encode(f, lv, q.region, x, &enc);
+    mlp_forward(f, q.region, enc.feat.data(), &act);
     re->sigma[i] = std::exp(act.o[0]);
     for (int c = 0; c < 3; ++c) re->rgb[3 * i + c] = sigmoid(act.o[1 + c]);
     if (keep) {
@@ -484,6 +536,7 @@ void field_adjoint(const oracle_field& f, const RayEval& re, const double* g_sig
   const int64_t P = mlp_params(I, W);
   std::vector<double> gz2(W), gz1(W), gfeat(I);
   for (size_t i = 0; i < re.iv.size(); ++i) {
+    if (re.skip[i]) continue;  // density fixed at 0: no parameter reaches it
     const int k = re.iv[i].region;
     const double* p = f.mlp + int64_t(k) * P;
     const double* W1 = p;
@@ -586,6 +639,50 @@ double loss_impl(const oracle_field& f, const oracle_sampling& s, int64_t R, con
     sd += dist[r];
   }
   return sp / (3.0 * (double)R) + lambda * sd / (double)R;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC 2011): ten rounds of two 32x32 -> 64-bit products mixed into
+// the 128-bit counter, the 64-bit key advanced by the Weyl constants between
+// rounds.
+void philox4x32_10(const uint32_t* ctr_in, const uint32_t* key_in, uint32_t* out) {
+  const uint64_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+  const uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k[2] = {key_in[0], key_in[1]};
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k[0] += kW0;
+      k[1] += kW1;
+    }
+    const uint64_t p0 = kM0 * c[0], p1 = kM1 * c[2];
+    const uint32_t n0 = uint32_t(p1 >> 32) ^ c[1] ^ k[0];
+    const uint32_t n1 = uint32_t(p1);
+    const uint32_t n2 = uint32_t(p0 >> 32) ^ c[3] ^ k[1];
+    const uint32_t n3 = uint32_t(p0);
+    c[0] = n0;
+    c[1] = n1;
+    c[2] = n2;
+    c[3] = n3;
+  }
+  for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+// Point drawn in cell (cx, cy, cz) of region `region` at refresh `step`:
+// counter (cell, region, step lo, step hi), key (seed lo, seed hi); each of the
+// first three words gives xi = (word >> 8) / 2^24 in [0, 1) and
+// u = ((float)c + xi) / G in FP32.
+void cell_point(int64_t cell, int region, int32_t G, const int32_t* c3, int64_t step, uint64_t seed, float* u) {
+  const uint32_t ctr[4] = {uint32_t(cell), uint32_t(region), uint32_t(uint64_t(step)),
+                           uint32_t(uint64_t(step) >> 32)};
+  const uint32_t key[2] = {uint32_t(seed), uint32_t(seed >> 32)};
+  uint32_t r[4];
+  philox4x32_10(ctr, key, r);
+  for (int ax = 0; ax < 3; ++ax) {
+    const float xi = (float)(r[ax] >> 8) * (1.0f / 16777216.0f);
+    u[ax] = ((float)c3[ax] + xi) / (float)G;
+  }
 }
 
 }  // namespace
@@ -712,7 +809,8 @@ void oracle_composite(int64_t nseg, const double* parts, double* out) { composit
 
 // Full render of rays. mode 0: single pass (i); mode 1: partitioned (ii).
 // rgb [R][3], depth/opacity/dist/tfinal [R]. n_samples [R] receives the
-// interval count of each ray.
+// number of samples evaluated on each ray: every interval, or with an
+// occupancy grid those in occupied cells.
 void oracle_render(const oracle_field* f, const oracle_sampling* s, int64_t R, const float* ro, const float* rd,
                    int32_t mode, double* rgb, double* depth, double* opacity, double* dist, double* tfinal,
                    int32_t* n_samples) {
@@ -727,7 +825,7 @@ void oracle_render(const oracle_field* f, const oracle_sampling* s, int64_t R, c
     opacity[r] = out[4];
     dist[r] = out[5];
     tfinal[r] = out[6];
-    n_samples[r] = (int32_t)re.iv.size();
+    n_samples[r] = (int32_t)(re.iv.size() - std::count(re.skip.begin(), re.skip.end(), 1));
   });
 }
 
@@ -847,6 +945,42 @@ void oracle_blob_render(const oracle_field* f, const oracle_sampling* s, int64_t
     depth[r] = D;
     opacity[r] = A;
   });
+}
+
+
+// Philox4x32-10 of one counter / key (for known-answer checks).
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
+
+// Occupancy-grid refresh of all K regions (grid G^3 per region, cells
+// x-fastest: cell = x + G (y + G z)). density [K][G^3] is updated in place to
+// max(decay * density, sigma(u_cell)); bits [K][ceil(G^3/32)] receive
+// density > threshold (cell c in word c / 32, bit c % 32; unused bits 0).
+// points (optional, [K][G^3][3]) receives the drawn region coordinates.
+void oracle_occupancy_update(const oracle_field* f, int32_t G, int64_t step, uint64_t seed, double decay,
+                             double threshold, double* density, uint32_t* bits, float* points) {
+  const std::vector<Level> lv = make_levels(f->L, f->level_res, f->log2_T);
+  const int64_t cells = int64_t(G) * G * G;
+  const int64_t words = (cells + 31) / 32;
+  for (int64_t i = 0; i < int64_t(f->K) * words; ++i) bits[i] = 0u;
+  std::vector<char> on(size_t(f->K) * cells, 0);
+  parallel_for(int64_t(f->K) * cells, [&](int64_t i, int) {
+    const int region = int(i / cells);
+    const int64_t cell = i % cells;
+    const int32_t c3[3] = {int32_t(cell % G), int32_t((cell / G) % G), int32_t(cell / (int64_t(G) * G))};
+    float u[3];
+    cell_point(cell, region, G, c3, step, seed, u);
+    if (points)
+      for (int ax = 0; ax < 3; ++ax) points[3 * i + ax] = u[ax];
+    Encoded enc;
+    MlpAct act;
+    encode_u(*f, lv, region, u, &enc);
+    mlp_forward(*f, region, enc.feat.data(), &act);
+    const double sigma = std::exp(act.o[0]);
+    density[i] = std::max(decay * density[i], sigma);
+    on[size_t(i)] = density[i] > threshold;
+  });
+  for (int64_t i = 0; i < int64_t(f->K) * cells; ++i)
+    if (on[size_t(i)]) bits[(i / cells) * words + (i % cells) / 32] |= 1u << ((i % cells) % 32);
 }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-"""Oracle of the spatial partitioning (Sec. 3.4 "Spatial Partitioning" and the
+"""Oracle of the spatial partitioning (Sec. 4.4 "Spatial Partitioning" and the
 appendix section of the same name with its partition-scheme figure).
 
 TEST INFRASTRUCTURE ONLY (callers: the test suite). Plain, recursive numpy

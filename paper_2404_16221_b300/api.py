@@ -38,10 +38,12 @@ class PartitionedField:
 
     boxes [K][6] float32; tables [K][E][F] float32 (or float16);
     mlp [K][P] float32 (or bf16/fp16; uint8 holding e4m3 with mlp_scales).
+    occupancy: optional [K][ceil(G^3/32)] int32/uint32 cell bits of a G^3 grid
+    per region (G = occ_res); samples in cells with a clear bit are skipped.
     """
 
     def __init__(self, boxes, level_res, log2_T: int, tables, mlp, F: int = 2, mlp_in: int = 32, width: int = 64,
-                 mlp_scales=None, device="cuda"):
+                 mlp_scales=None, device="cuda", occupancy=None, occ_res: int = 0):
         self.device = torch.device(device)
         self.boxes = torch.as_tensor(boxes, dtype=torch.float32).reshape(-1, 6).contiguous().to(self.device)
         self.level_res = [int(v) for v in level_res]
@@ -54,6 +56,17 @@ class PartitionedField:
         self.mlp = torch.as_tensor(mlp).to(self.device).reshape(self.K, self.P).contiguous()
         self.mlp_scales = None if mlp_scales is None else torch.as_tensor(
             mlp_scales, dtype=torch.float32).to(self.device).reshape(self.K, 3).contiguous()
+        self.set_occupancy(occupancy, occ_res)
+
+    def set_occupancy(self, occupancy, occ_res: int = 0):
+        """Attach (or, with None, drop) an occupancy bitfield [K][words]."""
+        self.occ_res = int(occ_res) if occupancy is not None else 0
+        self.occupancy = None
+        if occupancy is not None:
+            occ = torch.as_tensor(occupancy)
+            if occ.dtype != torch.int32:  # uint32 bit patterns travel as int32
+                occ = torch.from_numpy(np.ascontiguousarray(np.asarray(occ.cpu().numpy(), np.uint32).view(np.int32)))
+            self.occupancy = occ.to(self.device).reshape(self.K, occupancy_words(self.occ_res)).contiguous()
 
     def desc(self) -> N.FieldDesc:
         d = N.FieldDesc()
@@ -66,7 +79,47 @@ class PartitionedField:
         d.table_dtype = _DTYPE_CODE[self.tables.dtype]
         d.mlp_dtype = _DTYPE_CODE[self.mlp.dtype]
         d.mlp_scales = None if self.mlp_scales is None else self.mlp_scales.data_ptr()
+        d.occupancy = None if self.occupancy is None else self.occupancy.data_ptr()
+        d.occ_res = self.occ_res
         return d
+
+
+def occupancy_words(G: int) -> int:
+    """32-bit words of one region's G^3-cell occupancy bitfield."""
+    return (int(G) ** 3 + 31) // 32
+
+
+class OccupancyGrid:
+    """Per-region G^3 occupancy grid (Sec. 5.1's spatial skipping, the cited
+    Instant-NGP grid): a density estimate per cell and the bitfield the
+    renderer skips by. Starts with density 0 and every cell occupied;
+    ``update`` refreshes it from an FP32 field (nerfxl_occupancy_update)."""
+
+    def __init__(self, K: int, G: int, device="cuda", decay: float = 0.95, threshold: float = 0.01, seed: int = 0):
+        self.K, self.G = int(K), int(G)
+        self.decay, self.threshold, self.seed = float(decay), float(threshold), int(seed)
+        self.density = torch.zeros(self.K, self.G ** 3, dtype=torch.float32, device=device)
+        self.bits = torch.full((self.K, occupancy_words(self.G)), -1, dtype=torch.int32, device=device)
+        tail = self.G ** 3 % 32
+        if tail:
+            self.bits[:, -1] = (1 << tail) - 1
+        self.updates = 0
+
+    def attach(self, field: PartitionedField):
+        """Make ``field`` render with this grid (shares the bit tensor)."""
+        field.occupancy, field.occ_res = self.bits, self.G
+
+    def update(self, fp32_field: PartitionedField, stream=None):
+        """One refresh from an FP32 field (tables and MLP, e.g. the training masters)."""
+        st = N.lib().nerfxl_occupancy_update(C_ref(fp32_field.desc()), self.G, self.updates, self.seed, self.decay,
+                                             self.threshold, N._ptr(self.density), N._ptr(self.bits),
+                                             N._stream(stream))
+        N.check(st, "nerfxl_occupancy_update")
+        self.updates += 1
+
+    def occupied_fraction(self) -> float:
+        bits = self.bits.cpu().numpy().view(np.uint32)
+        return float(np.unpackbits(bits.view(np.uint8), bitorder="little").sum()) / (self.K * self.G ** 3)
 
 
 def _rays(rays_o, rays_d, device):
@@ -303,7 +356,7 @@ def dequantize_mlp_e4m3(q, scales):
 
 
 def partition_boxes(points, root, levels: int):
-    """Spatial partitioning (Sec. 3.4): 2^levels disjoint boxes [K][6] with
+    """Spatial partitioning (Sec. 4.4): 2^levels disjoint boxes [K][6] with
     balanced point counts, and the counts (host numpy arrays)."""
     pts = np.ascontiguousarray(np.asarray(points, np.float32).reshape(-1, 3))
     root = np.ascontiguousarray(np.asarray(root, np.float32).reshape(6))

@@ -225,8 +225,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
       gA = g1.x;
       gD = g1.y;
       gL = g1.z;
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
       const int i = c * kWarp + lane;
-      valid = i < seg_n(sd);
+      valid = i < ss.n;
       if (valid) {
         float o[3], d[3];
 #pragma unroll
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
           d[ax] = p.rays_d[3 * (size_t)ray + ax];
         }
         float a, b;
-        segment_interval(sd, h.tn, h.delta, i, a, b);
+        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
         const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
         dl = __fsub_rn(b, a);
         tr = __fsub_rn(tbar, h.tn);
@@ -429,7 +430,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
     return set_error(NERFXL_E_WORKSPACE, "backward needs the forward's workspace sized with for_backward=1");
   if (n_rays == 0) return NERFXL_OK;
   char* ws = static_cast<char*>(workspace);
-  const SampParams sp = samp_params(f, s);
+  const SampParams sp = samp_params(f, s, ws, L);
   float4* dpart = reinterpret_cast<float4*>(ws + L.dpartials);
   const bool tc = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
   if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");

@@ -109,7 +109,7 @@ nerfxl_status nerfxl_debug_segments(const nerfxl_field* f, const nerfxl_sampling
   if (!workspace || ws_bytes < L.total) return set_error(NERFXL_E_WORKSPACE, "workspace too small");
   if (max_seg < 1) return set_error(NERFXL_E_INVALID, "max_seg < 1");
   char* ws = static_cast<char*>(workspace);
-  const SampParams sp = samp_params(f, s);
+  const SampParams sp = samp_params(f, s, ws, L);
   st = run_sampling(f, sp, n_rays, rays_o, rays_d, ws, L, stream);
   if (st != NERFXL_OK || n_rays == 0) return st;
   k_debug_seg_out<<<(int)((n_rays + 127) / 128), 128, 0, stream>>>(

@@ -44,12 +44,20 @@ struct LevelParams {
   uint32_t E;                  // entries per region
 };
 
-// Sampling description shared by the kernels.
+// Sampling description shared by the kernels. With an occupancy grid the
+// samples of a segment are the intervals whose cell is occupied: seg_keep
+// holds, per segment, their count (low 16 bits) and the first slot of their
+// list in kept (high 16 bits); kept lists, per ray, interval indices within
+// their segment in increasing order. Without a grid seg_keep is NULL and
+// sample i of a segment is its interval i.
 struct SampParams {
   int32_t S;          // grid intervals over [tn, tf]
   int32_t max_seg;    // segments per ray bound (<= kMaxSeg)
   int32_t max_chunk;  // chunks per ray bound
   float t_min;
+  const int32_t* seg_keep;  // [R][max_seg], or NULL
+  const uint16_t* kept;     // [R][max_int]
+  int32_t max_int;          // list slots per ray (intervals per ray bound)
 };
 
 // One ray's sampling header.
@@ -72,6 +80,24 @@ __device__ __forceinline__ int seg_jlo(const SegDesc& s) { return s.jlo_n & 0xFF
 __device__ __forceinline__ int seg_n(const SegDesc& s) { return (s.jlo_n >> 16) & 0xFFFF; }
 __device__ __forceinline__ int seg_region(const SegDesc& s) { return s.reg_cb & 0xFFFF; }
 __device__ __forceinline__ int seg_chunk_base(const SegDesc& s) { return (s.reg_cb >> 16) & 0xFFFF; }
+
+// Samples of one segment: their count and where their interval list starts
+// (list < 0: sample i is interval i).
+struct SegSamples {
+  int n;
+  int64_t list;
+};
+
+__device__ __forceinline__ SegSamples seg_samples(const SampParams& sp, const SegDesc& sd, size_t ray, int seg) {
+  if (!sp.seg_keep) return {seg_n(sd), -1};
+  const int kp = sp.seg_keep[ray * sp.max_seg + seg];
+  return {kp & 0xFFFF, (int64_t)ray * sp.max_int + ((kp >> 16) & 0xFFFF)};
+}
+
+// Interval index of sample i (< n) of a segment.
+__device__ __forceinline__ int sample_interval(const SampParams& sp, const SegSamples& ss, int i) {
+  return ss.list < 0 ? i : (int)sp.kept[ss.list + i];
+}
 
 // ---------------------------------------------------------------------------
 // Geometry (Sec. 4.2).

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
       s.reg_cb = (sreg[k] & 0xFFFF) | (cbase << 16);
       segs[r * sp.max_seg + k] = s;
       const int nch = (n + kWarp - 1) / kWarp;
-      atomicAdd(&s_cnt[sreg[k]], nch);
+      if (counts) atomicAdd(&s_cnt[sreg[k]], nch);
       cbase += nch;
       n_samples += n;
     }
@@ -84,6 +84,98 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
     hdr[r] = h;
     atomicAdd(&s_samples, (unsigned long long)n_samples);
     atomicAdd(&s_chunks, (unsigned long long)cbase);
+  }
+  __syncthreads();
+  if (!counts) return;  // the occupancy pass buckets the kept samples
+  for (int i = threadIdx.x; i < K; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
+  if (threadIdx.x == 0) {
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
+    atomicAdd(stats + 0, s_samples);
+    atomicAdd(stats + 1, s_chunks);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_skip_empty: occupancy-grid skipping, one warp per ray. The lanes test 32
+// intervals of a segment at a time: the interval's sample point (the same
+// FP32 operations as the field kernels) falls in region cell
+// min(floor(u G), G - 1) per axis, and the interval is kept if that cell's bit
+// is set. A ballot compacts the kept interval indices, in order, into the
+// ray's list; the segment's chunk base, the ray's chunk count, the per-region
+// chunk histogram and the sample / chunk counters are then those of the kept
+// samples (a segment left empty has no chunk).
+
+__global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ rays_o, const float* __restrict__ rays_d,
+                                                    int64_t R, const float* __restrict__ boxes, int K, SampParams sp,
+                                                    const uint32_t* __restrict__ occ, int G, RayHdr* __restrict__ hdr,
+                                                    SegDesc* __restrict__ segs, int32_t* __restrict__ seg_keep,
+                                                    uint16_t* __restrict__ kept, int32_t* __restrict__ counts,
+                                                    int32_t* __restrict__ err) {
+  extern __shared__ float s_mem[];
+  float* s_boxes = s_mem;                                      // [K][6]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [K]
+  __shared__ unsigned long long s_samples, s_chunks;
+  for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
+  __syncthreads();
+
+  const int lane = threadIdx.x % kWarp;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  if (r < R) {  // warp-uniform
+    const RayHdr h = hdr[r];
+    float o[3], d[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      o[ax] = rays_o[3 * r + ax];
+      d[ax] = rays_d[3 * r + ax];
+    }
+    const size_t words = ((size_t)G * G * G + 31) / 32;
+    int cbase = 0, list = 0;
+    for (int k = 0; k < h.nseg; ++k) {
+      SegDesc sd = segs[r * sp.max_seg + k];
+      const int n = seg_n(sd), reg = seg_region(sd);
+      const uint32_t* bits = occ + (size_t)reg * words;
+      const float* box = s_boxes + 6 * reg;
+      int nk = 0;
+      for (int i0 = 0; i0 < n; i0 += kWarp) {
+        const int i = i0 + lane;
+        bool keep = false;
+        if (i < n) {
+          float a, b;
+          segment_interval(sd, h.tn, h.delta, i, a, b);
+          const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+          float x[3], u[3];
+          sample_point(o, d, tbar, x);
+          region_coord(box, x, u);
+          int c[3];
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            float fr;
+            level_cell(u[ax], G, c[ax], fr);
+          }
+          const uint32_t cell = (uint32_t)c[0] + (uint32_t)G * ((uint32_t)c[1] + (uint32_t)G * (uint32_t)c[2]);
+          keep = (__ldg(bits + (cell >> 5)) >> (cell & 31u)) & 1u;
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) kept[r * sp.max_int + list + nk + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+        nk += __popc(m);
+      }
+      const int nch = (nk + kWarp - 1) / kWarp;
+      if (lane == 0) {
+        seg_keep[r * sp.max_seg + k] = nk | (list << 16);
+        segs[r * sp.max_seg + k].reg_cb = (reg & 0xFFFF) | (cbase << 16);
+        if (nch) atomicAdd(&s_cnt[reg], nch);
+      }
+      cbase += nch;
+      list += nk;
+    }
+    if (lane == 0) {
+      hdr[r].nchunk = cbase;
+      atomicAdd(&s_samples, (unsigned long long)list);
+      atomicAdd(&s_chunks, (unsigned long long)cbase);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < K; i += blockDim.x)
@@ -133,7 +225,7 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
     nseg = hdr[r].nseg;
     for (int k = 0; k < nseg; ++k) {
       const SegDesc s = segs[r * sp.max_seg + k];
-      off[k] = atomicAdd(&s_cnt[seg_region(s)], (seg_n(s) + kWarp - 1) / kWarp);
+      off[k] = atomicAdd(&s_cnt[seg_region(s)], (seg_samples(sp, s, r, k).n + kWarp - 1) / kWarp);
     }
   }
   __syncthreads();
@@ -142,7 +234,7 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
   for (int k = 0; k < nseg; ++k) {
     const SegDesc s = segs[r * sp.max_seg + k];
     const int reg = seg_region(s);
-    const int nch = (seg_n(s) + kWarp - 1) / kWarp;
+    const int nch = (seg_samples(sp, s, r, k).n + kWarp - 1) / kWarp;
     const int dst = base[reg] + s_base[reg] + off[k];
     for (int c = 0; c < nch; ++c) chunks[dst + c] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
   }
@@ -208,13 +300,14 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       o[ax] = p.rays_o[3 * (size_t)ray + ax];
       d[ax] = p.rays_d[3 * (size_t)ray + ax];
     }
+    const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
     const int i = c * kWarp + lane;
-    const bool valid = i < seg_n(sd);
+    const bool valid = i < ss.n;
     float feat[kIn];
     float tbar = 0.0f, dl = 0.0f;
     if (valid) {
       float a, b;
-      segment_interval(sd, h.tn, h.delta, i, a, b);
+      segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
       tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
       dl = __fsub_rn(b, a);
       float x[3], u[3];
@@ -415,6 +508,12 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   L.base = take(sizeof(int32_t) * (K + 1));
   L.ray_hdr = take(sizeof(RayHdr) * R);
   L.segs = take(sizeof(SegDesc) * R * ms);
+  L.max_int = s->n_samples + ms - 1;
+  L.seg_keep = L.kept = 0;
+  if (f->occupancy) {  // before the backward-only regions: forward and backward layouts agree
+    L.seg_keep = take(sizeof(int32_t) * R * ms);
+    L.kept = take(sizeof(uint16_t) * R * L.max_int);
+  }
   L.chunk_cap = (int64_t)R * mc + (int64_t)kChunksPerTile * K;
   L.chunks = take(sizeof(uint2) * L.chunk_cap);
   L.partials = take(sizeof(float4) * 2 * R * mc);
@@ -454,6 +553,8 @@ nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t 
   if (max_chunks(s->n_samples, ms) > 0xFFFF) return fail(NERFXL_E_UNSUPPORTED, "too many chunks per ray");
   if (R < 0 || R > (int64_t)0x7FFFFFFF) return fail(NERFXL_E_INVALID, "n_rays out of range");
   if (!f->boxes || !f->tables || !f->mlp) return fail(NERFXL_E_INVALID, "null field pointer");
+  if (f->occupancy && (f->occ_res < 1 || f->occ_res > 1024))
+    return fail(NERFXL_E_INVALID, "occupancy grid resolution must be in [1, 1024]");
   return NERFXL_OK;
 }
 
@@ -487,6 +588,18 @@ SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s) {
   sp.max_seg = effective_max_seg(f, s);
   sp.max_chunk = max_chunks(s->n_samples, sp.max_seg);
   sp.t_min = s->t_min;
+  sp.seg_keep = nullptr;
+  sp.kept = nullptr;
+  sp.max_int = s->n_samples + sp.max_seg - 1;
+  return sp;
+}
+
+SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s, char* ws, const Layout& L) {
+  SampParams sp = samp_params(f, s);
+  if (f->occupancy) {
+    sp.seg_keep = reinterpret_cast<const int32_t*>(ws + L.seg_keep);
+    sp.kept = reinterpret_cast<const uint16_t*>(ws + L.kept);
+  }
   return sp;
 }
 
@@ -506,12 +619,23 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
   const int blocks = (int)((R + threads - 1) / threads);
   if (R > 0) {
     const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * K;
+    int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
     k_segments<<<blocks, threads, smem, stream>>>(rays_o, rays_d, R, f->boxes, K, sp,
                                                   reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
                                                   reinterpret_cast<SegDesc*>(ws + L.segs),
-                                                  reinterpret_cast<int32_t*>(ws + L.counts), hdr_words + 0);
+                                                  f->occupancy ? nullptr : counts, hdr_words + 0);
     nerfxl_status st = launch_check("k_segments");
     if (st != NERFXL_OK) return st;
+    if (f->occupancy) {
+      if (!sp.seg_keep) return set_error(NERFXL_E_INVALID, "occupancy lists not attached to the sampling");
+      const int64_t warps_per_block = threads / kWarp;
+      k_skip_empty<<<(int)((R + warps_per_block - 1) / warps_per_block), threads, smem, stream>>>(
+          rays_o, rays_d, R, f->boxes, K, sp, f->occupancy, f->occ_res, reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
+          reinterpret_cast<SegDesc*>(ws + L.segs), reinterpret_cast<int32_t*>(ws + L.seg_keep),
+          reinterpret_cast<uint16_t*>(ws + L.kept), counts, hdr_words + 0);
+      st = launch_check("k_skip_empty");
+      if (st != NERFXL_OK) return st;
+    }
   }
   k_region_scan<<<1, 32, 0, stream>>>(reinterpret_cast<int32_t*>(ws + L.counts), K, kChunksPerTile,
                                       reinterpret_cast<int32_t*>(ws + L.base), reinterpret_cast<uint2*>(ws + L.chunks),
@@ -599,7 +723,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   const Layout L = layout(f, s, n_rays, 0);
   if (!workspace || ws_bytes < L.total) return set_error(NERFXL_E_WORKSPACE, "workspace too small");
   char* ws = static_cast<char*>(workspace);
-  const SampParams sp = samp_params(f, s);
+  const SampParams sp = samp_params(f, s, ws, L);
   st = run_sampling(f, sp, n_rays, rays_o, rays_d, ws, L, stream);
   if (st != NERFXL_OK) return st;
   if (n_rays == 0) return NERFXL_OK;

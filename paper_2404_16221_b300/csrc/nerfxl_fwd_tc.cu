@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
     SegDesc sd = {0.0f, 0.0f, 0, 0};
-    int c = 0;
+    int c = 0, seg_count = 0;
     uint32_t ray = 0;
     if (chunk_ok) {
       ray = ref.x;
@@ -240,8 +240,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       c = ref.y & 0xFFFF;
       const RayHdr h = p.hdr[ray];
       sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+      seg_count = ss.n;
       const int i = c * kWarp + lane;
-      valid = i < seg_n(sd);
+      valid = i < ss.n;
       if (valid) {
         float o[3], d[3];
 #pragma unroll
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
           d[ax] = p.rays_d[3 * (size_t)ray + ax];
         }
         float a, b;
-        segment_interval(sd, h.tn, h.delta, i, a, b);
+        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
         const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
         dl = __fsub_rn(b, a);
         tr = __fsub_rn(tbar, h.tn);
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       if (g == 0) {
         __stcs(geo + 4 * kTcRows + row, dl);
         if (lane == 0) {
-          const int n_valid = chunk_ok ? min(kWarp, seg_n(sd) - c * kWarp) : 0;
+          const int n_valid = chunk_ok ? min(kWarp, seg_count - c * kWarp) : 0;
           reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] = n_valid;
           if (chunk_ok) p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = t * kTcChunks + q;
         }

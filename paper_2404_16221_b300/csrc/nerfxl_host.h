@@ -18,6 +18,9 @@ struct Layout {
   size_t base;       // int32[K+1] first chunk slot of each region bucket
   size_t ray_hdr;    // RayHdr[R]
   size_t segs;       // SegDesc[R][max_seg]
+  // Occupancy skipping (fields with an occupancy grid; 0 otherwise):
+  size_t seg_keep;   // int32[R][max_seg]: kept samples | first list slot << 16
+  size_t kept;       // uint16[R][max_int]: kept interval indices within their segment
   size_t chunks;     // uint2[chunk_cap]
   size_t partials;   // float4[R][max_chunk][2]
   size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
@@ -33,7 +36,7 @@ struct Layout {
   size_t total;
   int64_t rec_tiles; // tiles the record regions hold
   int64_t chunk_cap;
-  int max_seg, max_chunk;
+  int max_seg, max_chunk, max_int;
 };
 
 const char* last_error();
@@ -44,7 +47,10 @@ int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s);
 int max_chunks(int S, int max_seg);
 Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int for_backward);
 LevelParams level_params(const nerfxl_field* f);
+// Sampling parameters; the second form also points the kernels at the
+// workspace's occupancy lists when the field has an occupancy grid.
 SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s);
+SampParams samp_params(const nerfxl_field* f, const nerfxl_sampling* s, char* ws, const Layout& L);
 nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t R, const float* rays_o,
                            const float* rays_d, char* ws, const Layout& L, cudaStream_t stream);
 // Records the instrumentation event `which` (0 = before, 1 = after the

@@ -1,5 +1,5 @@
 // Spatial partitioning of the scene into 2^n disjoint boxes with balanced
-// content (Sec. 3.4 "Spatial Partitioning"; the appendix's partition scheme):
+// content (Sec. 4.4 "Spatial Partitioning"; the appendix's partition scheme):
 // recursively, split a box at the plane where the CDF of the points inside it
 // along an axis is 0.5, choosing among the three axes the split whose two
 // boxes are closest to cubic. Host code: it runs once per scene on a point

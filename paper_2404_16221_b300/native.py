@@ -33,7 +33,8 @@ class FieldDesc(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("F", C.c_int32), ("log2_T", C.c_int32),
                 ("mlp_in", C.c_int32), ("mlp_width", C.c_int32), ("level_res", C.c_int32 * MAX_LEVELS),
                 ("boxes", C.c_void_p), ("tables", C.c_void_p), ("mlp", C.c_void_p), ("table_dtype", C.c_int32),
-                ("mlp_dtype", C.c_int32), ("mlp_scales", C.c_void_p)]
+                ("mlp_dtype", C.c_int32), ("mlp_scales", C.c_void_p), ("occupancy", C.c_void_p),
+                ("occ_res", C.c_int32)]
 
 
 class AdamDesc(C.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_wait_probe": (C.c_int, [_vp, C.c_uint32, _i32, _vp]),
     "nerfxl_partition": (C.c_int, [_vp, _i64, _vp, _i32, _vp, _vp]),
+    "nerfxl_occupancy_update": (C.c_int, [_FP, _i32, _i64, C.c_uint64, C.c_float, C.c_float, _vp, _vp, _vp]),
     "nerfxl_region_chunks": (C.c_int, [_vp, _sz, _i32, _vp, _vp]),
     "nerfxl_debug_segments": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_samples": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

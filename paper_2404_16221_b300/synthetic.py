@@ -156,14 +156,44 @@ def uniform_params(shape, scale: float, seed: int, purpose: str) -> np.ndarray:
     return rng(seed, purpose).uniform(-scale, scale, size=shape).astype(np.float32)
 
 
-def blobs(n: int, seed: int, lo=-0.8, hi=0.8):
-    """[n][8] = mu xyz ~ U[lo,hi]^3, s ~ logU[0.05,0.2], a ~ U[5,50], rgb ~ U[0,1]^3."""
+def blobs(n: int, seed: int, lo=-0.8, hi=0.8, s_range=(0.05, 0.2), a_range=(5.0, 50.0)):
+    """[n][8] = mu xyz ~ U[lo,hi]^3, s ~ logU[s_range], a ~ U[a_range], rgb ~ U[0,1]^3."""
     g = rng(seed, "blobs")
     mu = g.uniform(lo, hi, (n, 3))
-    s = np.exp(g.uniform(math.log(0.05), math.log(0.2), n))
-    a = g.uniform(5.0, 50.0, n)
+    s = np.exp(g.uniform(math.log(s_range[0]), math.log(s_range[1]), n))
+    a = g.uniform(a_range[0], a_range[1], n)
     rgb = g.uniform(0.0, 1.0, (n, 3))
     return np.concatenate([mu, s[:, None], a[:, None], rgb], 1)
+
+
+def sparse_blobs(seed: int):
+    """A sparse blob scene: 24 small dense blobs in [-0.6, 0.6]^3 (s in
+    [0.04, 0.1], a in [20, 100]); about 10% of the [-1, 1]^3 volume has
+    density above 0.4, the share of empty space of real captures."""
+    return blobs(24, seed, -0.6, 0.6, (0.04, 0.1), (20.0, 100.0))
+
+
+def blob_occupancy(boxes, blob_params, G: int, threshold: float) -> np.ndarray:
+    """A stand-in for the occupancy grid of a field trained on a blob scene:
+    per region [K][ceil(G^3/32)] uint32 words whose bit c % 32 of word c / 32
+    is set where the blob density at the centre of cell c = x + G (y + G z)
+    exceeds threshold."""
+    boxes = np.asarray(boxes, np.float64).reshape(-1, 6)
+    K = len(boxes)
+    c = (np.arange(G) + 0.5) / G
+    cz, cy, cx = np.meshgrid(c, c, c, indexing="ij")  # x fastest in C order
+    u = np.stack([cx, cy, cz], -1).reshape(-1, 3)
+    words = (G ** 3 + 31) // 32
+    out = np.zeros((K, words), np.uint32)
+    for k in range(K):
+        x = boxes[k, :3] + u * (boxes[k, 3:] - boxes[k, :3])
+        sig = np.zeros(len(x))
+        for q in blob_params:
+            sig += q[4] * np.exp(-((x - q[:3]) ** 2).sum(-1) / (2.0 * q[3] ** 2))
+        on = np.zeros(words * 32, bool)
+        on[:G ** 3] = sig > threshold
+        out[k] = np.packbits(on.reshape(-1, 32), axis=-1, bitorder="little").view(np.uint32).reshape(-1)
+    return out
 
 
 @dataclasses.dataclass
@@ -274,7 +304,7 @@ def field_params_device(w: Workload, E: int, P: int, device, table_std: float = 
 
 
 # ---------------------------------------------------------------------------
-# Scene content for the spatial partitioning (Sec. 3.4): an SfM-like point
+# Scene content for the spatial partitioning (Sec. 4.4): an SfM-like point
 # cloud, or samples of training rays when no point cloud is available.
 
 def scene_root(w: Workload) -> np.ndarray:

@@ -1,4 +1,4 @@
-"""Rendering on regions from the spatial partitioning (Sec. 3.4): the boxes are
+"""Rendering on regions from the spatial partitioning (Sec. 4.4): the boxes are
 no longer a uniform grid, and the renderer must still match the oracle and
 the partitioned render must still equal the single pass; the partition spreads
 samples over the regions more evenly than the uniform grid."""

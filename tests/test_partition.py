@@ -1,4 +1,4 @@
-"""Spatial partitioning (Sec. 3.4 "Spatial Partitioning"): the oracle against
+"""Spatial partitioning (Sec. 4.4 "Spatial Partitioning"): the oracle against
 properties the paper's description fixes, and the library's host
 implementation against the oracle (bit for bit)."""
 import numpy as np

@@ -32,7 +32,7 @@ class _Field(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("F", C.c_int32), ("log2_T", C.c_int32),
                 ("mlp_in", C.c_int32), ("W", C.c_int32), ("level_res", C.c_void_p),
                 ("boxes", C.c_void_p), ("tables", C.c_void_p), ("mlp", C.c_void_p),
-                ("occupancy", C.c_void_p), ("occ_res", C.c_int32)]
+                ("occupancy", C.c_void_p), ("occ_res", C.c_int32), ("arch", C.c_int32)]
 
 
 class _Sampling(C.Structure):
@@ -75,7 +75,12 @@ def lib():
         L.oracle_hash_indices.restype = C.c_int
         L.oracle_hash_indices.argtypes = [fp, sp, C.c_int64, _f32p, _f32p, C.c_int32, _u32p]
         L.oracle_encode_points.argtypes = [fp, C.c_int64, _i32p, _f32p, _f64p, C.c_void_p]
-        L.oracle_mlp.argtypes = [fp, C.c_int64, _i32p, _f64p, _f64p]
+        L.oracle_mlp.argtypes = [fp, C.c_int64, _i32p, _f64p, C.c_void_p, _f64p]
+        L.oracle_density_params.restype = C.c_int64
+        L.oracle_density_params.argtypes = [C.c_int32, C.c_int32]
+        L.oracle_color_params.restype = C.c_int64
+        L.oracle_color_params.argtypes = [C.c_int32]
+        L.oracle_sh4.argtypes = [C.c_int64, _f64p, _f64p]
         L.oracle_render_samples.argtypes = [C.c_int64, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.oracle_render_local.argtypes = [C.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.oracle_composite.argtypes = [C.c_int64, _f64p, _f64p]
@@ -132,16 +137,24 @@ class Field:
     boxes [K][6] float32; tables [K][E][F] and mlp [K][P] promoted to float64.
     """
 
-    def __init__(self, boxes, level_res, log2_T, F, mlp_in, W, tables, mlp, occupancy=None, occ_res: int = 0):
+    def __init__(self, boxes, level_res, log2_T, F, mlp_in, W, tables, mlp, occupancy=None, occ_res: int = 0,
+                 arch: int = 0):
         self.boxes = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 6)
         self.level_res = np.ascontiguousarray(level_res, dtype=np.int32)
         self.K = self.boxes.shape[0]
         self.L = len(self.level_res)
         self.F, self.log2_T, self.mlp_in, self.W = int(F), int(log2_T), int(mlp_in), int(W)
         self.E = table_entries(self.level_res, self.log2_T)
+        self.arch = int(arch)
         self.P = mlp_params(self.mlp_in, self.W)
         self.tables = np.ascontiguousarray(tables, dtype=np.float64).reshape(self.K, self.E, self.F)
-        self.mlp = np.ascontiguousarray(mlp, dtype=np.float64).reshape(self.K, self.P)
+        if self.arch == 1:
+            # split representation: [K][density block] then the shared colour block, flat
+            self.Pd = density_params(self.mlp_in, self.W)
+            self.Pc = color_params(self.W)
+            self.mlp = np.ascontiguousarray(mlp, dtype=np.float64).reshape(self.K * self.Pd + self.Pc)
+        else:
+            self.mlp = np.ascontiguousarray(mlp, dtype=np.float64).reshape(self.K, self.P)
         # optional occupancy grid: [K][ceil(G^3/32)] uint32 cell bits, G = occ_res
         self.occ_res = int(occ_res)
         self.occupancy = None
@@ -150,18 +163,18 @@ class Field:
 
     def with_params(self, tables, mlp) -> "Field":
         return Field(self.boxes, self.level_res, self.log2_T, self.F, self.mlp_in, self.W, tables, mlp,
-                     self.occupancy, self.occ_res)
+                     self.occupancy, self.occ_res, self.arch)
 
     def with_occupancy(self, occupancy, occ_res: int) -> "Field":
         return Field(self.boxes, self.level_res, self.log2_T, self.F, self.mlp_in, self.W, self.tables, self.mlp,
-                     occupancy, occ_res)
+                     occupancy, occ_res, self.arch)
 
     def struct(self, tables=None, mlp=None) -> _Field:
         t = self.tables if tables is None else tables
         m = self.mlp if mlp is None else mlp
         occ = None if self.occupancy is None else self.occupancy.ctypes.data
         return _Field(self.K, self.L, self.F, self.log2_T, self.mlp_in, self.W, self.level_res.ctypes.data,
-                      self.boxes.ctypes.data, t.ctypes.data, m.ctypes.data, occ, self.occ_res)
+                      self.boxes.ctypes.data, t.ctypes.data, m.ctypes.data, occ, self.occ_res, self.arch)
 
 
 def occupancy_words(G: int) -> int:
@@ -230,14 +243,35 @@ def encode_points(field: Field, region, x, want_idx: bool = False):
     return (feat, idx) if want_idx else feat
 
 
-def mlp(field: Field, region, feat):
+def mlp(field: Field, region, feat, dirs=None):
+    """Raw outputs [n][4] (log density, three colour logits); the split
+    representation's colour also takes the unit view directions dirs [n][3]."""
     region = np.ascontiguousarray(region, dtype=np.int32)
     feat = np.ascontiguousarray(feat, dtype=np.float64)
     n = feat.shape[0]
     o = np.zeros((n, 4), np.float64)
+    dv = None
+    if dirs is not None:
+        dv = np.ascontiguousarray(dirs, dtype=np.float32).reshape(n, 3)
     fs = field.struct()
-    lib().oracle_mlp(C.byref(fs), n, region, feat, o)
+    lib().oracle_mlp(C.byref(fs), n, region, feat, None if dv is None else dv.ctypes.data, o)
     return o
+
+
+def density_params(mlp_in: int, W: int) -> int:
+    return int(lib().oracle_density_params(int(mlp_in), int(W)))
+
+
+def color_params(W: int) -> int:
+    return int(lib().oracle_color_params(int(W)))
+
+
+def sh4(dirs):
+    """Real spherical harmonics of degrees 0..3 (16 per direction)."""
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((len(d), 16))
+    lib().oracle_sh4(len(d), d, out)
+    return out
 
 
 def _f64(a):

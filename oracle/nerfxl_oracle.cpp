@@ -27,6 +27,14 @@
 //     colour = sigmoid(o1..o3).
 //   * Loss: mean squared RGB error + lambda * mean distortion; Adam (Kingma &
 //     Ba) with bias correction.
+//   * Split representation (App. A.1, the representation the paper trains):
+//     per region a hash encoding and a density MLP with one hidden layer,
+//     feat -> 64 -> 16 (ReLU, no biases), density = exp(g0); one colour MLP
+//     shared by all regions on [g (16), SH(d) (16)] -> 64 -> 64 -> 3, colour =
+//     sigmoid. The view direction is encoded by the real spherical harmonics
+//     of degrees 0-3 (Instant-NGP's direction encoding), written out below
+//     from their Cartesian closed forms. No appearance embedding (it is zero
+//     at novel-view rendering and there are no per-image captures here).
 //   * Occupancy grid (the spatial-skipping structure every compared method
 //     uses, Sec. 5.1; the grid is the one of the cited Instant-NGP paper): per
 //     region a G^3 grid of cells over the region box, one bit each. A sample
@@ -61,6 +69,7 @@ typedef struct {
   const double* mlp;         // [K][P]  W1[mlp_in][W] W2[W][W] W3[W][4]
   const uint32_t* occupancy; // [K][ceil(G^3/32)] cell bits, or NULL (no skipping)
   int32_t occ_res;           // G: cells per axis of each region's grid
+  int32_t arch;              // 0: one MLP per region; 1: density MLP per region + shared colour MLP
 } oracle_field;
 
 typedef struct {
@@ -134,6 +143,50 @@ std::vector<Level> make_levels(int L, const int32_t* res, int log2_T) {
 }
 
 int64_t mlp_params(int mlp_in, int W) { return int64_t(mlp_in) * W + int64_t(W) * W + int64_t(W) * 4; }
+
+// Split representation: density block Wd1 [mlp_in][W], Wd2 [W][16] per region;
+// shared colour block Wc1 [32][W], Wc2 [W][W], Wc3 [W][4] (column 3 unused).
+const int kGeo = 16;  // density MLP outputs: g0 (log density) and 15 more geometry features
+const int kSh = 16;   // spherical-harmonic coefficients of degrees 0..3
+int64_t density_params(int mlp_in, int W) { return int64_t(mlp_in) * W + int64_t(W) * kGeo; }
+int64_t color_params(int W) { return int64_t(kGeo + kSh) * W + int64_t(W) * W + int64_t(W) * 4; }
+// Elements of the field's mlp array.
+int64_t field_mlp_size(const oracle_field& f) {
+  return f.arch == 1 ? int64_t(f.K) * density_params(f.mlp_in, f.W) + color_params(f.W)
+                     : int64_t(f.K) * mlp_params(f.mlp_in, f.W);
+}
+
+// Real spherical harmonics of degrees 0..3 at the unit vector (x, y, z), with
+// the Condon-Shortley phase: Y_l^m for m = -l..l, degree by degree. Each
+// constant is the normalisation sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times
+// sqrt 2 for m != 0) folded with the Cartesian form of its associated
+// Legendre factor.
+void sh4(const double* d, double* y) {
+  const double x = d[0], yy = d[1], z = d[2];
+  const double pi = 3.14159265358979323846;
+  const double c0 = 0.5 * std::sqrt(1.0 / pi);
+  const double c1 = std::sqrt(3.0 / (4.0 * pi));
+  const double c2a = 0.5 * std::sqrt(15.0 / pi), c2b = 0.25 * std::sqrt(5.0 / pi), c2c = 0.25 * std::sqrt(15.0 / pi);
+  const double c3a = 0.25 * std::sqrt(35.0 / (2.0 * pi)), c3b = 0.5 * std::sqrt(105.0 / pi);
+  const double c3c = 0.25 * std::sqrt(21.0 / (2.0 * pi)), c3d = 0.25 * std::sqrt(7.0 / pi);
+  const double c3e = 0.25 * std::sqrt(105.0 / pi);
+  y[0] = c0;
+  y[1] = -c1 * yy;
+  y[2] = c1 * z;
+  y[3] = -c1 * x;
+  y[4] = c2a * x * yy;
+  y[5] = -c2a * yy * z;
+  y[6] = c2b * (3.0 * z * z - 1.0);
+  y[7] = -c2a * x * z;
+  y[8] = c2c * (x * x - yy * yy);
+  y[9] = -c3a * yy * (3.0 * x * x - yy * yy);
+  y[10] = c3b * x * yy * z;
+  y[11] = -c3c * yy * (5.0 * z * z - 1.0);
+  y[12] = c3d * z * (5.0 * z * z - 3.0);
+  y[13] = -c3c * x * (5.0 * z * z - 1.0);
+  y[14] = c3e * z * (x * x - yy * yy);
+  y[15] = -c3a * x * (x * x - 3.0 * yy * yy);
+}
 
 // ---------------------------------------------------------------------------
 // Geometry, in the prescribed FP32 operation order (one IEEE rounding per op).
@@ -284,12 +337,67 @@ void encode_u(const oracle_field& f, const std::vector<Level>& lv, int region, c
 
 // ---------------------------------------------------------------------------
 // MLP: z1 = W1^T feat, h1 = relu(z1), z2 = W2^T h1, h2 = relu(z2), o = W3^T h2.
+// Split representation: z1 = Wd1^T feat, h1 = relu(z1), g = Wd2^T h1 (o0 = g0);
+// xc = [g, SH(d)], z2 = Wc1^T xc, h2 = relu(z2), z3 = Wc2^T h2, h3 = relu(z3),
+// o1..3 = Wc3^T h3.
 struct MlpAct {
   std::vector<double> z1, h1, z2, h2;
+  std::vector<double> xc, z3, h3;  // split representation only
   double o[4];
 };
 
-void mlp_forward(const oracle_field& f, int region, const double* feat, MlpAct* a) {
+void mlp_forward_split(const oracle_field& f, int region, const double* feat, const float* dir, MlpAct* a) {
+  const int W = f.W, I = f.mlp_in;
+  const double* Wd1 = f.mlp + int64_t(region) * density_params(I, W);
+  const double* Wd2 = Wd1 + int64_t(I) * W;
+  const double* Wc1 = f.mlp + int64_t(f.K) * density_params(I, W);
+  const double* Wc2 = Wc1 + int64_t(kGeo + kSh) * W;
+  const double* Wc3 = Wc2 + int64_t(W) * W;
+  a->z1.assign(W, 0.0);
+  a->h1.assign(W, 0.0);
+  for (int n = 0; n < W; ++n) {
+    double s = 0.0;
+    for (int i = 0; i < I; ++i) s += feat[i] * Wd1[i * W + n];
+    a->z1[n] = s;
+    a->h1[n] = s > 0.0 ? s : 0.0;
+  }
+  a->xc.assign(kGeo + kSh, 0.0);
+  for (int m = 0; m < kGeo; ++m) {
+    double s = 0.0;
+    for (int i = 0; i < W; ++i) s += a->h1[i] * Wd2[i * kGeo + m];
+    a->xc[m] = s;
+  }
+  const double dd[3] = {(double)dir[0], (double)dir[1], (double)dir[2]};
+  sh4(dd, a->xc.data() + kGeo);
+  a->z2.assign(W, 0.0);
+  a->h2.assign(W, 0.0);
+  for (int n = 0; n < W; ++n) {
+    double s = 0.0;
+    for (int i = 0; i < kGeo + kSh; ++i) s += a->xc[i] * Wc1[i * W + n];
+    a->z2[n] = s;
+    a->h2[n] = s > 0.0 ? s : 0.0;
+  }
+  a->z3.assign(W, 0.0);
+  a->h3.assign(W, 0.0);
+  for (int n = 0; n < W; ++n) {
+    double s = 0.0;
+    for (int i = 0; i < W; ++i) s += a->h2[i] * Wc2[i * W + n];
+    a->z3[n] = s;
+    a->h3[n] = s > 0.0 ? s : 0.0;
+  }
+  a->o[0] = a->xc[0];
+  for (int m = 0; m < 3; ++m) {
+    double s = 0.0;
+    for (int i = 0; i < W; ++i) s += a->h3[i] * Wc3[i * 4 + m];
+    a->o[1 + m] = s;
+  }
+}
+
+void mlp_forward(const oracle_field& f, int region, const double* feat, const float* dir, MlpAct* a) {
+  if (f.arch == 1) {
+    mlp_forward_split(f, region, feat, dir, a);
+    return;
+  }
   const int W = f.W, I = f.mlp_in;
   const double* p = f.mlp + int64_t(region) * mlp_params(I, W);
   const double* W1 = p;
@@ -372,7 +480,7 @@ void eval_ray(const oracle_field& f, const oracle_sampling& s, const std::vector
       continue;
     }
     encode(f, lv, q.region, x, &enc);
-    mlp_forward(f, q.region, enc.feat.data(), &act);
+    mlp_forward(f, q.region, enc.feat.data(), d, &act);
     re->sigma[i] = std::exp(act.o[0]);
     for (int c = 0; c < 3; ++c) re->rgb[3 * i + c] = sigmoid(act.o[1 + c]);
     if (keep) {
@@ -530,6 +638,69 @@ struct Grads {
 
 // Adjoint of field evaluation for one ray: MLP reverse mode then the
 // trilinear scatter into the table entries that were read.
+// Reverse mode through the split representation for one sample: go[0] is
+// dL/dg0 (the log density), go[1..3] dL/d(colour logits). Accumulates into the
+// region's density block and the shared colour block of gm; returns dL/dfeat.
+void mlp_adjoint_split(const oracle_field& f, int k, const MlpAct& a, const double* feat, const double* go,
+                       double* gm, double* gfeat) {
+  const int W = f.W, I = f.mlp_in;
+  const int64_t Pd = density_params(I, W);
+  const double* Wd1 = f.mlp + int64_t(k) * Pd;
+  const double* Wd2 = Wd1 + int64_t(I) * W;
+  const double* Wc1 = f.mlp + int64_t(f.K) * Pd;
+  const double* Wc2 = Wc1 + int64_t(kGeo + kSh) * W;
+  const double* Wc3 = Wc2 + int64_t(W) * W;
+  double* gd1 = gm + int64_t(k) * Pd;
+  double* gd2 = gd1 + int64_t(I) * W;
+  double* gc1 = gm + int64_t(f.K) * Pd;
+  double* gc2 = gc1 + int64_t(kGeo + kSh) * W;
+  double* gc3 = gc2 + int64_t(W) * W;
+  std::vector<double> gz3(W), gz2(W), gxc(kGeo + kSh), gz1(W);
+  for (int n = 0; n < W; ++n) {  // colour output layer
+    double s = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      gc3[n * 4 + m] += a.h3[n] * go[1 + m];
+      s += Wc3[n * 4 + m] * go[1 + m];
+    }
+    gz3[n] = a.z3[n] > 0.0 ? s : 0.0;
+  }
+  for (int r = 0; r < W; ++r) {
+    double s = 0.0;
+    for (int n = 0; n < W; ++n) {
+      gc2[r * W + n] += a.h2[r] * gz3[n];
+      s += Wc2[r * W + n] * gz3[n];
+    }
+    gz2[r] = a.z2[r] > 0.0 ? s : 0.0;
+  }
+  for (int r = 0; r < kGeo + kSh; ++r) {
+    double s = 0.0;
+    for (int n = 0; n < W; ++n) {
+      gc1[r * W + n] += a.xc[r] * gz2[n];
+      s += Wc1[r * W + n] * gz2[n];
+    }
+    gxc[r] = s;  // the direction part (r >= kGeo) has no parameters behind it
+  }
+  gxc[0] += go[0];  // g0 feeds the density as well as the colour MLP
+  for (int r = 0; r < W; ++r) {
+    double s = 0.0;
+    for (int m = 0; m < kGeo; ++m) {
+      gd2[r * kGeo + m] += a.h1[r] * gxc[m];
+      s += Wd2[r * kGeo + m] * gxc[m];
+    }
+    gz1[r] = a.z1[r] > 0.0 ? s : 0.0;
+  }
+  for (int r = 0; r < I; ++r) {
+    double s = 0.0;
+    for (int n = 0; n < W; ++n) {
+      gd1[r * W + n] += feat[r] * gz1[n];
+      s += Wd1[r * W + n] * gz1[n];
+    }
+    gfeat[r] = s;
+  }
+}
+
+// Adjoint of field evaluation for one ray: MLP reverse mode then the
+// trilinear scatter into the table entries that were read.
 void field_adjoint(const oracle_field& f, const RayEval& re, const double* g_sigma, const double* g_rgb,
                    int64_t E, Grads* g) {
   const int W = f.W, I = f.mlp_in;
@@ -538,44 +709,48 @@ void field_adjoint(const oracle_field& f, const RayEval& re, const double* g_sig
   for (size_t i = 0; i < re.iv.size(); ++i) {
     if (re.skip[i]) continue;  // density fixed at 0: no parameter reaches it
     const int k = re.iv[i].region;
-    const double* p = f.mlp + int64_t(k) * P;
-    const double* W1 = p;
-    const double* W2 = W1 + int64_t(I) * W;
-    const double* W3 = W2 + int64_t(W) * W;
-    double* g1 = g->mlp.data() + int64_t(k) * P;
-    double* g2 = g1 + int64_t(I) * W;
-    double* g3 = g2 + int64_t(W) * W;
     const MlpAct& a = re.act[i];
+    const Encoded& e = re.enc[i];
     double go[4];
     go[0] = g_sigma[i] * re.sigma[i];
     for (int c = 0; c < 3; ++c) {
       const double cc = re.rgb[3 * i + c];
       go[1 + c] = g_rgb[3 * i + c] * cc * (1.0 - cc);
     }
-    for (int n = 0; n < W; ++n) {
-      double s = 0.0;
-      for (int m = 0; m < 4; ++m) {
-        g3[n * 4 + m] += a.h2[n] * go[m];
-        s += W3[n * 4 + m] * go[m];
-      }
-      gz2[n] = a.z2[n] > 0.0 ? s : 0.0;
-    }
-    for (int r = 0; r < W; ++r) {
-      double s = 0.0;
+    if (f.arch == 1) {
+      mlp_adjoint_split(f, k, a, e.feat.data(), go, g->mlp.data(), gfeat.data());
+    } else {
+      const double* p = f.mlp + int64_t(k) * P;
+      const double* W1 = p;
+      const double* W2 = W1 + int64_t(I) * W;
+      const double* W3 = W2 + int64_t(W) * W;
+      double* g1 = g->mlp.data() + int64_t(k) * P;
+      double* g2 = g1 + int64_t(I) * W;
+      double* g3 = g2 + int64_t(W) * W;
       for (int n = 0; n < W; ++n) {
-        g2[r * W + n] += a.h1[r] * gz2[n];
-        s += W2[r * W + n] * gz2[n];
+        double s = 0.0;
+        for (int m = 0; m < 4; ++m) {
+          g3[n * 4 + m] += a.h2[n] * go[m];
+          s += W3[n * 4 + m] * go[m];
+        }
+        gz2[n] = a.z2[n] > 0.0 ? s : 0.0;
       }
-      gz1[r] = a.z1[r] > 0.0 ? s : 0.0;
-    }
-    const Encoded& e = re.enc[i];
-    for (int r = 0; r < I; ++r) {
-      double s = 0.0;
-      for (int n = 0; n < W; ++n) {
-        g1[r * W + n] += e.feat[r] * gz1[n];
-        s += W1[r * W + n] * gz1[n];
+      for (int r = 0; r < W; ++r) {
+        double s = 0.0;
+        for (int n = 0; n < W; ++n) {
+          g2[r * W + n] += a.h1[r] * gz2[n];
+          s += W2[r * W + n] * gz2[n];
+        }
+        gz1[r] = a.z1[r] > 0.0 ? s : 0.0;
       }
-      gfeat[r] = s;
+      for (int r = 0; r < I; ++r) {
+        double s = 0.0;
+        for (int n = 0; n < W; ++n) {
+          g1[r * W + n] += e.feat[r] * gz1[n];
+          s += W1[r * W + n] * gz1[n];
+        }
+        gfeat[r] = s;
+      }
     }
     for (int l = 0; l < f.L; ++l) {
       for (int c = 0; c < 8; ++c) {
@@ -594,7 +769,6 @@ void render_grad_impl(const oracle_field& f, const oracle_sampling& s, int64_t R
                       double* g_mlp) {
   const std::vector<Level> lv = make_levels(f.L, f.level_res, f.log2_T);
   const int64_t E = lv.back().offset + lv.back().size;
-  const int64_t P = mlp_params(f.mlp_in, f.W);
   std::vector<Grads> per_ray(R);
   parallel_for(R, [&](int64_t r, int) {
     RayEval re;
@@ -605,7 +779,7 @@ void render_grad_impl(const oracle_field& f, const oracle_sampling& s, int64_t R
                           gA[r], gL[r], gs.data(), gc.data());
     // MLP gradient of this ray: only the regions it touches are non-zero.
     Grads g;
-    g.mlp.assign(size_t(f.K) * P, 0.0);
+    g.mlp.assign(size_t(field_mlp_size(f)), 0.0);
     field_adjoint(f, re, gs.data(), gc.data(), E, &g);
     per_ray[r] = std::move(g);
   });
@@ -704,6 +878,13 @@ int32_t oracle_level_dense(int32_t L, const int32_t* level_res, int32_t log2_T, 
   return make_levels(L, level_res, log2_T)[l].dense ? 1 : 0;
 }
 int64_t oracle_mlp_params(int32_t mlp_in, int32_t W) { return mlp_params(mlp_in, W); }
+int64_t oracle_density_params(int32_t mlp_in, int32_t W) { return density_params(mlp_in, W); }
+int64_t oracle_color_params(int32_t W) { return color_params(W); }
+
+// Spherical harmonics of degrees 0..3 of n unit directions: out [n][16].
+void oracle_sh4(int64_t n, const double* dirs, double* out) {
+  for (int64_t i = 0; i < n; ++i) sh4(dirs + 3 * i, out + 16 * i);
+}
 
 // Segments of each ray, ray order. Outputs sized [R][K]; unused slots left as is.
 void oracle_segments(const oracle_field* f, const oracle_sampling* s, int64_t R, const float* ro, const float* rd,
@@ -782,10 +963,12 @@ void oracle_encode_points(const oracle_field* f, int64_t n, const int32_t* regio
 }
 
 // Raw MLP outputs o[n][4] for explicit features.
-void oracle_mlp(const oracle_field* f, int64_t n, const int32_t* region, const double* feat, double* o) {
+void oracle_mlp(const oracle_field* f, int64_t n, const int32_t* region, const double* feat, const float* dirs,
+                double* o) {
+  const float up[3] = {0.0f, 0.0f, 1.0f};
   parallel_for(n, [&](int64_t i, int) {
     MlpAct a;
-    mlp_forward(*f, region[i], feat + i * f->mlp_in, &a);
+    mlp_forward(*f, region[i], feat + i * f->mlp_in, dirs ? dirs + 3 * i : up, &a);
     for (int m = 0; m < 4; ++m) o[i * 4 + m] = a.o[m];
   });
 }
@@ -974,7 +1157,8 @@ void oracle_occupancy_update(const oracle_field* f, int32_t G, int64_t step, uin
     Encoded enc;
     MlpAct act;
     encode_u(*f, lv, region, u, &enc);
-    mlp_forward(*f, region, enc.feat.data(), &act);
+    const float up[3] = {0.0f, 0.0f, 1.0f};  // the density does not depend on the direction
+    mlp_forward(*f, region, enc.feat.data(), up, &act);
     const double sigma = std::exp(act.o[0]);
     density[i] = std::max(decay * density[i], sigma);
     on[size_t(i)] = density[i] > threshold;

@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 _STREAMS = {"rays": 1, "tables": 2, "mlp": 3, "blobs": 4, "batch": 5, "requests": 6, "subset": 7, "misc": 8,
-            "content": 9, "ray_samples": 10}
+            "content": 9, "ray_samples": 10, "split_mlp": 11}
 
 
 def rng(seed: int, purpose: str) -> np.random.Generator:
@@ -262,6 +262,13 @@ def field_params(w: Workload, E: int, P: int, table_std: float = 1.0, mlp_std: f
         tables = uniform_params((w.K, E, w.F), table_std, w.seed, "tables")
     mlp = gaussian_params((w.K, P), mlp_std, w.seed, "mlp")
     return tables, mlp
+
+
+def split_mlp_params(w: Workload, n_params: int, mlp_std: float = 0.1):
+    """MLP parameters of the split representation (per-region density blocks
+    followed by the shared colour block, flat float32 of n_params values, the
+    size the consuming library reports), N(0, mlp_std)."""
+    return gaussian_params((n_params,), mlp_std, w.seed, "split_mlp")
 
 
 def subset(n_total: int, n: int, seed: int) -> np.ndarray:

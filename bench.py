@@ -424,6 +424,32 @@ def main():
                 "field at one Philox point per cell"}
     del grid, f32
     torch.cuda.empty_cache()
+    # ---- the split representation (App. A.1): per-region density MLP + one shared view-dependent colour
+    #      MLP, FP32 forward and training step on the grid8 shapes, next to the fused FP32 forms above
+    n_split = api.split_mlp_params(w.K, w.mlp_in, w.W)
+    gsm = torch.Generator(device=dev)
+    gsm.manual_seed(int(w.seed) * 7919 + 11)
+    m_split = torch.randn(n_split, generator=gsm, device=dev) * 0.1
+    fsplit = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.as_tensor(tables).to(dev), m_split, device=dev,
+                                  arch=N.ARCH_SPLIT)
+    r = fwd_form(w, fsplit, samp, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
+    split = {"fwd_fp32": {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0),
+                          "kernel_ms": statistics.mean(r["kern_ms"])}}
+    del r
+    strainer = api.Trainer(fsplit, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    sstep = lambda: strainer.step(o_dev, d_dev, tgt)
+    for _ in range(warm):
+        sstep()
+    torch.cuda.synchronize()
+    s_ms, s_kern = time_steps(sstep, steps, flush, stream)
+    split["train_fp32"] = {"rays_per_s": R / (statistics.mean(s_ms) / 1000.0), "kernel_ms": statistics.mean(s_kern),
+                           "kernel": "k_field_bwd_split_f32"}
+    forms["grid8_split"] = {
+        "split": split,
+        "note": "FP32 tables and MLPs; density MLP 32-64-16 per region, colour MLP 32-64-64-3 shared, on "
+                "[density features, degree-0..3 SH of the view direction]; compare grid8_fwd_fp32 / grid8_train_fp32"}
+    del strainer, fsplit, m_split
+    torch.cuda.empty_cache()
     # ---- city32 (K=32, 8x4x1 slabs, 2^20 rays, S=256): MLP precision variants
     if not args.skip_city:
         wc = sy.workload("city32")
@@ -503,7 +529,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops()
 
     def summary(f):
-        if "serve" in f or "partition" in f or "composition" in f or "occupancy" in f:
+        if "serve" in f or "partition" in f or "composition" in f or "occupancy" in f or "split" in f:
             return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
         r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}

@@ -57,6 +57,10 @@ typedef enum {
 
 typedef enum { NERFXL_F32 = 0, NERFXL_F16 = 1, NERFXL_BF16 = 2, NERFXL_E4M3 = 3 } nerfxl_dtype;
 
+/* Field representations (nerfxl_field.arch). */
+#define NERFXL_ARCH_FUSED 0 /* one MLP per region: feat -> W -> W -> 4 */
+#define NERFXL_ARCH_SPLIT 1 /* per-region density MLP + one shared, view-dependent colour MLP */
+
 /*
  * The partitioned field: K regions, each with a hash grid of L levels of F
  * features and an MLP mlp_in -> W -> W -> 4 (ReLU, no biases; density =
@@ -97,6 +101,20 @@ typedef struct nerfxl_field {
    */
   const uint32_t* occupancy;            /* [K][ceil(G^3/32)], or NULL */
   int32_t occ_res;                      /* G in [1, 1024] when occupancy is set */
+  /*
+   * Representation. NERFXL_ARCH_FUSED: as above. NERFXL_ARCH_SPLIT, the
+   * representation the paper trains (App. A.1, after Instant-NGP): region k's
+   * block is a density MLP Wd1 [mlp_in][W], Wd2 [W][16] (ReLU, no biases; its
+   * 16 outputs g, density = exp(g0)); one colour MLP shared by all regions
+   * follows the K density blocks in the same array: Wc1 [32][W], Wc2 [W][W],
+   * Wc3 [W][4] on [g, SH(d)] -> ReLU -> ReLU -> colour = sigmoid of the first
+   * three outputs (column 3 of Wc3 is unused). SH(d) is the 16 real spherical
+   * harmonics of degrees 0..3 of the ray's unit direction (Condon-Shortley
+   * phase; order Y_0^0, Y_1^-1, Y_1^0, Y_1^1, Y_2^-2, ..., Y_3^3). mlp then
+   * holds K * (mlp_in W + 16 W) + (32 W + W W + 4 W) values
+   * (nerfxl_field_mlp_params). Built for FP32 tables and MLP.
+   */
+  int32_t arch;
 } nerfxl_field;
 
 /*
@@ -139,6 +157,8 @@ typedef struct nerfxl_sampling {
 int64_t nerfxl_table_entries(const int32_t* level_res /* host [L] */, int32_t L, int32_t log2_T);
 /* Parameters per region MLP block: mlp_in*W + W*W + 4*W. */
 int64_t nerfxl_mlp_params(int32_t mlp_in, int32_t width);
+/* Elements of f->mlp for its representation (K * P fused; K density blocks + the colour block split), or -1. */
+int64_t nerfxl_field_mlp_params(const nerfxl_field* f);
 /* Largest number of 32-sample chunks one ray can produce. */
 int32_t nerfxl_max_chunks(const nerfxl_sampling* s, int32_t K);
 

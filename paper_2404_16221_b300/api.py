@@ -43,7 +43,7 @@ class PartitionedField:
     """
 
     def __init__(self, boxes, level_res, log2_T: int, tables, mlp, F: int = 2, mlp_in: int = 32, width: int = 64,
-                 mlp_scales=None, device="cuda", occupancy=None, occ_res: int = 0):
+                 mlp_scales=None, device="cuda", occupancy=None, occ_res: int = 0, arch: int = N.ARCH_FUSED):
         self.device = torch.device(device)
         self.boxes = torch.as_tensor(boxes, dtype=torch.float32).reshape(-1, 6).contiguous().to(self.device)
         self.level_res = [int(v) for v in level_res]
@@ -53,7 +53,13 @@ class PartitionedField:
         self.E = N.table_entries(self.level_res, self.log2_T)
         self.P = N.mlp_params(self.mlp_in, self.width)
         self.tables = torch.as_tensor(tables).to(self.device).reshape(self.K, self.E, self.F).contiguous()
-        self.mlp = torch.as_tensor(mlp).to(self.device).reshape(self.K, self.P).contiguous()
+        self.arch = int(arch)
+        if self.arch == N.ARCH_SPLIT:
+            # per-region density blocks, then the shared colour block (flat)
+            self.P = split_mlp_params(self.K, self.mlp_in, self.width)
+            self.mlp = torch.as_tensor(mlp).to(self.device).reshape(self.P).contiguous()
+        else:
+            self.mlp = torch.as_tensor(mlp).to(self.device).reshape(self.K, self.P).contiguous()
         self.mlp_scales = None if mlp_scales is None else torch.as_tensor(
             mlp_scales, dtype=torch.float32).to(self.device).reshape(self.K, 3).contiguous()
         self.set_occupancy(occupancy, occ_res)
@@ -81,7 +87,14 @@ class PartitionedField:
         d.mlp_scales = None if self.mlp_scales is None else self.mlp_scales.data_ptr()
         d.occupancy = None if self.occupancy is None else self.occupancy.data_ptr()
         d.occ_res = self.occ_res
+        d.arch = self.arch
         return d
+
+
+def split_mlp_params(K: int, mlp_in: int = 32, width: int = 64) -> int:
+    """MLP values of the split representation: K density blocks (mlp_in x W +
+    W x 16) and the shared colour block (32 x W + W x W + W x 4)."""
+    return K * (mlp_in * width + width * 16) + (32 * width + width * width + width * 4)
 
 
 def occupancy_words(G: int) -> int:
@@ -214,13 +227,13 @@ def render_bwd(field: PartitionedField, samp: Sampling, rays_o, rays_d, workspac
                d_opacity=None, d_dist=None, grad_tables=None, grad_mlp=None, stream=None):
     """Adjoint render. ``workspace`` must come from the matching render_fwd
     (allocated with for_backward=True). Gradients are accumulated into
-    grad_tables [K][E][F] and grad_mlp [K][P] (FP32; zero-filled if None)."""
+    grad_tables [K][E][F] and grad_mlp (the field's mlp shape; FP32; zero-filled if None)."""
     o, d = _rays(rays_o, rays_d, field.device)
     R = o.shape[0]
     if grad_tables is None:
         grad_tables = torch.zeros(field.K, field.E, field.F, dtype=torch.float32, device=field.device)
     if grad_mlp is None:
-        grad_mlp = torch.zeros(field.K, field.P, dtype=torch.float32, device=field.device)
+        grad_mlp = torch.zeros(field.mlp.shape, dtype=torch.float32, device=field.device)
 
     def c(t):
         return None if t is None else t.contiguous()

@@ -19,7 +19,7 @@
 
 #include <string>
 
-#include "nerfxl_field.cuh"
+#include "nerfxl_split.cuh"
 #include "nerfxl_host.h"
 
 namespace nerfxl {
@@ -406,6 +406,388 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
 }
 
+// ---------------------------------------------------------------------------
+// k_field_bwd_split_f32: the split representation's backward (FP32). Per
+// 256-sample tile: recompute encoding, density MLP (g), colour MLP on
+// [g, SH(d)]; chunk-local render adjoint; colour MLP backward (its weight
+// gradients accumulate in registers over every tile the CTA takes, whatever
+// the region, and reach the shared block once at the end); dL/dg0 from the
+// density and from the colour MLP; density MLP backward (accumulated per
+// region); table scatter. Activations of the tile live in three shared
+// buffers that the phases reuse:
+//   X [256][36]: xc = [g, SH] and dL/d(colour logits) -> dL/dg
+//   B [256][68]: hc1 -> dL/dzc1 -> feat
+//   C [256][68]: hc2 -> dL/dzc2 -> h1 -> dL/dz1
+// Weight-gradient accumulators per thread (GEMM over the tile's samples):
+//   Wc3 [n][m] n = t/4, m = t%4 | Wc2 [i][n0..+15] i = t/4, n0 = 16 (t%4) |
+//   Wc1 [j][n0..+7] j = t/8, n0 = 8 (t%8) | Wd2 [n][m0..+3] n = t/4, m0 = 4 (t%4) |
+//   Wd1 [j][n0..+7] j = t/8, n0 = 8 (t%8).
+
+constexpr int kSplitXPitch = 36;
+constexpr size_t kBwdSplitSmemFloats =
+    (size_t)kSplitSmemFloats + (size_t)kBwdThreads * kSplitXPitch + 2 * (size_t)kBwdThreads * kActPitch;
+
+__device__ __forceinline__ void flush_density_grad(float* __restrict__ g, const float aWd1[8], const float aWd2[4],
+                                                   int tid) {
+  const int j = tid >> 3, n0 = (tid & 7) * 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (aWd1[q] != 0.0f) atomicAdd(g + j * kWidth + n0 + q, aWd1[q]);
+  const int n = tid >> 2, m0 = (tid & 3) * 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (aWd2[q] != 0.0f) atomicAdd(g + kIn * kWidth + n * kGeo + m0 + q, aWd2[q]);
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParams p) {
+  extern __shared__ __align__(16) float sm[];
+  float* s_d = sm;                                  // Wd1t [64][32], Wd2 [64][16]
+  float* s_c = s_d + kDensityParams;                // Wc1t [64][32], Wc2t [64][64], Wc3 [64][4]
+  float* s_X = s_c + kColorParams;                  // [256][36]
+  float* s_B = s_X + kBwdThreads * kSplitXPitch;    // [256][68]
+  float* s_C = s_B + kBwdThreads * kActPitch;       // [256][68]
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_C + kBwdThreads * kActPitch);
+  const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+  const float* mlp = static_cast<const float*>(p.mlp);
+  for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  load_color_f32(mlp + (size_t)p.K * kDensityParams, s_c);
+  __syncthreads();
+  const int n_tiles = *p.n_tiles;
+  const float4* Wd1t = reinterpret_cast<const float4*>(s_d);
+  const float4* Wd2 = reinterpret_cast<const float4*>(s_d + kIn * kWidth);
+  const float4* Wc1t = reinterpret_cast<const float4*>(s_c);
+  const float4* Wc2t = reinterpret_cast<const float4*>(s_c + kColorIn * kWidth);
+  const float* Wc3 = s_c + kColorIn * kWidth + kWidth * kWidth;
+  float* my_X = s_X + tid * kSplitXPitch;
+  float* my_B = s_B + tid * kActPitch;
+  float* my_C = s_C + tid * kActPitch;
+  float aWc3 = 0.0f, aWc2[16], aWc1[8], aWd2[4], aWd1[8];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) aWc2[q] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) aWc1[q] = aWd1[q] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
+  int region = -1;
+  const float2* table = nullptr;
+  float2* gtab = nullptr;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
+    __syncthreads();  // previous tile's shared buffers fully consumed
+    if (k != region) {
+      if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, tid);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) aWd1[q] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
+      load_density_f32(mlp + (size_t)k * kDensityParams, s_d);
+      __syncthreads();
+      region = k;
+      table = static_cast<const float2*>(p.tables) + (size_t)k * p.lp.E;
+      gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+    }
+    const uint2 ref = p.chunks[t * kChunksPerTile + warp];
+    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
+    bool valid = false;
+    float feat[kIn], u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
+    float tr = 0.0f, dl = 0.0f;
+    float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+    if (chunk_ok) {
+      const uint32_t ray = ref.x;
+      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+      const RayHdr h = p.hdr[ray];
+      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+      const float4 g0 = p.dpart[2 * slot], g1 = p.dpart[2 * slot + 1];
+      gtc = g0.x;
+      gC[0] = g0.y;
+      gC[1] = g0.z;
+      gC[2] = g0.w;
+      gA = g1.x;
+      gD = g1.y;
+      gL = g1.z;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) dir[ax] = p.rays_d[3 * (size_t)ray + ax];
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+      const int i = c * kWarp + lane;
+      valid = i < ss.n;
+      if (valid) {
+        float o[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) o[ax] = p.rays_o[3 * (size_t)ray + ax];
+        float a, b;
+        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
+        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        dl = __fsub_rn(b, a);
+        tr = __fsub_rn(tbar, h.tn);
+        float x[3];
+        sample_point(o, dir, tbar, x);
+        region_coord(p.fp.boxes + 6 * k, x, u);
+        encode_f32(p.lp, table, u, feat);
+      }
+    }
+    // ---- forward recompute: g, xc -> X; hc1 -> B; hc2 -> C; colour logits
+    float xc[kColorIn];
+    density_f32_smem(s_d, feat, xc);
+    sh4_f32(dir, xc + kGeo);
+#pragma unroll
+    for (int q = 0; q < kColorIn; q += 4)
+      *reinterpret_cast<float4*>(my_X + q) = make_float4(xc[q], xc[q + 1], xc[q + 2], xc[q + 3]);
+    {
+      float hc1[kWidth];
+#pragma unroll
+      for (int n = 0; n < kWidth; ++n) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i4 = 0; i4 < kColorIn / 4; ++i4) {
+          const float4 w = Wc1t[n * (kColorIn / 4) + i4];
+          acc = fmaf(xc[4 * i4], w.x, acc);
+          acc = fmaf(xc[4 * i4 + 1], w.y, acc);
+          acc = fmaf(xc[4 * i4 + 2], w.z, acc);
+          acc = fmaf(xc[4 * i4 + 3], w.w, acc);
+        }
+        hc1[n] = fmaxf(acc, 0.0f);
+      }
+#pragma unroll
+      for (int q = 0; q < kWidth; q += 4)
+        *reinterpret_cast<float4*>(my_B + q) = make_float4(hc1[q], hc1[q + 1], hc1[q + 2], hc1[q + 3]);
+    }
+    float oc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+    for (int n = 0; n < kWidth; ++n) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
+        const float4 w = Wc2t[n * (kWidth / 4) + i4];
+        const float4 hv = *reinterpret_cast<const float4*>(my_B + 4 * i4);
+        acc = fmaf(hv.x, w.x, acc);
+        acc = fmaf(hv.y, w.y, acc);
+        acc = fmaf(hv.z, w.z, acc);
+        acc = fmaf(hv.w, w.w, acc);
+      }
+      const float h2 = fmaxf(acc, 0.0f);
+      my_C[n] = h2;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) oc[m] = fmaf(h2, Wc3[n * kOut + m], oc[m]);
+    }
+    // ---- chunk-local render adjoint -> dL/dg0 (density) and dL/d(colour logits)
+    float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+      sigma = expf(xc[0]);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-oc[m]));
+    }
+    float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+    const float go_d = valid ? g_sigma * sigma : 0.0f;
+    float go[3] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
+    }
+    *reinterpret_cast<float4*>(my_X + kColorIn) = make_float4(go[0], go[1], go[2], 0.0f);
+    __syncthreads();
+    // ---- Wc3[n][m] += sum_s hc2[s][n] go[s][m]
+    {
+      const int n = tid >> 2, m = tid & 3;
+      float acc = 0.0f;
+      for (int s = 0; s < kBwdThreads; ++s) acc = fmaf(s_C[s * kActPitch + n], s_X[s * kSplitXPitch + kColorIn + m], acc);
+      aWc3 += acc;
+    }
+    // ---- dL/dzc2 = (hc2 > 0) Wc3 go   (own row, written after everyone read C)
+    float gz[kWidth];
+#pragma unroll
+    for (int n = 0; n < kWidth; ++n)
+      gz[n] = my_C[n] > 0.0f ? Wc3[n * kOut] * go[0] + Wc3[n * kOut + 1] * go[1] + Wc3[n * kOut + 2] * go[2] : 0.0f;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_C + q) = make_float4(gz[q], gz[q + 1], gz[q + 2], gz[q + 3]);
+    __syncthreads();
+    // ---- Wc2[i][n] += sum_s hc1[s][i] dzc2[s][n]
+    {
+      const int i = tid >> 2, n0 = (tid & 3) * 16;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float hv = s_B[s * kActPitch + i];
+        const float4* qr = reinterpret_cast<const float4*>(s_C + s * kActPitch + n0);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 v = qr[q4];
+          aWc2[4 * q4] = fmaf(hv, v.x, aWc2[4 * q4]);
+          aWc2[4 * q4 + 1] = fmaf(hv, v.y, aWc2[4 * q4 + 1]);
+          aWc2[4 * q4 + 2] = fmaf(hv, v.z, aWc2[4 * q4 + 2]);
+          aWc2[4 * q4 + 3] = fmaf(hv, v.w, aWc2[4 * q4 + 3]);
+        }
+      }
+    }
+    // ---- dL/dzc1 = (hc1 > 0) Wc2 dzc2   (Wc2[i][n] = Wc2t[n][i])
+    float gz1c[kWidth];
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) gz1c[i] = 0.0f;
+#pragma unroll 2
+    for (int n = 0; n < kWidth; ++n) {
+      const float gzn = gz[n];
+#pragma unroll
+      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
+        const float4 w = Wc2t[n * (kWidth / 4) + i4];
+        gz1c[4 * i4] = fmaf(w.x, gzn, gz1c[4 * i4]);
+        gz1c[4 * i4 + 1] = fmaf(w.y, gzn, gz1c[4 * i4 + 1]);
+        gz1c[4 * i4 + 2] = fmaf(w.z, gzn, gz1c[4 * i4 + 2]);
+        gz1c[4 * i4 + 3] = fmaf(w.w, gzn, gz1c[4 * i4 + 3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) gz1c[i] = my_B[i] > 0.0f ? gz1c[i] : 0.0f;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_B + q) = make_float4(gz1c[q], gz1c[q + 1], gz1c[q + 2], gz1c[q + 3]);
+    __syncthreads();
+    // ---- Wc1[j][n] += sum_s xc[s][j] dzc1[s][n]
+    {
+      const int j = tid >> 3, n0 = (tid & 7) * 8;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float xv = s_X[s * kSplitXPitch + j];
+        const float4* qr = reinterpret_cast<const float4*>(s_B + s * kActPitch + n0);
+#pragma unroll
+        for (int q4 = 0; q4 < 2; ++q4) {
+          const float4 v = qr[q4];
+          aWc1[4 * q4] = fmaf(xv, v.x, aWc1[4 * q4]);
+          aWc1[4 * q4 + 1] = fmaf(xv, v.y, aWc1[4 * q4 + 1]);
+          aWc1[4 * q4 + 2] = fmaf(xv, v.z, aWc1[4 * q4 + 2]);
+          aWc1[4 * q4 + 3] = fmaf(xv, v.w, aWc1[4 * q4 + 3]);
+        }
+      }
+    }
+    // ---- dL/dg = (Wc1 dzc1)[0..15] + dL/dg0 from the density
+    float gg[kGeo];
+#pragma unroll
+    for (int m = 0; m < kGeo; ++m) gg[m] = 0.0f;
+#pragma unroll 4
+    for (int n = 0; n < kWidth; ++n) {
+      const float gzn = gz1c[n];
+#pragma unroll
+      for (int m4 = 0; m4 < kGeo / 4; ++m4) {
+        const float4 w = Wc1t[n * (kColorIn / 4) + m4];  // Wc1[4 m4 + j][n]
+        gg[4 * m4] = fmaf(w.x, gzn, gg[4 * m4]);
+        gg[4 * m4 + 1] = fmaf(w.y, gzn, gg[4 * m4 + 1]);
+        gg[4 * m4 + 2] = fmaf(w.z, gzn, gg[4 * m4 + 2]);
+        gg[4 * m4 + 3] = fmaf(w.w, gzn, gg[4 * m4 + 3]);
+      }
+    }
+    gg[0] += go_d;
+    // ---- recompute h1 of the density MLP
+    float h1[kWidth];
+#pragma unroll
+    for (int n = 0; n < kWidth; ++n) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i4 = 0; i4 < kIn / 4; ++i4) {
+        const float4 w = Wd1t[n * (kIn / 4) + i4];
+        acc = fmaf(feat[4 * i4], w.x, acc);
+        acc = fmaf(feat[4 * i4 + 1], w.y, acc);
+        acc = fmaf(feat[4 * i4 + 2], w.z, acc);
+        acc = fmaf(feat[4 * i4 + 3], w.w, acc);
+      }
+      h1[n] = fmaxf(acc, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGeo; q += 4)
+      *reinterpret_cast<float4*>(my_X + q) = make_float4(gg[q], gg[q + 1], gg[q + 2], gg[q + 3]);
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_C + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
+    __syncthreads();
+    // ---- Wd2[n][m] += sum_s h1[s][n] dg[s][m]
+    {
+      const int n = tid >> 2, m0 = (tid & 3) * 4;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float hv = s_C[s * kActPitch + n];
+        const float4 v = *reinterpret_cast<const float4*>(s_X + s * kSplitXPitch + m0);
+        aWd2[0] = fmaf(hv, v.x, aWd2[0]);
+        aWd2[1] = fmaf(hv, v.y, aWd2[1]);
+        aWd2[2] = fmaf(hv, v.z, aWd2[2]);
+        aWd2[3] = fmaf(hv, v.w, aWd2[3]);
+      }
+    }
+    // ---- dL/dz1 = (h1 > 0) Wd2 dg
+#pragma unroll
+    for (int n = 0; n < kWidth; ++n) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int m4 = 0; m4 < kGeo / 4; ++m4) {
+        const float4 w = Wd2[n * (kGeo / 4) + m4];
+        acc = fmaf(w.x, gg[4 * m4], acc);
+        acc = fmaf(w.y, gg[4 * m4 + 1], acc);
+        acc = fmaf(w.z, gg[4 * m4 + 2], acc);
+        acc = fmaf(w.w, gg[4 * m4 + 3], acc);
+      }
+      h1[n] = h1[n] > 0.0f ? acc : 0.0f;  // now dL/dz1
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kWidth; q += 4)
+      *reinterpret_cast<float4*>(my_C + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
+#pragma unroll
+    for (int q = 0; q < kIn; q += 4)
+      *reinterpret_cast<float4*>(my_B + q) = make_float4(feat[q], feat[q + 1], feat[q + 2], feat[q + 3]);
+    __syncthreads();
+    // ---- Wd1[j][n] += sum_s feat[s][j] dz1[s][n]
+    {
+      const int j = tid >> 3, n0 = (tid & 7) * 8;
+      for (int s = 0; s < kBwdThreads; ++s) {
+        const float fv = s_B[s * kActPitch + j];
+        const float4* qr = reinterpret_cast<const float4*>(s_C + s * kActPitch + n0);
+#pragma unroll
+        for (int q4 = 0; q4 < 2; ++q4) {
+          const float4 v = qr[q4];
+          aWd1[4 * q4] = fmaf(fv, v.x, aWd1[4 * q4]);
+          aWd1[4 * q4 + 1] = fmaf(fv, v.y, aWd1[4 * q4 + 1]);
+          aWd1[4 * q4 + 2] = fmaf(fv, v.z, aWd1[4 * q4 + 2]);
+          aWd1[4 * q4 + 3] = fmaf(fv, v.w, aWd1[4 * q4 + 3]);
+        }
+      }
+    }
+    // ---- dL/dfeat = Wd1 dz1, then the table scatter
+    if (valid) {
+      float gfeat[kIn];
+#pragma unroll
+      for (int j = 0; j < kIn; ++j) gfeat[j] = 0.0f;
+#pragma unroll 4
+      for (int n = 0; n < kWidth; ++n) {
+        const float gzn = h1[n];
+#pragma unroll
+        for (int i4 = 0; i4 < kIn / 4; ++i4) {
+          const float4 w = Wd1t[n * (kIn / 4) + i4];
+          gfeat[4 * i4] = fmaf(w.x, gzn, gfeat[4 * i4]);
+          gfeat[4 * i4 + 1] = fmaf(w.y, gzn, gfeat[4 * i4 + 1]);
+          gfeat[4 * i4 + 2] = fmaf(w.z, gzn, gfeat[4 * i4 + 2]);
+          gfeat[4 * i4 + 3] = fmaf(w.w, gzn, gfeat[4 * i4 + 3]);
+        }
+      }
+      scatter_table_grad(p.lp, gtab, u, gfeat);
+    }
+  }
+  if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, tid);
+  // the shared colour block: once per CTA
+  float* gc = p.grad_mlp + (size_t)p.K * kDensityParams;
+  {
+    const int n = tid >> 2, m = tid & 3;
+    if (aWc3 != 0.0f) atomicAdd(gc + kColorIn * kWidth + kWidth * kWidth + n * kOut + m, aWc3);
+    const int i = tid >> 2, n0 = (tid & 3) * 16;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (aWc2[q] != 0.0f) atomicAdd(gc + kColorIn * kWidth + i * kWidth + n0 + q, aWc2[q]);
+    const int j = tid >> 3, m0 = (tid & 7) * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (aWc1[q] != 0.0f) atomicAdd(gc + j * kWidth + m0 + q, aWc1[q]);
+  }
+}
+
 }  // namespace nerfxl
 
 using namespace nerfxl;
@@ -466,6 +848,18 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.dpart = dpart;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
+  if (f->arch == NERFXL_ARCH_SPLIT) {
+    const size_t smem_s = sizeof(float) * kBwdSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
+    if (smem_s > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
+    if (cudaFuncSetAttribute(k_field_bwd_split_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) !=
+        cudaSuccess)
+      return launch_check("k_field_bwd_split_f32 smem attribute");
+    const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);
+    profile_mark(0, stream);
+    k_field_bwd_split_f32<<<grid, kBwdThreads, smem_s, stream>>>(p);
+    profile_mark(1, stream);
+    return launch_check("k_field_bwd_split_f32");
+  }
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
   if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");

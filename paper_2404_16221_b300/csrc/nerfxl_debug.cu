@@ -126,6 +126,8 @@ nerfxl_status nerfxl_debug_samples(const nerfxl_field* f, const nerfxl_sampling*
   if (st != NERFXL_OK) return st;
   if (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32)
     return set_error(NERFXL_E_UNSUPPORTED, "debug views read FP32 parameters");
+  if (raw && f->arch != NERFXL_ARCH_FUSED)
+    return set_error(NERFXL_E_UNSUPPORTED, "raw MLP outputs are built for the fused representation");
   if (max_int < 1 || !count || !a || !b || !region) return set_error(NERFXL_E_INVALID, "bad debug outputs");
   if (n_rays == 0) return NERFXL_OK;
   FieldPtrs fp;

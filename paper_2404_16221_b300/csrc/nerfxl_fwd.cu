@@ -26,7 +26,7 @@
 #include <string>
 
 #include "nerfxl_device.cuh"
-#include "nerfxl_field.cuh"
+#include "nerfxl_split.cuh"
 #include "nerfxl_host.h"
 
 namespace nerfxl {
@@ -265,11 +265,16 @@ struct FwdParams {
 };
 
 
+// kSplit: the split representation (per-region density MLP; the shared
+// colour MLP is staged once, after the density block).
+template <bool kSplit>
 __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
   extern __shared__ __align__(16) float s_dyn[];
-  float* s_w = s_dyn;                                            // kMlpParams floats
-  int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kMlpParams);  // [K+1]
+  constexpr int kWFloats = kSplit ? kSplitSmemFloats : kMlpParams;
+  float* s_w = s_dyn;                                              // kWFloats floats
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kWFloats);  // [K+1]
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  if (kSplit) load_color_f32(p.fp.mlp + (size_t)p.K * kDensityParams, s_w + kDensityParams);
   __syncthreads();
   const int n_tiles = *p.n_tiles;
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
@@ -283,7 +288,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     if (k != region) {
       __syncthreads();
-      load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
+      if (kSplit) load_density_f32(p.fp.mlp + (size_t)k * kDensityParams, s_w);
+      else load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
       __syncthreads();
       region = k;
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
@@ -319,7 +325,13 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
     }
     float raw[kOut];
-    mlp_f32_smem(s_w, feat, raw);
+    if (kSplit) {
+      float sh[kSh];
+      sh4_f32(d, sh);  // the chunk's ray: the same for every lane
+      split_f32_smem(s_w, s_w + kDensityParams, feat, sh, raw);
+    } else {
+      mlp_f32_smem(s_w, feat, raw);
+    }
     float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
       sigma = expf(raw[0]);
@@ -555,6 +567,9 @@ nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t 
   if (!f->boxes || !f->tables || !f->mlp) return fail(NERFXL_E_INVALID, "null field pointer");
   if (f->occupancy && (f->occ_res < 1 || f->occ_res > 1024))
     return fail(NERFXL_E_INVALID, "occupancy grid resolution must be in [1, 1024]");
+  if (f->arch != NERFXL_ARCH_FUSED && f->arch != NERFXL_ARCH_SPLIT) return fail(NERFXL_E_INVALID, "unknown arch");
+  if (f->arch == NERFXL_ARCH_SPLIT && (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32))
+    return fail(NERFXL_E_UNSUPPORTED, "the split representation is built for FP32 tables and MLP");
   return NERFXL_OK;
 }
 
@@ -687,6 +702,15 @@ int64_t nerfxl_mlp_params(int32_t mlp_in, int32_t width) {
   return (int64_t)mlp_in * width + (int64_t)width * width + (int64_t)width * 4;
 }
 
+int64_t nerfxl_field_mlp_params(const nerfxl_field* f) {
+  if (!f || f->K < 1 || f->mlp_in < 1 || f->mlp_width < 1) return -1;
+  const int64_t W = f->mlp_width;
+  if (f->arch == NERFXL_ARCH_SPLIT)
+    return (int64_t)f->K * (f->mlp_in * W + W * kGeo) + (kColorIn * W + W * W + W * kOut);
+  if (f->arch != NERFXL_ARCH_FUSED) return -1;
+  return (int64_t)f->K * nerfxl_mlp_params(f->mlp_in, f->mlp_width);
+}
+
 int32_t nerfxl_max_chunks(const nerfxl_sampling* s, int32_t K) {
   if (!s) return -1;
   const int ms = s->max_segments > 0 ? s->max_segments : std::min<int>(K, kMaxSeg);
@@ -763,10 +787,15 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   const bool per_sample = (s->flags & NERFXL_SAMPLE_COMPOSITE) != 0;
   p.smp4 = per_sample ? reinterpret_cast<float4*>(ws + L.smp4) : nullptr;
   p.smp2 = per_sample ? reinterpret_cast<float2*>(ws + L.smp2) : nullptr;
-  const size_t smem = sizeof(float) * kMlpParams + sizeof(int32_t) * (f->K + 1);
+  const bool split = f->arch == NERFXL_ARCH_SPLIT;
+  const size_t smem = sizeof(float) * (split ? kSplitSmemFloats : kMlpParams) + sizeof(int32_t) * (f->K + 1);
   const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
+  void (*kern)(FwdParams) = split ? k_field_fwd_f32<true> : k_field_fwd_f32<false>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                               cudaSuccess)
+    return launch_check("k_field_fwd_f32 smem attribute");
   profile_mark(0, stream);
-  k_field_fwd_f32<<<grid, kFwdThreads, smem, stream>>>(p);
+  kern<<<grid, kFwdThreads, smem, stream>>>(p);
   profile_mark(1, stream);
   st = launch_check("k_field_fwd_f32");
   if (st != NERFXL_OK) return st;

@@ -12,7 +12,7 @@
 
 #include <cuda_runtime.h>
 
-#include "nerfxl_field.cuh"
+#include "nerfxl_split.cuh"
 #include "nerfxl_host.h"
 
 namespace nerfxl {
@@ -44,15 +44,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // xi = (w >> 8) * 2^-24 in [0, 1): a 24-bit integer scaled by a power of two, exact in FP32.
 __device__ __forceinline__ float unit_float(uint32_t w) { return __uint2float_rn(w >> 8) * (1.0f / 16777216.0f); }
 
+// kSplit: the split representation, whose density needs only the region's
+// density MLP.
+template <bool kSplit>
 __global__ void __launch_bounds__(kOccThreads) k_occupancy_update(FieldPtrs fp, LevelParams lp, int G, int64_t cells,
                                                                   int blocks_per_region, uint32_t step_lo,
                                                                   uint32_t step_hi, uint2 key, float decay,
                                                                   float threshold, float* __restrict__ density,
                                                                   uint32_t* __restrict__ bits) {
-  extern __shared__ __align__(16) float s_w[];  // kMlpParams floats
+  extern __shared__ __align__(16) float s_w[];  // the region's (density) MLP block
   const int k = blockIdx.x / blocks_per_region;
   const int64_t first = (int64_t)(blockIdx.x % blocks_per_region) * kOccCellsPerBlock;
-  load_mlp_f32(fp.mlp + (size_t)k * kMlpParams, s_w);
+  if (kSplit) load_density_f32(fp.mlp + (size_t)k * kDensityParams, s_w);
+  else load_mlp_f32(fp.mlp + (size_t)k * kMlpParams, s_w);
   __syncthreads();
   const float2* table = reinterpret_cast<const float2*>(fp.tables) + (size_t)k * lp.E;
   const int64_t words = (cells + 31) / 32;
@@ -69,10 +73,19 @@ __global__ void __launch_bounds__(kOccThreads) k_occupancy_update(FieldPtrs fp, 
       float u[3];
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) u[ax] = __fdiv_rn(__fadd_rn((float)c3[ax], xi[ax]), (float)G);
-      float feat[kIn], raw[kOut];
+      float feat[kIn];
       encode_f32(lp, table, u, feat);
-      mlp_f32_smem(s_w, feat, raw);
-      const float sigma = expf(raw[0]);
+      float raw0;
+      if (kSplit) {
+        float g[kGeo];
+        density_f32_smem(s_w, feat, g);
+        raw0 = g[0];
+      } else {
+        float raw[kOut];
+        mlp_f32_smem(s_w, feat, raw);
+        raw0 = raw[0];
+      }
+      const float sigma = expf(raw0);
       const size_t at = (size_t)k * cells + cell;
       const float dn = fmaxf(__fmul_rn(decay, density[at]), sigma);
       density[at] = dn;
@@ -110,7 +123,9 @@ extern "C" nerfxl_status nerfxl_occupancy_update(const nerfxl_field* f, int32_t 
   fp.tables = static_cast<const float*>(f->tables);
   fp.mlp = static_cast<const float*>(f->mlp);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  k_occupancy_update<<<(unsigned)(bpr * f->K), kOccThreads, sizeof(float) * kMlpParams, stream>>>(
+  const bool split = f->arch == NERFXL_ARCH_SPLIT;
+  (split ? k_occupancy_update<true> : k_occupancy_update<false>)<<<(unsigned)(bpr * f->K), kOccThreads,
+                                                                    sizeof(float) * kMlpParams, stream>>>(
       fp, level_params(f), G, cells, (int)bpr, (uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), key, decay,
       threshold, density, bits);
   return launch_check("k_occupancy_update");

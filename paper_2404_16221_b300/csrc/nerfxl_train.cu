@@ -187,7 +187,7 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
   float2* sums = reinterpret_cast<float2*>(ex + ((6 * R + 4 * R) * sizeof(float) + 255) / 256 * 256);
   const int nb = (int)std::max<int64_t>(1, (n_rays + kLossThreads - 1) / kLossThreads);
   const int64_t n_tab = (int64_t)f->K * nerfxl_table_entries(f->level_res, f->L, f->log2_T) * f->F;
-  const int64_t n_mlp = (int64_t)f->K * nerfxl_mlp_params(f->mlp_in, f->mlp_width);
+  const int64_t n_mlp = nerfxl_field_mlp_params(f);
   if (cudaMemsetAsync(st->grad_tables, 0, sizeof(float) * n_tab, stream) != cudaSuccess ||
       cudaMemsetAsync(st->grad_mlp, 0, sizeof(float) * n_mlp, stream) != cudaSuccess)
     return launch_check("gradient clear");

@@ -19,6 +19,7 @@ MAX_LEVELS = 32
 
 OK, E_INVALID, E_WORKSPACE, E_CUDA, E_TIMEOUT, E_UNSUPPORTED, E_OVERFLOW = range(7)
 F32, F16, BF16, E4M3 = range(4)
+ARCH_FUSED, ARCH_SPLIT = 0, 1
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_WORKSPACE", 3: "E_CUDA", 4: "E_TIMEOUT", 5: "E_UNSUPPORTED",
                 6: "E_OVERFLOW"}
 
@@ -34,7 +35,7 @@ class FieldDesc(C.Structure):
                 ("mlp_in", C.c_int32), ("mlp_width", C.c_int32), ("level_res", C.c_int32 * MAX_LEVELS),
                 ("boxes", C.c_void_p), ("tables", C.c_void_p), ("mlp", C.c_void_p), ("table_dtype", C.c_int32),
                 ("mlp_dtype", C.c_int32), ("mlp_scales", C.c_void_p), ("occupancy", C.c_void_p),
-                ("occ_res", C.c_int32)]
+                ("occ_res", C.c_int32), ("arch", C.c_int32)]
 
 
 class AdamDesc(C.Structure):
@@ -70,6 +71,7 @@ _FP, _SP = C.POINTER(FieldDesc), C.POINTER(SamplingDesc)
 SIGNATURES = {
     "nerfxl_table_entries": (_i64, [_vp, _i32, _i32]),
     "nerfxl_mlp_params": (_i64, [_i32, _i32]),
+    "nerfxl_field_mlp_params": (_i64, [_FP]),
     "nerfxl_max_chunks": (_i32, [_SP, _i32]),
     "nerfxl_workspace_bytes": (_sz, [_FP, _SP, _i64, _i32]),
     "nerfxl_render_fwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),

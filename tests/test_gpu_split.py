@@ -1,0 +1,221 @@
+"""Split representation on the GPU (App. A.1: per-region density MLP, one
+colour MLP shared by all regions, conditioned on the view direction's
+spherical harmonics) against the FP64 oracle: forward, backward (including
+the shared colour block's gradient, reduced over every region's samples),
+the training step, skipping and the grid refresh, and argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16221_b300 import synthetic as sy
+
+import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_16221_b300 import build
+
+    build.build()
+
+
+def _split(name="grid8", L=16, log2_T=14, S=None):
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload(name, L=L, log2_T=log2_T, S=S)
+    t, _ = H.params(w)
+    n = w.K * oracle.density_params(w.mlp_in, w.W) + oracle.color_params(w.W)
+    assert n == api.split_mlp_params(w.K, w.mlp_in, w.W)
+    m = sy.split_mlp_params(w, n)
+    of = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, t.astype(np.float64), m.astype(np.float64),
+                      arch=1)
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), torch.from_numpy(m), F=w.F,
+                              mlp_in=w.mlp_in, width=w.W, arch=N.ARCH_SPLIT)
+    assert int(N.lib().nerfxl_field_mlp_params(api.C_ref(gf.desc()))) == n
+    return w, t, m, of, gf
+
+
+def _grad_ok(g, ref, tol=1e-4):
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    err = np.abs(g - ref) / max(np.abs(ref).max(), 1e-30)
+    return float(np.mean(err > tol)) <= 1e-3 and err.max() <= 100 * tol, (float(np.mean(err > tol)), float(err.max()))
+
+
+@pytest.mark.parametrize("name,n", [("grid8", 2048), ("city32", 1024), ("unit", 1024)])
+def test_split_forward_matches_oracle(name, n):
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split(name, L=16 if name != "unit" else None, log2_T=14 if name != "unit" else None)
+    o, d = sy.workload_rays(w, n, seed=61)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, len(o))
+    out = {k: v.cpu().numpy() for k, v in api.render_fwd(gf, samp, o, d, workspace=ws).items()}
+    api.check(ws)
+    ref = oracle.render(of, w.S, o, d, 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(o))])
+    errs = H.assert_forward_close(out, ref, t_far)
+    print(name, "split forward", errs)
+
+
+def test_split_colour_depends_on_view_direction():
+    """Two rays through the same point from opposite sides: the densities
+    along the shared segment agree, the colours differ."""
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split("unit", L=None, log2_T=None)
+    o = np.array([[-2.0, 0.05, 0.1], [2.0, 0.05, 0.1]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [-1.0, 0.0, 0.0]], np.float32)
+    out = api.render_fwd(gf, H.sampling(w), o, d)
+    op = out["opacity"].cpu().numpy()
+    rgb = out["rgb"].cpu().numpy()
+    ref = oracle.render(of, w.S, o, d, 1)
+    np.testing.assert_allclose(op, ref["opacity"], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(rgb, ref["rgb"], rtol=1e-5, atol=1e-6)
+    assert abs(op[0] - op[1]) < 1e-3  # same densities, traversed in opposite order
+    assert np.abs(rgb[0] - rgb[1]).max() > 1e-3
+
+
+def test_split_backward_matches_oracle():
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split()
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 1024, 62)
+    o, d = o[sel].copy(), d[sel].copy()
+    R = len(o)
+    g = sy.rng(63, "misc")
+    gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(gC), dev(gD), dev(gA), dev(gL))
+    api.check(ws)
+    gt_ref, gm_ref = oracle.render_grad(of, w.S, o, d, gC, gD, gA, gL)
+    ok, e = _grad_ok(gt.cpu().numpy(), gt_ref)
+    assert ok, ("tables", e)
+    gm = gm.cpu().numpy()
+    Pd = of.Pd
+    for part, a, b in (("density", gm[:w.K * Pd], gm_ref[:w.K * Pd]), ("colour", gm[w.K * Pd:], gm_ref[w.K * Pd:])):
+        ok, e = _grad_ok(a, b)
+        assert ok, (part, e)
+    assert np.abs(gm_ref[w.K * Pd:]).max() > 0
+
+
+def test_split_training_step_matches_oracle():
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split()
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 2048, 64)
+    o, d = o[sel].copy(), d[sel].copy()
+    tgt = sy.rng(65, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
+    trainer = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    L = trainer.step(o, d, tgt).cpu().numpy()
+    L_ref, gt_ref, gm_ref = oracle.loss_grad(of, w.S, o, d, tgt, 0.01)
+    assert abs(L[0] - L_ref) <= 1e-5 * L_ref
+    for g, ref in ((trainer.grad_tables, gt_ref), (trainer.grad_mlp, gm_ref)):
+        ok, e = _grad_ok(g.cpu().numpy(), ref)
+        assert ok, e
+    delta = gf.mlp.cpu().numpy().astype(np.float64) - m
+    big = np.abs(gm_ref) > 1e-3 * np.abs(gm_ref).max()
+    assert np.mean(np.abs(delta[big] + 1e-2 * np.sign(gm_ref[big])) <= 2e-6) >= 0.999
+
+
+def test_split_with_occupancy_and_refresh():
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split()
+    G = 16
+    grid = api.OccupancyGrid(w.K, G, decay=0.9, threshold=1.0, seed=77)
+    grid.update(gf)
+    dens = np.zeros((w.K, G ** 3))
+    bits = oracle.occupancy_update(of, G, 0, 77, 0.9, 1.0, dens)
+    got = grid.density.cpu().numpy().astype(np.float64)
+    assert (np.abs(got - dens) / dens).max() <= 1e-5
+    on = np.unpackbits(bits.view(np.uint8), bitorder="little")
+    assert 0.05 < on.mean() < 0.95
+    grid.bits.copy_(torch.from_numpy(bits.view(np.int32)))  # the oracle's bits: identical decisions
+    grid.attach(gf)
+    ofo = of.with_occupancy(bits, G)
+    o, d = sy.workload_rays(w, 2048, seed=66)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, len(o))
+    out = {k: v.cpu().numpy() for k, v in api.render_fwd(gf, samp, o, d, workspace=ws).items()}
+    ref = oracle.render(ofo, w.S, o, d, 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(o))])
+    H.assert_forward_close(out, ref, t_far)
+    assert api.workspace_stats(ws)[0] == int(ref["n_samples"].sum())
+
+
+def test_split_rejects_unbuilt_forms():
+    from paper_2404_16221_b300 import api, native as N
+
+    w, t, m, of, gf = _split()
+    g16 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), torch.from_numpy(m).to(
+        torch.bfloat16), F=w.F, mlp_in=w.mlp_in, width=w.W, arch=N.ARCH_SPLIT)
+    with pytest.raises(N.NerfxlError) as e:
+        api.render_fwd(g16, H.sampling(w), *sy.workload_rays(w, 16))
+    assert "split representation is built for FP32" in str(e.value)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    o, d = (torch.from_numpy(a).cuda() for a in sy.workload_rays(w, 16))
+    out = torch.empty(16, 3, device="cuda")
+    st = N.lib().nerfxl_render_fwd(api.C_ref(g16.desc()), api.C_ref(H.sampling(w).desc()), 16, N._ptr(o), N._ptr(d),
+                                   N._ptr(out), N._ptr(out), N._ptr(out), None, N._ptr(ws), ws.numel(), N._stream())
+    assert st == N.E_UNSUPPORTED
+    gf.arch = 7
+    with pytest.raises(N.NerfxlError) as e:
+        api.render_fwd(gf, H.sampling(w), *sy.workload_rays(w, 16))
+    assert e.value.status == N.E_INVALID
+
+
+def _psnr(a, b):
+    return 10 * np.log10(1.0 / max(float(np.mean((np.asarray(a, np.float64) - b) ** 2)), 1e-12))
+
+
+def test_split_training_gains():
+    """Train the split representation on the K=8 blob scene with the
+    project's kernels: the training views are fitted closely and held-out
+    PSNR rises well above the initial field's. (With 16 training views the
+    view-dependent colour MLP fits them at ~38 dB but generalises to the 4
+    held-out views less well than the view-independent fused MLP: ~19.8 vs
+    ~23.3 dB after 400 steps.)"""
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload("train8", L=16, log2_T=16)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    t0, _ = sy.field_params(w, E, oracle.mlp_params(w.mlp_in, w.W), table_std=1e-4, mlp_std=0.1,
+                            table_init="uniform")
+    n = w.K * oracle.density_params(w.mlp_in, w.W) + oracle.color_params(w.W)
+    m0 = sy.split_mlp_params(w, n, 0.1)
+    blobs = sy.blobs(200, w.seed)
+    o_tr, d_tr = sy.orbit_cameras(16, 3.0, 64, 64, 50.0, 0, 20)
+    o_te, d_te = sy.orbit_cameras(4, 3.0, 64, 64, 50.0, 16, 20)
+    of = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, t0.astype(np.float64),
+                      m0.astype(np.float64), arch=1)
+    tgt_tr = oracle.blob_render(of, w.S, o_tr, d_tr, blobs)[0].astype(np.float32)
+    tgt_te = oracle.blob_render(of, w.S, o_te, d_te, blobs)[0]
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t0), torch.from_numpy(m0),
+                              arch=N.ARCH_SPLIT)
+    tr = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
+    g = sy.rng(16, "batch")
+    o_dev, d_dev = torch.from_numpy(o_tr).cuda(), torch.from_numpy(d_tr).cuda()
+    tgt_dev = torch.from_numpy(tgt_tr).cuda()
+    for s in range(400):
+        idx = torch.from_numpy(g.integers(0, len(o_tr), 8192)).cuda()
+        tr.step(o_dev[idx], d_dev[idx], tgt_dev[idx])
+    out = api.render_fwd(gf, H.sampling(w), o_te, d_te)
+    init = _psnr(oracle.render(of, w.S, o_te, d_te, 1)["rgb"], tgt_te)
+    trained = _psnr(out["rgb"].cpu().numpy(), tgt_te)
+    fit = _psnr(api.render_fwd(gf, H.sampling(w), o_tr[:16384], d_tr[:16384])["rgb"].cpu().numpy(), tgt_tr[:16384])
+    print("split representation PSNR: held-out initial %.2f, trained %.2f; training views %.2f" % (init, trained, fit))
+    assert trained > init + 4.0
+    assert fit > 33.0

@@ -241,6 +241,9 @@ def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
 # forward, then dX (12,800) and dW (12,800): 38,400 per sample.
 MLP_FWD_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 4)
 BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
+# split representation: density 32-64-16 + colour 32-64-64-3 (Wc3 counted as stored, 64 x 4)
+SPLIT_FWD_FLOP = 2 * (32 * 64 + 64 * 16) + 2 * (32 * 64 + 64 * 64 + 64 * 4)
+SPLIT_BWD_FLOP = 3 * SPLIT_FWD_FLOP
 # Algorithmic bytes of the tensor-core backward field kernel per sample (L=16
 # levels, F=2, 8 corners): its per-tile records (16-bit features 32 x 2 B,
 # geometry 8 x 4 B, chunk adjoints 32 B per 32 samples) and the read-modify-write
@@ -415,8 +418,11 @@ def main():
     for label, bits in (("no_grid", None), ("grid", occ_bits)):
         fmix.set_occupancy(bits, G_occ)
         r = fwd_form(w, fmix, samp, o_dev, d_dev, "k_field_fwd_tc", 8 * w.F * 2 * w.L)
-        occ["fwd_f16tab_bf16mlp_" + label] = {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0),
-                                             "samples_per_ray": r["samples"] / R}
+        km = statistics.mean(r["kern_ms"])
+        occ["fwd_f16tab_bf16mlp_" + label] = {
+            "rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0), "samples_per_ray": r["samples"] / R,
+            "field_kernel_ms": km, "chunk_fill": r["samples"] / (32.0 * max(r["chunks"], 1)),
+            "field_gbs_algorithmic": r["samples"] * 8 * w.F * 2 * w.L / (km / 1000.0) / 1e9}
         del r
         otrainer = api.Trainer(fmix, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01,
                                master_tables=torch.from_numpy(tables), master_mlp=torch.from_numpy(mlp))
@@ -452,9 +458,19 @@ def main():
     fsplit = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.as_tensor(tables).to(dev), m_split, device=dev,
                                   arch=N.ARCH_SPLIT)
     r = fwd_form(w, fsplit, samp, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
-    split = {"fwd_fp32": {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0),
-                          "kernel_ms": statistics.mean(r["kern_ms"])}}
+    km = statistics.mean(r["kern_ms"])
+    split = {"fwd_fp32": {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0), "kernel_ms": km,
+                          "mlp_tflops_algorithmic": r["samples"] * SPLIT_FWD_FLOP / (km / 1000.0) / 1e12,
+                          "fp32_alu_peak_tflops": fp32_alu_peak_tflops()}}
+    r_samples = r["samples"]
     del r
+    fsplit16 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.as_tensor(tables).to(dev, torch.float16),
+                                    m_split.to(torch.bfloat16), device=dev, arch=N.ARCH_SPLIT)
+    r = fwd_form(w, fsplit16, samp, o_dev, d_dev, "k_field_fwd_tc", 8 * w.F * 2 * w.L)
+    km = statistics.mean(r["kern_ms"])
+    split["fwd_f16tab_bf16mlp"] = {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0), "kernel_ms": km,
+                                   "mlp_tflops_algorithmic": r["samples"] * SPLIT_FWD_FLOP / (km / 1000.0) / 1e12}
+    del r, fsplit16
     strainer = api.Trainer(fsplit, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
     sstep = lambda: strainer.step(o_dev, d_dev, tgt)
     for _ in range(warm):
@@ -462,7 +478,9 @@ def main():
     torch.cuda.synchronize()
     s_ms, s_kern = time_steps(sstep, steps, flush, stream)
     split["train_fp32"] = {"rays_per_s": R / (statistics.mean(s_ms) / 1000.0), "kernel_ms": statistics.mean(s_kern),
-                           "kernel": "k_field_bwd_split_f32"}
+                           "kernel": "k_field_bwd_split_f32",
+                           "mlp_tflops_algorithmic": r_samples * SPLIT_BWD_FLOP / (statistics.mean(s_kern) / 1000.0)
+                           / 1e12}
     forms["grid8_split"] = {
         "split": split,
         "note": "FP32 tables and MLPs; density MLP 32-64-16 per region, colour MLP 32-64-64-3 shared, on "

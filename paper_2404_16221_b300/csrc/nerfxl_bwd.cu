@@ -801,6 +801,8 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   if (st != NERFXL_OK) return st;
   if (s->flags & NERFXL_SAMPLE_COMPOSITE)
     return set_error(NERFXL_E_UNSUPPORTED, "sample-level composition is forward only");
+  if (f->arch == NERFXL_ARCH_SPLIT && (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32))
+    return set_error(NERFXL_E_UNSUPPORTED, "the split representation's backward is built for FP32 tables and MLP");
   const bool f16tab = f->table_dtype == NERFXL_F16;
   if (!(f->table_dtype == NERFXL_F32 || f16tab) ||
       !(f->mlp_dtype == NERFXL_F32 || f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16))

@@ -97,14 +97,23 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
 }
 
 // ---------------------------------------------------------------------------
-// k_skip_empty: occupancy-grid skipping, one warp per ray. The lanes test 32
-// intervals of a segment at a time: the interval's sample point (the same
-// FP32 operations as the field kernels) falls in region cell
-// min(floor(u G), G - 1) per axis, and the interval is kept if that cell's bit
-// is set. A ballot compacts the kept interval indices, in order, into the
-// ray's list; the segment's chunk base, the ray's chunk count, the per-region
-// chunk histogram and the sample / chunk counters are then those of the kept
-// samples (a segment left empty has no chunk).
+// k_skip_empty: occupancy-grid skipping, one warp per ray. The ray's
+// intervals are numbered in ray order (segment by segment) and tested 32 at a
+// time, lane j of a group taking flat interval 32 gi + j. Lane k holds
+// segment k and its first flat index; a lane finds its segment from the
+// group's segment-start mask (an OR-reduction over the lanes), computes the
+// interval's sample point with the same FP32 operations as the field kernels
+// (the reciprocal box extents come from a per-CTA table, computed once with
+// the same IEEE division), and loads the word holding the bit of its region
+// cell min(floor(u G), G - 1). The loads of up to kSkipBatch groups are in
+// flight together; then a ballot per group compacts the kept interval
+// indices, in order, into the ray's list. Lane k counts its segment's kept
+// samples; warp scans give each segment its list start and chunk base, and
+// the ray's chunk count, the per-region chunk histogram and the sample /
+// chunk counters become those of the kept samples (an emptied segment has no
+// chunk).
+
+constexpr int kSkipBatch = 4;
 
 __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ rays_o, const float* __restrict__ rays_d,
                                                     int64_t R, const float* __restrict__ boxes, int K, SampParams sp,
@@ -115,40 +124,82 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
   extern __shared__ float s_mem[];
   float* s_boxes = s_mem;                                      // [K][6]
   int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [K]
+  float* s_inv = s_mem + 7 * K;                                // [K][3] 1 / box extent
   __shared__ unsigned long long s_samples, s_chunks;
   for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) {
+    const int k = i / 3, ax = i % 3;
+    s_inv[i] = __fdiv_rn(1.0f, __fsub_rn(boxes[6 * k + 3 + ax], boxes[6 * k + ax]));
+  }
   for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
   if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
   __syncthreads();
 
+  const unsigned kFull = 0xFFFFFFFFu;
   const int lane = threadIdx.x % kWarp;
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   if (r < R) {  // warp-uniform
     const RayHdr h = hdr[r];
+    const int nseg = h.nseg;
     float o[3], d[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       o[ax] = rays_o[3 * r + ax];
       d[ax] = rays_d[3 * r + ax];
     }
+    // lane k < nseg: segment k and its first flat interval index
+    SegDesc my = {0.0f, 0.0f, 0, 0};
+    if (lane < nseg) my = segs[r * sp.max_seg + lane];
+    const int my_n = lane < nseg ? seg_n(my) : 0;
+    int incl = my_n;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int my_start = incl - my_n;
+    const int my_end = incl;
+    const int total = __shfl_sync(kFull, incl, kWarp - 1);
     const size_t words = ((size_t)G * G * G + 31) / 32;
-    int cbase = 0, list = 0;
-    for (int k = 0; k < h.nseg; ++k) {
-      SegDesc sd = segs[r * sp.max_seg + k];
-      const int n = seg_n(sd), reg = seg_region(sd);
-      const uint32_t* bits = occ + (size_t)reg * words;
-      const float* box = s_boxes + 6 * reg;
-      int nk = 0;
-      for (int i0 = 0; i0 < n; i0 += kWarp) {
-        const int i = i0 + lane;
-        bool keep = false;
-        if (i < n) {
+    int kept_before = 0;  // kept samples of the ray so far (flat order)
+    int my_count = 0;     // lane k: kept samples of segment k
+    for (int base = 0; base < total; base += kSkipBatch * kWarp) {
+      uint32_t word[kSkipBatch];
+      int bit[kSkipBatch], iv[kSkipBatch];
+#pragma unroll
+      for (int gi = 0; gi < kSkipBatch; ++gi) {
+        word[gi] = 0u;
+        bit[gi] = 0;
+        iv[gi] = 0;
+        const int gbase = base + gi * kWarp;
+        if (gbase >= total) continue;  // warp-uniform
+        const int j = gbase + lane;
+        // segment of j: the last segment starting at or before j (every
+        // segment has >= 1 interval, so the starts strictly increase)
+        const bool mine = lane < nseg;
+        const unsigned heads = __reduce_or_sync(
+            kFull, (mine && my_start >= gbase && my_start < gbase + kWarp) ? 1u << (my_start - gbase) : 0u);
+        const int before = __popc(__ballot_sync(kFull, mine && my_start < gbase));
+        const int k = before + __popc(heads & (lane == 31 ? kFull : ((2u << lane) - 1u))) - 1;
+        SegDesc sd;
+        sd.t0 = __shfl_sync(kFull, my.t0, k);
+        sd.t1 = __shfl_sync(kFull, my.t1, k);
+        sd.jlo_n = __shfl_sync(kFull, my.jlo_n, k);
+        sd.reg_cb = __shfl_sync(kFull, my.reg_cb, k);
+        const int i = j - __shfl_sync(kFull, my_start, k);
+        iv[gi] = i;
+        if (j < total) {
           float a, b;
           segment_interval(sd, h.tn, h.delta, i, a, b);
           const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
           float x[3], u[3];
           sample_point(o, d, tbar, x);
-          region_coord(box, x, u);
+          const int reg = seg_region(sd);
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {  // region_coord with the CTA's reciprocal extents
+            const float v = __fmul_rn(__fsub_rn(x[ax], s_boxes[6 * reg + ax]), s_inv[3 * reg + ax]);
+            u[ax] = fminf(fmaxf(v, 0.0f), 1.0f);
+          }
           int c[3];
 #pragma unroll
           for (int ax = 0; ax < 3; ++ax) {
@@ -156,25 +207,50 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
             level_cell(u[ax], G, c[ax], fr);
           }
           const uint32_t cell = (uint32_t)c[0] + (uint32_t)G * ((uint32_t)c[1] + (uint32_t)G * (uint32_t)c[2]);
-          keep = (__ldg(bits + (cell >> 5)) >> (cell & 31u)) & 1u;
+          word[gi] = __ldg(occ + (size_t)reg * words + (cell >> 5));
+          bit[gi] = (int)(cell & 31u);
         }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-        if (keep) kept[r * sp.max_int + list + nk + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
-        nk += __popc(m);
       }
-      const int nch = (nk + kWarp - 1) / kWarp;
-      if (lane == 0) {
-        seg_keep[r * sp.max_seg + k] = nk | (list << 16);
-        segs[r * sp.max_seg + k].reg_cb = (reg & 0xFFFF) | (cbase << 16);
-        if (nch) atomicAdd(&s_cnt[reg], nch);
+#pragma unroll
+      for (int gi = 0; gi < kSkipBatch; ++gi) {
+        const int gbase = base + gi * kWarp;
+        if (gbase >= total) break;  // warp-uniform
+        const int j = gbase + lane;
+        const bool keep = j < total && ((word[gi] >> bit[gi]) & 1u);
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) kept[r * sp.max_int + kept_before + __popc(m & ((1u << lane) - 1u))] = (uint16_t)iv[gi];
+        kept_before += __popc(m);
+        // lane k: the part of this group inside segment k's flat range
+        const int lo = min(max(my_start - gbase, 0), kWarp), hi = min(max(my_end - gbase, 0), kWarp);
+        const unsigned below_hi = hi >= kWarp ? kFull : ((1u << hi) - 1u);
+        const unsigned below_lo = lo >= kWarp ? kFull : ((1u << lo) - 1u);
+        my_count += __popc(m & below_hi & ~below_lo);
       }
-      cbase += nch;
-      list += nk;
     }
+    // per segment: list start and chunk base (exclusive scans over the lanes)
+    const int my_nch = (my_count + kWarp - 1) / kWarp;
+    int inc_c = my_count, inc_h = my_nch;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+      const int vc = __shfl_up_sync(kFull, inc_c, off);
+      const int vh = __shfl_up_sync(kFull, inc_h, off);
+      if (lane >= off) {
+        inc_c += vc;
+        inc_h += vh;
+      }
+    }
+    if (lane < nseg) {
+      const int reg = seg_region(my);
+      const int cbase = inc_h - my_nch;
+      seg_keep[r * sp.max_seg + lane] = my_count | ((inc_c - my_count) << 16);
+      segs[r * sp.max_seg + lane].reg_cb = (reg & 0xFFFF) | (cbase << 16);
+      if (my_nch) atomicAdd(&s_cnt[reg], my_nch);
+    }
+    const int nchunk = __shfl_sync(kFull, inc_h, kWarp - 1);
     if (lane == 0) {
-      hdr[r].nchunk = cbase;
-      atomicAdd(&s_samples, (unsigned long long)list);
-      atomicAdd(&s_chunks, (unsigned long long)cbase);
+      hdr[r].nchunk = nchunk;
+      atomicAdd(&s_samples, (unsigned long long)kept_before);
+      atomicAdd(&s_chunks, (unsigned long long)nchunk);
     }
   }
   __syncthreads();
@@ -568,8 +644,8 @@ nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t 
   if (f->occupancy && (f->occ_res < 1 || f->occ_res > 1024))
     return fail(NERFXL_E_INVALID, "occupancy grid resolution must be in [1, 1024]");
   if (f->arch != NERFXL_ARCH_FUSED && f->arch != NERFXL_ARCH_SPLIT) return fail(NERFXL_E_INVALID, "unknown arch");
-  if (f->arch == NERFXL_ARCH_SPLIT && (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32))
-    return fail(NERFXL_E_UNSUPPORTED, "the split representation is built for FP32 tables and MLP");
+  if (f->arch == NERFXL_ARCH_SPLIT && f->mlp_dtype == NERFXL_E4M3)
+    return fail(NERFXL_E_UNSUPPORTED, "the split representation is built for FP32, BF16 and FP16 MLPs");
   return NERFXL_OK;
 }
 
@@ -644,7 +720,8 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
     if (f->occupancy) {
       if (!sp.seg_keep) return set_error(NERFXL_E_INVALID, "occupancy lists not attached to the sampling");
       const int64_t warps_per_block = threads / kWarp;
-      k_skip_empty<<<(int)((R + warps_per_block - 1) / warps_per_block), threads, smem, stream>>>(
+      k_skip_empty<<<(int)((R + warps_per_block - 1) / warps_per_block), threads, smem + sizeof(float) * 3 * K,
+                     stream>>>(
           rays_o, rays_d, R, f->boxes, K, sp, f->occupancy, f->occ_res, reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
           reinterpret_cast<SegDesc*>(ws + L.segs), reinterpret_cast<int32_t*>(ws + L.seg_keep),
           reinterpret_cast<uint16_t*>(ws + L.kept), counts, hdr_words + 0);

@@ -12,6 +12,12 @@
 //   layer 2  h1 = relu(D1) -> A1; D2 = A1 W2        (4 MMAs)
 //   layer 3  h2 = relu(D2) -> A0; D3[128x16] = A0 W3 (4 MMAs; columns 4..15 zero)
 //   render   sigma = exp(D3[:,0]), rgb = sigmoid(D3[:,1..3]); chunk partial
+// The split representation (kSplit) runs five layers on the same tile:
+//   density  D1 = A0 Wd1 -> relu -> A1;  G[128x16] = A1 Wd2
+//   colour   A0 = [G (16) | SH(d) (16)];  D1 = A0 Wc1 -> relu -> A1;
+//            D2 = A1 Wc2 -> relu -> A0;  D3 = A0 Wc3;  sigma = exp(G[:,0])
+// with the region's density weights reloaded per region and the shared
+// colour weights staged once per CTA.
 // One elected thread issues the MMAs and commits them to an mbarrier; each
 // warp reads 16 accumulator columns of its lane quarter with tcgen05.ld.
 // Waits on the mbarrier are bounded: on expiry the kernel flags
@@ -22,7 +28,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
-#include "nerfxl_field.cuh"
+#include "nerfxl_split.cuh"
 #include "nerfxl_half.cuh"
 #include "nerfxl_host.h"
 #include "nerfxl_tc.cuh"
@@ -41,7 +47,9 @@ constexpr uint32_t kOffA1 = kOffA0 + 128 * 128;   // 128 rows x 128 B
 constexpr uint32_t kOffB1 = kOffA1 + 128 * 128;   // 64 rows (n) x 128 B (k < 32 used)
 constexpr uint32_t kOffB2 = kOffB1 + 64 * 128;    // 64 rows x 128 B
 constexpr uint32_t kOffB3 = kOffB2 + 64 * 128;    // 16 rows x 128 B
-constexpr uint32_t kOffMisc = kOffB3 + 16 * 128;  // mbarrier (8 B), tmem base (4 B)
+constexpr uint32_t kOffC1 = kOffB3 + 16 * 128;    // split: Wc1, 64 rows x 128 B (k < 32 used)
+constexpr uint32_t kOffC3 = kOffC1 + 64 * 128;    // split: Wc3, 16 rows x 128 B
+constexpr uint32_t kOffMisc = kOffC3 + 16 * 128;  // mbarrier (8 B), tmem base (4 B)
 constexpr uint32_t kOffBase = kOffMisc + 64;      // int32 base[K+1]
 constexpr size_t kTcSmemFixed = kOffBase + 1024;  // + 1024 slack for the alignment of the base
 
@@ -93,6 +101,43 @@ struct MlpOp {
     }
   }
 };
+
+// Split representation, 16-bit kinds: B tiles of the region's density MLP
+// (B1 <- Wd1 [32][64], B3 <- Wd2 [64][16]) and of the shared colour MLP
+// (C1 <- Wc1 [32][64], B2 <- Wc2 [64][64], C3 <- Wc3 [64][4], rows >= 4 zero).
+template <bool kBF16>
+__device__ void load_density_tc(const void* blk, char* sm) {
+  uint16_t* b1 = reinterpret_cast<uint16_t*>(sm + kOffB1);
+  uint16_t* b3 = reinterpret_cast<uint16_t*>(sm + kOffB3);
+  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    b1[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, i);
+  }
+  for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
+    const int n = i / kWidth, k = i % kWidth;  // B3 row n = output n of Wd2
+    b3[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kIn * kWidth + k * kGeo + n);
+  }
+}
+
+template <bool kBF16>
+__device__ void load_color_tc(const void* blk, char* sm) {
+  uint16_t* c1 = reinterpret_cast<uint16_t*>(sm + kOffC1);
+  uint16_t* b2 = reinterpret_cast<uint16_t*>(sm + kOffB2);
+  uint16_t* c3 = reinterpret_cast<uint16_t*>(sm + kOffC3);
+  for (int i = threadIdx.x; i < kColorIn * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    c1[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, i);
+  }
+  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    b2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kColorIn * kWidth + i);
+  }
+  for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
+    const int n = i / kWidth, k = i % kWidth;
+    c3[tc::sw128_offset(n, k) >> 1] =
+        n < kOut ? Half2Of<kBF16>::bits(blk, kColorIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
+  }
+}
 
 // E4M3: byte (row, k) of a swizzled tile sits at row*128 + ((k/16 ^ row%8) * 16) + k%16.
 __device__ __forceinline__ uint32_t sw128_byte(uint32_t row, uint32_t k) {
@@ -173,8 +218,9 @@ struct FwdTcParams {
   int32_t* err;
 };
 
-template <bool kF16Table, int kKind, bool kRec>
+template <bool kF16Table, int kKind, bool kRec, bool kSplit>
 __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
+  static_assert(!kSplit || (!kRec && kKind != kKindE4M3), "the split form is a 16-bit forward");
   using Op = MlpOp<kKind>;
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
@@ -206,6 +252,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   const uint32_t b1 = sbase + kOffB1, b2 = sbase + kOffB2, b3 = sbase + kOffB3;
   using TabT = typename TableOf<kF16Table>::T;
 
+  const uint32_t c1 = sbase + kOffC1, c3 = sbase + kOffC3;
+  if (kSplit) load_color_tc<kKind == kKindBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm);
   const int n_sub = *p.n_tiles * (kChunksPerTile / kTcChunks);
   int region = -1;
   const TabT* table = nullptr;
@@ -215,7 +263,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
     if (k != region) {
       __syncthreads();
-      Op::load_weights(static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * kElem, sm);
+      if (kSplit) load_density_tc<kKind == kKindBF16>(static_cast<const char*>(p.mlp) + (size_t)k * kDensityParams * 2, sm);
+      else Op::load_weights(static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * kElem, sm);
       if (kKind == kKindE4M3) {
 #pragma unroll
         for (int l = 0; l < 3; ++l) scale[l] = p.mlp_scales[3 * k + l];
@@ -234,6 +283,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     SegDesc sd = {0.0f, 0.0f, 0, 0};
     int c = 0, seg_count = 0;
     uint32_t ray = 0;
+    float dir[3] = {0.0f, 0.0f, 0.0f};  // the ray's direction (the split form's colour input)
     if (chunk_ok) {
       ray = ref.x;
       const int seg = ref.y >> 16;
@@ -250,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         for (int ax = 0; ax < 3; ++ax) {
           o[ax] = p.rays_o[3 * (size_t)ray + ax];
           d[ax] = p.rays_d[3 * (size_t)ray + ax];
+          dir[ax] = d[ax];
         }
         float a, b;
         segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
@@ -286,6 +337,80 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
           if (chunk_ok) p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = t * kTcChunks + q;
         }
       }
+    }
+    if constexpr (kSplit) {
+      // one layer: issue its MMAs (one thread), wait (bounded), make TMEM visible
+      auto layer = [&](uint32_t d_tm, uint32_t a_sm, uint32_t b_sm, uint32_t id, int steps) -> bool {
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          for (int kk = 0; kk < steps; ++kk)
+            Op::mma(d_tm, tc::desc_sw128(a_sm + 32 * kk), tc::desc_sw128(b_sm + 32 * kk), id, kk);
+          tc::mma_commit(mbar);
+        }
+        const bool done = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
+        phase ^= 1;
+        if (__syncthreads_or(!done)) return false;
+        tc::fence_after_sync();
+        return true;
+      };
+      float v[16];
+      // density: D1 = X Wd1 -> relu -> A1; G = A1 Wd2 (columns 64..79)
+      if (!layer(tmem, a0, b1, idesc64, kSteps32)) { failed = true; break; }
+      tc::tmem_ld16(tmem_q + 16 * g, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      Op::store16(a1, row, g, v);
+      if (!layer(tmem + 64, a1, b3, idesc16, kSteps64)) { failed = true; break; }
+      // colour input [G | SH(d)] -> A0 columns 0..31
+      float g0 = 0.0f;
+      if (g == 0) {
+        tc::tmem_ld16(tmem_q + 64, v);
+        tc::tmem_ld_wait();
+        g0 = v[0];
+        Op::store16(a0, row, 0, v);
+      } else if (g == 1) {
+        float sh[kSh];
+        sh4_f32(dir, sh);
+        Op::store16(a0, row, 1, sh);
+      }
+      if (!layer(tmem, a0, c1, idesc64, kSteps32)) { failed = true; break; }
+      tc::tmem_ld16(tmem_q + 16 * g, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      Op::store16(a1, row, g, v);
+      if (!layer(tmem + 64, a1, b2, idesc64, kSteps64)) { failed = true; break; }
+      tc::tmem_ld16(tmem_q + 64 + 16 * g, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      Op::store16(a0, row, g, v);
+      if (!layer(tmem, a0, c3, idesc16, kSteps64)) { failed = true; break; }
+      if (g == 0) {
+        tc::tmem_ld16(tmem_q, v);
+        tc::tmem_ld_wait();
+        if (chunk_ok) {
+          float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+          if (valid) {
+            sigma = expf(g0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[j]));
+          }
+          const Partial pt = render_chunk(sigma, rgb, tr, dl, lane, nullptr, kTcRows);
+          if (lane == 0) {
+            float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
+            dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
+            dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();  // A tiles and TMEM free for the next tile
+      continue;
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -417,18 +542,26 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   const bool recs = rec.feat != nullptr;
   if (recs && kind == kKindE4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
   void (*kern)(FwdTcParams) = nullptr;
-  if (f16tab) {
-    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, true> : k_field_fwd_tc<true, kKindF16, true>;
+  if (f->arch == NERFXL_ARCH_SPLIT) {
+    if (recs || kind == kKindE4M3)
+      return set_error(NERFXL_E_UNSUPPORTED, "the split representation's tensor-core form is a BF16/FP16 forward");
+    if (f16tab)
+      kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, false, true> : k_field_fwd_tc<true, kKindF16, false, true>;
     else
-      kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, false>
-                               : (kind == kKindF16 ? k_field_fwd_tc<true, kKindF16, false>
-                                                   : k_field_fwd_tc<true, kKindE4M3, false>);
+      kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, false, true>
+                               : k_field_fwd_tc<false, kKindF16, false, true>;
+  } else if (f16tab) {
+    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, true, false> : k_field_fwd_tc<true, kKindF16, true, false>;
+    else
+      kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, false, false>
+                               : (kind == kKindF16 ? k_field_fwd_tc<true, kKindF16, false, false>
+                                                   : k_field_fwd_tc<true, kKindE4M3, false, false>);
   } else {
-    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, true> : k_field_fwd_tc<false, kKindF16, true>;
+    if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, true, false> : k_field_fwd_tc<false, kKindF16, true, false>;
     else
-      kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, false>
-                               : (kind == kKindF16 ? k_field_fwd_tc<false, kKindF16, false>
-                                                   : k_field_fwd_tc<false, kKindE4M3, false>);
+      kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, false, false>
+                               : (kind == kKindF16 ? k_field_fwd_tc<false, kKindF16, false, false>
+                                                   : k_field_fwd_tc<false, kKindE4M3, false, false>);
   }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_fwd_tc smem attribute");

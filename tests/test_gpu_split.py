@@ -156,24 +156,74 @@ def test_split_with_occupancy_and_refresh():
     assert api.workspace_stats(ws)[0] == int(ref["n_samples"].sum())
 
 
+def _rounded(a, dtype):
+    return torch.from_numpy(a).to(dtype).float().numpy()
+
+
+@pytest.mark.parametrize("tab,mlp", [(torch.float16, torch.bfloat16), (torch.float32, torch.float16),
+                                     (torch.float32, torch.bfloat16)])
+@pytest.mark.parametrize("name,n", [("grid8", 2048), ("city32", 1024)])
+def test_split_tensor_core_forward_matches_oracle(tab, mlp, name, n):
+    """The split representation on the tensor cores (five MMA layers per
+    128-row tile): against the oracle on the rounded parameters the GPU reads,
+    2e-3 absolute on RGB and opacity (activations rounded to the 16-bit type
+    between layers)."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w, t, m, of, _ = _split(name, L=16, log2_T=14 if name == "grid8" else 15)
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(tab),
+                              torch.from_numpy(m).to(mlp), F=w.F, mlp_in=w.mlp_in, width=w.W, arch=N.ARCH_SPLIT)
+    tq = _rounded(t, tab) if tab != torch.float32 else t
+    ofq = of.with_params(tq.astype(np.float64), _rounded(m, mlp).astype(np.float64))
+    o, d = sy.workload_rays(w, n, seed=67)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, len(o))
+    out = {k: v.cpu().numpy() for k, v in api.render_fwd(gf, samp, o, d, workspace=ws).items()}
+    api.check(ws)
+    ref = oracle.render(ofq, w.S, o, d, 1)
+    e_rgb = np.abs(out["rgb"] - ref["rgb"]).max()
+    e_op = np.abs(out["opacity"] - ref["opacity"]).max()
+    full = oracle.render(of, w.S, o, d, 1)
+    print(name, tab, mlp, "split tensor-core forward: rgb %.2e opacity %.2e (vs unrounded FP64 %.2e)"
+          % (e_rgb, e_op, np.abs(out["rgb"] - full["rgb"]).max()))
+    assert e_rgb <= 2e-3 and e_op <= 2e-3
+
+
 def test_split_rejects_unbuilt_forms():
     from paper_2404_16221_b300 import api, native as N
 
     w, t, m, of, gf = _split()
-    g16 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), torch.from_numpy(m).to(
-        torch.bfloat16), F=w.F, mlp_in=w.mlp_in, width=w.W, arch=N.ARCH_SPLIT)
+    g16 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                               torch.from_numpy(m).to(torch.bfloat16), F=w.F, mlp_in=w.mlp_in, width=w.W,
+                               arch=N.ARCH_SPLIT)
+    o, d = sy.workload_rays(w, 64)
+    samp = H.sampling(w)
+    # no 16-bit backward or training for the split representation
+    ws = api.alloc_workspace(g16, samp, len(o), for_backward=True)
+    api.render_fwd(g16, samp, o, d, workspace=ws)
     with pytest.raises(N.NerfxlError) as e:
-        api.render_fwd(g16, H.sampling(w), *sy.workload_rays(w, 16))
-    assert "split representation is built for FP32" in str(e.value)
-    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-    o, d = (torch.from_numpy(a).cuda() for a in sy.workload_rays(w, 16))
-    out = torch.empty(16, 3, device="cuda")
-    st = N.lib().nerfxl_render_fwd(api.C_ref(g16.desc()), api.C_ref(H.sampling(w).desc()), 16, N._ptr(o), N._ptr(d),
-                                   N._ptr(out), N._ptr(out), N._ptr(out), None, N._ptr(ws), ws.numel(), N._stream())
+        api.render_bwd(g16, samp, o, d, ws, torch.ones(len(o), 3, device="cuda"))
+    assert e.value.status == N.E_UNSUPPORTED
+    with pytest.raises(N.NerfxlError) as e:
+        api.Trainer(g16, samp, save_features=False).step(o, d, np.zeros((len(o), 3), np.float32))
+    assert e.value.status == N.E_UNSUPPORTED
+    with pytest.raises(N.NerfxlError) as e:  # the backward's records are not built for it
+        api.render_fwd(g16, api.Sampling(samp.n_samples, samp.max_segments, flags=api.SAVE_FEATURES), o, d,
+                       workspace=ws)
+    assert e.value.status == N.E_UNSUPPORTED
+    q8 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t),
+                              torch.zeros(m.shape, dtype=torch.uint8), F=w.F, mlp_in=w.mlp_in, width=w.W,
+                              arch=N.ARCH_SPLIT, mlp_scales=np.ones((w.K, 3), np.float32))
+    ws8 = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    od = [torch.from_numpy(a).cuda() for a in (o, d)]
+    out = torch.empty(len(o), 3, device="cuda")
+    st = N.lib().nerfxl_render_fwd(api.C_ref(q8.desc()), api.C_ref(samp.desc()), len(o), N._ptr(od[0]),
+                                   N._ptr(od[1]), N._ptr(out), N._ptr(out), N._ptr(out), None, N._ptr(ws8),
+                                   ws8.numel(), N._stream())
     assert st == N.E_UNSUPPORTED
     gf.arch = 7
     with pytest.raises(N.NerfxlError) as e:
-        api.render_fwd(gf, H.sampling(w), *sy.workload_rays(w, 16))
+        api.render_fwd(gf, samp, o, d)
     assert e.value.status == N.E_INVALID
 
 

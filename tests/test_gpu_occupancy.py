@@ -283,3 +283,44 @@ def test_training_with_a_refreshed_grid():
           % (p_plain, n_plain, p_grid, n_grid, 100 * occ))
     assert p_grid > p_plain - 0.5
     assert n_grid < 0.25 * n_plain
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_empty_grid_renders_nothing_and_has_no_gradient(mixed):
+    """Every cell clear: no sample survives, the rays render black with
+    opacity 0, no chunk is formed, and the backward leaves every gradient 0."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m, table_dtype=torch.float16 if mixed else None,
+                     mlp_dtype=torch.bfloat16 if mixed else None)
+    G = 8
+    gf.set_occupancy(np.zeros((w.K, oracle.occupancy_words(G)), np.uint32), G)
+    o, d = sy.workload_rays(w, 1024, seed=71)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, len(o), for_backward=True)
+    out = api.render_fwd(gf, samp, o, d, workspace=ws)
+    api.check(ws)
+    for k in ("rgb", "depth", "opacity", "dist"):
+        assert not out[k].any(), k
+    assert api.workspace_stats(ws) == (0, 0)
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, torch.ones(len(o), 3, device="cuda"))
+    api.check(ws)
+    assert not gt.any() and not gm.any()
+
+
+def test_no_rays_with_a_grid():
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    gf.set_occupancy(np.full((w.K, oracle.occupancy_words(4)), 0xFFFFFFFF, np.uint32), 4)
+    z = np.zeros((0, 3), np.float32)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, 0, for_backward=True)
+    out = api.render_fwd(gf, samp, z, z, workspace=ws)
+    assert out["rgb"].shape == (0, 3)
+    api.render_bwd(gf, samp, z, z, ws, torch.zeros(0, 3, device="cuda"))
+    api.check(ws)

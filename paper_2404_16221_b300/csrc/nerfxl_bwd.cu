@@ -596,15 +596,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       for (int s = 0; s < kBwdThreads; ++s) acc = fmaf(s_C[s * kActPitch + n], s_X[s * kSplitXPitch + kColorIn + m], acc);
       aWc3 += acc;
     }
-    // ---- dL/dzc2 = (hc2 > 0) Wc3 go   (own row, written after everyone read C)
-    float gz[kWidth];
-#pragma unroll
-    for (int n = 0; n < kWidth; ++n)
-      gz[n] = my_C[n] > 0.0f ? Wc3[n * kOut] * go[0] + Wc3[n * kOut + 1] * go[1] + Wc3[n * kOut + 2] * go[2] : 0.0f;
+    // ---- dL/dzc2 = (hc2 > 0) Wc3 go, in place in the own C row once everyone has read C
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_C + q) = make_float4(gz[q], gz[q + 1], gz[q + 2], gz[q + 3]);
+#pragma unroll 4
+    for (int n = 0; n < kWidth; ++n) {
+      const float h = my_C[n];
+      my_C[n] = h > 0.0f ? Wc3[n * kOut] * go[0] + Wc3[n * kOut + 1] * go[1] + Wc3[n * kOut + 2] * go[2] : 0.0f;
+    }
     __syncthreads();
     // ---- Wc2[i][n] += sum_s hc1[s][i] dzc2[s][n]
     {
@@ -622,13 +620,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         }
       }
     }
-    // ---- dL/dzc1 = (hc1 > 0) Wc2 dzc2   (Wc2[i][n] = Wc2t[n][i])
+    // ---- dL/dzc1 = (hc1 > 0) Wc2 dzc2   (Wc2[i][n] = Wc2t[n][i]; dzc2 read from the own C row)
     float gz1c[kWidth];
 #pragma unroll
     for (int i = 0; i < kWidth; ++i) gz1c[i] = 0.0f;
-#pragma unroll 2
+#pragma unroll 1
     for (int n = 0; n < kWidth; ++n) {
-      const float gzn = gz[n];
+      const float gzn = my_C[n];
 #pragma unroll
       for (int i4 = 0; i4 < kWidth / 4; ++i4) {
         const float4 w = Wc2t[n * (kWidth / 4) + i4];
@@ -639,7 +637,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       }
     }
 #pragma unroll
-    for (int i = 0; i < kWidth; ++i) gz1c[i] = my_B[i] > 0.0f ? gz1c[i] : 0.0f;
+    for (int q = 0; q < kWidth; q += 4) {
+      const float4 hv = *reinterpret_cast<const float4*>(my_B + q);
+      gz1c[q] = hv.x > 0.0f ? gz1c[q] : 0.0f;
+      gz1c[q + 1] = hv.y > 0.0f ? gz1c[q + 1] : 0.0f;
+      gz1c[q + 2] = hv.z > 0.0f ? gz1c[q + 2] : 0.0f;
+      gz1c[q + 3] = hv.w > 0.0f ? gz1c[q + 3] : 0.0f;
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kWidth; q += 4)
@@ -661,13 +665,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         }
       }
     }
-    // ---- dL/dg = (Wc1 dzc1)[0..15] + dL/dg0 from the density
+    // ---- dL/dg = (Wc1 dzc1)[0..15] + dL/dg0 from the density (dzc1 read from the own B row)
     float gg[kGeo];
 #pragma unroll
     for (int m = 0; m < kGeo; ++m) gg[m] = 0.0f;
-#pragma unroll 4
+#pragma unroll 1
     for (int n = 0; n < kWidth; ++n) {
-      const float gzn = gz1c[n];
+      const float gzn = my_B[n];
 #pragma unroll
       for (int m4 = 0; m4 < kGeo / 4; ++m4) {
         const float4 w = Wc1t[n * (kColorIn / 4) + m4];  // Wc1[4 m4 + j][n]
@@ -678,9 +682,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       }
     }
     gg[0] += go_d;
-    // ---- recompute h1 of the density MLP
-    float h1[kWidth];
-#pragma unroll
+    // ---- recompute h1 of the density MLP into the own C row (after everyone read B and X)
+    __syncthreads();
+#pragma unroll 4
     for (int n = 0; n < kWidth; ++n) {
       float acc = 0.0f;
 #pragma unroll
@@ -691,15 +695,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         acc = fmaf(feat[4 * i4 + 2], w.z, acc);
         acc = fmaf(feat[4 * i4 + 3], w.w, acc);
       }
-      h1[n] = fmaxf(acc, 0.0f);
+      my_C[n] = fmaxf(acc, 0.0f);
     }
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < kGeo; q += 4)
       *reinterpret_cast<float4*>(my_X + q) = make_float4(gg[q], gg[q + 1], gg[q + 2], gg[q + 3]);
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_C + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
     __syncthreads();
     // ---- Wd2[n][m] += sum_s h1[s][n] dg[s][m]
     {
@@ -713,8 +713,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         aWd2[3] = fmaf(hv, v.w, aWd2[3]);
       }
     }
-    // ---- dL/dz1 = (h1 > 0) Wd2 dg
-#pragma unroll
+    // ---- dL/dz1 = (h1 > 0) Wd2 dg, in place in the own C row once everyone has read C; feat -> B
+    __syncthreads();
+#pragma unroll 4
     for (int n = 0; n < kWidth; ++n) {
       float acc = 0.0f;
 #pragma unroll
@@ -725,12 +726,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         acc = fmaf(w.z, gg[4 * m4 + 2], acc);
         acc = fmaf(w.w, gg[4 * m4 + 3], acc);
       }
-      h1[n] = h1[n] > 0.0f ? acc : 0.0f;  // now dL/dz1
+      my_C[n] = my_C[n] > 0.0f ? acc : 0.0f;
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_C + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
 #pragma unroll
     for (int q = 0; q < kIn; q += 4)
       *reinterpret_cast<float4*>(my_B + q) = make_float4(feat[q], feat[q + 1], feat[q + 2], feat[q + 3]);
@@ -751,14 +748,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         }
       }
     }
-    // ---- dL/dfeat = Wd1 dz1, then the table scatter
+    // ---- dL/dfeat = Wd1 dz1 (dz1 from the own C row), then the table scatter
     if (valid) {
       float gfeat[kIn];
 #pragma unroll
       for (int j = 0; j < kIn; ++j) gfeat[j] = 0.0f;
-#pragma unroll 4
+#pragma unroll 1
       for (int n = 0; n < kWidth; ++n) {
-        const float gzn = h1[n];
+        const float gzn = my_C[n];
 #pragma unroll
         for (int i4 = 0; i4 < kIn / 4; ++i4) {
           const float4 w = Wd1t[n * (kIn / 4) + i4];

@@ -439,6 +439,31 @@ __device__ __forceinline__ void flush_density_grad(float* __restrict__ g, const 
     if (aWd2[q] != 0.0f) atomicAdd(g + kIn * kWidth + n * kGeo + m0 + q, aWd2[q]);
 }
 
+// Stage the split weights from FP32, BF16 or FP16 blocks (FP32 in shared memory,
+// the layouts of load_density_f32 / load_color_f32).
+template <int kMlpType>
+__device__ __forceinline__ void load_split_any(const void* dens, const void* color, float* __restrict__ s_d,
+                                               float* __restrict__ s_c) {
+  if (dens) {
+    for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x)
+      s_d[(i % kWidth) * kIn + i / kWidth] = mlp_elem<kMlpType>(dens, i);
+    for (int i = threadIdx.x; i < kWidth * kGeo; i += blockDim.x)
+      s_d[kIn * kWidth + i] = mlp_elem<kMlpType>(dens, kIn * kWidth + i);
+  }
+  if (color) {
+    for (int i = threadIdx.x; i < kColorIn * kWidth; i += blockDim.x)
+      s_c[(i % kWidth) * kColorIn + i / kWidth] = mlp_elem<kMlpType>(color, i);
+    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x)
+      s_c[kColorIn * kWidth + (i % kWidth) * kWidth + i / kWidth] = mlp_elem<kMlpType>(color, kColorIn * kWidth + i);
+    for (int i = threadIdx.x; i < kWidth * kOut; i += blockDim.x)
+      s_c[kColorIn * kWidth + kWidth * kWidth + i] = mlp_elem<kMlpType>(color, kColorIn * kWidth + kWidth * kWidth + i);
+  }
+}
+
+// kF16Table / kMlpType: the parameters the forward read (FP16 tables, BF16 or
+// FP16 MLP copies); the recompute and every product run in FP32 and the
+// gradients are FP32, as for the FP32 parameters.
+template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
   float* s_d = sm;                                  // Wd1t [64][32], Wd2 [64][16]
@@ -448,9 +473,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
   float* s_C = s_B + kBwdThreads * kActPitch;       // [256][68]
   int32_t* s_base = reinterpret_cast<int32_t*>(s_C + kBwdThreads * kActPitch);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
-  const float* mlp = static_cast<const float*>(p.mlp);
+  const char* mlp = static_cast<const char*>(p.mlp);
+  constexpr size_t kEsize = kMlpType == 0 ? 4 : 2;
+  using TabT = typename TableOf<kF16Table>::T;
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
-  load_color_f32(mlp + (size_t)p.K * kDensityParams, s_c);
+  load_split_any<kMlpType>(nullptr, mlp + (size_t)p.K * kDensityParams * kEsize, s_d, s_c);
   __syncthreads();
   const int n_tiles = *p.n_tiles;
   const float4* Wd1t = reinterpret_cast<const float4*>(s_d);
@@ -469,7 +496,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
 #pragma unroll
   for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
   int region = -1;
-  const float2* table = nullptr;
+  const TabT* table = nullptr;
   float2* gtab = nullptr;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
@@ -480,10 +507,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       for (int q = 0; q < 8; ++q) aWd1[q] = 0.0f;
 #pragma unroll
       for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
-      load_density_f32(mlp + (size_t)k * kDensityParams, s_d);
+      load_split_any<kMlpType>(mlp + (size_t)k * kDensityParams * kEsize, nullptr, s_d, s_c);
       __syncthreads();
       region = k;
-      table = static_cast<const float2*>(p.tables) + (size_t)k * p.lp.E;
+      table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
     const uint2 ref = p.chunks[t * kChunksPerTile + warp];
@@ -525,7 +552,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
         float x[3];
         sample_point(o, dir, tbar, x);
         region_coord(p.fp.boxes + 6 * k, x, u);
-        encode_f32(p.lp, table, u, feat);
+        TableOf<kF16Table>::encode(p.lp, table, u, feat);
       }
     }
     // ---- forward recompute: g, xc -> X; hc1 -> B; hc2 -> C; colour logits
@@ -798,8 +825,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   if (st != NERFXL_OK) return st;
   if (s->flags & NERFXL_SAMPLE_COMPOSITE)
     return set_error(NERFXL_E_UNSUPPORTED, "sample-level composition is forward only");
-  if (f->arch == NERFXL_ARCH_SPLIT && (f->table_dtype != NERFXL_F32 || f->mlp_dtype != NERFXL_F32))
-    return set_error(NERFXL_E_UNSUPPORTED, "the split representation's backward is built for FP32 tables and MLP");
+
   const bool f16tab = f->table_dtype == NERFXL_F16;
   if (!(f->table_dtype == NERFXL_F32 || f16tab) ||
       !(f->mlp_dtype == NERFXL_F32 || f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16))
@@ -813,7 +839,9 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   char* ws = static_cast<char*>(workspace);
   const SampParams sp = samp_params(f, s, ws, L);
   float4* dpart = reinterpret_cast<float4*>(ws + L.dpartials);
-  const bool tc = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
+  // the fused representation's 16-bit forms run the tensor-core backward from
+  // per-tile records; the split representation recomputes on CUDA cores
+  const bool tc = (f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16) && f->arch == NERFXL_ARCH_FUSED;
   if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");
   if (tc && !(s->flags & NERFXL_SAVE_FEATURES)) {
     // The forward did not keep the records: rebuild them (the forward's
@@ -850,12 +878,18 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   if (f->arch == NERFXL_ARCH_SPLIT) {
     const size_t smem_s = sizeof(float) * kBwdSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
     if (smem_s > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-    if (cudaFuncSetAttribute(k_field_bwd_split_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) !=
-        cudaSuccess)
+    void (*ks)(BwdParams) = nullptr;
+    if (f->mlp_dtype == NERFXL_F32)
+      ks = f16tab ? k_field_bwd_split_f32<true, 0> : k_field_bwd_split_f32<false, 0>;
+    else if (f->mlp_dtype == NERFXL_BF16)
+      ks = f16tab ? k_field_bwd_split_f32<true, 1> : k_field_bwd_split_f32<false, 1>;
+    else
+      ks = f16tab ? k_field_bwd_split_f32<true, 2> : k_field_bwd_split_f32<false, 2>;
+    if (cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
       return launch_check("k_field_bwd_split_f32 smem attribute");
     const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);
     profile_mark(0, stream);
-    k_field_bwd_split_f32<<<grid, kBwdThreads, smem_s, stream>>>(p);
+    ks<<<grid, kBwdThreads, smem_s, stream>>>(p);
     profile_mark(1, stream);
     return launch_check("k_field_bwd_split_f32");
   }

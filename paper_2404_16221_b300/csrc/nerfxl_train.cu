@@ -168,8 +168,6 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
       !st->m_mlp || !st->v_mlp)
     return set_error(NERFXL_E_INVALID, "null train-state pointer");
   const bool tab32 = f->table_dtype == NERFXL_F32, mlp32 = f->mlp_dtype == NERFXL_F32;
-  if (f->arch == NERFXL_ARCH_SPLIT && !(tab32 && mlp32))
-    return set_error(NERFXL_E_UNSUPPORTED, "the split representation trains in FP32");
   if ((tab32 && st->tables != f->tables) || (mlp32 && st->mlp != f->mlp))
     return set_error(NERFXL_E_INVALID, "an FP32 field block must be the master itself");
   if ((!tab32 && f->table_dtype != NERFXL_F16) || (!mlp32 && f->mlp_dtype != NERFXL_BF16 && f->mlp_dtype != NERFXL_F16))

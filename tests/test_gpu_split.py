@@ -189,6 +189,68 @@ def test_split_tensor_core_forward_matches_oracle(tab, mlp, name, n):
     assert e_rgb <= 2e-3 and e_op <= 2e-3
 
 
+def test_split_mixed_backward_matches_oracle():
+    """FP16 tables + BF16 MLPs: the forward on the tensor cores, the backward
+    on CUDA cores in FP32 from the same 16-bit parameters. Against the oracle
+    on the rounded parameters, on the kink-free network (positive features
+    and hidden weights): no entry off by more than 1e-2 of max|ref| (the
+    composite adjoint starts from the forward's 16-bit-activation partials)."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    Pd, Pc = oracle.density_params(w.mlp_in, w.W), oracle.color_params(w.W)
+    g = sy.rng(24, "misc")
+    t = g.uniform(0.1, 1.0, (w.K, E, 2)).astype(np.float32)
+    dens = np.concatenate([g.uniform(0.0, 0.05, (w.K, 32 * 64)), g.normal(0.0, 0.1, (w.K, 64 * 16))], 1)
+    col = np.concatenate([g.uniform(0.0, 0.05, 32 * 64), g.uniform(0.0, 0.05, 64 * 64), g.normal(0.0, 0.1, 64 * 4)])
+    m = np.concatenate([dens.reshape(-1), col]).astype(np.float32)
+    assert m.size == w.K * Pd + Pc
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 2048, 68)
+    o, d = o[sel].copy(), d[sel].copy()
+    R = len(o)
+    gg = sy.rng(69, "misc")
+    gC, gD, gA, gL = gg.standard_normal((R, 3)), gg.standard_normal(R), gg.standard_normal(R), gg.standard_normal(R)
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                              torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(gC), dev(gD), dev(gA), dev(gL))
+    api.check(ws)
+    ofq = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, _rounded(t, torch.float16),
+                       _rounded(m, torch.bfloat16), arch=1)
+    gt_ref, gm_ref = oracle.render_grad(ofq, w.S, o, d, gC, gD, gA, gL)
+    for name, a, b in (("tables", gt.cpu().numpy(), gt_ref), ("mlp", gm.cpu().numpy(), gm_ref)):
+        err = np.abs(a.astype(np.float64).reshape(-1) - b.reshape(-1)) / np.abs(b).max()
+        print("split mixed backward", name, "max err / max |grad| %.2e" % err.max())
+        assert err.max() <= 1e-2, (name, err.max())
+
+
+def test_split_mixed_training_step_runs_and_refreshes_copies():
+    """nerfxl_step on the split representation with FP16 tables and BF16 MLPs:
+    the FP32 masters move by about lr where the gradient is clear, and the
+    16-bit copies the forward reads are their rounding."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w, t, m, of, _ = _split()
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                              torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+    tr = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=torch.from_numpy(t),
+                     master_mlp=torch.from_numpy(m))
+    o, d = sy.workload_rays(w, 2048, seed=70)
+    tgt = sy.rng(71, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
+    L = tr.step(o, d, tgt).cpu().numpy()
+    assert np.isfinite(L).all() and L[0] > 0
+    assert torch.equal(gf.mlp, tr.mlp.to(torch.bfloat16)) and torch.equal(gf.tables, tr.tables.to(torch.float16))
+    g = tr.grad_mlp.cpu().numpy()
+    moved = tr.mlp.cpu().numpy() - m
+    big = np.abs(g) > 1e-2 * np.abs(g).max()
+    assert big.sum() > 100 and np.mean(np.abs(np.abs(moved[big]) - 1e-2) < 1e-4) > 0.99
+
+
 def test_split_rejects_unbuilt_forms():
     from paper_2404_16221_b300 import api, native as N
 
@@ -198,16 +260,8 @@ def test_split_rejects_unbuilt_forms():
                                arch=N.ARCH_SPLIT)
     o, d = sy.workload_rays(w, 64)
     samp = H.sampling(w)
-    # no 16-bit backward or training for the split representation
     ws = api.alloc_workspace(g16, samp, len(o), for_backward=True)
-    api.render_fwd(g16, samp, o, d, workspace=ws)
-    with pytest.raises(N.NerfxlError) as e:
-        api.render_bwd(g16, samp, o, d, ws, torch.ones(len(o), 3, device="cuda"))
-    assert e.value.status == N.E_UNSUPPORTED
-    with pytest.raises(N.NerfxlError) as e:
-        api.Trainer(g16, samp, save_features=False).step(o, d, np.zeros((len(o), 3), np.float32))
-    assert e.value.status == N.E_UNSUPPORTED
-    with pytest.raises(N.NerfxlError) as e:  # the backward's records are not built for it
+    with pytest.raises(N.NerfxlError) as e:  # the tensor-core backward's records are not built for it
         api.render_fwd(g16, api.Sampling(samp.n_samples, samp.max_segments, flags=api.SAVE_FEATURES), o, d,
                        workspace=ws)
     assert e.value.status == N.E_UNSUPPORTED

@@ -91,3 +91,34 @@ def test_poisson_stream_reports_latency():
     assert m["requests"] == 40 and m["p50_ms"] > 0 and m["p99_ms"] >= m["p50_ms"]
     for r in reqs:
         assert r.done_s >= r.arrival_s
+
+
+@pytest.mark.parametrize("form", ["occupancy", "split"])
+def test_serving_with_a_grid_or_the_split_representation(form):
+    """The serving path renders through the same forward: a field with an
+    occupancy grid, or the split representation, serves each request as a
+    plain render of its rays does."""
+    import oracle
+    from paper_2404_16221_b300 import api, native as N, serve
+
+    w = H.workload("serve32", L=16, log2_T=16)
+    t, m = H.params(w, table_std=1.0, mlp_std=0.1)
+    if form == "split":
+        n = api.split_mlp_params(w.K, w.mlp_in, w.W)
+        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                                     torch.from_numpy(sy.split_mlp_params(w, n)).to(torch.bfloat16),
+                                     arch=N.ARCH_SPLIT)
+    else:
+        field = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+        G = 16
+        bits = sy.rng(25, "misc").integers(0, 2 ** 32, (w.K, oracle.occupancy_words(G)), dtype=np.uint64)
+        field.set_occupancy(bits.astype(np.uint32), G)
+    samp = H.sampling(w)
+    reqs = _requests(6, 9)
+    eng = serve.ServeEngine(field, samp, max_batch_rays=1 << 16, arena_pixels=1 << 18, keep_results=True)
+    eng.run(reqs, realtime=False)
+    for r in reqs:
+        o, d = serve.camera_rays(r)
+        ref = api.render_fwd(field, samp, o, d)
+        err = (r.result["rgb"] - ref["rgb"]).abs()
+        assert float(err.max()) < 1e-3 and float(err.mean()) < 1e-5, (r.rid, float(err.max()))

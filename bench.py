@@ -575,6 +575,16 @@ def main():
         return
     hbm, bf16, src = peaks()
     alu_peak = fp32_alu_peak_tflops()
+    # fractions of the peaks for the occupancy and split forms' field kernels
+    for v in forms.get("grid8_occupancy", {}).get("occupancy", {}).values():
+        if isinstance(v, dict) and "field_gbs_algorithmic" in v:
+            v["field_frac_of_hbm"] = v["field_gbs_algorithmic"] / hbm
+    for name, v in forms.get("grid8_split", {}).get("split", {}).items():
+        if "mlp_tflops_algorithmic" in v:
+            if name.endswith("fp32"):
+                v["frac_of_fp32_alu"] = v["mlp_tflops_algorithmic"] / alu_peak
+            else:
+                v["frac_of_bf16_tensor"] = v["mlp_tflops_algorithmic"] / bf16
 
     def summary(f):
         if "serve" in f or "partition" in f or "composition" in f or "occupancy" in f or "split" in f:

@@ -324,3 +324,37 @@ def test_no_rays_with_a_grid():
     assert out["rgb"].shape == (0, 3)
     api.render_bwd(gf, samp, z, z, ws, torch.zeros(0, 3, device="cuda"))
     api.check(ws)
+
+
+def test_full_size_forward_with_grid_sampled_rays():
+    """The bench's occupancy form in its launch configuration: the full grid8
+    workload (2^18 rays, L=16, T=2^19) with the blob scene's 64^3 grid, FP32
+    and FP16/BF16 fields; 1024 seeded rays checked against the oracle."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8")
+    t, m = H.params(w)
+    G = 64
+    bits = sy.blob_occupancy(w.boxes, sy.sparse_blobs(w.seed), G, 0.4)
+    o, d = sy.workload_rays(w)
+    sel = sy.subset(len(o), 1024, 103)
+    for tab, mlp in ((None, None), (torch.float16, torch.bfloat16)):
+        gf = H.gpu_field(w, t, m, table_dtype=tab, mlp_dtype=mlp)
+        gf.set_occupancy(bits, G)
+        ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+        out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+        api.check(ws)
+        got = {k: v.cpu().numpy()[sel] for k, v in out.items()}
+        tq = t if tab is None else _rounded(t, tab)
+        mq = m if mlp is None else _rounded(m, mlp)
+        of = H.oracle_field(w, tq, mq).with_occupancy(bits, G)
+        ref = oracle.render(of, w.S, o[sel], d[sel], 1)
+        if tab is None:
+            nseg, region, t0, t1, nint = oracle.segments(of, w.S, o[sel], d[sel])
+            t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sel))])
+            H.assert_forward_close(got, ref, t_far)
+        else:
+            assert np.abs(got["rgb"] - ref["rgb"]).max() <= 2e-3
+            assert np.abs(got["opacity"] - ref["opacity"]).max() <= 2e-3
+        del gf, ws, out
+        torch.cuda.empty_cache()

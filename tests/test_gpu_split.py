@@ -323,3 +323,38 @@ def test_split_training_gains():
     print("split representation PSNR: held-out initial %.2f, trained %.2f; training views %.2f" % (init, trained, fit))
     assert trained > init + 4.0
     assert fit > 33.0
+
+
+def test_full_size_split_forward_sampled_rays():
+    """The bench's split form in its launch configuration: the full grid8
+    workload (2^18 rays, L=16, T=2^19), FP32 and FP16 tables + BF16 MLPs;
+    1024 seeded rays checked against the oracle."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload("grid8")
+    t, _ = H.params(w)
+    n = api.split_mlp_params(w.K, w.mlp_in, w.W)
+    m = sy.split_mlp_params(w, n)
+    o, d = sy.workload_rays(w)
+    sel = sy.subset(len(o), 1024, 104)
+    for tab, mlp in ((torch.float32, torch.float32), (torch.float16, torch.bfloat16)):
+        gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(tab),
+                                  torch.from_numpy(m).to(mlp), arch=N.ARCH_SPLIT)
+        ws = api.alloc_workspace(gf, H.sampling(w), len(o))
+        out = api.render_fwd(gf, H.sampling(w), o, d, workspace=ws)
+        api.check(ws)
+        got = {k: v.cpu().numpy()[sel] for k, v in out.items()}
+        tq = t if tab == torch.float32 else _rounded(t, tab)
+        mq = m if mlp == torch.float32 else _rounded(m, mlp)
+        of = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, tq.astype(np.float64),
+                          mq.astype(np.float64), arch=1)
+        ref = oracle.render(of, w.S, o[sel], d[sel], 1)
+        if tab == torch.float32:
+            nseg, region, t0, t1, nint = oracle.segments(of, w.S, o[sel], d[sel])
+            t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sel))])
+            H.assert_forward_close(got, ref, t_far)
+        else:
+            assert np.abs(got["rgb"] - ref["rgb"]).max() <= 2e-3
+            assert np.abs(got["opacity"] - ref["opacity"]).max() <= 2e-3
+        del gf, ws, out
+        torch.cuda.empty_cache()

@@ -471,7 +471,7 @@ def main():
     split["fwd_f16tab_bf16mlp"] = {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0), "kernel_ms": km,
                                    "mlp_tflops_algorithmic": r["samples"] * SPLIT_FWD_FLOP / (km / 1000.0) / 1e12}
     del r
-    # mixed training of the split form: tensor-core forward, CUDA-core FP32 backward from the 16-bit copies
+    # mixed training of the split form: tensor-core forward and backward, FP32 Adam masters
     mtr = api.Trainer(fsplit16, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01,
                       master_tables=torch.as_tensor(tables), master_mlp=m_split.float().cpu())
     mst = lambda: mtr.step(o_dev, d_dev, tgt)
@@ -480,7 +480,9 @@ def main():
     torch.cuda.synchronize()
     m_ms, m_kern = time_steps(mst, steps, flush, stream)
     split["train_f16tab_bf16mlp"] = {"rays_per_s": R / (statistics.mean(m_ms) / 1000.0),
-                                     "kernel_ms": statistics.mean(m_kern), "kernel": "k_field_bwd_split_f32"}
+                                     "kernel_ms": statistics.mean(m_kern), "kernel": "k_field_bwd_split_tc",
+                                     "mlp_tflops_algorithmic": r_samples * SPLIT_BWD_FLOP
+                                     / (statistics.mean(m_kern) / 1000.0) / 1e12}
     del mtr, fsplit16
     strainer = api.Trainer(fsplit, samp, lr=1e-2, eps=1e-15, lambda_dist=0.01)
     sstep = lambda: strainer.step(o_dev, d_dev, tgt)

@@ -113,9 +113,9 @@ typedef struct nerfxl_field {
    * phase; order Y_0^0, Y_1^-1, Y_1^0, Y_1^1, Y_2^-2, ..., Y_3^3). mlp then
    * holds K * (mlp_in W + 16 W) + (32 W + W W + 4 W) values
    * (nerfxl_field_mlp_params). Built: FP32 tables and MLP (forward, backward,
-   * training step, grid refresh); FP32/FP16 tables with a BF16/FP16 MLP: the
-   * forward on the tensor cores, the backward on CUDA cores in FP32 from the
-   * 16-bit parameters (no NERFXL_SAVE_FEATURES records). E4M3: E_UNSUPPORTED.
+   * training step, grid refresh); FP32/FP16 tables with a BF16/FP16 MLP:
+   * forward and backward on the tensor cores (the backward recomputes the
+   * field; no NERFXL_SAVE_FEATURES records). E4M3: E_UNSUPPORTED.
    */
   int32_t arch;
 } nerfxl_field;

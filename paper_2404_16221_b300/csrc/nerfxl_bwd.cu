@@ -875,6 +875,8 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.dpart = dpart;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
+  if (f->arch == NERFXL_ARCH_SPLIT && f->mlp_dtype != NERFXL_F32)
+    return launch_field_bwd_split_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart, grad_tables, grad_mlp, stream);
   if (f->arch == NERFXL_ARCH_SPLIT) {
     const size_t smem_s = sizeof(float) * kBwdSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
     if (smem_s > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");

@@ -1,0 +1,586 @@
+// Backward of the split representation on the tensor cores (16-bit MLPs,
+// FP32 accumulation in tensor memory). One CTA of 16 warps per SM takes
+// 128-row tiles (4 chunks of one region); warp w serves rows 32 (w % 4) + lane
+// (its TMEM lane quarter) and column / level group w / 4. Per tile:
+//   gather    as the forward: four threads per row, four levels each -> X
+//   density   D = X Wd1 -> H1 = relu; G = H1 Wd2 (N = 16)
+//   colour    Xc = [G | SH(d)]; D = Xc Wc1 -> Hc1; D = Hc1 Wc2 -> Hc2; o = Hc2 Wc3
+//   adjoint   sigma = exp(G0), rgb = sigmoid(o); chunk-local render adjoint
+//             (one warp per chunk) -> dL/d(colour logits) goC, dL/dG0
+//   colour    Gz2 = (Hc2 > 0) (goC Wc3^T); Gz1 = (Hc1 > 0) (Gz2 Wc2^T);
+//             dG = (Gz1 Wc1^T)[0..15] + dL/dG0 e0
+//   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T -> table scatter-add
+//   weights   DW3 += [Hc2 | Hc1]^T goC, DWc += [Gz2 | Gz1]^T [Hc1 | Xc],
+//             DWd += [Gz0 | dG]^T [X | H1], MN-major reads of the row-major
+//             activation tiles (the samples are the contraction); DW3 and
+//             DWc run behind the next chain step, DWd under the tile's last
+//             commit; accumulated in TMEM over a region's tiles and flushed
+//             at region changes (density block of the region, shared colour
+//             block) by atomics.
+// The transposed weights of the dX products are MN-major reads of the
+// forward's weight tiles (K = the layer's output index), except the two with
+// 32 outputs (Wc1^T and Wd1^T), staged K-major. Gradients enter the products
+// as single 16-bit values.
+// Every wait is bounded: on expiry the kernel flags kErrTimeout, frees its
+// tensor memory and returns.
+
+#include <cuda_runtime.h>
+
+#include "nerfxl_half.cuh"
+#include "nerfxl_host.h"
+#include "nerfxl_split.cuh"
+#include "nerfxl_tc.cuh"
+
+namespace nerfxl {
+namespace {
+
+constexpr int kRowsS = 128;
+constexpr int kThreadsS = 512;
+constexpr int kChunksS = kRowsS / kWarp;
+constexpr uint32_t kColsS = 512;  // 0 D_A, 64 D_B, 128 D_S (N <= 32), 192 DWc, 288 DWd, 384 DW3
+constexpr uint32_t kDA = 0, kDB = 64, kDS = 128, kDWc = 192, kDWd = 288, kDW3 = 384;
+constexpr uint32_t kSpinS = 1u << 24;
+constexpr uint32_t kTile = 128 * 128;  // one 128-row, 128-byte-swizzled tile
+
+// Shared-memory plan (offsets from a 1024-byte-aligned base).
+constexpr uint32_t oX = 0;                 // SW64 [128][32]: features
+constexpr uint32_t oXc = oX + 8192;        // SW64 [128][32]: [G | SH]
+constexpr uint32_t oH1 = oXc + 8192;       // SW128 [128][64]
+constexpr uint32_t oHc2 = oH1 + kTile;     // SW128, then Hc1 right after (DW3's A = [Hc2 | Hc1])
+constexpr uint32_t oHc1 = oHc2 + kTile;
+constexpr uint32_t oGoC = oHc1 + kTile;    // SW128, 16 columns used
+constexpr uint32_t oGz2 = oGoC + kTile;    // [Gz2 | Gz1]: DWc's A
+constexpr uint32_t oGz1 = oGz2 + kTile;
+constexpr uint32_t oGz0 = oGz1 + kTile;    // [Gz0 | dG]: DWd's A
+constexpr uint32_t oGG = oGz0 + kTile;     // 16 columns used
+constexpr uint32_t oWd1 = oGG + kTile;     // B: 64 rows (out) x 32 (in), SW128
+constexpr uint32_t oWd2 = oWd1 + 64 * 128;  // B: 16 rows x 64
+constexpr uint32_t oWc1 = oWd2 + 16 * 128;  // B: 64 rows x 32
+constexpr uint32_t oWc2 = oWc1 + 64 * 128;  // B: 64 rows x 64
+constexpr uint32_t oWc3 = oWc2 + 64 * 128;  // B: 16 rows x 64 (rows >= 4 zero)
+constexpr uint32_t oWd1t = oWc3 + 16 * 128;  // B of dX: 32 rows (in) x 64 (out), K-major
+constexpr uint32_t oWc1t = oWd1t + 32 * 128;  // B of dXc: 32 rows (in) x 64 (out)
+constexpr uint32_t oMiscS = oWc1t + 32 * 128;  // mbarrier (8 B), tmem slot (4 B)
+constexpr uint32_t oBaseS = oMiscS + 64;
+constexpr size_t kSmemS = oBaseS + 1024;
+
+struct BwdSplitTcParams {
+  const float* rays_o;
+  const float* rays_d;
+  const float* boxes;
+  const void* tables;  // [K][E] half2 or float2
+  const void* mlp;     // 16-bit: K density blocks, then the colour block
+  LevelParams lp;
+  SampParams sp;
+  int K;
+  const RayHdr* hdr;
+  const SegDesc* segs;
+  const int32_t* base;
+  const uint2* chunks;
+  const int32_t* n_tiles;
+  const float4* dpart;  // chunk-partial adjoints [R][max_chunk][2]
+  float* grad_tables;
+  float* grad_mlp;
+  int32_t* err;
+};
+
+// 16-byte chunk c of row r of a 64-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw64_chunk(uint32_t row, uint32_t c) {
+  return row * 64u + ((c ^ ((row >> 1) & 3u)) << 4);
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void st_chunk8(uint32_t addr, const float* f) {
+  tc::st_shared_v4(addr, Half2Of<kBF16>::pack(f[0], f[1]), Half2Of<kBF16>::pack(f[2], f[3]),
+                   Half2Of<kBF16>::pack(f[4], f[5]), Half2Of<kBF16>::pack(f[6], f[7]));
+}
+
+// Sixteen values -> columns 16 c .. 16 c + 15 of a 128-byte-swizzled row.
+template <bool kBF16>
+__device__ __forceinline__ void st_row16(uint32_t tile, uint32_t row, int c, const float* v) {
+  st_chunk8<kBF16>(tile + tc::sw128_chunk(row, 2 * c), v);
+  st_chunk8<kBF16>(tile + tc::sw128_chunk(row, 2 * c + 1), v + 8);
+}
+
+// B tiles of the forward products (row = output n, column = input k) and the
+// K-major transposed tiles of the two dX products with 32 outputs.
+template <bool kBF16>
+__device__ void load_density_bwd(const void* blk, char* sm) {
+  uint16_t* wd1 = reinterpret_cast<uint16_t*>(sm + oWd1);
+  uint16_t* wd2 = reinterpret_cast<uint16_t*>(sm + oWd2);
+  uint16_t* wd1t = reinterpret_cast<uint16_t*>(sm + oWd1t);
+  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;  // Wd1[k][n]
+    const uint16_t b = Half2Of<kBF16>::bits(blk, i);
+    wd1[tc::sw128_offset(n, k) >> 1] = b;
+    wd1t[tc::sw128_offset(k, n) >> 1] = b;
+  }
+  for (int i = threadIdx.x; i < kGeo * kWidth; i += blockDim.x) {
+    const int n = i / kWidth, k = i % kWidth;  // B row n = output n of Wd2 [64][16]
+    wd2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kIn * kWidth + k * kGeo + n);
+  }
+}
+
+template <bool kBF16>
+__device__ void load_color_bwd(const void* blk, char* sm) {
+  uint16_t* wc1 = reinterpret_cast<uint16_t*>(sm + oWc1);
+  uint16_t* wc2 = reinterpret_cast<uint16_t*>(sm + oWc2);
+  uint16_t* wc3 = reinterpret_cast<uint16_t*>(sm + oWc3);
+  uint16_t* wc1t = reinterpret_cast<uint16_t*>(sm + oWc1t);
+  for (int i = threadIdx.x; i < kColorIn * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;  // Wc1[k][n]
+    const uint16_t b = Half2Of<kBF16>::bits(blk, i);
+    wc1[tc::sw128_offset(n, k) >> 1] = b;
+    wc1t[tc::sw128_offset(k, n) >> 1] = b;
+  }
+  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+    const int k = i / kWidth, n = i % kWidth;
+    wc2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kColorIn * kWidth + i);
+  }
+  for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
+    const int n = i / kWidth, k = i % kWidth;
+    wc3[tc::sw128_offset(n, k) >> 1] =
+        n < 3 ? Half2Of<kBF16>::bits(blk, kColorIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
+  }
+}
+
+// Table gradient of levels l0..l0+3 of one sample (F = 2): entry += corner weight * g.
+__device__ __forceinline__ void scatter4(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l0,
+                                         const float g8[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int l = l0 + q;
+    if (l >= lp.L) break;
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+    float2* gl = gtab + lp.off[l];
+    const float g0 = g8[2 * q], g1 = g8[2 * q + 1];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+      const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+      const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+      if ((i0 ^ i1) == 1u) {
+        const bool odd = i0 & 1u;
+        const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
+                             : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
+        atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
+      } else {
+        atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
+        atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
+      }
+    }
+  }
+}
+
+template <bool kF16Table, bool kBF16>
+__global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcParams p) {
+  extern __shared__ __align__(1024) char s_raw[];
+  char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sb = tc::smem_u32(sm);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMiscS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMiscS + 8);
+  int32_t* s_base = reinterpret_cast<int32_t*>(sm + oBaseS);
+  const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+  const int q = warp & 3, g = warp >> 2;
+  const uint32_t row = (uint32_t)(q * kWarp + lane);
+  using TabT = typename TableOf<kF16Table>::T;
+
+  for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  // zero the activation and gradient tiles once (unused columns of the
+  // 16-column tiles feed rows of the weight gradients that are never read)
+  for (uint32_t i = tid; i < oWd1 / 16; i += blockDim.x) tc::st_shared_v4(sb + 16 * i, 0u, 0u, 0u, 0u);
+  load_color_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kColsS);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+
+  constexpr uint32_t id64 = tc::idesc_f16(kBF16, kRowsS, 64);
+  constexpr uint32_t id32 = tc::idesc_f16(kBF16, kRowsS, 32);
+  constexpr uint32_t id16 = tc::idesc_f16(kBF16, kRowsS, 16);
+  constexpr uint32_t id64_bt = id64 | tc::kMnMajorB;
+  constexpr uint32_t id64_abt = id64 | tc::kMnMajorA | tc::kMnMajorB;
+  constexpr uint32_t id32_abt = id32 | tc::kMnMajorA | tc::kMnMajorB;
+  constexpr uint32_t id16_abt = id16 | tc::kMnMajorA | tc::kMnMajorB;
+
+  const int n_sub = *p.n_tiles * (kChunksPerTile / kChunksS);
+  int region = -1;
+  const TabT* table = nullptr;
+  float2* gtab = nullptr;
+  uint32_t phase = 0;
+  bool failed = false, dw_started = false;
+
+  // publish shared-memory writes, issue one chain step (plus optional
+  // weight-gradient MMAs behind it), wait for the step's commit
+  auto step = [&](auto&& issue) -> bool {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue();
+    }
+    const bool done = tc::mbar_wait_bounded(mbar, phase, kSpinS);
+    phase ^= 1;
+    if (__syncthreads_or(!done)) return false;
+    tc::fence_after_sync();
+    return true;
+  };
+
+  // weight-gradient accumulators -> global (all MMAs complete)
+  auto flush = [&]() {
+    if (!dw_started) return;
+    tc::fence_after_sync();
+    float* gd = p.grad_mlp + (size_t)region * kDensityParams;
+    float* gc = p.grad_mlp + (size_t)p.K * kDensityParams;
+    const int r = (int)row;
+    float v[16];
+    for (int h = g; h < 6; h += 4) {  // DWc: 96 columns
+      tc::tmem_ld16(tq + kDWc + 16 * h, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = 16 * h + i;
+        if (r < 64 && c < 64) atomicAdd(gc + kColorIn * kWidth + c * kWidth + r, v[i]);          // dWc2[c][r]
+        else if (r >= 64 && c >= 64) atomicAdd(gc + (c - 64) * kWidth + (r - 64), v[i]);        // dWc1[c-64][r-64]
+      }
+    }
+    for (int h = g; h < 6; h += 4) {  // DWd: 96 columns
+      tc::tmem_ld16(tq + kDWd + 16 * h, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = 16 * h + i;
+        if (r < 64 && c < 32) atomicAdd(gd + c * kWidth + r, v[i]);                                // dWd1[c][r]
+        else if (r >= 64 && r < 64 + kGeo && c >= 32) atomicAdd(gd + kIn * kWidth + (c - 32) * kGeo + (r - 64), v[i]);
+      }
+    }
+    if (g == 0) {  // DW3: rows 0..63 = Hc2 index, columns 0..2
+      tc::tmem_ld8(tq + kDW3, v);
+      tc::tmem_ld_wait();
+      if (r < 64)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) atomicAdd(gc + kColorIn * kWidth + kWidth * kWidth + r * kOut + m, v[m]);
+    }
+    dw_started = false;
+  };
+
+  for (int t = blockIdx.x; t < n_sub; t += gridDim.x) {
+    const int k = region_of_chunk(s_base, p.K, t * kChunksS);
+    if (k != region) {
+      flush();
+      __syncthreads();
+      load_density_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)k * kDensityParams * 2, sm);
+      region = k;
+      table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
+      gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+    }
+    // ---- gather (four threads per row, four levels each) and the chunk's adjoints
+    const uint2 ref = p.chunks[t * kChunksS + q];
+    const bool chunk_ok = ref.x != kEmptyChunk;
+    bool valid = false;
+    float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
+    float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
+    float f8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
+    if (chunk_ok) {
+      const uint32_t ray = ref.x;
+      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+      const RayHdr h = p.hdr[ray];
+      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      if (g == 0) {
+        const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+        const float4 a0 = p.dpart[2 * slot], a1 = p.dpart[2 * slot + 1];
+        gtc = a0.x;
+        gC[0] = a0.y;
+        gC[1] = a0.z;
+        gC[2] = a0.w;
+        gA = a1.x;
+        gD = a1.y;
+        gL = a1.z;
+      }
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+      const int i = c * kWarp + lane;
+      valid = i < ss.n;
+      if (valid) {
+        float o[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          o[ax] = p.rays_o[3 * (size_t)ray + ax];
+          dir[ax] = p.rays_d[3 * (size_t)ray + ax];
+        }
+        float a, b;
+        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
+        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        dl = __fsub_rn(b, a);
+        tr = __fsub_rn(tbar, h.tn);
+        float x[3];
+        sample_point(o, dir, tbar, x);
+        region_coord(p.boxes + 6 * k, x, u);
+        gather4<TabT>(p.lp, table, u, 4 * g, f8);
+      }
+    }
+    st_chunk8<kBF16>(sb + oX + sw64_chunk(row, g), f8);
+    float v[16];
+    uint32_t mH1 = 0, mHc1 = 0, mHc2 = 0;  // ReLU masks of this thread's 16 columns
+    // ---- density: D_A = X Wd1 -> H1
+    if (!step([&] {
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tmem + kDA, tc::desc_sw64(sb + oX + 32 * kk, 16), tc::desc_sw128(sb + oWd1 + 32 * kk), id64,
+                        kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDA + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (v[i] > 0.0f) mH1 |= 1u << i;
+      else v[i] = 0.0f;
+    }
+    st_row16<kBF16>(sb + oH1, row, g, v);
+    // ---- G = H1 Wd2 (16 outputs) -> Xc = [G | SH(d)]
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oH1 + 32 * kk), tc::desc_sw128(sb + oWd2 + 32 * kk), id16,
+                        kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    float g0 = 0.0f;
+    if (g == 0) {
+      tc::tmem_ld16(tq + kDS, v);
+      tc::tmem_ld_wait();
+      g0 = v[0];
+      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 0), v);
+      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 1), v + 8);
+    } else if (g == 1) {
+      float sh[kSh];
+      sh4_f32(dir, sh);
+      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 2), sh);
+      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 3), sh + 8);
+    }
+    // ---- colour: D_A = Xc Wc1 -> Hc1
+    if (!step([&] {
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tmem + kDA, tc::desc_sw64(sb + oXc + 32 * kk, 16), tc::desc_sw128(sb + oWc1 + 32 * kk), id64,
+                        kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDA + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (v[i] > 0.0f) mHc1 |= 1u << i;
+      else v[i] = 0.0f;
+    }
+    st_row16<kBF16>(sb + oHc1, row, g, v);
+    // ---- D_B = Hc1 Wc2 -> Hc2
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oHc1 + 32 * kk), tc::desc_sw128(sb + oWc2 + 32 * kk), id64,
+                        kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDB + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (v[i] > 0.0f) mHc2 |= 1u << i;
+      else v[i] = 0.0f;
+    }
+    st_row16<kBF16>(sb + oHc2, row, g, v);
+    // ---- o = Hc2 Wc3 (3 of 16 outputs)
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oHc2 + 32 * kk), tc::desc_sw128(sb + oWc3 + 32 * kk), id16,
+                        kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    // ---- chunk-local render adjoint (warp g == 0 of each lane quarter = one chunk)
+    float go_d = 0.0f;
+    if (g == 0) {
+      tc::tmem_ld16(tq + kDS, v);
+      tc::tmem_ld_wait();
+      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (valid) {
+        sigma = expf(g0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-v[m]));
+      }
+      float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+      float go[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) go[m] = 0.0f;
+      if (valid) {
+        go_d = g_sigma * sigma;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
+      }
+      st_row16<kBF16>(sb + oGoC, row, 0, go);
+    }
+    const bool acc = dw_started;
+    // ---- Gz2 = (Hc2 > 0) goC Wc3^T (Wc3 tile read MN-major, K = 16); DW3 += [Hc2 | Hc1]^T goC behind it
+    if (!step([&] {
+          tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGoC), tc::desc_sw128_mn(sb + oWc3, 1024), id64_bt, 0);
+          tc::mma_commit(mbar);
+          for (int kk = 0; kk < 8; ++kk)
+            tc::mma_f16(tmem + kDW3, tc::desc_sw128_mn(sb + oHc2 + 2048 * kk, kTile),
+                        tc::desc_sw128_mn(sb + oGoC + 2048 * kk, 1024), id16_abt, (acc || kk > 0) ? 1u : 0u);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDA + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (!((mHc2 >> i) & 1u)) v[i] = 0.0f;
+    st_row16<kBF16>(sb + oGz2, row, g, v);
+    // ---- Gz1 = (Hc1 > 0) Gz2 Wc2^T (Wc2 tile read MN-major, K = 64)
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz2 + 32 * kk), tc::desc_sw128_mn(sb + oWc2 + 2048 * kk, 1024),
+                        id64_bt, kk);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDB + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (!((mHc1 >> i) & 1u)) v[i] = 0.0f;
+    st_row16<kBF16>(sb + oGz1, row, g, v);
+    // ---- dXc = Gz1 Wc1^T (32 outputs; G's are the first 16); DWc += [Gz2 | Gz1]^T [Hc1 | Xc] behind it
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oGz1 + 32 * kk), tc::desc_sw128(sb + oWc1t + 32 * kk), id32,
+                        kk);
+          tc::mma_commit(mbar);
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t a = tc::desc_sw128_mn(sb + oGz2 + 2048 * kk, kTile);
+            const uint32_t on = (acc || kk > 0) ? 1u : 0u;
+            tc::mma_f16(tmem + kDWc, a, tc::desc_sw128_mn(sb + oHc1 + 2048 * kk, 1024), id64_abt, on);
+            tc::mma_f16(tmem + kDWc + 64, a, tc::desc_sw64(sb + oXc + 1024 * kk, 512), id32_abt, on);
+          }
+        })) {
+      failed = true;
+      break;
+    }
+    if (g == 0) {
+      tc::tmem_ld16(tq + kDS, v);
+      tc::tmem_ld_wait();
+      v[0] += go_d;  // G0 is also the log density
+      st_row16<kBF16>(sb + oGG, row, 0, v);
+    }
+    // ---- Gz0 = (H1 > 0) dG Wd2^T (Wd2 tile read MN-major, K = 16)
+    if (!step([&] {
+          tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGG), tc::desc_sw128_mn(sb + oWd2, 1024), id64_bt, 0);
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    tc::tmem_ld16(tq + kDA + 16 * g, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (!((mH1 >> i) & 1u)) v[i] = 0.0f;
+    st_row16<kBF16>(sb + oGz0, row, g, v);
+    // ---- dX = Gz0 Wd1^T (32 outputs) and DWd += [Gz0 | dG]^T [X | H1], under one commit: the next
+    //      tile's gather overwrites X before its first commit
+    if (!step([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz0 + 32 * kk), tc::desc_sw128(sb + oWd1t + 32 * kk), id32,
+                        kk);
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t a = tc::desc_sw128_mn(sb + oGz0 + 2048 * kk, kTile);
+            const uint32_t on = (acc || kk > 0) ? 1u : 0u;
+            tc::mma_f16(tmem + kDWd, a, tc::desc_sw64(sb + oX + 1024 * kk, 512), id32_abt, on);
+            tc::mma_f16(tmem + kDWd + 32, a, tc::desc_sw128_mn(sb + oH1 + 2048 * kk, 1024), id64_abt, on);
+          }
+          tc::mma_commit(mbar);
+        })) {
+      failed = true;
+      break;
+    }
+    dw_started = true;
+    // ---- table scatter: thread (row, g) takes levels 4g..4g+3 (columns 8g..8g+7 of dX)
+    tc::tmem_ld8(tq + kDB + 8 * g, v);
+    tc::tmem_ld_wait();
+    if (valid) scatter4(p.lp, gtab, u, 4 * g, v);
+    tc::fence_before_sync();
+    __syncthreads();  // tiles and TMEM free for the next tile
+  }
+  if (!failed) flush();  // every tile ends with all of its MMAs complete
+  if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kColsS);
+}
+
+}  // namespace
+
+// Host dispatch (called from nerfxl_render_bwd for the split representation's 16-bit forms).
+nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
+                                        const float* rays_o, const float* rays_d, char* ws, const Layout& L,
+                                        const float4* dpart, float* grad_tables, float* grad_mlp,
+                                        cudaStream_t stream) {
+  BwdSplitTcParams p;
+  p.rays_o = rays_o;
+  p.rays_d = rays_d;
+  p.boxes = f->boxes;
+  p.tables = f->tables;
+  p.mlp = f->mlp;
+  p.lp = lp;
+  p.sp = sp;
+  p.K = f->K;
+  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
+  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
+  p.base = reinterpret_cast<const int32_t*>(ws + L.base);
+  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
+  p.dpart = dpart;
+  p.grad_tables = grad_tables;
+  p.grad_mlp = grad_mlp;
+  p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
+  const size_t smem = kSmemS + sizeof(int32_t) * (f->K + 1);
+  if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
+  const bool f16tab = f->table_dtype == NERFXL_F16, bf16 = f->mlp_dtype == NERFXL_BF16;
+  void (*kern)(BwdSplitTcParams) = f16tab ? (bf16 ? k_field_bwd_split_tc<true, true> : k_field_bwd_split_tc<true, false>)
+                                          : (bf16 ? k_field_bwd_split_tc<false, true> : k_field_bwd_split_tc<false, false>);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return launch_check("k_field_bwd_split_tc smem attribute");
+  const int grid = fwd_grid(L.chunk_cap / kChunksS, 1);
+  profile_mark(0, stream);
+  kern<<<grid, kThreadsS, smem, stream>>>(p);
+  profile_mark(1, stream);
+  return launch_check("k_field_bwd_split_tc");
+}
+
+}  // namespace nerfxl

@@ -87,6 +87,12 @@ RecordOut record_out(char* ws, const Layout& L);
 // Tensor-core field backward (16-bit MLP), from the per-tile records.
 nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,
                                   float* grad_tables, float* grad_mlp, cudaStream_t stream);
+// Tensor-core backward of the split representation (BF16/FP16 MLPs; FP32 or
+// FP16 tables), recomputing the field from the tables; dpart = chunk adjoints.
+nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
+                                        const float* rays_o, const float* rays_d, char* ws, const Layout& L,
+                                        const float4* dpart, float* grad_tables, float* grad_mlp,
+                                        cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,

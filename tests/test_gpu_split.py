@@ -190,11 +190,11 @@ def test_split_tensor_core_forward_matches_oracle(tab, mlp, name, n):
 
 
 def test_split_mixed_backward_matches_oracle():
-    """FP16 tables + BF16 MLPs: the forward on the tensor cores, the backward
-    on CUDA cores in FP32 from the same 16-bit parameters. Against the oracle
-    on the rounded parameters, on the kink-free network (positive features
-    and hidden weights): no entry off by more than 1e-2 of max|ref| (the
-    composite adjoint starts from the forward's 16-bit-activation partials)."""
+    """FP16 tables + BF16 MLPs: forward and backward on the tensor cores.
+    Against the oracle on the rounded parameters, on the kink-free network
+    (positive features and hidden weights): no entry off by more than 1e-2
+    of max|ref| (activations and gradients enter the products as 16-bit
+    values; measured 1.1e-3 for the tables, 2.2e-4 for the MLPs)."""
     from paper_2404_16221_b300 import api, native as N
 
     w = H.workload("grid8", L=16, log2_T=14)

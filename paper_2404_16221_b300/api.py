@@ -310,6 +310,13 @@ class Trainer:
         self._ws = None
         self.loss = torch.zeros(3, dtype=torch.float32, device=field.device)
 
+    def master_field(self) -> PartitionedField:
+        """The FP32 masters as a field (shares their memory; no copy), e.g. for
+        refreshing an occupancy grid while training with 16-bit copies."""
+        f = self.field
+        return PartitionedField(f.boxes, f.level_res, f.log2_T, self.tables, self.mlp, F=f.F, mlp_in=f.mlp_in,
+                                width=f.width, device=f.device, arch=f.arch)
+
     def state_desc(self) -> N.TrainStateDesc:
         return N.TrainStateDesc(self.tables.data_ptr(), self.mlp.data_ptr(), self.grad_tables.data_ptr(),
                                 self.grad_mlp.data_ptr(), self.m_tables.data_ptr(), self.v_tables.data_ptr(),

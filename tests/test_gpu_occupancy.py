@@ -358,3 +358,23 @@ def test_full_size_forward_with_grid_sampled_rays():
             assert np.abs(got["opacity"] - ref["opacity"]).max() <= 2e-3
         del gf, ws, out
         torch.cuda.empty_cache()
+
+
+def test_refresh_from_mixed_trainer_masters():
+    """Training with FP16 tables and a BF16 MLP keeps FP32 masters; the grid
+    refresh reads them through Trainer.master_field() (no copy) and matches
+    the oracle on the same FP32 values."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+    tr = api.Trainer(gf, H.sampling(w), master_tables=torch.from_numpy(t), master_mlp=torch.from_numpy(m))
+    mf = tr.master_field()
+    assert mf.tables.data_ptr() == tr.tables.data_ptr() and mf.mlp.data_ptr() == tr.mlp.data_ptr()
+    G = 8
+    grid = api.OccupancyGrid(w.K, G, decay=0.9, threshold=1.0, seed=9)
+    grid.update(mf)
+    dens = np.zeros((w.K, G ** 3))
+    oracle.occupancy_update(H.oracle_field(w, t, m), G, 0, 9, 0.9, 1.0, dens)
+    assert (np.abs(grid.density.cpu().numpy() - dens) / dens).max() <= 1e-5

@@ -432,3 +432,44 @@ def test_split_mixed_training_gains():
     print("split mixed training PSNR: held-out initial %.2f, trained %.2f; training views %.2f" % (init, trained, fit))
     assert trained > init + 4.0
     assert fit > 30.0
+
+
+def test_split_mixed_backward_with_occupancy_matches_oracle():
+    """The split representation's tensor-core backward over the kept samples
+    of a sparse occupancy grid, on the kink-free network: no entry off by
+    more than 1e-2 of max|ref| against the oracle with the same grid."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload("grid8", L=16, log2_T=14)
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    Pd, Pc = oracle.density_params(w.mlp_in, w.W), oracle.color_params(w.W)
+    g = sy.rng(26, "misc")
+    t = g.uniform(0.1, 1.0, (w.K, E, 2)).astype(np.float32)
+    dens = np.concatenate([g.uniform(0.0, 0.05, (w.K, 32 * 64)), g.normal(0.0, 0.1, (w.K, 64 * 16))], 1)
+    col = np.concatenate([g.uniform(0.0, 0.05, 32 * 64), g.uniform(0.0, 0.05, 64 * 64), g.normal(0.0, 0.1, 64 * 4)])
+    m = np.concatenate([dens.reshape(-1), col]).astype(np.float32)
+    G = 16
+    bits = (g.integers(0, 2 ** 32, (w.K, oracle.occupancy_words(G)), dtype=np.uint64)
+            & g.integers(0, 2 ** 32, (w.K, oracle.occupancy_words(G)), dtype=np.uint64)).astype(np.uint32)  # ~25%
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 2048, 74)
+    o, d = o[sel].copy(), d[sel].copy()
+    R = len(o)
+    gg = sy.rng(75, "misc")
+    gC, gD, gA, gL = gg.standard_normal((R, 3)), gg.standard_normal(R), gg.standard_normal(R), gg.standard_normal(R)
+    gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                              torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+    gf.set_occupancy(bits, G)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(gC), dev(gD), dev(gA), dev(gL))
+    api.check(ws)
+    ofq = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, _rounded(t, torch.float16),
+                       _rounded(m, torch.bfloat16), arch=1).with_occupancy(bits, G)
+    gt_ref, gm_ref = oracle.render_grad(ofq, w.S, o, d, gC, gD, gA, gL)
+    for name, a, b in (("tables", gt.cpu().numpy(), gt_ref), ("mlp", gm.cpu().numpy(), gm_ref)):
+        err = np.abs(a.astype(np.float64).reshape(-1) - b.reshape(-1)) / np.abs(b).max()
+        print("split mixed backward with a grid", name, "max err / max |grad| %.2e" % err.max())
+        assert err.max() <= 1e-2, (name, err.max())

@@ -68,3 +68,55 @@ def test_workspace_size_grows_with_rays(lib):
     c = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 2000, 1)
     assert 0 < a < b < c
     assert lib.nerfxl_max_chunks(ctypes.byref(s), 8) == 4 + 127 // 32
+
+
+def test_occupancy_and_split_arguments_on_the_host(lib):
+    """Host-side checks of the occupancy grid and the split representation:
+    grid resolution, representation code, dtype combinations, workspace
+    sizes and parameter counts (no kernel is launched)."""
+    s = N.SamplingDesc(128, 4, 0.0, 0)
+    d = _desc()
+    base = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0)
+    assert base > 0
+    # an occupancy grid adds the per-segment kept counts and the kept-interval lists
+    d.occupancy, d.occ_res = 1, 64
+    grown = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0)
+    assert grown >= base + 1000 * 4 * 4 + 1000 * 2 * (128 + 4 - 1)
+    for bad in (0, 1025):
+        d.occ_res = bad
+        assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0) == 0
+        st = lib.nerfxl_render_fwd(ctypes.byref(d), ctypes.byref(s), 16, 1, 1, 1, 1, 1, 1, 1, 1 << 30, None)
+        assert st == N.E_INVALID
+    # representations: fused and split counts, unknown code rejected
+    d = _desc()
+    assert lib.nerfxl_field_mlp_params(ctypes.byref(d)) == 8 * N.mlp_params(32, 64)
+    d.arch = N.ARCH_SPLIT
+    assert lib.nerfxl_field_mlp_params(ctypes.byref(d)) == \
+        8 * oracle.density_params(32, 64) + oracle.color_params(64)
+    d.mlp_dtype = N.E4M3
+    assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0) == 0
+    d.mlp_dtype = N.BF16
+    # the split form keeps no tensor-core backward records
+    assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 1) < \
+        lib.nerfxl_workspace_bytes(ctypes.byref(_fused_bf16()), ctypes.byref(s), 1000, 1)
+    d.arch = 7
+    assert lib.nerfxl_field_mlp_params(ctypes.byref(d)) == -1
+    assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0) == 0
+
+
+def _fused_bf16():
+    d = _desc()
+    d.mlp_dtype = N.BF16
+    return d
+
+
+def test_occupancy_refresh_arguments_on_the_host(lib):
+    d = _desc()
+    d.level_res[15] = 16 + 8 * 15
+    for G, decay, tdt, mdt in ((0, 0.9, N.F32, N.F32), (2048, 0.9, N.F32, N.F32), (8, 1.5, N.F32, N.F32),
+                               (8, 0.9, N.F16, N.BF16)):
+        d.table_dtype, d.mlp_dtype = tdt, mdt
+        st = lib.nerfxl_occupancy_update(ctypes.byref(d), G, 0, 1, decay, 0.01, 1, 1, None)
+        assert st in (N.E_INVALID, N.E_UNSUPPORTED), (G, decay, st)
+    d.table_dtype, d.mlp_dtype = N.F32, N.F32
+    assert lib.nerfxl_occupancy_update(ctypes.byref(d), 8, 0, 1, 0.9, 0.01, None, None, None) == N.E_INVALID

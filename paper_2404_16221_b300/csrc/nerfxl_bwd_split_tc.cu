@@ -22,7 +22,9 @@
 // 32 outputs (Wc1^T and Wd1^T), staged K-major. Gradients enter the products
 // as single 16-bit values.
 // Every wait is bounded: on expiry the kernel flags kErrTimeout, frees its
-// tensor memory and returns.
+// tensor memory and returns. One block barrier per MMA step: it publishes the
+// step's shared-memory operands and carries any timed-out wait of the step
+// before; each thread waits on the commit itself.
 
 #include <cuda_runtime.h>
 
@@ -220,17 +222,19 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
   // publish shared-memory writes, issue one chain step (plus optional
   // weight-gradient MMAs behind it), wait for the step's commit
+  // One barrier per step: the publishing barrier also agrees on any earlier
+  // timed-out wait; every thread then waits on the step's commit itself.
+  bool timed_out = false;
   auto step = [&](auto&& issue) -> bool {
     tc::fence_proxy_async();
     tc::fence_before_sync();
-    __syncthreads();
+    if (__syncthreads_or(timed_out)) return false;
     if (tid == 0) {
       tc::fence_after_sync();
       issue();
     }
-    const bool done = tc::mbar_wait_bounded(mbar, phase, kSpinS);
+    timed_out = !tc::mbar_wait_bounded(mbar, phase, kSpinS);
     phase ^= 1;
-    if (__syncthreads_or(!done)) return false;
     tc::fence_after_sync();
     return true;
   };
@@ -535,7 +539,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     tc::tmem_ld_wait();
     if (valid) scatter4(p.lp, gtab, u, 4 * g, v);
     tc::fence_before_sync();
-    __syncthreads();  // tiles and TMEM free for the next tile
+    if (__syncthreads_or(timed_out)) {  // tiles and TMEM free for the next tile
+      failed = true;
+      break;
+    }
   }
   if (!failed) flush();  // every tile ends with all of its MMAs complete
   if (failed && tid == 0) atomicOr(p.err, kErrTimeout);

@@ -9,7 +9,8 @@
 //             (one warp per chunk) -> dL/d(colour logits) goC, dL/dG0
 //   colour    Gz2 = (Hc2 > 0) (goC Wc3^T); Gz1 = (Hc1 > 0) (Gz2 Wc2^T);
 //             dG = (Gz1 Wc1^T)[0..15] + dL/dG0 e0
-//   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T -> table scatter-add
+//   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T -> table scatter-add,
+//             one level per MMA step of the next tile (under the MMA waits)
 //   weights   DW3 += [Hc2 | Hc1]^T goC, DWc += [Gz2 | Gz1]^T [Hc1 | Xc],
 //             DWd += [Gz0 | dG]^T [X | H1], MN-major reads of the row-major
 //             activation tiles (the samples are the contraction); DW3 and
@@ -146,35 +147,29 @@ __device__ void load_color_bwd(const void* blk, char* sm) {
   }
 }
 
-// Table gradient of levels l0..l0+3 of one sample (F = 2): entry += corner weight * g.
-__device__ __forceinline__ void scatter4(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l0,
-                                         const float g8[8]) {
+// Table gradient of level l of one sample (F = 2): entry += corner weight * (g0, g1).
+__device__ __forceinline__ void scatter_one(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l,
+                                            float g0, float g1) {
+  int c[3];
+  float f[3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int l = l0 + q;
-    if (l >= lp.L) break;
-    int c[3];
-    float f[3];
+  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  float2* gl = gtab + lp.off[l];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-    float2* gl = gtab + lp.off[l];
-    const float g0 = g8[2 * q], g1 = g8[2 * q + 1];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-      const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-      const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
-      if ((i0 ^ i1) == 1u) {
-        const bool odd = i0 & 1u;
-        const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
-                             : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
-        atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
-      } else {
-        atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
-        atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
-      }
+  for (int e = 0; e < 8; e += 2) {
+    const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+    const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+    const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+    const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+    const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+    if ((i0 ^ i1) == 1u) {
+      const bool odd = i0 & 1u;
+      const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
+                           : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
+      atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
+    } else {
+      atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
+      atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
     }
   }
 }
@@ -222,6 +217,22 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
   // publish shared-memory writes, issue one chain step (plus optional
   // weight-gradient MMAs behind it), wait for the step's commit
+  // The previous tile's table gradient (this thread's row, levels 4g..4g+3)
+  // is scattered one level per MMA step of the next tile, while the step's
+  // MMAs run: the atomics then share the load/store path with MMA waits
+  // instead of stalling the warps after the chain.
+  float cg[8], cu[3] = {0.0f, 0.0f, 0.0f};
+  bool cvalid = false;
+  float2* cgtab = nullptr;
+  int cpart = 4;  // levels of the carried sample still to scatter start at 4g + cpart
+  auto scatter_part = [&]() {
+    if (cpart < 4) {
+      const int l = 4 * g + cpart;
+      if (cvalid && l < p.lp.L) scatter_one(p.lp, cgtab, cu, l, cg[2 * cpart], cg[2 * cpart + 1]);
+      ++cpart;
+    }
+  };
+
   // One barrier per step: the publishing barrier also agrees on any earlier
   // timed-out wait; every thread then waits on the step's commit itself.
   bool timed_out = false;
@@ -233,6 +244,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       tc::fence_after_sync();
       issue();
     }
+    scatter_part();
     timed_out = !tc::mbar_wait_bounded(mbar, phase, kSpinS);
     phase ^= 1;
     tc::fence_after_sync();
@@ -537,14 +549,24 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     // ---- table scatter: thread (row, g) takes levels 4g..4g+3 (columns 8g..8g+7 of dX)
     tc::tmem_ld8(tq + kDB + 8 * g, v);
     tc::tmem_ld_wait();
-    if (valid) scatter4(p.lp, gtab, u, 4 * g, v);
+    while (cpart < 4) scatter_part();  // (the chain has nine steps: nothing is left here)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cg[i] = v[i];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) cu[ax] = u[ax];
+    cvalid = valid;
+    cgtab = gtab;
+    cpart = 0;
     tc::fence_before_sync();
     if (__syncthreads_or(timed_out)) {  // tiles and TMEM free for the next tile
       failed = true;
       break;
     }
   }
-  if (!failed) flush();  // every tile ends with all of its MMAs complete
+  if (!failed) {
+    while (cpart < 4) scatter_part();  // the last tile's table gradient
+    flush();                           // every tile ends with all of its MMAs complete
+  }
   if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
   tc::fence_before_sync();
   __syncthreads();

@@ -114,8 +114,9 @@ typedef struct nerfxl_field {
    * holds K * (mlp_in W + 16 W) + (32 W + W W + 4 W) values
    * (nerfxl_field_mlp_params). Built: FP32 tables and MLP (forward, backward,
    * training step, grid refresh); FP32/FP16 tables with a BF16/FP16 MLP:
-   * forward and backward on the tensor cores (the backward recomputes the
-   * field; no NERFXL_SAVE_FEATURES records). E4M3: E_UNSUPPORTED.
+   * forward and backward on the tensor cores (the backward reads the forward's
+   * NERFXL_SAVE_FEATURES records and recomputes both MLPs). E4M3:
+   * E_UNSUPPORTED.
    */
   int32_t arch;
 } nerfxl_field;

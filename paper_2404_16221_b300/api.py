@@ -288,8 +288,8 @@ class Trainer:
     def __init__(self, field: PartitionedField, samp: Sampling, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
                  lambda_dist=0.01, master_tables=None, master_mlp=None, save_features: bool = True):
         self.field = field
-        if save_features and field.mlp.dtype in (torch.bfloat16, torch.float16) and field.arch == N.ARCH_FUSED:
-            # fused 16-bit MLP: keep the forward's features for the tensor-core backward
+        if save_features and field.mlp.dtype in (torch.bfloat16, torch.float16):
+            # 16-bit MLP: keep the forward's records for the tensor-core backward
             samp = dataclasses.replace(samp, flags=samp.flags | SAVE_FEATURES)
         self.samp = samp
         self.lr, self.beta1, self.beta2, self.eps, self.lambda_dist = lr, beta1, beta2, eps, lambda_dist

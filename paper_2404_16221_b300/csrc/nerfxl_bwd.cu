@@ -460,9 +460,9 @@ __device__ __forceinline__ void load_split_any(const void* dens, const void* col
   }
 }
 
-// kF16Table / kMlpType: the parameters the forward read (FP16 tables, BF16 or
-// FP16 MLP copies); the recompute and every product run in FP32 and the
-// gradients are FP32, as for the FP32 parameters.
+// kF16Table / kMlpType: the parameters the forward read (FP16 tables; the
+// host launches the FP32 MLP form, 16-bit MLPs take the tensor-core backward);
+// the recompute and every product run in FP32 and the gradients are FP32.
 template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
@@ -839,9 +839,9 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   char* ws = static_cast<char*>(workspace);
   const SampParams sp = samp_params(f, s, ws, L);
   float4* dpart = reinterpret_cast<float4*>(ws + L.dpartials);
-  // the fused representation's 16-bit forms run the tensor-core backward from
-  // per-tile records; the split representation recomputes on CUDA cores
-  const bool tc = (f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16) && f->arch == NERFXL_ARCH_FUSED;
+  // the 16-bit forms of both representations run the tensor-core backward
+  // from per-tile records; FP32 MLPs recompute on CUDA cores
+  const bool tc = f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16;
   if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "the E4M3 MLP is forward-only");
   if (tc && !(s->flags & NERFXL_SAVE_FEATURES)) {
     // The forward did not keep the records: rebuild them (the forward's
@@ -855,6 +855,8 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
       tc ? reinterpret_cast<float4*>(ws + L.rec_dpart) : nullptr);
   st = launch_check("k_composite_bwd");
   if (st != NERFXL_OK) return st;
+  if (tc && f->arch == NERFXL_ARCH_SPLIT)
+    return launch_field_bwd_split_tc(f, level_params(f), ws, L, grad_tables, grad_mlp, stream);
   if (tc) return launch_field_bwd_tc(f, level_params(f), ws, L, grad_tables, grad_mlp, stream);
   BwdParams p;
   p.rays_o = rays_o;
@@ -875,18 +877,10 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.dpart = dpart;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
-  if (f->arch == NERFXL_ARCH_SPLIT && f->mlp_dtype != NERFXL_F32)
-    return launch_field_bwd_split_tc(f, sp, p.lp, rays_o, rays_d, ws, L, dpart, grad_tables, grad_mlp, stream);
   if (f->arch == NERFXL_ARCH_SPLIT) {
     const size_t smem_s = sizeof(float) * kBwdSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
     if (smem_s > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-    void (*ks)(BwdParams) = nullptr;
-    if (f->mlp_dtype == NERFXL_F32)
-      ks = f16tab ? k_field_bwd_split_f32<true, 0> : k_field_bwd_split_f32<false, 0>;
-    else if (f->mlp_dtype == NERFXL_BF16)
-      ks = f16tab ? k_field_bwd_split_f32<true, 1> : k_field_bwd_split_f32<false, 1>;
-    else
-      ks = f16tab ? k_field_bwd_split_f32<true, 2> : k_field_bwd_split_f32<false, 2>;
+    void (*ks)(BwdParams) = f16tab ? k_field_bwd_split_f32<true, 0> : k_field_bwd_split_f32<false, 0>;  // FP32 MLP
     if (cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
       return launch_check("k_field_bwd_split_f32 smem attribute");
     const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);

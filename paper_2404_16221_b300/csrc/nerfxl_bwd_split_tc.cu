@@ -2,7 +2,10 @@
 // FP32 accumulation in tensor memory). One CTA of 16 warps per SM takes
 // 128-row tiles (4 chunks of one region); warp w serves rows 32 (w % 4) + lane
 // (its TMEM lane quarter) and column / level group w / 4. Per tile:
-//   gather    as the forward: four threads per row, four levels each -> X
+//   records   written by the forward for this tile: X exactly as its first
+//             MMA read it; per row the region coordinates, interval and ray
+//             direction; per chunk the sample count and, from the composite
+//             adjoint, the chunk's partial adjoints in tile order
 //   density   D = X Wd1 -> H1 = relu; G = H1 Wd2 (N = 16)
 //   colour    Xc = [G | SH(d)]; D = Xc Wc1 -> Hc1; D = Hc1 Wc2 -> Hc2; o = Hc2 Wc3
 //   adjoint   sigma = exp(G0), rgb = sigmoid(o); chunk-local render adjoint
@@ -66,22 +69,17 @@ constexpr uint32_t oWc1t = oWd1t + 32 * 128;  // B of dXc: 32 rows (in) x 64 (ou
 constexpr uint32_t oMiscS = oWc1t + 32 * 128;  // mbarrier (8 B), tmem slot (4 B)
 constexpr uint32_t oBaseS = oMiscS + 64;
 constexpr size_t kSmemS = oBaseS + 1024;
+static_assert(kRowsS == kRecRows, "one backward tile is one record tile");
 
 struct BwdSplitTcParams {
-  const float* rays_o;
-  const float* rays_d;
-  const float* boxes;
-  const void* tables;  // [K][E] half2 or float2
-  const void* mlp;     // 16-bit: K density blocks, then the colour block
+  const void* mlp;  // 16-bit: K density blocks, then the colour block
   LevelParams lp;
-  SampParams sp;
   int K;
-  const RayHdr* hdr;
-  const SegDesc* segs;
   const int32_t* base;
-  const uint2* chunks;
   const int32_t* n_tiles;
-  const float4* dpart;  // chunk-partial adjoints [R][max_chunk][2]
+  const uint4* rec_feat;    // per tile: the 128 x 32 feature tile, 64-byte swizzled
+  const float* rec_geom;    // per tile: rows u0 u1 u2 tr dl d0 d1 d2 (of kGeomRowFields), chunk counts
+  const float4* rec_dpart;  // per tile: 4 chunks x 2 partial adjoints
   float* grad_tables;
   float* grad_mlp;
   int32_t* err;
@@ -174,7 +172,7 @@ __device__ __forceinline__ void scatter_one(const LevelParams& lp, float2* __res
   }
 }
 
-template <bool kF16Table, bool kBF16>
+template <bool kBF16>
 __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcParams p) {
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
@@ -185,7 +183,6 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
   const int q = warp & 3, g = warp >> 2;
   const uint32_t row = (uint32_t)(q * kWarp + lane);
-  using TabT = typename TableOf<kF16Table>::T;
 
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   // zero the activation and gradient tiles once (unused columns of the
@@ -210,7 +207,6 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
   const int n_sub = *p.n_tiles * (kChunksPerTile / kChunksS);
   int region = -1;
-  const TabT* table = nullptr;
   float2* gtab = nullptr;
   uint32_t phase = 0;
   bool failed = false, dw_started = false;
@@ -221,7 +217,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   // is scattered one level per MMA step of the next tile, while the step's
   // MMAs run: the atomics then share the load/store path with MMA waits
   // instead of stalling the warps after the chain.
-  float cg[8], cu[3] = {0.0f, 0.0f, 0.0f};
+  float cg[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, cu[3] = {0.0f, 0.0f, 0.0f};
   bool cvalid = false;
   float2* cgtab = nullptr;
   int cpart = 4;  // levels of the carried sample still to scatter start at 4g + cpart
@@ -296,26 +292,26 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       __syncthreads();
       load_density_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)k * kDensityParams * 2, sm);
       region = k;
-      table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
-    // ---- gather (four threads per row, four levels each) and the chunk's adjoints
-    const uint2 ref = p.chunks[t * kChunksS + q];
-    const bool chunk_ok = ref.x != kEmptyChunk;
-    bool valid = false;
-    float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
+    // ---- this tile's records: X (the record is the tile's shared-memory image),
+    //      the row's region coordinates (for the scatter), interval (render
+    //      adjoint, g == 0) and direction (SH, g == 1), the chunk's adjoints
+    const float* geo = p.rec_geom + (size_t)t * kGeomFloats;
+    const int n_valid = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
+    const bool chunk_ok = n_valid > 0, valid = (int)lane < n_valid;
+    const uint4 xr = __ldcs(p.rec_feat + (size_t)t * (kRecFeatBytes / 16) + row * 4u + ((uint32_t)g ^ ((row >> 1) & 3u)));
+    tc::st_shared_v4(sb + oX + sw64_chunk(row, g), xr.x, xr.y, xr.z, xr.w);
+    float tr = 0.0f, dl = 0.0f, u[3], dir[3] = {0.0f, 0.0f, 0.0f};
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
-    float f8[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) f8[i] = 0.0f;
-    if (chunk_ok) {
-      const uint32_t ray = ref.x;
-      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
-      const RayHdr h = p.hdr[ray];
-      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
-      if (g == 0) {
-        const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
-        const float4 a0 = p.dpart[2 * slot], a1 = p.dpart[2 * slot + 1];
+    for (int ax = 0; ax < 3; ++ax) u[ax] = __ldg(geo + ax * kRecRows + row);
+    if (g == 0) {
+      tr = __ldcs(geo + 3 * kRecRows + row);
+      dl = __ldcs(geo + 4 * kRecRows + row);
+      if (chunk_ok) {
+        const float4 a0 = __ldcs(p.rec_dpart + 2 * ((size_t)t * kChunksS + q));
+        const float4 a1 = __ldcs(p.rec_dpart + 2 * ((size_t)t * kChunksS + q) + 1);
         gtc = a0.x;
         gC[0] = a0.y;
         gC[1] = a0.z;
@@ -324,28 +320,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         gD = a1.y;
         gL = a1.z;
       }
-      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-      const int i = c * kWarp + lane;
-      valid = i < ss.n;
-      if (valid) {
-        float o[3];
+    } else if (g == 1) {
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          o[ax] = p.rays_o[3 * (size_t)ray + ax];
-          dir[ax] = p.rays_d[3 * (size_t)ray + ax];
-        }
-        float a, b;
-        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
-        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
-        dl = __fsub_rn(b, a);
-        tr = __fsub_rn(tbar, h.tn);
-        float x[3];
-        sample_point(o, dir, tbar, x);
-        region_coord(p.boxes + 6 * k, x, u);
-        gather4<TabT>(p.lp, table, u, 4 * g, f8);
-      }
+      for (int ax = 0; ax < 3; ++ax) dir[ax] = __ldcs(geo + (5 + ax) * kRecRows + row);
     }
-    st_chunk8<kBF16>(sb + oX + sw64_chunk(row, g), f8);
     float v[16];
     uint32_t mH1 = 0, mHc1 = 0, mHc2 = 0;  // ReLU masks of this thread's 16 columns
     // ---- density: D_A = X Wd1 -> H1
@@ -529,7 +507,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       if (!((mH1 >> i) & 1u)) v[i] = 0.0f;
     st_row16<kBF16>(sb + oGz0, row, g, v);
     // ---- dX = Gz0 Wd1^T (32 outputs) and DWd += [Gz0 | dG]^T [X | H1], under one commit: the next
-    //      tile's gather overwrites X before its first commit
+    //      tile's records overwrite X before its first commit
     if (!step([&] {
           for (int kk = 0; kk < 4; ++kk)
             tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz0 + 32 * kk), tc::desc_sw128(sb + oWd1t + 32 * kk), id32,
@@ -575,34 +553,27 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
 }  // namespace
 
-// Host dispatch (called from nerfxl_render_bwd for the split representation's 16-bit forms).
-nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                        const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                        const float4* dpart, float* grad_tables, float* grad_mlp,
-                                        cudaStream_t stream) {
+// Host dispatch (called from nerfxl_render_bwd for the split representation's
+// 16-bit forms, after the composite adjoint wrote the tile-order chunk adjoints).
+nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,
+                                        float* grad_tables, float* grad_mlp, cudaStream_t stream) {
+  if (L.rec_tiles == 0) return set_error(NERFXL_E_WORKSPACE, "workspace has no tensor-core backward records");
   BwdSplitTcParams p;
-  p.rays_o = rays_o;
-  p.rays_d = rays_d;
-  p.boxes = f->boxes;
-  p.tables = f->tables;
   p.mlp = f->mlp;
   p.lp = lp;
-  p.sp = sp;
   p.K = f->K;
-  p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
-  p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
-  p.dpart = dpart;
+  p.rec_feat = reinterpret_cast<const uint4*>(ws + L.rec_feat);
+  p.rec_geom = reinterpret_cast<const float*>(ws + L.rec_geom);
+  p.rec_dpart = reinterpret_cast<const float4*>(ws + L.rec_dpart);
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
   const size_t smem = kSmemS + sizeof(int32_t) * (f->K + 1);
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-  const bool f16tab = f->table_dtype == NERFXL_F16, bf16 = f->mlp_dtype == NERFXL_BF16;
-  void (*kern)(BwdSplitTcParams) = f16tab ? (bf16 ? k_field_bwd_split_tc<true, true> : k_field_bwd_split_tc<true, false>)
-                                          : (bf16 ? k_field_bwd_split_tc<false, true> : k_field_bwd_split_tc<false, false>);
+  void (*kern)(BwdSplitTcParams) =
+      f->mlp_dtype == NERFXL_BF16 ? k_field_bwd_split_tc<true> : k_field_bwd_split_tc<false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_bwd_split_tc smem attribute");
   const int grid = fwd_grid(L.chunk_cap / kChunksS, 1);

@@ -608,7 +608,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
   L.rec_feat = L.rec_geom = L.rec_dpart = L.rec_pos = 0;
   L.rec_tiles = 0;
-  if (for_backward && (f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16) && f->arch == NERFXL_ARCH_FUSED) {
+  if (for_backward && (f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16)) {
     L.rec_tiles = (L.chunk_cap + 3) / 4;
     L.rec_feat = take(kRecFeatBytes * L.rec_tiles);
     L.rec_geom = take(sizeof(float) * kGeomFloats * L.rec_tiles);
@@ -834,8 +834,6 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
     RecordOut rec = {nullptr, nullptr, nullptr};
     if (s->flags & NERFXL_SAVE_FEATURES) {
       if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
-      if (f->arch != NERFXL_ARCH_FUSED)
-        return set_error(NERFXL_E_UNSUPPORTED, "NERFXL_SAVE_FEATURES keeps the fused representation's records");
       const Layout LB = layout(f, s, n_rays, 1);
       if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
       rec = record_out(ws, LB);

@@ -220,7 +220,7 @@ struct FwdTcParams {
 
 template <bool kF16Table, int kKind, bool kRec, bool kSplit>
 __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
-  static_assert(!kSplit || (!kRec && kKind != kKindE4M3), "the split form is a 16-bit forward");
+  static_assert(!kSplit || kKind != kKindE4M3, "the split form is a 16-bit forward");
   using Op = MlpOp<kKind>;
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
@@ -329,6 +329,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
       __stcs(geo + g * kTcRows + row, g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr)));
+      if (kSplit && g == 1) {  // the split form's colour input: the ray direction, rows 5..7
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) __stcs(geo + (5 + ax) * kTcRows + row, dir[ax]);
+      }
       if (g == 0) {
         __stcs(geo + 4 * kTcRows + row, dl);
         if (lane == 0) {
@@ -543,13 +547,15 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   if (recs && kind == kKindE4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
   void (*kern)(FwdTcParams) = nullptr;
   if (f->arch == NERFXL_ARCH_SPLIT) {
-    if (recs || kind == kKindE4M3)
+    if (kind == kKindE4M3)
       return set_error(NERFXL_E_UNSUPPORTED, "the split representation's tensor-core form is a BF16/FP16 forward");
+    const bool bf = kind == kKindBF16;
     if (f16tab)
-      kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, false, true> : k_field_fwd_tc<true, kKindF16, false, true>;
+      kern = recs ? (bf ? k_field_fwd_tc<true, kKindBF16, true, true> : k_field_fwd_tc<true, kKindF16, true, true>)
+                  : (bf ? k_field_fwd_tc<true, kKindBF16, false, true> : k_field_fwd_tc<true, kKindF16, false, true>);
     else
-      kern = kind == kKindBF16 ? k_field_fwd_tc<false, kKindBF16, false, true>
-                               : k_field_fwd_tc<false, kKindF16, false, true>;
+      kern = recs ? (bf ? k_field_fwd_tc<false, kKindBF16, true, true> : k_field_fwd_tc<false, kKindF16, true, true>)
+                  : (bf ? k_field_fwd_tc<false, kKindBF16, false, true> : k_field_fwd_tc<false, kKindF16, false, true>);
   } else if (f16tab) {
     if (recs) kern = kind == kKindBF16 ? k_field_fwd_tc<true, kKindBF16, true, false> : k_field_fwd_tc<true, kKindF16, true, false>;
     else

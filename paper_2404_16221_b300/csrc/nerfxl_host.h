@@ -27,7 +27,8 @@ struct Layout {
   // Per-tile records of the tensor-core backward (backward workspaces with a
   // 16-bit MLP only; 0 otherwise). A tile is 4 chunks = 128 sample rows.
   size_t rec_feat;   // [tiles][128 rows][64 B]: 16-bit features, 64-byte-swizzled MMA tile
-  size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl Tn w pair sigma rgb; chunk counts
+  size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl, then Tn w pair sigma rgb
+                     // (fused) or the ray direction d0 d1 d2 (split); chunk counts
   size_t rec_dpart;  // float4[tiles * 4][2]: chunk adjoints in tile order
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
   // Sample-level composition (NERFXL_SAMPLE_COMPOSITE; 0 otherwise):
@@ -69,7 +70,10 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
 //             dl (interval length), Tn (transmittance after the sample within its
 //             chunk), w (chunk-local weight), pair (sum over the chunk of
 //             w_j |tr_i - tr_j|), sigma, r, g, b (the MLP outputs after exp /
-//             sigmoid); then the valid-sample count of each chunk (int32).
+//             sigmoid); then the valid-sample count of each chunk (int32). The
+//             split representation's backward recomputes its two MLPs and the
+//             render quantities; its rows 5..7 hold the ray direction instead
+//             (the colour MLP's SH input) and rows 8..11 are unused.
 constexpr int kRecRows = 128;
 constexpr int kGeomRowFields = 12;
 constexpr int kGeomFloats = kGeomRowFields * kRecRows + 4;  // 6160 bytes, a multiple of 16
@@ -89,10 +93,8 @@ nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, 
                                   float* grad_tables, float* grad_mlp, cudaStream_t stream);
 // Tensor-core backward of the split representation (BF16/FP16 MLPs; FP32 or
 // FP16 tables), recomputing the field from the tables; dpart = chunk adjoints.
-nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                        const float* rays_o, const float* rays_d, char* ws, const Layout& L,
-                                        const float4* dpart, float* grad_tables, float* grad_mlp,
-                                        cudaStream_t stream);
+nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,
+                                        float* grad_tables, float* grad_mlp, cudaStream_t stream);
 // Tensor-core field forward (BF16/FP16 MLP; FP32 or FP16 tables).
 nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L,

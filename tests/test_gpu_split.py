@@ -189,7 +189,8 @@ def test_split_tensor_core_forward_matches_oracle(tab, mlp, name, n):
     assert e_rgb <= 2e-3 and e_op <= 2e-3
 
 
-def test_split_mixed_backward_matches_oracle():
+@pytest.mark.parametrize("name", ["grid8", "city32"])
+def test_split_mixed_backward_matches_oracle(name):
     """FP16 tables + BF16 MLPs: forward and backward on the tensor cores.
     Against the oracle on the rounded parameters, on the kink-free network
     (positive features and hidden weights): no entry off by more than 1e-2
@@ -197,7 +198,7 @@ def test_split_mixed_backward_matches_oracle():
     values; measured 1.1e-3 for the tables, 2.2e-4 for the MLPs)."""
     from paper_2404_16221_b300 import api, native as N
 
-    w = H.workload("grid8", L=16, log2_T=14)
+    w = H.workload(name, L=16, log2_T=14)
     E = oracle.table_entries(w.level_res, w.log2_T)
     Pd, Pc = oracle.density_params(w.mlp_in, w.W), oracle.color_params(w.W)
     g = sy.rng(24, "misc")
@@ -223,10 +224,51 @@ def test_split_mixed_backward_matches_oracle():
     ofq = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, _rounded(t, torch.float16),
                        _rounded(m, torch.bfloat16), arch=1)
     gt_ref, gm_ref = oracle.render_grad(ofq, w.S, o, d, gC, gD, gA, gL)
-    for name, a, b in (("tables", gt.cpu().numpy(), gt_ref), ("mlp", gm.cpu().numpy(), gm_ref)):
+    for which, a, b in (("tables", gt.cpu().numpy(), gt_ref), ("mlp", gm.cpu().numpy(), gm_ref)):
         err = np.abs(a.astype(np.float64).reshape(-1) - b.reshape(-1)) / np.abs(b).max()
-        print("split mixed backward", name, "max err / max |grad| %.2e" % err.max())
-        assert err.max() <= 1e-2, (name, err.max())
+        print("split mixed backward", name, which, "max err / max |grad| %.2e" % err.max())
+        assert err.max() <= 1e-2, (which, err.max())
+
+
+@pytest.mark.parametrize("tab", [torch.float16, torch.float32])
+def test_split_saved_records_backward_equals_rebuilt(tab):
+    """The split tensor-core backward reads the forward's per-tile records
+    (features as the first MMA read them, region coordinates, interval, ray
+    direction, chunk adjoints in tile order). Written by the training forward
+    (NERFXL_SAVE_FEATURES) or rebuilt by the backward itself, the gradients
+    agree up to the order of the FP32 atomic sums, and an occupancy grid
+    changes nothing about that."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import api, native as N
+
+    w, t, m, of, _ = _split()
+    o, d = sy.workload_rays(w, 2048, seed=72)
+    R = len(o)
+    g = sy.rng(73, "misc")
+    adj = [torch.from_numpy(a.astype(np.float32)).cuda() for a in
+           (g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R))]
+    occ = None
+    for with_grid in (False, True):
+        runs = []
+        for flags in (0, api.SAVE_FEATURES, 0, api.SAVE_FEATURES):
+            gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(tab),
+                                      torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+            if with_grid:
+                if occ is None:  # every other cell of a 16^3 grid per region
+                    occ = torch.from_numpy(np.full((w.K, 16 ** 3 // 32), 0x55555555, np.uint32).view(np.int32))
+                gf.set_occupancy(occ.cuda(), 16)
+            samp = dataclasses.replace(H.sampling(w), flags=flags)
+            ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+            out = api.render_fwd(gf, samp, o, d, workspace=ws)
+            gt, gm = api.render_bwd(gf, samp, o, d, ws, *adj)
+            api.check(ws)
+            runs.append((out["rgb"].cpu().numpy(), gt.cpu().numpy(), gm.cpu().numpy()))
+        assert np.abs(runs[0][1]).max() > 0 and np.abs(runs[0][2]).max() > 0
+        for other in runs[1:]:
+            assert np.array_equal(runs[0][0], other[0])  # the forward is deterministic
+            for a, b in zip(runs[0][1:], other[1:]):
+                assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), (with_grid, np.abs(a - b).max())
 
 
 def test_split_mixed_training_step_runs_and_refreshes_copies():
@@ -260,11 +302,6 @@ def test_split_rejects_unbuilt_forms():
                                arch=N.ARCH_SPLIT)
     o, d = sy.workload_rays(w, 64)
     samp = H.sampling(w)
-    ws = api.alloc_workspace(g16, samp, len(o), for_backward=True)
-    with pytest.raises(N.NerfxlError) as e:  # the tensor-core backward's records are not built for it
-        api.render_fwd(g16, api.Sampling(samp.n_samples, samp.max_segments, flags=api.SAVE_FEATURES), o, d,
-                       workspace=ws)
-    assert e.value.status == N.E_UNSUPPORTED
     q8 = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t),
                               torch.zeros(m.shape, dtype=torch.uint8), F=w.F, mlp_in=w.mlp_in, width=w.W,
                               arch=N.ARCH_SPLIT, mlp_scales=np.ones((w.K, 3), np.float32))

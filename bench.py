@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--cpu-rays", type=int, default=1 << 14, help="oracle sample size for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-city", action="store_true", help="skip the city32 precision and serving forms")
+    ap.add_argument("--profile-rays", type=int, default=0,
+                    help="ncu captures only: use the first N rays of the workload per step (a smaller device "
+                         "footprint); 0, the default, keeps the full batch")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
@@ -306,6 +309,8 @@ def main():
         serve_sweep(args, dev, [float(r) for r in args.serve_sweep.split(",")])
         return
     w, tables, mlp, o, d = setup_workload(rank)
+    if args.profile_rays > 0:
+        o, d = o[:args.profile_rays].copy(), d[:args.profile_rays].copy()
     samp = api.Sampling(w.S, w.max_segments)
     R = len(o)
     o_dev = torch.from_numpy(o).to(dev)
@@ -618,6 +623,8 @@ def main():
                                "(16->2048), FP16 hash tables, BF16 MLP 32-64-64-4 with FP32 accumulation on the "
                                "tensor cores, FP32 Adam masters, 2^18 rays from 64 pinhole cameras, S=128",
                    "rays_per_gpu": R, "samples_per_step": int(head["samples"]),
+                   **({"reduced_batch": "first %d rays of the workload (profiling capture, not a bench value)"
+                       % R} if args.profile_rays > 0 else {}),
                    "l2": "flushed before every timed step (252 MB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "train_target": "uniform random colours (throughput does not depend on the target)",

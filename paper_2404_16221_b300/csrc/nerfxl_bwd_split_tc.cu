@@ -5,7 +5,9 @@
 //   records   written by the forward for this tile: X exactly as its first
 //             MMA read it; per row the region coordinates, interval and ray
 //             direction; per chunk the sample count and, from the composite
-//             adjoint, the chunk's partial adjoints in tile order
+//             adjoint, the chunk's partial adjoints in tile order. One thread
+//             bulk-copies the next tile's records into the other of two
+//             shared-memory stages while this tile runs.
 //   density   D = X Wd1 -> H1 = relu; G = H1 Wd2 (N = 16)
 //   colour    Xc = [G | SH(d)]; D = Xc Wc1 -> Hc1; D = Hc1 Wc2 -> Hc2; o = Hc2 Wc3
 //   adjoint   sigma = exp(G0), rgb = sigmoid(o); chunk-local render adjoint
@@ -49,7 +51,7 @@ constexpr uint32_t kSpinS = 1u << 24;
 constexpr uint32_t kTile = 128 * 128;  // one 128-row, 128-byte-swizzled tile
 
 // Shared-memory plan (offsets from a 1024-byte-aligned base).
-constexpr uint32_t oX = 0;                 // SW64 [128][32]: features
+constexpr uint32_t oX = 0;                 // SW64 [128][32]: features, record stage 0
 constexpr uint32_t oXc = oX + 8192;        // SW64 [128][32]: [G | SH]
 constexpr uint32_t oH1 = oXc + 8192;       // SW128 [128][64]
 constexpr uint32_t oHc2 = oH1 + kTile;     // SW128, then Hc1 right after (DW3's A = [Hc2 | Hc1])
@@ -66,10 +68,19 @@ constexpr uint32_t oWc2 = oWc1 + 64 * 128;  // B: 64 rows x 64
 constexpr uint32_t oWc3 = oWc2 + 64 * 128;  // B: 16 rows x 64 (rows >= 4 zero)
 constexpr uint32_t oWd1t = oWc3 + 16 * 128;  // B of dX: 32 rows (in) x 64 (out), K-major
 constexpr uint32_t oWc1t = oWd1t + 32 * 128;  // B of dXc: 32 rows (in) x 64 (out)
-constexpr uint32_t oMiscS = oWc1t + 32 * 128;  // mbarrier (8 B), tmem slot (4 B)
+constexpr uint32_t oX1 = oWc1t + 32 * 128;    // SW64 [128][32]: features, record stage 1
+// Geometry + chunk adjoints of record stages 0, 1 (the bulk copies' images).
+constexpr uint32_t kGeoBytesS = 4 * kGeomFloats;
+constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 4 * 16;
+constexpr uint32_t oGeoS = oX1 + 8192;
+constexpr uint32_t kStageTxS = 8192 + kGeoStageS;  // bytes per stage fill
+constexpr uint32_t oMiscS = (oGeoS + 2 * kGeoStageS + 63) / 64 * 64;  // mbarriers, tmem slot (40 B)
 constexpr uint32_t oBaseS = oMiscS + 64;
 constexpr size_t kSmemS = oBaseS + 1024;
 static_assert(kRowsS == kRecRows, "one backward tile is one record tile");
+static_assert(oX1 % 1024 == 0, "X stages keep the swizzle phase");
+static_assert(kGeoBytesS % 16 == 0 && kGeoStageS % 16 == 0 && oGeoS % 16 == 0, "bulk copies need 16 B");
+static_assert(kSmemS + 1024 + 4 * 1024 <= 232448, "shared memory");
 
 struct BwdSplitTcParams {
   const void* mlp;  // 16-bit: K density blocks, then the colour block
@@ -179,6 +190,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   const uint32_t sb = tc::smem_u32(sm);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMiscS);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMiscS + 8);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + oMiscS + 16);  // record stages 0, 1 filled
+  uint64_t* drain = reinterpret_cast<uint64_t*>(sm + oMiscS + 32);  // error path: all MMAs done
   int32_t* s_base = reinterpret_cast<int32_t*>(sm + oBaseS);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
   const int q = warp & 3, g = warp >> 2;
@@ -190,7 +203,13 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   for (uint32_t i = tid; i < oWd1 / 16; i += blockDim.x) tc::st_shared_v4(sb + 16 * i, 0u, 0u, 0u, 0u);
   load_color_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm);
   if (warp == 0) tc::tmem_alloc(tmem_slot, kColsS);
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::mbar_init(full, 1);
+    tc::mbar_init(full + 1, 1);
+    tc::mbar_init(drain, 1);
+  }
+  tc::fence_proxy_async();  // the zeroed stage-0 tile before the first record copy overwrites it
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -224,7 +243,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   auto scatter_part = [&]() {
     if (cpart < 4) {
       const int l = 4 * g + cpart;
-      if (cvalid && l < p.lp.L) scatter_one(p.lp, cgtab, cu, l, cg[2 * cpart], cg[2 * cpart + 1]);
+      // constant indices keep cg in registers (a computed index would place it in local memory)
+      const float g0 = cpart == 0 ? cg[0] : (cpart == 1 ? cg[2] : (cpart == 2 ? cg[4] : cg[6]));
+      const float g1 = cpart == 0 ? cg[1] : (cpart == 1 ? cg[3] : (cpart == 2 ? cg[5] : cg[7]));
+      if (cvalid && l < p.lp.L) scatter_one(p.lp, cgtab, cu, l, g0, g1);
       ++cpart;
     }
   };
@@ -285,8 +307,27 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     dw_started = false;
   };
 
-  for (int t = blockIdx.x; t < n_sub; t += gridDim.x) {
+  // Thread kCopier issues the record copies (thread 0 issues the MMAs);
+  // pend0 / pend1 = iteration whose records are in flight into stage 0 / 1 (-1: none).
+  constexpr int kCopier = kWarp;
+  int pend0 = -1, pend1 = -1;
+  auto issue = [&](int it, int t) {
+    const int s = it & 1;
+    tc::fence_proxy_async();  // order earlier generic accesses of the stage before the overwrite
+    tc::mbar_expect_tx(full + s, kStageTxS);
+    const uint32_t geo = sb + oGeoS + (uint32_t)s * kGeoStageS;
+    const uint64_t pol = tc::policy_evict_first();  // read once: keep the gradient lines in L2
+    tc::bulk_g2s_hint(sb + (s ? oX1 : oX), p.rec_feat + (size_t)t * (kRecFeatBytes / 16), 8192, full + s, pol);
+    tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeomFloats, kGeoBytesS, full + s, pol);
+    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 2 * kChunksS, 2 * kChunksS * 16, full + s, pol);
+    (s ? pend1 : pend0) = it;
+  };
+  if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
+
+  int it = 0;
+  for (int t = blockIdx.x; t < n_sub; t += gridDim.x, ++it) {
     const int k = region_of_chunk(s_base, p.K, t * kChunksS);
+    const int s = it & 1;
     if (k != region) {
       flush();
       __syncthreads();
@@ -294,24 +335,29 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       region = k;
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
-    // ---- this tile's records: X (the record is the tile's shared-memory image),
-    //      the row's region coordinates (for the scatter), interval (render
-    //      adjoint, g == 0) and direction (SH, g == 1), the chunk's adjoints
-    const float* geo = p.rec_geom + (size_t)t * kGeomFloats;
+    // ---- the next tile's records into the other stage (free: its last readers,
+    //      the previous tile's first and last MMAs, have completed)
+    if (tid == kCopier && t + (int)gridDim.x < n_sub) issue(it + 1, t + (int)gridDim.x);
+    // ---- this tile's records: X (the record is the tile's shared-memory image,
+    //      read in place by the MMAs), the row's region coordinates (for the
+    //      scatter), interval (render adjoint, g == 0) and direction (SH,
+    //      g == 1), the chunk's adjoints
+    if (!tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpinS)) timed_out = true;
+    else if (tid == kCopier) (s ? pend1 : pend0) = -1;
+    const uint32_t xs = sb + (s ? oX1 : oX);
+    const float* geo = reinterpret_cast<const float*>(sm + oGeoS + (uint32_t)s * kGeoStageS);
+    const float4* dps = reinterpret_cast<const float4*>(sm + oGeoS + (uint32_t)s * kGeoStageS + kGeoBytesS);
     const int n_valid = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
     const bool chunk_ok = n_valid > 0, valid = (int)lane < n_valid;
-    const uint4 xr = __ldcs(p.rec_feat + (size_t)t * (kRecFeatBytes / 16) + row * 4u + ((uint32_t)g ^ ((row >> 1) & 3u)));
-    tc::st_shared_v4(sb + oX + sw64_chunk(row, g), xr.x, xr.y, xr.z, xr.w);
     float tr = 0.0f, dl = 0.0f, u[3], dir[3] = {0.0f, 0.0f, 0.0f};
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) u[ax] = __ldg(geo + ax * kRecRows + row);
+    for (int ax = 0; ax < 3; ++ax) u[ax] = geo[ax * kRecRows + row];
     if (g == 0) {
-      tr = __ldcs(geo + 3 * kRecRows + row);
-      dl = __ldcs(geo + 4 * kRecRows + row);
+      tr = geo[3 * kRecRows + row];
+      dl = geo[4 * kRecRows + row];
       if (chunk_ok) {
-        const float4 a0 = __ldcs(p.rec_dpart + 2 * ((size_t)t * kChunksS + q));
-        const float4 a1 = __ldcs(p.rec_dpart + 2 * ((size_t)t * kChunksS + q) + 1);
+        const float4 a0 = dps[2 * q], a1 = dps[2 * q + 1];
         gtc = a0.x;
         gC[0] = a0.y;
         gC[1] = a0.z;
@@ -322,14 +368,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       }
     } else if (g == 1) {
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) dir[ax] = __ldcs(geo + (5 + ax) * kRecRows + row);
+      for (int ax = 0; ax < 3; ++ax) dir[ax] = geo[(5 + ax) * kRecRows + row];
     }
     float v[16];
     uint32_t mH1 = 0, mHc1 = 0, mHc2 = 0;  // ReLU masks of this thread's 16 columns
     // ---- density: D_A = X Wd1 -> H1
     if (!step([&] {
           for (int kk = 0; kk < 2; ++kk)
-            tc::mma_f16(tmem + kDA, tc::desc_sw64(sb + oX + 32 * kk, 16), tc::desc_sw128(sb + oWd1 + 32 * kk), id64,
+            tc::mma_f16(tmem + kDA, tc::desc_sw64(xs + 32 * kk, 16), tc::desc_sw128(sb + oWd1 + 32 * kk), id64,
                         kk);
           tc::mma_commit(mbar);
         })) {
@@ -507,7 +553,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       if (!((mH1 >> i) & 1u)) v[i] = 0.0f;
     st_row16<kBF16>(sb + oGz0, row, g, v);
     // ---- dX = Gz0 Wd1^T (32 outputs) and DWd += [Gz0 | dG]^T [X | H1], under one commit: the next
-    //      tile's records overwrite X before its first commit
+    //      tile after next overwrites this stage's X at its start
     if (!step([&] {
           for (int kk = 0; kk < 4; ++kk)
             tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz0 + 32 * kk), tc::desc_sw128(sb + oWd1t + 32 * kk), id32,
@@ -515,7 +561,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
           for (int kk = 0; kk < 8; ++kk) {
             const uint64_t a = tc::desc_sw128_mn(sb + oGz0 + 2048 * kk, kTile);
             const uint32_t on = (acc || kk > 0) ? 1u : 0u;
-            tc::mma_f16(tmem + kDWd, a, tc::desc_sw64(sb + oX + 1024 * kk, 512), id32_abt, on);
+            tc::mma_f16(tmem + kDWd, a, tc::desc_sw64(xs + 1024 * kk, 512), id32_abt, on);
             tc::mma_f16(tmem + kDWd + 32, a, tc::desc_sw128_mn(sb + oH1 + 2048 * kk, 1024), id64_abt, on);
           }
           tc::mma_commit(mbar);
@@ -545,7 +591,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     while (cpart < 4) scatter_part();  // the last tile's table gradient
     flush();                           // every tile ends with all of its MMAs complete
   }
-  if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
+  if (failed && tid == 0) {
+    atomicOr(p.err, kErrTimeout);
+    // let MMAs still in flight land before the tensor memory is freed
+    tc::mma_commit(drain);
+    tc::mbar_wait_bounded(drain, 0u, kSpinS);
+  }
+  if (failed && tid == kCopier) {  // and the record copies still in flight
+    if (pend0 >= 0) tc::mbar_wait_bounded(full, (uint32_t)(pend0 >> 1) & 1u, kSpinS);
+    if (pend1 >= 0) tc::mbar_wait_bounded(full + 1, (uint32_t)(pend1 >> 1) & 1u, kSpinS);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kColsS);

@@ -116,7 +116,7 @@ struct BwdParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;
-  const uint2* chunks;
+  const uint4* chunks;  // slots
   const int32_t* n_tiles;
   const float4* dpart;   // chunk partial adjoints
   float* grad_tables;    // [K][E][2] accumulated
@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
       table = static_cast<const char*>(p.tables) + (size_t)k * p.lp.E * sizeof(TabT);
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
-    const uint2 ref = p.chunks[t * kChunksPerTile + warp];
+    const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
+    const uint2 ref = sl.ref;
     const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
     bool valid = false;
     float feat[kIn], u[3];
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
       gD = g1.y;
       gL = g1.z;
       const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-      const int i = c * kWarp + lane;
+      const int i = c * kWarp + sl.sl;
       valid = i < ss.n;
       if (valid) {
         float o[3], d[3];
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
       rgb[2] = 1.0f / (1.0f + expf(-o3));
     }
     float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
-    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sl.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sl.width);
     float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (valid) {
       go[0] = g_sigma * sigma;
@@ -513,7 +514,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
-    const uint2 ref = p.chunks[t * kChunksPerTile + warp];
+    const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
+    const uint2 ref = sl.ref;
     const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
     bool valid = false;
     float feat[kIn], u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) dir[ax] = p.rays_d[3 * (size_t)ray + ax];
       const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-      const int i = c * kWarp + lane;
+      const int i = c * kWarp + sl.sl;
       valid = i < ss.n;
       if (valid) {
         float o[3];
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-oc[m]));
     }
     float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
-    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sl.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sl.width);
     const float go_d = valid ? g_sigma * sigma : 0.0f;
     float go[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
@@ -872,7 +874,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.dpart = dpart;
   p.grad_tables = grad_tables;

@@ -71,7 +71,7 @@ constexpr uint32_t oWc1t = oWd1t + 32 * 128;  // B of dXc: 32 rows (in) x 64 (ou
 constexpr uint32_t oX1 = oWc1t + 32 * 128;    // SW64 [128][32]: features, record stage 1
 // Geometry + chunk adjoints of record stages 0, 1 (the bulk copies' images).
 constexpr uint32_t kGeoBytesS = 4 * kGeomFloats;
-constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 4 * 16;
+constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 8 * 16;  // + 8 chunk positions (2 per slot) x 2 float4
 constexpr uint32_t oGeoS = oX1 + 8192;
 constexpr uint32_t kStageTxS = 8192 + kGeoStageS;  // bytes per stage fill
 constexpr uint32_t oMiscS = (oGeoS + 2 * kGeoStageS + 63) / 64 * 64;  // mbarriers, tmem slot (40 B)
@@ -90,7 +90,7 @@ struct BwdSplitTcParams {
   const int32_t* n_tiles;
   const uint4* rec_feat;    // per tile: the 128 x 32 feature tile, 64-byte swizzled
   const float* rec_geom;    // per tile: rows u0 u1 u2 tr dl d0 d1 d2 (of kGeomRowFields), chunk counts
-  const float4* rec_dpart;  // per tile: 4 chunks x 2 partial adjoints
+  const float4* rec_dpart;  // per tile: 8 chunk positions (2 per slot) x 2 partial adjoints
   float* grad_tables;
   float* grad_mlp;
   int32_t* err;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     const uint64_t pol = tc::policy_evict_first();  // read once: keep the gradient lines in L2
     tc::bulk_g2s_hint(sb + (s ? oX1 : oX), p.rec_feat + (size_t)t * (kRecFeatBytes / 16), 8192, full + s, pol);
     tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeomFloats, kGeoBytesS, full + s, pol);
-    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 2 * kChunksS, 2 * kChunksS * 16, full + s, pol);
+    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 16, 256, full + s, pol);
     (s ? pend1 : pend0) = it;
   };
   if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
@@ -347,8 +347,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     const uint32_t xs = sb + (s ? oX1 : oX);
     const float* geo = reinterpret_cast<const float*>(sm + oGeoS + (uint32_t)s * kGeoStageS);
     const float4* dps = reinterpret_cast<const float4*>(sm + oGeoS + (uint32_t)s * kGeoStageS + kGeoBytesS);
-    const int n_valid = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
-    const bool chunk_ok = n_valid > 0, valid = (int)lane < n_valid;
+    const int32_t nword = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
+    const SlotCount sc = slot_count(nword, lane);
+    const bool chunk_ok = nword != 0, valid = sc.sl < sc.n;  // chunk_ok: warp-uniform
     float tr = 0.0f, dl = 0.0f, u[3], dir[3] = {0.0f, 0.0f, 0.0f};
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
 #pragma unroll
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       tr = geo[3 * kRecRows + row];
       dl = geo[4 * kRecRows + row];
       if (chunk_ok) {
-        const float4 a0 = dps[2 * q], a1 = dps[2 * q + 1];
+        const float4 a0 = dps[2 * (2 * q + sc.half)], a1 = dps[2 * (2 * q + sc.half) + 1];
         gtc = a0.x;
         gC[0] = a0.y;
         gC[1] = a0.z;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-v[m]));
       }
       float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
-      if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, lane, gtc, gC, gA, gD, gL, g_sigma, g_rgb);
+      if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sc.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sc.width);
       float go[16];
 #pragma unroll
       for (int m = 0; m < 16; ++m) go[m] = 0.0f;

@@ -85,11 +85,11 @@ constexpr uint32_t oXs = oGO + kTileBytes;
 constexpr uint32_t kXBytes = (uint32_t)kRecFeatBytes;
 constexpr uint32_t oGeo = oXs + 2 * kXBytes;
 constexpr uint32_t kGeoBytes = 4 * kGeomFloats;
-constexpr uint32_t kGeoStage = kGeoBytes + 2 * 4 * 16;  // + 4 chunks x 2 float4
+constexpr uint32_t kGeoStage = kGeoBytes + 2 * 8 * 16;  // + 8 chunk positions (2 per slot) x 2 float4
 constexpr uint32_t kStageTx = kXBytes + kGeoStage;      // bytes per stage fill
 // Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][128 rows]
 // (row-contiguous, so both roles access it without bank conflicts), u as
-// float [3][128], then int32 n_valid[4] and the region.
+// float [3][128], then the 4 slots' count words (int32) and the region.
 constexpr uint32_t oHand = oGeo + 2 * kGeoStage;
 constexpr uint32_t kHdDf = 0, kHdU = 16384, kHdNv = kHdU + 3 * 4 * kRows, kHdRegion = kHdNv + 16;
 constexpr uint32_t kHandBytes = kHdRegion + 16;
@@ -108,7 +108,7 @@ struct BwdTcParams {
   const int32_t* n_tiles;
   const char* rec_feat;   // kRecFeatBytes per tile
   const char* rec_geom;   // kGeomFloats floats per tile
-  const char* rec_dpart;  // 4 chunks x 2 float4 per tile
+  const char* rec_dpart;  // 8 chunk positions x 2 float4 per tile
   float* grad_tables;     // FP32 [K][E][2]
   float* grad_mlp;        // FP32 [K][kMlpParams]
   int32_t* err;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         break;
       }
       const char* hd = sm + oHand + (uint32_t)b * kHandBytes;
-      const int n_valid = reinterpret_cast<const int32_t*>(hd + kHdNv)[q];
+      const SlotCount sc = slot_count(reinterpret_cast<const int32_t*>(hd + kHdNv)[q], lane);
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegion);
       const float* hu = reinterpret_cast<const float*>(hd + kHdU);
       const float u[3] = {hu[row], hu[kRows + row], hu[2 * kRows + row]};
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       }
       tc::bar_sync(kBarScatter, kGroup);  // slot read by every scatter thread
       if (tid == kGroup) tc::mbar_arrive(hempty + b);
-      if (lane < n_valid) {
+      if (sc.sl < sc.n) {
         float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       const uint64_t pol = tc::policy_evict_first();
       tc::bulk_g2s_hint(sb + oXs + (uint32_t)s * kXBytes, p.rec_feat + (size_t)t * kXBytes, kXBytes, full + s, pol);
       tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeoBytes, kGeoBytes, full + s, pol);
-      tc::bulk_g2s_hint(geo + kGeoBytes, p.rec_dpart + (size_t)t * 128, 128, full + s, pol);
+      tc::bulk_g2s_hint(geo + kGeoBytes, p.rec_dpart + (size_t)t * 256, 256, full + s, pol);
       pend[s] = it;
     };
     if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
@@ -378,8 +378,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       const uint32_t xs = sb + oXs + (uint32_t)s * kXBytes;
       const char* gst = sm + oGeo + (uint32_t)s * kGeoStage;
       const float* geo = reinterpret_cast<const float*>(gst);
-      const int n_valid = reinterpret_cast<const int32_t*>(geo)[kGeomRowFields * kRows + q];
-      const bool valid = lane < n_valid;
+      const int32_t nword = reinterpret_cast<const int32_t*>(geo)[kGeomRowFields * kRows + q];
+      const SlotCount sc = slot_count(nword, lane);
+      const bool valid = sc.sl < sc.n;
       // ---- forward recompute: D1 = X W1
       if (tid == 0 && staged) {
         tc::fence_after_sync();
@@ -392,16 +393,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       //      samples outside the chunks
       if (g == 0 && staged) {
         float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (n_valid > 0) {
-          const float4 a0 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q);
-          const float4 a1 = *reinterpret_cast<const float4*>(gst + kGeoBytes + 32 * q + 16);
+        if (nword != 0) {  // (warp-uniform: a slot is empty or all its chunks are not)
+          const char* ap = gst + kGeoBytes + 32 * (2 * q + sc.half);
+          const float4 a0 = *reinterpret_cast<const float4*>(ap);
+          const float4 a1 = *reinterpret_cast<const float4*>(ap + 16);
           const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
           const float Tn = geo[5 * kRows + row], w = geo[6 * kRows + row], pair = geo[7 * kRows + row];
           const float sigma = geo[8 * kRows + row];
           const float rgb[3] = {geo[9 * kRows + row], geo[10 * kRows + row], geo[11 * kRows + row]};
           float g_tau;
-          render_chunk_adjoint_kept(a0.y * rgb[0] + a0.z * rgb[1] + a0.w * rgb[2], tr, dl, Tn, w, pair, lane, a0.x,
-                                    a1.x, a1.y, a1.z, g_tau);
+          render_chunk_adjoint_kept(a0.y * rgb[0] + a0.z * rgb[1] + a0.w * rgb[2], tr, dl, Tn, w, pair, sc.sl, a0.x,
+                                    a1.x, a1.y, a1.z, g_tau, sc.width);
           if (valid) {
             const float gC[3] = {a0.y, a0.z, a0.w};
             go[0] = g_tau * dl * sigma;
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         float* hu = reinterpret_cast<float*>(hd + kHdU);
 #pragma unroll
         for (int a = 0; a < 3; ++a) hu[a * kRows + row] = geo[a * kRows + row];
-        if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNv)[q] = n_valid;
+        if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNv)[q] = nword;
         if (tid == 0) *reinterpret_cast<int32_t*>(hd + kHdRegion) = k;
       }
       tc::fence_before_sync();

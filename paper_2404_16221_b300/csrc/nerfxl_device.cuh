@@ -27,8 +27,55 @@ constexpr int kWidth = 64;
 constexpr int kOut = 4;
 constexpr int kMlpParams = kIn * kWidth + kWidth * kWidth + kWidth * kOut;
 
-// Chunks per CTA tile (one warp per chunk); region buckets are padded to it.
+// Chunk slots per CTA tile (one warp per slot); region buckets are padded to it.
 constexpr int kChunksPerTile = 8;
+
+// A chunk is up to 32 consecutive samples of one ray segment, the unit of the
+// local render. A slot is the 32 rows (one warp) a chunk is evaluated in: it
+// holds one chunk (lane = sample), or two chunks of at most 16 samples each
+// (a segment's tail or a short segment) in lanes 0-15 and 16-31. Slot layout
+// {ray A, seg A << 16 | chunk A, ray B, seg B << 16 | chunk B}; ray B =
+// kEmptyChunk when the slot holds one chunk, ray A = kEmptyChunk when it is
+// padding.
+constexpr int kHalfChunk = 16;
+
+struct SlotLane {
+  uint2 ref;  // the lane's chunk {ray, seg << 16 | chunk}; ref.x == kEmptyChunk: none
+  int width;  // lanes of the lane's chunk: 32, or 16 in a shared slot
+  int sl;     // the lane's sample index within its chunk
+};
+
+__device__ __forceinline__ SlotLane slot_lane(const uint4 s, int lane) {
+  const bool shared = s.z != kEmptyChunk;
+  const bool hi = shared && lane >= kHalfChunk;
+  SlotLane o;
+  o.ref = hi ? make_uint2(s.z, s.w) : make_uint2(s.x, s.y);
+  o.width = shared ? kHalfChunk : 32;
+  o.sl = shared ? (lane & (kHalfChunk - 1)) : lane;
+  return o;
+}
+
+// A slot's sample counts as the tensor-core records keep them (one int32:
+// n | 0, or nA | nB << 8 | 1 << 16 for two half-slot chunks), resolved for a
+// lane: its chunk's count, width, the lane's index in it and which half.
+struct SlotCount {
+  int n, width, sl, half;
+};
+
+__device__ __forceinline__ SlotCount slot_count(int32_t word, int lane) {
+  const bool shared = (word >> 16) & 1;
+  const bool hi = shared && lane >= kHalfChunk;
+  SlotCount o;
+  o.n = hi ? (word >> 8) & 0xFF : word & 0xFF;
+  o.width = shared ? kHalfChunk : 32;
+  o.sl = shared ? (lane & (kHalfChunk - 1)) : lane;
+  o.half = hi ? 1 : 0;
+  return o;
+}
+
+// Chunks of a segment of n samples, and whether its last one fits half a slot.
+__device__ __forceinline__ int seg_chunks(int n) { return (n + 31) / 32; }
+__device__ __forceinline__ bool seg_half_tail(int n) { return n > 0 && n - 32 * ((n - 1) / 32) <= kHalfChunk; }
 
 // Error flags written into the workspace header.
 constexpr int kErrOverflow = 1;
@@ -234,32 +281,39 @@ __device__ __forceinline__ int region_of_chunk(const int32_t* base, int K, int c
 // ---------------------------------------------------------------------------
 // Warp scans and reductions.
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums and scans over segments of `width` lanes (32 or 16; every lane of the
+// warp takes part); `lane` is the index within the segment. With width 16 the
+// two half-warps are independent, and a chunk's results equal those over 32
+// lanes with zeros after it, bit for bit (the extra steps add zeros).
+__device__ __forceinline__ float warp_sum(float v, int width = 32) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  for (int o = 16; o > 0; o >>= 1)
+    if (o < width) v += __shfl_xor_sync(0xFFFFFFFFu, v, o, width);
   return v;
 }
 
-__device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
+__device__ __forceinline__ float warp_inclusive_scan(float v, int lane, int width = 32) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (o >= width) break;
+    const float t = __shfl_up_sync(0xFFFFFFFFu, v, o, width);
     if (lane >= o) v += t;
   }
   return v;
 }
 
-__device__ __forceinline__ float warp_exclusive_from_inclusive(float incl, int lane) {
-  const float t = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+__device__ __forceinline__ float warp_exclusive_from_inclusive(float incl, int lane, int width = 32) {
+  const float t = __shfl_up_sync(0xFFFFFFFFu, incl, 1, width);
   return lane == 0 ? 0.0f : t;
 }
 
-// Suffix sum (sum over lanes >= lane).
-__device__ __forceinline__ float warp_suffix_scan(float v, int lane) {
+// Suffix sum (sum over lanes >= lane of the segment).
+__device__ __forceinline__ float warp_suffix_scan(float v, int lane, int width = 32) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float t = __shfl_down_sync(0xFFFFFFFFu, v, o);
-    if (lane + o < 32) v += t;
+    if (o >= width) break;
+    const float t = __shfl_down_sync(0xFFFFFFFFu, v, o, width);
+    if (lane + o < width) v += t;
   }
   return v;
 }

@@ -271,38 +271,39 @@ struct Partial {
   float tau, c0, c1, c2, A, D, L;
 };
 
-// Region-local volume rendering of one 32-sample chunk by one warp
-// (Eq. 1-2 restricted to the chunk, transmittance restarting at 1). If `keep`
-// is given, the lane also stores the quantities its adjoint reuses:
+// Region-local volume rendering of one chunk by the `width` lanes holding it
+// (Eq. 1-2 restricted to the chunk, transmittance restarting at 1; `lane` is
+// the sample's index in the chunk, every lane of the warp calls this). If
+// `keep` is given, the lane also stores the quantities its adjoint reuses:
 // keep[0] = Tn (transmittance after the sample), keep[stride] = w,
 // keep[2 stride] = sum_j w_j |tr - tr_j| over the chunk.
 __device__ __forceinline__ Partial render_chunk(float sigma, const float rgb[3], float tr, float dl, int lane,
-                                                float* keep = nullptr, int stride = 0) {
+                                                float* keep = nullptr, int stride = 0, int width = 32) {
   const float tau = sigma * dl;
-  const float incl = warp_inclusive_scan(tau, lane);
-  const float excl = warp_exclusive_from_inclusive(incl, lane);
+  const float incl = warp_inclusive_scan(tau, lane, width);
+  const float excl = warp_exclusive_from_inclusive(incl, lane, width);
   const float T = expf(-excl);
   const float alpha = -expm1f(-tau);
   const float w = T * alpha;
   const float wt = w * tr;
-  const float Wx = warp_exclusive_from_inclusive(warp_inclusive_scan(w, lane), lane);
-  const float WTx = warp_exclusive_from_inclusive(warp_inclusive_scan(wt, lane), lane);
+  const float Wx = warp_exclusive_from_inclusive(warp_inclusive_scan(w, lane, width), lane, width);
+  const float WTx = warp_exclusive_from_inclusive(warp_inclusive_scan(wt, lane, width), lane, width);
   const float l = 2.0f * w * (tr * Wx - WTx) + w * w * dl * (1.0f / 3.0f);
   if (keep) {
-    const float W_gt = warp_suffix_scan(w, lane) - w;
-    const float WT_gt = warp_suffix_scan(wt, lane) - wt;
+    const float W_gt = warp_suffix_scan(w, lane, width) - w;
+    const float WT_gt = warp_suffix_scan(wt, lane, width) - wt;
     __stcs(keep, expf(-incl));
     __stcs(keep + stride, w);
     __stcs(keep + 2 * stride, (tr * Wx - WTx) + (WT_gt - tr * W_gt));
   }
   Partial p;
-  p.tau = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  p.c0 = warp_sum(w * rgb[0]);
-  p.c1 = warp_sum(w * rgb[1]);
-  p.c2 = warp_sum(w * rgb[2]);
-  p.A = warp_sum(w);
-  p.D = warp_sum(wt);
-  p.L = warp_sum(l);
+  p.tau = __shfl_sync(0xFFFFFFFFu, incl, width - 1, width);
+  p.c0 = warp_sum(w * rgb[0], width);
+  p.c1 = warp_sum(w * rgb[1], width);
+  p.c2 = warp_sum(w * rgb[2], width);
+  p.A = warp_sum(w, width);
+  p.D = warp_sum(wt, width);
+  p.L = warp_sum(l, width);
   return p;
 }
 
@@ -366,31 +367,31 @@ struct TableOf<true> {
   }
 };
 
-// Adjoint of the chunk-local render for one warp (one chunk). Inputs per lane:
-// sigma, rgb, t' (tbar - tn), delta; chunk adjoints gtc, gC, gA, gD, gL.
-// Returns dL/d(sigma), dL/d(rgb).
+// Adjoint of the chunk-local render for the `width` lanes of one chunk
+// (`lane`: index in the chunk). Inputs per lane: sigma, rgb, t' (tbar - tn),
+// delta; chunk adjoints gtc, gC, gA, gD, gL. Returns dL/d(sigma), dL/d(rgb).
 __device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rgb[3], float tr, float dl, int lane,
                                                      float gtc, const float gC[3], float gA, float gD, float gL,
-                                                     float& g_sigma, float g_rgb[3]) {
+                                                     float& g_sigma, float g_rgb[3], int width = 32) {
   const float tau = sigma * dl;
-  const float incl = warp_inclusive_scan(tau, lane);
-  const float excl = warp_exclusive_from_inclusive(incl, lane);
+  const float incl = warp_inclusive_scan(tau, lane, width);
+  const float excl = warp_exclusive_from_inclusive(incl, lane, width);
   const float T = expf(-excl);
   const float Tn = expf(-incl);
   const float w = T * -expm1f(-tau);
   const float wt = w * tr;
-  const float W_in = warp_inclusive_scan(w, lane);
-  const float WT_in = warp_inclusive_scan(wt, lane);
-  const float W_lt = warp_exclusive_from_inclusive(W_in, lane);
-  const float WT_lt = warp_exclusive_from_inclusive(WT_in, lane);
-  const float W_gt = warp_suffix_scan(w, lane) - w;
-  const float WT_gt = warp_suffix_scan(wt, lane) - wt;
+  const float W_in = warp_inclusive_scan(w, lane, width);
+  const float WT_in = warp_inclusive_scan(wt, lane, width);
+  const float W_lt = warp_exclusive_from_inclusive(W_in, lane, width);
+  const float WT_lt = warp_exclusive_from_inclusive(WT_in, lane, width);
+  const float W_gt = warp_suffix_scan(w, lane, width) - w;
+  const float WT_gt = warp_suffix_scan(wt, lane, width) - wt;
   // sum_j w_j |t_i - t_j| over the chunk
   const float pair = (tr * W_lt - WT_lt) + (WT_gt - tr * W_gt);
   const float gw = gC[0] * rgb[0] + gC[1] * rgb[1] + gC[2] * rgb[2] + gA + gD * tr +
                    gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
   const float gww = gw * w;
-  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
+  const float later = warp_suffix_scan(gww, lane, width) - gww;  // sum_{j > i} g_w_j w_j
   const float g_tau = gtc + gw * Tn - later;
   g_sigma = g_tau * dl;
 #pragma unroll
@@ -401,10 +402,10 @@ __device__ __forceinline__ void render_chunk_adjoint(float sigma, const float rg
 // (see render_chunk): one suffix scan instead of the recomputed prefix sums.
 __device__ __forceinline__ void render_chunk_adjoint_kept(float rgb_dot_gC, float tr, float dl, float Tn, float w,
                                                           float pair, int lane, float gtc, float gA, float gD, float gL,
-                                                          float& g_tau) {
+                                                          float& g_tau, int width = 32) {
   const float gw = rgb_dot_gC + gA + gD * tr + gL * (2.0f * pair + (2.0f / 3.0f) * w * dl);
   const float gww = gw * w;
-  const float later = warp_suffix_scan(gww, lane) - gww;  // sum_{j > i} g_w_j w_j
+  const float later = warp_suffix_scan(gww, lane, width) - gww;  // sum_{j > i} g_w_j w_j
   g_tau = gtc + gw * Tn - later;
 }
 

@@ -40,10 +40,10 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
                                                   int32_t* __restrict__ counts, int32_t* __restrict__ err) {
   extern __shared__ float s_mem[];
   float* s_boxes = s_mem;                                 // [K][6]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [K]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [2][K]: chunks, half-slot chunks
   __shared__ unsigned long long s_samples, s_chunks;
   for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
   if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
   __syncthreads();
 
@@ -75,8 +75,11 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
       s.jlo_n = (jlo & 0xFFFF) | (n << 16);
       s.reg_cb = (sreg[k] & 0xFFFF) | (cbase << 16);
       segs[r * sp.max_seg + k] = s;
-      const int nch = (n + kWarp - 1) / kWarp;
-      if (counts) atomicAdd(&s_cnt[sreg[k]], nch);
+      const int nch = seg_chunks(n);
+      if (counts) {
+        atomicAdd(&s_cnt[sreg[k]], nch);
+        if (seg_half_tail(n)) atomicAdd(&s_cnt[K + sreg[k]], 1);
+      }
       cbase += nch;
       n_samples += n;
     }
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
   }
   __syncthreads();
   if (!counts) return;  // the occupancy pass buckets the kept samples
-  for (int i = threadIdx.x; i < K; i += blockDim.x)
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
   if (threadIdx.x == 0) {
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
@@ -123,15 +126,15 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
                                                     int32_t* __restrict__ err) {
   extern __shared__ float s_mem[];
   float* s_boxes = s_mem;                                      // [K][6]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [K]
-  float* s_inv = s_mem + 7 * K;                                // [K][3] 1 / box extent
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [2][K]: chunks, half-slot chunks
+  float* s_inv = s_mem + 8 * K;                                // [K][3] 1 / box extent
   __shared__ unsigned long long s_samples, s_chunks;
   for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
   for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) {
     const int k = i / 3, ax = i % 3;
     s_inv[i] = __fdiv_rn(1.0f, __fsub_rn(boxes[6 * k + 3 + ax], boxes[6 * k + ax]));
   }
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
   if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
   __syncthreads();
 
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
       }
     }
     // per segment: list start and chunk base (exclusive scans over the lanes)
-    const int my_nch = (my_count + kWarp - 1) / kWarp;
+    const int my_nch = seg_chunks(my_count);
     int inc_c = my_count, inc_h = my_nch;
 #pragma unroll
     for (int off = 1; off < kWarp; off <<= 1) {
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
       seg_keep[r * sp.max_seg + lane] = my_count | ((inc_c - my_count) << 16);
       segs[r * sp.max_seg + lane].reg_cb = (reg & 0xFFFF) | (cbase << 16);
       if (my_nch) atomicAdd(&s_cnt[reg], my_nch);
+      if (seg_half_tail(my_count)) atomicAdd(&s_cnt[K + reg], 1);
     }
     const int nchunk = __shfl_sync(kFull, inc_h, kWarp - 1);
     if (lane == 0) {
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x)
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
   if (threadIdx.x == 0) {
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
@@ -264,8 +268,11 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
 }
 
 // ---------------------------------------------------------------------------
-// k_region_scan: base[k] = sum_{k' < k} round_up(count[k'], tile); padding
-// slots get the empty marker; header word 1 = total tiles.
+// k_region_scan: region k holds counts[k] chunks, counts[K + k] of them of at
+// most 16 samples; its slots are one per longer chunk, then one per pair of
+// short ones: slots_k = counts[k] - counts[K + k] + ceil(counts[K + k] / 2).
+// base[k] = sum_{k' < k} round_up(slots_k', tile); padding slots and the free
+// half of an odd last pair get the empty marker; header word 1 = total tiles.
 
 __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chunks_per_tile,
                               int32_t* __restrict__ base, uint2* __restrict__ chunks, int32_t* __restrict__ n_tiles) {
@@ -273,9 +280,14 @@ __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chu
   int32_t acc = 0;
   for (int k = 0; k < K; ++k) {
     base[k] = acc;
-    const int c = counts[k];
-    const int padded = (c + chunks_per_tile - 1) / chunks_per_tile * chunks_per_tile;
-    for (int i = c; i < padded; ++i) chunks[acc + i] = make_uint2(kEmptyChunk, 0u);
+    const int h = counts[K + k];
+    const int slots = counts[k] - h + (h + 1) / 2;
+    const int padded = (slots + chunks_per_tile - 1) / chunks_per_tile * chunks_per_tile;
+    if (h & 1) chunks[2 * (acc + slots - 1) + 1] = make_uint2(kEmptyChunk, 0u);
+    for (int i = slots; i < padded; ++i) {
+      chunks[2 * (acc + i)] = make_uint2(kEmptyChunk, 0u);
+      chunks[2 * (acc + i) + 1] = make_uint2(kEmptyChunk, 0u);
+    }
     acc += padded;
   }
   base[K] = acc;
@@ -283,36 +295,54 @@ __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chu
 }
 
 // ---------------------------------------------------------------------------
-// k_fill_chunks: chunk references {ray, seg << 16 | chunk-in-segment}.
+// k_fill_chunks: chunk references {ray, seg << 16 | chunk-in-segment} into
+// the region's slots (chunks = uint2 [slots][2]): a chunk of more than 16
+// samples fills a slot alone, a segment's last chunk of at most 16 takes the
+// next free half of the region's paired slots.
 
 __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParams sp, const RayHdr* __restrict__ hdr,
                                                      const SegDesc* __restrict__ segs,
+                                                     const int32_t* __restrict__ counts,
                                                      const int32_t* __restrict__ base, int32_t* __restrict__ cursor,
                                                      uint2* __restrict__ chunks) {
   extern __shared__ int32_t s_i[];
-  int32_t* s_cnt = s_i;       // [K]
-  int32_t* s_base = s_i + K;  // [K]
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_cnt[i] = 0;
+  int32_t* s_cnt = s_i;  // [2][K]: this block's whole-slot chunks, half-slot chunks
+  int32_t* s_base = s_i + 2 * K;  // [2][K]: their first index in the region
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int nseg = 0;
-  int off[kMaxSeg];
+  int off[kMaxSeg], hoff[kMaxSeg];
   if (r < R) {
     nseg = hdr[r].nseg;
     for (int k = 0; k < nseg; ++k) {
       const SegDesc s = segs[r * sp.max_seg + k];
-      off[k] = atomicAdd(&s_cnt[seg_region(s)], (seg_samples(sp, s, r, k).n + kWarp - 1) / kWarp);
+      const int n = seg_samples(sp, s, r, k).n;
+      const bool half = seg_half_tail(n);
+      off[k] = atomicAdd(&s_cnt[seg_region(s)], seg_chunks(n) - (half ? 1 : 0));
+      hoff[k] = half ? atomicAdd(&s_cnt[K + seg_region(s)], 1) : 0;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_base[i] = s_cnt[i] ? atomicAdd(&cursor[i], s_cnt[i]) : 0;
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_base[i] = s_cnt[i] ? atomicAdd(&cursor[i], s_cnt[i]) : 0;
   __syncthreads();
   for (int k = 0; k < nseg; ++k) {
     const SegDesc s = segs[r * sp.max_seg + k];
     const int reg = seg_region(s);
-    const int nch = (seg_samples(sp, s, r, k).n + kWarp - 1) / kWarp;
+    const int n = seg_samples(sp, s, r, k).n;
+    const int nch = seg_chunks(n);
+    const bool half = seg_half_tail(n);
+    const int nfull = nch - (half ? 1 : 0);
     const int dst = base[reg] + s_base[reg] + off[k];
-    for (int c = 0; c < nch; ++c) chunks[dst + c] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
+    for (int c = 0; c < nfull; ++c) {
+      chunks[2 * (dst + c)] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
+      chunks[2 * (dst + c) + 1] = make_uint2(kEmptyChunk, 0u);
+    }
+    if (half) {
+      const int h = s_base[K + reg] + hoff[k];  // index among the region's short chunks
+      const int slot = base[reg] + (counts[reg] - counts[K + reg]) + (h >> 1);
+      chunks[2 * slot + (h & 1)] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | (nch - 1)));
+    }
   }
 }
 
@@ -333,7 +363,7 @@ struct FwdParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;     // [K+1]
-  const uint2* chunks;
+  const uint4* chunks;     // slots
   const int32_t* n_tiles;
   float4* partials;        // [R][max_chunk][2]
   float4* smp4;            // per sample slot: sigma, rgb (sample-level composition), or NULL
@@ -370,8 +400,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       region = k;
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
     }
-    const uint2 ref = p.chunks[chunk];
-    if (ref.x == kEmptyChunk) continue;  // warp-uniform
+    const SlotLane sl = slot_lane(p.chunks[chunk], lane);
+    if (sl.ref.x == kEmptyChunk) continue;  // warp-uniform (padding)
+    const uint2 ref = sl.ref;
     const uint32_t ray = ref.x;
     const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
     const RayHdr h = p.hdr[ray];
@@ -383,7 +414,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       d[ax] = p.rays_d[3 * (size_t)ray + ax];
     }
     const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-    const int i = c * kWarp + lane;
+    const int i = c * kWarp + sl.sl;
     const bool valid = i < ss.n;
     float feat[kIn];
     float tbar = 0.0f, dl = 0.0f;
@@ -403,7 +434,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     float raw[kOut];
     if (kSplit) {
       float sh[kSh];
-      sh4_f32(d, sh);  // the chunk's ray: the same for every lane
+      sh4_f32(d, sh);  // the lane's ray
       split_f32_smem(s_w, s_w + kDensityParams, feat, sh, raw);
     } else {
       mlp_f32_smem(s_w, feat, raw);
@@ -417,12 +448,16 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     const float tr = valid ? __fsub_rn(tbar, h.tn) : 0.0f;
     const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
     if (p.smp4) {  // sample-level composition: every sample leaves the kernel
-      p.smp4[slot * kWarp + lane] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
-      p.smp2[slot * kWarp + lane] = make_float2(tr, dl);
+      p.smp4[slot * kWarp + sl.sl] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+      p.smp2[slot * kWarp + sl.sl] = make_float2(tr, dl);
+      if (sl.width < kWarp) {  // a half-slot chunk: its sample slots 16..31 are empty
+        p.smp4[slot * kWarp + kHalfChunk + sl.sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        p.smp2[slot * kWarp + kHalfChunk + sl.sl] = make_float2(0.0f, 0.0f);
+      }
       continue;
     }
-    const Partial pt = render_chunk(sigma, rgb, tr, dl, lane);
-    if (lane == 0) {
+    const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl, nullptr, 0, sl.width);
+    if (sl.sl == 0) {
       float4* dst = p.partials + 2 * slot;
       dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
       dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -590,8 +625,8 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     return at;
   };
   L.hdr = take(sizeof(int32_t) * 16);
-  L.counts = take(sizeof(int32_t) * K);
-  L.cursor = take(sizeof(int32_t) * K);
+  L.counts = take(sizeof(int32_t) * 2 * K);  // chunks per region, then those of at most 16 samples
+  L.cursor = take(sizeof(int32_t) * 2 * K);
   L.zero_end = off;
   L.base = take(sizeof(int32_t) * (K + 1));
   L.ray_hdr = take(sizeof(RayHdr) * R);
@@ -603,7 +638,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.kept = take(sizeof(uint16_t) * R * L.max_int);
   }
   L.chunk_cap = (int64_t)R * mc + (int64_t)kChunksPerTile * K;
-  L.chunks = take(sizeof(uint2) * L.chunk_cap);
+  L.chunks = take(sizeof(uint4) * L.chunk_cap);  // slots (at most one per chunk)
   L.partials = take(sizeof(float4) * 2 * R * mc);
   L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
   L.rec_feat = L.rec_geom = L.rec_dpart = L.rec_pos = 0;
@@ -612,7 +647,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.rec_tiles = (L.chunk_cap + 3) / 4;
     L.rec_feat = take(kRecFeatBytes * L.rec_tiles);
     L.rec_geom = take(sizeof(float) * kGeomFloats * L.rec_tiles);
-    L.rec_dpart = take(sizeof(float4) * 2 * 4 * L.rec_tiles);
+    L.rec_dpart = take(sizeof(float4) * 2 * 8 * L.rec_tiles);
     L.rec_pos = take(sizeof(int32_t) * R * mc);
   }
   L.smp4 = L.smp2 = 0;
@@ -709,7 +744,7 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
   const int threads = 256;
   const int blocks = (int)((R + threads - 1) / threads);
   if (R > 0) {
-    const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * K;
+    const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * 2 * K;
     int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
     k_segments<<<blocks, threads, smem, stream>>>(rays_o, rays_d, R, f->boxes, K, sp,
                                                   reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
@@ -735,10 +770,10 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
   nerfxl_status st = launch_check("k_region_scan");
   if (st != NERFXL_OK) return st;
   if (R > 0) {
-    k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 2 * K, stream>>>(
+    k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 4 * K, stream>>>(
         R, K, sp, reinterpret_cast<RayHdr*>(ws + L.ray_hdr), reinterpret_cast<SegDesc*>(ws + L.segs),
-        reinterpret_cast<int32_t*>(ws + L.base), reinterpret_cast<int32_t*>(ws + L.cursor),
-        reinterpret_cast<uint2*>(ws + L.chunks));
+        reinterpret_cast<int32_t*>(ws + L.counts), reinterpret_cast<int32_t*>(ws + L.base),
+        reinterpret_cast<int32_t*>(ws + L.cursor), reinterpret_cast<uint2*>(ws + L.chunks));
     st = launch_check("k_fill_chunks");
     if (st != NERFXL_OK) return st;
   }
@@ -858,7 +893,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   const bool per_sample = (s->flags & NERFXL_SAMPLE_COMPOSITE) != 0;

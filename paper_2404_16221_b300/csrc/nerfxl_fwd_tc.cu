@@ -211,7 +211,7 @@ struct FwdTcParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;
-  const uint2* chunks;
+  const uint4* chunks;  // slots
   const int32_t* n_tiles;  // tiles of kChunksPerTile chunks
   float4* partials;
   RecordOut rec;  // the backward's per-tile records, or all NULL
@@ -273,8 +273,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
     }
     // ---- gather: the four threads of a row each gather four levels
-    const uint2 ref = p.chunks[t * kTcChunks + q];
-    const bool chunk_ok = ref.x != kEmptyChunk;
+    const SlotLane sl = slot_lane(p.chunks[t * kTcChunks + q], lane);
+    const uint2 ref = sl.ref;
+    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
     bool valid = false;
     float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f};
     float f8[8];
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
       const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
       seg_count = ss.n;
-      const int i = c * kWarp + lane;
+      const int i = c * kWarp + sl.sl;
       valid = i < ss.n;
       if (valid) {
         float o[3], d[3];
@@ -317,8 +318,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     if (kRec) {
       // Records for the backward: the features exactly as the first MMA reads
       // them, the sample's region coordinates / position / length (thread g
-      // stores one of u0, u1, u2, tr; g == 0 also dl), the chunk's sample
-      // count, and the chunk's tile-order position for the composite adjoint
+      // stores one of u0, u1, u2, tr; g == 0 also dl), the slot's sample
+      // counts, and each chunk's tile-order position for the composite adjoint
       // (Tn, w, pair, sigma and rgb follow from the chunk render below).
       // Streaming stores: the records are read once, by the backward, and
       // should not push the region's tables out of L2 meanwhile.
@@ -335,11 +336,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       }
       if (g == 0) {
         __stcs(geo + 4 * kTcRows + row, dl);
-        if (lane == 0) {
-          const int n_valid = chunk_ok ? min(kWarp, seg_count - c * kWarp) : 0;
-          reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] = n_valid;
-          if (chunk_ok) p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = t * kTcChunks + q;
-        }
+        // the slot's counts: n(chunk A) | n(chunk B) << 8 | shared << 16
+        const int n_mine = chunk_ok ? min(kWarp, seg_count - c * kWarp) : 0;
+        const int n_hi = __shfl_sync(0xFFFFFFFFu, n_mine, kHalfChunk);
+        if (lane == 0)
+          reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] =
+              sl.width < kWarp ? (n_mine | (n_hi << 8) | (1 << 16)) : n_mine;
+        if (chunk_ok && sl.sl == 0)  // tile-order position of the chunk's adjoints: 2 per slot
+          p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] =
+              2 * (t * kTcChunks + q) + (lane >= kHalfChunk ? 1 : 0);
       }
     }
     if constexpr (kSplit) {
@@ -404,8 +409,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[j]));
           }
-          const Partial pt = render_chunk(sigma, rgb, tr, dl, lane, nullptr, kTcRows);
-          if (lane == 0) {
+          const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl, nullptr, kTcRows, sl.width);
+          if (sl.sl == 0) {
             float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
             dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
             dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -492,16 +497,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 #pragma unroll
           for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[1 + j] * scale[2]));
         }
-        const Partial pt = render_chunk(sigma, rgb, tr, dl, lane,
+        const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl,
                                         kRec ? p.rec.geom + (size_t)t * kGeomFloats + 5 * kTcRows + row : nullptr,
-                                        kTcRows);
+                                        kTcRows, sl.width);
         if (kRec) {
           float* geo = p.rec.geom + (size_t)t * kGeomFloats;
           __stcs(geo + 8 * kTcRows + row, sigma);
 #pragma unroll
           for (int j = 0; j < 3; ++j) __stcs(geo + (9 + j) * kTcRows + row, rgb[j]);
         }
-        if (lane == 0) {
+        if (sl.sl == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
           dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
           dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -535,7 +540,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint2*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);

@@ -226,3 +226,33 @@ def test_training_gains_over_untrained_and_frozen_grid():
     print("held-out PSNR: initial %.2f, frozen grid %.2f, trained %.2f" % (init, frozen, trained))
     assert trained > init + 6.0
     assert trained > frozen + 1.0
+
+
+def test_render_bwd_in_paired_slots_matches_oracle():
+    """16 samples per ray: every chunk has at most 16 samples, so chunks share
+    warps pairwise (half-warp render adjoints). The FP32 gradient still
+    matches the oracle's within the FP32 bound."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8", L=8, log2_T=12, S=16)
+    t, m = H.params(w)
+    o, d = sy.workload_rays(w, 1024, seed=77)
+    R = len(o)
+    g = sy.rng(78, "misc")
+    adj = {"rgb": g.standard_normal((R, 3)), "depth": g.standard_normal(R), "opacity": g.standard_normal(R),
+           "dist": g.standard_normal(R)}
+    of = H.oracle_field(w, t, m)
+    gt_ref, gm_ref = oracle.render_grad(of, w.S, o, d, adj["rgb"], adj["depth"], adj["opacity"], adj["dist"])
+    gf = H.gpu_field(w, t, m)
+    samp = H.sampling(w)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    n_samples, n_chunks = api.workspace_stats(ws)
+    assert 0 < n_samples <= 16 * n_chunks
+    dev = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(adj["rgb"]), dev(adj["depth"]), dev(adj["opacity"]),
+                            dev(adj["dist"]))
+    api.check(ws)
+    okt, et = grad_close(gt.cpu().numpy(), gt_ref)
+    okm, em = grad_close(gm.cpu().numpy(), gm_ref)
+    assert okt and okm, (et, em)

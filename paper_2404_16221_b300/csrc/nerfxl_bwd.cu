@@ -116,7 +116,7 @@ struct BwdParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;
-  const uint4* chunks;  // slots
+  const Slot* chunks;  // slots
   const int32_t* n_tiles;
   const float4* dpart;   // chunk partial adjoints
   float* grad_tables;    // [K][E][2] accumulated
@@ -205,14 +205,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
     }
     const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
     const uint2 ref = sl.ref;
-    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
+    const bool chunk_ok = sl.slot_ok;  // warp-uniform; lanes of an unused part of the slot are empty samples
     bool valid = false;
     float feat[kIn], u[3];
     float tr = 0.0f, dl = 0.0f;
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
 #pragma unroll
     for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
-    if (chunk_ok) {
+    if (sl.has) {
       const uint32_t ray = ref.x;
       const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
       const RayHdr h = p.hdr[ray];
@@ -516,14 +516,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
     }
     const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
     const uint2 ref = sl.ref;
-    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
+    const bool chunk_ok = sl.slot_ok;  // warp-uniform; lanes of an unused part of the slot are empty samples
     bool valid = false;
     float feat[kIn], u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
     float tr = 0.0f, dl = 0.0f;
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
 #pragma unroll
     for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
-    if (chunk_ok) {
+    if (sl.has) {
       const uint32_t ray = ref.x;
       const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
       const RayHdr h = p.hdr[ray];
@@ -874,7 +874,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.dpart = dpart;
   p.grad_tables = grad_tables;

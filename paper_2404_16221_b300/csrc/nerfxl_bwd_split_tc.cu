@@ -71,7 +71,7 @@ constexpr uint32_t oWc1t = oWd1t + 32 * 128;  // B of dXc: 32 rows (in) x 64 (ou
 constexpr uint32_t oX1 = oWc1t + 32 * 128;    // SW64 [128][32]: features, record stage 1
 // Geometry + chunk adjoints of record stages 0, 1 (the bulk copies' images).
 constexpr uint32_t kGeoBytesS = 4 * kGeomFloats;
-constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 8 * 16;  // + 8 chunk positions (2 per slot) x 2 float4
+constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 16 * 16;  // + 16 chunk positions (4 per slot) x 2 float4
 constexpr uint32_t oGeoS = oX1 + 8192;
 constexpr uint32_t kStageTxS = 8192 + kGeoStageS;  // bytes per stage fill
 constexpr uint32_t oMiscS = (oGeoS + 2 * kGeoStageS + 63) / 64 * 64;  // mbarriers, tmem slot (40 B)
@@ -90,7 +90,7 @@ struct BwdSplitTcParams {
   const int32_t* n_tiles;
   const uint4* rec_feat;    // per tile: the 128 x 32 feature tile, 64-byte swizzled
   const float* rec_geom;    // per tile: rows u0 u1 u2 tr dl d0 d1 d2 (of kGeomRowFields), chunk counts
-  const float4* rec_dpart;  // per tile: 8 chunk positions (2 per slot) x 2 partial adjoints
+  const float4* rec_dpart;  // per tile: 16 chunk positions (4 per slot) x 2 partial adjoints
   float* grad_tables;
   float* grad_mlp;
   int32_t* err;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     const uint64_t pol = tc::policy_evict_first();  // read once: keep the gradient lines in L2
     tc::bulk_g2s_hint(sb + (s ? oX1 : oX), p.rec_feat + (size_t)t * (kRecFeatBytes / 16), 8192, full + s, pol);
     tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeomFloats, kGeoBytesS, full + s, pol);
-    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 16, 256, full + s, pol);
+    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 32, 512, full + s, pol);
     (s ? pend1 : pend0) = it;
   };
   if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     if (g == 0) {
       tr = geo[3 * kRecRows + row];
       dl = geo[4 * kRecRows + row];
-      if (chunk_ok) {
-        const float4 a0 = dps[2 * (2 * q + sc.half)], a1 = dps[2 * (2 * q + sc.half) + 1];
+      if (chunk_ok && sc.n > 0) {  // (an unused part of the slot keeps zero adjoints)
+        const float4 a0 = dps[2 * (4 * q + sc.part)], a1 = dps[2 * (4 * q + sc.part) + 1];
         gtc = a0.x;
         gC[0] = a0.y;
         gC[1] = a0.z;

@@ -85,7 +85,7 @@ constexpr uint32_t oXs = oGO + kTileBytes;
 constexpr uint32_t kXBytes = (uint32_t)kRecFeatBytes;
 constexpr uint32_t oGeo = oXs + 2 * kXBytes;
 constexpr uint32_t kGeoBytes = 4 * kGeomFloats;
-constexpr uint32_t kGeoStage = kGeoBytes + 2 * 8 * 16;  // + 8 chunk positions (2 per slot) x 2 float4
+constexpr uint32_t kGeoStage = kGeoBytes + 2 * 16 * 16;  // + 16 chunk positions (4 per slot) x 2 float4
 constexpr uint32_t kStageTx = kXBytes + kGeoStage;      // bytes per stage fill
 // Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][128 rows]
 // (row-contiguous, so both roles access it without bank conflicts), u as
@@ -108,7 +108,7 @@ struct BwdTcParams {
   const int32_t* n_tiles;
   const char* rec_feat;   // kRecFeatBytes per tile
   const char* rec_geom;   // kGeomFloats floats per tile
-  const char* rec_dpart;  // 8 chunk positions x 2 float4 per tile
+  const char* rec_dpart;  // 16 chunk positions x 2 float4 per tile
   float* grad_tables;     // FP32 [K][E][2]
   float* grad_mlp;        // FP32 [K][kMlpParams]
   int32_t* err;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       const uint64_t pol = tc::policy_evict_first();
       tc::bulk_g2s_hint(sb + oXs + (uint32_t)s * kXBytes, p.rec_feat + (size_t)t * kXBytes, kXBytes, full + s, pol);
       tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeoBytes, kGeoBytes, full + s, pol);
-      tc::bulk_g2s_hint(geo + kGeoBytes, p.rec_dpart + (size_t)t * 256, 256, full + s, pol);
+      tc::bulk_g2s_hint(geo + kGeoBytes, p.rec_dpart + (size_t)t * 512, 512, full + s, pol);
       pend[s] = it;
     };
     if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
@@ -393,10 +393,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       //      samples outside the chunks
       if (g == 0 && staged) {
         float go[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (nword != 0) {  // (warp-uniform: a slot is empty or all its chunks are not)
-          const char* ap = gst + kGeoBytes + 32 * (2 * q + sc.half);
-          const float4 a0 = *reinterpret_cast<const float4*>(ap);
-          const float4 a1 = *reinterpret_cast<const float4*>(ap + 16);
+        if (nword != 0) {  // (warp-uniform; an unused part of the slot has n = 0 and zero adjoints)
+          const char* ap = gst + kGeoBytes + 32 * (4 * q + sc.part);
+          const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          const float4 a0 = sc.n ? *reinterpret_cast<const float4*>(ap) : z;
+          const float4 a1 = sc.n ? *reinterpret_cast<const float4*>(ap + 16) : z;
           const float tr = geo[3 * kRows + row], dl = geo[4 * kRows + row];
           const float Tn = geo[5 * kRows + row], w = geo[6 * kRows + row], pair = geo[7 * kRows + row];
           const float sigma = geo[8 * kRows + row];

@@ -31,51 +31,72 @@ constexpr int kMlpParams = kIn * kWidth + kWidth * kWidth + kWidth * kOut;
 constexpr int kChunksPerTile = 8;
 
 // A chunk is up to 32 consecutive samples of one ray segment, the unit of the
-// local render. A slot is the 32 rows (one warp) a chunk is evaluated in: it
-// holds one chunk (lane = sample), or two chunks of at most 16 samples each
-// (a segment's tail or a short segment) in lanes 0-15 and 16-31. Slot layout
-// {ray A, seg A << 16 | chunk A, ray B, seg B << 16 | chunk B}; ray B =
-// kEmptyChunk when the slot holds one chunk, ray A = kEmptyChunk when it is
-// padding.
-constexpr int kHalfChunk = 16;
+// local render. A slot is the 32 rows (one warp) chunks are evaluated in: one
+// chunk (width 32, lane = sample), two chunks of at most 16 samples (width 16:
+// lanes 0-15 and 16-31) or four of at most 8 (width 8) - segment tails and
+// short segments. A slot is four references {ray, seg << 16 | chunk}; the
+// unused references of a narrow slot hold kUnusedPart, a padding slot holds
+// kEmptyChunk everywhere, and a slot's width is 8 if its third reference is
+// not kEmptyChunk, else 16 if its second is not, else 32.
+constexpr uint32_t kUnusedPart = 0xFFFFFFFEu;
 
-struct SlotLane {
-  uint2 ref;  // the lane's chunk {ray, seg << 16 | chunk}; ref.x == kEmptyChunk: none
-  int width;  // lanes of the lane's chunk: 32, or 16 in a shared slot
-  int sl;     // the lane's sample index within its chunk
+struct Slot {
+  uint4 a, b;  // references 0, 1 and 2, 3
 };
 
-__device__ __forceinline__ SlotLane slot_lane(const uint4 s, int lane) {
-  const bool shared = s.z != kEmptyChunk;
-  const bool hi = shared && lane >= kHalfChunk;
+struct SlotLane {
+  uint2 ref;     // the lane's chunk {ray, seg << 16 | chunk}
+  bool slot_ok;  // the slot is not padding (warp-uniform)
+  bool has;      // the lane's part of the slot holds a chunk
+  int width;     // lanes per chunk in this slot: 32, 16 or 8
+  int sl;        // the lane's sample index within its chunk
+  int part;      // which chunk of the slot: lane / width
+};
+
+__device__ __forceinline__ SlotLane slot_lane(const Slot& s, int lane) {
   SlotLane o;
-  o.ref = hi ? make_uint2(s.z, s.w) : make_uint2(s.x, s.y);
-  o.width = shared ? kHalfChunk : 32;
-  o.sl = shared ? (lane & (kHalfChunk - 1)) : lane;
+  o.width = s.b.x != kEmptyChunk ? 8 : (s.a.z != kEmptyChunk ? 16 : 32);
+  o.part = lane / o.width;
+  o.sl = lane % o.width;
+  o.ref = o.part == 0 ? make_uint2(s.a.x, s.a.y)
+                      : (o.part == 1 ? make_uint2(s.a.z, s.a.w) : (o.part == 2 ? make_uint2(s.b.x, s.b.y)
+                                                                             : make_uint2(s.b.z, s.b.w)));
+  o.slot_ok = s.a.x != kEmptyChunk;
+  o.has = o.ref.x < kUnusedPart;
   return o;
 }
 
 // A slot's sample counts as the tensor-core records keep them (one int32:
-// n | 0, or nA | nB << 8 | 1 << 16 for two half-slot chunks), resolved for a
-// lane: its chunk's count, width, the lane's index in it and which half.
+// 6 bits per chunk, chunk p at bit 6 p, the width code at bit 24: 0 for 32,
+// 1 for 16, 2 for 8), resolved for a lane: its chunk's count, width, index
+// in it and part. 0 is an empty slot.
 struct SlotCount {
-  int n, width, sl, half;
+  int n, width, sl, part;
 };
 
+__device__ __forceinline__ int32_t slot_count_word(int width, const int n[4]) {
+  const int code = width == 32 ? 0 : (width == 16 ? 1 : 2);
+  return n[0] | (n[1] << 6) | (n[2] << 12) | (n[3] << 18) | (code << 24);
+}
+
 __device__ __forceinline__ SlotCount slot_count(int32_t word, int lane) {
-  const bool shared = (word >> 16) & 1;
-  const bool hi = shared && lane >= kHalfChunk;
   SlotCount o;
-  o.n = hi ? (word >> 8) & 0xFF : word & 0xFF;
-  o.width = shared ? kHalfChunk : 32;
-  o.sl = shared ? (lane & (kHalfChunk - 1)) : lane;
-  o.half = hi ? 1 : 0;
+  o.width = 32 >> ((word >> 24) & 3);
+  o.part = lane / o.width;
+  o.sl = lane % o.width;
+  o.n = (word >> (6 * o.part)) & 63;
   return o;
 }
 
-// Chunks of a segment of n samples, and whether its last one fits half a slot.
+// Chunks of a segment of n samples, and the width its last chunk takes in a
+// slot: 8 for at most 8 samples, 16 for at most 16, else 32 (also for an
+// emptied segment, which has no chunk).
 __device__ __forceinline__ int seg_chunks(int n) { return (n + 31) / 32; }
-__device__ __forceinline__ bool seg_half_tail(int n) { return n > 0 && n - 32 * ((n - 1) / 32) <= kHalfChunk; }
+__device__ __forceinline__ int seg_tail_width(int n) {
+  if (n <= 0) return 32;
+  const int tail = n - 32 * ((n - 1) / 32);
+  return tail <= 8 ? 8 : (tail <= 16 ? 16 : 32);
+}
 
 // Error flags written into the workspace header.
 constexpr int kErrOverflow = 1;
@@ -283,7 +304,7 @@ __device__ __forceinline__ int region_of_chunk(const int32_t* base, int K, int c
 
 // Sums and scans over segments of `width` lanes (32 or 16; every lane of the
 // warp takes part); `lane` is the index within the segment. With width 16 the
-// two half-warps are independent, and a chunk's results equal those over 32
+// half-warps (with 8, the quarter-warps) are independent, and a chunk's results equal those over 32
 // lanes with zeros after it, bit for bit (the extra steps add zeros).
 __device__ __forceinline__ float warp_sum(float v, int width = 32) {
 #pragma unroll

@@ -40,10 +40,10 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
                                                   int32_t* __restrict__ counts, int32_t* __restrict__ err) {
   extern __shared__ float s_mem[];
   float* s_boxes = s_mem;                                 // [K][6]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [2][K]: chunks, half-slot chunks
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [3][K]: chunks, of them width 16, width 8
   __shared__ unsigned long long s_samples, s_chunks;
   for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) s_cnt[i] = 0;
   if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
   __syncthreads();
 
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
       const int nch = seg_chunks(n);
       if (counts) {
         atomicAdd(&s_cnt[sreg[k]], nch);
-        if (seg_half_tail(n)) atomicAdd(&s_cnt[K + sreg[k]], 1);
+        const int tw = seg_tail_width(n);
+        if (tw < kWarp) atomicAdd(&s_cnt[(tw == 16 ? K : 2 * K) + sreg[k]], 1);
       }
       cbase += nch;
       n_samples += n;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(256) k_segments(const float* __restrict__ rays
   }
   __syncthreads();
   if (!counts) return;  // the occupancy pass buckets the kept samples
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
   if (threadIdx.x == 0) {
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
@@ -126,15 +127,15 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
                                                     int32_t* __restrict__ err) {
   extern __shared__ float s_mem[];
   float* s_boxes = s_mem;                                      // [K][6]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [2][K]: chunks, half-slot chunks
-  float* s_inv = s_mem + 8 * K;                                // [K][3] 1 / box extent
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_mem + 6 * K);  // [3][K]: chunks, of them width 16, width 8
+  float* s_inv = s_mem + 9 * K;                                // [K][3] 1 / box extent
   __shared__ unsigned long long s_samples, s_chunks;
   for (int i = threadIdx.x; i < 6 * K; i += blockDim.x) s_boxes[i] = boxes[i];
   for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) {
     const int k = i / 3, ax = i % 3;
     s_inv[i] = __fdiv_rn(1.0f, __fsub_rn(boxes[6 * k + 3 + ax], boxes[6 * k + ax]));
   }
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) s_cnt[i] = 0;
   if (threadIdx.x == 0) s_samples = s_chunks = 0ull;
   __syncthreads();
 
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
       seg_keep[r * sp.max_seg + lane] = my_count | ((inc_c - my_count) << 16);
       segs[r * sp.max_seg + lane].reg_cb = (reg & 0xFFFF) | (cbase << 16);
       if (my_nch) atomicAdd(&s_cnt[reg], my_nch);
-      if (seg_half_tail(my_count)) atomicAdd(&s_cnt[K + reg], 1);
+      if (my_nch && seg_tail_width(my_count) < kWarp)
+        atomicAdd(&s_cnt[(seg_tail_width(my_count) == 16 ? K : 2 * K) + reg], 1);
     }
     const int nchunk = __shfl_sync(kFull, inc_h, kWarp - 1);
     if (lane == 0) {
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(&counts[i], s_cnt[i]);
   if (threadIdx.x == 0) {
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(err + 2);
@@ -268,11 +270,17 @@ __global__ void __launch_bounds__(256) k_skip_empty(const float* __restrict__ ra
 }
 
 // ---------------------------------------------------------------------------
-// k_region_scan: region k holds counts[k] chunks, counts[K + k] of them of at
-// most 16 samples; its slots are one per longer chunk, then one per pair of
-// short ones: slots_k = counts[k] - counts[K + k] + ceil(counts[K + k] / 2).
-// base[k] = sum_{k' < k} round_up(slots_k', tile); padding slots and the free
-// half of an odd last pair get the empty marker; header word 1 = total tiles.
+// k_region_scan: region k holds counts[k] chunks, counts[K + k] of them of
+// width 16 (at most 16 samples) and counts[2K + k] of width 8 (at most 8); its
+// slots are one per wider chunk, then one per pair of width-16 chunks, then
+// one per four of width 8: full_k + ceil(h_k / 2) + ceil(q_k / 4).
+// base[k] = sum_{k' < k} round_up(slots_k', tile); padding slots get the
+// empty marker, the free parts of the last pair / quad the unused marker;
+// header word 1 = total tiles.
+
+__device__ __forceinline__ void set_ref(uint2* chunks, int64_t slot, int part, uint32_t x) {
+  chunks[4 * slot + part] = make_uint2(x, 0u);
+}
 
 __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chunks_per_tile,
                               int32_t* __restrict__ base, uint2* __restrict__ chunks, int32_t* __restrict__ n_tiles) {
@@ -280,14 +288,14 @@ __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chu
   int32_t acc = 0;
   for (int k = 0; k < K; ++k) {
     base[k] = acc;
-    const int h = counts[K + k];
-    const int slots = counts[k] - h + (h + 1) / 2;
+    const int h = counts[K + k], qn = counts[2 * K + k];
+    const int full = counts[k] - h - qn, hs = (h + 1) / 2, qs = (qn + 3) / 4;
+    const int slots = full + hs + qs;
     const int padded = (slots + chunks_per_tile - 1) / chunks_per_tile * chunks_per_tile;
-    if (h & 1) chunks[2 * (acc + slots - 1) + 1] = make_uint2(kEmptyChunk, 0u);
-    for (int i = slots; i < padded; ++i) {
-      chunks[2 * (acc + i)] = make_uint2(kEmptyChunk, 0u);
-      chunks[2 * (acc + i) + 1] = make_uint2(kEmptyChunk, 0u);
-    }
+    if (h & 1) set_ref(chunks, acc + full + hs - 1, 1, kUnusedPart);
+    for (int p = qn & 3; p > 0 && p < 4; ++p) set_ref(chunks, acc + full + hs + qs - 1, p, kUnusedPart);
+    for (int i = slots; i < padded; ++i)
+      for (int p = 0; p < 4; ++p) set_ref(chunks, acc + i, p, kEmptyChunk);
     acc += padded;
   }
   base[K] = acc;
@@ -296,9 +304,9 @@ __global__ void k_region_scan(const int32_t* __restrict__ counts, int K, int chu
 
 // ---------------------------------------------------------------------------
 // k_fill_chunks: chunk references {ray, seg << 16 | chunk-in-segment} into
-// the region's slots (chunks = uint2 [slots][2]): a chunk of more than 16
-// samples fills a slot alone, a segment's last chunk of at most 16 takes the
-// next free half of the region's paired slots.
+// the region's slots (chunks = uint2 [slots][4]): a chunk of more than 16
+// samples fills a slot alone; a segment's last chunk of at most 16 (8) takes
+// the next free half (quarter) of the region's width-16 (width-8) slots.
 
 __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParams sp, const RayHdr* __restrict__ hdr,
                                                      const SegDesc* __restrict__ segs,
@@ -306,42 +314,55 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
                                                      const int32_t* __restrict__ base, int32_t* __restrict__ cursor,
                                                      uint2* __restrict__ chunks) {
   extern __shared__ int32_t s_i[];
-  int32_t* s_cnt = s_i;  // [2][K]: this block's whole-slot chunks, half-slot chunks
-  int32_t* s_base = s_i + 2 * K;  // [2][K]: their first index in the region
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_cnt[i] = 0;
+  int32_t* s_cnt = s_i;           // [3][K]: this block's whole-slot, width-16 and width-8 chunks
+  int32_t* s_base = s_i + 3 * K;  // [3][K]: their first index in the region
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int nseg = 0;
-  int off[kMaxSeg], hoff[kMaxSeg];
+  int off[kMaxSeg], toff[kMaxSeg];
   if (r < R) {
     nseg = hdr[r].nseg;
     for (int k = 0; k < nseg; ++k) {
       const SegDesc s = segs[r * sp.max_seg + k];
       const int n = seg_samples(sp, s, r, k).n;
-      const bool half = seg_half_tail(n);
-      off[k] = atomicAdd(&s_cnt[seg_region(s)], seg_chunks(n) - (half ? 1 : 0));
-      hoff[k] = half ? atomicAdd(&s_cnt[K + seg_region(s)], 1) : 0;
+      const int tw = seg_tail_width(n);
+      off[k] = atomicAdd(&s_cnt[seg_region(s)], seg_chunks(n) - (tw < kWarp ? 1 : 0));
+      toff[k] = tw < kWarp ? atomicAdd(&s_cnt[(tw == 16 ? K : 2 * K) + seg_region(s)], 1) : 0;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) s_base[i] = s_cnt[i] ? atomicAdd(&cursor[i], s_cnt[i]) : 0;
+  for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) s_base[i] = s_cnt[i] ? atomicAdd(&cursor[i], s_cnt[i]) : 0;
   __syncthreads();
   for (int k = 0; k < nseg; ++k) {
     const SegDesc s = segs[r * sp.max_seg + k];
     const int reg = seg_region(s);
     const int n = seg_samples(sp, s, r, k).n;
     const int nch = seg_chunks(n);
-    const bool half = seg_half_tail(n);
-    const int nfull = nch - (half ? 1 : 0);
+    const int tw = seg_tail_width(n);
+    const int nfull = nch - (tw < kWarp ? 1 : 0);
     const int dst = base[reg] + s_base[reg] + off[k];
     for (int c = 0; c < nfull; ++c) {
-      chunks[2 * (dst + c)] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
-      chunks[2 * (dst + c) + 1] = make_uint2(kEmptyChunk, 0u);
+      chunks[4 * (int64_t)(dst + c)] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | c));
+      for (int p = 1; p < 4; ++p) set_ref(chunks, dst + c, p, kEmptyChunk);
     }
-    if (half) {
-      const int h = s_base[K + reg] + hoff[k];  // index among the region's short chunks
-      const int slot = base[reg] + (counts[reg] - counts[K + reg]) + (h >> 1);
-      chunks[2 * slot + (h & 1)] = make_uint2((uint32_t)r, (uint32_t)((k << 16) | (nch - 1)));
+    if (tw < kWarp) {
+      const int h = counts[K + reg], qn = counts[2 * K + reg];
+      const int full = counts[reg] - h - qn;
+      const uint2 ref = make_uint2((uint32_t)r, (uint32_t)((k << 16) | (nch - 1)));
+      if (tw == 16) {
+        const int i = s_base[K + reg] + toff[k];  // index among the region's width-16 chunks
+        const int64_t slot = base[reg] + full + (i >> 1);
+        chunks[4 * slot + (i & 1)] = ref;
+        if ((i & 1) == 0) {  // a width-16 slot's references 2, 3 stay empty
+          set_ref(chunks, slot, 2, kEmptyChunk);
+          set_ref(chunks, slot, 3, kEmptyChunk);
+        }
+      } else {
+        const int i = s_base[2 * K + reg] + toff[k];  // index among the region's width-8 chunks
+        const int64_t slot = base[reg] + full + (h + 1) / 2 + (i >> 2);
+        chunks[4 * slot + (i & 3)] = ref;
+      }
     }
   }
 }
@@ -363,7 +384,7 @@ struct FwdParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;     // [K+1]
-  const uint4* chunks;     // slots
+  const Slot* chunks;      // slots
   const int32_t* n_tiles;
   float4* partials;        // [R][max_chunk][2]
   float4* smp4;            // per sample slot: sigma, rgb (sample-level composition), or NULL
@@ -401,21 +422,29 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
     }
     const SlotLane sl = slot_lane(p.chunks[chunk], lane);
-    if (sl.ref.x == kEmptyChunk) continue;  // warp-uniform (padding)
+    if (!sl.slot_ok) continue;  // warp-uniform (padding)
+    // lanes of an unused part of a narrow slot take part in the scans as empty samples
     const uint2 ref = sl.ref;
-    const uint32_t ray = ref.x;
+    const uint32_t ray = sl.has ? ref.x : 0u;
     const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
-    const RayHdr h = p.hdr[ray];
-    const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
-    float o[3], d[3];
+    RayHdr h = {0.0f, 0.0f, 0, 0};
+    SegDesc sd = {0.0f, 0.0f, 0, 0};
+    float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 0.0f};
+    bool valid = false;
+    int i = 0;
+    SegSamples ss = {0, 0};
+    if (sl.has) {
+      h = p.hdr[ray];
+      sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      o[ax] = p.rays_o[3 * (size_t)ray + ax];
-      d[ax] = p.rays_d[3 * (size_t)ray + ax];
+      for (int ax = 0; ax < 3; ++ax) {
+        o[ax] = p.rays_o[3 * (size_t)ray + ax];
+        d[ax] = p.rays_d[3 * (size_t)ray + ax];
+      }
+      ss = seg_samples(p.sp, sd, ray, seg);
+      i = c * kWarp + sl.sl;
+      valid = i < ss.n;
     }
-    const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-    const int i = c * kWarp + sl.sl;
-    const bool valid = i < ss.n;
     float feat[kIn];
     float tbar = 0.0f, dl = 0.0f;
     if (valid) {
@@ -448,16 +477,18 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     const float tr = valid ? __fsub_rn(tbar, h.tn) : 0.0f;
     const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
     if (p.smp4) {  // sample-level composition: every sample leaves the kernel
-      p.smp4[slot * kWarp + sl.sl] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
-      p.smp2[slot * kWarp + sl.sl] = make_float2(tr, dl);
-      if (sl.width < kWarp) {  // a half-slot chunk: its sample slots 16..31 are empty
-        p.smp4[slot * kWarp + kHalfChunk + sl.sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        p.smp2[slot * kWarp + kHalfChunk + sl.sl] = make_float2(0.0f, 0.0f);
+      if (sl.has) {
+        p.smp4[slot * kWarp + sl.sl] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+        p.smp2[slot * kWarp + sl.sl] = make_float2(tr, dl);
+        for (int j = sl.width + sl.sl; j < kWarp; j += sl.width) {  // a narrow chunk's other sample slots
+          p.smp4[slot * kWarp + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          p.smp2[slot * kWarp + j] = make_float2(0.0f, 0.0f);
+        }
       }
       continue;
     }
     const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl, nullptr, 0, sl.width);
-    if (sl.sl == 0) {
+    if (sl.has && sl.sl == 0) {
       float4* dst = p.partials + 2 * slot;
       dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
       dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -625,8 +656,8 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     return at;
   };
   L.hdr = take(sizeof(int32_t) * 16);
-  L.counts = take(sizeof(int32_t) * 2 * K);  // chunks per region, then those of at most 16 samples
-  L.cursor = take(sizeof(int32_t) * 2 * K);
+  L.counts = take(sizeof(int32_t) * 3 * K);  // chunks per region, then those of width 16, width 8
+  L.cursor = take(sizeof(int32_t) * 3 * K);
   L.zero_end = off;
   L.base = take(sizeof(int32_t) * (K + 1));
   L.ray_hdr = take(sizeof(RayHdr) * R);
@@ -638,7 +669,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.kept = take(sizeof(uint16_t) * R * L.max_int);
   }
   L.chunk_cap = (int64_t)R * mc + (int64_t)kChunksPerTile * K;
-  L.chunks = take(sizeof(uint4) * L.chunk_cap);  // slots (at most one per chunk)
+  L.chunks = take(sizeof(Slot) * L.chunk_cap);  // slots (at most one per chunk)
   L.partials = take(sizeof(float4) * 2 * R * mc);
   L.dpartials = for_backward ? take(sizeof(float4) * 2 * R * mc) : 0;
   L.rec_feat = L.rec_geom = L.rec_dpart = L.rec_pos = 0;
@@ -647,7 +678,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.rec_tiles = (L.chunk_cap + 3) / 4;
     L.rec_feat = take(kRecFeatBytes * L.rec_tiles);
     L.rec_geom = take(sizeof(float) * kGeomFloats * L.rec_tiles);
-    L.rec_dpart = take(sizeof(float4) * 2 * 8 * L.rec_tiles);
+    L.rec_dpart = take(sizeof(float4) * 2 * 16 * L.rec_tiles);
     L.rec_pos = take(sizeof(int32_t) * R * mc);
   }
   L.smp4 = L.smp2 = 0;
@@ -744,7 +775,7 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
   const int threads = 256;
   const int blocks = (int)((R + threads - 1) / threads);
   if (R > 0) {
-    const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * 2 * K;
+    const size_t smem = sizeof(float) * 6 * K + sizeof(int32_t) * 3 * K;
     int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
     k_segments<<<blocks, threads, smem, stream>>>(rays_o, rays_d, R, f->boxes, K, sp,
                                                   reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
@@ -770,7 +801,7 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
   nerfxl_status st = launch_check("k_region_scan");
   if (st != NERFXL_OK) return st;
   if (R > 0) {
-    k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 4 * K, stream>>>(
+    k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 6 * K, stream>>>(
         R, K, sp, reinterpret_cast<RayHdr*>(ws + L.ray_hdr), reinterpret_cast<SegDesc*>(ws + L.segs),
         reinterpret_cast<int32_t*>(ws + L.counts), reinterpret_cast<int32_t*>(ws + L.base),
         reinterpret_cast<int32_t*>(ws + L.cursor), reinterpret_cast<uint2*>(ws + L.chunks));
@@ -893,7 +924,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   const bool per_sample = (s->flags & NERFXL_SAMPLE_COMPOSITE) != 0;

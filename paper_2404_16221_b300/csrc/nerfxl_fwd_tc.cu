@@ -211,7 +211,7 @@ struct FwdTcParams {
   const RayHdr* hdr;
   const SegDesc* segs;
   const int32_t* base;
-  const uint4* chunks;  // slots
+  const Slot* chunks;  // slots
   const int32_t* n_tiles;  // tiles of kChunksPerTile chunks
   float4* partials;
   RecordOut rec;  // the backward's per-tile records, or all NULL
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     // ---- gather: the four threads of a row each gather four levels
     const SlotLane sl = slot_lane(p.chunks[t * kTcChunks + q], lane);
     const uint2 ref = sl.ref;
-    const bool chunk_ok = ref.x != kEmptyChunk;  // warp-uniform
+    const bool chunk_ok = sl.slot_ok;  // warp-uniform; lanes of an unused part of the slot are empty samples
     bool valid = false;
     float tr = 0.0f, dl = 0.0f, u[3] = {0.0f, 0.0f, 0.0f};
     float f8[8];
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
     int c = 0, seg_count = 0;
     uint32_t ray = 0;
     float dir[3] = {0.0f, 0.0f, 0.0f};  // the ray's direction (the split form's colour input)
-    if (chunk_ok) {
+    if (sl.has) {
       ray = ref.x;
       const int seg = ref.y >> 16;
       c = ref.y & 0xFFFF;
@@ -336,15 +336,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       }
       if (g == 0) {
         __stcs(geo + 4 * kTcRows + row, dl);
-        // the slot's counts: n(chunk A) | n(chunk B) << 8 | shared << 16
-        const int n_mine = chunk_ok ? min(kWarp, seg_count - c * kWarp) : 0;
-        const int n_hi = __shfl_sync(0xFFFFFFFFu, n_mine, kHalfChunk);
+        // the slot's sample counts, one per part (see slot_count)
+        const int n_mine = sl.has ? min(kWarp, seg_count - c * kWarp) : 0;
+        int n4[4];
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) n4[pp] = __shfl_sync(0xFFFFFFFFu, n_mine, (pp * sl.width) & (kWarp - 1));
+        if (sl.width == kWarp) n4[1] = n4[2] = n4[3] = 0;
+        else if (sl.width == 16) n4[2] = n4[3] = 0;
         if (lane == 0)
-          reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] =
-              sl.width < kWarp ? (n_mine | (n_hi << 8) | (1 << 16)) : n_mine;
-        if (chunk_ok && sl.sl == 0)  // tile-order position of the chunk's adjoints: 2 per slot
-          p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] =
-              2 * (t * kTcChunks + q) + (lane >= kHalfChunk ? 1 : 0);
+          reinterpret_cast<int32_t*>(geo)[kGeomRowFields * kTcRows + q] = chunk_ok ? slot_count_word(sl.width, n4) : 0;
+        if (sl.has && sl.sl == 0)  // tile-order position of the chunk's adjoints: 4 per slot
+          p.rec.pos[(size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c] = 4 * (t * kTcChunks + q) + sl.part;
       }
     }
     if constexpr (kSplit) {
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
             for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-v[j]));
           }
           const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl, nullptr, kTcRows, sl.width);
-          if (sl.sl == 0) {
+          if (sl.has && sl.sl == 0) {
             float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
             dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
             dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 #pragma unroll
           for (int j = 0; j < 3; ++j) __stcs(geo + (9 + j) * kTcRows + row, rgb[j]);
         }
-        if (sl.sl == 0) {
+        if (sl.has && sl.sl == 0) {
           float4* dst = p.partials + 2 * ((size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c);
           dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
           dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
@@ -540,7 +542,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.hdr = reinterpret_cast<const RayHdr*>(ws + L.ray_hdr);
   p.segs = reinterpret_cast<const SegDesc*>(ws + L.segs);
   p.base = reinterpret_cast<const int32_t*>(ws + L.base);
-  p.chunks = reinterpret_cast<const uint4*>(ws + L.chunks);
+  p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);

@@ -21,7 +21,7 @@ struct Layout {
   // Occupancy skipping (fields with an occupancy grid; 0 otherwise):
   size_t seg_keep;   // int32[R][max_seg]: kept samples | first list slot << 16
   size_t kept;       // uint16[R][max_int]: kept interval indices within their segment
-  size_t chunks;     // uint4[chunk_cap]: chunk slots (one or two chunks each; see slot_lane)
+  size_t chunks;     // Slot[chunk_cap]: chunk slots (one, two or four chunks each; see slot_lane)
   size_t partials;   // float4[R][max_chunk][2]
   size_t dpartials;  // float4[R][max_chunk][2] (backward workspaces only)
   // Per-tile records of the tensor-core backward (backward workspaces with a
@@ -29,7 +29,7 @@ struct Layout {
   size_t rec_feat;   // [tiles][128 rows][64 B]: 16-bit features, 64-byte-swizzled MMA tile
   size_t rec_geom;   // float[tiles][kGeomFloats]: per row u0 u1 u2 tr dl, then Tn w pair sigma rgb
                      // (fused) or the ray direction d0 d1 d2 (split); chunk counts
-  size_t rec_dpart;  // float4[tiles * 8][2]: chunk adjoints in tile order (2 positions per slot)
+  size_t rec_dpart;  // float4[tiles * 16][2]: chunk adjoints in tile order (4 positions per slot)
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
   // Sample-level composition (NERFXL_SAMPLE_COMPOSITE; 0 otherwise):
   size_t smp4;       // float4[R][max_chunk][32]: sigma, r, g, b per sample slot
@@ -70,8 +70,8 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
 //             dl (interval length), Tn (transmittance after the sample within its
 //             chunk), w (chunk-local weight), pair (sum over the chunk of
 //             w_j |tr_i - tr_j|), sigma, r, g, b (the MLP outputs after exp /
-//             sigmoid); then per slot (int32) the sample count of its chunk, or of
-//             its two half-slot chunks as nA | nB << 8 | 1 << 16. The
+//             sigmoid); then per slot (int32) the sample counts of its chunks and
+//             its width (slot_count_word). The
 //             split representation's backward recomputes its two MLPs and the
 //             render quantities; its rows 5..7 hold the ray direction instead
 //             (the colour MLP's SH input) and rows 8..11 are unused.

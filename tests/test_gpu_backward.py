@@ -230,7 +230,7 @@ def test_training_gains_over_untrained_and_frozen_grid():
 
 def test_render_bwd_in_paired_slots_matches_oracle():
     """16 samples per ray: every chunk has at most 16 samples, so chunks share
-    warps pairwise (half-warp render adjoints). The FP32 gradient still
+    warps by twos or fours (half- and quarter-warp render adjoints). The FP32 gradient still
     matches the oracle's within the FP32 bound."""
     from paper_2404_16221_b300 import api
 

@@ -302,10 +302,10 @@ __device__ __forceinline__ int region_of_chunk(const int32_t* base, int K, int c
 // ---------------------------------------------------------------------------
 // Warp scans and reductions.
 
-// Sums and scans over segments of `width` lanes (32 or 16; every lane of the
-// warp takes part); `lane` is the index within the segment. With width 16 the
-// half-warps (with 8, the quarter-warps) are independent, and a chunk's results equal those over 32
-// lanes with zeros after it, bit for bit (the extra steps add zeros).
+// Sums and scans over segments of `width` lanes (32, 16 or 8; every lane of
+// the warp takes part); `lane` is the index within the segment. With a width
+// below 32 the segments are independent, and a chunk's results equal those
+// over 32 lanes with zeros after it, bit for bit (the extra steps add zeros).
 __device__ __forceinline__ float warp_sum(float v, int width = 32) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)

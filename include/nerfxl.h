@@ -345,7 +345,7 @@ nerfxl_status nerfxl_region_chunks(const void* workspace, size_t ws_bytes, int32
  * outputs and results as nerfxl_render_fwd; the scratch comes from a fixed
  * 32 MiB array in the library's device image, reserved on every GPU that
  * loads the library until exit. Batches needing more scratch are refused
- * with NERFXL_E_WORKSPACE (grid8-sized rays: roughly 80 thousand per call).
+ * with NERFXL_E_WORKSPACE (grid8-sized rays: roughly 60 thousand per call).
  * The first call on a device looks up the array's address; make it before
  * any stream capture. Calls share the array: calls that overlap on the GPU
  * race, so order them on one stream. Allocates nothing.

@@ -156,7 +156,12 @@ __device__ void load_color_bwd(const void* blk, char* sm) {
   }
 }
 
-// Table gradient of level l of one sample (F = 2): entry += corner weight * (g0, g1).
+// Table gradient of level l of one sample (F = 2): entry += corner weight *
+// (g0, g1) at its 8 corners. The corners of an x-pair (x, x+1) go out as one
+// 16-byte reduction on the aligned entry pair holding the first corner (zero
+// in the other half unless the second corner is that pair's other entry)
+// plus, when it is not, one 8-byte reduction; the dense and hashed index forms
+// are both formed and selected per corner pair (no branch on the level).
 __device__ __forceinline__ void scatter_one(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l,
                                             float g0, float g1) {
   int c[3];
@@ -164,22 +169,26 @@ __device__ __forceinline__ void scatter_one(const LevelParams& lp, float2* __res
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
   float2* gl = gtab + lp.off[l];
+  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+  const float wx0 = 1.0f - f[0], wx1 = f[0];
+  const bool dense = (lp.dense_mask >> l) & 1u;
+  const LevelIndex<true> dix(lp, l, c[1], c[2]);
+  const LevelIndex<false> hix(lp, l, c[1], c[2]);
+  const uint32_t x0 = (uint32_t)c[0];
+  const uint64_t pol = tc::policy_evict_last();  // the region's gradient lines stay in L2 while its tiles run
 #pragma unroll
-  for (int e = 0; e < 8; e += 2) {
-    const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-    const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-    const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-    const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-    const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
-    if ((i0 ^ i1) == 1u) {
-      const bool odd = i0 & 1u;
-      const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
-                           : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
-      atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
-    } else {
-      atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
-      atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
-    }
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t i0 = dense ? dix(x0, e) : hix(x0, e);
+    const uint32_t i1 = dense ? i0 + 1u : hix(x0 + 1u, e);
+    const float wyz = wy[e & 1] * wz[e >> 1];
+    const float w0 = wx0 * wyz, w1 = wx1 * wyz;
+    const float a0 = w0 * g0, a1 = w0 * g1, b0 = w1 * g0, b1 = w1 * g1;
+    const bool pair = (i0 ^ i1) == 1u;
+    const bool odd = i0 & 1u;
+    const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
+    tc::red_add_v4(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
+                   odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1), pol);
+    if (!pair) tc::red_add_v2(gl + i1, make_float2(b0, b1), pol);
   }
 }
 

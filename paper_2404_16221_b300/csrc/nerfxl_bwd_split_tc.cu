@@ -1,6 +1,6 @@
 // Backward of the split representation on the tensor cores (16-bit MLPs,
 // FP32 accumulation in tensor memory). One CTA of 16 warps per SM takes
-// 128-row tiles (4 chunks of one region); warp w serves rows 32 (w % 4) + lane
+// 128-row tiles (4 chunk slots of one region); warp w serves rows 32 (w % 4) + lane
 // (its TMEM lane quarter) and column / level group w / 4. Per tile:
 //   records   written by the forward for this tile: X exactly as its first
 //             MMA read it; per row the region coordinates, interval and ray
@@ -11,7 +11,8 @@
 //   density   D = X Wd1 -> H1 = relu; G = H1 Wd2 (N = 16)
 //   colour    Xc = [G | SH(d)]; D = Xc Wc1 -> Hc1; D = Hc1 Wc2 -> Hc2; o = Hc2 Wc3
 //   adjoint   sigma = exp(G0), rgb = sigmoid(o); chunk-local render adjoint
-//             (one warp per chunk) -> dL/d(colour logits) goC, dL/dG0
+//             (one warp per slot, scans segmented per chunk) -> dL/d(colour
+//             logits) goC, dL/dG0
 //   colour    Gz2 = (Hc2 > 0) (goC Wc3^T); Gz1 = (Hc1 > 0) (Gz2 Wc2^T);
 //             dG = (Gz1 Wc1^T)[0..15] + dL/dG0 e0
 //   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T -> table scatter-add,
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
       failed = true;
       break;
     }
-    // ---- chunk-local render adjoint (warp g == 0 of each lane quarter = one chunk)
+    // ---- chunk-local render adjoint (warp g == 0 of each lane quarter = one slot)
     float go_d = 0.0f;
     if (g == 0) {
       tc::tmem_ld16(tq + kDS, v);

@@ -14,7 +14,7 @@
 // One CTA per SM, 16 warps in two roles. The table-gradient scatter is bound
 // by the SM's throughput for scattered vector atomics (about one address per
 // clock), so it runs concurrently with the MMA pipeline instead of after it:
-//   compute warps 0-7   one 128-row tile (4 chunks of one region) at a time;
+//   compute warps 0-7   one 128-row tile (4 chunk slots of one region) at a time;
 //                       warp w serves TMEM lane quarter q = w % 4 (rows
 //                       32q..32q+31) and column half / level half g = w / 4
 //   scatter warps 8-15  scatter the previous tile's dL/dfeatures, handed over

@@ -2,8 +2,9 @@
 // tensor memory): the mixed-precision forms (BF16 or FP16 MLP with FP32
 // accumulation; FP32 or FP16 hash features).
 //
-// One CTA = 16 warps on one 128-row MMA tile (4 chunks of 32 samples, all of
-// one region). Warp w serves rows 32 (w % 4) .. + 31 (its TMEM lane quarter)
+// One CTA = 16 warps on one 128-row MMA tile (4 slots of 32 rows, each one
+// chunk of up to 32 samples or two or four shorter ones, all of one region).
+// Warp w serves rows 32 (w % 4) .. + 31 (its TMEM lane quarter)
 // and level group / column block w / 4, so each sample's 16-level gather is
 // spread over four threads that run concurrently. Per tile:
 //   gather   thread (row, g) encodes levels 4g..4g+3 and writes their eight
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       break;
     }
     tc::fence_after_sync();
-    // ---- chunk render by the warps of level group 0 (one chunk per warp)
+    // ---- chunk render by the warps of level group 0 (one slot per warp, scans segmented per chunk)
     if (g == 0) {
       tc::tmem_ld16(tmem_q, v);
       tc::tmem_ld_wait();

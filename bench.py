@@ -253,10 +253,10 @@ SPLIT_BWD_FLOP = 3 * SPLIT_FWD_FLOP
 # of the FP32 gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
 TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 8 * 4 + 1 + 2 * 8 * 2 * 4 * 16
 # DRAM bytes (read + write) of one k_field_bwd_tc launch on this workload, from
-# one ncu capture of the kernel as it stands (dram__bytes_read.sum 4.510 GB +
-# dram__bytes_write.sum 4.105 GB, one-pass metrics on the full workload);
+# one ncu capture of the kernel as it stands (dram__bytes_read.sum 5.138 GB +
+# dram__bytes_write.sum 4.361 GB, one-pass metrics on the full workload);
 # re-capture when the kernel changes.
-BWD_TC_DRAM_BYTES = 4.509654e9 + 4.105237e9
+BWD_TC_DRAM_BYTES = 5.137525e9 + 4.360513e9
 
 
 def serve_sweep(args, dev, rates):
@@ -642,7 +642,7 @@ def main():
                      "binding_resource": "latency of the compute warps' per-tile chain (four MMA round trips "
                                          "and their epilogues, one tile in flight per SM): 10.1 ms alone, "
                                          "~17 ms beside the scatter warps, which share the SM's issue slots "
-                                         "and load/store pipe; not HBM (DRAM traffic 0.14x the algorithmic "
+                                         "and load/store pipe; not HBM (DRAM traffic 0.15x the algorithmic "
                                          "bytes, the swept region stays in L2) and not the atomics' request "
                                          "count (a copy summing same-cell runs first, 37% fewer requests, "
                                          "ran 3% slower)"},

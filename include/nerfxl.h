@@ -139,7 +139,7 @@ typedef struct nerfxl_sampling {
 /*
  * Training with a 16-bit MLP: the forward writes the tensor-core backward's
  * per-tile records (the 16-bit encoded features, sample geometry and the
- * chunk-render values its adjoint reuses: 97 bytes per sample slot) into a
+ * chunk-render values its adjoint reuses: about 116 bytes per sample row) into a
  * backward-sized workspace. Without the flag nerfxl_render_bwd rebuilds them
  * with one more forward pass first.
  */

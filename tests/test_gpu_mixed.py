@@ -114,13 +114,17 @@ def _mixed_backward(w, t, m, tab, mlp, n=1024, seed=21):
     return gt.cpu().numpy(), gm.cpu().numpy(), gt_ref, gm_ref
 
 
+@pytest.mark.parametrize("S", [None, 16])
 @pytest.mark.parametrize("tab,mlp", [(torch.float16, torch.bfloat16), (torch.float32, torch.float16)])
-def test_mixed_backward_structure_matches_oracle(tab, mlp):
+def test_mixed_backward_structure_matches_oracle(tab, mlp, S):
     """Tensor-core backward against the oracle on a network without ReLU
     kinks (positive features and hidden weights, so every pre-activation is
     well above zero): the 16-bit activations then only perturb values, by
-    ~1e-3, and any wrong index, transpose or dropped term shows as O(1)."""
-    w = H.workload("grid8", L=16, log2_T=14)
+    ~1e-3, and any wrong index, transpose or dropped term shows as O(1).
+    With 16 samples per ray every chunk has at most 16 samples, so the
+    records, chunk adjoints and render adjoint all run in slots shared by
+    two or four chunks."""
+    w = H.workload("grid8", L=16, log2_T=14, S=S)
     E = oracle.table_entries(w.level_res, w.log2_T)
     P = oracle.mlp_params(w.mlp_in, w.W)
     g = sy.rng(22, "misc")

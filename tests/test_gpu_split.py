@@ -189,8 +189,8 @@ def test_split_tensor_core_forward_matches_oracle(tab, mlp, name, n):
     assert e_rgb <= 2e-3 and e_op <= 2e-3
 
 
-@pytest.mark.parametrize("name", ["grid8", "city32"])
-def test_split_mixed_backward_matches_oracle(name):
+@pytest.mark.parametrize("name,S", [("grid8", None), ("city32", None), ("grid8", 16)])
+def test_split_mixed_backward_matches_oracle(name, S):
     """FP16 tables + BF16 MLPs: forward and backward on the tensor cores.
     Against the oracle on the rounded parameters, on the kink-free network
     (positive features and hidden weights): no entry off by more than 1e-2
@@ -198,7 +198,7 @@ def test_split_mixed_backward_matches_oracle(name):
     values; measured 1.1e-3 for the tables, 2.2e-4 for the MLPs)."""
     from paper_2404_16221_b300 import api, native as N
 
-    w = H.workload(name, L=16, log2_T=14)
+    w = H.workload(name, L=16, log2_T=14, S=S)  # S = 16: every chunk shares its slot
     E = oracle.table_entries(w.level_res, w.log2_T)
     Pd, Pc = oracle.density_params(w.mlp_in, w.W), oracle.color_params(w.W)
     g = sy.rng(24, "misc")

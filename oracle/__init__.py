@@ -98,6 +98,8 @@ def lib():
                                   C.c_double, C.c_double]
         L.oracle_blob_render.argtypes = [fp, sp, C.c_int64, _f32p, _f32p, C.c_int64, _f64p, _f64p, _f64p, _f64p]
         L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.oracle_relu_margin.argtypes = [fp, sp, C.c_int64, _f32p, _f32p, _f64p]
+        L.oracle_camera_rays.argtypes = [_f32p, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _f32p, _f32p]
         L.oracle_occupancy_update.argtypes = [fp, C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_double, _f64p,
                                               _u32p, C.c_void_p]
         _lib = L
@@ -411,3 +413,31 @@ def occupancy_update(field: Field, G: int, step: int, seed: int, decay: float, t
     lib().oracle_occupancy_update(C.byref(fs), int(G), int(step), int(seed), float(decay), float(threshold), density,
                                   bits, None if pts is None else pts.ctypes.data)
     return (bits, pts) if want_points else bits
+
+
+def relu_margin(field: Field, S: int, o, d):
+    """Per ray, the smallest distance of any evaluated sample's hidden unit
+    from its ReLU kink, relative to the scale that unit's rounding error
+    grows with (see relu_margin_sample in the C source); +inf for a ray
+    without evaluated samples. A test diagnostic: rays whose margin is within
+    a few orders of magnitude of the FP32 unit roundoff may take the other
+    ReLU decision in FP32."""
+    o, d = _rays(o, d)
+    out = np.zeros(o.shape[0])
+    fs = field.struct()
+    lib().oracle_relu_margin(C.byref(fs), C.byref(_samp(S)), o.shape[0], o, d, out)
+    return out
+
+
+def camera_rays(origin, right, up, forward, tan_half_fov: float, width: int, height: int, first: int = 0,
+                count: int | None = None):
+    """Pinhole rays of pixels first..first+count-1 (row-major) in the
+    prescribed FP32 operation order; returns (o, d) [count][3] float32."""
+    cam = np.concatenate([np.asarray(v, np.float32).reshape(3) for v in (origin, right, up, forward)] +
+                         [np.asarray([tan_half_fov], np.float32)])
+    cam = np.ascontiguousarray(cam, dtype=np.float32)
+    count = int(width) * int(height) - int(first) if count is None else int(count)
+    o = np.zeros((count, 3), np.float32)
+    d = np.zeros((count, 3), np.float32)
+    lib().oracle_camera_rays(cam, int(width), int(height), int(first), count, o, d)
+    return o, d

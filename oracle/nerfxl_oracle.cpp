@@ -45,6 +45,11 @@
 //     and its bit is set where the estimate exceeds a threshold. The points
 //     come from Philox4x32-10 (Salmon et al., SC 2011), written out below from
 //     its published definition.
+//   * Test diagnostics, not part of the method: the distance of each sample's
+//     hidden units from their ReLU kinks relative to their rounding-error
+//     scale (which rays an FP32 gradient may legitimately see on the other
+//     side of a kink), and the pinhole rays of a render request in a
+//     prescribed FP32 operation order (the rays a served image is checked on).
 //
 // Parity status: every function here is pinned by CPU tests (closed forms,
 // brute force, library GEMMs, finite differences); none is "parity unpinned".
@@ -859,6 +864,103 @@ void cell_point(int64_t cell, int region, int32_t G, const int32_t* c3, int64_t 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Distance of a sample's hidden units from their ReLU kinks (a diagnostic for
+// the gradient tests, not part of the method). A unit's pre-activation z is
+// compared with the scale its rounding error grows with: the sum of the
+// magnitudes of the products that form it, where each input carries its own
+// scale forward (running error analysis: an input h computed from products of
+// total magnitude s may be off by a multiple of s, not of |h|). For the fused
+// MLP
+//   s1_n = sum_i |feat_i W1_in|,   s2_m = sum_n |W2_nm| (h1_n + s1_n);
+// for the split representation
+//   s1_n = sum_i |feat_i Wd1_in|,  sg_m = sum_n |Wd2_nm| (h1_n + s1_n),
+//   s2_n = sum_{m<16} |Wc1_mn| (|g_m| + sg_m) + sum_{m>=16} |Wc1_mn SH_m|,
+//   s3_n = sum_i |Wc2_in| (h2_i + s2_i).
+// The margin of a sample is min over units of |z| / s (a unit with s = 0 has
+// z = 0 in any precision and counts as infinitely far).
+double relu_margin_sample(const oracle_field& f, int region, const double* feat, const float* dir) {
+  const int W = f.W, I = f.mlp_in;
+  double best = INFINITY;
+  auto take = [&](double z, double sc) {
+    if (sc > 0.0) best = std::min(best, std::fabs(z) / sc);
+  };
+  if (f.arch == 1) {
+    const double* Wd1 = f.mlp + int64_t(region) * density_params(I, W);
+    const double* Wd2 = Wd1 + int64_t(I) * W;
+    const double* Wc1 = f.mlp + int64_t(f.K) * density_params(I, W);
+    const double* Wc2 = Wc1 + int64_t(kGeo + kSh) * W;
+    std::vector<double> h1(W), s1(W), g(kGeo), sg(kGeo), h2(W), s2(W);
+    for (int n = 0; n < W; ++n) {
+      double z = 0.0, sc = 0.0;
+      for (int i = 0; i < I; ++i) {
+        z += feat[i] * Wd1[i * W + n];
+        sc += std::fabs(feat[i] * Wd1[i * W + n]);
+      }
+      take(z, sc);
+      h1[n] = z > 0.0 ? z : 0.0;
+      s1[n] = sc;
+    }
+    for (int m = 0; m < kGeo; ++m) {
+      double z = 0.0, sc = 0.0;
+      for (int n = 0; n < W; ++n) {
+        z += h1[n] * Wd2[n * kGeo + m];
+        sc += std::fabs(Wd2[n * kGeo + m]) * (h1[n] + s1[n]);
+      }
+      g[m] = z;
+      sg[m] = sc;
+    }
+    double sh[kSh];
+    const double dd[3] = {(double)dir[0], (double)dir[1], (double)dir[2]};
+    sh4(dd, sh);
+    for (int n = 0; n < W; ++n) {
+      double z = 0.0, sc = 0.0;
+      for (int m = 0; m < kGeo; ++m) {
+        z += g[m] * Wc1[m * W + n];
+        sc += std::fabs(Wc1[m * W + n]) * (std::fabs(g[m]) + sg[m]);
+      }
+      for (int m = 0; m < kSh; ++m) {
+        z += sh[m] * Wc1[(kGeo + m) * W + n];
+        sc += std::fabs(sh[m] * Wc1[(kGeo + m) * W + n]);
+      }
+      take(z, sc);
+      h2[n] = z > 0.0 ? z : 0.0;
+      s2[n] = sc;
+    }
+    for (int n = 0; n < W; ++n) {
+      double z = 0.0, sc = 0.0;
+      for (int i = 0; i < W; ++i) {
+        z += h2[i] * Wc2[i * W + n];
+        sc += std::fabs(Wc2[i * W + n]) * (h2[i] + s2[i]);
+      }
+      take(z, sc);
+    }
+    return best;
+  }
+  const double* W1 = f.mlp + int64_t(region) * mlp_params(I, W);
+  const double* W2 = W1 + int64_t(I) * W;
+  std::vector<double> h1(W), s1(W);
+  for (int n = 0; n < W; ++n) {
+    double z = 0.0, sc = 0.0;
+    for (int i = 0; i < I; ++i) {
+      z += feat[i] * W1[i * W + n];
+      sc += std::fabs(feat[i] * W1[i * W + n]);
+    }
+    take(z, sc);
+    h1[n] = z > 0.0 ? z : 0.0;
+    s1[n] = sc;
+  }
+  for (int m = 0; m < W; ++m) {
+    double z = 0.0, sc = 0.0;
+    for (int n = 0; n < W; ++n) {
+      z += h1[n] * W2[n * W + m];
+      sc += std::fabs(W2[n * W + m]) * (h1[n] + s1[n]);
+    }
+    take(z, sc);
+  }
+  return best;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1165,6 +1267,59 @@ void oracle_occupancy_update(const oracle_field* f, int32_t G, int64_t step, uin
   });
   for (int64_t i = 0; i < int64_t(f->K) * cells; ++i)
     if (on[size_t(i)]) bits[(i / cells) * words + (i % cells) / 32] |= 1u << ((i % cells) % 32);
+}
+
+
+// Smallest ReLU margin (relu_margin_sample) over each ray's evaluated samples:
+// margin [R], +inf for a ray without evaluated samples.
+void oracle_relu_margin(const oracle_field* f, const oracle_sampling* s, int64_t R, const float* ro, const float* rd,
+                        double* margin) {
+  const std::vector<Level> lv = make_levels(f->L, f->level_res, f->log2_T);
+  parallel_for(R, [&](int64_t r, int) {
+    const float* o = ro + 3 * r;
+    const float* d = rd + 3 * r;
+    RayEval re;
+    eval_ray(*f, *s, lv, o, d, true, &re);
+    double best = INFINITY;
+    for (size_t i = 0; i < re.iv.size(); ++i) {
+      if (re.skip[i]) continue;
+      best = std::min(best, relu_margin_sample(*f, re.iv[i].region, re.enc[i].feat.data(), d));
+    }
+    margin[r] = best;
+  });
+}
+
+// Pinhole camera rays (the rays a render request asks for). cam = {origin[3],
+// right[3], up[3], forward[3], tan_half_fov} as float32, the frame orthonormal;
+// pixel p = i W + j (row i from the top, column j), p in [first, first +
+// count). Prescribed FP32 operation sequence, one IEEE rounding per operation
+// and no fused multiply-add (the GPU follows the same sequence, so the rays
+// agree bit for bit):
+//   aspect = W / H
+//   x = ((((j + 0.5) / W) * 2 - 1) * tan) * aspect
+//   y = (1 - ((i + 0.5) / H) * 2) * tan
+//   v_a = (x right_a + y up_a) + forward_a
+//   n = sqrt((v_0 v_0 + v_1 v_1) + v_2 v_2),   d_a = v_a / n,   o = origin.
+void oracle_camera_rays(const float* cam, int32_t W, int32_t H, int64_t first, int64_t count, float* ro, float* rd) {
+  const float* org = cam;
+  const float* right = cam + 3;
+  const float* up = cam + 6;
+  const float* fwd = cam + 9;
+  const float tan_h = cam[12];
+  const float aspect = (float)W / (float)H;
+  for (int64_t k = 0; k < count; ++k) {
+    const int64_t p = first + k;
+    const int32_t i = (int32_t)(p / W), j = (int32_t)(p % W);
+    const float x = ((((float)j + 0.5f) / (float)W) * 2.0f - 1.0f) * tan_h * aspect;
+    const float y = (1.0f - (((float)i + 0.5f) / (float)H) * 2.0f) * tan_h;
+    float v[3];
+    for (int a = 0; a < 3; ++a) v[a] = (x * right[a] + y * up[a]) + fwd[a];
+    const float n = std::sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    for (int a = 0; a < 3; ++a) {
+      ro[3 * k + a] = org[a];
+      rd[3 * k + a] = v[a] / n;
+    }
+  }
 }
 
 }  // extern "C"

@@ -16,8 +16,15 @@
 
 namespace nerfxl {
 
-// Pixel (i, j) of camera c: x = ((j + 0.5) / W * 2 - 1) * tan * W / H,
-// y = (1 - (i + 0.5) / H * 2) * tan, d = normalize(x right + y up + forward).
+// Pixel p = i W + j (row i from the top, column j) of camera c, in a
+// prescribed FP32 operation sequence with one IEEE rounding per operation and
+// no fused multiply-add, so that any implementation of the same sequence gives
+// the same rays bit for bit:
+//   aspect = W / H
+//   x = ((((j + 0.5) / W) * 2 - 1) * tan) * aspect
+//   y = (1 - ((i + 0.5) / H) * 2) * tan
+//   v_a = (x right_a + y up_a) + forward_a
+//   n = sqrt((v_0 v_0 + v_1 v_1) + v_2 v_2),   d_a = v_a / n,   o = origin.
 // A ray outside its item, its camera's image, or the camera list is rendered
 // as a miss and gets output slot -1 (the composite skips it).
 __global__ void __launch_bounds__(256) k_gen_rays(int64_t R, int n_items, const nerfxl_ray_item* __restrict__ items,
@@ -44,23 +51,26 @@ __global__ void __launch_bounds__(256) k_gen_rays(int64_t R, int n_items, const 
       rays_o[3 * r + a] = miss_o[a];
       rays_d[3 * r + a] = a == 0 ? 1.0f : 0.0f;
     }
-    out_index[r] = -1;
+    if (out_index) out_index[r] = -1;
     return;
   }
   const int i = (int)(pix / cam.width), j = (int)(pix % cam.width);
-  const float aspect = (float)cam.width / (float)cam.height;
-  const float x = (((float)j + 0.5f) / (float)cam.width * 2.0f - 1.0f) * cam.tan_half_fov * aspect;
-  const float y = (1.0f - ((float)i + 0.5f) / (float)cam.height * 2.0f) * cam.tan_half_fov;
-  float d[3];
+  const float Wf = (float)cam.width, Hf = (float)cam.height, tanh_ = cam.tan_half_fov;
+  const float aspect = __fdiv_rn(Wf, Hf);
+  const float x =
+      __fmul_rn(__fmul_rn(__fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn((float)j, 0.5f), Wf), 2.0f), 1.0f), tanh_), aspect);
+  const float y = __fmul_rn(__fsub_rn(1.0f, __fmul_rn(__fdiv_rn(__fadd_rn((float)i, 0.5f), Hf), 2.0f)), tanh_);
+  float v[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) d[a] = x * cam.right[a] + y * cam.up[a] + cam.forward[a];
-  const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int a = 0; a < 3; ++a)
+    v[a] = __fadd_rn(__fadd_rn(__fmul_rn(x, cam.right[a]), __fmul_rn(y, cam.up[a])), cam.forward[a]);
+  const float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2])));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     rays_o[3 * r + a] = cam.origin[a];
-    rays_d[3 * r + a] = d[a] * inv;
+    rays_d[3 * r + a] = __fdiv_rn(v[a], n);
   }
-  out_index[r] = it.out_offset + local;
+  if (out_index) out_index[r] = it.out_offset + local;
 }
 
 }  // namespace nerfxl
@@ -95,10 +105,21 @@ nerfxl_status nerfxl_render_cameras(const nerfxl_field* f, const nerfxl_sampling
   int64_t* out_index = reinterpret_cast<int64_t*>(rays_d + 3 * (size_t)n_rays);
   k_gen_rays<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, n_items, items, cams, n_cams, rays_o, rays_d,
                                                               out_index);
-  st = launch_check("k_gen_rays");
+  st = kernel_launched("k_gen_rays");
   if (st != NERFXL_OK) return st;
   return render_fwd_impl(f, s, n_rays, rays_o, rays_d, rgb, depth, opacity, nullptr, out_index, workspace, L.total,
                          stream);
+}
+
+nerfxl_status nerfxl_debug_camera_rays(int64_t n_rays, int32_t n_items, const nerfxl_ray_item* items,
+                                       const nerfxl_camera* cams, int32_t n_cams, float* rays_o, float* rays_d,
+                                       cudaStream_t stream) {
+  if (n_rays < 0 || (n_rays > 0 && (n_items < 1 || n_cams < 1 || !items || !cams || !rays_o || !rays_d)))
+    return set_error(NERFXL_E_INVALID, "bad camera ray arguments");
+  if (n_rays == 0) return NERFXL_OK;
+  k_gen_rays<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, n_items, items, cams, n_cams, rays_o, rays_d,
+                                                              nullptr);
+  return kernel_launched("k_gen_rays");
 }
 
 }  // extern "C"

@@ -99,18 +99,22 @@ def camera_desc(req: Request) -> N.CameraDesc:
     return c
 
 
-def camera_rays(req: Request):
-    """Host copy of the rays nerfxl_render_cameras generates for a request
-    (same formula; used to check a served image against a plain render)."""
-    c = camera_desc(req)
-    r, u, f = (np.array(list(v), np.float32) for v in (c.right, c.up, c.forward))
-    js, is_ = np.meshgrid(np.arange(req.width, dtype=np.float32), np.arange(req.height, dtype=np.float32))
-    x = ((js + 0.5) / req.width * 2 - 1) * np.float32(c.tan_half_fov) * np.float32(req.width / req.height)
-    y = (1 - (is_ + 0.5) / req.height * 2) * np.float32(c.tan_half_fov)
-    d = x[..., None] * r + y[..., None] * u + f
-    d = (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3).astype(np.float32)
-    o = np.broadcast_to(np.array(list(c.origin), np.float32), d.shape).copy()
-    return o, d
+def camera_rays(req: Request, device=None):
+    """The rays nerfxl_render_cameras renders for a request, generated by the
+    library's own ray generator (nerfxl_debug_camera_rays); returns host
+    (o, d) [H*W][3] float32. Used to check a served image against a plain
+    render of the same rays."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    n = req.pixels
+    cam = camera_desc(req)
+    item = N.RayItemDesc(0, 0, 0, 0, n)
+    cam_d = torch.frombuffer(bytearray(bytes(cam)), dtype=torch.uint8).to(dev)
+    item_d = torch.frombuffer(bytearray(bytes(item)), dtype=torch.uint8).to(dev)
+    o = torch.empty(n, 3, device=dev)
+    d = torch.empty(n, 3, device=dev)
+    N.check(N.lib().nerfxl_debug_camera_rays(n, 1, N._ptr(item_d), N._ptr(cam_d), 1, N._ptr(o), N._ptr(d),
+                                             N._stream(torch.cuda.current_stream(dev))), "nerfxl_debug_camera_rays")
+    return o.cpu().numpy(), d.cpu().numpy()
 
 
 class ServeEngine:

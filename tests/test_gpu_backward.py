@@ -1,8 +1,10 @@
 """Backward, loss, Adam and training through the C ABI, against the FP64 oracle.
 
-Gradients: |gpu - ref| <= 1e-4 * max|ref| per tensor (FP32 atomics reorder
-the sums). The oracle's own gradient is pinned to central differences by
-tests/test_oracle.py, so GPU == oracle == finite differences.
+Gradients: |gpu - ref| <= 1e-4 * max|ref| for every entry of every tensor
+(FP32 atomics reorder the sums), on rays the oracle finds clear of ReLU kinks
+at FP32 precision (helpers.kink_free). The oracle's own gradient is pinned to
+central differences by tests/test_oracle.py, so GPU == oracle == finite
+differences.
 """
 import numpy as np
 import pytest
@@ -25,34 +27,19 @@ def _cuda():
     build.build()
 
 
-def grad_err(g, ref):
-    g = np.asarray(g, np.float64)
-    ref = np.asarray(ref, np.float64)
-    return float(np.abs(g - ref).max() / max(np.abs(ref).max(), 1e-30))
-
-
-def grad_close(g, ref, tol=1e-4):
-    """FP32 gradient bound: |g - ref| <= tol * max|ref| per tensor.
-
-    A ReLU whose pre-activation lies within ~1e-7 of zero (relative) can take
-    opposite decisions in FP32 and FP64, and then the whole contribution of
-    that unit at that sample differs. Such kinks touch a tiny share of the
-    entries, so at most 0.1% of entries may exceed the bound, and none may
-    exceed 100x the bound. A wrong term, sign or index breaks both."""
-    g = np.asarray(g, np.float64).reshape(-1)
-    ref = np.asarray(ref, np.float64).reshape(-1)
-    scale = max(np.abs(ref).max(), 1e-30)
-    err = np.abs(g - ref) / scale
-    frac = float(np.mean(err > tol))
-    return frac <= 1e-3 and err.max() <= 100 * tol, (frac, float(err.max()))
+grad_close = H.grad_close
 
 
 def _case(name="grid8", n=1024, L=16, log2_T=14, S=None):
+    """n seeded rays of the workload, the kink-free ones kept (about 80%)."""
     w = H.workload(name, L=L, log2_T=log2_T, S=S)
     t, m = H.params(w)
     o, d = sy.workload_rays(w, 4096)
     sel = sy.subset(4096, n, 5)
-    return w, t, m, o[sel].copy(), d[sel].copy()
+    o, d = o[sel].copy(), d[sel].copy()
+    keep = H.kink_free(H.oracle_field(w, t, m), w.S, o, d)
+    assert keep.mean() > 0.6
+    return w, t, m, o[keep].copy(), d[keep].copy()
 
 
 @pytest.mark.parametrize("which", ["rgb", "depth", "opacity", "dist", "all"])
@@ -155,7 +142,7 @@ def test_training_step_matches_oracle():
     computed from the oracle's gradient."""
     from paper_2404_16221_b300 import api
 
-    w, t, m, o, d = _case(n=2048)
+    w, t, m, o, d = _case(n=2560)
     tgt = sy.rng(15, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
     gf = H.gpu_field(w, t, m)
     trainer = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
@@ -166,18 +153,9 @@ def test_training_step_matches_oracle():
     for g, ref in ((trainer.grad_tables, gt_ref), (trainer.grad_mlp, gm_ref)):
         ok, e = grad_close(g.cpu().numpy(), ref)
         assert ok, e
-    # The first Adam step moves each parameter by lr * g / (|g| + eps): by
-    # +-lr where the gradient is clearly non-zero, not at all where it is zero.
-    for new, old, gref in ((gf.tables, t, gt_ref), (gf.mlp, m, gm_ref)):
-        delta = new.cpu().numpy().astype(np.float64) - old
-        gref = gref.reshape(delta.shape)
-        big = np.abs(gref) > 1e-3 * np.abs(gref).max()
-        moved = np.abs(delta[big] + 1e-2 * np.sign(gref[big])) <= 1e-6 + 1e-4 * 1e-2
-        assert np.mean(moved) >= 0.999, np.mean(moved)
-        # untouched entries (no sample reads them) do not move
-        zero = gref == 0
-        if zero.any():
-            assert np.mean(delta[zero] != 0) < 1e-4
+    # the first Adam step, every entry
+    H.assert_first_adam_step(gf.tables.cpu().numpy(), t, gt_ref, 1e-2, 1e-4)
+    H.assert_first_adam_step(gf.mlp.cpu().numpy(), m, gm_ref, 1e-2, 1e-4)
 
 
 def _psnr(a, b):
@@ -237,6 +215,8 @@ def test_render_bwd_in_paired_slots_matches_oracle():
     w = H.workload("grid8", L=8, log2_T=12, S=16)
     t, m = H.params(w)
     o, d = sy.workload_rays(w, 1024, seed=77)
+    keep = H.kink_free(H.oracle_field(w, t, m), w.S, o, d)
+    o, d = o[keep].copy(), d[keep].copy()
     R = len(o)
     g = sy.rng(78, "misc")
     adj = {"rgb": g.standard_normal((R, 3)), "depth": g.standard_normal(R), "opacity": g.standard_normal(R),

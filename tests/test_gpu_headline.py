@@ -1,0 +1,85 @@
+"""The timed training call itself against the FP64 oracle.
+
+nerfxl_step exactly as the benchmark times it: grid8 at its full table size
+(K=8, L=16, T=2^19: five dense and eleven hashed levels per region), FP16
+tables, BF16 MLP on the tensor cores, the forward's NERFXL_SAVE_FEATURES
+records feeding the tensor-core backward, FP32 Adam masters refreshing the
+16-bit copies. On a network without ReLU kinks (16-bit activations cannot
+flip a decision there) every entry of the table and MLP gradients is held to
+1e-2 of max|ref| against the oracle's gradient on the rounded parameters
+(BF16 activations carry 2^-9 relative rounding through three layers), the
+loss to 2e-3, and every parameter's Adam update is checked entry by entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16221_b300 import synthetic as sy
+
+import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_16221_b300 import build
+
+    build.build()
+
+
+def _rounded(a, dtype):
+    return torch.from_numpy(a).to(dtype).float().numpy()
+
+
+@pytest.mark.parametrize("n_rays", [1536])
+def test_headline_training_step_matches_oracle(n_rays):
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("grid8")
+    assert w.log2_T == 19 and w.L == 16
+    t, m = H.kinkless_params(w, seed=81)
+    o, d = sy.workload_rays(w)
+    sel = sy.subset(len(o), n_rays, 82)
+    o, d = o[sel].copy(), d[sel].copy()
+    tgt = sy.rng(83, "misc").uniform(0, 1, (n_rays, 3)).astype(np.float32)
+    gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+    tr = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=t, master_mlp=m)
+    assert tr.samp.flags & api.SAVE_FEATURES
+    loss = tr.step(o, d, tgt).cpu().numpy()
+    torch.cuda.synchronize()
+    of = H.oracle_field(w, _rounded(t, torch.float16), _rounded(m, torch.bfloat16))
+    L_ref, gt_ref, gm_ref = oracle.loss_grad(of, w.S, o, d, tgt, 0.01)
+    print("headline step: loss %.6f oracle %.6f" % (loss[0], L_ref))
+    assert abs(loss[0] - L_ref) <= 2e-3 * L_ref
+    dense = [oracle.level_dense(w.level_res, w.log2_T, l) for l in range(w.L)]
+    assert sum(dense) == 5
+    for name, g, ref in (("tables", tr.grad_tables, gt_ref), ("mlp", tr.grad_mlp, gm_ref)):
+        g = g.cpu().numpy()
+        ok, e = H.grad_close(g, ref, TOL)
+        a, b = g.reshape(-1).astype(np.float64), ref.reshape(-1)
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        rel = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        print("headline step %s gradient: max err %.2e of max|ref|, cosine %.7f, relative L2 %.2e"
+              % (name, e, cos, rel))
+        assert ok, (name, e)
+        assert cos > 0.9999 and rel < 1e-2, (name, cos, rel)
+    # per level of the tables: the dense levels and the hashed ones each hold
+    # the bound on their own scale too
+    E = oracle.table_entries(w.level_res, w.log2_T)
+    gt = tr.grad_tables.cpu().numpy().reshape(w.K, E, 2)
+    for l in range(w.L):
+        lo = oracle.level_offset(w.level_res, w.log2_T, l)
+        hi = oracle.level_offset(w.level_res, w.log2_T, l + 1) if l + 1 < w.L else E
+        ok, e = H.grad_close(gt[:, lo:hi], gt_ref[:, lo:hi], 2 * TOL)
+        assert ok, ("level", l, dense[l], e)
+    # Adam on the FP32 masters, every entry; the 16-bit copies are the rounded masters
+    H.assert_first_adam_step(tr.tables.cpu().numpy(), t, gt_ref, 1e-2, TOL)
+    H.assert_first_adam_step(tr.mlp.cpu().numpy(), m, gm_ref, 1e-2, TOL)
+    assert torch.equal(gf.tables, tr.tables.to(torch.float16))
+    assert torch.equal(gf.mlp, tr.mlp.to(torch.bfloat16))

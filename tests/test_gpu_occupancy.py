@@ -107,8 +107,8 @@ def _grad_close(g, ref, tol):
 
 
 def test_sparse_grid_backward_matches_oracle():
-    """FP32 backward with skipping: gradients within 1e-4 of max|ref| (at most
-    0.1% of entries above, none above 100x), and exactly zero on the entries
+    """FP32 backward with skipping: every gradient entry within 1e-4 of
+    max|ref| on the rays clear of ReLU kinks, and exactly zero on the entries
     that only skipped samples read."""
     from paper_2404_16221_b300 import api
 
@@ -117,8 +117,10 @@ def test_sparse_grid_backward_matches_oracle():
     G = 16
     occ = _random_grid(w.K, G, 0.3, 45)
     o, d = sy.workload_rays(w, 4096)
-    sel = sy.subset(4096, 1024, 46)
+    sel = sy.subset(4096, 1280, 46)
     o, d = o[sel].copy(), d[sel].copy()
+    keep = H.kink_free(H.oracle_field(w, t, m).with_occupancy(occ, G), w.S, o, d)
+    o, d = o[keep].copy(), d[keep].copy()
     R = len(o)
     g = sy.rng(47, "misc")
     gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
@@ -131,8 +133,8 @@ def test_sparse_grid_backward_matches_oracle():
     of = H.oracle_field(w, t, m).with_occupancy(occ, G)
     gt_ref, gm_ref = oracle.render_grad(of, w.S, o, d, gC, gD, gA, gL)
     for a, b in ((gt.cpu().numpy(), gt_ref), (gm.cpu().numpy(), gm_ref)):
-        frac, emax = _grad_close(a, b, 1e-4)
-        assert frac <= 1e-3 and emax <= 1e-2, (frac, emax)
+        ok, emax = H.grad_close(a, b, 1e-4)
+        assert ok, emax
     gt_full, _ = oracle.render_grad(H.oracle_field(w, t, m), w.S, o, d, gC, gD, gA, gL)
     dead = (gt_ref.reshape(-1) == 0) & (gt_full.reshape(-1) != 0)
     assert dead.sum() > 1000 and not gt.cpu().numpy().reshape(-1)[dead].any()

@@ -40,11 +40,20 @@ def _split(name="grid8", L=16, log2_T=14, S=None):
     return w, t, m, of, gf
 
 
-def _grad_ok(g, ref, tol=1e-4):
-    g = np.asarray(g, np.float64).reshape(-1)
-    ref = np.asarray(ref, np.float64).reshape(-1)
-    err = np.abs(g - ref) / max(np.abs(ref).max(), 1e-30)
-    return float(np.mean(err > tol)) <= 1e-3 and err.max() <= 100 * tol, (float(np.mean(err > tol)), float(err.max()))
+_grad_ok = H.grad_close
+
+
+def _kink_free_rays(of, w, n, seed, pool=16384):
+    """Up to n seeded rays clear of ReLU kinks at FP32 precision. The split
+    representation stacks three hidden layers (density, two colour layers),
+    so only about one ray in ten qualifies; they are drawn from a larger
+    pool."""
+    o, d = sy.workload_rays(w, pool)
+    sel = sy.subset(pool, pool // 2, seed)
+    o, d = o[sel].copy(), d[sel].copy()
+    keep = np.nonzero(H.kink_free(of, w.S, o, d))[0][:n]
+    assert len(keep) >= min(n, 400), len(keep)
+    return o[keep].copy(), d[keep].copy()
 
 
 @pytest.mark.parametrize("name,n", [("grid8", 2048), ("city32", 1024), ("unit", 1024)])
@@ -86,9 +95,7 @@ def test_split_backward_matches_oracle():
     from paper_2404_16221_b300 import api
 
     w, t, m, of, gf = _split()
-    o, d = sy.workload_rays(w, 4096)
-    sel = sy.subset(4096, 1024, 62)
-    o, d = o[sel].copy(), d[sel].copy()
+    o, d = _kink_free_rays(of, w, 1024, 62)
     R = len(o)
     g = sy.rng(63, "misc")
     gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
@@ -113,9 +120,7 @@ def test_split_training_step_matches_oracle():
     from paper_2404_16221_b300 import api
 
     w, t, m, of, gf = _split()
-    o, d = sy.workload_rays(w, 4096)
-    sel = sy.subset(4096, 2048, 64)
-    o, d = o[sel].copy(), d[sel].copy()
+    o, d = _kink_free_rays(of, w, 1024, 64)
     tgt = sy.rng(65, "misc").uniform(0, 1, (len(o), 3)).astype(np.float32)
     trainer = api.Trainer(gf, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01)
     L = trainer.step(o, d, tgt).cpu().numpy()
@@ -124,9 +129,8 @@ def test_split_training_step_matches_oracle():
     for g, ref in ((trainer.grad_tables, gt_ref), (trainer.grad_mlp, gm_ref)):
         ok, e = _grad_ok(g.cpu().numpy(), ref)
         assert ok, e
-    delta = gf.mlp.cpu().numpy().astype(np.float64) - m
-    big = np.abs(gm_ref) > 1e-3 * np.abs(gm_ref).max()
-    assert np.mean(np.abs(delta[big] + 1e-2 * np.sign(gm_ref[big])) <= 2e-6) >= 0.999
+    H.assert_first_adam_step(gf.tables.cpu().numpy(), t, gt_ref, 1e-2, 1e-4)
+    H.assert_first_adam_step(gf.mlp.cpu().numpy(), m, gm_ref, 1e-2, 1e-4)
 
 
 def test_split_with_occupancy_and_refresh():

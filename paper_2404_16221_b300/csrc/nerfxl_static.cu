@@ -14,9 +14,14 @@
 //    library keeps it reserved until the process exits. Calls whose workspace
 //    would exceed it are refused with NERFXL_E_WORKSPACE before anything is
 //    launched; split such batches.
-//  - The first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture begins.
+//  - Every call looks up the array's device address (cudaGetSymbolAddress,
+//    which allocates nothing) with the caller's device current, so the address
+//    is never stale, even after a cudaDeviceReset reloaded the module. The
+//    first call on a device also loads the library's device code there; make
+//    it before any stream capture begins.
+//  - Device-side conditions (a ray crossing more regions than max_segments,
+//    an expired bounded wait) are flagged in the array's header; read them
+//    with nerfxl_static_check after the call.
 //  - All calls share the one array, and it keeps the previous call's
 //    contents: the call clears the counters it needs at zero itself. Calls
 //    that overlap on the GPU (different streams, or host threads without
@@ -25,7 +30,6 @@
 
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "nerfxl_host.h"
@@ -34,30 +38,18 @@ namespace nerfxl {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mutex;
-void* g_static_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; looked up once
-// per device. In host code g_static_scratch names a host-side stand-in, never
-// the device memory, so only the looked-up address is passed to kernels.
+// Device address of the scratch array on the current device. In host code
+// g_static_scratch names a host-side stand-in, never the device memory, so
+// only the looked-up address is passed to kernels.
 nerfxl_status static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(NERFXL_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(NERFXL_E_UNSUPPORTED, "device index beyond 64");
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(NERFXL_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(NERFXL_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return NERFXL_OK;
 }
 
@@ -80,4 +72,11 @@ extern "C" nerfxl_status nerfxl_render_fwd_static(const nerfxl_field* f, const n
   if (st != NERFXL_OK) return st;
   return nerfxl_render_fwd(f, s, n_rays, rays_o, rays_d, rgb, depth, opacity, dist, scratch, kStaticScratchBytes,
                            stream);
+}
+
+extern "C" nerfxl_status nerfxl_static_check(cudaStream_t stream) {
+  void* scratch = nullptr;
+  const nerfxl_status st = static_scratch(&scratch);
+  if (st != NERFXL_OK) return st;
+  return nerfxl_check(scratch, kStaticScratchBytes, stream);
 }

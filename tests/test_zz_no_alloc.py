@@ -45,7 +45,7 @@ def _static_call(field, samp, o, d):
 
 
 def test_static_scratch_matches_workspace_entry_point():
-    from paper_2404_16221_b300 import api
+    from paper_2404_16221_b300 import api, native as N
 
     w = H.workload("grid8")
     t, m = H.params(w)
@@ -60,8 +60,29 @@ def test_static_scratch_matches_workspace_entry_point():
         ref = api.render_fwd(field, samp, o_t, d_t)
         got = _static_call(field, samp, o_t, d_t)
         for k in ref:
-            # same kernels on the same inputs; the forward tolerance is 1e-5 relative
-            assert H.rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy(), 1.0) <= 1e-5, k
+            # the same kernels on the same inputs: the same bits
+            assert torch.equal(got[k], ref[k]), k
+        assert N.lib().nerfxl_static_check(N._stream(None)) == N.OK
+
+
+def test_static_scratch_reports_device_side_overflow():
+    """A ray crossing more regions than max_segments is flagged on the device;
+    the static caller reads that flag with nerfxl_static_check, and the next
+    call starts clean."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import native as N
+
+    w = H.workload("grid8", L=8, log2_T=14)
+    t, m = H.params(w)
+    field = H.gpu_field(w, t, m)
+    o, d = sy.workload_rays(w, 2048)
+    o_t, d_t = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    _static_call(field, dataclasses.replace(H.sampling(w), max_segments=1), o_t, d_t)
+    assert N.lib().nerfxl_static_check(N._stream(None)) == N.E_OVERFLOW
+    assert b"max_segments" in N.lib().nerfxl_last_error()
+    _static_call(field, H.sampling(w), o_t, d_t)
+    assert N.lib().nerfxl_static_check(N._stream(None)) == N.OK
 
 
 def test_static_scratch_refuses_oversized_batch():

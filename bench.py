@@ -138,15 +138,29 @@ def max_over_ranks(values, device=None):
     return [float(x) for x in t]
 
 
-def setup_workload(rank: int = 0):
-    from paper_2404_16221_b300 import native as N, synthetic as sy
+def setup_workload(rank: int = 0, sizes=None):
+    """The headline workload's field and rays. sizes(w) -> (E, P) gives the
+    table entries and MLP parameters per region; by default the library's
+    own layout functions (the reference arm passes the oracle's, so that it
+    never loads the library)."""
+    from paper_2404_16221_b300 import synthetic as sy
 
     w = sy.workload(WORKLOAD)
-    E = N.table_entries(w.level_res, w.log2_T)
-    P = N.mlp_params(w.mlp_in, w.W)
+    if sizes is None:
+        from paper_2404_16221_b300 import native as N
+
+        E, P = N.table_entries(w.level_res, w.log2_T), N.mlp_params(w.mlp_in, w.W)
+    else:
+        E, P = sizes(w)
     tables, mlp = sy.field_params(w, E, P)
     o, d = rank_rays(w, rank)
     return w, tables, mlp, o, d
+
+
+def oracle_sizes(w):
+    import oracle
+
+    return oracle.table_entries(w.level_res, w.log2_T), oracle.mlp_params(w.mlp_in, w.W)
 
 
 def cpu_baseline(w, tables, mlp, o, d, n_rays: int, batch: int = 2048):
@@ -185,22 +199,33 @@ def cpu_baseline(w, tables, mlp, o, d, n_rays: int, batch: int = 2048):
 
 
 def run_reference(args, rank, world):
+    """The oracle's training step on the host cores. Each step is a bounded
+    sample of the headline workload (cpu_rays / 8 of its rays, at least 256,
+    plus one FP64 Adam step over every parameter), timed as it runs; rays/s
+    is the sample's rays over the measured time of its ray part."""
     if rank != 0:
         return
-    w, tables, mlp, o, d = setup_workload()
+    w, tables, mlp, o, d = setup_workload(sizes=oracle_sizes)
+    n = max(256, args.cpu_rays // 8)
     for _ in range(max(0, args.warmup)):
         cpu_baseline(w, tables, mlp, o, d, 256)
-    vals = []
+    vals, secs = [], []
     for _ in range(args.steps):
-        cb = cpu_baseline(w, tables, mlp, o, d, max(256, args.cpu_rays // 8))
+        t0 = time.perf_counter()
+        cb = cpu_baseline(w, tables, mlp, o, d, n)
+        secs.append(time.perf_counter() - t0)
         vals.append(cb["value"])
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * (w.n_rays / v),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "grid8 training step (loss L2 + 0.01 distortion, gradient, Adam): K=8 2x2x2 over "
-                                   "[-1,1]^3, L=16 F=2 T=2^19 (16->2048), 2^18 rays from 64 cameras, S=128; per step "
-                                   "a bounded ray sample, rays/s extrapolated"},
+                                   "[-1,1]^3, L=16 F=2 T=2^19 (16->2048), 2^18 rays from 64 cameras, S=128. Each "
+                                   "timed step is a bounded sample: the FP64 loss and gradient of %d seeded rays "
+                                   "and one FP64 Adam step over all parameters; ms_per_step is that sample's "
+                                   "measured time, value = rays/s of the full 2^18-ray step extrapolated from "
+                                   "the sample's per-ray time plus the Adam time" % n,
+                       "rays_per_step": n},
             "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -248,15 +273,34 @@ BWD_FLOP_PER_SAMPLE = 3 * MLP_FWD_FLOP
 SPLIT_FWD_FLOP = 2 * (32 * 64 + 64 * 16) + 2 * (32 * 64 + 64 * 64 + 64 * 4)
 SPLIT_BWD_FLOP = 3 * SPLIT_FWD_FLOP
 # Algorithmic bytes of the tensor-core backward field kernel per sample (L=16
-# levels, F=2, 8 corners): its per-tile records (16-bit features 32 x 2 B,
-# geometry 8 x 4 B, chunk adjoints 32 B per 32 samples) and the read-modify-write
-# of the FP32 gradient entries the sample touches (2 x 8 x 2 x 4 B x 16 = 2048 B).
-TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 8 * 4 + 1 + 2 * 8 * 2 * 4 * 16
-# DRAM bytes (read + write) of one k_field_bwd_tc launch on this workload, from
-# one ncu capture of the kernel as it stands (dram__bytes_read.sum 5.138 GB +
-# dram__bytes_write.sum 4.361 GB, one-pass metrics on the full workload);
-# re-capture when the kernel changes.
-BWD_TC_DRAM_BYTES = 5.137525e9 + 4.360513e9
+# levels, F=2, 8 corners): its per-tile records (16-bit features 32 x 2 B, the
+# 12 geometry floats of a record row 48 B, chunk adjoints 32 B per 32 samples)
+# and the read-modify-write of the FP32 gradient entries the sample touches
+# (2 x 8 x 2 x 4 B x 16 = 2048 B).
+TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 12 * 4 + 1 + 2 * 8 * 2 * 4 * 16
+# DRAM bytes (read + write) of one k_field_bwd_tc launch on this workload from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), with a hash
+# of the kernel's sources at the time of the capture: the figure is reported
+# only while the sources are unchanged (None: not captured for this build).
+BWD_TC_DRAM = {"bytes": None, "sources_sha16": None}
+BWD_TC_SOURCES = ("nerfxl_bwd_tc.cu", "nerfxl_tc.cuh", "nerfxl_field.cuh", "nerfxl_half.cuh", "nerfxl_device.cuh",
+                  "nerfxl_host.h")
+
+
+def sources_sha16(names=BWD_TC_SOURCES):
+    import hashlib
+
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2404_16221_b300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def bwd_tc_traffic():
+    if BWD_TC_DRAM["bytes"] is None or BWD_TC_DRAM["sources_sha16"] != sources_sha16():
+        return None
+    return BWD_TC_DRAM["bytes"]
 
 
 def serve_sweep(args, dev, rates):
@@ -380,8 +424,10 @@ def main():
     for _ in range(warm):
         mstep()
     torch.cuda.synchronize()
+    launches0 = int(N.lib().nerfxl_launch_count())
     with Clocks(local) as clk:
         step_ms, kern_ms = time_steps(mstep, steps, flush, stream)
+    head_launches = int(N.lib().nerfxl_launch_count()) - launches0
     forms["grid8_train_f16tab_bf16mlp"] = {"rays": R, "step_ms": step_ms, "kern_ms": kern_ms,
                                            "clocks": clk.summary(), "kernel": "k_field_bwd_tc",
                                            "samples": forms["grid8_fwd_fp32"]["samples"],
@@ -622,7 +668,9 @@ def main():
         "config": {"workload": "grid8 training step (sampling, gather, MLP, local render, composite, loss "
                                "L2 + 0.01 distortion, backward, Adam): K=8 2x2x2 over [-1,1]^3, L=16 F=2 T=2^19 "
                                "(16->2048), FP16 hash tables, BF16 MLP 32-64-64-4 with FP32 accumulation on the "
-                               "tensor cores, FP32 Adam masters, 2^18 rays from 64 pinhole cameras, S=128",
+                               "tensor cores, FP32 Adam masters, 2^18 rays from 64 pinhole cameras, S=128; "
+                               "the target colours are uniform random instead of the 200-blob render (the "
+                               "dense field's throughput does not depend on the target)",
                    "rays_per_gpu": R, "samples_per_step": int(head["samples"]),
                    **({"reduced_batch": "first %d rays of the workload (profiling capture, not a bench value)"
                        % R} if args.profile_rays > 0 else {}),
@@ -632,10 +680,12 @@ def main():
                    "precision": "FP16 tables, BF16 MLP operands, FP32 accumulation, gradients and Adam"},
         "e2e": {"value": rays_total / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(3 * R * 12),
                 "d2h_bytes_per_step": 12},
-        "gpu_launches": 11 * steps,
+        "gpu_launches": head_launches,
         "roofline": {"bound": "hbm", "kernel": head["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": BWD_TC_DRAM_BYTES,
-                     "basis": "%d B/sample algorithmic (records: 16-bit features 64 B + geometry 32 B + chunk "
+                     "frac": achieved / hbm, "traffic": bwd_tc_traffic(),
+                     "frac_kind": "notional: algorithmic bytes against the HBM copy peak; the kernel is not "
+                                  "bound by HBM bandwidth (binding_resource)",
+                     "basis": "%d B/sample algorithmic (records: 16-bit features 64 B + geometry 48 B + chunk "
                               "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
                               "%.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src),

@@ -274,7 +274,8 @@ size_t nerfxl_render_cameras_workspace_bytes(const nerfxl_field* f, const nerfxl
 
 /*
  * Render a batch of pixel ranges from many cameras in one pass (the device
- * side of the serving loop). items [n_items] and cams [n_cams] are DEVICE arrays; the
+ * side of the serving loop; the paper renders novel views of the partitioned
+ * field by Algorithm 1 on each pixel's camera ray, Sec. 4.3). items [n_items] and cams [n_cams] are DEVICE arrays; the
  * batch has n_rays = sum of item counts rays, generated on the device from
  * the cameras. Pixel p of item it is written to rgb [(out_offset + p) * 3],
  * depth and opacity [out_offset + p]. A ray's result does not depend on the
@@ -286,6 +287,22 @@ nerfxl_status nerfxl_render_cameras(const nerfxl_field* f, const nerfxl_sampling
                                     const nerfxl_ray_item* items, const nerfxl_camera* cams, int32_t n_cams,
                                     float* rgb, float* depth, float* opacity, void* workspace, size_t ws_bytes,
                                     cudaStream_t stream);
+
+/*
+ * Pixel p = i W + j (row i from the top) of a camera generates the ray
+ *   aspect = W / H,  x = ((((j + 0.5) / W) * 2 - 1) * tan_half_fov) * aspect,
+ *   y = (1 - ((i + 0.5) / H) * 2) * tan_half_fov,
+ *   v = (x right + y up) + forward,  d = v / sqrt((v0 v0 + v1 v1) + v2 v2),
+ *   o = origin,
+ * each operation one IEEE FP32 rounding, no fused multiply-add, evaluated in
+ * the order written; the rays are therefore reproducible bit for bit.
+ * nerfxl_debug_camera_rays writes the rays nerfxl_render_cameras renders for
+ * the same items and cameras (device arrays rays_o, rays_d [n_rays][3]; a ray
+ * outside its item, image or camera list gets origin 3e30 and direction +x).
+ */
+nerfxl_status nerfxl_debug_camera_rays(int64_t n_rays, int32_t n_items, const nerfxl_ray_item* items,
+                                       const nerfxl_camera* cams, int32_t n_cams, float* rays_o, float* rays_d,
+                                       cudaStream_t stream);
 
 /*
  * Occupancy-grid refresh (keeps the grid of nerfxl_field.occupancy current
@@ -346,13 +363,25 @@ nerfxl_status nerfxl_region_chunks(const void* workspace, size_t ws_bytes, int32
  * 32 MiB array in the library's device image, reserved on every GPU that
  * loads the library until exit. Batches needing more scratch are refused
  * with NERFXL_E_WORKSPACE (grid8-sized rays: roughly 60 thousand per call).
- * The first call on a device looks up the array's address; make it before
- * any stream capture. Calls share the array: calls that overlap on the GPU
- * race, so order them on one stream. Allocates nothing.
+ * Each call looks up the array's address on the current device (no caching,
+ * so a cudaDeviceReset leaves nothing stale); the first call on a device also
+ * loads the library's device code there, so make it before any stream
+ * capture. Calls share the array: calls that overlap on the GPU race, so
+ * order them on one stream. Allocates nothing.
  */
 nerfxl_status nerfxl_render_fwd_static(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
                                        const float* rays_o, const float* rays_d, float* rgb, float* depth,
                                        float* opacity, float* dist, cudaStream_t stream);
+
+/*
+ * Device-side status of the last nerfxl_render_fwd_static call on the current
+ * device (synchronises the stream), as nerfxl_check reports it for a caller
+ * workspace: NERFXL_OK, NERFXL_E_OVERFLOW (a ray crossed more regions than
+ * max_segments; its segments beyond that were dropped) or NERFXL_E_TIMEOUT
+ * (the tensor-core forward gave up a bounded wait; that call's outputs are
+ * invalid). Allocates nothing.
+ */
+nerfxl_status nerfxl_static_check(cudaStream_t stream);
 
 /*
  * Status of device-side checks of the last call made with this workspace
@@ -378,6 +407,13 @@ nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int
  * Process-wide setting; not for concurrent use from several threads.
  */
 nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
+
+/*
+ * Instrumentation: the number of kernels this library has launched in this
+ * process (all entry points, all devices and streams), for counting the
+ * launches of a timed region. The paper has no counterpart.
+ */
+int64_t nerfxl_launch_count(void);
 
 /*
  * Failure-path probe: one thread waits on an mbarrier with the same bounded

@@ -855,7 +855,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
       n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
       d_rgb, d_depth, d_opacity, d_dist, dpart, tc ? reinterpret_cast<const int32_t*>(ws + L.rec_pos) : nullptr,
       tc ? reinterpret_cast<float4*>(ws + L.rec_dpart) : nullptr);
-  st = launch_check("k_composite_bwd");
+  st = kernel_launched("k_composite_bwd");
   if (st != NERFXL_OK) return st;
   if (tc && f->arch == NERFXL_ARCH_SPLIT)
     return launch_field_bwd_split_tc(f, level_params(f), ws, L, grad_tables, grad_mlp, stream);
@@ -889,7 +889,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
     profile_mark(0, stream);
     ks<<<grid, kBwdThreads, smem_s, stream>>>(p);
     profile_mark(1, stream);
-    return launch_check("k_field_bwd_split_f32");
+    return kernel_launched("k_field_bwd_split_f32");
   }
   const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
   if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
@@ -901,5 +901,5 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   profile_mark(0, stream);
   kern<<<grid, kBwdThreads, smem, stream>>>(p);
   profile_mark(1, stream);
-  return launch_check("k_field_bwd_f32");
+  return kernel_launched("k_field_bwd_f32");
 }

@@ -646,7 +646,7 @@ nerfxl_status launch_field_bwd_split_tc(const nerfxl_field* f, const LevelParams
   profile_mark(0, stream);
   kern<<<grid, kThreadsS, smem, stream>>>(p);
   profile_mark(1, stream);
-  return launch_check("k_field_bwd_split_tc");
+  return kernel_launched("k_field_bwd_split_tc");
 }
 
 }  // namespace nerfxl

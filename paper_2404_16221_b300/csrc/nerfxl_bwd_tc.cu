@@ -612,7 +612,7 @@ nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, 
   profile_mark(0, stream);
   kern<<<grid, kThreads, smem, stream>>>(p);
   profile_mark(1, stream);
-  return launch_check("k_field_bwd_tc");
+  return kernel_launched("k_field_bwd_tc");
 }
 
 }  // namespace nerfxl

@@ -115,7 +115,7 @@ nerfxl_status nerfxl_debug_segments(const nerfxl_field* f, const nerfxl_sampling
   k_debug_seg_out<<<(int)((n_rays + 127) / 128), 128, 0, stream>>>(
       n_rays, L.max_seg, max_seg, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr),
       reinterpret_cast<const SegDesc*>(ws + L.segs), nseg, region, t0, t1, n_intervals);
-  return launch_check("k_debug_seg_out");
+  return kernel_launched("k_debug_seg_out");
 }
 
 nerfxl_status nerfxl_debug_samples(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays,
@@ -137,7 +137,7 @@ nerfxl_status nerfxl_debug_samples(const nerfxl_field* f, const nerfxl_sampling*
   k_debug_samples<<<(int)((n_rays + 63) / 64), 64, 0, stream>>>(n_rays, rays_o, rays_d, fp, f->K, level_params(f),
                                                                 samp_params(f, s), max_int, count, a, b, region, idx,
                                                                 feat, raw);
-  return launch_check("k_debug_samples");
+  return kernel_launched("k_debug_samples");
 }
 
 }  // extern "C"

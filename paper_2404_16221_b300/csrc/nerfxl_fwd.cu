@@ -20,6 +20,8 @@
 //   k_composite    per ray: exclusive prefix product over chunk partials
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdio.h>
 
 #include <algorithm>
@@ -766,6 +768,14 @@ nerfxl_status launch_check(const char* what) {
   return NERFXL_OK;
 }
 
+// Process-wide count of the kernels this library has launched.
+std::atomic<int64_t> g_launches(0);
+
+nerfxl_status kernel_launched(const char* name) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return launch_check(name);
+}
+
 // Steps (a) and bucketing, shared by forward, backward and debug calls.
 nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t R, const float* rays_o,
                            const float* rays_d, char* ws, const Layout& L, cudaStream_t stream) {
@@ -781,7 +791,7 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
                                                   reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
                                                   reinterpret_cast<SegDesc*>(ws + L.segs),
                                                   f->occupancy ? nullptr : counts, hdr_words + 0);
-    nerfxl_status st = launch_check("k_segments");
+    nerfxl_status st = kernel_launched("k_segments");
     if (st != NERFXL_OK) return st;
     if (f->occupancy) {
       if (!sp.seg_keep) return set_error(NERFXL_E_INVALID, "occupancy lists not attached to the sampling");
@@ -791,21 +801,21 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
           rays_o, rays_d, R, f->boxes, K, sp, f->occupancy, f->occ_res, reinterpret_cast<RayHdr*>(ws + L.ray_hdr),
           reinterpret_cast<SegDesc*>(ws + L.segs), reinterpret_cast<int32_t*>(ws + L.seg_keep),
           reinterpret_cast<uint16_t*>(ws + L.kept), counts, hdr_words + 0);
-      st = launch_check("k_skip_empty");
+      st = kernel_launched("k_skip_empty");
       if (st != NERFXL_OK) return st;
     }
   }
   k_region_scan<<<1, 32, 0, stream>>>(reinterpret_cast<int32_t*>(ws + L.counts), K, kChunksPerTile,
                                       reinterpret_cast<int32_t*>(ws + L.base), reinterpret_cast<uint2*>(ws + L.chunks),
                                       hdr_words + 1);
-  nerfxl_status st = launch_check("k_region_scan");
+  nerfxl_status st = kernel_launched("k_region_scan");
   if (st != NERFXL_OK) return st;
   if (R > 0) {
     k_fill_chunks<<<blocks, threads, sizeof(int32_t) * 6 * K, stream>>>(
         R, K, sp, reinterpret_cast<RayHdr*>(ws + L.ray_hdr), reinterpret_cast<SegDesc*>(ws + L.segs),
         reinterpret_cast<int32_t*>(ws + L.counts), reinterpret_cast<int32_t*>(ws + L.base),
         reinterpret_cast<int32_t*>(ws + L.cursor), reinterpret_cast<uint2*>(ws + L.chunks));
-    st = launch_check("k_fill_chunks");
+    st = kernel_launched("k_fill_chunks");
     if (st != NERFXL_OK) return st;
   }
   return NERFXL_OK;
@@ -909,7 +919,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
     k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(
         n_rays, sp, reinterpret_cast<const RayHdr*>(ws + L.ray_hdr), reinterpret_cast<const float4*>(ws + L.partials),
         rgb, depth, opacity, dist, out_index);
-    return launch_check("k_composite");
+    return kernel_launched("k_composite");
   }
 
   FwdParams p;
@@ -940,22 +950,24 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   profile_mark(0, stream);
   kern<<<grid, kFwdThreads, smem, stream>>>(p);
   profile_mark(1, stream);
-  st = launch_check("k_field_fwd_f32");
+  st = kernel_launched("k_field_fwd_f32");
   if (st != NERFXL_OK) return st;
   if (per_sample) {
     const int64_t threads = n_rays * kWarp;
     k_composite_samples<<<(int)((threads + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.smp4, p.smp2, rgb,
                                                                            depth, opacity, dist, out_index);
-    return launch_check("k_composite_samples");
+    return kernel_launched("k_composite_samples");
   }
   k_composite<<<(int)((n_rays + 255) / 256), 256, 0, stream>>>(n_rays, sp, p.hdr, p.partials, rgb, depth, opacity,
                                                                 dist, out_index);
-  return launch_check("k_composite");
+  return kernel_launched("k_composite");
 }
 
 }  // namespace nerfxl
 
 extern "C" {
+
+int64_t nerfxl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 nerfxl_status nerfxl_check(const void* workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!workspace || ws_bytes < 64) return set_error(NERFXL_E_WORKSPACE, "no workspace");

@@ -583,7 +583,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   profile_mark(0, stream);
   kern<<<grid, kTcThreads, smem, stream>>>(p);
   profile_mark(1, stream);
-  return launch_check("k_field_fwd_tc");
+  return kernel_launched("k_field_fwd_tc");
 }
 
 }  // namespace nerfxl

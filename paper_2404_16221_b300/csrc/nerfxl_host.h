@@ -43,6 +43,8 @@ struct Layout {
 const char* last_error();
 nerfxl_status set_error(nerfxl_status st, const std::string& msg);
 nerfxl_status launch_check(const char* what);
+// launch_check after a kernel launch, counting the launch (nerfxl_launch_count).
+nerfxl_status kernel_launched(const char* name);
 nerfxl_status validate(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R);
 int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s);
 int max_chunks(int S, int max_seg);

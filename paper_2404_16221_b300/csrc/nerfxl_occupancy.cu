@@ -128,5 +128,5 @@ extern "C" nerfxl_status nerfxl_occupancy_update(const nerfxl_field* f, int32_t 
                                                                     sizeof(float) * kMlpParams, stream>>>(
       fp, level_params(f), G, cells, (int)bpr, (uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), key, decay,
       threshold, density, bits);
-  return launch_check("k_occupancy_update");
+  return kernel_launched("k_occupancy_update");
 }

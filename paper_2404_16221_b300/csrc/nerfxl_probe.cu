@@ -31,7 +31,7 @@ extern "C" nerfxl_status nerfxl_debug_wait_probe(int32_t* status, uint32_t spins
                                                 cudaStream_t stream) {
   if (!status || spins == 0 || spins > (1u << 26)) return set_error(NERFXL_E_INVALID, "bad probe arguments");
   k_wait_probe<<<1, 32, 0, stream>>>(status, spins, arrive);
-  nerfxl_status st = launch_check("k_wait_probe");
+  nerfxl_status st = kernel_launched("k_wait_probe");
   if (st != NERFXL_OK) return st;
   int32_t h = -1;
   if (cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||

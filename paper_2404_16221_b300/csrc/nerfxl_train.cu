@@ -111,7 +111,7 @@ nerfxl_status launch_adam(int64_t n, float* p, const float* g, float* m, float* 
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
   k_adam<<<blocks, 256, 0, stream>>>(n, p, g, m, v, opt->lr, opt->beta1, opt->beta2, opt->eps, (float)(1.0 / c1),
                                      (float)(1.0 / std::sqrt(c2)), copy, copy_dtype);
-  return launch_check("k_adam");
+  return kernel_launched("k_adam");
 }
 
 }  // namespace nerfxl
@@ -131,11 +131,11 @@ nerfxl_status nerfxl_loss(int64_t n_rays, const float* rgb, const float* dist, c
   float2* sums = static_cast<float2*>(scratch);
   if (nb > 0) {
     k_loss<<<nb, kLossThreads, 0, stream>>>(n_rays, rgb, dist, target_rgb, lambda_dist, d_rgb, d_dist, sums);
-    nerfxl_status st = launch_check("k_loss");
+    nerfxl_status st = kernel_launched("k_loss");
     if (st != NERFXL_OK) return st;
   }
   k_loss_final<<<1, kFinalThreads, 0, stream>>>(sums, nb, n_rays, lambda_dist, loss_out);
-  return launch_check("k_loss_final");
+  return kernel_launched("k_loss_final");
 }
 
 nerfxl_status nerfxl_adam_update(int64_t n, float* params, const float* grads, float* m, float* v,

@@ -77,9 +77,11 @@ SIGNATURES = {
     "nerfxl_render_fwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_check": (C.c_int, [_vp, _sz, _vp]),
     "nerfxl_render_fwd_static": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nerfxl_static_check": (C.c_int, [_vp]),
     "nerfxl_last_error": (C.c_char_p, []),
     "nerfxl_workspace_stats": (C.c_int, [_vp, _sz, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]),
     "nerfxl_set_profile_events": (C.c_int, [_vp, _vp]),
+    "nerfxl_launch_count": (_i64, []),
     "nerfxl_render_bwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_loss": (C.c_int, [_i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_adam_update": (C.c_int, [_i64, _vp, _vp, _vp, _vp, C.c_void_p, _vp, _i32, _vp]),
@@ -88,6 +90,7 @@ SIGNATURES = {
     "nerfxl_render_cameras_workspace_bytes": (_sz, [_FP, _SP, _i64]),
     "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_wait_probe": (C.c_int, [_vp, C.c_uint32, _i32, _vp]),
+    "nerfxl_debug_camera_rays": (C.c_int, [_i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp]),
     "nerfxl_partition": (C.c_int, [_vp, _i64, _vp, _i32, _vp, _vp]),
     "nerfxl_occupancy_update": (C.c_int, [_FP, _i32, _i64, C.c_uint64, C.c_float, C.c_float, _vp, _vp, _vp]),
     "nerfxl_region_chunks": (C.c_int, [_vp, _sz, _i32, _vp, _vp]),

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
+    ap.add_argument("--serve-policies", type=str, default="fair", help="serving sweep: batching policies")
+    ap.add_argument("--serve-batches", type=str, default=str(1 << 20), help="serving sweep: max rays per batch")
     return ap.parse_args()
 
 
@@ -320,12 +322,16 @@ def serve_sweep(args, dev, rates):
     samp = api.Sampling(ws_.S, ws_.max_segments)
     serve.ServeEngine(field, samp).run(serve.requests_from_stream(4, 100.0, ws_.seed + 17), realtime=False)
     rows = []
-    for rate in rates:
-        reqs = serve.requests_from_stream(args.serve_requests, rate, ws_.seed)
-        px = sum(r.pixels for r in reqs)
-        m_ = serve.ServeEngine(field, samp, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(reqs)
-        m_.update({"rate_req_s": rate, "offered_rays_per_s": px / max(reqs[-1].arrival_s, 1e-9)})
-        rows.append(m_)
+    for policy, batch in [(p_, int(b_)) for p_ in args.serve_policies.split(",")
+                          for b_ in args.serve_batches.split(",")]:
+        for rate in rates:
+            reqs = serve.requests_from_stream(args.serve_requests, rate, ws_.seed)
+            px = sum(r.pixels for r in reqs)
+            m_ = serve.ServeEngine(field, samp, max_batch_rays=batch, arena_pixels=1 << 26, policy=policy).run(reqs)
+            m_.update({"rate_req_s": rate, "offered_rays_per_s": px / max(reqs[-1].arrival_s, 1e-9),
+                       "policy": policy, "max_batch_rays": batch,
+                       "largest_request_pixels": max(r.pixels for r in reqs)})
+            rows.append(m_)
     print(json.dumps({"serve_sweep": rows, "workload": "serve32: K=32 city field, FP16 tables + BF16 MLP, "
                       "log-uniform 64x64..1920x1080 requests, Poisson arrivals, %d requests per rate"
                       % args.serve_requests}), flush=True)
@@ -570,6 +576,30 @@ def main():
                 forms[name].pop(k)
             del fc
             torch.cuda.empty_cache()
+        # ---- city32 training step (FP16 tables, BF16 MLP, records, FP32 Adam) under a 4 GB workspace cap:
+        #      the step runs in ray sub-batches (its one-pass workspace is several times larger)
+        tgt_c = torch.rand(len(oc), 3, generator=torch.Generator().manual_seed(1003)).to(dev)
+        fcm = mk_field(wc, tc_, mc_, torch.float16, torch.bfloat16)
+        cap = 4 << 30
+        ctr = api.Trainer(fcm, sc, lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=tc_, master_mlp=mc_,
+                          workspace_cap=cap)
+        cstep = lambda: ctr.step(oc_d, dc_d, tgt_c)
+        for _ in range(warm):
+            cstep()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            c_ms, _ = time_steps(cstep, max(2, steps // 4), flush, stream, prof=False)
+        fdc, sdc = fcm.desc(), ctr.samp.desc()
+        forms["city32_train_f16tab_bf16mlp"] = {
+            "train_capped": {
+                "rays_per_s": len(oc) / (statistics.mean(c_ms) / 1000.0), "ms_per_step": statistics.mean(c_ms),
+                "clocks": clk.summary(), "cap_bytes": cap, "used_bytes": int(ctr._ws.numel()),
+                "one_pass_bytes": int(N.lib().nerfxl_step_workspace_bytes(api.C_ref(fdc), api.C_ref(sdc), len(oc))),
+                "sub_batch_rays": ctr.sub_batch(len(oc))},
+            "note": "K=32 city field, 2^20 rays, S=256, FP16 tables + BF16 MLP + FP32 Adam masters, uniform random "
+                    "target; the step's workspace capped at 4 GB, so it runs in ray sub-batches"}
+        del ctr, fcm
+        torch.cuda.empty_cache()
         # ---- spatial partitioning (Sec. 4.4) on an uneven trajectory: 32 regions from the CDF splits of
         #      training-ray samples vs the uniform 8x4x1 slabs, held-out rays of the same trajectory
         root = sy.scene_root(wc)
@@ -641,7 +671,7 @@ def main():
                 v["frac_of_bf16_tensor"] = v["mlp_tflops_algorithmic"] / bf16
 
     def summary(f):
-        if "serve" in f or "partition" in f or "composition" in f or "occupancy" in f or "split" in f:
+        if any(k in f for k in ("serve", "partition", "composition", "occupancy", "split", "train_capped")):
             return {k: v for k, v in f.items()}
         ms = statistics.mean(f["step_ms"])
         r = {"rays_per_s": f["rays"] / (ms / 1000.0), "ms_per_step": ms}

@@ -224,6 +224,18 @@ typedef struct nerfxl_adam {
 nerfxl_status nerfxl_adam_update(int64_t n, float* params, const float* grads, float* m, float* v,
                                  const nerfxl_adam* opt, void* compute_copy, int32_t copy_dtype, cudaStream_t stream);
 
+/*
+ * E4M3 weights of fused MLP blocks for the FP8 precision form (the MLP
+ * precision sweep; forward only). mlp [K][P] FP32 blocks W1 [mlp_in][width],
+ * W2 [width][width], W3 [width][4] (P = nerfxl_mlp_params); per region k and
+ * layer li: scales[k][li] = max(max |W|, 1e-30) / 448 (FP32, IEEE division),
+ * q = E4M3(W / scale) rounded to nearest even and saturated to +-448, so W ~=
+ * scale q. Outputs q [K][P] bytes and scales [K][3] (device), the
+ * field's mlp and mlp_scales for mlp_dtype NERFXL_E4M3.
+ */
+nerfxl_status nerfxl_quantize_e4m3(int32_t K, int32_t mlp_in, int32_t width, const float* mlp, uint8_t* q,
+                                   float* scales, cudaStream_t stream);
+
 /* FP32 master parameters, their gradients and Adam moments (all [K][E][F] / [K][P]). */
 typedef struct nerfxl_train_state {
   float* tables;
@@ -236,15 +248,34 @@ typedef struct nerfxl_train_state {
   float* v_mlp;
 } nerfxl_train_state;
 
-/* Workspace of nerfxl_step for R rays. */
+/*
+ * Workspace of nerfxl_step for R rays in one pass. A smaller workspace runs
+ * the step in ray sub-batches (below); nerfxl_step_sub_batch returns the
+ * sub-batch a workspace of ws_bytes gives: R itself when the one-pass
+ * workspace fits, else the largest multiple of 256 rays that fits, 0 if none
+ * does (-1 on invalid arguments).
+ */
 size_t nerfxl_step_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays);
+int64_t nerfxl_step_sub_batch(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, size_t ws_bytes);
 
 /*
- * One training step: clear gradients, forward render, loss (lambda_dist
- * weighs the distortion term), backward, Adam on tables and MLP. loss_out[3]
- * as nerfxl_loss (the loss of the parameters before the update). For the FP32
- * path the field must point at the masters (f->tables == st->tables,
- * f->mlp == st->mlp).
+ * One training step of the partitioned field (Sec. 4.1: the photometric L2
+ * loss plus lambda_dist times the distortion loss of Eq. 2, normalised as
+ * mean over rays and channels and mean over rays; gradients reach each
+ * region's parameters only through its own samples, Sec. 4.2-4.3; then one
+ * Adam step, Kingma & Ba, with bias correction): clear the gradients, forward
+ * render, loss, backward, Adam on tables and MLP. loss_out[3] as nerfxl_loss
+ * (the loss of the parameters before the update). For the FP32 path the field
+ * must point at the masters (f->tables == st->tables, f->mlp == st->mlp).
+ *
+ * Bounded memory: the per-sample state the backward needs grows with the
+ * batch (about 116 bytes per sample with a 16-bit MLP). When ws_bytes is below
+ * nerfxl_step_workspace_bytes(f, s, n_rays), the rays are processed in
+ * sub-batches of nerfxl_step_sub_batch(...) rays: forward, loss adjoints
+ * (normalised by all n_rays) and backward per sub-batch, gradients summed,
+ * then one Adam step. The result equals the one-pass step up to the order of
+ * the FP32 gradient sums; the loss is the same fixed-order sum.
+ * E_WORKSPACE if not even 256 rays fit.
  */
 nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
                           const float* rays_d, const float* target_rgb, float lambda_dist,

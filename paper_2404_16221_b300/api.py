@@ -286,8 +286,12 @@ class Trainer:
     refreshes the copies from them."""
 
     def __init__(self, field: PartitionedField, samp: Sampling, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
-                 lambda_dist=0.01, master_tables=None, master_mlp=None, save_features: bool = True):
+                 lambda_dist=0.01, master_tables=None, master_mlp=None, save_features: bool = True,
+                 workspace_cap: int | None = None):
+        """workspace_cap (bytes): bound the step's workspace; a batch whose
+        one-pass workspace is larger runs in ray sub-batches (nerfxl_step)."""
         self.field = field
+        self.workspace_cap = workspace_cap
         if save_features and field.mlp.dtype in (torch.bfloat16, torch.float16):
             # 16-bit MLP: keep the forward's records for the tensor-core backward
             samp = dataclasses.replace(samp, flags=samp.flags | SAVE_FEATURES)
@@ -317,6 +321,15 @@ class Trainer:
         return PartitionedField(f.boxes, f.level_res, f.log2_T, self.tables, self.mlp, F=f.F, mlp_in=f.mlp_in,
                                 width=f.width, device=f.device, arch=f.arch)
 
+    def sub_batch(self, n_rays: int) -> int:
+        """Rays per sub-batch of a step over n_rays under the workspace cap
+        (n_rays itself when the one-pass workspace fits)."""
+        fd, sd = self.field.desc(), self.samp.desc()
+        need = int(N.lib().nerfxl_step_workspace_bytes(C_ref(fd), C_ref(sd), int(n_rays)))
+        if self.workspace_cap is not None:
+            need = min(need, int(self.workspace_cap))
+        return int(N.lib().nerfxl_step_sub_batch(C_ref(fd), C_ref(sd), int(n_rays), need))
+
     def state_desc(self) -> N.TrainStateDesc:
         return N.TrainStateDesc(self.tables.data_ptr(), self.mlp.data_ptr(), self.grad_tables.data_ptr(),
                                 self.grad_mlp.data_ptr(), self.m_tables.data_ptr(), self.v_tables.data_ptr(),
@@ -330,6 +343,8 @@ class Trainer:
         need = int(N.lib().nerfxl_step_workspace_bytes(C_ref(fd), C_ref(sd), R))
         if need == 0:
             N.check(N.E_INVALID, "nerfxl_step_workspace_bytes")
+        if self.workspace_cap is not None:
+            need = min(need, int(self.workspace_cap))
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(need, dtype=torch.uint8, device=self.field.device)
         self.step_count += 1
@@ -342,37 +357,18 @@ class Trainer:
         return self.loss
 
 
-MLP_LAYER_SIZES = (32 * 64, 64 * 64, 64 * 4)  # W1, W2, W3 of one region block
-
-
-def quantize_mlp_e4m3(mlp):
-    """FP32 MLP blocks [K][P] -> (E4M3 bytes [K][P] uint8, scales [K][3]).
-
-    Per region and per layer: scale = max|W| / 448 (the largest finite E4M3
-    value), W_q = e4m3(W / scale), so W ~= scale * W_q."""
-    m = torch.as_tensor(mlp, dtype=torch.float32)
+def quantize_mlp_e4m3(mlp, mlp_in: int = 32, width: int = 64, device=None):
+    """FP32 fused MLP blocks [K][P] -> (E4M3 bytes [K][P] uint8, scales [K][3]),
+    on the device, by nerfxl_quantize_e4m3 (per region and layer: scale =
+    max|W| / 448, W_q = e4m3(W / scale), so W ~= scale * W_q)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    m = torch.as_tensor(mlp, dtype=torch.float32).to(dev).contiguous()
     K = m.shape[0]
-    q = torch.empty(m.shape, dtype=torch.uint8, device=m.device)
-    scales = torch.empty(K, 3, dtype=torch.float32, device=m.device)
-    off = 0
-    for li, n in enumerate(MLP_LAYER_SIZES):
-        blk = m[:, off:off + n]
-        s = blk.abs().amax(dim=1).clamp_min(1e-30) / 448.0
-        q[:, off:off + n] = (blk / s[:, None]).to(torch.float8_e4m3fn).view(torch.uint8)
-        scales[:, li] = s
-        off += n
+    q = torch.empty(m.shape, dtype=torch.uint8, device=dev)
+    scales = torch.empty(K, 3, dtype=torch.float32, device=dev)
+    N.check(N.lib().nerfxl_quantize_e4m3(K, int(mlp_in), int(width), N._ptr(m), N._ptr(q), N._ptr(scales),
+                                         N._stream(torch.cuda.current_stream(dev))), "nerfxl_quantize_e4m3")
     return q, scales
-
-
-def dequantize_mlp_e4m3(q, scales):
-    """Inverse of quantize_mlp_e4m3 (FP32), for references."""
-    q = torch.as_tensor(q)
-    out = q.view(torch.float8_e4m3fn).float()
-    off = 0
-    for li, n in enumerate(MLP_LAYER_SIZES):
-        out[:, off:off + n] *= torch.as_tensor(scales)[:, li:li + 1]
-        off += n
-    return out
 
 
 def partition_boxes(points, root, levels: int):

@@ -7,6 +7,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,7 +20,9 @@ namespace nerfxl {
 constexpr int kLossThreads = 256;
 
 // Kahan-compensated block sums of the two loss terms; per-ray adjoints.
-__global__ void __launch_bounds__(kLossThreads) k_loss(int64_t R, const float* __restrict__ rgb,
+// R rays of a batch whose loss is a mean over R_norm rays (R_norm > R when the
+// batch is one sub-batch of a larger step).
+__global__ void __launch_bounds__(kLossThreads) k_loss(int64_t R, int64_t R_norm, const float* __restrict__ rgb,
                                                        const float* __restrict__ dist,
                                                        const float* __restrict__ target, float lambda,
                                                        float* __restrict__ d_rgb, float* __restrict__ d_dist,
@@ -27,7 +30,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int64_t R, const float* _
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float photo = 0.0f, dd = 0.0f;
   if (r < R) {
-    const float inv = 1.0f / (3.0f * (float)R);
+    const float inv = 1.0f / (3.0f * (float)R_norm);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float e = rgb[3 * r + c] - target[3 * r + c];
@@ -35,7 +38,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int64_t R, const float* _
       if (d_rgb) d_rgb[3 * r + c] = 2.0f * e * inv;
     }
     dd = dist ? dist[r] : 0.0f;
-    if (d_dist) d_dist[r] = lambda / (float)R;
+    if (d_dist) d_dist[r] = lambda / (float)R_norm;
   }
   // fixed-order tree reduction within the block
   __shared__ float s_p[kLossThreads], s_d[kLossThreads];
@@ -114,6 +117,42 @@ nerfxl_status launch_adam(int64_t n, float* p, const float* g, float* m, float* 
   return kernel_launched("k_adam");
 }
 
+// E4M3 weight quantisation of fused MLP blocks (the FP8 experiment of the
+// precision forms). Per region k and layer li (W1, W2, W3 of the block):
+//   scale[k][li] = max(max |W|, 1e-30) / 448   (448: the largest finite E4M3 value)
+//   q = e4m3(W / scale), round to nearest even, saturating to +-448,
+// so W ~= scale * q. One block per (region, layer) finds max |W| in a fixed
+// order (exact: a maximum does not round).
+constexpr int kQuantThreads = 256;
+__global__ void __launch_bounds__(kQuantThreads) k_e4m3_scales(const float* __restrict__ mlp, int64_t P, int64_t n1,
+                                                               int64_t n2, int64_t n3, float* __restrict__ scales) {
+  const int k = blockIdx.x, li = blockIdx.y;
+  const int64_t off = li == 0 ? 0 : (li == 1 ? n1 : n1 + n2);
+  const int64_t n = li == 0 ? n1 : (li == 1 ? n2 : n3);
+  const float* w = mlp + (int64_t)k * P + off;
+  float a = 0.0f;
+  for (int64_t i = threadIdx.x; i < n; i += kQuantThreads) a = fmaxf(a, fabsf(w[i]));
+  __shared__ float s_a[kQuantThreads];
+  s_a[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kQuantThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s_a[threadIdx.x] = fmaxf(s_a[threadIdx.x], s_a[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scales[3 * k + li] = __fdiv_rn(fmaxf(s_a[0], 1e-30f), 448.0f);
+}
+
+__global__ void __launch_bounds__(kQuantThreads) k_e4m3_quantize(const float* __restrict__ mlp, int64_t P, int64_t K,
+                                                                 int64_t n1, int64_t n2,
+                                                                 const float* __restrict__ scales,
+                                                                 uint8_t* __restrict__ q) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K * P; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / P, j = i % P;
+    const int li = j < n1 ? 0 : (j < n1 + n2 ? 1 : 2);
+    q[i] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(mlp[i], scales[3 * k + li]), __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
 }  // namespace nerfxl
 
 using namespace nerfxl;
@@ -130,7 +169,7 @@ nerfxl_status nerfxl_loss(int64_t n_rays, const float* rgb, const float* dist, c
     return set_error(NERFXL_E_WORKSPACE, "loss scratch too small");
   float2* sums = static_cast<float2*>(scratch);
   if (nb > 0) {
-    k_loss<<<nb, kLossThreads, 0, stream>>>(n_rays, rgb, dist, target_rgb, lambda_dist, d_rgb, d_dist, sums);
+    k_loss<<<nb, kLossThreads, 0, stream>>>(n_rays, n_rays, rgb, dist, target_rgb, lambda_dist, d_rgb, d_dist, sums);
     nerfxl_status st = kernel_launched("k_loss");
     if (st != NERFXL_OK) return st;
   }
@@ -149,12 +188,61 @@ nerfxl_status nerfxl_adam_update(int64_t n, float* params, const float* grads, f
   return launch_adam(n, params, grads, m, v, opt, compute_copy, copy_dtype == NERFXL_F32 ? 0 : copy_dtype, stream);
 }
 
+nerfxl_status nerfxl_quantize_e4m3(int32_t K, int32_t mlp_in, int32_t width, const float* mlp, uint8_t* q,
+                                   float* scales, cudaStream_t stream) {
+  if (K < 1 || K > NERFXL_MAX_REGIONS || mlp_in < 1 || width < 1 || !mlp || !q || !scales)
+    return set_error(NERFXL_E_INVALID, "bad E4M3 quantisation arguments");
+  const int64_t n1 = (int64_t)mlp_in * width, n2 = (int64_t)width * width, n3 = (int64_t)width * 4;
+  const int64_t P = n1 + n2 + n3;
+  k_e4m3_scales<<<dim3((unsigned)K, 3), kQuantThreads, 0, stream>>>(mlp, P, n1, n2, n3, scales);
+  nerfxl_status st = kernel_launched("k_e4m3_scales");
+  if (st != NERFXL_OK) return st;
+  const int blocks = (int)std::min<int64_t>((K * P + kQuantThreads - 1) / kQuantThreads, 148 * 8);
+  k_e4m3_quantize<<<blocks, kQuantThreads, 0, stream>>>(mlp, P, K, n1, n2, scales, q);
+  return kernel_launched("k_e4m3_quantize");
+}
+
+}  // extern "C"
+
+namespace nerfxl {
+namespace {
+
+// Workspace of a training step over R rays run in sub-batches of Rb rays:
+// the backward layout of Rb rays, Rb rays of outputs and adjoints
+// (rgb, d_rgb [3], depth, opacity, dist, d_dist), and the loss's block sums
+// of all R rays.
+size_t step_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t Rb, int64_t R) {
+  const size_t nb = (size_t)std::max<int64_t>(1, (R + kLossThreads - 1) / kLossThreads);
+  const size_t per_ray = ((size_t)Rb * 10 * sizeof(float) + 255) / 256 * 256;
+  return (layout(f, s, Rb, 1).total + 255) / 256 * 256 + per_ray + nb * sizeof(float2) + 256;
+}
+
+// Largest sub-batch (the whole batch, else a multiple of the loss block) whose
+// step workspace fits in ws_bytes; 0 if none does.
+int64_t step_sub_batch(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, size_t ws_bytes) {
+  if (R == 0 || step_bytes(f, s, R, R) <= ws_bytes) return R;
+  int64_t lo = 0, hi = (R - 1) / kLossThreads;  // in units of kLossThreads rays
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (step_bytes(f, s, mid * kLossThreads, R) <= ws_bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * kLossThreads;
+}
+
+}  // namespace
+}  // namespace nerfxl
+
+extern "C" {
+
 size_t nerfxl_step_workspace_bytes(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays) {
   if (validate(f, s, n_rays) != NERFXL_OK) return 0;
-  const size_t nb = (size_t)std::max<int64_t>(1, (n_rays + kLossThreads - 1) / kLossThreads);
-  const size_t extra = ((size_t)n_rays * (3 + 3 + 1 + 1 + 1 + 1) * sizeof(float) + nb * sizeof(float2) + 1023) /
-                       256 * 256 + 1024;
-  return layout(f, s, n_rays, 1).total + extra;
+  return step_bytes(f, s, n_rays, n_rays);
+}
+
+int64_t nerfxl_step_sub_batch(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, size_t ws_bytes) {
+  if (validate(f, s, n_rays) != NERFXL_OK) return -1;
+  return step_sub_batch(f, s, n_rays, ws_bytes);
 }
 
 nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
@@ -172,32 +260,46 @@ nerfxl_status nerfxl_step(const nerfxl_field* f, const nerfxl_sampling* s, int64
     return set_error(NERFXL_E_INVALID, "an FP32 field block must be the master itself");
   if ((!tab32 && f->table_dtype != NERFXL_F16) || (!mlp32 && f->mlp_dtype != NERFXL_BF16 && f->mlp_dtype != NERFXL_F16))
     return set_error(NERFXL_E_UNSUPPORTED, "compute copies must be FP16 tables and BF16/FP16 MLP");
-  const size_t need = nerfxl_step_workspace_bytes(f, s, n_rays);
-  if (!workspace || ws_bytes < need) return set_error(NERFXL_E_WORKSPACE, "step workspace too small");
-  const Layout L = layout(f, s, n_rays, 1);
+  const int64_t Rb = workspace ? step_sub_batch(f, s, n_rays, ws_bytes) : 0;
+  if (n_rays > 0 && Rb == 0)
+    return set_error(NERFXL_E_WORKSPACE, "step workspace too small even for a sub-batch of 256 rays");
+  const Layout L = layout(f, s, Rb, 1);
   char* ws = static_cast<char*>(workspace);
   char* ex = ws + (L.total + 255) / 256 * 256;
-  const size_t R = (size_t)n_rays;
   float* rgb = reinterpret_cast<float*>(ex);
-  float* d_rgb = rgb + 3 * R;
-  float* depth = d_rgb + 3 * R;
-  float* opacity = depth + R;
-  float* dist = opacity + R;
-  float* d_dist = dist + R;
-  float2* sums = reinterpret_cast<float2*>(ex + ((6 * R + 4 * R) * sizeof(float) + 255) / 256 * 256);
+  float* d_rgb = rgb + 3 * (size_t)Rb;
+  float* depth = d_rgb + 3 * (size_t)Rb;
+  float* opacity = depth + Rb;
+  float* dist = opacity + Rb;
+  float* d_dist = dist + Rb;
+  float2* sums = reinterpret_cast<float2*>(ex + ((size_t)Rb * 10 * sizeof(float) + 255) / 256 * 256);
   const int nb = (int)std::max<int64_t>(1, (n_rays + kLossThreads - 1) / kLossThreads);
   const int64_t n_tab = (int64_t)f->K * nerfxl_table_entries(f->level_res, f->L, f->log2_T) * f->F;
   const int64_t n_mlp = nerfxl_field_mlp_params(f);
   if (cudaMemsetAsync(st->grad_tables, 0, sizeof(float) * n_tab, stream) != cudaSuccess ||
       cudaMemsetAsync(st->grad_mlp, 0, sizeof(float) * n_mlp, stream) != cudaSuccess)
     return launch_check("gradient clear");
-  rc = nerfxl_render_fwd(f, s, n_rays, rays_o, rays_d, rgb, depth, opacity, dist, workspace, L.total, stream);
-  if (rc != NERFXL_OK) return rc;
-  rc = nerfxl_loss(n_rays, rgb, dist, target_rgb, lambda_dist, d_rgb, d_dist, loss_out, sums, sizeof(float2) * nb,
-                   stream);
-  if (rc != NERFXL_OK) return rc;
-  rc = nerfxl_render_bwd(f, s, n_rays, rays_o, rays_d, d_rgb, nullptr, nullptr, d_dist, st->grad_tables,
-                         st->grad_mlp, workspace, L.total, stream);
+  // Sub-batches: forward, per-ray loss adjoints (normalised by all n_rays) and
+  // backward, the gradients accumulating over the sub-batches; the loss's
+  // block sums land at each sub-batch's own blocks, so the loss is the same
+  // fixed-order sum as in one pass.
+  for (int64_t b0 = 0; b0 < n_rays; b0 += Rb) {
+    const int64_t n = std::min<int64_t>(Rb, n_rays - b0);
+    const float* o = rays_o + 3 * b0;
+    const float* d = rays_d + 3 * b0;
+    const size_t Ln = layout(f, s, n, 1).total;
+    rc = nerfxl_render_fwd(f, s, n, o, d, rgb, depth, opacity, dist, workspace, Ln, stream);
+    if (rc != NERFXL_OK) return rc;
+    k_loss<<<(int)((n + kLossThreads - 1) / kLossThreads), kLossThreads, 0, stream>>>(
+        n, n_rays, rgb, dist, target_rgb + 3 * b0, lambda_dist, d_rgb, d_dist, sums + b0 / kLossThreads);
+    rc = kernel_launched("k_loss");
+    if (rc != NERFXL_OK) return rc;
+    rc = nerfxl_render_bwd(f, s, n, o, d, d_rgb, nullptr, nullptr, d_dist, st->grad_tables, st->grad_mlp, workspace,
+                           Ln, stream);
+    if (rc != NERFXL_OK) return rc;
+  }
+  k_loss_final<<<1, kFinalThreads, 0, stream>>>(sums, n_rays > 0 ? nb : 0, n_rays, lambda_dist, loss_out);
+  rc = kernel_launched("k_loss_final");
   if (rc != NERFXL_OK) return rc;
   // masters updated in FP32; 16-bit compute copies refreshed from them
   rc = launch_adam(n_tab, st->tables, st->grad_tables, st->m_tables, st->v_tables, opt,

@@ -85,7 +85,9 @@ SIGNATURES = {
     "nerfxl_render_bwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_loss": (C.c_int, [_i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_adam_update": (C.c_int, [_i64, _vp, _vp, _vp, _vp, C.c_void_p, _vp, _i32, _vp]),
+    "nerfxl_quantize_e4m3": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "nerfxl_step_workspace_bytes": (_sz, [_FP, _SP, _i64]),
+    "nerfxl_step_sub_batch": (_i64, [_FP, _SP, _i64, _sz]),
     "nerfxl_step": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_render_cameras_workspace_bytes": (_sz, [_FP, _SP, _i64]),
     "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),

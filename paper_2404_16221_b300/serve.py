@@ -4,9 +4,10 @@ Requests (a pinhole camera and an image size) arrive over time. The engine
 keeps the field and every admitted request's state on the device: its camera
 in a device camera table and its output image in a fixed-capacity device
 arena. A request is admitted when its image fits in the arena (admission by
-memory). Each iteration forms a batch of up to ``max_batch_rays`` pixels taken
-first-in-first-out from the admitted requests (a large request spans several
-batches; small ones share a batch with others) and renders it with one call,
+memory). Each iteration forms a batch of up to ``max_batch_rays`` pixels
+shared fairly among the admitted requests (water-filling: a request needing
+less than an equal share renders all of it; a large request spans several
+batches at an equal share) and renders it with one call,
 whose field kernel is a persistent launch over the whole batch. At most two
 batches are in flight, so requests that arrive while the GPU works are
 admitted into the next batch. Completion times are device times (CUDA events
@@ -120,11 +121,14 @@ def camera_rays(req: Request, device=None):
 class ServeEngine:
     def __init__(self, field: api.PartitionedField, samp: api.Sampling, max_batch_rays: int = 1 << 20,
                  arena_pixels: int = 1 << 26, max_cameras: int = 4096, max_inflight: int = 2,
-                 one_at_a_time: bool = False, keep_results: bool = False):
+                 one_at_a_time: bool = False, keep_results: bool = False, policy: str = "fair"):
         self.field, self.samp = field, samp
         self.dev = field.device
         self.max_batch = int(max_batch_rays)
         self.one_at_a_time = one_at_a_time
+        if policy not in ("fair", "fifo", "srpt"):
+            raise ValueError("policy must be fair, fifo or srpt")
+        self.policy = policy
         self.max_inflight = 1 if one_at_a_time else int(max_inflight)
         self.keep_results = keep_results
         self.arena = Arena(arena_pixels)
@@ -174,15 +178,63 @@ class ServeEngine:
         self.arena.release(req.slot, req.pixels)
         self.free_cams.append(req.cam)
 
+    def _shares(self, active: deque):
+        """Pixels each admitted request renders in the next batch. Fair share
+        by water-filling: requests that need less than an equal share of the
+        batch get all they need, and the rest is split evenly among the
+        others (in arrival order for the remainder), so a large image never
+        holds the small requests admitted behind it for more than one batch.
+        With one_at_a_time, the first request alone (FIFO). Other policies:
+        "fifo" fills the batch in arrival order; "srpt" in order of fewest
+        remaining pixels (ties by arrival)."""
+        if self.one_at_a_time:
+            r = active[0]
+            return [(r, min(r.pixels - r.next_pixel, self.max_batch))]
+        if self.policy in ("fifo", "srpt"):
+            order = list(active)
+            if self.policy == "srpt":
+                order.sort(key=lambda r: (r.pixels - r.next_pixel, r.arrival_s))
+            out, budget = [], self.max_batch
+            for r in order[:self.max_items]:
+                if budget == 0:
+                    break
+                t = min(r.pixels - r.next_pixel, budget)
+                out.append((r, t))
+                budget -= t
+            return out
+        reqs = list(active)[:self.max_items]
+        need = {id(r): r.pixels - r.next_pixel for r in reqs}
+        take = {id(r): 0 for r in reqs}
+        budget = self.max_batch
+        left = sorted(reqs, key=lambda r: need[id(r)])
+        while left and budget > 0:
+            share = budget // len(left)
+            if share == 0:  # fewer pixels than requests: one each, in arrival order
+                for r in sorted(left, key=lambda r: r.arrival_s)[:budget]:
+                    take[id(r)] += 1
+                break
+            r = left[0]
+            t = min(need[id(r)] - take[id(r)], share)
+            if t == need[id(r)] - take[id(r)]:
+                take[id(r)] += t
+                budget -= t
+                left.pop(0)
+            else:  # everyone left needs at least a share
+                for q in left:
+                    take[id(q)] += share
+                budget -= share * len(left)
+                for q in left[:budget]:  # the remainder, one pixel each
+                    take[id(q)] += 1
+                budget = 0
+        return [(r, take[id(r)]) for r in reqs if take[id(r)] > 0]
+
     def _launch(self, active: deque, buf: int):
-        """One batch: FIFO pixel ranges from the admitted requests."""
+        """One batch: each admitted request's next pixel range (fair share)."""
         items = (N.RayItemDesc * self.max_items).from_buffer(self.items_host[buf].numpy())
         n_items = 0
         n_rays = 0
         finished = []
-        while active and n_rays < self.max_batch and n_items < self.max_items:
-            req = active[0]
-            take = min(req.pixels - req.next_pixel, self.max_batch - n_rays)
+        for req, take in self._shares(active):
             it = items[n_items]
             it.batch_offset, it.first_pixel, it.out_offset = n_rays, req.next_pixel, req.slot + req.next_pixel
             it.camera, it.count = req.cam, take
@@ -190,9 +242,9 @@ class ServeEngine:
             n_rays += take
             req.next_pixel += take
             if req.next_pixel == req.pixels:
-                finished.append(active.popleft())
-            if self.one_at_a_time:
-                break
+                finished.append(req)
+        for r in finished:
+            active.remove(r)
         nbytes = n_items * ctypes.sizeof(N.RayItemDesc)
         self.items_dev[buf][:nbytes].copy_(self.items_host[buf][:nbytes], non_blocking=True)
         fd, sd = self.field.desc(), self.samp.desc()

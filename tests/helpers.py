@@ -139,3 +139,40 @@ def assert_first_adam_step(new, old, g_ref, lr, tol):
     rest = ~sure & ~zero
     if rest.any():
         assert np.abs(delta[rest]).max() <= lr * (1 + 1e-6) + 1e-6
+
+
+MLP_LAYER_SIZES = (32 * 64, 64 * 64, 64 * 4)  # W1, W2, W3 of one fused region block
+
+
+def e4m3_definition(mlp):
+    """The E4M3 weight quantisation written out in torch on the CPU (the
+    definition the library's nerfxl_quantize_e4m3 is checked against): per
+    region and layer scale = max(max|W|, 1e-30) / 448, W_q = e4m3(W / scale)
+    (round to nearest even). Returns (bytes [K][P] uint8, scales [K][3])."""
+    import torch
+
+    m = torch.as_tensor(mlp, dtype=torch.float32).cpu()
+    q = torch.empty(m.shape, dtype=torch.uint8)
+    scales = torch.empty(m.shape[0], 3, dtype=torch.float32)
+    off = 0
+    for li, n in enumerate(MLP_LAYER_SIZES):
+        blk = m[:, off:off + n]
+        s = blk.abs().amax(dim=1).clamp_min(1e-30) / 448.0
+        q[:, off:off + n] = (blk / s[:, None]).to(torch.float8_e4m3fn).view(torch.uint8)
+        scales[:, li] = s
+        off += n
+    return q, scales
+
+
+def e4m3_dequantize(q, scales):
+    """W = scale * e4m3 value, FP32 [K][P] (host)."""
+    import torch
+
+    q = torch.as_tensor(q).cpu()
+    out = q.view(torch.float8_e4m3fn).float()
+    sc = torch.as_tensor(scales).cpu()
+    off = 0
+    for li, n in enumerate(MLP_LAYER_SIZES):
+        out[:, off:off + n] *= sc[:, li:li + 1]
+        off += n
+    return out

@@ -226,6 +226,26 @@ def test_precision_sweep_city32():
     assert rows["e4m3"][0] <= 0.1 and rows["e4m3"][1] <= 0.02
 
 
+def test_e4m3_quantisation_matches_its_definition():
+    """nerfxl_quantize_e4m3 against the definition written out in torch on the
+    CPU: the same scales and the same E4M3 bytes, bit for bit; every weight
+    within half an E4M3 step of its quantised value."""
+    from paper_2404_16221_b300 import api
+
+    w = H.workload("city32", L=16, log2_T=14)
+    _, m = H.params(w)
+    m[3, :10] = 0.0  # a few zeros, and one layer of one region all zero (scale floor)
+    m[5, 32 * 64 + 64 * 64:] = 0.0
+    q, sc = api.quantize_mlp_e4m3(torch.from_numpy(m))
+    q_ref, sc_ref = H.e4m3_definition(m)
+    assert torch.equal(sc.cpu(), sc_ref)
+    assert torch.equal(q.cpu(), q_ref)
+    deq = H.e4m3_dequantize(q, sc).numpy()
+    v = np.abs(m) / np.repeat(sc_ref.numpy(), H.MLP_LAYER_SIZES, axis=1)
+    normal = v >= 2.0 ** -6  # E4M3 normals: 3 mantissa bits, half a step is 2^-4 relative
+    assert np.all(np.abs(deq - m)[normal] <= 2.0 ** -4 * np.abs(m)[normal] * (1 + 1e-6))
+
+
 def test_e4m3_matches_oracle_on_dequantized_weights():
     """E4M3 forward against the oracle run on the dequantized weights: what
     is left is the E4M3 rounding of activations (3 mantissa bits)."""
@@ -234,7 +254,7 @@ def test_e4m3_matches_oracle_on_dequantized_weights():
     w = H.workload("grid8", L=16, log2_T=14)
     t, m = H.params(w)
     q, sc = api.quantize_mlp_e4m3(torch.from_numpy(m))
-    mq = api.dequantize_mlp_e4m3(q, sc).numpy()
+    mq = H.e4m3_dequantize(q, sc).numpy()
     gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t), q, mlp_scales=sc)
     o, d = sy.workload_rays(w, 2048)
     ws = api.alloc_workspace(gf, H.sampling(w), len(o))

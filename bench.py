@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
-    ap.add_argument("--serve-policies", type=str, default="fair", help="serving sweep: batching policies")
-    ap.add_argument("--serve-batches", type=str, default=str(1 << 20), help="serving sweep: max rays per batch")
+    ap.add_argument("--serve-policies", type=str, default="srpt", help="serving sweep: batching policies")
+    ap.add_argument("--serve-batches", type=str, default=str(1 << 18), help="serving sweep: max rays per batch")
     return ap.parse_args()
 
 
@@ -631,11 +631,12 @@ def main():
         warm_reqs = serve.requests_from_stream(4, 200.0, ws_.seed + 17)
         serve.ServeEngine(sfield, ss, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(warm_reqs, realtime=False)
         with Clocks(local) as clk:
-            m = serve.ServeEngine(sfield, ss, max_batch_rays=1 << 20, arena_pixels=1 << 26).run(reqs)
+            m = serve.ServeEngine(sfield, ss, max_batch_rays=1 << 18, arena_pixels=1 << 26).run(reqs)
         m["clocks"] = clk.summary()
         forms["serve32_poisson200"] = {"serve": m, "requests": len(reqs),
-                                       "note": "FP16 tables + BF16 MLP, batches of up to 2^20 rays, 2 in flight, "
-                                               "arena 2^26 pixel slots; latency = arrival to device completion"}
+                                       "note": "FP16 tables + BF16 MLP, batches of up to 2^18 rays (fewest remaining "
+                                               "pixels first), 2 in flight, arena 2^26 pixel slots; latency = "
+                                               "arrival to device completion"}
         del sfield
         torch.cuda.empty_cache()
         ffield = mk_field(ws_, tc_, mc_, torch.float32, torch.float32)

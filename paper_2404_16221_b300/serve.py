@@ -4,10 +4,12 @@ Requests (a pinhole camera and an image size) arrive over time. The engine
 keeps the field and every admitted request's state on the device: its camera
 in a device camera table and its output image in a fixed-capacity device
 arena. A request is admitted when its image fits in the arena (admission by
-memory). Each iteration forms a batch of up to ``max_batch_rays`` pixels
-shared fairly among the admitted requests (water-filling: a request needing
-less than an equal share renders all of it; a large request spans several
-batches at an equal share) and renders it with one call,
+memory). Each iteration forms a batch of up to ``max_batch_rays`` pixels from
+the admitted requests, by default those with the fewest pixels left first
+(policy "srpt"; "fifo" takes them in arrival order, "fair" splits the batch
+evenly by water-filling), so a large image does not hold the small requests
+admitted behind it; a large request spans several batches. The batch is
+rendered with one call,
 whose field kernel is a persistent launch over the whole batch. At most two
 batches are in flight, so requests that arrive while the GPU works are
 admitted into the next batch. Completion times are device times (CUDA events
@@ -121,7 +123,7 @@ def camera_rays(req: Request, device=None):
 class ServeEngine:
     def __init__(self, field: api.PartitionedField, samp: api.Sampling, max_batch_rays: int = 1 << 20,
                  arena_pixels: int = 1 << 26, max_cameras: int = 4096, max_inflight: int = 2,
-                 one_at_a_time: bool = False, keep_results: bool = False, policy: str = "fair"):
+                 one_at_a_time: bool = False, keep_results: bool = False, policy: str = "srpt"):
         self.field, self.samp = field, samp
         self.dev = field.device
         self.max_batch = int(max_batch_rays)

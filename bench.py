@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
+    ap.add_argument("--only", type=str, default="",
+                    choices=["", "city32_fwd", "grid8_fwd", "grid8_train", "grid8_split_train"],
+                    help="profiler captures: run one form alone and print its own line")
+    ap.add_argument("--log2-t", type=int, default=0, help="--only: override the hash table size (log2 entries)")
     ap.add_argument("--serve-policies", type=str, default="srpt", help="serving sweep: batching policies")
     ap.add_argument("--serve-batches", type=str, default=str(1 << 18), help="serving sweep: max rays per batch")
     return ap.parse_args()
@@ -305,6 +309,60 @@ def bwd_tc_traffic():
     return BWD_TC_DRAM["bytes"]
 
 
+def single_form(args, dev):
+    """One form alone, for profiler captures (--only): its steps timed with
+    CUDA events and one JSON line printed. city32_fwd: the street/city
+    forward with FP16 tables and a BF16 MLP; grid8_fwd / grid8_train: the
+    mixed grid8 forward and training step; grid8_split_train: the split
+    representation's mixed training step. --profile-rays keeps the first N
+    rays (a smaller device footprint for captures)."""
+    import torch
+
+    from paper_2404_16221_b300 import api, native as N, synthetic as sy
+
+    name = args.only
+    w = sy.workload("city32" if name.startswith("city32") else "grid8")
+    if args.log2_t:
+        w.log2_T = args.log2_t
+    E = N.table_entries(w.level_res, w.log2_T)
+    if name == "grid8_split_train":
+        n_split = api.split_mlp_params(w.K, w.mlp_in, w.W)
+        t, _ = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(w.seed) * 7919 + 11)
+        m = torch.randn(n_split, generator=g, device=dev) * 0.1
+        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
+                                     device=dev, arch=N.ARCH_SPLIT)
+    else:
+        t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
+        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
+                                     device=dev)
+    if name.endswith("_fwd"):
+        del t, m  # a forward holds only the 16-bit field
+        torch.cuda.empty_cache()
+    o, d = sy.workload_rays(w)
+    if args.profile_rays > 0:
+        o, d = o[:args.profile_rays].copy(), d[:args.profile_rays].copy()
+    o, d = torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)
+    samp = api.Sampling(w.S, w.max_segments)
+    if name.endswith("_fwd"):
+        ws = api.alloc_workspace(field, samp, len(o))
+        step = lambda: api.render_fwd(field, samp, o, d, workspace=ws)
+    else:
+        tgt = torch.rand(len(o), 3, generator=torch.Generator().manual_seed(1002)).to(dev)
+        tr = api.Trainer(field, samp, master_tables=t, master_mlp=m)
+        step = lambda: tr.step(o, d, tgt)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    step_ms, kern_ms = time_steps(step, args.steps, flush, stream)
+    print(json.dumps({"only": name, "rays": len(o), "ms_per_step": statistics.mean(step_ms),
+                      "rays_per_s": len(o) / (statistics.mean(step_ms) / 1000.0),
+                      "dominant_kernel_ms": statistics.mean(kern_ms)}), flush=True)
+
+
 def serve_sweep(args, dev, rates):
     """p50/p99 latency and served rays/s of the city32 serving loop (FP16
     tables + BF16 MLP) at several Poisson arrival rates, args.serve_requests
@@ -356,6 +414,9 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     dev = torch.device("cuda", local)
+    if args.only:
+        single_form(args, dev)
+        return
     if args.serve_sweep:
         serve_sweep(args, dev, [float(r) for r in args.serve_sweep.split(",")])
         return

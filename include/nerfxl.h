@@ -440,6 +440,23 @@ nerfxl_status nerfxl_workspace_stats(const void* workspace, size_t ws_bytes, int
 nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
 
 /*
+ * Level-grouped gather of the tensor-core forward (BF16/FP16 MLP). The
+ * forward sweeps the regions one at a time, so one region's table is the
+ * working set of its random gathers; beyond some 30-40 MB (measured on B300)
+ * the L2 stops holding it and the gather reads the table many times from HBM.
+ * A field whose region table exceeds min_table_bytes is therefore gathered
+ * one group of levels (at most group_bytes of table, at least one level) at a
+ * time over all of a region's samples, into feature tiles of 64 bytes per
+ * sample row, which the MLP and render then read (results bit for bit those
+ * of the one-pass gather). Forward workspaces of such fields hold a window of
+ * window_tiles tiles of 128 rows (8 KiB each); a record-writing forward uses
+ * its record tiles. Process-wide; pass 0 for a default (32 MiB, 24 MiB, 65536
+ * tiles); set it before sizing workspaces. The paper has no counterpart (its
+ * GPUs each hold one region).
+ */
+nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles);
+
+/*
  * Instrumentation: the number of kernels this library has launched in this
  * process (all entry points, all devices and streams), for counting the
  * launches of a timed region. The paper has no counterpart.

@@ -202,6 +202,50 @@ __device__ __forceinline__ void gather4<__half2>(const LevelParams& lp, const __
   }
 }
 
+// One level l < L of one sample, with exactly the arithmetic of one level of
+// gather4 (the level-grouped gather computes the same features bit for bit).
+template <typename TabT>
+__device__ __forceinline__ float2 gather1(const LevelParams& lp, const TabT* __restrict__ table, const float u[3],
+                                          int l) {
+  int c[3];
+  float f[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  const TabT* tl = table + lp.off[l];
+  if ((lp.dense_mask >> l) & 1u) return gather_level<true>(lp, tl, l, c, f);
+  return gather_level<false>(lp, tl, l, c, f);
+}
+
+template <>
+__device__ __forceinline__ float2 gather1<__half2>(const LevelParams& lp, const __half2* __restrict__ table,
+                                                   const float u[3], int l) {
+  float s0 = 0.0f, s1 = 0.0f;
+  int c[3];
+  float f[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  const __half2* tl = table + lp.off[l];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+    const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+    const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+    const uint2 qv = __ldg(reinterpret_cast<const uint2*>(tl + (i0 & ~1u)));
+    const bool odd = i0 & 1u;
+    const uint32_t a = odd ? qv.y : qv.x, b = odd ? qv.x : qv.y;
+    const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&a));
+    float2 v1;
+    if ((i0 ^ i1) == 1u) v1 = __half22float2(*reinterpret_cast<const __half2*>(&b));
+    else v1 = __half22float2(__ldg(tl + i1));
+    const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+    const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
+    s0 = fmaf(w0, v0.x, s0);
+    s1 = fmaf(w0, v0.y, s1);
+    s0 = fmaf(w1, v1.x, s0);
+    s1 = fmaf(w1, v1.y, s1);
+  }
+  return make_float2(s0, s1);
+}
 
 // MLP with weights staged in shared memory as W1t [64][32] (row n holds
 // column n of W1), W2t [64][64], W3 [64][4]. Layer 2 and 3 are fused per

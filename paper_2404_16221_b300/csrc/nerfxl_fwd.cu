@@ -688,6 +688,14 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.smp4 = take(sizeof(float4) * (size_t)R * mc * kWarp);
     L.smp2 = take(sizeof(float2) * (size_t)R * mc * kWarp);
   }
+  // last, so that the regions before it agree between forward and backward
+  // layouts; a backward layout with records gathers into its record tiles
+  L.gfeat = 0;
+  L.gfeat_tiles = 0;
+  if (grouped_gather(f) && L.rec_tiles == 0) {
+    L.gfeat_tiles = std::min<int64_t>((L.chunk_cap + 3) / 4, gather_window_tiles());
+    L.gfeat = take(kRecFeatBytes * (size_t)L.gfeat_tiles);
+  }
   L.total = off;
   L.max_seg = ms;
   L.max_chunk = mc;

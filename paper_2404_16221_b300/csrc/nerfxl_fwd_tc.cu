@@ -217,9 +217,13 @@ struct FwdTcParams {
   float4* partials;
   RecordOut rec;  // the backward's per-tile records, or all NULL
   int32_t* err;
+  // Level-grouped gather (kFeatIn): the features of tile t come from
+  // feat_in + (t - w0) * kRecFeatBytes / 16; the kernel covers tiles w0..w1-1.
+  const uint4* feat_in;
+  int64_t w0, w1;
 };
 
-template <bool kF16Table, int kKind, bool kRec, bool kSplit>
+template <bool kF16Table, int kKind, bool kRec, bool kSplit, bool kFeatIn = false>
 __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   static_assert(!kSplit || kKind != kKindE4M3, "the split form is a 16-bit forward");
   using Op = MlpOp<kKind>;
@@ -255,12 +259,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
 
   const uint32_t c1 = sbase + kOffC1, c3 = sbase + kOffC3;
   if (kSplit) load_color_tc<kKind == kKindBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm);
-  const int n_sub = *p.n_tiles * (kChunksPerTile / kTcChunks);
+  const int n_all = *p.n_tiles * (kChunksPerTile / kTcChunks);
+  const int n_sub = (int)(p.w1 < (int64_t)n_all ? p.w1 : (int64_t)n_all);
   int region = -1;
   const TabT* table = nullptr;
   uint32_t phase = 0;
   bool failed = false;
-  for (int t = blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
+  // kFeatIn: this thread's 16 bytes of the next tile's features, loaded one
+  // tile ahead so that the HBM latency hides behind the current tile
+  uint4 feat_next = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t feat_chunk = row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u));
+  if (kFeatIn && (int)p.w0 + (int)blockIdx.x < n_sub)
+    feat_next = __ldcs(p.feat_in + (size_t)blockIdx.x * (kRecFeatBytes / 16) + feat_chunk);
+  for (int t = (int)p.w0 + blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
     const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
     if (k != region) {
       __syncthreads();
@@ -312,10 +323,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         float x[3];
         sample_point(o, d, tbar, x);
         region_coord(p.boxes + 6 * k, x, u);
-        gather4<TabT>(p.lp, table, u, 4 * g, f8);
+        if (!kFeatIn) gather4<TabT>(p.lp, table, u, 4 * g, f8);
       }
     }
-    Op::store8(a0, row, g, f8);
+    if (kFeatIn) {  // the level-grouped gather's features: 16 bytes of row `row`, levels 4g..4g+3
+      const uint4 pk = feat_next;
+      if (t + (int)gridDim.x < n_sub)
+        feat_next = __ldcs(p.feat_in + (size_t)(t + gridDim.x - p.w0) * (kRecFeatBytes / 16) + feat_chunk);
+      tc::st_shared_v4(a0 + tc::sw128_chunk(row, g), pk.x, pk.y, pk.z, pk.w);
+    } else {
+      Op::store8(a0, row, g, f8);
+    }
     if (kRec) {
       // Records for the backward: the features exactly as the first MMA reads
       // them, the sample's region coordinates / position / length (thread g
@@ -328,7 +346,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
                                   Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
                                   Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
+      if (!kFeatIn)  // with the grouped gather the records already hold them
+        __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
       __stcs(geo + g * kTcRows + row, g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr)));
       if (kSplit && g == 1) {  // the split form's colour input: the ray direction, rows 5..7
@@ -547,17 +566,53 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
+  p.feat_in = nullptr;
+  p.w0 = 0;
+  p.w1 = INT64_MAX;
   const size_t smem = kTcSmemFixed + sizeof(int32_t) * (f->K + 1);
   const int kind = f->mlp_dtype == NERFXL_BF16 ? kKindBF16 : (f->mlp_dtype == NERFXL_F16 ? kKindF16 : kKindE4M3);
   if (kind == kKindE4M3 && !f->mlp_scales) return set_error(NERFXL_E_INVALID, "E4M3 MLP needs mlp_scales");
   const bool f16tab = f->table_dtype == NERFXL_F16;
   const bool recs = rec.feat != nullptr;
   if (recs && kind == kKindE4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
+  const bool split = f->arch == NERFXL_ARCH_SPLIT;
+  if (split && kind == kKindE4M3)
+    return set_error(NERFXL_E_UNSUPPORTED, "the split representation's tensor-core form is a BF16/FP16 forward");
+  const bool bf = kind == kKindBF16;
+  const int64_t max_tiles = L.chunk_cap / kTcChunks;
+  if (grouped_gather(f)) {
+    // Level-grouped gather into feature tiles (the record tiles when the
+    // forward writes records, else the layout's window buffer), then the MLP
+    // and render from those tiles, window by window.
+    uint4* feat = recs ? rec.feat : reinterpret_cast<uint4*>(ws + L.gfeat);
+    const int64_t window = recs ? max_tiles : L.gfeat_tiles;
+    if (!feat || window < 1) return set_error(NERFXL_E_WORKSPACE, "workspace has no feature tiles for the grouped gather");
+    void (*kern)(FwdTcParams) = nullptr;
+    if (split)
+      kern = recs ? (bf ? k_field_fwd_tc<true, kKindBF16, true, true, true> : k_field_fwd_tc<true, kKindF16, true, true, true>)
+                  : (bf ? k_field_fwd_tc<true, kKindBF16, false, true, true> : k_field_fwd_tc<true, kKindF16, false, true, true>);
+    else
+      kern = recs ? (bf ? k_field_fwd_tc<true, kKindBF16, true, false, true> : k_field_fwd_tc<true, kKindF16, true, false, true>)
+                  : (bf ? k_field_fwd_tc<true, kKindBF16, false, false, true> : k_field_fwd_tc<true, kKindF16, false, false, true>);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return launch_check("k_field_fwd_tc smem attribute");
+    profile_mark(0, stream);
+    for (int64_t w0 = 0; w0 < max_tiles; w0 += window) {
+      const int64_t w1 = std::min(max_tiles, w0 + window);
+      nerfxl_status st = launch_gather_groups(f, sp, lp, rays_o, rays_d, ws, L, feat, w0, w1, stream);
+      if (st != NERFXL_OK) return st;
+      p.feat_in = feat;
+      p.w0 = w0;
+      p.w1 = w1;
+      kern<<<fwd_grid(w1 - w0, 2), kTcThreads, smem, stream>>>(p);
+      st = kernel_launched("k_field_fwd_tc");
+      if (st != NERFXL_OK) return st;
+    }
+    profile_mark(1, stream);
+    return NERFXL_OK;
+  }
   void (*kern)(FwdTcParams) = nullptr;
-  if (f->arch == NERFXL_ARCH_SPLIT) {
-    if (kind == kKindE4M3)
-      return set_error(NERFXL_E_UNSUPPORTED, "the split representation's tensor-core form is a BF16/FP16 forward");
-    const bool bf = kind == kKindBF16;
+  if (split) {
     if (f16tab)
       kern = recs ? (bf ? k_field_fwd_tc<true, kKindBF16, true, true> : k_field_fwd_tc<true, kKindF16, true, true>)
                   : (bf ? k_field_fwd_tc<true, kKindBF16, false, true> : k_field_fwd_tc<true, kKindF16, false, true>);
@@ -579,7 +634,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return launch_check("k_field_fwd_tc smem attribute");
-  const int grid = fwd_grid(L.chunk_cap / kTcChunks, 2);
+  const int grid = fwd_grid(max_tiles, 2);
   profile_mark(0, stream);
   kern<<<grid, kTcThreads, smem, stream>>>(p);
   profile_mark(1, stream);

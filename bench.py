@@ -52,9 +52,13 @@ def parse():
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
     ap.add_argument("--only", type=str, default="",
-                    choices=["", "city32_fwd", "grid8_fwd", "grid8_train", "grid8_split_train"],
+                    choices=["", "city32_fwd", "city32_train", "grid8_fwd", "grid8_train", "grid8_split_train"],
                     help="profiler captures: run one form alone and print its own line")
     ap.add_argument("--log2-t", type=int, default=0, help="--only: override the hash table size (log2 entries)")
+    ap.add_argument("--group-min-mb", type=float, default=0.0,
+                    help="--only: region-table size above which the forward gathers by level groups (0: default)")
+    ap.add_argument("--group-mb", type=float, default=0.0, help="--only: table bytes per level group (0: default)")
+    ap.add_argument("--window-tiles", type=int, default=0, help="--only: tiles per gather window (0: default)")
     ap.add_argument("--serve-policies", type=str, default="srpt", help="serving sweep: batching policies")
     ap.add_argument("--serve-batches", type=str, default=str(1 << 18), help="serving sweep: max rays per batch")
     return ap.parse_args()
@@ -321,6 +325,9 @@ def single_form(args, dev):
     from paper_2404_16221_b300 import api, native as N, synthetic as sy
 
     name = args.only
+    if args.group_min_mb > 0 or args.group_mb > 0 or args.window_tiles > 0:
+        N.check(N.lib().nerfxl_set_gather_groups(int(args.group_min_mb * (1 << 20)), int(args.group_mb * (1 << 20)),
+                                                 args.window_tiles), "gather groups")
     w = sy.workload("city32" if name.startswith("city32") else "grid8")
     if args.log2_t:
         w.log2_T = args.log2_t
@@ -350,7 +357,8 @@ def single_form(args, dev):
         step = lambda: api.render_fwd(field, samp, o, d, workspace=ws)
     else:
         tgt = torch.rand(len(o), 3, generator=torch.Generator().manual_seed(1002)).to(dev)
-        tr = api.Trainer(field, samp, master_tables=t, master_mlp=m)
+        tr = api.Trainer(field, samp, master_tables=t, master_mlp=m,
+                         workspace_cap=(4 << 30) if name == "city32_train" else None)
         step = lambda: tr.step(o, d, tgt)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()

@@ -446,13 +446,15 @@ nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
  * the L2 stops holding it and the gather reads the table many times from HBM.
  * A field whose region table exceeds min_table_bytes is therefore gathered
  * one group of levels (at most group_bytes of table, at least one level) at a
- * time over all of a region's samples, into feature tiles of 64 bytes per
- * sample row, which the MLP and render then read (results bit for bit those
- * of the one-pass gather). Forward workspaces of such fields hold a window of
- * window_tiles tiles of 128 rows (8 KiB each); a record-writing forward uses
- * its record tiles. Process-wide; pass 0 for a default (32 MiB, 24 MiB, 65536
- * tiles); set it before sizing workspaces. The paper has no counterpart (its
- * GPUs each hold one region).
+ * time over all of a region's samples, into level-major feature words (4
+ * bytes per level per sample row), which the MLP and render then read
+ * (results bit for bit those of the one-pass gather). Workspaces of such
+ * fields hold a window of window_tiles tiles of 128 rows (L x 512 bytes
+ * each). Process-wide; pass 0 for a default (64 MiB, 64 MiB, 65536
+ * tiles: on the street/city field, 2 groups of a 96 MB FP16 region table ran
+ * faster than 3 to 11 smaller ones, whose extra passes cost more than their
+ * fewer L2 misses save); set it before sizing workspaces. The paper has no
+ * counterpart (its GPUs each hold one region).
  */
 nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles);
 

@@ -638,11 +638,13 @@ int effective_max_seg(const nerfxl_field* f, const nerfxl_sampling* s) {
 int max_chunks(int S, int max_seg) { return max_seg + (S - 1) / kWarp; }
 
 RecordOut record_out(char* ws, const Layout& L) {
-  RecordOut r = {nullptr, nullptr, nullptr};
+  RecordOut r = {nullptr, nullptr, nullptr, nullptr, 0};
   if (L.rec_tiles == 0) return r;
   r.feat = reinterpret_cast<uint4*>(ws + L.rec_feat);
   r.geom = reinterpret_cast<float*>(ws + L.rec_geom);
   r.pos = reinterpret_cast<int32_t*>(ws + L.rec_pos);
+  r.gfeat = L.gfeat_tiles ? reinterpret_cast<uint32_t*>(ws + L.gfeat) : nullptr;
+  r.gfeat_tiles = L.gfeat_tiles;
   return r;
 }
 
@@ -689,12 +691,12 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.smp2 = take(sizeof(float2) * (size_t)R * mc * kWarp);
   }
   // last, so that the regions before it agree between forward and backward
-  // layouts; a backward layout with records gathers into its record tiles
+  // layouts
   L.gfeat = 0;
   L.gfeat_tiles = 0;
-  if (grouped_gather(f) && L.rec_tiles == 0) {
+  if (grouped_gather(f)) {
     L.gfeat_tiles = std::min<int64_t>((L.chunk_cap + 3) / 4, gather_window_tiles());
-    L.gfeat = take(kRecFeatBytes * (size_t)L.gfeat_tiles);
+    L.gfeat = take(sizeof(uint32_t) * 128 * (size_t)f->L * (size_t)L.gfeat_tiles);
   }
   L.total = off;
   L.max_seg = ms;
@@ -915,7 +917,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   if (tc_mlp && (s->flags & NERFXL_SAMPLE_COMPOSITE))
     return set_error(NERFXL_E_UNSUPPORTED, "sample-level composition is built for the FP32 MLP only");
   if (tc_mlp) {
-    RecordOut rec = {nullptr, nullptr, nullptr};
+    RecordOut rec = {nullptr, nullptr, nullptr, nullptr, 0};
     if (s->flags & NERFXL_SAVE_FEATURES) {
       if (f->mlp_dtype == NERFXL_E4M3) return set_error(NERFXL_E_UNSUPPORTED, "E4M3 is forward-only");
       const Layout LB = layout(f, s, n_rays, 1);

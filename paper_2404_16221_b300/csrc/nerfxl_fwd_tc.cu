@@ -217,9 +217,10 @@ struct FwdTcParams {
   float4* partials;
   RecordOut rec;  // the backward's per-tile records, or all NULL
   int32_t* err;
-  // Level-grouped gather (kFeatIn): the features of tile t come from
-  // feat_in + (t - w0) * kRecFeatBytes / 16; the kernel covers tiles w0..w1-1.
-  const uint4* feat_in;
+  // Level-grouped gather (kFeatIn): level l of row r of tile t is the word
+  // feat_in[(l * window + t - w0) * 128 + r]; the kernel covers tiles w0..w1-1.
+  const uint32_t* feat_in;
+  int64_t window;
   int64_t w0, w1;
 };
 
@@ -265,12 +266,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
   const TabT* table = nullptr;
   uint32_t phase = 0;
   bool failed = false;
-  // kFeatIn: this thread's 16 bytes of the next tile's features, loaded one
-  // tile ahead so that the HBM latency hides behind the current tile
-  uint4 feat_next = make_uint4(0u, 0u, 0u, 0u);
-  const uint32_t feat_chunk = row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u));
-  if (kFeatIn && (int)p.w0 + (int)blockIdx.x < n_sub)
-    feat_next = __ldcs(p.feat_in + (size_t)blockIdx.x * (kRecFeatBytes / 16) + feat_chunk);
+  // kFeatIn: this thread's four levels (4g..4g+3) of the next tile's
+  // features, loaded one tile ahead so that the HBM latency hides behind the
+  // current tile
+  uint32_t feat_next[4] = {0u, 0u, 0u, 0u};
+  auto load_feat = [&](int64_t tl, uint32_t* w) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = 4 * g + j < p.lp.L ? __ldcs(p.feat_in + ((size_t)(4 * g + j) * p.window + tl) * kTcRows + row) : 0u;
+  };
+  if (kFeatIn && (int)p.w0 + (int)blockIdx.x < n_sub) load_feat(blockIdx.x, feat_next);
   for (int t = (int)p.w0 + blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
     const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
     if (k != region) {
@@ -326,11 +331,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         if (!kFeatIn) gather4<TabT>(p.lp, table, u, 4 * g, f8);
       }
     }
-    if (kFeatIn) {  // the level-grouped gather's features: 16 bytes of row `row`, levels 4g..4g+3
-      const uint4 pk = feat_next;
-      if (t + (int)gridDim.x < n_sub)
-        feat_next = __ldcs(p.feat_in + (size_t)(t + gridDim.x - p.w0) * (kRecFeatBytes / 16) + feat_chunk);
-      tc::st_shared_v4(a0 + tc::sw128_chunk(row, g), pk.x, pk.y, pk.z, pk.w);
+    uint4 fw = make_uint4(0u, 0u, 0u, 0u);  // kFeatIn: this thread's packed features
+    if (kFeatIn) {  // the level-grouped gather's words of row `row`, levels 4g..4g+3
+      fw = make_uint4(feat_next[0], feat_next[1], feat_next[2], feat_next[3]);
+      if (t + (int)gridDim.x < n_sub) load_feat(t + gridDim.x - p.w0, feat_next);
+      tc::st_shared_v4(a0 + tc::sw128_chunk(row, g), fw.x, fw.y, fw.z, fw.w);
     } else {
       Op::store8(a0, row, g, f8);
     }
@@ -342,12 +347,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       // (Tn, w, pair, sigma and rgb follow from the chunk render below).
       // Streaming stores: the records are read once, by the backward, and
       // should not push the region's tables out of L2 meanwhile.
-      const uint4 pk = make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
-                                  Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
-                                  Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
-                                  Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      if (!kFeatIn)  // with the grouped gather the records already hold them
-        __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
+      const uint4 pk = kFeatIn ? fw
+                               : make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
+                                            Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
+                                            Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
+                                            Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
+      __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
       __stcs(geo + g * kTcRows + row, g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr)));
       if (kSplit && g == 1) {  // the split form's colour input: the ray direction, rows 5..7
@@ -567,6 +572,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   p.partials = reinterpret_cast<float4*>(ws + L.partials);
   p.err = reinterpret_cast<int32_t*>(ws + L.hdr);
   p.feat_in = nullptr;
+  p.window = 0;
   p.w0 = 0;
   p.w1 = INT64_MAX;
   const size_t smem = kTcSmemFixed + sizeof(int32_t) * (f->K + 1);
@@ -581,11 +587,11 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
   const bool bf = kind == kKindBF16;
   const int64_t max_tiles = L.chunk_cap / kTcChunks;
   if (grouped_gather(f)) {
-    // Level-grouped gather into feature tiles (the record tiles when the
-    // forward writes records, else the layout's window buffer), then the MLP
-    // and render from those tiles, window by window.
-    uint4* feat = recs ? rec.feat : reinterpret_cast<uint4*>(ws + L.gfeat);
-    const int64_t window = recs ? max_tiles : L.gfeat_tiles;
+    // Level-grouped gather into the layout's window of level-major feature
+    // words (the backward layout's when the forward writes records), then the
+    // MLP and render from those words, window by window.
+    uint32_t* feat = recs ? rec.gfeat : reinterpret_cast<uint32_t*>(ws + L.gfeat);
+    const int64_t window = recs ? rec.gfeat_tiles : L.gfeat_tiles;
     if (!feat || window < 1) return set_error(NERFXL_E_WORKSPACE, "workspace has no feature tiles for the grouped gather");
     void (*kern)(FwdTcParams) = nullptr;
     if (split)
@@ -599,9 +605,10 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
     profile_mark(0, stream);
     for (int64_t w0 = 0; w0 < max_tiles; w0 += window) {
       const int64_t w1 = std::min(max_tiles, w0 + window);
-      nerfxl_status st = launch_gather_groups(f, sp, lp, rays_o, rays_d, ws, L, feat, w0, w1, stream);
+      nerfxl_status st = launch_gather_groups(f, sp, lp, rays_o, rays_d, ws, L, feat, window, w0, w1, stream);
       if (st != NERFXL_OK) return st;
       p.feat_in = feat;
+      p.window = window;
       p.w0 = w0;
       p.w1 = w1;
       kern<<<fwd_grid(w1 - w0, 2), kTcThreads, smem, stream>>>(p);

@@ -3,18 +3,19 @@
 //
 // The tensor-core forward sweeps the regions one at a time, so a region's
 // whole table (every level) is the working set of the gather. Random 4- or
-// 8-byte gathers keep their L2 hit rate only while that set stays below some
-// 30-40 MB on this GPU (measured: 95 % at 27 MB, 44 % at 50 MB, 27 % at the
-// 96 MB of a street/city region with 2^21-entry levels, where the forward then
-// reads 214x the tables' bytes from HBM). This pass instead sweeps (region,
-// group of levels) pairs: for every tile of the region, the features of one
-// group of levels (a working set under the budget), then the next group. It
-// writes each row's 16-bit features into a feature-tile buffer in the layout
-// the first MMA reads (the backward's record layout: 16-byte chunk c of row r at
-// byte 64 r + 16 (c ^ (r / 2 mod 4)), levels 4c..4c+3), and the tensor-core
-// forward then reads the features from there instead of gathering. The
-// features equal the fused gather's bit for bit (same per-level arithmetic,
-// same rounding to the MLP's 16-bit type).
+// 8-byte gathers keep their L2 hit rate only while that set stays small
+// (measured on the street/city shapes: 95 % at 27 MB, 44 % at 50 MB, 27 % at
+// the 96 MB of a region with 2^21-entry levels, where the forward then reads
+// 214x the tables' bytes from HBM). This pass instead sweeps (region, group
+// of levels) pairs: for every tile of the region, the features of one group
+// of levels, then the next group. It writes each row's 16-bit features as
+// level-major words (whole sectors: 512 contiguous bytes per level and tile),
+// and the tensor-core forward then reads the features from there instead of
+// gathering. The features equal the fused gather's bit for bit (same
+// per-level arithmetic, same rounding to the MLP's 16-bit type). Each group is
+// one more pass over the region's samples (positions, launch, feature words),
+// so the groups are as large as still pays: two groups of a 96 MB table beat
+// three to eleven smaller ones.
 //
 // Work items are (region, group, tile) in that order over a window of tiles;
 // the persistent CTAs take consecutive items, so the GPU works on one
@@ -46,8 +47,9 @@ struct GatherGroupsParams {
   const int32_t* base;
   const Slot* chunks;
   const int32_t* n_tiles;
-  uint4* feat;     // feature tiles, tile t at feat + (t - w0) * kRecFeatBytes / 16
-  int64_t w0, w1;  // the window of 4-chunk tiles
+  uint32_t* feat;  // level-major words: level l, tile t, row r at feat[(l * window + t - w0) * 128 + r]
+  int64_t window;  // tiles per level in feat
+  int64_t w0, w1;  // the window of 4-chunk tiles (w1 - w0 <= window)
   int n_groups;
   int32_t g_lo[kMaxLevels + 1];  // group g holds levels g_lo[g] .. g_lo[g + 1] - 1
 };
@@ -119,20 +121,14 @@ __global__ void __launch_bounds__(kGThreads, 4) k_gather_groups(GatherGroupsPara
       }
     }
     const TabT* table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
-    char* dst = reinterpret_cast<char*>(p.feat) + (size_t)(t - wa) * kRecFeatBytes + 64 * row;
-    const uint32_t swz = (row >> 1) & 3u;
+    // level-major words: the 128 rows of a tile write 512 contiguous bytes per
+    // level, whole sectors (a partly written sector would cost L2 a read
+    // from HBM to merge)
+    uint32_t* dst = p.feat + (size_t)(t - wa) * kGRows + row;
     const int l_end = p.g_lo[g + 1];
     for (int l = p.g_lo[g]; l < l_end; ++l) {
-      const float2 v0 = valid ? gather1<TabT>(p.lp, table, u, l) : make_float2(0.0f, 0.0f);
-      const uint32_t w0 = Half2Of<kBF16>::pack(v0.x, v0.y);
-      uint32_t* at = reinterpret_cast<uint32_t*>(dst + 16 * (((uint32_t)l >> 2) ^ swz) + 4 * (l & 3));
-      if (!(l & 1) && l + 1 < l_end) {  // an aligned level pair: one 8-byte store
-        const float2 v1 = valid ? gather1<TabT>(p.lp, table, u, l + 1) : make_float2(0.0f, 0.0f);
-        __stcs(reinterpret_cast<uint2*>(at), make_uint2(w0, Half2Of<kBF16>::pack(v1.x, v1.y)));
-        ++l;
-      } else {
-        __stcs(at, w0);
-      }
+      const float2 v = valid ? gather1<TabT>(p.lp, table, u, l) : make_float2(0.0f, 0.0f);
+      __stcs(dst + (size_t)l * p.window * kGRows, Half2Of<kBF16>::pack(v.x, v.y));
     }
   }
 }
@@ -171,8 +167,8 @@ int gather_groups(const nerfxl_field* f, const LevelParams& lp, int32_t* g_lo) {
 }
 
 nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L, uint4* feat,
-                                   int64_t w0, int64_t w1, cudaStream_t stream) {
+                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L, uint32_t* feat,
+                                   int64_t window, int64_t w0, int64_t w1, cudaStream_t stream) {
   GatherGroupsParams p;
   p.rays_o = rays_o;
   p.rays_d = rays_d;
@@ -187,6 +183,7 @@ nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, 
   p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.feat = feat;
+  p.window = window;
   p.w0 = w0;
   p.w1 = w1;
   p.n_groups = gather_groups(f, lp, p.g_lo);

@@ -34,9 +34,9 @@ struct Layout {
   // Sample-level composition (NERFXL_SAMPLE_COMPOSITE; 0 otherwise):
   size_t smp4;       // float4[R][max_chunk][32]: sigma, r, g, b per sample slot
   size_t smp2;       // float2[R][max_chunk][32]: tbar - tn, delta per sample slot
-  // Level-grouped gather (fields whose region table exceeds kGroupMinBytes;
-  // forward layouts, and backward ones without records): a window of
-  // gfeat_tiles feature tiles of kRecFeatBytes each.
+  // Level-grouped gather (fields whose region table exceeds kGroupMinBytes):
+  // a window of gfeat_tiles tiles of level-major feature words,
+  // [L][gfeat_tiles][128] uint32 (two 16-bit features per word).
   size_t gfeat;
   int64_t gfeat_tiles;
   size_t total;
@@ -93,6 +93,8 @@ struct RecordOut {
   uint4* feat;
   float* geom;
   int32_t* pos;
+  uint32_t* gfeat;  // the backward layout's level-grouped gather window (or NULL)
+  int64_t gfeat_tiles;
 };
 RecordOut record_out(char* ws, const Layout& L);
 
@@ -100,8 +102,8 @@ RecordOut record_out(char* ws, const Layout& L);
 // kGroupMinBytes is gathered one group of levels at a time (groups of at most
 // kGroupBytes, at least one level), over windows of at most
 // kGatherWindowTiles 4-chunk tiles, into feature tiles the forward then reads.
-constexpr size_t kGroupMinBytes = size_t(32) << 20;
-constexpr size_t kGroupBytes = size_t(24) << 20;
+constexpr size_t kGroupMinBytes = size_t(64) << 20;
+constexpr size_t kGroupBytes = size_t(64) << 20;
 constexpr int64_t kGatherWindowTiles = 65536;
 // The values in force (nerfxl_set_gather_groups may change them).
 size_t group_min_bytes();
@@ -109,8 +111,8 @@ int64_t gather_window_tiles();
 bool grouped_gather(const nerfxl_field* f);
 int gather_groups(const nerfxl_field* f, const LevelParams& lp, int32_t* g_lo);
 nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
-                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L, uint4* feat,
-                                   int64_t w0, int64_t w1, cudaStream_t stream);
+                                   const float* rays_o, const float* rays_d, char* ws, const Layout& L, uint32_t* feat,
+                                   int64_t window, int64_t w0, int64_t w1, cudaStream_t stream);
 
 // Tensor-core field backward (16-bit MLP), from the per-tile records.
 nerfxl_status launch_field_bwd_tc(const nerfxl_field* f, const LevelParams& lp, char* ws, const Layout& L,

@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--serve-sweep", type=str, default="",
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
     ap.add_argument("--only", type=str, default="",
-                    choices=["", "city32_fwd", "city32_train", "grid8_fwd", "grid8_train", "grid8_split_train"],
+                    choices=["", "city32_fwd", "city32_train", "grid8_fwd", "grid8_train", "grid8_train_fp32",
+                             "grid8_split_train"],
                     help="profiler captures: run one form alone and print its own line")
     ap.add_argument("--log2-t", type=int, default=0, help="--only: override the hash table size (log2 entries)")
     ap.add_argument("--group-min-mb", type=float, default=0.0,
@@ -340,6 +341,9 @@ def single_form(args, dev):
         m = torch.randn(n_split, generator=g, device=dev) * 0.1
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
                                      device=dev, arch=N.ARCH_SPLIT)
+    elif name == "grid8_train_fp32":
+        t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
+        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t, m, device=dev)
     else:
         t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
@@ -357,7 +361,8 @@ def single_form(args, dev):
         step = lambda: api.render_fwd(field, samp, o, d, workspace=ws)
     else:
         tgt = torch.rand(len(o), 3, generator=torch.Generator().manual_seed(1002)).to(dev)
-        tr = api.Trainer(field, samp, master_tables=t, master_mlp=m,
+        masters = {} if name == "grid8_train_fp32" else {"master_tables": t, "master_mlp": m}
+        tr = api.Trainer(field, samp, **masters,
                          workspace_cap=(4 << 30) if name == "city32_train" else None)
         step = lambda: tr.step(o, d, tgt)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)

@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t R, SampParams sp,
 // k_field_bwd_f32
 
 constexpr int kBwdThreads = kChunksPerTile * kWarp;  // 256 samples per tile
-constexpr int kFeatPitch = 36;                        // cols 32..35 hold dL/d(raw outputs)
 constexpr int kActPitch = 68;
 
 struct BwdParams {
@@ -123,8 +122,6 @@ struct BwdParams {
   float* grad_mlp;       // [K][kMlpParams] accumulated
 };
 
-constexpr size_t kBwdSmemFloats =
-    2 * kMlpParams + (size_t)kBwdThreads * kFeatPitch + 2 * (size_t)kBwdThreads * kActPitch;
 
 // Scatter dL/dfeat into the region table: entry += corner weight * gfeat.
 __device__ __forceinline__ void scatter_table_grad(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
@@ -166,25 +163,128 @@ __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, 
   }
 }
 
+// The MLP part of the FP32 backward runs as register-tiled GEMMs over the
+// 256-sample tile (each thread owns an 8 x 8, 8 x 4 or 4 x 4 block of
+// outputs, so a weight or activation read from shared memory feeds 4-8
+// multiply-adds). Activations are stored unit-major, A[unit][sample] with a
+// pitch of kUPitch floats: a thread's samples are the two float4 groups
+// 4 b .. 4 b + 3 and 128 + 4 b .. (b = thread % 32), and unit rows sit 4 banks
+// apart, so that both the sample-blocked and the unit-blocked products read
+// shared memory without bank conflicts.
+constexpr int kUPitch = 260;
+constexpr size_t kBwdSmemFloatsT = 2 * (size_t)kMlpParams + (size_t)kUPitch * (kIn + 2 * kWidth + kOut);
+
+// acc[i][j] = sum_k A[k][samples i] B[k][n0 + j]; A unit-major, B row-major [K][64].
+template <int K>
+__device__ __forceinline__ void tile_gemm_ab(const float* __restrict__ A, const float* __restrict__ B, int sb, int n0,
+                                             float acc[8][8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kUPitch + 4 * sb);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kUPitch + 128 + 4 * sb);
+    const float4 b0 = *reinterpret_cast<const float4*>(B + k * kWidth + n0);
+    const float4 b1 = *reinterpret_cast<const float4*>(B + k * kWidth + n0 + 4);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
+
+// acc[i][j] = sum_k A[k][samples i] W[j0 + j][k]; W row-major with rows of 64
+// (the transposed weight of a dX product), NJ of its rows.
+template <int K, int NJ>
+__device__ __forceinline__ void tile_gemm_abt(const float* __restrict__ A, const float* __restrict__ W, int sb, int j0,
+                                              float acc[8][NJ]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kUPitch + 4 * sb);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kUPitch + 128 + 4 * sb);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    float b[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) b[j] = W[(j0 + j) * kWidth + k];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
+
+// Weight gradient: acc[a][c] = sum_s P[ib + 16 a][s] Q[nb + 16 c][s] over the
+// 256 samples (both unit-major).
+template <int RA>
+__device__ __forceinline__ void tile_gemm_dw(const float* __restrict__ P, const float* __restrict__ Q, int ib, int nb,
+                                             float acc[RA][4]) {
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+#pragma unroll 2
+  for (int s = 0; s < kBwdThreads; s += 4) {
+    float4 pv[RA], qv[4];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) pv[a] = *reinterpret_cast<const float4*>(P + (ib + 16 * a) * kUPitch + s);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) qv[c] = *reinterpret_cast<const float4*>(Q + (nb + 16 * c) * kUPitch + s);
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc[a][c] = fmaf(pv[a].x, qv[c].x, acc[a][c]);
+        acc[a][c] = fmaf(pv[a].y, qv[c].y, acc[a][c]);
+        acc[a][c] = fmaf(pv[a].z, qv[c].z, acc[a][c]);
+        acc[a][c] = fmaf(pv[a].w, qv[c].w, acc[a][c]);
+      }
+  }
+}
+
+// Stores a thread's 8 x NJ block (samples x units) unit-major, optionally
+// through relu or a mask.
+template <int NJ>
+__device__ __forceinline__ void tile_store(float* __restrict__ A, int sb, int n0, const float acc[8][NJ]) {
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    float* row = A + (n0 + j) * kUPitch;
+    *reinterpret_cast<float4*>(row + 4 * sb) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    *reinterpret_cast<float4*>(row + 128 + 4 * sb) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+  }
+}
+
 template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
-  float* s_w = sm;                                       // W1t [64][32], W2t [64][64], W3 [64][4]
-  float* s_acc = s_w + kMlpParams;                       // gW1 [32][64], gW2 [64][64], gW3 [64][4]
-  float* s_feat = s_acc + kMlpParams;                    // [256][36]
-  float* s_P = s_feat + kBwdThreads * kFeatPitch;        // [256][68]
-  float* s_Q = s_P + kBwdThreads * kActPitch;            // [256][68]
-  int32_t* s_base = reinterpret_cast<int32_t*>(s_Q + kBwdThreads * kActPitch);
+  float* s_w = sm;                             // W1 [32][64], W2 [64][64], W3 [64][4], row-major
+  float* s_acc = s_w + kMlpParams;             // gW1 [32][64], gW2 [64][64], gW3 [64][4]
+  float* s_F = s_acc + kMlpParams;             // [32][pitch]: features, then dL/dfeatures
+  float* s_H1 = s_F + kIn * kUPitch;           // [64][pitch]: h1, then dL/dz1
+  float* s_H2 = s_H1 + kWidth * kUPitch;       // [64][pitch]: h2, then dL/dz2
+  float* s_Go = s_H2 + kWidth * kUPitch;       // [4][pitch]: dL/d(raw outputs)
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_Go + kOut * kUPitch);
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   __syncthreads();
   const int n_tiles = *p.n_tiles;
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
-  const float4* W1t4 = reinterpret_cast<const float4*>(s_w);
-  const float4* W2t4 = reinterpret_cast<const float4*>(s_w + kIn * kWidth);
-  const float4* W34 = reinterpret_cast<const float4*>(s_w + kIn * kWidth + kWidth * kWidth);
+  const float* W1 = s_w;
+  const float* W2 = s_w + kIn * kWidth;
+  const float* W3 = W2 + kWidth * kWidth;
   float* gW1 = s_acc;
   float* gW2 = s_acc + kIn * kWidth;
   float* gW3 = gW2 + kWidth * kWidth;
+  // this thread's blocks of the tiled products
+  const int sb = tid & 31;        // samples 4 sb .. 4 sb + 3 and 128 + 4 sb ..
+  const int ub = tid >> 5;        // units 8 ub .. 8 ub + 7 (or features 4 ub .. 4 ub + 3)
+  const int ib = tid >> 4, nb = tid & 15;  // weight gradients: rows ib + 16 a, columns nb + 16 c
   int region = -1;
   const void* table = nullptr;
   float2* gtab = nullptr;
@@ -196,13 +296,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
     if (k != region) {
       if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
       __syncthreads();
-      load_mlp_any<kMlpType>(static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * mlp_esize, s_w);
-      for (int i = tid; i < kMlpParams; i += blockDim.x) s_acc[i] = 0.0f;
+      const char* blk = static_cast<const char*>(p.mlp) + (size_t)k * kMlpParams * mlp_esize;
+      for (int i = tid; i < kMlpParams; i += blockDim.x) {
+        s_w[i] = mlp_elem<kMlpType>(blk, i);
+        s_acc[i] = 0.0f;
+      }
       __syncthreads();
       region = k;
       table = static_cast<const char*>(p.tables) + (size_t)k * p.lp.E * sizeof(TabT);
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
+    // ---- per sample (thread = sample s = tid of slot `warp`): position, chunk adjoints, encoding
     const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
     const uint2 ref = sl.ref;
     const bool chunk_ok = sl.slot_ok;  // warp-uniform; lanes of an unused part of the slot are empty samples
@@ -247,57 +351,42 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
         TableOf<kF16Table>::encode(p.lp, table, u, feat);
       }
     }
-    // ---- forward recompute: feat -> h1 (s_P) -> h2 (s_Q) -> raw outputs
-    float* my_feat = s_feat + tid * kFeatPitch;
-    float* my_P = s_P + tid * kActPitch;
-    float* my_Q = s_Q + tid * kActPitch;
 #pragma unroll
-    for (int q = 0; q < kIn; q += 4)
-      *reinterpret_cast<float4*>(my_feat + q) = make_float4(feat[q], feat[q + 1], feat[q + 2], feat[q + 3]);
-    float h1[kWidth];
+    for (int j = 0; j < kIn; ++j) s_F[j * kUPitch + tid] = feat[j];
+    __syncthreads();
+    float acc[8][8];
+    // ---- forward recompute: H1 = relu(F W1), H2 = relu(H1 W2)
+    tile_gemm_ab<kIn>(s_F, W1, sb, 8 * ub, acc);
 #pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaxf(acc[i][j], 0.0f);
+    tile_store<8>(s_H1, sb, 8 * ub, acc);
+    __syncthreads();
+    tile_gemm_ab<kWidth>(s_H1, W2, sb, 8 * ub, acc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaxf(acc[i][j], 0.0f);
+    tile_store<8>(s_H2, sb, 8 * ub, acc);
+    __syncthreads();
+    // ---- per sample: raw outputs o = h2 W3, chunk-local render adjoint -> dL/d(raw outputs)
+    float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
     for (int n = 0; n < kWidth; ++n) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int i4 = 0; i4 < kIn / 4; ++i4) {
-        const float4 wv = W1t4[n * (kIn / 4) + i4];
-        acc = fmaf(feat[4 * i4], wv.x, acc);
-        acc = fmaf(feat[4 * i4 + 1], wv.y, acc);
-        acc = fmaf(feat[4 * i4 + 2], wv.z, acc);
-        acc = fmaf(feat[4 * i4 + 3], wv.w, acc);
-      }
-      h1[n] = fmaxf(acc, 0.0f);
+      const float h2 = s_H2[n * kUPitch + tid];
+      const float4 w3 = *reinterpret_cast<const float4*>(W3 + 4 * n);
+      o4[0] = fmaf(h2, w3.x, o4[0]);
+      o4[1] = fmaf(h2, w3.y, o4[1]);
+      o4[2] = fmaf(h2, w3.z, o4[2]);
+      o4[3] = fmaf(h2, w3.w, o4[3]);
     }
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_P + q) = make_float4(h1[q], h1[q + 1], h1[q + 2], h1[q + 3]);
-    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, o3 = 0.0f;
-#pragma unroll 2
-    for (int n = 0; n < kWidth; ++n) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
-        const float4 wv = W2t4[n * (kWidth / 4) + i4];
-        acc = fmaf(h1[4 * i4], wv.x, acc);
-        acc = fmaf(h1[4 * i4 + 1], wv.y, acc);
-        acc = fmaf(h1[4 * i4 + 2], wv.z, acc);
-        acc = fmaf(h1[4 * i4 + 3], wv.w, acc);
-      }
-      const float h2 = fmaxf(acc, 0.0f);
-      my_Q[n] = h2;
-      const float4 w3 = W34[n];
-      o0 = fmaf(h2, w3.x, o0);
-      o1 = fmaf(h2, w3.y, o1);
-      o2 = fmaf(h2, w3.z, o2);
-      o3 = fmaf(h2, w3.w, o3);
-    }
-    // ---- chunk-local render adjoint -> dL/d(raw outputs)
     float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
-      sigma = expf(o0);
-      rgb[0] = 1.0f / (1.0f + expf(-o1));
-      rgb[1] = 1.0f / (1.0f + expf(-o2));
-      rgb[2] = 1.0f / (1.0f + expf(-o3));
+      sigma = expf(o4[0]);
+      rgb[0] = 1.0f / (1.0f + expf(-o4[1]));
+      rgb[1] = 1.0f / (1.0f + expf(-o4[2]));
+      rgb[2] = 1.0f / (1.0f + expf(-o4[3]));
     }
     float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
     if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sl.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sl.width);
@@ -307,101 +396,82 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) go[1 + q] = g_rgb[q] * rgb[q] * (1.0f - rgb[q]);
     }
-    *reinterpret_cast<float4*>(my_feat + kIn) = make_float4(go[0], go[1], go[2], go[3]);
+#pragma unroll
+    for (int m = 0; m < kOut; ++m) s_Go[m * kUPitch + tid] = go[m];
     __syncthreads();
     // ---- gW3[n][m] += sum_s h2[s][n] go[s][m]   (one output per thread)
     {
       const int n = tid >> 2, m = tid & 3;
-      float acc = 0.0f;
-      for (int s = 0; s < kBwdThreads; ++s) acc = fmaf(s_Q[s * kActPitch + n], s_feat[s * kFeatPitch + kIn + m], acc);
-      gW3[n * kOut + m] += acc;
+      float a = 0.0f;
+#pragma unroll 4
+      for (int s = 0; s < kBwdThreads; s += 4) {
+        const float4 hv = *reinterpret_cast<const float4*>(s_H2 + n * kUPitch + s);
+        const float4 gv = *reinterpret_cast<const float4*>(s_Go + m * kUPitch + s);
+        a = fmaf(hv.x, gv.x, a);
+        a = fmaf(hv.y, gv.y, a);
+        a = fmaf(hv.z, gv.z, a);
+        a = fmaf(hv.w, gv.w, a);
+      }
+      gW3[n * kOut + m] += a;
     }
     __syncthreads();
-    // ---- dL/dz2 (into s_Q) and dL/dh1 = W2 dz2
-    float gh1[kWidth];
-#pragma unroll
-    for (int i = 0; i < kWidth; ++i) gh1[i] = 0.0f;
-#pragma unroll 2
+    // ---- dL/dz2 = (h2 > 0) (go W3^T), per sample, in place of h2
+#pragma unroll 8
     for (int n = 0; n < kWidth; ++n) {
-      const float4 w3 = W34[n];
-      const float gz2 = my_Q[n] > 0.0f ? w3.x * go[0] + w3.y * go[1] + w3.z * go[2] + w3.w * go[3] : 0.0f;
-      my_Q[n] = gz2;
-#pragma unroll
-      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
-        const float4 wv = W2t4[n * (kWidth / 4) + i4];  // W2[4 i4 + j][n]
-        gh1[4 * i4] = fmaf(wv.x, gz2, gh1[4 * i4]);
-        gh1[4 * i4 + 1] = fmaf(wv.y, gz2, gh1[4 * i4 + 1]);
-        gh1[4 * i4 + 2] = fmaf(wv.z, gz2, gh1[4 * i4 + 2]);
-        gh1[4 * i4 + 3] = fmaf(wv.w, gz2, gh1[4 * i4 + 3]);
-      }
+      const float4 w3 = *reinterpret_cast<const float4*>(W3 + 4 * n);
+      float* at = s_H2 + n * kUPitch + tid;
+      *at = *at > 0.0f ? w3.x * go[0] + w3.y * go[1] + w3.z * go[2] + w3.w * go[3] : 0.0f;
     }
-#pragma unroll
-    for (int i = 0; i < kWidth; ++i) gh1[i] = my_P[i] > 0.0f ? gh1[i] : 0.0f;  // dL/dz1
     __syncthreads();
-    // ---- gW2[i][n] += sum_s h1[s][i] dz2[s][n]   (16 outputs per thread)
+    // ---- gW2[i][n] += sum_s h1[s][i] dz2[s][n]
     {
-      const int i = tid >> 2, n0 = (tid & 3) * 16;
-      float acc[16];
+      float dw[4][4];
+      tile_gemm_dw<4>(s_H1, s_H2, ib, nb, dw);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float hv = s_P[s * kActPitch + i];
-        const float4* qr = reinterpret_cast<const float4*>(s_Q + s * kActPitch + n0);
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 v = qr[q4];
-          acc[4 * q4] = fmaf(hv, v.x, acc[4 * q4]);
-          acc[4 * q4 + 1] = fmaf(hv, v.y, acc[4 * q4 + 1]);
-          acc[4 * q4 + 2] = fmaf(hv, v.z, acc[4 * q4 + 2]);
-          acc[4 * q4 + 3] = fmaf(hv, v.w, acc[4 * q4 + 3]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) gW2[i * kWidth + n0 + q] += acc[q];
+        for (int c = 0; c < 4; ++c) gW2[(ib + 16 * a) * kWidth + nb + 16 * c] += dw[a][c];
     }
     __syncthreads();
-    // ---- dz1 into s_P; dL/dfeat = W1 dz1
+    // ---- dL/dz1 = (h1 > 0) (dz2 W2^T), in place of h1 (each thread reads the h1 it overwrites)
+    tile_gemm_abt<kWidth, 8>(s_H2, W2, sb, 8 * ub, acc);
 #pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_P + q) = make_float4(gh1[q], gh1[q + 1], gh1[q + 2], gh1[q + 3]);
-    float gfeat[kIn];
-#pragma unroll
-    for (int j = 0; j < kIn; ++j) gfeat[j] = 0.0f;
-#pragma unroll
-    for (int n = 0; n < kWidth; ++n) {
-#pragma unroll
-      for (int i4 = 0; i4 < kIn / 4; ++i4) {
-        const float4 wv = W1t4[n * (kIn / 4) + i4];  // W1[4 i4 + j][n]
-        gfeat[4 * i4] = fmaf(wv.x, gh1[n], gfeat[4 * i4]);
-        gfeat[4 * i4 + 1] = fmaf(wv.y, gh1[n], gfeat[4 * i4 + 1]);
-        gfeat[4 * i4 + 2] = fmaf(wv.z, gh1[n], gfeat[4 * i4 + 2]);
-        gfeat[4 * i4 + 3] = fmaf(wv.w, gh1[n], gfeat[4 * i4 + 3]);
-      }
+    for (int j = 0; j < 8; ++j) {
+      float* row = s_H1 + (8 * ub + j) * kUPitch;
+      const float4 h0 = *reinterpret_cast<const float4*>(row + 4 * sb);
+      const float4 h1 = *reinterpret_cast<const float4*>(row + 128 + 4 * sb);
+      *reinterpret_cast<float4*>(row + 4 * sb) =
+          make_float4(h0.x > 0.0f ? acc[0][j] : 0.0f, h0.y > 0.0f ? acc[1][j] : 0.0f, h0.z > 0.0f ? acc[2][j] : 0.0f,
+                      h0.w > 0.0f ? acc[3][j] : 0.0f);
+      *reinterpret_cast<float4*>(row + 128 + 4 * sb) =
+          make_float4(h1.x > 0.0f ? acc[4][j] : 0.0f, h1.y > 0.0f ? acc[5][j] : 0.0f, h1.z > 0.0f ? acc[6][j] : 0.0f,
+                      h1.w > 0.0f ? acc[7][j] : 0.0f);
     }
     __syncthreads();
-    // ---- gW1[j][n] += sum_s feat[s][j] dz1[s][n]   (8 outputs per thread)
+    // ---- gW1[j][n] += sum_s feat[s][j] dz1[s][n]
     {
-      const int j = tid >> 3, n0 = (tid & 7) * 8;
-      float acc[8];
+      float dw[2][4];
+      tile_gemm_dw<2>(s_F, s_H1, ib, nb, dw);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float fv = s_feat[s * kFeatPitch + j];
-        const float4* qr = reinterpret_cast<const float4*>(s_P + s * kActPitch + n0);
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int q4 = 0; q4 < 2; ++q4) {
-          const float4 v = qr[q4];
-          acc[4 * q4] = fmaf(fv, v.x, acc[4 * q4]);
-          acc[4 * q4 + 1] = fmaf(fv, v.y, acc[4 * q4 + 1]);
-          acc[4 * q4 + 2] = fmaf(fv, v.z, acc[4 * q4 + 2]);
-          acc[4 * q4 + 3] = fmaf(fv, v.w, acc[4 * q4 + 3]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) gW1[j * kWidth + n0 + q] += acc[q];
+        for (int c = 0; c < 4; ++c) gW1[(ib + 16 * a) * kWidth + nb + 16 * c] += dw[a][c];
     }
-    // ---- table gradients
-    if (valid) scatter_table_grad(p.lp, gtab, u, gfeat);
+    __syncthreads();
+    // ---- dL/dfeatures = dz1 W1^T, in place of the features
+    {
+      float gx[8][4];
+      tile_gemm_abt<kWidth, 4>(s_H1, W1, sb, 4 * ub, gx);
+      tile_store<4>(s_F, sb, 4 * ub, gx);
+    }
+    __syncthreads();
+    // ---- table gradients (thread = sample)
+    if (valid) {
+      float gfeat[kIn];
+#pragma unroll
+      for (int j = 0; j < kIn; ++j) gfeat[j] = s_F[j * kUPitch + tid];
+      scatter_table_grad(p.lp, gtab, u, gfeat);
+    }
   }
   __syncthreads();
   if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
@@ -891,7 +961,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
     profile_mark(1, stream);
     return kernel_launched("k_field_bwd_split_f32");
   }
-  const size_t smem = sizeof(float) * kBwdSmemFloats + sizeof(int32_t) * (f->K + 1);
+  const size_t smem = sizeof(float) * kBwdSmemFloatsT + sizeof(int32_t) * (f->K + 1);
   if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
   void (*kern)(BwdParams) = k_field_bwd_f32<false, 0>;

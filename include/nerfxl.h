@@ -137,11 +137,15 @@ typedef struct nerfxl_sampling {
 } nerfxl_sampling;
 
 /*
- * Training with a 16-bit MLP: the forward writes the tensor-core backward's
- * per-tile records (the 16-bit encoded features, sample geometry and the
- * chunk-render values its adjoint reuses: about 116 bytes per sample row) into a
- * backward-sized workspace. Without the flag nerfxl_render_bwd rebuilds them
- * with one more forward pass first.
+ * Training: the forward keeps per-sample records for the backward in a
+ * backward-sized workspace, so that the backward does not gather the tables
+ * again. With a 16-bit MLP these are the tensor-core backward's per-tile
+ * records (the 16-bit encoded features, sample geometry and the chunk-render
+ * values its adjoint reuses: about 116 bytes per sample row); without the flag
+ * nerfxl_render_bwd rebuilds them with one more forward pass first. With the
+ * fused FP32 MLP they are the FP32 features (128 bytes per sample row); without
+ * the flag the backward encodes again. The flag must be the same on the
+ * forward and the backward call.
  */
 #define NERFXL_SAVE_FEATURES 1
 

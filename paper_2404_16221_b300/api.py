@@ -292,8 +292,9 @@ class Trainer:
         one-pass workspace is larger runs in ray sub-batches (nerfxl_step)."""
         self.field = field
         self.workspace_cap = workspace_cap
-        if save_features and field.mlp.dtype in (torch.bfloat16, torch.float16):
-            # 16-bit MLP: keep the forward's records for the tensor-core backward
+        if save_features and (field.mlp.dtype in (torch.bfloat16, torch.float16) or field.arch == N.ARCH_FUSED):
+            # keep the forward's records (features, and for a 16-bit MLP the
+            # tensor-core backward's geometry) instead of encoding again
             samp = dataclasses.replace(samp, flags=samp.flags | SAVE_FEATURES)
         self.samp = samp
         self.lr, self.beta1, self.beta2, self.eps, self.lambda_dist = lr, beta1, beta2, eps, lambda_dist

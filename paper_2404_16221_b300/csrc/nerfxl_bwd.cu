@@ -118,6 +118,7 @@ struct BwdParams {
   const Slot* chunks;  // slots
   const int32_t* n_tiles;
   const float4* dpart;   // chunk partial adjoints
+  const float* rec32;    // the forward's FP32 feature records [tiles][32][256], or NULL (encode again)
   float* grad_tables;    // [K][E][2] accumulated
   float* grad_mlp;       // [K][kMlpParams] accumulated
 };
@@ -348,7 +349,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
         float x[3];
         sample_point(o, d, tbar, x);
         region_coord(p.fp.boxes + 6 * k, x, u);
-        TableOf<kF16Table>::encode(p.lp, table, u, feat);
+        if (p.rec32) {  // the forward's features, unit-major like s_F (coalesced)
+          const float* rec = p.rec32 + (size_t)t * kIn * kBwdThreads + tid;
+#pragma unroll
+          for (int j = 0; j < kIn; ++j) feat[j] = __ldcs(rec + j * kBwdThreads);
+        } else {
+          TableOf<kF16Table>::encode(p.lp, table, u, feat);
+        }
       }
     }
 #pragma unroll
@@ -947,6 +954,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.dpart = dpart;
+  p.rec32 = (s->flags & NERFXL_SAVE_FEATURES) && L.rec32 ? reinterpret_cast<const float*>(ws + L.rec32) : nullptr;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   if (f->arch == NERFXL_ARCH_SPLIT) {

@@ -391,6 +391,7 @@ struct FwdParams {
   float4* partials;        // [R][max_chunk][2]
   float4* smp4;            // per sample slot: sigma, rgb (sample-level composition), or NULL
   float2* smp2;            // per sample slot: tbar - tn, delta
+  float* rec32;            // the backward's FP32 feature records [tiles][32][256], or NULL
 };
 
 
@@ -461,6 +462,11 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     } else {
 #pragma unroll
       for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+    }
+    if (!kSplit && p.rec32) {  // records for the backward: feature j of sample (warp, lane), unit-major
+      float* rec = p.rec32 + (size_t)t * kIn * (kWarp * kChunksPerTile) + warp * kWarp + lane;
+#pragma unroll
+      for (int q = 0; q < kIn; ++q) __stcs(rec + q * (kWarp * kChunksPerTile), feat[q]);
     }
     float raw[kOut];
     if (kSplit) {
@@ -685,6 +691,9 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.rec_dpart = take(sizeof(float4) * 2 * 16 * L.rec_tiles);
     L.rec_pos = take(sizeof(int32_t) * R * mc);
   }
+  L.rec32 = 0;
+  if (for_backward && f->mlp_dtype == NERFXL_F32 && f->arch == NERFXL_ARCH_FUSED)
+    L.rec32 = take(sizeof(float) * kIn * kWarp * kChunksPerTile * (size_t)((L.chunk_cap + kChunksPerTile - 1) / kChunksPerTile));
   L.smp4 = L.smp2 = 0;
   if (s->flags & NERFXL_SAMPLE_COMPOSITE) {
     L.smp4 = take(sizeof(float4) * (size_t)R * mc * kWarp);
@@ -951,6 +960,12 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   p.smp4 = per_sample ? reinterpret_cast<float4*>(ws + L.smp4) : nullptr;
   p.smp2 = per_sample ? reinterpret_cast<float2*>(ws + L.smp2) : nullptr;
   const bool split = f->arch == NERFXL_ARCH_SPLIT;
+  p.rec32 = nullptr;
+  if ((s->flags & NERFXL_SAVE_FEATURES) && !split) {
+    const Layout LB = layout(f, s, n_rays, 1);
+    if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
+    p.rec32 = reinterpret_cast<float*>(ws + LB.rec32);
+  }
   const size_t smem = sizeof(float) * (split ? kSplitSmemFloats : kMlpParams) + sizeof(int32_t) * (f->K + 1);
   const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
   void (*kern)(FwdParams) = split ? k_field_fwd_f32<true> : k_field_fwd_f32<false>;

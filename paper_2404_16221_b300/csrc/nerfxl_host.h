@@ -31,6 +31,9 @@ struct Layout {
                      // (fused) or the ray direction d0 d1 d2 (split); chunk counts
   size_t rec_dpart;  // float4[tiles * 16][2]: chunk adjoints in tile order (4 positions per slot)
   size_t rec_pos;    // int32[R][max_chunk]: tile-order position of each chunk
+  // FP32 records (backward workspaces of the fused FP32 MLP): the forward's
+  // features per 256-row tile, unit-major [tiles][32][256] float.
+  size_t rec32;
   // Sample-level composition (NERFXL_SAMPLE_COMPOSITE; 0 otherwise):
   size_t smp4;       // float4[R][max_chunk][32]: sigma, r, g, b per sample slot
   size_t smp2;       // float2[R][max_chunk][32]: tbar - tn, delta per sample slot

@@ -327,7 +327,7 @@ def single_form(args, dev):
     name = args.only
     if args.group_min_mb > 0 or args.group_mb > 0 or args.window_tiles > 0:
         N.check(N.lib().nerfxl_set_gather_groups(int(args.group_min_mb * (1 << 20)), int(args.group_mb * (1 << 20)),
-                                                 args.window_tiles), "gather groups")
+                                                 args.window_tiles, 0), "gather groups")
     w = sy.workload("city32" if name.startswith("city32") else "grid8")
     if args.log2_t:
         w.log2_T = args.log2_t

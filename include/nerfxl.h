@@ -448,19 +448,24 @@ nerfxl_status nerfxl_set_profile_events(cudaEvent_t start, cudaEvent_t stop);
  * forward sweeps the regions one at a time, so one region's table is the
  * working set of its random gathers; beyond some 30-40 MB (measured on B300)
  * the L2 stops holding it and the gather reads the table many times from HBM.
- * A field whose region table exceeds min_table_bytes is therefore gathered
+ * A batch whose field has a region table above min_table_bytes, and which
+ * brings at least min_region_samples samples per region (n_rays x n_samples /
+ * K; each group is one more pass over the samples, which pays only when a
+ * region's samples reuse its table lines: a city training sub-batch of 62 K
+ * rays ran slower grouped), is therefore gathered
  * one group of levels (at most group_bytes of table, at least one level) at a
  * time over all of a region's samples, into level-major feature words (4
  * bytes per level per sample row), which the MLP and render then read
  * (results bit for bit those of the one-pass gather). Workspaces of such
  * fields hold a window of window_tiles tiles of 128 rows (L x 512 bytes
  * each). Process-wide; pass 0 for a default (64 MiB, 64 MiB, 65536
- * tiles: on the street/city field, 2 groups of a 96 MB FP16 region table ran
+ * tiles, 2^21 samples: on the street/city field, 2 groups of a 96 MB FP16 region table ran
  * faster than 3 to 11 smaller ones, whose extra passes cost more than their
  * fewer L2 misses save); set it before sizing workspaces. The paper has no
  * counterpart (its GPUs each hold one region).
  */
-nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles);
+nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles,
+                                       int64_t min_region_samples);
 
 /*
  * Instrumentation: the number of kernels this library has launched in this

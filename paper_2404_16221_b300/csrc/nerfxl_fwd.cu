@@ -703,7 +703,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   // layouts
   L.gfeat = 0;
   L.gfeat_tiles = 0;
-  if (grouped_gather(f)) {
+  if (grouped_gather(f, s, R)) {
     L.gfeat_tiles = std::min<int64_t>((L.chunk_cap + 3) / 4, gather_window_tiles());
     L.gfeat = take(sizeof(uint32_t) * 128 * (size_t)f->L * (size_t)L.gfeat_tiles);
   }

@@ -586,7 +586,7 @@ nerfxl_status launch_field_fwd_tc(const nerfxl_field* f, const SampParams& sp, c
     return set_error(NERFXL_E_UNSUPPORTED, "the split representation's tensor-core form is a BF16/FP16 forward");
   const bool bf = kind == kKindBF16;
   const int64_t max_tiles = L.chunk_cap / kTcChunks;
-  if (grouped_gather(f)) {
+  if (L.gfeat_tiles > 0) {
     // Level-grouped gather into the layout's window of level-major feature
     // words (the backward layout's when the forward writes records), then the
     // MLP and render from those words, window by window.

@@ -136,17 +136,18 @@ __global__ void __launch_bounds__(kGThreads, 4) k_gather_groups(GatherGroupsPara
 size_t g_group_min = kGroupMinBytes;
 size_t g_group_bytes = kGroupBytes;
 int64_t g_window = kGatherWindowTiles;
+int64_t g_group_samples = kGroupMinRegionSamples;
 
 }  // namespace
 
 size_t group_min_bytes() { return g_group_min; }
 int64_t gather_window_tiles() { return g_window; }
 
-bool grouped_gather(const nerfxl_field* f) {
+bool grouped_gather(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R) {
   if (f->mlp_dtype != NERFXL_BF16 && f->mlp_dtype != NERFXL_F16) return false;
   const int64_t E = nerfxl_table_entries(f->level_res, f->L, f->log2_T);
   const int64_t bytes = E * f->F * (f->table_dtype == NERFXL_F16 ? 2 : 4);
-  return (size_t)bytes > g_group_min;
+  return (size_t)bytes > g_group_min && R * (int64_t)s->n_samples >= g_group_samples * (int64_t)f->K;
 }
 
 int gather_groups(const nerfxl_field* f, const LevelParams& lp, int32_t* g_lo) {
@@ -201,10 +202,13 @@ nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, 
 
 using namespace nerfxl;
 
-extern "C" nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles) {
-  if (window_tiles < 0) return set_error(NERFXL_E_INVALID, "window_tiles must be >= 0");
+extern "C" nerfxl_status nerfxl_set_gather_groups(size_t min_table_bytes, size_t group_bytes, int64_t window_tiles,
+                                                  int64_t min_region_samples) {
+  if (window_tiles < 0 || min_region_samples < 0)
+    return set_error(NERFXL_E_INVALID, "window_tiles and min_region_samples must be >= 0");
   g_group_min = min_table_bytes ? min_table_bytes : kGroupMinBytes;
   g_group_bytes = group_bytes ? group_bytes : kGroupBytes;
   g_window = window_tiles ? window_tiles : kGatherWindowTiles;
+  g_group_samples = min_region_samples ? min_region_samples : kGroupMinRegionSamples;
   return NERFXL_OK;
 }

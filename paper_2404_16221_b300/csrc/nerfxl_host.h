@@ -111,7 +111,12 @@ constexpr int64_t kGatherWindowTiles = 65536;
 // The values in force (nerfxl_set_gather_groups may change them).
 size_t group_min_bytes();
 int64_t gather_window_tiles();
-bool grouped_gather(const nerfxl_field* f);
+// A batch of R rays gathers by groups when the region table exceeds the
+// size threshold and the batch brings at least kGroupMinRegionSamples samples
+// per region (R * n_samples / K): each group is one more pass over the
+// samples, which only pays when a region's samples reuse its table lines.
+constexpr int64_t kGroupMinRegionSamples = int64_t(1) << 21;
+bool grouped_gather(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R);
 int gather_groups(const nerfxl_field* f, const LevelParams& lp, int32_t* g_lo);
 nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, const LevelParams& lp,
                                    const float* rays_o, const float* rays_d, char* ws, const Layout& L, uint32_t* feat,

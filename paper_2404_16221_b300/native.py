@@ -82,7 +82,7 @@ SIGNATURES = {
     "nerfxl_workspace_stats": (C.c_int, [_vp, _sz, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]),
     "nerfxl_set_profile_events": (C.c_int, [_vp, _vp]),
     "nerfxl_launch_count": (_i64, []),
-    "nerfxl_set_gather_groups": (C.c_int, [_sz, _sz, _i64]),
+    "nerfxl_set_gather_groups": (C.c_int, [_sz, _sz, _i64, _i64]),
     "nerfxl_render_bwd": (C.c_int, [_FP, _SP, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_loss": (C.c_int, [_i64, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_adam_update": (C.c_int, [_i64, _vp, _vp, _vp, _vp, C.c_void_p, _vp, _i32, _vp]),

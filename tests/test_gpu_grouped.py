@@ -35,10 +35,10 @@ def groups():
     from paper_2404_16221_b300 import native as N
 
     def set_(min_bytes, group_bytes, window):
-        N.check(N.lib().nerfxl_set_gather_groups(int(min_bytes), int(group_bytes), int(window)), "groups")
+        N.check(N.lib().nerfxl_set_gather_groups(int(min_bytes), int(group_bytes), int(window), 1), "groups")
 
     yield set_
-    N.check(N.lib().nerfxl_set_gather_groups(0, 0, 0), "groups")
+    N.check(N.lib().nerfxl_set_gather_groups(0, 0, 0, 0), "groups")
 
 
 def _render(field, samp, o, d):
@@ -92,10 +92,12 @@ def test_grouped_split_forward_equals_one_pass(groups):
         assert np.array_equal(got[k], ref[k]), k
 
 
-def test_grouped_training_step_equals_one_pass(groups):
-    """The record-writing forward of nerfxl_step gathers its groups straight
-    into the record tiles: loss bit for bit, gradients up to the order of the
-    FP32 sums, and the records' features feed the backward unchanged."""
+@pytest.mark.parametrize("window", [0, 9])
+def test_grouped_training_step_equals_one_pass(groups, window):
+    """The record-writing forward of nerfxl_step with the grouped gather
+    (the default window, or 9 tiles: many windows, regions cut by window
+    ends) writes the records from the feature words: loss bit for bit,
+    gradients up to the order of the FP32 sums."""
     from paper_2404_16221_b300 import api
 
     w = H.workload("city32", L=16, log2_T=16)
@@ -105,7 +107,7 @@ def test_grouped_training_step_equals_one_pass(groups):
     runs = []
     for grouped in (False, True):
         if grouped:
-            groups(1, 1 << 20, 0)
+            groups(1, 1 << 20, window)
         field = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
         tr = api.Trainer(field, H.sampling(w), lr=1e-2, eps=1e-15, lambda_dist=0.01, master_tables=t, master_mlp=m)
         L = tr.step(o, d, tgt).cpu().numpy().copy()
@@ -119,4 +121,5 @@ def test_grouped_training_step_equals_one_pass(groups):
 def test_set_gather_groups_rejects_bad_window():
     from paper_2404_16221_b300 import native as N
 
-    assert N.lib().nerfxl_set_gather_groups(0, 0, -1) == N.E_INVALID
+    assert N.lib().nerfxl_set_gather_groups(0, 0, -1, 0) == N.E_INVALID
+    assert N.lib().nerfxl_set_gather_groups(0, 0, 0, -1) == N.E_INVALID

@@ -53,7 +53,7 @@ def parse():
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
     ap.add_argument("--only", type=str, default="",
                     choices=["", "city32_fwd", "city32_train", "grid8_fwd", "grid8_train", "grid8_train_fp32",
-                             "grid8_split_train"],
+                             "grid8_split_train", "grid8_split_train_fp32"],
                     help="profiler captures: run one form alone and print its own line")
     ap.add_argument("--log2-t", type=int, default=0, help="--only: override the hash table size (log2 entries)")
     ap.add_argument("--group-min-mb", type=float, default=0.0,
@@ -317,8 +317,8 @@ def single_form(args, dev):
     """One form alone, for profiler captures (--only): its steps timed with
     CUDA events and one JSON line printed. city32_fwd: the street/city
     forward with FP16 tables and a BF16 MLP; grid8_fwd / grid8_train: the
-    mixed grid8 forward and training step; grid8_split_train: the split
-    representation's mixed training step. --profile-rays keeps the first N
+    mixed grid8 forward and training step; grid8_split_train(_fp32): the
+    split representation's mixed (FP32) training step. --profile-rays keeps the first N
     rays (a smaller device footprint for captures)."""
     import torch
 
@@ -332,14 +332,15 @@ def single_form(args, dev):
     if args.log2_t:
         w.log2_T = args.log2_t
     E = N.table_entries(w.level_res, w.log2_T)
-    if name == "grid8_split_train":
+    fp32 = name.endswith("_fp32")
+    if name.startswith("grid8_split_train"):
         n_split = api.split_mlp_params(w.K, w.mlp_in, w.W)
         t, _ = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         g = torch.Generator(device=dev)
         g.manual_seed(int(w.seed) * 7919 + 11)
         m = torch.randn(n_split, generator=g, device=dev) * 0.1
-        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
-                                     device=dev, arch=N.ARCH_SPLIT)
+        field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t if fp32 else t.to(torch.float16),
+                                     m if fp32 else m.to(torch.bfloat16), device=dev, arch=N.ARCH_SPLIT)
     elif name == "grid8_train_fp32":
         t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t, m, device=dev)
@@ -360,7 +361,7 @@ def single_form(args, dev):
         step = lambda: api.render_fwd(field, samp, o, d, workspace=ws)
     else:
         tgt = torch.rand(len(o), 3, generator=torch.Generator().manual_seed(1002)).to(dev)
-        masters = {} if name == "grid8_train_fp32" else {"master_tables": t, "master_mlp": m}
+        masters = {} if fp32 else {"master_tables": t, "master_mlp": m}
         tr = api.Trainer(field, samp, **masters,
                          workspace_cap=(4 << 30) if name == "city32_train" else None)
         step = lambda: tr.step(o, d, tgt)

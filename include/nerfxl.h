@@ -142,10 +142,11 @@ typedef struct nerfxl_sampling {
  * again. With a 16-bit MLP these are the tensor-core backward's per-tile
  * records (the 16-bit encoded features, sample geometry and the chunk-render
  * values its adjoint reuses: about 116 bytes per sample row); without the flag
- * nerfxl_render_bwd rebuilds them with one more forward pass first. With the
- * fused FP32 MLP they are the FP32 features (128 bytes per sample row); without
- * the flag the backward encodes again. The flag must be the same on the
- * forward and the backward call.
+ * nerfxl_render_bwd rebuilds them with one more forward pass first. With an
+ * FP32 MLP they are the FP32 features (128 bytes per sample row); without the
+ * flag the backward encodes again (the split representation's backward then
+ * writes the records itself, as it reads the features twice). The flag must
+ * be the same on the forward and the backward call.
  */
 #define NERFXL_SAVE_FEATURES 1
 

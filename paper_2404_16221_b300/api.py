@@ -292,7 +292,7 @@ class Trainer:
         one-pass workspace is larger runs in ray sub-batches (nerfxl_step)."""
         self.field = field
         self.workspace_cap = workspace_cap
-        if save_features and (field.mlp.dtype in (torch.bfloat16, torch.float16) or field.arch == N.ARCH_FUSED):
+        if save_features:
             # keep the forward's records (features, and for a 16-bit MLP the
             # tensor-core backward's geometry) instead of encoding again
             samp = dataclasses.replace(samp, flags=samp.flags | SAVE_FEATURES)

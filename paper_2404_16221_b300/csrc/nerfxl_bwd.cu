@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t R, SampParams sp,
 // k_field_bwd_f32
 
 constexpr int kBwdThreads = kChunksPerTile * kWarp;  // 256 samples per tile
-constexpr int kActPitch = 68;
 
 struct BwdParams {
   const float* rays_o;
@@ -118,7 +117,8 @@ struct BwdParams {
   const Slot* chunks;  // slots
   const int32_t* n_tiles;
   const float4* dpart;   // chunk partial adjoints
-  const float* rec32;    // the forward's FP32 feature records [tiles][32][256], or NULL (encode again)
+  float* rec32;          // FP32 feature records [tiles][32][256], or NULL (encode again)
+  int rec_in;            // rec32 holds the forward's records (else the split backward writes them)
   float* grad_tables;    // [K][E][2] accumulated
   float* grad_mlp;       // [K][kMlpParams] accumulated
 };
@@ -175,32 +175,41 @@ __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, 
 constexpr int kUPitch = 260;
 constexpr size_t kBwdSmemFloatsT = 2 * (size_t)kMlpParams + (size_t)kUPitch * (kIn + 2 * kWidth + kOut);
 
-// acc[i][j] = sum_k A[k][samples i] B[k][n0 + j]; A unit-major, B row-major [K][64].
-template <int K>
+// acc[i][j] = sum_k A[k][samples i] B[k][n0 + j]; A unit-major, B row-major
+// [K][NB] (NJ = 8 or 2 outputs per thread).
+template <int K, int NJ = 8, int NB = kWidth>
 __device__ __forceinline__ void tile_gemm_ab(const float* __restrict__ A, const float* __restrict__ B, int sb, int n0,
-                                             float acc[8][8]) {
+                                             float acc[8][NJ]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
     const float4 a0 = *reinterpret_cast<const float4*>(A + k * kUPitch + 4 * sb);
     const float4 a1 = *reinterpret_cast<const float4*>(A + k * kUPitch + 128 + 4 * sb);
-    const float4 b0 = *reinterpret_cast<const float4*>(B + k * kWidth + n0);
-    const float4 b1 = *reinterpret_cast<const float4*>(B + k * kWidth + n0 + 4);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float b[NJ];
+    if (NJ == 8) {
+      const float4 b0 = *reinterpret_cast<const float4*>(B + k * NB + n0);
+      const float4 b1 = *reinterpret_cast<const float4*>(B + k * NB + n0 + 4);
+      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) b[j] = bb[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) b[j] = B[k * NB + n0 + j];
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
 }
 
-// acc[i][j] = sum_k A[k][samples i] W[j0 + j][k]; W row-major with rows of 64
+// acc[i][j] = sum_k A[k][samples i] W[j0 + j][k]; W row-major with rows of WS
 // (the transposed weight of a dX product), NJ of its rows.
-template <int K, int NJ>
+template <int K, int NJ, int WS = kWidth>
 __device__ __forceinline__ void tile_gemm_abt(const float* __restrict__ A, const float* __restrict__ W, int sb, int j0,
                                               float acc[8][NJ]) {
 #pragma unroll
@@ -214,7 +223,7 @@ __device__ __forceinline__ void tile_gemm_abt(const float* __restrict__ A, const
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     float b[NJ];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) b[j] = W[(j0 + j) * kWidth + k];
+    for (int j = 0; j < NJ; ++j) b[j] = W[(j0 + j) * WS + k];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -224,24 +233,24 @@ __device__ __forceinline__ void tile_gemm_abt(const float* __restrict__ A, const
 
 // Weight gradient: acc[a][c] = sum_s P[ib + 16 a][s] Q[nb + 16 c][s] over the
 // 256 samples (both unit-major).
-template <int RA>
+template <int RA, int RC = 4>
 __device__ __forceinline__ void tile_gemm_dw(const float* __restrict__ P, const float* __restrict__ Q, int ib, int nb,
-                                             float acc[RA][4]) {
+                                             float acc[RA][RC]) {
 #pragma unroll
   for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+    for (int c = 0; c < RC; ++c) acc[a][c] = 0.0f;
 #pragma unroll 2
   for (int s = 0; s < kBwdThreads; s += 4) {
-    float4 pv[RA], qv[4];
+    float4 pv[RA], qv[RC];
 #pragma unroll
     for (int a = 0; a < RA; ++a) pv[a] = *reinterpret_cast<const float4*>(P + (ib + 16 * a) * kUPitch + s);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) qv[c] = *reinterpret_cast<const float4*>(Q + (nb + 16 * c) * kUPitch + s);
+    for (int c = 0; c < RC; ++c) qv[c] = *reinterpret_cast<const float4*>(Q + (nb + 16 * c) * kUPitch + s);
 #pragma unroll
     for (int a = 0; a < RA; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < RC; ++c) {
         acc[a][c] = fmaf(pv[a].x, qv[c].x, acc[a][c]);
         acc[a][c] = fmaf(pv[a].y, qv[c].y, acc[a][c]);
         acc[a][c] = fmaf(pv[a].z, qv[c].z, acc[a][c]);
@@ -485,94 +494,110 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// k_field_bwd_split_f32: the split representation's backward (FP32). Per
-// 256-sample tile: recompute encoding, density MLP (g), colour MLP on
-// [g, SH(d)]; chunk-local render adjoint; colour MLP backward (its weight
-// gradients accumulate in registers over every tile the CTA takes, whatever
-// the region, and reach the shared block once at the end); dL/dg0 from the
-// density and from the colour MLP; density MLP backward (accumulated per
-// region); table scatter. Activations of the tile live in three shared
-// buffers that the phases reuse:
-//   X [256][36]: xc = [g, SH] and dL/d(colour logits) -> dL/dg
-//   B [256][68]: hc1 -> dL/dzc1 -> feat
-//   C [256][68]: hc2 -> dL/dzc2 -> h1 -> dL/dz1
-// Weight-gradient accumulators per thread (GEMM over the tile's samples):
-//   Wc3 [n][m] n = t/4, m = t%4 | Wc2 [i][n0..+15] i = t/4, n0 = 16 (t%4) |
-//   Wc1 [j][n0..+7] j = t/8, n0 = 8 (t%8) | Wd2 [n][m0..+3] n = t/4, m0 = 4 (t%4) |
-//   Wd1 [j][n0..+7] j = t/8, n0 = 8 (t%8).
+// k_field_bwd_split_f32: the split representation's backward (FP32), as
+// register-tiled GEMMs over the 256-sample tile like k_field_bwd_f32. Per
+// tile: the features (the forward's FP32 records; encoded and recorded here
+// when the forward kept none), the density MLP (g), the colour MLP on
+// [g, SH(d)], the chunk-local render adjoint, the colour MLP backward, dL/dg
+// (through the colour MLP and, for g0, through the density), the density MLP
+// backward with h1 recomputed from the features read back, and the table
+// scatter. Four unit-major buffers of kUPitch-float rows serve the phases:
+//   A [64]: h1 -> hc2 -> dL/dzc2 -> h1 -> dL/dz1
+//   C [32]: xc = [g, SH(d)] -> dL/dg (rows 0..15)
+//   D [64]: features -> hc1 -> dL/dzc1 -> features -> dL/dfeatures
+//   O [4]:  dL/d(colour logits) (rows 0..2), dL/dg0 through the density (row 3)
+// Weight gradients accumulate in registers (a thread owns rows ib + 16 a and
+// columns nb + 16 c of each matrix): the shared colour MLP's over every tile
+// the CTA takes, flushed once at the end; the density MLP's per region.
 
-constexpr int kSplitXPitch = 36;
-constexpr size_t kBwdSplitSmemFloats =
-    (size_t)kSplitSmemFloats + (size_t)kBwdThreads * kSplitXPitch + 2 * (size_t)kBwdThreads * kActPitch;
+constexpr size_t kBwdSplitSmemFloats = (size_t)kSplitSmemFloats + (size_t)kUPitch * (2 * kWidth + kColorIn + kOut);
 
-__device__ __forceinline__ void flush_density_grad(float* __restrict__ g, const float aWd1[8], const float aWd2[4],
-                                                   int tid) {
-  const int j = tid >> 3, n0 = (tid & 7) * 8;
+__device__ __forceinline__ void flush_density_grad(float* __restrict__ g, const float aWd1[2][4],
+                                                   const float aWd2[4][1], int ib, int nb) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (aWd1[q] != 0.0f) atomicAdd(g + j * kWidth + n0 + q, aWd1[q]);
-  const int n = tid >> 2, m0 = (tid & 3) * 4;
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (aWd2[q] != 0.0f) atomicAdd(g + kIn * kWidth + n * kGeo + m0 + q, aWd2[q]);
+    for (int c = 0; c < 4; ++c)
+      if (aWd1[a][c] != 0.0f) atomicAdd(g + (ib + 16 * a) * kWidth + nb + 16 * c, aWd1[a][c]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    if (aWd2[a][0] != 0.0f) atomicAdd(g + kIn * kWidth + (ib + 16 * a) * kGeo + nb, aWd2[a][0]);
 }
 
-// Stage the split weights from FP32, BF16 or FP16 blocks (FP32 in shared memory,
-// the layouts of load_density_f32 / load_color_f32).
-template <int kMlpType>
-__device__ __forceinline__ void load_split_any(const void* dens, const void* color, float* __restrict__ s_d,
-                                               float* __restrict__ s_c) {
-  if (dens) {
-    for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x)
-      s_d[(i % kWidth) * kIn + i / kWidth] = mlp_elem<kMlpType>(dens, i);
-    for (int i = threadIdx.x; i < kWidth * kGeo; i += blockDim.x)
-      s_d[kIn * kWidth + i] = mlp_elem<kMlpType>(dens, kIn * kWidth + i);
-  }
-  if (color) {
-    for (int i = threadIdx.x; i < kColorIn * kWidth; i += blockDim.x)
-      s_c[(i % kWidth) * kColorIn + i / kWidth] = mlp_elem<kMlpType>(color, i);
-    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x)
-      s_c[kColorIn * kWidth + (i % kWidth) * kWidth + i / kWidth] = mlp_elem<kMlpType>(color, kColorIn * kWidth + i);
-    for (int i = threadIdx.x; i < kWidth * kOut; i += blockDim.x)
-      s_c[kColorIn * kWidth + kWidth * kWidth + i] = mlp_elem<kMlpType>(color, kColorIn * kWidth + kWidth * kWidth + i);
+// Overwrites a thread's 8 x 8 block of A (samples 4 sb.., 128 + 4 sb..; units
+// n0..n0 + 7) with acc where A is positive and 0 elsewhere: the gradient
+// through a ReLU whose output A holds.
+__device__ __forceinline__ void tile_store_masked(float* __restrict__ A, int sb, int n0, const float acc[8][8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float* row = A + (n0 + j) * kUPitch;
+    const float4 h0 = *reinterpret_cast<const float4*>(row + 4 * sb);
+    const float4 h1 = *reinterpret_cast<const float4*>(row + 128 + 4 * sb);
+    *reinterpret_cast<float4*>(row + 4 * sb) =
+        make_float4(h0.x > 0.0f ? acc[0][j] : 0.0f, h0.y > 0.0f ? acc[1][j] : 0.0f, h0.z > 0.0f ? acc[2][j] : 0.0f,
+                    h0.w > 0.0f ? acc[3][j] : 0.0f);
+    *reinterpret_cast<float4*>(row + 128 + 4 * sb) =
+        make_float4(h1.x > 0.0f ? acc[4][j] : 0.0f, h1.y > 0.0f ? acc[5][j] : 0.0f, h1.z > 0.0f ? acc[6][j] : 0.0f,
+                    h1.w > 0.0f ? acc[7][j] : 0.0f);
   }
 }
 
-// kF16Table / kMlpType: the parameters the forward read (FP16 tables; the
-// host launches the FP32 MLP form, 16-bit MLPs take the tensor-core backward);
-// the recompute and every product run in FP32 and the gradients are FP32.
+__device__ __forceinline__ void relu8x8(float acc[8][8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = fmaxf(acc[i][j], 0.0f);
+}
+
+template <int RA, int RC>
+__device__ __forceinline__ void add_block(float acc[RA][RC], const float dw[RA][RC]) {
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[a][c] += dw[a][c];
+}
+
+// kF16Table / kMlpType: the parameters the forward read (the host launches
+// the FP32 MLP form; 16-bit MLPs take the tensor-core backward); the
+// recompute and every product run in FP32 and the gradients are FP32.
 template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
-  float* s_d = sm;                                  // Wd1t [64][32], Wd2 [64][16]
-  float* s_c = s_d + kDensityParams;                // Wc1t [64][32], Wc2t [64][64], Wc3 [64][4]
-  float* s_X = s_c + kColorParams;                  // [256][36]
-  float* s_B = s_X + kBwdThreads * kSplitXPitch;    // [256][68]
-  float* s_C = s_B + kBwdThreads * kActPitch;       // [256][68]
-  int32_t* s_base = reinterpret_cast<int32_t*>(s_C + kBwdThreads * kActPitch);
+  float* s_w = sm;  // Wd1 [32][64], Wd2 [64][16] | Wc1 [32][64], Wc2 [64][64], Wc3 [64][4], row-major
+  float* s_A = s_w + kSplitSmemFloats;
+  float* s_C = s_A + kWidth * kUPitch;
+  float* s_D = s_C + kColorIn * kUPitch;
+  float* s_O = s_D + kWidth * kUPitch;
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_O + kOut * kUPitch);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
   const char* mlp = static_cast<const char*>(p.mlp);
   constexpr size_t kEsize = kMlpType == 0 ? 4 : 2;
   using TabT = typename TableOf<kF16Table>::T;
+  const float* Wd1 = s_w;
+  const float* Wd2 = s_w + kIn * kWidth;
+  const float* Wc1 = s_w + kDensityParams;
+  const float* Wc2 = Wc1 + kColorIn * kWidth;
+  const float* Wc3 = Wc2 + kWidth * kWidth;
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
-  load_split_any<kMlpType>(nullptr, mlp + (size_t)p.K * kDensityParams * kEsize, s_d, s_c);
+  {
+    const char* cblk = mlp + (size_t)p.K * kDensityParams * kEsize;
+    for (int i = tid; i < kColorParams; i += blockDim.x) s_w[kDensityParams + i] = mlp_elem<kMlpType>(cblk, i);
+  }
   __syncthreads();
   const int n_tiles = *p.n_tiles;
-  const float4* Wd1t = reinterpret_cast<const float4*>(s_d);
-  const float4* Wd2 = reinterpret_cast<const float4*>(s_d + kIn * kWidth);
-  const float4* Wc1t = reinterpret_cast<const float4*>(s_c);
-  const float4* Wc2t = reinterpret_cast<const float4*>(s_c + kColorIn * kWidth);
-  const float* Wc3 = s_c + kColorIn * kWidth + kWidth * kWidth;
-  float* my_X = s_X + tid * kSplitXPitch;
-  float* my_B = s_B + tid * kActPitch;
-  float* my_C = s_C + tid * kActPitch;
-  float aWc3 = 0.0f, aWc2[16], aWc1[8], aWd2[4], aWd1[8];
+  const int sb = tid & 31, ub = tid >> 5;  // GEMM blocks: samples 4 sb.., 128 + 4 sb..; units of block ub
+  const int ib = tid >> 4, nb = tid & 15;  // weight gradients: rows ib + 16 a, columns nb + 16 c
+  float aWc3 = 0.0f, aWc2[4][4], aWc1[2][4], aWd2[4][1], aWd1[2][4];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) aWc2[q] = 0.0f;
+  for (int a = 0; a < 4; ++a) {
+    aWd2[a][0] = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) aWc1[q] = aWd1[q] = 0.0f;
+    for (int c = 0; c < 4; ++c) aWc2[a][c] = 0.0f;
+  }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) aWc1[a][c] = aWd1[a][c] = 0.0f;
   int region = -1;
   const TabT* table = nullptr;
   float2* gtab = nullptr;
@@ -580,315 +605,249 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     __syncthreads();  // previous tile's shared buffers fully consumed
     if (k != region) {
-      if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, tid);
+      if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, ib, nb);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) aWd1[q] = 0.0f;
+      for (int a = 0; a < 4; ++a) aWd2[a][0] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) aWd2[q] = 0.0f;
-      load_split_any<kMlpType>(mlp + (size_t)k * kDensityParams * kEsize, nullptr, s_d, s_c);
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) aWd1[a][c] = 0.0f;
+      const char* dblk = mlp + (size_t)k * kDensityParams * kEsize;
+      for (int i = tid; i < kDensityParams; i += blockDim.x) s_w[i] = mlp_elem<kMlpType>(dblk, i);
       __syncthreads();
       region = k;
       table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
       gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
     }
+    // ---- per sample (thread = sample tid of slot `warp`): chunk adjoints, geometry, features, SH(d)
     const SlotLane sl = slot_lane(p.chunks[t * kChunksPerTile + warp], lane);
     const uint2 ref = sl.ref;
     const bool chunk_ok = sl.slot_ok;  // warp-uniform; lanes of an unused part of the slot are empty samples
     bool valid = false;
-    float feat[kIn], u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
+    float u[3] = {0.0f, 0.0f, 0.0f}, dir[3] = {0.0f, 0.0f, 0.0f};
     float tr = 0.0f, dl = 0.0f;
     float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
-    if (sl.has) {
-      const uint32_t ray = ref.x;
-      const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
-      const RayHdr h = p.hdr[ray];
-      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
-      const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
-      const float4 g0 = p.dpart[2 * slot], g1 = p.dpart[2 * slot + 1];
-      gtc = g0.x;
-      gC[0] = g0.y;
-      gC[1] = g0.z;
-      gC[2] = g0.w;
-      gA = g1.x;
-      gD = g1.y;
-      gL = g1.z;
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) dir[ax] = p.rays_d[3 * (size_t)ray + ax];
-      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-      const int i = c * kWarp + sl.sl;
-      valid = i < ss.n;
-      if (valid) {
-        float o[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) o[ax] = p.rays_o[3 * (size_t)ray + ax];
-        float a, b;
-        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
-        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
-        dl = __fsub_rn(b, a);
-        tr = __fsub_rn(tbar, h.tn);
-        float x[3];
-        sample_point(o, dir, tbar, x);
-        region_coord(p.fp.boxes + 6 * k, x, u);
-        TableOf<kF16Table>::encode(p.lp, table, u, feat);
-      }
-    }
-    // ---- forward recompute: g, xc -> X; hc1 -> B; hc2 -> C; colour logits
-    float xc[kColorIn];
-    density_f32_smem(s_d, feat, xc);
-    sh4_f32(dir, xc + kGeo);
-#pragma unroll
-    for (int q = 0; q < kColorIn; q += 4)
-      *reinterpret_cast<float4*>(my_X + q) = make_float4(xc[q], xc[q + 1], xc[q + 2], xc[q + 3]);
+    float* rec = p.rec32 + (size_t)t * kIn * kBwdThreads + tid;  // feature j at rec[j * 256]
     {
-      float hc1[kWidth];
+      float feat[kIn];
 #pragma unroll
-      for (int n = 0; n < kWidth; ++n) {
-        float acc = 0.0f;
+      for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
+      if (sl.has) {
+        const uint32_t ray = ref.x;
+        const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+        const RayHdr h = p.hdr[ray];
+        const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+        const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+        const float4 g0 = p.dpart[2 * slot], g1 = p.dpart[2 * slot + 1];
+        gtc = g0.x;
+        gC[0] = g0.y;
+        gC[1] = g0.z;
+        gC[2] = g0.w;
+        gA = g1.x;
+        gD = g1.y;
+        gL = g1.z;
 #pragma unroll
-        for (int i4 = 0; i4 < kColorIn / 4; ++i4) {
-          const float4 w = Wc1t[n * (kColorIn / 4) + i4];
-          acc = fmaf(xc[4 * i4], w.x, acc);
-          acc = fmaf(xc[4 * i4 + 1], w.y, acc);
-          acc = fmaf(xc[4 * i4 + 2], w.z, acc);
-          acc = fmaf(xc[4 * i4 + 3], w.w, acc);
+        for (int ax = 0; ax < 3; ++ax) dir[ax] = p.rays_d[3 * (size_t)ray + ax];
+        const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+        const int i = c * kWarp + sl.sl;
+        valid = i < ss.n;
+        if (valid) {
+          float o[3];
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) o[ax] = p.rays_o[3 * (size_t)ray + ax];
+          float a, b;
+          segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
+          const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+          dl = __fsub_rn(b, a);
+          tr = __fsub_rn(tbar, h.tn);
+          float x[3];
+          sample_point(o, dir, tbar, x);
+          region_coord(p.fp.boxes + 6 * k, x, u);
+          if (p.rec_in) {
+#pragma unroll
+            for (int j = 0; j < kIn; ++j) feat[j] = __ldcg(rec + j * kBwdThreads);
+          } else {  // record them here: the density backward reads them again
+            TableOf<kF16Table>::encode(p.lp, table, u, feat);
+#pragma unroll
+            for (int j = 0; j < kIn; ++j) __stcg(rec + j * kBwdThreads, feat[j]);
+          }
         }
-        hc1[n] = fmaxf(acc, 0.0f);
       }
 #pragma unroll
-      for (int q = 0; q < kWidth; q += 4)
-        *reinterpret_cast<float4*>(my_B + q) = make_float4(hc1[q], hc1[q + 1], hc1[q + 2], hc1[q + 3]);
-    }
-    float oc[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll 2
-    for (int n = 0; n < kWidth; ++n) {
-      float acc = 0.0f;
+      for (int j = 0; j < kIn; ++j) s_D[j * kUPitch + tid] = feat[j];
+      float sh[kSh];
+      sh4_f32(dir, sh);
 #pragma unroll
-      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
-        const float4 w = Wc2t[n * (kWidth / 4) + i4];
-        const float4 hv = *reinterpret_cast<const float4*>(my_B + 4 * i4);
-        acc = fmaf(hv.x, w.x, acc);
-        acc = fmaf(hv.y, w.y, acc);
-        acc = fmaf(hv.z, w.z, acc);
-        acc = fmaf(hv.w, w.w, acc);
-      }
-      const float h2 = fmaxf(acc, 0.0f);
-      my_C[n] = h2;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) oc[m] = fmaf(h2, Wc3[n * kOut + m], oc[m]);
+      for (int j = 0; j < kSh; ++j) s_C[(kGeo + j) * kUPitch + tid] = sh[j];
     }
-    // ---- chunk-local render adjoint -> dL/dg0 (density) and dL/d(colour logits)
-    float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
-    if (valid) {
-      sigma = expf(xc[0]);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-oc[m]));
-    }
-    float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
-    if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sl.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sl.width);
-    const float go_d = valid ? g_sigma * sigma : 0.0f;
-    float go[3] = {0.0f, 0.0f, 0.0f};
-    if (valid) {
-#pragma unroll
-      for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
-    }
-    *reinterpret_cast<float4*>(my_X + kColorIn) = make_float4(go[0], go[1], go[2], 0.0f);
     __syncthreads();
-    // ---- Wc3[n][m] += sum_s hc2[s][n] go[s][m]
+    float acc[8][8];
+    // ---- forward recompute: h1 = relu(F Wd1) -> A; g = h1 Wd2 -> C rows 0..15
+    tile_gemm_ab<kIn>(s_D, Wd1, sb, 8 * ub, acc);
+    relu8x8(acc);
+    tile_store<8>(s_A, sb, 8 * ub, acc);
+    __syncthreads();
+    {
+      float g2[8][2];
+      tile_gemm_ab<kWidth, 2, kGeo>(s_A, Wd2, sb, 2 * ub, g2);
+      tile_store<2>(s_C, sb, 2 * ub, g2);
+    }
+    __syncthreads();
+    // ---- hc1 = relu(xc Wc1) -> D; hc2 = relu(hc1 Wc2) -> A
+    tile_gemm_ab<kColorIn>(s_C, Wc1, sb, 8 * ub, acc);
+    relu8x8(acc);
+    tile_store<8>(s_D, sb, 8 * ub, acc);
+    __syncthreads();
+    tile_gemm_ab<kWidth>(s_D, Wc2, sb, 8 * ub, acc);
+    relu8x8(acc);
+    tile_store<8>(s_A, sb, 8 * ub, acc);
+    __syncthreads();
+    // ---- per sample: colour logits o = hc2 Wc3; chunk-local render adjoint
+    float go[3] = {0.0f, 0.0f, 0.0f};
+    {
+      float oc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+      for (int n = 0; n < kWidth; ++n) {
+        const float h2 = s_A[n * kUPitch + tid];
+        const float4 w3 = *reinterpret_cast<const float4*>(Wc3 + 4 * n);
+        oc[0] = fmaf(h2, w3.x, oc[0]);
+        oc[1] = fmaf(h2, w3.y, oc[1]);
+        oc[2] = fmaf(h2, w3.z, oc[2]);
+      }
+      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (valid) {
+        sigma = expf(s_C[tid]);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-oc[m]));
+      }
+      float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sl.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sl.width);
+      float go_d = 0.0f;
+      if (valid) {
+        go_d = g_sigma * sigma;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) s_O[m * kUPitch + tid] = go[m];
+      s_O[3 * kUPitch + tid] = go_d;
+    }
+    __syncthreads();
+    // ---- Wc3[n][m] += sum_s hc2[s][n] go[s][m]   (one output per thread; column 3 unused)
     {
       const int n = tid >> 2, m = tid & 3;
-      float acc = 0.0f;
-      for (int s = 0; s < kBwdThreads; ++s) acc = fmaf(s_C[s * kActPitch + n], s_X[s * kSplitXPitch + kColorIn + m], acc);
-      aWc3 += acc;
-    }
-    // ---- dL/dzc2 = (hc2 > 0) Wc3 go, in place in the own C row once everyone has read C
-    __syncthreads();
+      if (m < 3) {
+        float a = 0.0f;
 #pragma unroll 4
-    for (int n = 0; n < kWidth; ++n) {
-      const float h = my_C[n];
-      my_C[n] = h > 0.0f ? Wc3[n * kOut] * go[0] + Wc3[n * kOut + 1] * go[1] + Wc3[n * kOut + 2] * go[2] : 0.0f;
-    }
-    __syncthreads();
-    // ---- Wc2[i][n] += sum_s hc1[s][i] dzc2[s][n]
-    {
-      const int i = tid >> 2, n0 = (tid & 3) * 16;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float hv = s_B[s * kActPitch + i];
-        const float4* qr = reinterpret_cast<const float4*>(s_C + s * kActPitch + n0);
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 v = qr[q4];
-          aWc2[4 * q4] = fmaf(hv, v.x, aWc2[4 * q4]);
-          aWc2[4 * q4 + 1] = fmaf(hv, v.y, aWc2[4 * q4 + 1]);
-          aWc2[4 * q4 + 2] = fmaf(hv, v.z, aWc2[4 * q4 + 2]);
-          aWc2[4 * q4 + 3] = fmaf(hv, v.w, aWc2[4 * q4 + 3]);
+        for (int s = 0; s < kBwdThreads; s += 4) {
+          const float4 hv = *reinterpret_cast<const float4*>(s_A + n * kUPitch + s);
+          const float4 gv = *reinterpret_cast<const float4*>(s_O + m * kUPitch + s);
+          a = fmaf(hv.x, gv.x, a);
+          a = fmaf(hv.y, gv.y, a);
+          a = fmaf(hv.z, gv.z, a);
+          a = fmaf(hv.w, gv.w, a);
         }
+        aWc3 += a;
       }
     }
-    // ---- dL/dzc1 = (hc1 > 0) Wc2 dzc2   (Wc2[i][n] = Wc2t[n][i]; dzc2 read from the own C row)
-    float gz1c[kWidth];
-#pragma unroll
-    for (int i = 0; i < kWidth; ++i) gz1c[i] = 0.0f;
-#pragma unroll 1
+    __syncthreads();
+    // ---- dL/dzc2 = (hc2 > 0) (go Wc3^T), per sample, in place of hc2
+#pragma unroll 8
     for (int n = 0; n < kWidth; ++n) {
-      const float gzn = my_C[n];
-#pragma unroll
-      for (int i4 = 0; i4 < kWidth / 4; ++i4) {
-        const float4 w = Wc2t[n * (kWidth / 4) + i4];
-        gz1c[4 * i4] = fmaf(w.x, gzn, gz1c[4 * i4]);
-        gz1c[4 * i4 + 1] = fmaf(w.y, gzn, gz1c[4 * i4 + 1]);
-        gz1c[4 * i4 + 2] = fmaf(w.z, gzn, gz1c[4 * i4 + 2]);
-        gz1c[4 * i4 + 3] = fmaf(w.w, gzn, gz1c[4 * i4 + 3]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4) {
-      const float4 hv = *reinterpret_cast<const float4*>(my_B + q);
-      gz1c[q] = hv.x > 0.0f ? gz1c[q] : 0.0f;
-      gz1c[q + 1] = hv.y > 0.0f ? gz1c[q + 1] : 0.0f;
-      gz1c[q + 2] = hv.z > 0.0f ? gz1c[q + 2] : 0.0f;
-      gz1c[q + 3] = hv.w > 0.0f ? gz1c[q + 3] : 0.0f;
+      const float4 w3 = *reinterpret_cast<const float4*>(Wc3 + 4 * n);
+      float* at = s_A + n * kUPitch + tid;
+      *at = *at > 0.0f ? w3.x * go[0] + w3.y * go[1] + w3.z * go[2] : 0.0f;
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kWidth; q += 4)
-      *reinterpret_cast<float4*>(my_B + q) = make_float4(gz1c[q], gz1c[q + 1], gz1c[q + 2], gz1c[q + 3]);
-    __syncthreads();
-    // ---- Wc1[j][n] += sum_s xc[s][j] dzc1[s][n]
+    // ---- Wc2 += hc1^T dzc2
     {
-      const int j = tid >> 3, n0 = (tid & 7) * 8;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float xv = s_X[s * kSplitXPitch + j];
-        const float4* qr = reinterpret_cast<const float4*>(s_B + s * kActPitch + n0);
-#pragma unroll
-        for (int q4 = 0; q4 < 2; ++q4) {
-          const float4 v = qr[q4];
-          aWc1[4 * q4] = fmaf(xv, v.x, aWc1[4 * q4]);
-          aWc1[4 * q4 + 1] = fmaf(xv, v.y, aWc1[4 * q4 + 1]);
-          aWc1[4 * q4 + 2] = fmaf(xv, v.z, aWc1[4 * q4 + 2]);
-          aWc1[4 * q4 + 3] = fmaf(xv, v.w, aWc1[4 * q4 + 3]);
-        }
-      }
+      float dw[4][4];
+      tile_gemm_dw<4>(s_D, s_A, ib, nb, dw);
+      add_block<4, 4>(aWc2, dw);
     }
-    // ---- dL/dg = (Wc1 dzc1)[0..15] + dL/dg0 from the density (dzc1 read from the own B row)
-    float gg[kGeo];
-#pragma unroll
-    for (int m = 0; m < kGeo; ++m) gg[m] = 0.0f;
-#pragma unroll 1
-    for (int n = 0; n < kWidth; ++n) {
-      const float gzn = my_B[n];
-#pragma unroll
-      for (int m4 = 0; m4 < kGeo / 4; ++m4) {
-        const float4 w = Wc1t[n * (kColorIn / 4) + m4];  // Wc1[4 m4 + j][n]
-        gg[4 * m4] = fmaf(w.x, gzn, gg[4 * m4]);
-        gg[4 * m4 + 1] = fmaf(w.y, gzn, gg[4 * m4 + 1]);
-        gg[4 * m4 + 2] = fmaf(w.z, gzn, gg[4 * m4 + 2]);
-        gg[4 * m4 + 3] = fmaf(w.w, gzn, gg[4 * m4 + 3]);
-      }
-    }
-    gg[0] += go_d;
-    // ---- recompute h1 of the density MLP into the own C row (after everyone read B and X)
     __syncthreads();
-#pragma unroll 4
-    for (int n = 0; n < kWidth; ++n) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int i4 = 0; i4 < kIn / 4; ++i4) {
-        const float4 w = Wd1t[n * (kIn / 4) + i4];
-        acc = fmaf(feat[4 * i4], w.x, acc);
-        acc = fmaf(feat[4 * i4 + 1], w.y, acc);
-        acc = fmaf(feat[4 * i4 + 2], w.z, acc);
-        acc = fmaf(feat[4 * i4 + 3], w.w, acc);
-      }
-      my_C[n] = fmaxf(acc, 0.0f);
-    }
-#pragma unroll
-    for (int q = 0; q < kGeo; q += 4)
-      *reinterpret_cast<float4*>(my_X + q) = make_float4(gg[q], gg[q + 1], gg[q + 2], gg[q + 3]);
+    // ---- dL/dzc1 = (hc1 > 0) (dzc2 Wc2^T), in place of hc1
+    tile_gemm_abt<kWidth, 8>(s_A, Wc2, sb, 8 * ub, acc);
+    tile_store_masked(s_D, sb, 8 * ub, acc);
     __syncthreads();
-    // ---- Wd2[n][m] += sum_s h1[s][n] dg[s][m]
+    // ---- Wc1 += xc^T dzc1; dL/dg = (dzc1 Wc1^T)[0..15], plus dL/dg0 through the density
     {
-      const int n = tid >> 2, m0 = (tid & 3) * 4;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float hv = s_C[s * kActPitch + n];
-        const float4 v = *reinterpret_cast<const float4*>(s_X + s * kSplitXPitch + m0);
-        aWd2[0] = fmaf(hv, v.x, aWd2[0]);
-        aWd2[1] = fmaf(hv, v.y, aWd2[1]);
-        aWd2[2] = fmaf(hv, v.z, aWd2[2]);
-        aWd2[3] = fmaf(hv, v.w, aWd2[3]);
-      }
+      float dw[2][4];
+      tile_gemm_dw<2>(s_C, s_D, ib, nb, dw);
+      add_block<2, 4>(aWc1, dw);
     }
-    // ---- dL/dz1 = (h1 > 0) Wd2 dg, in place in the own C row once everyone has read C; feat -> B
-    __syncthreads();
-#pragma unroll 4
-    for (int n = 0; n < kWidth; ++n) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int m4 = 0; m4 < kGeo / 4; ++m4) {
-        const float4 w = Wd2[n * (kGeo / 4) + m4];
-        acc = fmaf(w.x, gg[4 * m4], acc);
-        acc = fmaf(w.y, gg[4 * m4 + 1], acc);
-        acc = fmaf(w.z, gg[4 * m4 + 2], acc);
-        acc = fmaf(w.w, gg[4 * m4 + 3], acc);
-      }
-      my_C[n] = my_C[n] > 0.0f ? acc : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < kIn; q += 4)
-      *reinterpret_cast<float4*>(my_B + q) = make_float4(feat[q], feat[q + 1], feat[q + 2], feat[q + 3]);
-    __syncthreads();
-    // ---- Wd1[j][n] += sum_s feat[s][j] dz1[s][n]
     {
-      const int j = tid >> 3, n0 = (tid & 7) * 8;
-      for (int s = 0; s < kBwdThreads; ++s) {
-        const float fv = s_B[s * kActPitch + j];
-        const float4* qr = reinterpret_cast<const float4*>(s_C + s * kActPitch + n0);
-#pragma unroll
-        for (int q4 = 0; q4 < 2; ++q4) {
-          const float4 v = qr[q4];
-          aWd1[4 * q4] = fmaf(fv, v.x, aWd1[4 * q4]);
-          aWd1[4 * q4 + 1] = fmaf(fv, v.y, aWd1[4 * q4 + 1]);
-          aWd1[4 * q4 + 2] = fmaf(fv, v.z, aWd1[4 * q4 + 2]);
-          aWd1[4 * q4 + 3] = fmaf(fv, v.w, aWd1[4 * q4 + 3]);
-        }
+      float dg[8][2];
+      tile_gemm_abt<kWidth, 2>(s_D, Wc1, sb, 2 * ub, dg);
+      if (ub == 0) {
+        const float4 d0 = *reinterpret_cast<const float4*>(s_O + 3 * kUPitch + 4 * sb);
+        const float4 d1 = *reinterpret_cast<const float4*>(s_O + 3 * kUPitch + 128 + 4 * sb);
+        dg[0][0] += d0.x;
+        dg[1][0] += d0.y;
+        dg[2][0] += d0.z;
+        dg[3][0] += d0.w;
+        dg[4][0] += d1.x;
+        dg[5][0] += d1.y;
+        dg[6][0] += d1.z;
+        dg[7][0] += d1.w;
       }
+      __syncthreads();  // xc and dzc1 fully read
+      tile_store<2>(s_C, sb, 2 * ub, dg);
     }
-    // ---- dL/dfeat = Wd1 dz1 (dz1 from the own C row), then the table scatter
+    // ---- the features again -> D rows 0..31
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) s_D[j * kUPitch + tid] = valid ? __ldcs(rec + j * kBwdThreads) : 0.0f;
+    __syncthreads();
+    // ---- density MLP backward: h1 again -> A; Wd2 += h1^T dg; dz1 = (h1 > 0) (dg Wd2^T)
+    tile_gemm_ab<kIn>(s_D, Wd1, sb, 8 * ub, acc);
+    relu8x8(acc);
+    tile_store<8>(s_A, sb, 8 * ub, acc);
+    __syncthreads();
+    {
+      float dw[4][1];
+      tile_gemm_dw<4, 1>(s_A, s_C, ib, nb, dw);
+      add_block<4, 1>(aWd2, dw);
+    }
+    tile_gemm_abt<kGeo, 8, kGeo>(s_C, Wd2, sb, 8 * ub, acc);
+    __syncthreads();  // h1 fully read
+    tile_store_masked(s_A, sb, 8 * ub, acc);
+    __syncthreads();
+    // ---- Wd1 += F^T dz1; dL/dfeatures = dz1 Wd1^T -> D rows 0..31
+    {
+      float dw[2][4];
+      tile_gemm_dw<2>(s_D, s_A, ib, nb, dw);
+      add_block<2, 4>(aWd1, dw);
+    }
+    {
+      float gx[8][4];
+      tile_gemm_abt<kWidth, 4>(s_A, Wd1, sb, 4 * ub, gx);
+      __syncthreads();  // features fully read
+      tile_store<4>(s_D, sb, 4 * ub, gx);
+    }
+    __syncthreads();
+    // ---- table gradients (thread = sample)
     if (valid) {
       float gfeat[kIn];
 #pragma unroll
-      for (int j = 0; j < kIn; ++j) gfeat[j] = 0.0f;
-#pragma unroll 1
-      for (int n = 0; n < kWidth; ++n) {
-        const float gzn = my_C[n];
-#pragma unroll
-        for (int i4 = 0; i4 < kIn / 4; ++i4) {
-          const float4 w = Wd1t[n * (kIn / 4) + i4];
-          gfeat[4 * i4] = fmaf(w.x, gzn, gfeat[4 * i4]);
-          gfeat[4 * i4 + 1] = fmaf(w.y, gzn, gfeat[4 * i4 + 1]);
-          gfeat[4 * i4 + 2] = fmaf(w.z, gzn, gfeat[4 * i4 + 2]);
-          gfeat[4 * i4 + 3] = fmaf(w.w, gzn, gfeat[4 * i4 + 3]);
-        }
-      }
+      for (int j = 0; j < kIn; ++j) gfeat[j] = s_D[j * kUPitch + tid];
       scatter_table_grad(p.lp, gtab, u, gfeat);
     }
   }
-  if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, tid);
+  if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, ib, nb);
   // the shared colour block: once per CTA
   float* gc = p.grad_mlp + (size_t)p.K * kDensityParams;
-  {
-    const int n = tid >> 2, m = tid & 3;
-    if (aWc3 != 0.0f) atomicAdd(gc + kColorIn * kWidth + kWidth * kWidth + n * kOut + m, aWc3);
-    const int i = tid >> 2, n0 = (tid & 3) * 16;
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (aWc2[q] != 0.0f) atomicAdd(gc + kColorIn * kWidth + i * kWidth + n0 + q, aWc2[q]);
-    const int j = tid >> 3, m0 = (tid & 7) * 8;
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (aWc1[q] != 0.0f) atomicAdd(gc + j * kWidth + m0 + q, aWc1[q]);
-  }
+    for (int c = 0; c < 4; ++c)
+      if (aWc1[a][c] != 0.0f) atomicAdd(gc + (ib + 16 * a) * kWidth + nb + 16 * c, aWc1[a][c]);
+  float* gc2 = gc + kColorIn * kWidth;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (aWc2[a][c] != 0.0f) atomicAdd(gc2 + (ib + 16 * a) * kWidth + nb + 16 * c, aWc2[a][c]);
+  if (aWc3 != 0.0f) atomicAdd(gc2 + kWidth * kWidth + tid, aWc3);  // [n][m] at n * 4 + m = tid
 }
 
 }  // namespace nerfxl
@@ -954,7 +913,10 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   p.chunks = reinterpret_cast<const Slot*>(ws + L.chunks);
   p.n_tiles = reinterpret_cast<const int32_t*>(ws + L.hdr) + 1;
   p.dpart = dpart;
-  p.rec32 = (s->flags & NERFXL_SAVE_FEATURES) && L.rec32 ? reinterpret_cast<const float*>(ws + L.rec32) : nullptr;
+  p.rec_in = (s->flags & NERFXL_SAVE_FEATURES) != 0;
+  // the fused kernel encodes again without the forward's records; the split
+  // one records the features it encodes and reads them back
+  p.rec32 = f->arch == NERFXL_ARCH_SPLIT || p.rec_in ? reinterpret_cast<float*>(ws + L.rec32) : nullptr;
   p.grad_tables = grad_tables;
   p.grad_mlp = grad_mlp;
   if (f->arch == NERFXL_ARCH_SPLIT) {

@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
 #pragma unroll
       for (int q = 0; q < kIn; ++q) feat[q] = 0.0f;
     }
-    if (!kSplit && p.rec32) {  // records for the backward: feature j of sample (warp, lane), unit-major
+    if (p.rec32) {  // records for the backward: feature j of sample (warp, lane), unit-major
       float* rec = p.rec32 + (size_t)t * kIn * (kWarp * kChunksPerTile) + warp * kWarp + lane;
 #pragma unroll
       for (int q = 0; q < kIn; ++q) __stcs(rec + q * (kWarp * kChunksPerTile), feat[q]);
@@ -692,7 +692,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
     L.rec_pos = take(sizeof(int32_t) * R * mc);
   }
   L.rec32 = 0;
-  if (for_backward && f->mlp_dtype == NERFXL_F32 && f->arch == NERFXL_ARCH_FUSED)
+  if (for_backward && f->mlp_dtype == NERFXL_F32)
     L.rec32 = take(sizeof(float) * kIn * kWarp * kChunksPerTile * (size_t)((L.chunk_cap + kChunksPerTile - 1) / kChunksPerTile));
   L.smp4 = L.smp2 = 0;
   if (s->flags & NERFXL_SAMPLE_COMPOSITE) {
@@ -961,7 +961,7 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
   p.smp2 = per_sample ? reinterpret_cast<float2*>(ws + L.smp2) : nullptr;
   const bool split = f->arch == NERFXL_ARCH_SPLIT;
   p.rec32 = nullptr;
-  if ((s->flags & NERFXL_SAVE_FEATURES) && !split) {
+  if (s->flags & NERFXL_SAVE_FEATURES) {
     const Layout LB = layout(f, s, n_rays, 1);
     if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
     p.rec32 = reinterpret_cast<float*>(ws + LB.rec32);

@@ -96,12 +96,15 @@ def test_occupancy_and_split_arguments_on_the_host(lib):
     d.mlp_dtype = N.E4M3
     assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0) == 0
     d.mlp_dtype = N.BF16
-    # both representations keep the same per-tile records for the tensor-core backward;
-    # the FP32 MLP recomputes and keeps none
+    # both representations keep the same records for the backward: the
+    # tensor-core backward's per-tile records with a 16-bit MLP (about 116
+    # bytes per sample row), the FP32 features (128 bytes) with an FP32 MLP
     with_rec = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 1)
     assert with_rec == lib.nerfxl_workspace_bytes(ctypes.byref(_fused_bf16()), ctypes.byref(s), 1000, 1)
     d.mlp_dtype = N.F32
-    assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 1) < with_rec
+    f32_rec = lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 1)
+    assert f32_rec == lib.nerfxl_workspace_bytes(ctypes.byref(_desc()), ctypes.byref(s), 1000, 1)
+    assert lib.nerfxl_workspace_bytes(ctypes.byref(d), ctypes.byref(s), 1000, 0) < f32_rec
     d.mlp_dtype = N.BF16
     d.arch = 7
     assert lib.nerfxl_field_mlp_params(ctypes.byref(d)) == -1

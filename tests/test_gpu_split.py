@@ -91,7 +91,13 @@ def test_split_colour_depends_on_view_direction():
     assert np.abs(rgb[0] - rgb[1]).max() > 1e-3
 
 
-def test_split_backward_matches_oracle():
+@pytest.mark.parametrize("save", [False, True])
+def test_split_backward_matches_oracle(save):
+    """FP32 split backward: with the forward's feature records
+    (NERFXL_SAVE_FEATURES) or with the backward encoding and recording the
+    features itself, both against the oracle's gradients."""
+    import dataclasses
+
     from paper_2404_16221_b300 import api
 
     w, t, m, of, gf = _split()
@@ -99,7 +105,7 @@ def test_split_backward_matches_oracle():
     R = len(o)
     g = sy.rng(63, "misc")
     gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
-    samp = H.sampling(w)
+    samp = dataclasses.replace(H.sampling(w), flags=api.SAVE_FEATURES if save else 0)
     ws = api.alloc_workspace(gf, samp, R, for_backward=True)
     api.render_fwd(gf, samp, o, d, workspace=ws)
     dev = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()

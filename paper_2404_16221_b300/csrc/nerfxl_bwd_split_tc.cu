@@ -1,7 +1,16 @@
 // Backward of the split representation on the tensor cores (16-bit MLPs,
 // FP32 accumulation in tensor memory). One CTA of 16 warps per SM takes
-// 128-row tiles (4 chunk slots of one region); warp w serves rows 32 (w % 4) + lane
-// (its TMEM lane quarter) and column / level group w / 4. Per tile:
+// 128-row tiles (4 chunk slots of one region), in two roles:
+//   compute warps 0-7   the MMA chain of one tile at a time; warp w serves
+//                       rows 32 (w % 4) + lane (its TMEM lane quarter) and
+//                       columns 32 (w / 4) .. + 31 of the 64-wide products
+//   scatter warps 8-15  scatter the previous tile's dL/dX into the region's
+//                       table gradient: warp 8 + w reads its lane quarter's
+//                       columns of one of two dL/dX buffers in TMEM (levels
+//                       8 (w / 4) .. + 7), while the compute warps run the
+//                       next tile; hand-off through full / empty mbarriers
+// The table scatter is bound by the SM's rate for scattered vector atomics,
+// so it runs beside the chain instead of on its critical path. Per tile:
 //   records   written by the forward for this tile: X exactly as its first
 //             MMA read it; per row the region coordinates, interval and ray
 //             direction; per chunk the sample count and, from the composite
@@ -15,8 +24,8 @@
 //             logits) goC, dL/dG0
 //   colour    Gz2 = (Hc2 > 0) (goC Wc3^T); Gz1 = (Hc1 > 0) (Gz2 Wc2^T);
 //             dG = (Gz1 Wc1^T)[0..15] + dL/dG0 e0
-//   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T -> table scatter-add,
-//             one level per MMA step of the next tile (under the MMA waits)
+//   density   Gz0 = (H1 > 0) (dG Wd2^T); dX = Gz0 Wd1^T into TMEM buffer
+//             (tile & 1) -> table scatter-add by the scatter warps
 //   weights   DW3 += [Hc2 | Hc1]^T goC, DWc += [Gz2 | Gz1]^T [Hc1 | Xc],
 //             DWd += [Gz0 | dG]^T [X | H1], MN-major reads of the row-major
 //             activation tiles (the samples are the contraction); DW3 and
@@ -29,9 +38,9 @@
 // 32 outputs (Wc1^T and Wd1^T), staged K-major. Gradients enter the products
 // as single 16-bit values.
 // Every wait is bounded: on expiry the kernel flags kErrTimeout, frees its
-// tensor memory and returns. One block barrier per MMA step: it publishes the
-// step's shared-memory operands and carries any timed-out wait of the step
-// before; each thread waits on the commit itself.
+// tensor memory and returns. One compute-warp barrier per MMA step: it
+// publishes the step's shared-memory operands and carries any timed-out wait
+// of the step before; each compute thread waits on the commit itself.
 
 #include <cuda_runtime.h>
 
@@ -45,9 +54,12 @@ namespace {
 
 constexpr int kRowsS = 128;
 constexpr int kThreadsS = 512;
+constexpr int kGroupS = 256;  // threads per role
+constexpr int kBarComputeS = 1, kBarScatterS = 2;
 constexpr int kChunksS = kRowsS / kWarp;
-constexpr uint32_t kColsS = 512;  // 0 D_A, 64 D_B, 128 D_S (N <= 32), 192 DWc, 288 DWd, 384 DW3
-constexpr uint32_t kDA = 0, kDB = 64, kDS = 128, kDWc = 192, kDWd = 288, kDW3 = 384;
+// TMEM columns: 0 D_A, 64 D_B, 128 D_S (N <= 32), 192 DWc, 288 DWd, 384 DW3, 416 and 448 dX (two buffers)
+constexpr uint32_t kColsS = 512;
+constexpr uint32_t kDA = 0, kDB = 64, kDS = 128, kDWc = 192, kDWd = 288, kDW3 = 384, kDX = 416;
 constexpr uint32_t kSpinS = 1u << 24;
 constexpr uint32_t kTile = 128 * 128;  // one 128-row, 128-byte-swizzled tile
 
@@ -75,12 +87,20 @@ constexpr uint32_t kGeoBytesS = 4 * kGeomFloats;
 constexpr uint32_t kGeoStageS = kGeoBytesS + 2 * 16 * 16;  // + 16 chunk positions (4 per slot) x 2 float4
 constexpr uint32_t oGeoS = oX1 + 8192;
 constexpr uint32_t kStageTxS = 8192 + kGeoStageS;  // bytes per stage fill
-constexpr uint32_t oMiscS = (oGeoS + 2 * kGeoStageS + 63) / 64 * 64;  // mbarriers, tmem slot (40 B)
-constexpr uint32_t oBaseS = oMiscS + 64;
+// Hand-off slots 0, 1 from the compute to the scatter warps (dL/dX itself
+// stays in TMEM): the rows' region coordinates u as float [3][128], the 4
+// chunk slots' count words, the region.
+constexpr uint32_t oHandS = oGeoS + 2 * kGeoStageS;
+constexpr uint32_t kHdUS = 0, kHdNvS = 3 * 4 * kRowsS, kHdRegionS = kHdNvS + 16;
+constexpr uint32_t kHandS = kHdRegionS + 16;
+constexpr uint32_t oMiscS = (oHandS + 2 * kHandS + 63) / 64 * 64;  // 8 mbarriers, TMEM base, abort flag
+constexpr uint32_t oBaseS = oMiscS + 128;
 constexpr size_t kSmemS = oBaseS + 1024;
 static_assert(kRowsS == kRecRows, "one backward tile is one record tile");
 static_assert(oX1 % 1024 == 0, "X stages keep the swizzle phase");
 static_assert(kGeoBytesS % 16 == 0 && kGeoStageS % 16 == 0 && oGeoS % 16 == 0, "bulk copies need 16 B");
+static_assert(oHandS % 16 == 0 && kHandS % 16 == 0, "hand-off slot alignment");
+static_assert(kDX + 64 <= kColsS, "tensor memory columns");
 static_assert(kSmemS + 1024 + 4 * 1024 <= 232448, "shared memory");
 
 struct BwdSplitTcParams {
@@ -118,39 +138,39 @@ __device__ __forceinline__ void st_row16(uint32_t tile, uint32_t row, int c, con
 // B tiles of the forward products (row = output n, column = input k) and the
 // K-major transposed tiles of the two dX products with 32 outputs.
 template <bool kBF16>
-__device__ void load_density_bwd(const void* blk, char* sm) {
+__device__ void load_density_bwd(const void* blk, char* sm, int tid, int nthreads) {
   uint16_t* wd1 = reinterpret_cast<uint16_t*>(sm + oWd1);
   uint16_t* wd2 = reinterpret_cast<uint16_t*>(sm + oWd2);
   uint16_t* wd1t = reinterpret_cast<uint16_t*>(sm + oWd1t);
-  for (int i = threadIdx.x; i < kIn * kWidth; i += blockDim.x) {
+  for (int i = tid; i < kIn * kWidth; i += nthreads) {
     const int k = i / kWidth, n = i % kWidth;  // Wd1[k][n]
     const uint16_t b = Half2Of<kBF16>::bits(blk, i);
     wd1[tc::sw128_offset(n, k) >> 1] = b;
     wd1t[tc::sw128_offset(k, n) >> 1] = b;
   }
-  for (int i = threadIdx.x; i < kGeo * kWidth; i += blockDim.x) {
+  for (int i = tid; i < kGeo * kWidth; i += nthreads) {
     const int n = i / kWidth, k = i % kWidth;  // B row n = output n of Wd2 [64][16]
     wd2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kIn * kWidth + k * kGeo + n);
   }
 }
 
 template <bool kBF16>
-__device__ void load_color_bwd(const void* blk, char* sm) {
+__device__ void load_color_bwd(const void* blk, char* sm, int tid, int nthreads) {
   uint16_t* wc1 = reinterpret_cast<uint16_t*>(sm + oWc1);
   uint16_t* wc2 = reinterpret_cast<uint16_t*>(sm + oWc2);
   uint16_t* wc3 = reinterpret_cast<uint16_t*>(sm + oWc3);
   uint16_t* wc1t = reinterpret_cast<uint16_t*>(sm + oWc1t);
-  for (int i = threadIdx.x; i < kColorIn * kWidth; i += blockDim.x) {
+  for (int i = tid; i < kColorIn * kWidth; i += nthreads) {
     const int k = i / kWidth, n = i % kWidth;  // Wc1[k][n]
     const uint16_t b = Half2Of<kBF16>::bits(blk, i);
     wc1[tc::sw128_offset(n, k) >> 1] = b;
     wc1t[tc::sw128_offset(k, n) >> 1] = b;
   }
-  for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+  for (int i = tid; i < kWidth * kWidth; i += nthreads) {
     const int k = i / kWidth, n = i % kWidth;
     wc2[tc::sw128_offset(n, k) >> 1] = Half2Of<kBF16>::bits(blk, kColorIn * kWidth + i);
   }
-  for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
+  for (int i = tid; i < 16 * kWidth; i += nthreads) {
     const int n = i / kWidth, k = i % kWidth;
     wc3[tc::sw128_offset(n, k) >> 1] =
         n < 3 ? Half2Of<kBF16>::bits(blk, kColorIn * kWidth + kWidth * kWidth + k * kOut + n) : 0;
@@ -198,419 +218,428 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   extern __shared__ __align__(1024) char s_raw[];
   char* sm = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = tc::smem_u32(sm);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMiscS);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMiscS + 8);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + oMiscS + 16);  // record stages 0, 1 filled
-  uint64_t* drain = reinterpret_cast<uint64_t*>(sm + oMiscS + 32);  // error path: all MMAs done
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + oMiscS);  // MMA completion
+  uint64_t* full = mbar + 1;                                   // record stages 0, 1 filled
+  uint64_t* hfull = mbar + 3;                                  // hand-off slots 0, 1 written
+  uint64_t* hempty = mbar + 5;                                 // hand-off slots 0, 1 read
+  uint64_t* drain = mbar + 7;                                  // error path: all MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + oMiscS + 64);
+  volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(sm + oMiscS + 68);
   int32_t* s_base = reinterpret_cast<int32_t*>(sm + oBaseS);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
-  const int q = warp & 3, g = warp >> 2;
-  const uint32_t row = (uint32_t)(q * kWarp + lane);
 
   for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   // zero the activation and gradient tiles once (unused columns of the
   // 16-column tiles feed rows of the weight gradients that are never read)
   for (uint32_t i = tid; i < oWd1 / 16; i += blockDim.x) tc::st_shared_v4(sb + 16 * i, 0u, 0u, 0u, 0u);
-  load_color_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm);
+  load_color_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)p.K * kDensityParams * 2, sm, tid, blockDim.x);
   if (warp == 0) tc::tmem_alloc(tmem_slot, kColsS);
   if (tid == 0) {
-    tc::mbar_init(mbar, 1);
-    tc::mbar_init(full, 1);
-    tc::mbar_init(full + 1, 1);
-    tc::mbar_init(drain, 1);
+    for (int i = 0; i < 8; ++i) tc::mbar_init(mbar + i, 1);
+    *s_abort = 0;
   }
   tc::fence_proxy_async();  // the zeroed stage-0 tile before the first record copy overwrites it
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-
-  constexpr uint32_t id64 = tc::idesc_f16(kBF16, kRowsS, 64);
-  constexpr uint32_t id32 = tc::idesc_f16(kBF16, kRowsS, 32);
-  constexpr uint32_t id16 = tc::idesc_f16(kBF16, kRowsS, 16);
-  constexpr uint32_t id64_bt = id64 | tc::kMnMajorB;
-  constexpr uint32_t id64_abt = id64 | tc::kMnMajorA | tc::kMnMajorB;
-  constexpr uint32_t id32_abt = id32 | tc::kMnMajorA | tc::kMnMajorB;
-  constexpr uint32_t id16_abt = id16 | tc::kMnMajorA | tc::kMnMajorB;
-
   const int n_sub = *p.n_tiles * (kChunksPerTile / kChunksS);
-  int region = -1;
-  float2* gtab = nullptr;
-  uint32_t phase = 0;
-  bool failed = false, dw_started = false;
+  const int G = (int)gridDim.x;
 
-  // publish shared-memory writes, issue one chain step (plus optional
-  // weight-gradient MMAs behind it), wait for the step's commit
-  // The previous tile's table gradient (this thread's row, levels 4g..4g+3)
-  // is scattered one level per MMA step of the next tile, while the step's
-  // MMAs run: the atomics then share the load/store path with MMA waits
-  // instead of stalling the warps after the chain.
-  float cg[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, cu[3] = {0.0f, 0.0f, 0.0f};
-  bool cvalid = false;
-  float2* cgtab = nullptr;
-  int cpart = 4;  // levels of the carried sample still to scatter start at 4g + cpart
-  auto scatter_part = [&]() {
-    if (cpart < 4) {
-      const int l = 4 * g + cpart;
-      // constant indices keep cg in registers (a computed index would place it in local memory)
-      const float g0 = cpart == 0 ? cg[0] : (cpart == 1 ? cg[2] : (cpart == 2 ? cg[4] : cg[6]));
-      const float g1 = cpart == 0 ? cg[1] : (cpart == 1 ? cg[3] : (cpart == 2 ? cg[5] : cg[7]));
-      if (cvalid && l < p.lp.L) scatter_one(p.lp, cgtab, cu, l, g0, g1);
-      ++cpart;
-    }
-  };
-
-  // One barrier per step: the publishing barrier also agrees on any earlier
-  // timed-out wait; every thread then waits on the step's commit itself.
-  bool timed_out = false;
-  auto step = [&](auto&& issue) -> bool {
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    if (__syncthreads_or(timed_out)) return false;
-    if (tid == 0) {
+  if (warp >= kGroupS / kWarp) {
+    // ===================== scatter warps =====================
+    // warp (q, h): rows 32 q .. 32 q + 31 (its TMEM lane quarter), levels 8 h .. 8 h + 7
+    const int sw = warp - kGroupS / kWarp, q = sw & 3, h = sw >> 2;
+    const uint32_t row = (uint32_t)(q * kWarp + lane);
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    int it = 0;
+    for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
+      const int b = it & 1;
+      const bool ok = tc::mbar_wait_bounded(hfull + b, (uint32_t)(it >> 1) & 1u, kSpinS);
+      if (tc::bar_or(kBarScatterS, kGroupS, !ok || *s_abort != 0)) {
+        if (!ok && tid == kGroupS) atomicOr(p.err, kErrTimeout);
+        break;
+      }
       tc::fence_after_sync();
-      issue();
+      float gx[16];
+      tc::tmem_ld16(tq + kDX + 32 * (uint32_t)b + 16 * (uint32_t)h, gx);  // dL/dX, levels 8h..8h+7
+      const char* hd = sm + oHandS + (uint32_t)b * kHandS;
+      const SlotCount sc = slot_count(reinterpret_cast<const int32_t*>(hd + kHdNvS)[q], lane);
+      const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegionS);
+      const float* hu = reinterpret_cast<const float*>(hd + kHdUS);
+      const float u[3] = {hu[row], hu[kRowsS + row], hu[2 * kRowsS + row]};
+      tc::tmem_ld_wait();
+      tc::fence_before_sync();
+      tc::bar_sync(kBarScatterS, kGroupS);  // slot and TMEM buffer read by every scatter thread
+      if (tid == kGroupS) tc::mbar_arrive(hempty + b);
+      if (sc.sl < sc.n) {
+        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (8 * h + j < p.lp.L) scatter_one(p.lp, gtab, u, 8 * h + j, gx[2 * j], gx[2 * j + 1]);
+      }
     }
-    scatter_part();
-    timed_out = !tc::mbar_wait_bounded(mbar, phase, kSpinS);
-    phase ^= 1;
-    tc::fence_after_sync();
-    return true;
-  };
+  } else {
+    // ===================== compute warps =====================
+    // warp (q, g): rows 32 q .. 32 q + 31, columns 32 g .. 32 g + 31 of the 64-wide products
+    const int q = warp & 3, g = warp >> 2;
+    const uint32_t row = (uint32_t)(q * kWarp + lane);
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    constexpr uint32_t id64 = tc::idesc_f16(kBF16, kRowsS, 64);
+    constexpr uint32_t id32 = tc::idesc_f16(kBF16, kRowsS, 32);
+    constexpr uint32_t id16 = tc::idesc_f16(kBF16, kRowsS, 16);
+    constexpr uint32_t id64_bt = id64 | tc::kMnMajorB;
+    constexpr uint32_t id64_abt = id64 | tc::kMnMajorA | tc::kMnMajorB;
+    constexpr uint32_t id32_abt = id32 | tc::kMnMajorA | tc::kMnMajorB;
+    constexpr uint32_t id16_abt = id16 | tc::kMnMajorA | tc::kMnMajorB;
 
-  // weight-gradient accumulators -> global (all MMAs complete)
-  auto flush = [&]() {
-    if (!dw_started) return;
-    tc::fence_after_sync();
-    float* gd = p.grad_mlp + (size_t)region * kDensityParams;
-    float* gc = p.grad_mlp + (size_t)p.K * kDensityParams;
-    const int r = (int)row;
-    float v[16];
-    for (int h = g; h < 6; h += 4) {  // DWc: 96 columns
-      tc::tmem_ld16(tq + kDWc + 16 * h, v);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = 16 * h + i;
-        if (r < 64 && c < 64) atomicAdd(gc + kColorIn * kWidth + c * kWidth + r, v[i]);          // dWc2[c][r]
-        else if (r >= 64 && c >= 64) atomicAdd(gc + (c - 64) * kWidth + (r - 64), v[i]);        // dWc1[c-64][r-64]
-      }
-    }
-    for (int h = g; h < 6; h += 4) {  // DWd: 96 columns
-      tc::tmem_ld16(tq + kDWd + 16 * h, v);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = 16 * h + i;
-        if (r < 64 && c < 32) atomicAdd(gd + c * kWidth + r, v[i]);                                // dWd1[c][r]
-        else if (r >= 64 && r < 64 + kGeo && c >= 32) atomicAdd(gd + kIn * kWidth + (c - 32) * kGeo + (r - 64), v[i]);
-      }
-    }
-    if (g == 0) {  // DW3: rows 0..63 = Hc2 index, columns 0..2
-      tc::tmem_ld8(tq + kDW3, v);
-      tc::tmem_ld_wait();
-      if (r < 64)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) atomicAdd(gc + kColorIn * kWidth + kWidth * kWidth + r * kOut + m, v[m]);
-    }
-    dw_started = false;
-  };
+    int region = -1;
+    uint32_t phase = 0;
+    bool failed = false, dw_started = false;
 
-  // Thread kCopier issues the record copies (thread 0 issues the MMAs);
-  // pend0 / pend1 = iteration whose records are in flight into stage 0 / 1 (-1: none).
-  constexpr int kCopier = kWarp;
-  int pend0 = -1, pend1 = -1;
-  auto issue = [&](int it, int t) {
-    const int s = it & 1;
-    tc::fence_proxy_async();  // order earlier generic accesses of the stage before the overwrite
-    tc::mbar_expect_tx(full + s, kStageTxS);
-    const uint32_t geo = sb + oGeoS + (uint32_t)s * kGeoStageS;
-    const uint64_t pol = tc::policy_evict_first();  // read once: keep the gradient lines in L2
-    tc::bulk_g2s_hint(sb + (s ? oX1 : oX), p.rec_feat + (size_t)t * (kRecFeatBytes / 16), 8192, full + s, pol);
-    tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeomFloats, kGeoBytesS, full + s, pol);
-    tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 32, 512, full + s, pol);
-    (s ? pend1 : pend0) = it;
-  };
-  if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
+    // One compute barrier per step: it publishes the step's shared-memory
+    // operands and agrees on any earlier timed-out wait; every compute thread
+    // then waits on the step's commit itself.
+    bool timed_out = false;
+    auto step = [&](auto&& issue) -> bool {
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      if (tc::bar_or(kBarComputeS, kGroupS, timed_out)) return false;
+      if (tid == 0) {
+        tc::fence_after_sync();
+        issue();
+      }
+      timed_out = !tc::mbar_wait_bounded(mbar, phase, kSpinS);
+      phase ^= 1;
+      tc::fence_after_sync();
+      return true;
+    };
+    // relu of this thread's 32 columns of accumulator `col` -> 16-bit tile;
+    // returns the mask of positive values
+    auto relu_store = [&](uint32_t col, uint32_t tile) -> uint32_t {
+      float v[32];
+      tc::tmem_ld16(tq + col + 32 * g, v);
+      tc::tmem_ld16(tq + col + 32 * g + 16, v + 16);
+      tc::tmem_ld_wait();
+      uint32_t m = 0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (v[i] > 0.0f) m |= 1u << i;
+        else v[i] = 0.0f;
+      }
+      st_row16<kBF16>(tile, row, 2 * g, v);
+      st_row16<kBF16>(tile, row, 2 * g + 1, v + 16);
+      return m;
+    };
+    // this thread's 32 columns of accumulator `col`, zero where `mask` is clear -> 16-bit tile
+    auto mask_store = [&](uint32_t col, uint32_t tile, uint32_t mask) {
+      float v[32];
+      tc::tmem_ld16(tq + col + 32 * g, v);
+      tc::tmem_ld16(tq + col + 32 * g + 16, v + 16);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (!((mask >> i) & 1u)) v[i] = 0.0f;
+      st_row16<kBF16>(tile, row, 2 * g, v);
+      st_row16<kBF16>(tile, row, 2 * g + 1, v + 16);
+    };
 
-  int it = 0;
-  for (int t = blockIdx.x; t < n_sub; t += gridDim.x, ++it) {
-    const int k = region_of_chunk(s_base, p.K, t * kChunksS);
-    const int s = it & 1;
-    if (k != region) {
-      flush();
-      __syncthreads();
-      load_density_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)k * kDensityParams * 2, sm);
-      region = k;
-      gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-    }
-    // ---- the next tile's records into the other stage (free: its last readers,
-    //      the previous tile's first and last MMAs, have completed)
-    if (tid == kCopier && t + (int)gridDim.x < n_sub) issue(it + 1, t + (int)gridDim.x);
-    // ---- this tile's records: X (the record is the tile's shared-memory image,
-    //      read in place by the MMAs), the row's region coordinates (for the
-    //      scatter), interval (render adjoint, g == 0) and direction (SH,
-    //      g == 1), the chunk's adjoints
-    if (!tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpinS)) timed_out = true;
-    else if (tid == kCopier) (s ? pend1 : pend0) = -1;
-    const uint32_t xs = sb + (s ? oX1 : oX);
-    const float* geo = reinterpret_cast<const float*>(sm + oGeoS + (uint32_t)s * kGeoStageS);
-    const float4* dps = reinterpret_cast<const float4*>(sm + oGeoS + (uint32_t)s * kGeoStageS + kGeoBytesS);
-    const int32_t nword = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
-    const SlotCount sc = slot_count(nword, lane);
-    const bool chunk_ok = nword != 0, valid = sc.sl < sc.n;  // chunk_ok: warp-uniform
-    float tr = 0.0f, dl = 0.0f, u[3], dir[3] = {0.0f, 0.0f, 0.0f};
-    float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
+    // weight-gradient accumulators -> global (all MMAs complete)
+    auto flush = [&]() {
+      if (!dw_started) return;
+      tc::fence_after_sync();
+      float* gd = p.grad_mlp + (size_t)region * kDensityParams;
+      float* gc = p.grad_mlp + (size_t)p.K * kDensityParams;
+      const int r = (int)row;
+      float v[16];
+      for (int hh = g; hh < 6; hh += 2) {  // DWc: 96 columns
+        tc::tmem_ld16(tq + kDWc + 16 * hh, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) u[ax] = geo[ax * kRecRows + row];
-    if (g == 0) {
-      tr = geo[3 * kRecRows + row];
-      dl = geo[4 * kRecRows + row];
-      if (chunk_ok && sc.n > 0) {  // (an unused part of the slot keeps zero adjoints)
-        const float4 a0 = dps[2 * (4 * q + sc.part)], a1 = dps[2 * (4 * q + sc.part) + 1];
-        gtc = a0.x;
-        gC[0] = a0.y;
-        gC[1] = a0.z;
-        gC[2] = a0.w;
-        gA = a1.x;
-        gD = a1.y;
-        gL = a1.z;
+        for (int i = 0; i < 16; ++i) {
+          const int c = 16 * hh + i;
+          if (r < 64 && c < 64) atomicAdd(gc + kColorIn * kWidth + c * kWidth + r, v[i]);          // dWc2[c][r]
+          else if (r >= 64 && c >= 64) atomicAdd(gc + (c - 64) * kWidth + (r - 64), v[i]);        // dWc1[c-64][r-64]
+        }
       }
-    } else if (g == 1) {
+      for (int hh = g; hh < 6; hh += 2) {  // DWd: 96 columns
+        tc::tmem_ld16(tq + kDWd + 16 * hh, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) dir[ax] = geo[(5 + ax) * kRecRows + row];
-    }
-    float v[16];
-    uint32_t mH1 = 0, mHc1 = 0, mHc2 = 0;  // ReLU masks of this thread's 16 columns
-    // ---- density: D_A = X Wd1 -> H1
-    if (!step([&] {
-          for (int kk = 0; kk < 2; ++kk)
-            tc::mma_f16(tmem + kDA, tc::desc_sw64(xs + 32 * kk, 16), tc::desc_sw128(sb + oWd1 + 32 * kk), id64,
-                        kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDA + 16 * g, v);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (v[i] > 0.0f) mH1 |= 1u << i;
-      else v[i] = 0.0f;
-    }
-    st_row16<kBF16>(sb + oH1, row, g, v);
-    // ---- G = H1 Wd2 (16 outputs) -> Xc = [G | SH(d)]
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oH1 + 32 * kk), tc::desc_sw128(sb + oWd2 + 32 * kk), id16,
-                        kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    float g0 = 0.0f;
-    if (g == 0) {
-      tc::tmem_ld16(tq + kDS, v);
-      tc::tmem_ld_wait();
-      g0 = v[0];
-      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 0), v);
-      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 1), v + 8);
-    } else if (g == 1) {
-      float sh[kSh];
-      sh4_f32(dir, sh);
-      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 2), sh);
-      st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 3), sh + 8);
-    }
-    // ---- colour: D_A = Xc Wc1 -> Hc1
-    if (!step([&] {
-          for (int kk = 0; kk < 2; ++kk)
-            tc::mma_f16(tmem + kDA, tc::desc_sw64(sb + oXc + 32 * kk, 16), tc::desc_sw128(sb + oWc1 + 32 * kk), id64,
-                        kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDA + 16 * g, v);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (v[i] > 0.0f) mHc1 |= 1u << i;
-      else v[i] = 0.0f;
-    }
-    st_row16<kBF16>(sb + oHc1, row, g, v);
-    // ---- D_B = Hc1 Wc2 -> Hc2
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oHc1 + 32 * kk), tc::desc_sw128(sb + oWc2 + 32 * kk), id64,
-                        kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDB + 16 * g, v);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (v[i] > 0.0f) mHc2 |= 1u << i;
-      else v[i] = 0.0f;
-    }
-    st_row16<kBF16>(sb + oHc2, row, g, v);
-    // ---- o = Hc2 Wc3 (3 of 16 outputs)
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oHc2 + 32 * kk), tc::desc_sw128(sb + oWc3 + 32 * kk), id16,
-                        kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    // ---- chunk-local render adjoint (warp g == 0 of each lane quarter = one slot)
-    float go_d = 0.0f;
-    if (g == 0) {
-      tc::tmem_ld16(tq + kDS, v);
-      tc::tmem_ld_wait();
-      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
-      if (valid) {
-        sigma = expf(g0);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-v[m]));
+        for (int i = 0; i < 16; ++i) {
+          const int c = 16 * hh + i;
+          if (r < 64 && c < 32) atomicAdd(gd + c * kWidth + r, v[i]);                                // dWd1[c][r]
+          else if (r >= 64 && r < 64 + kGeo && c >= 32) atomicAdd(gd + kIn * kWidth + (c - 32) * kGeo + (r - 64), v[i]);
+        }
       }
-      float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
-      if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sc.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sc.width);
-      float go[16];
+      if (g == 0) {  // DW3: rows 0..63 = Hc2 index, columns 0..2
+        tc::tmem_ld8(tq + kDW3, v);
+        tc::tmem_ld_wait();
+        if (r < 64)
 #pragma unroll
-      for (int m = 0; m < 16; ++m) go[m] = 0.0f;
-      if (valid) {
-        go_d = g_sigma * sigma;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
+          for (int m = 0; m < 3; ++m) atomicAdd(gc + kColorIn * kWidth + kWidth * kWidth + r * kOut + m, v[m]);
       }
-      st_row16<kBF16>(sb + oGoC, row, 0, go);
-    }
-    const bool acc = dw_started;
-    // ---- Gz2 = (Hc2 > 0) goC Wc3^T (Wc3 tile read MN-major, K = 16); DW3 += [Hc2 | Hc1]^T goC behind it
-    if (!step([&] {
-          tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGoC), tc::desc_sw128_mn(sb + oWc3, 1024), id64_bt, 0);
-          tc::mma_commit(mbar);
-          for (int kk = 0; kk < 8; ++kk)
-            tc::mma_f16(tmem + kDW3, tc::desc_sw128_mn(sb + oHc2 + 2048 * kk, kTile),
-                        tc::desc_sw128_mn(sb + oGoC + 2048 * kk, 1024), id16_abt, (acc || kk > 0) ? 1u : 0u);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDA + 16 * g, v);
-    tc::tmem_ld_wait();
+      dw_started = false;
+    };
+
+    // Thread kCopier issues the record copies (thread 0 issues the MMAs);
+    // pend0 / pend1 = iteration whose records are in flight into stage 0 / 1 (-1: none).
+    constexpr int kCopier = kWarp;
+    int pend0 = -1, pend1 = -1;
+    auto issue = [&](int it, int t) {
+      const int s = it & 1;
+      tc::fence_proxy_async();  // order earlier generic accesses of the stage before the overwrite
+      tc::mbar_expect_tx(full + s, kStageTxS);
+      const uint32_t geo = sb + oGeoS + (uint32_t)s * kGeoStageS;
+      const uint64_t pol = tc::policy_evict_first();  // read once: keep the gradient lines in L2
+      tc::bulk_g2s_hint(sb + (s ? oX1 : oX), p.rec_feat + (size_t)t * (kRecFeatBytes / 16), 8192, full + s, pol);
+      tc::bulk_g2s_hint(geo, p.rec_geom + (size_t)t * kGeomFloats, kGeoBytesS, full + s, pol);
+      tc::bulk_g2s_hint(geo + kGeoBytesS, p.rec_dpart + (size_t)t * 32, 512, full + s, pol);
+      (s ? pend1 : pend0) = it;
+    };
+    if (tid == kCopier && (int)blockIdx.x < n_sub) issue(0, blockIdx.x);
+
+    int it = 0;
+    for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
+      const int k = region_of_chunk(s_base, p.K, t * kChunksS);
+      const int s = it & 1;
+      if (k != region) {
+        flush();
+        tc::fence_before_sync();
+        tc::bar_sync(kBarComputeS, kGroupS);
+        load_density_bwd<kBF16>(static_cast<const char*>(p.mlp) + (size_t)k * kDensityParams * 2, sm, tid, kGroupS);
+        region = k;
+      }
+      // ---- the next tile's records into the other stage (free: its last readers,
+      //      the previous tile's first and last MMAs, have completed)
+      if (tid == kCopier && t + G < n_sub) issue(it + 1, t + G);
+      // ---- this tile's records: X (the record is the tile's shared-memory image,
+      //      read in place by the MMAs), the row's region coordinates (for the
+      //      hand-off), interval (render adjoint, g == 0) and direction (SH,
+      //      g == 1), the chunk's adjoints
+      if (!tc::mbar_wait_bounded(full + s, (uint32_t)(it >> 1) & 1u, kSpinS)) timed_out = true;
+      else if (tid == kCopier) (s ? pend1 : pend0) = -1;
+      const uint32_t xs = sb + (s ? oX1 : oX);
+      const float* geo = reinterpret_cast<const float*>(sm + oGeoS + (uint32_t)s * kGeoStageS);
+      const float4* dps = reinterpret_cast<const float4*>(sm + oGeoS + (uint32_t)s * kGeoStageS + kGeoBytesS);
+      const int32_t nword = reinterpret_cast<const int32_t*>(geo + kGeomRowFields * kRecRows)[q];
+      const SlotCount sc = slot_count(nword, lane);
+      const bool chunk_ok = nword != 0, valid = sc.sl < sc.n;  // chunk_ok: warp-uniform
+      float tr = 0.0f, dl = 0.0f, dir[3] = {0.0f, 0.0f, 0.0f};
+      float gtc = 0.0f, gC[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f, gD = 0.0f, gL = 0.0f;
+      if (g == 0) {
+        tr = geo[3 * kRecRows + row];
+        dl = geo[4 * kRecRows + row];
+        if (chunk_ok && sc.n > 0) {  // (an unused part of the slot keeps zero adjoints)
+          const float4 a0 = dps[2 * (4 * q + sc.part)], a1 = dps[2 * (4 * q + sc.part) + 1];
+          gtc = a0.x;
+          gC[0] = a0.y;
+          gC[1] = a0.z;
+          gC[2] = a0.w;
+          gA = a1.x;
+          gD = a1.y;
+          gL = a1.z;
+        }
+      } else {
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (!((mHc2 >> i) & 1u)) v[i] = 0.0f;
-    st_row16<kBF16>(sb + oGz2, row, g, v);
-    // ---- Gz1 = (Hc1 > 0) Gz2 Wc2^T (Wc2 tile read MN-major, K = 64)
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz2 + 32 * kk), tc::desc_sw128_mn(sb + oWc2 + 2048 * kk, 1024),
-                        id64_bt, kk);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDB + 16 * g, v);
-    tc::tmem_ld_wait();
+        for (int ax = 0; ax < 3; ++ax) dir[ax] = geo[(5 + ax) * kRecRows + row];
+      }
+      float v[16];
+      // ---- density: D_A = X Wd1 -> H1
+      if (!step([&] {
+            for (int kk = 0; kk < 2; ++kk)
+              tc::mma_f16(tmem + kDA, tc::desc_sw64(xs + 32 * kk, 16), tc::desc_sw128(sb + oWd1 + 32 * kk), id64,
+                          kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      const uint32_t mH1 = relu_store(kDA, sb + oH1);
+      // ---- G = H1 Wd2 (16 outputs) -> Xc = [G | SH(d)]
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oH1 + 32 * kk), tc::desc_sw128(sb + oWd2 + 32 * kk), id16,
+                          kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      float g0 = 0.0f;
+      if (g == 0) {
+        tc::tmem_ld16(tq + kDS, v);
+        tc::tmem_ld_wait();
+        g0 = v[0];
+        st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 0), v);
+        st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 1), v + 8);
+      } else {
+        float sh[kSh];
+        sh4_f32(dir, sh);
+        st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 2), sh);
+        st_chunk8<kBF16>(sb + oXc + sw64_chunk(row, 3), sh + 8);
+      }
+      // ---- colour: D_A = Xc Wc1 -> Hc1
+      if (!step([&] {
+            for (int kk = 0; kk < 2; ++kk)
+              tc::mma_f16(tmem + kDA, tc::desc_sw64(sb + oXc + 32 * kk, 16), tc::desc_sw128(sb + oWc1 + 32 * kk),
+                          id64, kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      const uint32_t mHc1 = relu_store(kDA, sb + oHc1);
+      // ---- D_B = Hc1 Wc2 -> Hc2
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oHc1 + 32 * kk), tc::desc_sw128(sb + oWc2 + 32 * kk), id64,
+                          kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      const uint32_t mHc2 = relu_store(kDB, sb + oHc2);
+      // ---- o = Hc2 Wc3 (3 of 16 outputs)
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oHc2 + 32 * kk), tc::desc_sw128(sb + oWc3 + 32 * kk), id16,
+                          kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      // ---- chunk-local render adjoint (warp g == 0 of each lane quarter = one slot)
+      float go_d = 0.0f;
+      if (g == 0) {
+        tc::tmem_ld16(tq + kDS, v);
+        tc::tmem_ld_wait();
+        float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+          sigma = expf(g0);
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (!((mHc1 >> i) & 1u)) v[i] = 0.0f;
-    st_row16<kBF16>(sb + oGz1, row, g, v);
-    // ---- dXc = Gz1 Wc1^T (32 outputs; G's are the first 16); DWc += [Gz2 | Gz1]^T [Hc1 | Xc] behind it
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oGz1 + 32 * kk), tc::desc_sw128(sb + oWc1t + 32 * kk), id32,
-                        kk);
-          tc::mma_commit(mbar);
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t a = tc::desc_sw128_mn(sb + oGz2 + 2048 * kk, kTile);
-            const uint32_t on = (acc || kk > 0) ? 1u : 0u;
-            tc::mma_f16(tmem + kDWc, a, tc::desc_sw128_mn(sb + oHc1 + 2048 * kk, 1024), id64_abt, on);
-            tc::mma_f16(tmem + kDWc + 64, a, tc::desc_sw64(sb + oXc + 1024 * kk, 512), id32_abt, on);
-          }
-        })) {
-      failed = true;
-      break;
-    }
-    if (g == 0) {
-      tc::tmem_ld16(tq + kDS, v);
-      tc::tmem_ld_wait();
-      v[0] += go_d;  // G0 is also the log density
-      st_row16<kBF16>(sb + oGG, row, 0, v);
-    }
-    // ---- Gz0 = (H1 > 0) dG Wd2^T (Wd2 tile read MN-major, K = 16)
-    if (!step([&] {
-          tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGG), tc::desc_sw128_mn(sb + oWd2, 1024), id64_bt, 0);
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    tc::tmem_ld16(tq + kDA + 16 * g, v);
-    tc::tmem_ld_wait();
+          for (int m = 0; m < 3; ++m) rgb[m] = 1.0f / (1.0f + expf(-v[m]));
+        }
+        float g_sigma = 0.0f, g_rgb[3] = {0.0f, 0.0f, 0.0f};
+        if (chunk_ok) render_chunk_adjoint(sigma, rgb, tr, dl, sc.sl, gtc, gC, gA, gD, gL, g_sigma, g_rgb, sc.width);
+        float go[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (!((mH1 >> i) & 1u)) v[i] = 0.0f;
-    st_row16<kBF16>(sb + oGz0, row, g, v);
-    // ---- dX = Gz0 Wd1^T (32 outputs) and DWd += [Gz0 | dG]^T [X | H1], under one commit: the next
-    //      tile after next overwrites this stage's X at its start
-    if (!step([&] {
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz0 + 32 * kk), tc::desc_sw128(sb + oWd1t + 32 * kk), id32,
-                        kk);
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t a = tc::desc_sw128_mn(sb + oGz0 + 2048 * kk, kTile);
-            const uint32_t on = (acc || kk > 0) ? 1u : 0u;
-            tc::mma_f16(tmem + kDWd, a, tc::desc_sw64(xs + 1024 * kk, 512), id32_abt, on);
-            tc::mma_f16(tmem + kDWd + 32, a, tc::desc_sw128_mn(sb + oH1 + 2048 * kk, 1024), id64_abt, on);
-          }
-          tc::mma_commit(mbar);
-        })) {
-      failed = true;
-      break;
-    }
-    dw_started = true;
-    // ---- table scatter: thread (row, g) takes levels 4g..4g+3 (columns 8g..8g+7 of dX)
-    tc::tmem_ld8(tq + kDB + 8 * g, v);
-    tc::tmem_ld_wait();
-    while (cpart < 4) scatter_part();  // (the chain has nine steps: nothing is left here)
+        for (int m = 0; m < 16; ++m) go[m] = 0.0f;
+        if (valid) {
+          go_d = g_sigma * sigma;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) cg[i] = v[i];
+          for (int m = 0; m < 3; ++m) go[m] = g_rgb[m] * rgb[m] * (1.0f - rgb[m]);
+        }
+        st_row16<kBF16>(sb + oGoC, row, 0, go);
+      }
+      const bool acc = dw_started;
+      // ---- Gz2 = (Hc2 > 0) goC Wc3^T (Wc3 tile read MN-major, K = 16); DW3 += [Hc2 | Hc1]^T goC behind it
+      if (!step([&] {
+            tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGoC), tc::desc_sw128_mn(sb + oWc3, 1024), id64_bt, 0);
+            tc::mma_commit(mbar);
+            for (int kk = 0; kk < 8; ++kk)
+              tc::mma_f16(tmem + kDW3, tc::desc_sw128_mn(sb + oHc2 + 2048 * kk, kTile),
+                          tc::desc_sw128_mn(sb + oGoC + 2048 * kk, 1024), id16_abt, (acc || kk > 0) ? 1u : 0u);
+          })) {
+        failed = true;
+        break;
+      }
+      mask_store(kDA, sb + oGz2, mHc2);
+      // ---- Gz1 = (Hc1 > 0) Gz2 Wc2^T (Wc2 tile read MN-major, K = 64)
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDB, tc::desc_sw128(sb + oGz2 + 32 * kk),
+                          tc::desc_sw128_mn(sb + oWc2 + 2048 * kk, 1024), id64_bt, kk);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      mask_store(kDB, sb + oGz1, mHc1);
+      // ---- dXc = Gz1 Wc1^T (32 outputs; G's are the first 16); DWc += [Gz2 | Gz1]^T [Hc1 | Xc] behind it
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDS, tc::desc_sw128(sb + oGz1 + 32 * kk), tc::desc_sw128(sb + oWc1t + 32 * kk), id32,
+                          kk);
+            tc::mma_commit(mbar);
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t a = tc::desc_sw128_mn(sb + oGz2 + 2048 * kk, kTile);
+              const uint32_t on = (acc || kk > 0) ? 1u : 0u;
+              tc::mma_f16(tmem + kDWc, a, tc::desc_sw128_mn(sb + oHc1 + 2048 * kk, 1024), id64_abt, on);
+              tc::mma_f16(tmem + kDWc + 64, a, tc::desc_sw64(sb + oXc + 1024 * kk, 512), id32_abt, on);
+            }
+          })) {
+        failed = true;
+        break;
+      }
+      if (g == 0) {
+        tc::tmem_ld16(tq + kDS, v);
+        tc::tmem_ld_wait();
+        v[0] += go_d;  // G0 is also the log density
+        st_row16<kBF16>(sb + oGG, row, 0, v);
+      }
+      // ---- Gz0 = (H1 > 0) dG Wd2^T (Wd2 tile read MN-major, K = 16)
+      if (!step([&] {
+            tc::mma_f16(tmem + kDA, tc::desc_sw128(sb + oGG), tc::desc_sw128_mn(sb + oWd2, 1024), id64_bt, 0);
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      mask_store(kDA, sb + oGz0, mH1);
+      // ---- hand-off slot b: free once the scatter warps have read it (and TMEM buffer b) two tiles ago
+      const int b = it & 1;
+      if (it >= 2 && !tc::mbar_wait_bounded(hempty + b, (uint32_t)((it >> 1) + 1) & 1u, kSpinS)) timed_out = true;
+      if (g == 0) {
+        char* hd = sm + oHandS + (uint32_t)b * kHandS;
+        float* hu = reinterpret_cast<float*>(hd + kHdUS);
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) cu[ax] = u[ax];
-    cvalid = valid;
-    cgtab = gtab;
-    cpart = 0;
-    tc::fence_before_sync();
-    if (__syncthreads_or(timed_out)) {  // tiles and TMEM free for the next tile
-      failed = true;
-      break;
+        for (int ax = 0; ax < 3; ++ax) hu[ax * kRowsS + row] = geo[ax * kRecRows + row];
+        if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNvS)[q] = nword;
+        if (tid == 0) *reinterpret_cast<int32_t*>(hd + kHdRegionS) = k;
+      }
+      // ---- dX = Gz0 Wd1^T (32 outputs) into TMEM buffer b for the scatter warps, and
+      //      DWd += [Gz0 | dG]^T [X | H1], under one commit: the next tile after next
+      //      overwrites this stage's X at its start
+      if (!step([&] {
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_f16(tmem + kDX + 32 * (uint32_t)b, tc::desc_sw128(sb + oGz0 + 32 * kk),
+                          tc::desc_sw128(sb + oWd1t + 32 * kk), id32, kk);
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t a = tc::desc_sw128_mn(sb + oGz0 + 2048 * kk, kTile);
+              const uint32_t on = (acc || kk > 0) ? 1u : 0u;
+              tc::mma_f16(tmem + kDWd, a, tc::desc_sw64(xs + 1024 * kk, 512), id32_abt, on);
+              tc::mma_f16(tmem + kDWd + 32, a, tc::desc_sw128_mn(sb + oH1 + 2048 * kk, 1024), id64_abt, on);
+            }
+            tc::mma_commit(mbar);
+          })) {
+        failed = true;
+        break;
+      }
+      dw_started = true;
+      tc::fence_before_sync();
+      if (tc::bar_or(kBarComputeS, kGroupS, timed_out)) {  // slot written, dX landed; tiles free for the next tile
+        failed = true;
+        break;
+      }
+      if (tid == 0) tc::mbar_arrive(hfull + b);
     }
-  }
-  if (!failed) {
-    while (cpart < 4) scatter_part();  // the last tile's table gradient
-    flush();                           // every tile ends with all of its MMAs complete
-  }
-  if (failed && tid == 0) {
-    atomicOr(p.err, kErrTimeout);
-    // let MMAs still in flight land before the tensor memory is freed
-    tc::mma_commit(drain);
-    tc::mbar_wait_bounded(drain, 0u, kSpinS);
-  }
-  if (failed && tid == kCopier) {  // and the record copies still in flight
-    if (pend0 >= 0) tc::mbar_wait_bounded(full, (uint32_t)(pend0 >> 1) & 1u, kSpinS);
-    if (pend1 >= 0) tc::mbar_wait_bounded(full + 1, (uint32_t)(pend1 >> 1) & 1u, kSpinS);
+    if (!failed) flush();  // every tile ends with all of its MMAs complete
+    if (failed && tid == 0) {
+      atomicOr(p.err, kErrTimeout);
+      *s_abort = 1;  // wake the scatter warps; they see the flag and stop
+      tc::mbar_arrive(hfull);
+      tc::mbar_arrive(hfull + 1);
+      // let MMAs still in flight land before the tensor memory is freed
+      tc::mma_commit(drain);
+      tc::mbar_wait_bounded(drain, 0u, kSpinS);
+    }
+    if (failed && tid == kCopier) {  // and the record copies still in flight
+      if (pend0 >= 0) tc::mbar_wait_bounded(full, (uint32_t)(pend0 >> 1) & 1u, kSpinS);
+      if (pend1 >= 0) tc::mbar_wait_bounded(full + 1, (uint32_t)(pend1 >> 1) & 1u, kSpinS);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -794,13 +794,13 @@ def main():
                               "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
                               "%.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src),
-                     "binding_resource": "latency of the compute warps' per-tile chain (four MMA round trips "
-                                         "and their epilogues, one tile in flight per SM): 10.1 ms alone, "
-                                         "~17 ms beside the scatter warps, which share the SM's issue slots "
-                                         "and load/store pipe; not HBM (DRAM traffic 0.15x the algorithmic "
-                                         "bytes, the swept region stays in L2) and not the atomics' request "
-                                         "count (a copy summing same-cell runs first, 37% fewer requests, "
-                                         "ran 3% slower)"},
+                     "binding_resource": "the table-gradient reductions: ~96 lane-addresses per sample "
+                                         "(8 corners x 16 levels, x-pairs sharing one 16-byte vector half "
+                                         "the time) at ~1.35 SM clocks each on the L1-to-L2 path; "
+                                         "instrumented, the scatter warps are busy 16.1-16.4 K cycles per "
+                                         "128-row tile while the compute warps' chain alone takes 9.3 K; "
+                                         "not HBM (DRAM traffic 0.18x the algorithmic bytes, the swept "
+                                         "region stays in L2)"},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }

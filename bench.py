@@ -53,7 +53,8 @@ def parse():
                     help="comma-separated arrival rates (req/s): run only the city32 serving sweep")
     ap.add_argument("--only", type=str, default="",
                     choices=["", "city32_fwd", "city32_train", "grid8_fwd", "grid8_train", "grid8_train_fp32",
-                             "grid8_split_train", "grid8_split_train_fp32"],
+                             "grid8_split_train", "grid8_split_train_fp32", "grid8_fwd_fp32",
+                             "grid8_split_fwd_fp32"],
                     help="profiler captures: run one form alone and print its own line")
     ap.add_argument("--log2-t", type=int, default=0, help="--only: override the hash table size (log2 entries)")
     ap.add_argument("--group-min-mb", type=float, default=0.0,
@@ -318,8 +319,10 @@ def single_form(args, dev):
     CUDA events and one JSON line printed. city32_fwd: the street/city
     forward with FP16 tables and a BF16 MLP; grid8_fwd / grid8_train: the
     mixed grid8 forward and training step; grid8_split_train(_fp32): the
-    split representation's mixed (FP32) training step. --profile-rays keeps the first N
-    rays (a smaller device footprint for captures)."""
+    split representation's mixed (FP32) training step; grid8_fwd_fp32 /
+    grid8_split_fwd_fp32: the FP32 forward of either representation.
+    --profile-rays keeps the first N rays (a smaller device footprint for
+    captures)."""
     import torch
 
     from paper_2404_16221_b300 import api, native as N, synthetic as sy
@@ -333,7 +336,8 @@ def single_form(args, dev):
         w.log2_T = args.log2_t
     E = N.table_entries(w.level_res, w.log2_T)
     fp32 = name.endswith("_fp32")
-    if name.startswith("grid8_split_train"):
+    forward = "_fwd" in name
+    if name.startswith("grid8_split"):
         n_split = api.split_mlp_params(w.K, w.mlp_in, w.W)
         t, _ = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         g = torch.Generator(device=dev)
@@ -341,22 +345,22 @@ def single_form(args, dev):
         m = torch.randn(n_split, generator=g, device=dev) * 0.1
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t if fp32 else t.to(torch.float16),
                                      m if fp32 else m.to(torch.bfloat16), device=dev, arch=N.ARCH_SPLIT)
-    elif name == "grid8_train_fp32":
+    elif fp32:
         t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t, m, device=dev)
     else:
         t, m = sy.field_params_device(w, E, N.mlp_params(w.mlp_in, w.W), dev)
         field = api.PartitionedField(w.boxes, w.level_res, w.log2_T, t.to(torch.float16), m.to(torch.bfloat16),
                                      device=dev)
-    if name.endswith("_fwd"):
-        del t, m  # a forward holds only the 16-bit field
+    if forward:
+        del t, m  # a forward holds only the field it reads
         torch.cuda.empty_cache()
     o, d = sy.workload_rays(w)
     if args.profile_rays > 0:
         o, d = o[:args.profile_rays].copy(), d[:args.profile_rays].copy()
     o, d = torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)
     samp = api.Sampling(w.S, w.max_segments)
-    if name.endswith("_fwd"):
+    if forward:
         ws = api.alloc_workspace(field, samp, len(o))
         step = lambda: api.render_fwd(field, samp, o, d, workspace=ws)
     else:

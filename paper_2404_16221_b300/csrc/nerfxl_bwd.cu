@@ -21,6 +21,7 @@
 
 #include "nerfxl_split.cuh"
 #include "nerfxl_host.h"
+#include "nerfxl_tile.cuh"
 
 namespace nerfxl {
 
@@ -175,100 +176,21 @@ __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, 
 constexpr int kUPitch = 260;
 constexpr size_t kBwdSmemFloatsT = 2 * (size_t)kMlpParams + (size_t)kUPitch * (kIn + 2 * kWidth + kOut);
 
-// acc[i][j] = sum_k A[k][samples i] B[k][n0 + j]; A unit-major, B row-major
-// [K][NB] (NJ = 8 or 2 outputs per thread).
 template <int K, int NJ = 8, int NB = kWidth>
-__device__ __forceinline__ void tile_gemm_ab(const float* __restrict__ A, const float* __restrict__ B, int sb, int n0,
-                                             float acc[8][NJ]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0f;
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kUPitch + 4 * sb);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kUPitch + 128 + 4 * sb);
-    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    float b[NJ];
-    if (NJ == 8) {
-      const float4 b0 = *reinterpret_cast<const float4*>(B + k * NB + n0);
-      const float4 b1 = *reinterpret_cast<const float4*>(B + k * NB + n0 + 4);
-      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) b[j] = bb[j];
-    } else {
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) b[j] = B[k * NB + n0 + j];
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
+__device__ __forceinline__ void tile_gemm_ab(const float* A, const float* B, int sb, int n0, float acc[8][NJ]) {
+  tile_ab<kUPitch, kBwdThreads / 2, K, NJ, NB>(A, B, sb, n0, acc);
 }
-
-// acc[i][j] = sum_k A[k][samples i] W[j0 + j][k]; W row-major with rows of WS
-// (the transposed weight of a dX product), NJ of its rows.
 template <int K, int NJ, int WS = kWidth>
-__device__ __forceinline__ void tile_gemm_abt(const float* __restrict__ A, const float* __restrict__ W, int sb, int j0,
-                                              float acc[8][NJ]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0f;
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kUPitch + 4 * sb);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kUPitch + 128 + 4 * sb);
-    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    float b[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) b[j] = W[(j0 + j) * WS + k];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
+__device__ __forceinline__ void tile_gemm_abt(const float* A, const float* W, int sb, int j0, float acc[8][NJ]) {
+  tile_abt<kUPitch, kBwdThreads / 2, K, NJ, WS>(A, W, sb, j0, acc);
 }
-
-// Weight gradient: acc[a][c] = sum_s P[ib + 16 a][s] Q[nb + 16 c][s] over the
-// 256 samples (both unit-major).
 template <int RA, int RC = 4>
-__device__ __forceinline__ void tile_gemm_dw(const float* __restrict__ P, const float* __restrict__ Q, int ib, int nb,
-                                             float acc[RA][RC]) {
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int c = 0; c < RC; ++c) acc[a][c] = 0.0f;
-#pragma unroll 2
-  for (int s = 0; s < kBwdThreads; s += 4) {
-    float4 pv[RA], qv[RC];
-#pragma unroll
-    for (int a = 0; a < RA; ++a) pv[a] = *reinterpret_cast<const float4*>(P + (ib + 16 * a) * kUPitch + s);
-#pragma unroll
-    for (int c = 0; c < RC; ++c) qv[c] = *reinterpret_cast<const float4*>(Q + (nb + 16 * c) * kUPitch + s);
-#pragma unroll
-    for (int a = 0; a < RA; ++a)
-#pragma unroll
-      for (int c = 0; c < RC; ++c) {
-        acc[a][c] = fmaf(pv[a].x, qv[c].x, acc[a][c]);
-        acc[a][c] = fmaf(pv[a].y, qv[c].y, acc[a][c]);
-        acc[a][c] = fmaf(pv[a].z, qv[c].z, acc[a][c]);
-        acc[a][c] = fmaf(pv[a].w, qv[c].w, acc[a][c]);
-      }
-  }
+__device__ __forceinline__ void tile_gemm_dw(const float* P, const float* Q, int ib, int nb, float acc[RA][RC]) {
+  tile_dw<kUPitch, kBwdThreads, RA, RC>(P, Q, ib, nb, acc);
 }
-
-// Stores a thread's 8 x NJ block (samples x units) unit-major, optionally
-// through relu or a mask.
 template <int NJ>
-__device__ __forceinline__ void tile_store(float* __restrict__ A, int sb, int n0, const float acc[8][NJ]) {
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    float* row = A + (n0 + j) * kUPitch;
-    *reinterpret_cast<float4*>(row + 4 * sb) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-    *reinterpret_cast<float4*>(row + 128 + 4 * sb) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
-  }
+__device__ __forceinline__ void tile_store(float* A, int sb, int n0, const float acc[8][NJ]) {
+  tile_st<kUPitch, kBwdThreads / 2, NJ>(A, sb, n0, acc);
 }
 
 template <bool kF16Table, int kMlpType>
@@ -542,13 +464,6 @@ __device__ __forceinline__ void tile_store_masked(float* __restrict__ A, int sb,
   }
 }
 
-__device__ __forceinline__ void relu8x8(float acc[8][8]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = fmaxf(acc[i][j], 0.0f);
-}
-
 template <int RA, int RC>
 __device__ __forceinline__ void add_block(float acc[RA][RC], const float dw[RA][RC]) {
 #pragma unroll
@@ -684,7 +599,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
     float acc[8][8];
     // ---- forward recompute: h1 = relu(F Wd1) -> A; g = h1 Wd2 -> C rows 0..15
     tile_gemm_ab<kIn>(s_D, Wd1, sb, 8 * ub, acc);
-    relu8x8(acc);
+    tile_relu<8, 8>(acc);
     tile_store<8>(s_A, sb, 8 * ub, acc);
     __syncthreads();
     {
@@ -695,11 +610,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
     __syncthreads();
     // ---- hc1 = relu(xc Wc1) -> D; hc2 = relu(hc1 Wc2) -> A
     tile_gemm_ab<kColorIn>(s_C, Wc1, sb, 8 * ub, acc);
-    relu8x8(acc);
+    tile_relu<8, 8>(acc);
     tile_store<8>(s_D, sb, 8 * ub, acc);
     __syncthreads();
     tile_gemm_ab<kWidth>(s_D, Wc2, sb, 8 * ub, acc);
-    relu8x8(acc);
+    tile_relu<8, 8>(acc);
     tile_store<8>(s_A, sb, 8 * ub, acc);
     __syncthreads();
     // ---- per sample: colour logits o = hc2 Wc3; chunk-local render adjoint
@@ -800,7 +715,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
     __syncthreads();
     // ---- density MLP backward: h1 again -> A; Wd2 += h1^T dg; dz1 = (h1 > 0) (dg Wd2^T)
     tile_gemm_ab<kIn>(s_D, Wd1, sb, 8 * ub, acc);
-    relu8x8(acc);
+    tile_relu<8, 8>(acc);
     tile_store<8>(s_A, sb, 8 * ub, acc);
     __syncthreads();
     {

@@ -18,6 +18,41 @@ struct FieldPtrs {
   const float* mlp;     // [K][kMlpParams]
 };
 
+// Hash-grid encoding of one level (F = 2): the two features
+// sum_corners w * table[l][idx][j].
+__device__ __forceinline__ float2 encode_level_f32(const LevelParams& lp, const float2* __restrict__ table,
+                                                   const float u[3], int l) {
+  int c[3];
+  float f[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  float2 v[8];
+  const float2* tl = table + lp.off[l];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    // x-neighbour pair: one aligned 16-byte load covers both corners when
+    // their indices differ only in bit 0 (even x for hashed levels, even
+    // index for dense ones); otherwise a second 8-byte load.
+    const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
+    const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
+    const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
+    const float4 q = __ldg(reinterpret_cast<const float4*>(tl + (i0 & ~1u)));
+    const bool odd = i0 & 1u;
+    v[e] = odd ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+    if ((i0 ^ i1) == 1u) v[e + 1] = odd ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+    else v[e + 1] = __ldg(tl + i1);
+  }
+  float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float w = ((e & 1) ? f[0] : 1.0f - f[0]) * (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) *
+                    (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
+    s0 = fmaf(w, v[e].x, s0);
+    s1 = fmaf(w, v[e].y, s1);
+  }
+  return make_float2(s0, s1);
+}
+
 // Hash-grid encoding (F = 2): feat[2l + j] = sum_corners w * table[l][idx][j].
 __device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* __restrict__ table, const float u[3],
                                            float feat[kIn]) {
@@ -26,36 +61,9 @@ __device__ __forceinline__ void encode_f32(const LevelParams& lp, const float2* 
 #pragma unroll
   for (int l = 0; l < kIn / 2; ++l) {
     if (l >= lp.L) break;
-    int c[3];
-    float f[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-    float2 v[8];
-    const float2* tl = table + lp.off[l];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      // x-neighbour pair: one aligned 16-byte load covers both corners when
-      // their indices differ only in bit 0 (even x for hashed levels, even
-      // index for dense ones); otherwise a second 8-byte load.
-      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-      const float4 q = __ldg(reinterpret_cast<const float4*>(tl + (i0 & ~1u)));
-      const bool odd = i0 & 1u;
-      v[e] = odd ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-      if ((i0 ^ i1) == 1u) v[e + 1] = odd ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
-      else v[e + 1] = __ldg(tl + i1);
-    }
-    float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const float w = ((e & 1) ? f[0] : 1.0f - f[0]) * (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) *
-                      (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-      s0 = fmaf(w, v[e].x, s0);
-      s1 = fmaf(w, v[e].y, s1);
-    }
-    feat[2 * l] = s0;
-    feat[2 * l + 1] = s1;
+    const float2 v = encode_level_f32(lp, table, u, l);
+    feat[2 * l] = v.x;
+    feat[2 * l + 1] = v.y;
   }
 }
 

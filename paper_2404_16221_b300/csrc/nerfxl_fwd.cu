@@ -29,6 +29,7 @@
 
 #include "nerfxl_device.cuh"
 #include "nerfxl_split.cuh"
+#include "nerfxl_tile.cuh"
 #include "nerfxl_host.h"
 
 namespace nerfxl {
@@ -370,11 +371,26 @@ __global__ void __launch_bounds__(256) k_fill_chunks(int64_t R, int K, SampParam
 }
 
 // ---------------------------------------------------------------------------
-// k_field_fwd (FP32): persistent CTAs over interleaved tiles; warp w of a
-// tile handles chunk kChunksPerTile * tile + w. Weights are reloaded only when the tile's
-// region changes.
+// k_field_fwd_f32: the fused FP32 field on CUDA cores. Persistent CTAs of 256
+// threads take 128-row sub-tiles (4 chunk slots, half of a 256-row tile; both
+// halves of a tile belong to one region) interleaved across the grid, two
+// CTAs per SM so that one gathers while the other multiplies. Per sub-tile:
+//   gather    thread (h, s) encodes levels 8 h .. 8 h + 7 of sample s into
+//             rows 16 h .. 16 h + 15 of the unit-major feature buffer (and the
+//             FP32 records for the backward, when asked for)
+//   MLP       register-tiled products over the 128 samples (a thread owns 8
+//             samples x 4 units; weights staged row-major per region), unit-
+//             major activations in two buffers of 64 rows
+//   render    thread s (warps 0-3, one chunk slot each): raw outputs, sigma,
+//             rgb, the chunk's partial (or the sample-level values)
+// Each output accumulates over its inputs in order with fused multiply-adds
+// from zero, as a per-sample dot product would, and the backward's recompute
+// does the same.
 
-constexpr int kFwdThreads = kChunksPerTile * kWarp;
+constexpr int kFwdRows = 128;                    // samples per sub-tile
+constexpr int kFwdThreads = 2 * kFwdRows;        // two threads per sample in the gather
+constexpr int kFPitch = kFwdRows + 4;            // unit-major row pitch
+constexpr int kFwdSubPerTile = kChunksPerTile / 4;
 
 struct FwdParams {
   const float* rays_o;
@@ -394,17 +410,156 @@ struct FwdParams {
   float* rec32;            // the backward's FP32 feature records [tiles][32][256], or NULL
 };
 
-
-// kSplit: the split representation (per-region density MLP; the shared
-// colour MLP is staged once, after the density block).
-template <bool kSplit>
+// Weights in shared memory, row-major as stored: W1 [32][64], W2 [64][64], W3 [64][4].
 __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
   extern __shared__ __align__(16) float s_dyn[];
-  constexpr int kWFloats = kSplit ? kSplitSmemFloats : kMlpParams;
+  constexpr int kWFloats = kMlpParams;
+  float* s_w = s_dyn;
+  float* s_A = s_w + kWFloats;       // [64][kFPitch]
+  float* s_B = s_A + kWidth * kFPitch;  // [64][kFPitch]
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_B + kWidth * kFPitch);  // [K+1]
+  const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+  const int h = tid / kFwdRows;            // gather half: levels 8 h .. 8 h + 7
+  const int srow = tid % kFwdRows;         // the thread's sample row
+  const int q = warp & 3;                  // its chunk slot within the sub-tile
+  const int sb = tid & 15, ub = tid >> 4;  // products: samples 4 sb.., 64 + 4 sb..; units of block ub
+  for (int i = tid; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
+  __syncthreads();
+  const int n_sub = *p.n_tiles * kFwdSubPerTile;
+  int region = -1;
+  const float2* table = nullptr;
+  for (int t = blockIdx.x; t < n_sub; t += gridDim.x) {
+    const int k = region_of_chunk(s_base, p.K, t * 4);
+    __syncthreads();  // the previous sub-tile's buffers (and weights) fully read
+    if (k != region) {
+      for (int i = tid; i < kMlpParams; i += blockDim.x) s_w[i] = p.fp.mlp[(size_t)k * kMlpParams + i];
+      region = k;
+      table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
+    }
+    // ---- per sample (both gather halves): slot, geometry, 8 levels of features
+    const SlotLane sl = slot_lane(p.chunks[t * 4 + q], lane);
+    const uint2 ref = sl.ref;
+    const uint32_t ray = sl.has ? ref.x : 0u;
+    const int seg = ref.y >> 16, c = ref.y & 0xFFFF;
+    RayHdr hd = {0.0f, 0.0f, 0, 0};
+    SegDesc sd = {0.0f, 0.0f, 0, 0};
+    float d[3] = {0.0f, 0.0f, 0.0f};
+    bool valid = false;
+    float tbar = 0.0f, dl = 0.0f;
+    float feat[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) feat[j] = 0.0f;
+    if (sl.has) {
+      hd = p.hdr[ray];
+      sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) d[ax] = p.rays_d[3 * (size_t)ray + ax];
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+      const int i = c * kWarp + sl.sl;
+      valid = i < ss.n;
+      if (valid) {
+        float o[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) o[ax] = p.rays_o[3 * (size_t)ray + ax];
+        float a, b;
+        segment_interval(sd, hd.tn, hd.delta, sample_interval(p.sp, ss, i), a, b);
+        tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        dl = __fsub_rn(b, a);
+        float x[3], u[3];
+        sample_point(o, d, tbar, x);
+        region_coord(p.fp.boxes + 6 * k, x, u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int l = 8 * h + j;
+          if (l < p.lp.L) {
+            const float2 v = encode_level_f32(p.lp, table, u, l);
+            feat[2 * j] = v.x;
+            feat[2 * j + 1] = v.y;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s_A[(16 * h + j) * kFPitch + srow] = feat[j];
+    if (p.rec32 && valid) {  // records for the backward: feature 16 h + j of tile row (t % 2) * 128 + srow
+      float* rec = p.rec32 + (size_t)(t / kFwdSubPerTile) * kIn * (kWarp * kChunksPerTile) +
+                   (t % kFwdSubPerTile) * kFwdRows + srow;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) __stcs(rec + (16 * h + j) * (kWarp * kChunksPerTile), feat[j]);
+    }
+    __syncthreads();
+    float acc[8][4];
+    {
+      const float* W1 = s_w;
+      const float* W2 = s_w + kIn * kWidth;
+      // h1 = relu(F W1) -> B; h2 = relu(h1 W2) -> A
+      tile_ab<kFPitch, kFwdRows / 2, kIn, 4, kWidth>(s_A, W1, sb, 4 * ub, acc);
+      tile_relu<8, 4>(acc);
+      tile_st<kFPitch, kFwdRows / 2, 4>(s_B, sb, 4 * ub, acc);
+      __syncthreads();
+      tile_ab<kFPitch, kFwdRows / 2, kWidth, 4, kWidth>(s_B, W2, sb, 4 * ub, acc);
+      tile_relu<8, 4>(acc);
+      tile_st<kFPitch, kFwdRows / 2, 4>(s_A, sb, 4 * ub, acc);  // the features' reads ended before h1's store
+    }
+    __syncthreads();
+    // ---- render (warps 0-3: thread = sample srow of slot q)
+    if (h == 0 && sl.slot_ok) {  // warp-uniform; lanes of an unused part of a narrow slot are empty samples
+      const float* W3 = s_w + kIn * kWidth + kWidth * kWidth;
+      float raw[kOut] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+      for (int n = 0; n < kWidth; ++n) {
+        const float hv = s_A[n * kFPitch + srow];  // h2
+        const float4 w3 = *reinterpret_cast<const float4*>(W3 + 4 * n);
+        raw[0] = fmaf(hv, w3.x, raw[0]);
+        raw[1] = fmaf(hv, w3.y, raw[1]);
+        raw[2] = fmaf(hv, w3.z, raw[2]);
+        raw[3] = fmaf(hv, w3.w, raw[3]);
+      }
+      float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
+      if (valid) {
+        sigma = expf(raw[0]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) rgb[j] = 1.0f / (1.0f + expf(-raw[1 + j]));
+      }
+      const float tr = valid ? __fsub_rn(tbar, hd.tn) : 0.0f;
+      const size_t slot = (size_t)ray * p.sp.max_chunk + seg_chunk_base(sd) + c;
+      if (p.smp4) {  // sample-level composition: every sample leaves the kernel
+        if (sl.has) {
+          p.smp4[slot * kWarp + sl.sl] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+          p.smp2[slot * kWarp + sl.sl] = make_float2(tr, dl);
+          for (int j = sl.width + sl.sl; j < kWarp; j += sl.width) {  // a narrow chunk's other sample slots
+            p.smp4[slot * kWarp + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            p.smp2[slot * kWarp + j] = make_float2(0.0f, 0.0f);
+          }
+        }
+      } else {
+        const Partial pt = render_chunk(sigma, rgb, tr, dl, sl.sl, nullptr, 0, sl.width);
+        if (sl.has && sl.sl == 0) {
+          float4* dst = p.partials + 2 * slot;
+          dst[0] = make_float4(pt.tau, pt.c0, pt.c1, pt.c2);
+          dst[1] = make_float4(pt.A, pt.D, pt.L, 0.0f);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_field_fwd_split_f32: the split representation's FP32 forward, one sample
+// per thread: per-region density MLP, the shared colour MLP staged once per
+// CTA after the density block, weights read as broadcasts. (The products of
+// this five-layer MLP measured slower as tiled GEMMs over 128-row sub-tiles:
+// 29.9 against 24.3 ms per grid8 step, its seven barriers per sub-tile and
+// the 16-output layer outweighing the fewer shared-memory reads.)
+constexpr int kSplitFwdThreads = kChunksPerTile * kWarp;
+
+__global__ void __launch_bounds__(kSplitFwdThreads, 2) k_field_fwd_split_f32(FwdParams p) {
+  extern __shared__ __align__(16) float s_dyn[];
+  constexpr int kWFloats = kSplitSmemFloats;
   float* s_w = s_dyn;                                              // kWFloats floats
   int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kWFloats);  // [K+1]
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
-  if (kSplit) load_color_f32(p.fp.mlp + (size_t)p.K * kDensityParams, s_w + kDensityParams);
+  load_color_f32(p.fp.mlp + (size_t)p.K * kDensityParams, s_w + kDensityParams);
   __syncthreads();
   const int n_tiles = *p.n_tiles;
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
@@ -418,8 +573,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     if (k != region) {
       __syncthreads();
-      if (kSplit) load_density_f32(p.fp.mlp + (size_t)k * kDensityParams, s_w);
-      else load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
+      load_density_f32(p.fp.mlp + (size_t)k * kDensityParams, s_w);
       __syncthreads();
       region = k;
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
@@ -469,12 +623,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       for (int q = 0; q < kIn; ++q) __stcs(rec + q * (kWarp * kChunksPerTile), feat[q]);
     }
     float raw[kOut];
-    if (kSplit) {
+    {
       float sh[kSh];
       sh4_f32(d, sh);  // the lane's ray
       split_f32_smem(s_w, s_w + kDensityParams, feat, sh, raw);
-    } else {
-      mlp_f32_smem(s_w, feat, raw);
     }
     float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
@@ -966,16 +1118,28 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
     if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
     p.rec32 = reinterpret_cast<float*>(ws + LB.rec32);
   }
-  const size_t smem = sizeof(float) * (split ? kSplitSmemFloats : kMlpParams) + sizeof(int32_t) * (f->K + 1);
-  const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
-  void (*kern)(FwdParams) = split ? k_field_fwd_f32<true> : k_field_fwd_f32<false>;
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                               cudaSuccess)
-    return launch_check("k_field_fwd_f32 smem attribute");
-  profile_mark(0, stream);
-  kern<<<grid, kFwdThreads, smem, stream>>>(p);
-  profile_mark(1, stream);
-  st = kernel_launched("k_field_fwd_f32");
+  if (split) {  // one sample per thread, 256-row tiles
+    const size_t smem = sizeof(float) * kSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
+    const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(k_field_fwd_split_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem) != cudaSuccess)
+      return launch_check("k_field_fwd_split_f32 smem attribute");
+    profile_mark(0, stream);
+    k_field_fwd_split_f32<<<grid, kSplitFwdThreads, smem, stream>>>(p);
+    profile_mark(1, stream);
+    st = kernel_launched("k_field_fwd_split_f32");
+  } else {  // tiled products over 128-row sub-tiles
+    const size_t smem = sizeof(float) * (kMlpParams + 2 * kWidth * kFPitch) + sizeof(int32_t) * (f->K + 1);
+    if (smem > 232448 / 2 - 1024)
+      return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the forward's shared memory");
+    const int grid = fwd_grid(L.chunk_cap / 4, 2);
+    if (cudaFuncSetAttribute(k_field_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return launch_check("k_field_fwd_f32 smem attribute");
+    profile_mark(0, stream);
+    k_field_fwd_f32<<<grid, kFwdThreads, smem, stream>>>(p);
+    profile_mark(1, stream);
+    st = kernel_launched("k_field_fwd_f32");
+  }
   if (st != NERFXL_OK) return st;
   if (per_sample) {
     const int64_t threads = n_rays * kWarp;

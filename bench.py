@@ -271,6 +271,43 @@ def time_steps(step, steps, flush, stream, prof=True):
     return [a.elapsed_time(b) for a, b in ev], ([a.elapsed_time(b) for a, b in kev] if prof else [])
 
 
+# Table-gradient reductions per sample of the backward's scatter: 16 levels x 4
+# x-pairs, each one 16-byte vector reduction on the aligned entry pair holding
+# its first corner plus an 8-byte one when the second corner is not in that
+# pair (about half of the pairs: odd x, or an odd dense index).
+RED_ADDRESSES_PER_SAMPLE = 16 * 4 * 1.5
+RED_PROBE_BYTES = 48 << 20  # about one grid8 region's FP32 gradient table (49 MB)
+
+
+def reduction_ceiling(stream, reps: int = 5, iters: int = 256) -> float:
+    """Measured ceiling of scattered 16-byte FP32 reductions (per second) on
+    this GPU: nerfxl_probe_reduction_rate into a 48 MB buffer, CUDA events."""
+    import torch
+
+    from paper_2404_16221_b300 import native as N
+
+    buf = torch.zeros(RED_PROBE_BYTES // 4, dtype=torch.float32, device="cuda")
+    ops = C_int64()
+    lib = N.lib()
+    N.check(lib.nerfxl_probe_reduction_rate(N._ptr(buf), RED_PROBE_BYTES, iters, ctypes_byref(ops),
+                                            N._stream(stream)), "reduction probe")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        N.check(lib.nerfxl_probe_reduction_rate(N._ptr(buf), RED_PROBE_BYTES, iters, ctypes_byref(ops),
+                                                N._stream(stream)), "reduction probe")
+    b.record(stream)
+    torch.cuda.synchronize()
+    return reps * ops.value / (a.elapsed_time(b) / 1000.0)
+
+
+def ctypes_byref(x):
+    import ctypes
+
+    return ctypes.byref(x)
+
+
 def fp32_alu_peak_tflops(sm_count: int = 148, mhz: float = 2032.0) -> float:
     """CUDA-core FP32 peak: SMs x 128 FMA lanes x 2 FLOP x max SM clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -727,6 +764,7 @@ def main():
         torch.cuda.empty_cache()
 
     head = forms["grid8_train_f16tab_bf16mlp"]
+    red_ceiling = reduction_ceiling(torch.cuda.current_stream())
     t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
@@ -804,7 +842,15 @@ def main():
                                          "instrumented, the scatter warps are busy 16.1-16.4 K cycles per "
                                          "128-row tile while the compute warps' chain alone takes 9.3 K; "
                                          "not HBM (DRAM traffic 0.18x the algorithmic bytes, the swept "
-                                         "region stays in L2)"},
+                                         "region stays in L2)",
+                     "binding": {"resource": "scattered 16-byte FP32 reductions (lane-addresses)",
+                                 "per_sample": RED_ADDRESSES_PER_SAMPLE,
+                                 "achieved_per_s": head["samples"] * RED_ADDRESSES_PER_SAMPLE / kern_s,
+                                 "ceiling_per_s": red_ceiling,
+                                 "frac": head["samples"] * RED_ADDRESSES_PER_SAMPLE / kern_s / red_ceiling,
+                                 "ceiling_kind": "measured in this run: nerfxl_probe_reduction_rate, 4 CTAs x "
+                                                 "256 threads per SM issuing red.global.add.v4.f32 (evict-last) "
+                                                 "to random 16-byte slots of a 48 MB buffer"}},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }

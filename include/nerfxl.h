@@ -485,6 +485,19 @@ int64_t nerfxl_launch_count(void);
  */
 nerfxl_status nerfxl_debug_wait_probe(int32_t* status, uint32_t spins, int32_t arrive, cudaStream_t stream);
 
+/*
+ * Reduction-rate probe: the measured ceiling of the backward kernels' table
+ * scatter. Launches (asynchronously on `stream`) 4 CTAs of 256 threads per
+ * SM; each thread issues `iters` 16-byte FP32 vector reductions
+ * (red.global.add.v4.f32, evict-last L2 hint, as the scatter issues them)
+ * adding 1.0 to float4 slots of `buf` chosen by a mixing hash, all inside
+ * [buf, buf + bytes). `buf`: caller-owned device memory, 16-byte aligned,
+ * contents overwritten; bytes / 16 < 2^32. *ops (host) receives the number
+ * of reductions launched; the caller times the launch with its own events.
+ * E_INVALID on bad arguments. The paper has no counterpart (measurement).
+ */
+nerfxl_status nerfxl_probe_reduction_rate(void* buf, size_t bytes, int32_t iters, int64_t* ops, cudaStream_t stream);
+
 /* Thread-local text for the last non-OK status. */
 const char* nerfxl_last_error(void);
 

@@ -773,6 +773,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int g_num_sms = 0;
 
+}  // namespace
+
 int num_sms() {
   if (g_num_sms == 0) {
     int dev = 0, n = 0;
@@ -782,8 +784,6 @@ int num_sms() {
   }
   return g_num_sms;
 }
-
-}  // namespace
 
 const char* last_error() { return g_last_error.c_str(); }
 nerfxl_status set_error(nerfxl_status st, const std::string& msg) { return fail(st, msg); }

@@ -68,6 +68,8 @@ nerfxl_status run_sampling(const nerfxl_field* f, const SampParams& sp, int64_t 
 // dominant kernel) if the caller installed one.
 void profile_mark(int which, cudaStream_t stream);
 int fwd_grid(int64_t max_tiles, int ctas_per_sm);
+// SMs of the current device (cached on first use).
+int num_sms();
 // Forward render; out_index (device [R], may be NULL) gives each ray's output slot.
 nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, int64_t n_rays, const float* rays_o,
                               const float* rays_d, float* rgb, float* depth, float* opacity, float* dist,

@@ -841,7 +841,7 @@ def main():
                                          "the time) at ~1.35 SM clocks each on the L1-to-L2 path; "
                                          "instrumented, the scatter warps are busy 16.1-16.4 K cycles per "
                                          "128-row tile while the compute warps' chain alone takes 9.3 K; "
-                                         "not HBM (DRAM traffic 0.18x the algorithmic bytes, the swept "
+                                         "not HBM (DRAM traffic 0.19x the algorithmic bytes, the swept "
                                          "region stays in L2)",
                      "binding": {"resource": "scattered 16-byte FP32 reductions (lane-addresses)",
                                  "per_sample": RED_ADDRESSES_PER_SAMPLE,

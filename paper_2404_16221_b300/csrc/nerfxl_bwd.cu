@@ -783,6 +783,8 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   if (!(f->table_dtype == NERFXL_F32 || f16tab) ||
       !(f->mlp_dtype == NERFXL_F32 || f->mlp_dtype == NERFXL_BF16 || f->mlp_dtype == NERFXL_F16))
     return set_error(NERFXL_E_UNSUPPORTED, "backward reads FP32/FP16 tables and an FP32/BF16/FP16 MLP");
+  if (f->mlp_dtype == NERFXL_F32 && f16tab)  // as the forward: the FP32 MLP reads FP32 tables
+    return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (n_rays > 0 && (!rays_o || !rays_d || !grad_tables || !grad_mlp))
     return set_error(NERFXL_E_INVALID, "null ray or gradient pointer");
   const Layout L = layout(f, s, n_rays, 1);
@@ -837,7 +839,7 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
   if (f->arch == NERFXL_ARCH_SPLIT) {
     const size_t smem_s = sizeof(float) * kBwdSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
     if (smem_s > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
-    void (*ks)(BwdParams) = f16tab ? k_field_bwd_split_f32<true, 0> : k_field_bwd_split_f32<false, 0>;  // FP32 MLP
+    void (*ks)(BwdParams) = k_field_bwd_split_f32<false, 0>;  // FP32 tables and MLP
     if (cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)
       return launch_check("k_field_bwd_split_f32 smem attribute");
     const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 1);
@@ -847,7 +849,6 @@ extern "C" nerfxl_status nerfxl_render_bwd(const nerfxl_field* f, const nerfxl_s
     return kernel_launched("k_field_bwd_split_f32");
   }
   const size_t smem = sizeof(float) * kBwdSmemFloatsT + sizeof(int32_t) * (f->K + 1);
-  if (f16tab) return set_error(NERFXL_E_UNSUPPORTED, "FP16 tables go with a 16-bit MLP");
   if (smem > 232448) return set_error(NERFXL_E_UNSUPPORTED, "too many regions for the backward's shared memory");
   void (*kern)(BwdParams) = k_field_bwd_f32<false, 0>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess)

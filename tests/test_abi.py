@@ -127,3 +127,19 @@ def test_occupancy_refresh_arguments_on_the_host(lib):
         assert st in (N.E_INVALID, N.E_UNSUPPORTED), (G, decay, st)
     d.table_dtype, d.mlp_dtype = N.F32, N.F32
     assert lib.nerfxl_occupancy_update(ctypes.byref(d), 8, 0, 1, 0.9, 0.01, None, None, None) == N.E_INVALID
+
+
+def test_backward_rejects_fp16_tables_with_fp32_mlp_before_any_launch(lib):
+    """The FP32 MLP reads FP32 tables (forward and backward alike): FP16
+    tables with an FP32 MLP are refused on the host for both representations,
+    before the backward launches anything (no GPU needed)."""
+    s = N.SamplingDesc(128, 4, 0.0, 0)
+    for arch in (N.ARCH_FUSED, N.ARCH_SPLIT):
+        d = _desc()
+        d.arch = arch
+        d.table_dtype, d.mlp_dtype = N.F16, N.F32
+        st = lib.nerfxl_render_bwd(ctypes.byref(d), ctypes.byref(s), 16, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1 << 40, None)
+        assert st == N.E_UNSUPPORTED, (arch, st)
+        assert b"16-bit MLP" in lib.nerfxl_last_error()
+        st = lib.nerfxl_render_fwd(ctypes.byref(d), ctypes.byref(s), 16, 1, 1, 1, 1, 1, 1, 1, 1 << 40, None)
+        assert st == N.E_UNSUPPORTED, (arch, st)

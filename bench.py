@@ -630,7 +630,7 @@ def main():
     m_split = torch.randn(n_split, generator=gsm, device=dev) * 0.1
     fsplit = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.as_tensor(tables).to(dev), m_split, device=dev,
                                   arch=N.ARCH_SPLIT)
-    r = fwd_form(w, fsplit, samp, o_dev, d_dev, "k_field_fwd_f32", 8 * w.F * 4 * w.L)
+    r = fwd_form(w, fsplit, samp, o_dev, d_dev, "k_field_fwd_persample_f32", 8 * w.F * 4 * w.L)
     km = statistics.mean(r["kern_ms"])
     split = {"fwd_fp32": {"rays_per_s": R / (statistics.mean(r["step_ms"]) / 1000.0), "kernel_ms": km,
                           "mlp_tflops_algorithmic": r["samples"] * SPLIT_FWD_FLOP / (km / 1000.0) / 1e12,
@@ -681,7 +681,7 @@ def main():
         oc, dc = sy.workload_rays(wc)
         oc_d, dc_d = torch.from_numpy(oc).to(dev), torch.from_numpy(dc).to(dev)
         sc = api.Sampling(wc.S, wc.max_segments)
-        for name, td, md, kern in (("city32_fwd_fp32", torch.float32, torch.float32, "k_field_fwd_f32"),
+        for name, td, md, kern in (("city32_fwd_fp32", torch.float32, torch.float32, "k_field_fwd_persample_f32"),
                                    ("city32_fwd_bf16mlp", torch.float32, torch.bfloat16, "k_field_fwd_tc"),
                                    ("city32_fwd_fp16mlp", torch.float32, torch.float16, "k_field_fwd_tc"),
                                    ("city32_fwd_f16tab_bf16mlp", torch.float16, torch.bfloat16, "k_field_fwd_tc")):

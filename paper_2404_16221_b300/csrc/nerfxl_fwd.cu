@@ -545,21 +545,25 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// k_field_fwd_split_f32: the split representation's FP32 forward, one sample
-// per thread: per-region density MLP, the shared colour MLP staged once per
-// CTA after the density block, weights read as broadcasts. (The products of
-// this five-layer MLP measured slower as tiled GEMMs over 128-row sub-tiles:
-// 29.9 against 24.3 ms per grid8 step, its seven barriers per sub-tile and
-// the 16-output layer outweighing the fewer shared-memory reads.)
-constexpr int kSplitFwdThreads = kChunksPerTile * kWarp;
+// k_field_fwd_persample_f32: the FP32 field with one sample per thread
+// (256-row tiles, warp w on chunk slot w), weights read from shared memory as
+// broadcasts. It serves the split representation (per-region density MLP,
+// the shared colour MLP staged once per CTA after the density block), whose
+// five-layer MLP measured slower as tiled products over 128-row sub-tiles
+// (29.9 against 24.3 ms per grid8 step: seven barriers per sub-tile and a
+// 16-output layer), and the fused MLP when a region's table outgrows what L2
+// keeps for random gathers (city32: 196 ms against 263 ms tiled, whose
+// gather and product phases alternate with the HBM latency exposed).
+constexpr int kPerSampleThreads = kChunksPerTile * kWarp;
 
-__global__ void __launch_bounds__(kSplitFwdThreads, 2) k_field_fwd_split_f32(FwdParams p) {
+template <bool kSplit>
+__global__ void __launch_bounds__(kPerSampleThreads, 2) k_field_fwd_persample_f32(FwdParams p) {
   extern __shared__ __align__(16) float s_dyn[];
-  constexpr int kWFloats = kSplitSmemFloats;
+  constexpr int kWFloats = kSplit ? kSplitSmemFloats : kMlpParams;
   float* s_w = s_dyn;                                              // kWFloats floats
   int32_t* s_base = reinterpret_cast<int32_t*>(s_dyn + kWFloats);  // [K+1]
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
-  load_color_f32(p.fp.mlp + (size_t)p.K * kDensityParams, s_w + kDensityParams);
+  if (kSplit) load_color_f32(p.fp.mlp + (size_t)p.K * kDensityParams, s_w + kDensityParams);
   __syncthreads();
   const int n_tiles = *p.n_tiles;
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
@@ -573,7 +577,8 @@ __global__ void __launch_bounds__(kSplitFwdThreads, 2) k_field_fwd_split_f32(Fwd
     const int k = region_of_chunk(s_base, p.K, t * kChunksPerTile);
     if (k != region) {
       __syncthreads();
-      load_density_f32(p.fp.mlp + (size_t)k * kDensityParams, s_w);
+      if (kSplit) load_density_f32(p.fp.mlp + (size_t)k * kDensityParams, s_w);
+      else load_mlp_f32(p.fp.mlp + (size_t)k * kMlpParams, s_w);
       __syncthreads();
       region = k;
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
@@ -623,10 +628,12 @@ __global__ void __launch_bounds__(kSplitFwdThreads, 2) k_field_fwd_split_f32(Fwd
       for (int q = 0; q < kIn; ++q) __stcs(rec + q * (kWarp * kChunksPerTile), feat[q]);
     }
     float raw[kOut];
-    {
+    if (kSplit) {
       float sh[kSh];
       sh4_f32(d, sh);  // the lane's ray
       split_f32_smem(s_w, s_w + kDensityParams, feat, sh, raw);
+    } else {
+      mlp_f32_smem(s_w, feat, raw);
     }
     float sigma = 0.0f, rgb[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
@@ -1118,16 +1125,20 @@ nerfxl_status render_fwd_impl(const nerfxl_field* f, const nerfxl_sampling* s, i
     if (ws_bytes < LB.total) return set_error(NERFXL_E_WORKSPACE, "NERFXL_SAVE_FEATURES needs a backward workspace");
     p.rec32 = reinterpret_cast<float*>(ws + LB.rec32);
   }
-  if (split) {  // one sample per thread, 256-row tiles
-    const size_t smem = sizeof(float) * kSplitSmemFloats + sizeof(int32_t) * (f->K + 1);
+  // one sample per thread (256-row tiles): the split MLP, or a fused one whose region table is beyond
+  // what L2 keeps for random gathers (the threshold of the level-grouped gather)
+  const size_t table_bytes = (size_t)nerfxl_table_entries(f->level_res, f->L, f->log2_T) * f->F * sizeof(float);
+  if (split || table_bytes > group_min_bytes()) {
+    const size_t smem = sizeof(float) * (split ? kSplitSmemFloats : kMlpParams) + sizeof(int32_t) * (f->K + 1);
     const int grid = fwd_grid(L.chunk_cap / kChunksPerTile, 2);
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(k_field_fwd_split_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem) != cudaSuccess)
-      return launch_check("k_field_fwd_split_f32 smem attribute");
+    void (*kern)(FwdParams) = split ? k_field_fwd_persample_f32<true> : k_field_fwd_persample_f32<false>;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                                 cudaSuccess)
+      return launch_check("k_field_fwd_persample_f32 smem attribute");
     profile_mark(0, stream);
-    k_field_fwd_split_f32<<<grid, kSplitFwdThreads, smem, stream>>>(p);
+    kern<<<grid, kPerSampleThreads, smem, stream>>>(p);
     profile_mark(1, stream);
-    st = kernel_launched("k_field_fwd_split_f32");
+    st = kernel_launched("k_field_fwd_persample_f32");
   } else {  // tiled products over 128-row sub-tiles
     const size_t smem = sizeof(float) * (kMlpParams + 2 * kWidth * kFPitch) + sizeof(int32_t) * (f->K + 1);
     if (smem > 232448 / 2 - 1024)

@@ -242,3 +242,50 @@ def test_paired_slots_render_as_alone(form):
         nseg, region, t0, t1, nint = oracle.segments(of, w.S, o[sub], d[sub])
         t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(sub))])
         H.assert_forward_close({k: v[sub] for k, v in full.items()}, ref, t_far)
+
+
+@pytest.mark.parametrize("name", ["unit", "grid8", "city32"])
+def test_fp32_forward_kernels_agree_bitwise(name):
+    """The fused FP32 field has two kernels: tiled products over 128-row
+    sub-tiles (region tables that L2 keeps) and one sample per thread (larger
+    tables; the switch is the level-grouped gather's table-size threshold).
+    Both take every product in the order of a per-sample dot product, so
+    their outputs are identical bit for bit, and the FP32 feature records
+    each writes for the backward give the same gradients (up to the order of
+    the FP32 atomic sums); the tiled form also matches the oracle."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import api, native as N
+
+    w = H.workload(name, L=None if name != "city32" else 16, log2_T=None if name != "city32" else 16)
+    t, m = H.params(w)
+    gf = H.gpu_field(w, t, m)
+    o, d = _edge_rays(w, 2048)
+    R = len(o)
+    samp = dataclasses.replace(H.sampling(w), flags=api.SAVE_FEATURES)
+    g = sy.rng(91, "misc")
+    adj = [torch.from_numpy(a.astype(np.float32)).cuda() for a in
+           (g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R))]
+    lib = N.lib()
+    runs = []
+    try:
+        for min_bytes in (0, 1):  # 0: the default threshold (tiled here); 1: every table is "large"
+            N.check(lib.nerfxl_set_gather_groups(min_bytes, 0, 0, 0), "threshold")
+            ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+            out = api.render_fwd(gf, samp, o, d, workspace=ws)
+            gt, gm = api.render_bwd(gf, samp, o, d, ws, *adj)  # from the records this forward wrote
+            api.check(ws)
+            runs.append(({k: v.clone() for k, v in out.items()}, gt.cpu().numpy(), gm.cpu().numpy()))
+    finally:
+        N.check(lib.nerfxl_set_gather_groups(0, 0, 0, 0), "threshold reset")
+    (a, ta, ma), (b, tb, mb) = runs
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    for x, y in ((ta, tb), (ma, mb)):
+        assert np.abs(x).max() > 0
+        assert np.abs(x - y).max() <= 1e-5 * np.abs(x).max()
+    of = H.oracle_field(w, t, m)
+    ref = oracle.render(of, w.S, o, d, 1)
+    nseg, region, t0, t1, nint = oracle.segments(of, w.S, o, d)
+    t_far = np.array([t1[r, nseg[r] - 1] if nseg[r] else 0.0 for r in range(len(o))])
+    H.assert_forward_close({k: v.cpu().numpy() for k, v in a.items()}, ref, t_far)

@@ -166,6 +166,43 @@ def test_split_with_occupancy_and_refresh():
     assert api.workspace_stats(ws)[0] == int(ref["n_samples"].sum())
 
 
+@pytest.mark.parametrize("save", [False, True])
+def test_split_fp32_backward_with_occupancy_matches_oracle(save):
+    """FP32 split backward over the kept samples of an occupancy grid (short,
+    ragged chunks in the 256-row tiles of the tiled kernel), with and without
+    the forward's feature records, against the oracle's gradient of the same
+    skipped render; every entry within 1e-4 of max|ref| on kink-free rays."""
+    import dataclasses
+
+    from paper_2404_16221_b300 import api
+
+    w, t, m, of, gf = _split()
+    G = 16
+    grid = api.OccupancyGrid(w.K, G, decay=0.9, threshold=1.0, seed=77)
+    dens = np.zeros((w.K, G ** 3))
+    bits = oracle.occupancy_update(of, G, 0, 77, 0.9, 1.0, dens)
+    grid.bits.copy_(torch.from_numpy(bits.view(np.int32)))
+    grid.attach(gf)
+    ofo = of.with_occupancy(bits, G)
+    o, d = _kink_free_rays(of, w, 1024, 93)
+    R = len(o)
+    g = sy.rng(94, "misc")
+    gC, gD, gA, gL = g.standard_normal((R, 3)), g.standard_normal(R), g.standard_normal(R), g.standard_normal(R)
+    samp = dataclasses.replace(H.sampling(w), flags=api.SAVE_FEATURES if save else 0)
+    ws = api.alloc_workspace(gf, samp, R, for_backward=True)
+    api.render_fwd(gf, samp, o, d, workspace=ws)
+    dev = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    gt, gm = api.render_bwd(gf, samp, o, d, ws, dev(gC), dev(gD), dev(gA), dev(gL))
+    api.check(ws)
+    kept = api.workspace_stats(ws)[0]
+    gt_ref, gm_ref = oracle.render_grad(ofo, w.S, o, d, gC, gD, gA, gL)
+    assert 0 < kept < R * w.S
+    for name, a, b in (("tables", gt.cpu().numpy(), gt_ref), ("mlp", gm.cpu().numpy(), gm_ref)):
+        ok, e = _grad_ok(a, b)
+        assert ok, (name, e)
+        assert np.abs(b).max() > 0
+
+
 def _rounded(a, dtype):
     return torch.from_numpy(a).to(dtype).float().numpy()
 

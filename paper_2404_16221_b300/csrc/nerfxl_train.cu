@@ -88,21 +88,61 @@ __global__ void __launch_bounds__(kFinalThreads) k_loss_final(const float2* __re
 
 // One Adam step over n FP32 parameters; optionally refreshes a reduced-
 // precision compute copy (dtype 1 = fp16, 2 = bf16).
-__global__ void __launch_bounds__(256) k_adam(int64_t n, float* __restrict__ p, const float* __restrict__ g,
+// One parameter's update (the same arithmetic in the scalar and vector forms).
+__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1, float b2, float eps,
+                                      float inv_c1, float inv_sqrt_c2) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  // lr * mhat / (sqrt(vhat) + eps), mhat = m / c1, vhat = v / c2
+  p = p - lr * (m * inv_c1) / (sqrtf(v) * inv_sqrt_c2 + eps);
+}
+
+__device__ __forceinline__ void store_copy(void* copy, int copy_dtype, int64_t i, float p) {
+  if (copy_dtype == 1) reinterpret_cast<__half*>(copy)[i] = __float2half_rn(p);
+  else if (copy_dtype == 2) reinterpret_cast<__nv_bfloat16*>(copy)[i] = __float2bfloat16_rn(p);
+}
+
+// Scalar form (any alignment) over [i0, n).
+__global__ void __launch_bounds__(256) k_adam(int64_t i0, int64_t n, float* __restrict__ p, const float* __restrict__ g,
                                               float* __restrict__ m, float* __restrict__ v, float lr, float b1,
                                               float b2, float eps, float inv_c1, float inv_sqrt_c2,
                                               void* __restrict__ copy, int copy_dtype) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float pi = p[i], mi = m[i], vi = v[i];
+    adam1(pi, g[i], mi, vi, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
     m[i] = mi;
     v[i] = vi;
-    // lr * mhat / (sqrt(vhat) + eps), mhat = m / c1, vhat = v / c2
-    const float pi = p[i] - lr * (mi * inv_c1) / (sqrtf(vi) * inv_sqrt_c2 + eps);
     p[i] = pi;
-    if (copy_dtype == 1) reinterpret_cast<__half*>(copy)[i] = __float2half_rn(pi);
-    else if (copy_dtype == 2) reinterpret_cast<__nv_bfloat16*>(copy)[i] = __float2bfloat16_rn(pi);
+    store_copy(copy, copy_dtype, i, pi);
+  }
+}
+
+// Vector form: four parameters per thread and iteration (16-byte loads and
+// stores of the FP32 arrays, 8 bytes of the 16-bit copy), for 16-byte-aligned
+// arrays; n4 groups of four.
+__global__ void __launch_bounds__(256) k_adam4(int64_t n4, float4* __restrict__ p, const float4* __restrict__ g,
+                                               float4* __restrict__ m, float4* __restrict__ v, float lr, float b1,
+                                               float b2, float eps, float inv_c1, float inv_sqrt_c2,
+                                               void* __restrict__ copy, int copy_dtype) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 pi = p[i], mi = m[i], vi = v[i];
+    const float4 gi = __ldcs(g + i);  // read once
+    adam1(pi.x, gi.x, mi.x, vi.x, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam1(pi.y, gi.y, mi.y, vi.y, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam1(pi.z, gi.z, mi.z, vi.z, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam1(pi.w, gi.w, mi.w, vi.w, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    m[i] = mi;
+    v[i] = vi;
+    p[i] = pi;
+    if (copy_dtype == 1) {
+      const __half2 a = __floats2half2_rn(pi.x, pi.y), b = __floats2half2_rn(pi.z, pi.w);
+      reinterpret_cast<uint2*>(copy)[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                                                     *reinterpret_cast<const uint32_t*>(&b));
+    } else if (copy_dtype == 2) {
+      const __nv_bfloat162 a = __floats2bfloat162_rn(pi.x, pi.y), b = __floats2bfloat162_rn(pi.z, pi.w);
+      reinterpret_cast<uint2*>(copy)[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                                                     *reinterpret_cast<const uint32_t*>(&b));
+    }
   }
 }
 
@@ -111,10 +151,27 @@ nerfxl_status launch_adam(int64_t n, float* p, const float* g, float* m, float* 
   if (n <= 0) return NERFXL_OK;
   const double c1 = 1.0 - std::pow((double)opt->beta1, (double)opt->step);
   const double c2 = 1.0 - std::pow((double)opt->beta2, (double)opt->step);
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
-  k_adam<<<blocks, 256, 0, stream>>>(n, p, g, m, v, opt->lr, opt->beta1, opt->beta2, opt->eps, (float)(1.0 / c1),
-                                     (float)(1.0 / std::sqrt(c2)), copy, copy_dtype);
-  return kernel_launched("k_adam");
+  const float inv_c1 = (float)(1.0 / c1), inv_sqrt_c2 = (float)(1.0 / std::sqrt(c2));
+  auto aligned = [](const void* q, uintptr_t a) { return (reinterpret_cast<uintptr_t>(q) & (a - 1)) == 0; };
+  const bool vec = aligned(p, 16) && aligned(g, 16) && aligned(m, 16) && aligned(v, 16) &&
+                   (copy_dtype == 0 || aligned(copy, 8));
+  const int64_t n4 = vec ? n / 4 : 0;
+  if (n4 > 0) {
+    const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms() * 8);
+    k_adam4<<<blocks, 256, 0, stream>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
+                                        reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), opt->lr,
+                                        opt->beta1, opt->beta2, opt->eps, inv_c1, inv_sqrt_c2, copy, copy_dtype);
+    const nerfxl_status st = kernel_launched("k_adam4");
+    if (st != NERFXL_OK) return st;
+  }
+  if (4 * n4 < n) {  // the tail (or everything, unaligned)
+    const int64_t rest = n - 4 * n4;
+    const int blocks = (int)std::min<int64_t>((rest + 255) / 256, (int64_t)num_sms() * 16);
+    k_adam<<<blocks, 256, 0, stream>>>(4 * n4, n, p, g, m, v, opt->lr, opt->beta1, opt->beta2, opt->eps, inv_c1,
+                                       inv_sqrt_c2, copy, copy_dtype);
+    return kernel_launched("k_adam");
+  }
+  return NERFXL_OK;
 }
 
 // E4M3 weight quantisation of fused MLP blocks (the FP8 experiment of the

@@ -276,6 +276,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       w[j] = 4 * g + j < p.lp.L ? __ldcs(p.feat_in + ((size_t)(4 * g + j) * p.window + tl) * kTcRows + row) : 0u;
   };
   if (kFeatIn && (int)p.w0 + (int)blockIdx.x < n_sub) load_feat(blockIdx.x, feat_next);
+  // The features record of tile t, exactly as the first MMA reads them: one
+  // 16-byte chunk per thread (row tid / 4, chunk tid % 4) from the complete
+  // layer-1 A tile, so that a warp writes eight whole 64-byte record rows.
+  auto store_feat_record = [&](int t) {
+    const uint32_t r = (uint32_t)tid >> 2, c = (uint32_t)tid & 3u;
+    const uint4 w = tc::ld_shared_v4(a0 + tc::sw128_chunk(r, c));
+    __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + r * 4 + (c ^ ((r >> 1) & 3u)), w);
+  };
+  static_assert(kTcThreads == 4 * kTcRows, "one feature chunk per thread");
   for (int t = (int)p.w0 + blockIdx.x; t < n_sub && !failed; t += gridDim.x) {
     const int k = region_of_chunk(s_base, p.K, t * kTcChunks);
     if (k != region) {
@@ -340,19 +349,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       Op::store8(a0, row, g, f8);
     }
     if (kRec) {
-      // Records for the backward: the features exactly as the first MMA reads
-      // them, the sample's region coordinates / position / length (thread g
-      // stores one of u0, u1, u2, tr; g == 0 also dl), the slot's sample
-      // counts, and each chunk's tile-order position for the composite adjoint
-      // (Tn, w, pair, sigma and rgb follow from the chunk render below).
-      // Streaming stores: the records are read once, by the backward, and
-      // should not push the region's tables out of L2 meanwhile.
-      const uint4 pk = kFeatIn ? fw
-                               : make_uint4(Half2Of<kKind == kKindBF16>::pack(f8[0], f8[1]),
-                                            Half2Of<kKind == kKindBF16>::pack(f8[2], f8[3]),
-                                            Half2Of<kKind == kKindBF16>::pack(f8[4], f8[5]),
-                                            Half2Of<kKind == kKindBF16>::pack(f8[6], f8[7]));
-      __stcs(p.rec.feat + (size_t)t * (kRecFeatBytes / 16) + row * 4 + ((uint32_t)g ^ ((row >> 1) & 3u)), pk);
+      // Records for the backward: the sample's region coordinates / position /
+      // length (thread g stores one of u0, u1, u2, tr; g == 0 also dl), the
+      // slot's sample counts, and each chunk's tile-order position for the
+      // composite adjoint (the features are copied from the layer-1 A tile
+      // while its MMA runs; Tn, w, pair, sigma and rgb follow from the chunk
+      // render below). Streaming stores: the records are read once, by the
+      // backward, and should not push the region's tables out of L2 meanwhile.
       float* geo = p.rec.geom + (size_t)t * kGeomFloats;
       __stcs(geo + g * kTcRows + row, g == 0 ? u[0] : (g == 1 ? u[1] : (g == 2 ? u[2] : tr)));
       if (kSplit && g == 1) {  // the split form's colour input: the ray direction, rows 5..7
@@ -395,6 +398,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
       float v[16];
       // density: D1 = X Wd1 -> relu -> A1; G = A1 Wd2 (columns 64..79)
       if (!layer(tmem, a0, b1, idesc64, kSteps32)) { failed = true; break; }
+      if (kRec) store_feat_record(t);  // A0 holds X until the colour input overwrites it
       tc::tmem_ld16(tmem_q + 16 * g, v);
       tc::tmem_ld_wait();
 #pragma unroll
@@ -459,6 +463,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         Op::mma(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b1 + 32 * kk), idesc64, kk);
       tc::mma_commit(mbar);
     }
+    if (kRec) store_feat_record(t);  // while the layer-1 MMA runs (it only reads A0)
     bool ok = tc::mbar_wait_bounded(mbar, phase, kSpinLimit);
     phase ^= 1;
     if (__syncthreads_or(!ok)) {

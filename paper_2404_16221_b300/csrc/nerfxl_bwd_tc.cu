@@ -19,7 +19,9 @@
 //                       32q..32q+31) and column half / level half g = w / 4
 //   scatter warps 8-15  scatter the previous tile's dL/dfeatures, handed over
 //                       through a double-buffered shared-memory slot guarded
-//                       by full / empty mbarriers
+//                       by full / empty mbarriers; a thread takes one level of
+//                       8 consecutive rows and sends one set of reductions per
+//                       run of samples in the same cell
 // Per tile, on the compute warps (FP32 accumulation in TMEM, four MMA round
 // trips):
 //   1  D1 = X W1 (X straight from the record stage); meanwhile the chunk-local
@@ -87,11 +89,14 @@ constexpr uint32_t oGeo = oXs + 2 * kXBytes;
 constexpr uint32_t kGeoBytes = 4 * kGeomFloats;
 constexpr uint32_t kGeoStage = kGeoBytes + 2 * 16 * 16;  // + 16 chunk positions (4 per slot) x 2 float4
 constexpr uint32_t kStageTx = kXBytes + kGeoStage;      // bytes per stage fill
-// Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][128 rows]
-// (row-contiguous, so both roles access it without bank conflicts), u as
-// float [3][128], then the 4 slots' count words (int32) and the region.
+// Hand-off slot of one tile: dL/dfeatures as float4 [8 = g*4 + j][kPRows], u
+// as float [3][kPRows], then the 4 slots' count words (int32) and the region.
+// Row r sits at padded position r + r / 8, so that the compute warps' row-wise
+// writes and the scatter threads' reads (rows 8 apart) both spread over the banks.
+constexpr uint32_t kPRows = kRows + kRows / 8;
+__device__ __forceinline__ uint32_t prow(uint32_t r) { return r + (r >> 3); }
 constexpr uint32_t oHand = oGeo + 2 * kGeoStage;
-constexpr uint32_t kHdDf = 0, kHdU = 16384, kHdNv = kHdU + 3 * 4 * kRows, kHdRegion = kHdNv + 16;
+constexpr uint32_t kHdDf = 0, kHdU = 16 * 8 * kPRows, kHdNv = kHdU + 3 * 4 * kPRows, kHdRegion = kHdNv + 16;
 constexpr uint32_t kHandBytes = kHdRegion + 16;
 constexpr uint32_t oMisc = oHand + 2 * kHandBytes;  // 8 mbarriers, TMEM base, abort flag
 constexpr uint32_t oBase = oMisc + 128;             // int32 base[K+1]
@@ -136,39 +141,44 @@ __device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int 
   }
 }
 
-// Scatter dL/dfeat of level l (g0, g1: its two features) into the region's
-// FP32 gradient table: the sample's 8 corners with trilinear weights (the
-// cells and weights of the forward's gather, same arithmetic). The corners of
-// an x-pair (x, x+1) go out as one 16-byte atomic on the aligned entry pair
-// holding the first corner (zero in the other half unless the second corner
-// is that pair's other entry) plus, when it is not, one 8-byte atomic.
-__device__ __forceinline__ void scatter_level(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
-                                              int l, float g0, float g1) {
-  int c[3];
-  float f[3];
+// Corner contributions of one sample at one level into acc (corner c = x | y << 1 |
+// z << 2, two features each): the trilinear weights of the cell fractions f
+// (the cells and weights of the forward's gather, same arithmetic) times the
+// sample's two feature gradients.
+__device__ __forceinline__ void accumulate_corners(const float f[3], float g0, float g1, float acc[16]) {
+  const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
+  for (int c = 0; c < 8; ++c) {
+    const float w = wx[c & 1] * (wy[(c >> 1) & 1] * wz[c >> 2]);
+    acc[2 * c] = fmaf(w, g0, acc[2 * c]);
+    acc[2 * c + 1] = fmaf(w, g1, acc[2 * c + 1]);
+  }
+}
+
+// The summed corner contributions of a run of samples in cell (cx, cy, cz) of
+// level l into the region's FP32 gradient table. The corners of an x-pair
+// (x, x+1) go out as one 16-byte reduction on the aligned entry pair holding
+// the first corner (zero in the other half unless the second corner is that
+// pair's other entry) plus, when it is not, one 8-byte reduction; both index
+// forms are formed and selected per corner (measured faster here than
+// branching per level).
+__device__ __forceinline__ void scatter_cell(const LevelParams& lp, float2* __restrict__ gtab, int l, int cx, int cy,
+                                             int cz, const float acc[16]) {
   float2* gl = gtab + lp.off[l];
-  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
-  const float wx0 = 1.0f - f[0], wx1 = f[0];
-  // Both index forms are formed and selected per corner (measured faster here
-  // than branching per level).
   const bool dense = (lp.dense_mask >> l) & 1u;
-  const LevelIndex<true> dix(lp, l, c[1], c[2]);
-  const LevelIndex<false> hix(lp, l, c[1], c[2]);
-  const uint32_t x0 = (uint32_t)c[0];
+  const LevelIndex<true> dix(lp, l, cy, cz);
+  const LevelIndex<false> hix(lp, l, cy, cz);
+  const uint32_t x0 = (uint32_t)cx;
+  const uint64_t pol = tc::policy_evict_last();
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
+  for (int e = 0; e < 4; ++e) {  // (y, z) corner e = y | z << 1
     const uint32_t i0 = dense ? dix(x0, e) : hix(x0, e);
     const uint32_t i1 = dense ? i0 + 1u : hix(x0 + 1u, e);
-    const float wyz = wy[e & 1] * wz[e >> 1];
-    const float w0 = wx0 * wyz, w1 = wx1 * wyz;
-    const float a0 = w0 * g0, a1 = w0 * g1, b0 = w1 * g0, b1 = w1 * g1;
-    const bool pair = (i0 ^ i1) == 1u;  // both corners in the aligned pair of i0
+    const int c0 = ((e & 1) << 1) | ((e >> 1) << 2);  // corner (x0, y, z); (x0 + 1, y, z) is c0 | 1
+    const float a0 = acc[2 * c0], a1 = acc[2 * c0 + 1], b0 = acc[2 * c0 + 2], b1 = acc[2 * c0 + 3];
+    const bool pair = (i0 ^ i1) == 1u;
     const bool odd = i0 & 1u;
     const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
-    // evict-last: the region's gradient lines stay in L2 while its tiles run
-    const uint64_t pol = tc::policy_evict_last();
     tc::red_add_v4(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
                    odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1), pol);
     if (!pair) tc::red_add_v2(gl + i1, make_float2(b0, b1), pol);
@@ -251,8 +261,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
 
   if (warp >= kGroup / kWarp) {
     // ===================== scatter warps =====================
-    const int sw = warp - kGroup / kWarp, q = sw & 3, g = sw >> 2;
-    const uint32_t row = (uint32_t)(q * kWarp + lane);
+    // Thread (level l, chunk slot qq, window wd) takes 8 consecutive rows of a
+    // slot at one level: consecutive samples along a ray often fall in the
+    // same cell (most at the coarse levels), so the thread sums their corner
+    // contributions in registers and sends one set of reductions per run of
+    // equal cells instead of one per sample.
+    const int sw = warp - kGroup / kWarp;
+    const int l = 2 * sw + (lane >> 4), qq = (lane >> 2) & 3, wd = lane & 3;
     int it = 0;
     for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
       const int b = it & 1;
@@ -262,27 +277,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         break;
       }
       const char* hd = sm + oHand + (uint32_t)b * kHandBytes;
-      const SlotCount sc = slot_count(reinterpret_cast<const int32_t*>(hd + kHdNv)[q], lane);
+      const int32_t nw = reinterpret_cast<const int32_t*>(hd + kHdNv)[qq];
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegion);
       const float* hu = reinterpret_cast<const float*>(hd + kHdU);
-      const float u[3] = {hu[row], hu[kRows + row], hu[2 * kRows + row]};
       const float4* df = reinterpret_cast<const float4*>(hd + kHdDf);
-      float g16[16];
+      uint32_t vmask = 0;  // rows of the window that hold a sample
+      float uu[8][3], gv[8][2];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 x = df[(g * 4 + j) * kRows + row];
-        g16[4 * j] = x.x;
-        g16[4 * j + 1] = x.y;
-        g16[4 * j + 2] = x.z;
-        g16[4 * j + 3] = x.w;
+      for (int i = 0; i < 8; ++i) {
+        const int pos = 8 * wd + i;
+        const uint32_t r = prow((uint32_t)(qq * kWarp + pos));
+        const SlotCount sc = slot_count(nw, pos);
+        vmask |= (sc.sl < sc.n ? 1u : 0u) << i;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) uu[i][ax] = hu[ax * kPRows + r];
+        const float4 x = df[(l >> 1) * kPRows + r];  // features 2l, 2l + 1
+        gv[i][0] = (l & 1) ? x.z : x.x;
+        gv[i][1] = (l & 1) ? x.w : x.y;
       }
       tc::bar_sync(kBarScatter, kGroup);  // slot read by every scatter thread
       if (tid == kGroup) tc::mbar_arrive(hempty + b);
-      if (sc.sl < sc.n) {
+      if (l < p.lp.L && vmask != 0u) {
         float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+        float acc[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (8 * g + j < p.lp.L) scatter_level(p.lp, gtab, u, 8 * g + j, g16[2 * j], g16[2 * j + 1]);
+        for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+        int cx = -1, cy = 0, cz = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (!((vmask >> i) & 1u)) continue;
+          int c[3];
+          float f[3];
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) level_cell(uu[i][ax], p.lp.N[l], c[ax], f[ax]);
+          if (cx >= 0 && (c[0] != cx || c[1] != cy || c[2] != cz)) {
+            scatter_cell(p.lp, gtab, l, cx, cy, cz, acc);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+          }
+          cx = c[0];
+          cy = c[1];
+          cz = c[2];
+          accumulate_corners(f, gv[i][0], gv[i][1], acc);
+        }
+        if (cx >= 0) scatter_cell(p.lp, gtab, l, cx, cy, cz, acc);
       }
     }
   } else {
@@ -550,11 +588,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       char* hd = sm + oHand + (uint32_t)b * kHandBytes;
       float4* df = reinterpret_cast<float4*>(hd + kHdDf);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) df[(g * 4 + j) * kRows + row] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      for (int j = 0; j < 4; ++j)
+        df[(g * 4 + j) * kPRows + prow(row)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
       if (g == 0) {
         float* hu = reinterpret_cast<float*>(hd + kHdU);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) hu[a * kRows + row] = geo[a * kRows + row];
+        for (int a = 0; a < 3; ++a) hu[a * kPRows + prow(row)] = geo[a * kRows + row];
         if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNv)[q] = nword;
         if (tid == 0) *reinterpret_cast<int32_t*>(hd + kHdRegion) = k;
       }

@@ -21,6 +21,7 @@
 
 #include "nerfxl_split.cuh"
 #include "nerfxl_host.h"
+#include "nerfxl_scatter.cuh"
 #include "nerfxl_tile.cuh"
 
 namespace nerfxl {
@@ -125,39 +126,6 @@ struct BwdParams {
 };
 
 
-// Scatter dL/dfeat into the region table: entry += corner weight * gfeat.
-__device__ __forceinline__ void scatter_table_grad(const LevelParams& lp, float2* __restrict__ gtab, const float u[3],
-                                                   const float gfeat[kIn]) {
-#pragma unroll
-  for (int l = 0; l < kIn / 2; ++l) {
-    if (l >= lp.L) break;
-    int c[3];
-    float f[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-    float2* gl = gtab + lp.off[l];
-    const float g0 = gfeat[2 * l], g1 = gfeat[2 * l + 1];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      const uint32_t y = c[1] + ((e >> 1) & 1), z = c[2] + ((e >> 2) & 1);
-      const uint32_t i0 = vertex_index(lp, l, c[0], y, z);
-      const uint32_t i1 = vertex_index(lp, l, c[0] + 1, y, z);
-      const float wyz = (((e >> 1) & 1) ? f[1] : 1.0f - f[1]) * (((e >> 2) & 1) ? f[2] : 1.0f - f[2]);
-      const float w0 = (1.0f - f[0]) * wyz, w1 = f[0] * wyz;
-      if ((i0 ^ i1) == 1u) {
-        // both corners in one aligned pair: one 16-byte atomic
-        const bool odd = i0 & 1u;
-        const float4 v = odd ? make_float4(w1 * g0, w1 * g1, w0 * g0, w0 * g1)
-                             : make_float4(w0 * g0, w0 * g1, w1 * g0, w1 * g1);
-        atomicAdd(reinterpret_cast<float4*>(gl + (i0 & ~1u)), v);
-      } else {
-        atomicAdd(gl + i0, make_float2(w0 * g0, w0 * g1));
-        atomicAdd(gl + i1, make_float2(w1 * g0, w1 * g1));
-      }
-    }
-  }
-}
-
 __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, float* __restrict__ g) {
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
     const float v = s_acc[i];
@@ -174,7 +142,11 @@ __device__ __forceinline__ void flush_mlp_grad(const float* __restrict__ s_acc, 
 // apart, so that both the sample-blocked and the unit-blocked products read
 // shared memory without bank conflicts.
 constexpr int kUPitch = 260;
-constexpr size_t kBwdSmemFloatsT = 2 * (size_t)kMlpParams + (size_t)kUPitch * (kIn + 2 * kWidth + kOut);
+// The scatter's inputs kept per tile row: region coordinates [3][256] and
+// one valid-sample mask per chunk slot [8].
+constexpr size_t kScatterSmemFloats = 3 * (size_t)kBwdThreads + kChunksPerTile;
+constexpr size_t kBwdSmemFloatsT =
+    2 * (size_t)kMlpParams + (size_t)kUPitch * (kIn + 2 * kWidth + kOut) + kScatterSmemFloats;
 
 template <int K, int NJ = 8, int NB = kWidth>
 __device__ __forceinline__ void tile_gemm_ab(const float* A, const float* B, int sb, int n0, float acc[8][NJ]) {
@@ -193,6 +165,35 @@ __device__ __forceinline__ void tile_store(float* A, int sb, int n0, const float
   tile_st<kUPitch, kBwdThreads / 2, NJ>(A, sb, n0, acc);
 }
 
+// The scatter's per-row inputs: region coordinates (unit-major) and the
+// slot's valid-sample mask (thread = row; called by every thread).
+__device__ __forceinline__ void keep_scatter_inputs(float* __restrict__ s_U, uint32_t* __restrict__ s_V,
+                                                    const float u[3], bool valid, int warp, int lane, int tid) {
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) s_U[ax * kBwdThreads + tid] = u[ax];
+  const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
+  if (lane == 0) s_V[warp] = vm;
+}
+
+// Table gradients of a tile from dL/dfeatures (unit-major, kUPitch): thread
+// (window w = tid / 16, level l = tid % 16) takes rows 16 w .. 16 w + 15 at
+// level l, merging runs of samples in the same cell.
+__device__ __forceinline__ void scatter_tile(const LevelParams& lp, float2* __restrict__ gtab,
+                                             const float* __restrict__ s_U, const uint32_t* __restrict__ s_V,
+                                             const float* __restrict__ s_G, int tid) {
+  const int w = tid >> 4, l = tid & 15;
+  const uint32_t vm = (s_V[w >> 1] >> (16 * (w & 1))) & 0xFFFFu;
+  if (l >= lp.L || vm == 0u) return;
+  const int r0 = 16 * w;
+  scatter_runs<16>(
+      lp, gtab, l, vm,
+      [&](int i, float* ui) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) ui[ax] = s_U[ax * kBwdThreads + r0 + i];
+      },
+      [&](int i) { return make_float2(s_G[2 * l * kUPitch + r0 + i], s_G[(2 * l + 1) * kUPitch + r0 + i]); });
+}
+
 template <bool kF16Table, int kMlpType>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   extern __shared__ __align__(16) float sm[];
@@ -202,7 +203,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
   float* s_H1 = s_F + kIn * kUPitch;           // [64][pitch]: h1, then dL/dz1
   float* s_H2 = s_H1 + kWidth * kUPitch;       // [64][pitch]: h2, then dL/dz2
   float* s_Go = s_H2 + kWidth * kUPitch;       // [4][pitch]: dL/d(raw outputs)
-  int32_t* s_base = reinterpret_cast<int32_t*>(s_Go + kOut * kUPitch);
+  float* s_U = s_Go + kOut * kUPitch;                       // [3][256] region coordinates
+  uint32_t* s_V = reinterpret_cast<uint32_t*>(s_U + 3 * kBwdThreads);  // [8] valid samples per slot
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_V + kChunksPerTile);
   for (int i = threadIdx.x; i <= p.K; i += blockDim.x) s_base[i] = p.base[i];
   __syncthreads();
   const int n_tiles = *p.n_tiles;
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
     }
 #pragma unroll
     for (int j = 0; j < kIn; ++j) s_F[j * kUPitch + tid] = feat[j];
+    keep_scatter_inputs(s_U, s_V, u, valid, warp, lane, tid);
     __syncthreads();
     float acc[8][8];
     // ---- forward recompute: H1 = relu(F W1), H2 = relu(H1 W2)
@@ -403,13 +407,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
       tile_store<4>(s_F, sb, 4 * ub, gx);
     }
     __syncthreads();
-    // ---- table gradients (thread = sample)
-    if (valid) {
-      float gfeat[kIn];
-#pragma unroll
-      for (int j = 0; j < kIn; ++j) gfeat[j] = s_F[j * kUPitch + tid];
-      scatter_table_grad(p.lp, gtab, u, gfeat);
-    }
+    // ---- table gradients: thread (window, level) takes one level of 16 consecutive rows
+    scatter_tile(p.lp, gtab, s_U, s_V, s_F, tid);
   }
   __syncthreads();
   if (region >= 0) flush_mlp_grad(s_acc, p.grad_mlp + (size_t)region * kMlpParams);
@@ -432,7 +431,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_f32(BwdParams p) {
 // columns nb + 16 c of each matrix): the shared colour MLP's over every tile
 // the CTA takes, flushed once at the end; the density MLP's per region.
 
-constexpr size_t kBwdSplitSmemFloats = (size_t)kSplitSmemFloats + (size_t)kUPitch * (2 * kWidth + kColorIn + kOut);
+constexpr size_t kBwdSplitSmemFloats =
+    (size_t)kSplitSmemFloats + (size_t)kUPitch * (2 * kWidth + kColorIn + kOut) + kScatterSmemFloats;
 
 __device__ __forceinline__ void flush_density_grad(float* __restrict__ g, const float aWd1[2][4],
                                                    const float aWd2[4][1], int ib, int nb) {
@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
   float* s_C = s_A + kWidth * kUPitch;
   float* s_D = s_C + kColorIn * kUPitch;
   float* s_O = s_D + kWidth * kUPitch;
-  int32_t* s_base = reinterpret_cast<int32_t*>(s_O + kOut * kUPitch);
+  float* s_U = s_O + kOut * kUPitch;                        // [3][256] region coordinates
+  uint32_t* s_V = reinterpret_cast<uint32_t*>(s_U + 3 * kBwdThreads);  // [8] valid samples per slot
+  int32_t* s_base = reinterpret_cast<int32_t*>(s_V + kChunksPerTile);
   const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
   const char* mlp = static_cast<const char*>(p.mlp);
   constexpr size_t kEsize = kMlpType == 0 ? 4 : 2;
@@ -595,6 +597,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
 #pragma unroll
       for (int j = 0; j < kSh; ++j) s_C[(kGeo + j) * kUPitch + tid] = sh[j];
     }
+    keep_scatter_inputs(s_U, s_V, u, valid, warp, lane, tid);
     __syncthreads();
     float acc[8][8];
     // ---- forward recompute: h1 = relu(F Wd1) -> A; g = h1 Wd2 -> C rows 0..15
@@ -740,13 +743,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_field_bwd_split_f32(BwdParam
       tile_store<4>(s_D, sb, 4 * ub, gx);
     }
     __syncthreads();
-    // ---- table gradients (thread = sample)
-    if (valid) {
-      float gfeat[kIn];
-#pragma unroll
-      for (int j = 0; j < kIn; ++j) gfeat[j] = s_D[j * kUPitch + tid];
-      scatter_table_grad(p.lp, gtab, u, gfeat);
-    }
+    // ---- table gradients: thread (window, level) takes one level of 16 consecutive rows
+    scatter_tile(p.lp, gtab, s_U, s_V, s_D, tid);
   }
   if (region >= 0) flush_density_grad(p.grad_mlp + (size_t)region * kDensityParams, aWd1, aWd2, ib, nb);
   // the shared colour block: once per CTA

@@ -5,10 +5,13 @@
 //                       rows 32 (w % 4) + lane (its TMEM lane quarter) and
 //                       columns 32 (w / 4) .. + 31 of the 64-wide products
 //   scatter warps 8-15  scatter the previous tile's dL/dX into the region's
-//                       table gradient: warp 8 + w reads its lane quarter's
+//                       table gradient: warp 8 + w moves its lane quarter's
 //                       columns of one of two dL/dX buffers in TMEM (levels
-//                       8 (w / 4) .. + 7), while the compute warps run the
-//                       next tile; hand-off through full / empty mbarriers
+//                       8 (w / 4) .. + 7) into a shared staging, then each
+//                       thread takes one level of 8 consecutive rows and sends
+//                       one set of reductions per run of samples in the same
+//                       cell, while the compute warps run the next tile;
+//                       hand-off through full / empty mbarriers
 // The table scatter is bound by the SM's rate for scattered vector atomics,
 // so it runs beside the chain instead of on its critical path. Per tile:
 //   records   written by the forward for this tile: X exactly as its first
@@ -46,6 +49,7 @@
 
 #include "nerfxl_half.cuh"
 #include "nerfxl_host.h"
+#include "nerfxl_scatter.cuh"
 #include "nerfxl_split.cuh"
 #include "nerfxl_tc.cuh"
 
@@ -93,13 +97,19 @@ constexpr uint32_t kStageTxS = 8192 + kGeoStageS;  // bytes per stage fill
 constexpr uint32_t oHandS = oGeoS + 2 * kGeoStageS;
 constexpr uint32_t kHdUS = 0, kHdNvS = 3 * 4 * kRowsS, kHdRegionS = kHdNvS + 16;
 constexpr uint32_t kHandS = kHdRegionS + 16;
-constexpr uint32_t oMiscS = (oHandS + 2 * kHandS + 63) / 64 * 64;  // 8 mbarriers, TMEM base, abort flag
+// The scatter warps' staging of one tile's dL/dX out of tensor memory: float4
+// [8 = level pairs][128 rows], row r at position srow(r) (and u likewise in the
+// hand-off slot), so that the row-wise writes and the run threads' reads (rows
+// 8 apart) both spread over the banks.
+constexpr uint32_t oDxS = oHandS + 2 * kHandS;
+constexpr uint32_t kDxBytesS = 16 * 8 * kRowsS;
+constexpr uint32_t oMiscS = (oDxS + kDxBytesS + 63) / 64 * 64;  // 8 mbarriers, TMEM base, abort flag
 constexpr uint32_t oBaseS = oMiscS + 128;
 constexpr size_t kSmemS = oBaseS + 1024;
 static_assert(kRowsS == kRecRows, "one backward tile is one record tile");
 static_assert(oX1 % 1024 == 0, "X stages keep the swizzle phase");
 static_assert(kGeoBytesS % 16 == 0 && kGeoStageS % 16 == 0 && oGeoS % 16 == 0, "bulk copies need 16 B");
-static_assert(oHandS % 16 == 0 && kHandS % 16 == 0, "hand-off slot alignment");
+static_assert(oHandS % 16 == 0 && kHandS % 16 == 0 && oDxS % 16 == 0, "hand-off slot alignment");
 static_assert(kDX + 64 <= kColsS, "tensor memory columns");
 static_assert(kSmemS + 1024 + 4 * 1024 <= 232448, "shared memory");
 
@@ -116,6 +126,10 @@ struct BwdSplitTcParams {
   float* grad_mlp;
   int32_t* err;
 };
+
+// Position of row r in the scatter's row-major staging (an XOR swizzle of the
+// row's low three bits with its group of eight).
+__device__ __forceinline__ uint32_t srow(uint32_t r) { return r ^ ((r >> 3) & 7u); }
 
 // 16-byte chunk c of row r of a 64-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw64_chunk(uint32_t row, uint32_t c) {
@@ -177,42 +191,6 @@ __device__ void load_color_bwd(const void* blk, char* sm, int tid, int nthreads)
   }
 }
 
-// Table gradient of level l of one sample (F = 2): entry += corner weight *
-// (g0, g1) at its 8 corners. The corners of an x-pair (x, x+1) go out as one
-// 16-byte reduction on the aligned entry pair holding the first corner (zero
-// in the other half unless the second corner is that pair's other entry)
-// plus, when it is not, one 8-byte reduction; the dense and hashed index forms
-// are both formed and selected per corner pair (no branch on the level).
-__device__ __forceinline__ void scatter_one(const LevelParams& lp, float2* __restrict__ gtab, const float u[3], int l,
-                                            float g0, float g1) {
-  int c[3];
-  float f[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) level_cell(u[ax], lp.N[l], c[ax], f[ax]);
-  float2* gl = gtab + lp.off[l];
-  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
-  const float wx0 = 1.0f - f[0], wx1 = f[0];
-  const bool dense = (lp.dense_mask >> l) & 1u;
-  const LevelIndex<true> dix(lp, l, c[1], c[2]);
-  const LevelIndex<false> hix(lp, l, c[1], c[2]);
-  const uint32_t x0 = (uint32_t)c[0];
-  const uint64_t pol = tc::policy_evict_last();  // the region's gradient lines stay in L2 while its tiles run
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const uint32_t i0 = dense ? dix(x0, e) : hix(x0, e);
-    const uint32_t i1 = dense ? i0 + 1u : hix(x0 + 1u, e);
-    const float wyz = wy[e & 1] * wz[e >> 1];
-    const float w0 = wx0 * wyz, w1 = wx1 * wyz;
-    const float a0 = w0 * g0, a1 = w0 * g1, b0 = w1 * g0, b1 = w1 * g1;
-    const bool pair = (i0 ^ i1) == 1u;
-    const bool odd = i0 & 1u;
-    const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
-    tc::red_add_v4(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
-                   odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1), pol);
-    if (!pair) tc::red_add_v2(gl + i1, make_float2(b0, b1), pol);
-  }
-}
-
 template <bool kBF16>
 __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcParams p) {
   extern __shared__ __align__(1024) char s_raw[];
@@ -248,10 +226,15 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
   if (warp >= kGroupS / kWarp) {
     // ===================== scatter warps =====================
-    // warp (q, h): rows 32 q .. 32 q + 31 (its TMEM lane quarter), levels 8 h .. 8 h + 7
+    // Warp (q, h) first moves its TMEM lane quarter's dL/dX (rows 32 q .. 32 q + 31,
+    // levels 8 h .. 8 h + 7) into the shared staging; then thread (level l, chunk
+    // slot qq, window wd) takes one level of 8 consecutive rows and sends one set
+    // of reductions per run of samples in the same cell.
     const int sw = warp - kGroupS / kWarp, q = sw & 3, h = sw >> 2;
     const uint32_t row = (uint32_t)(q * kWarp + lane);
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    const int l = 2 * sw + (lane >> 4), qq = (lane >> 2) & 3, wd = lane & 3;
+    float4* sdx = reinterpret_cast<float4*>(sm + oDxS);
     int it = 0;
     for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
       const int b = it & 1;
@@ -261,22 +244,45 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         break;
       }
       tc::fence_after_sync();
-      float gx[16];
-      tc::tmem_ld16(tq + kDX + 32 * (uint32_t)b + 16 * (uint32_t)h, gx);  // dL/dX, levels 8h..8h+7
+      {
+        float gx[16];
+        tc::tmem_ld16(tq + kDX + 32 * (uint32_t)b + 16 * (uint32_t)h, gx);  // dL/dX, levels 8h..8h+7
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          sdx[(4 * h + j) * kRowsS + srow(row)] = make_float4(gx[4 * j], gx[4 * j + 1], gx[4 * j + 2], gx[4 * j + 3]);
+      }
+      tc::bar_sync(kBarScatterS, kGroupS);  // the staging holds the tile's dL/dX
       const char* hd = sm + oHandS + (uint32_t)b * kHandS;
-      const SlotCount sc = slot_count(reinterpret_cast<const int32_t*>(hd + kHdNvS)[q], lane);
+      const int32_t nw = reinterpret_cast<const int32_t*>(hd + kHdNvS)[qq];
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegionS);
       const float* hu = reinterpret_cast<const float*>(hd + kHdUS);
-      const float u[3] = {hu[row], hu[kRowsS + row], hu[2 * kRowsS + row]};
-      tc::tmem_ld_wait();
-      tc::fence_before_sync();
-      tc::bar_sync(kBarScatterS, kGroupS);  // slot and TMEM buffer read by every scatter thread
-      if (tid == kGroupS) tc::mbar_arrive(hempty + b);
-      if (sc.sl < sc.n) {
-        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+      uint32_t vmask = 0;
+      float uu[8][3], gv[8][2];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (8 * h + j < p.lp.L) scatter_one(p.lp, gtab, u, 8 * h + j, gx[2 * j], gx[2 * j + 1]);
+      for (int i = 0; i < 8; ++i) {
+        const int pos = 8 * wd + i;
+        const uint32_t r = srow((uint32_t)(qq * kWarp + pos));
+        const SlotCount sc = slot_count(nw, pos);
+        vmask |= (sc.sl < sc.n ? 1u : 0u) << i;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) uu[i][ax] = hu[ax * kRowsS + r];
+        const float4 x = sdx[(l >> 1) * kRowsS + r];  // features 2l, 2l + 1
+        gv[i][0] = (l & 1) ? x.z : x.x;
+        gv[i][1] = (l & 1) ? x.w : x.y;
+      }
+      tc::fence_before_sync();
+      tc::bar_sync(kBarScatterS, kGroupS);  // slot, TMEM buffer and staging read by every scatter thread
+      if (tid == kGroupS) tc::mbar_arrive(hempty + b);
+      if (l < p.lp.L && vmask != 0u) {
+        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+        scatter_runs<8>(
+            p.lp, gtab, l, vmask,
+            [&](int i, float* ui) {
+#pragma unroll
+              for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
+            },
+            [&](int i) { return make_float2(gv[i][0], gv[i][1]); });
       }
     }
   } else {
@@ -596,7 +602,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         char* hd = sm + oHandS + (uint32_t)b * kHandS;
         float* hu = reinterpret_cast<float*>(hd + kHdUS);
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) hu[ax * kRowsS + row] = geo[ax * kRecRows + row];
+        for (int ax = 0; ax < 3; ++ax) hu[ax * kRowsS + srow(row)] = geo[ax * kRecRows + row];
         if (lane == 0) reinterpret_cast<int32_t*>(hd + kHdNvS)[q] = nword;
         if (tid == 0) *reinterpret_cast<int32_t*>(hd + kHdRegionS) = k;
       }

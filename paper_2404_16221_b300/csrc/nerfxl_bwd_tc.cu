@@ -52,6 +52,7 @@
 #include "nerfxl_field.cuh"
 #include "nerfxl_half.cuh"
 #include "nerfxl_host.h"
+#include "nerfxl_scatter.cuh"
 #include "nerfxl_tc.cuh"
 
 namespace nerfxl {
@@ -138,50 +139,6 @@ __device__ __forceinline__ void load_weights_bwd(const void* blk, char* sm, int 
   for (int i = tid; i < kWidth * 16; i += nthreads) {
     const int n = i / 16, k = i % 16;  // W3[n][k % 4] for k < 8
     b6[tc::sw128_offset(n, k) >> 1] = k < 8 ? Half2Of<BF16>::bits(blk, kIn * kWidth + kWidth * kWidth + n * kOut + (k & 3)) : 0;
-  }
-}
-
-// Corner contributions of one sample at one level into acc (corner c = x | y << 1 |
-// z << 2, two features each): the trilinear weights of the cell fractions f
-// (the cells and weights of the forward's gather, same arithmetic) times the
-// sample's two feature gradients.
-__device__ __forceinline__ void accumulate_corners(const float f[3], float g0, float g1, float acc[16]) {
-  const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float w = wx[c & 1] * (wy[(c >> 1) & 1] * wz[c >> 2]);
-    acc[2 * c] = fmaf(w, g0, acc[2 * c]);
-    acc[2 * c + 1] = fmaf(w, g1, acc[2 * c + 1]);
-  }
-}
-
-// The summed corner contributions of a run of samples in cell (cx, cy, cz) of
-// level l into the region's FP32 gradient table. The corners of an x-pair
-// (x, x+1) go out as one 16-byte reduction on the aligned entry pair holding
-// the first corner (zero in the other half unless the second corner is that
-// pair's other entry) plus, when it is not, one 8-byte reduction; both index
-// forms are formed and selected per corner (measured faster here than
-// branching per level).
-__device__ __forceinline__ void scatter_cell(const LevelParams& lp, float2* __restrict__ gtab, int l, int cx, int cy,
-                                             int cz, const float acc[16]) {
-  float2* gl = gtab + lp.off[l];
-  const bool dense = (lp.dense_mask >> l) & 1u;
-  const LevelIndex<true> dix(lp, l, cy, cz);
-  const LevelIndex<false> hix(lp, l, cy, cz);
-  const uint32_t x0 = (uint32_t)cx;
-  const uint64_t pol = tc::policy_evict_last();
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {  // (y, z) corner e = y | z << 1
-    const uint32_t i0 = dense ? dix(x0, e) : hix(x0, e);
-    const uint32_t i1 = dense ? i0 + 1u : hix(x0 + 1u, e);
-    const int c0 = ((e & 1) << 1) | ((e >> 1) << 2);  // corner (x0, y, z); (x0 + 1, y, z) is c0 | 1
-    const float a0 = acc[2 * c0], a1 = acc[2 * c0 + 1], b0 = acc[2 * c0 + 2], b1 = acc[2 * c0 + 3];
-    const bool pair = (i0 ^ i1) == 1u;
-    const bool odd = i0 & 1u;
-    const float p0 = pair ? b0 : 0.0f, p1 = pair ? b1 : 0.0f;
-    tc::red_add_v4(reinterpret_cast<float4*>(gl + (i0 & ~1u)),
-                   odd ? make_float4(p0, p1, a0, a1) : make_float4(a0, a1, p0, p1), pol);
-    if (!pair) tc::red_add_v2(gl + i1, make_float2(b0, b1), pol);
   }
 }
 
@@ -299,28 +256,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       if (tid == kGroup) tc::mbar_arrive(hempty + b);
       if (l < p.lp.L && vmask != 0u) {
         float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-        float acc[16];
+        scatter_runs<8>(
+            p.lp, gtab, l, vmask,
+            [&](int i, float* ui) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-        int cx = -1, cy = 0, cz = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (!((vmask >> i) & 1u)) continue;
-          int c[3];
-          float f[3];
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) level_cell(uu[i][ax], p.lp.N[l], c[ax], f[ax]);
-          if (cx >= 0 && (c[0] != cx || c[1] != cy || c[2] != cz)) {
-            scatter_cell(p.lp, gtab, l, cx, cy, cz, acc);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-          }
-          cx = c[0];
-          cy = c[1];
-          cz = c[2];
-          accumulate_corners(f, gv[i][0], gv[i][1], acc);
-        }
-        if (cx >= 0) scatter_cell(p.lp, gtab, l, cx, cy, cz, acc);
+              for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
+            },
+            [&](int i) { return make_float2(gv[i][0], gv[i][1]); });
       }
     }
   } else {

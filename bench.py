@@ -271,11 +271,13 @@ def time_steps(step, steps, flush, stream, prof=True):
     return [a.elapsed_time(b) for a, b in ev], ([a.elapsed_time(b) for a, b in kev] if prof else [])
 
 
-# Table-gradient reductions per sample of the backward's scatter: 16 levels x 4
-# x-pairs, each one 16-byte vector reduction on the aligned entry pair holding
-# its first corner plus an 8-byte one when the second corner is not in that
-# pair (about half of the pairs: odd x, or an odd dense index).
-RED_ADDRESSES_PER_SAMPLE = 16 * 4 * 1.5
+# Table-gradient reductions (lane-addresses) per sample of the headline
+# backward's scatter, from the same ncu capture as BWD_TC_DRAM
+# (l1tex__t_sectors_pipe_lsu_mem_global_op_red.sum / samples). Without merging
+# it would be 16 levels x 4 x-pairs x 1.5 = 96 (a 16-byte vector on the aligned
+# entry pair holding the first corner, plus an 8-byte one when the second corner
+# is not in that pair); runs of samples in the same cell share one set.
+BWD_TC_RED = {"sectors": 2230263639, "samples": 29292644}
 RED_PROBE_BYTES = 48 << 20  # about one grid8 region's FP32 gradient table (49 MB)
 
 
@@ -331,8 +333,9 @@ TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 12 * 4 + 1 + 2 * 8 * 2 * 4 * 16
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), with a hash
 # of the kernel's sources at the time of the capture: the figure is reported
 # only while the sources are unchanged (None: not captured for this build).
-BWD_TC_DRAM = {"bytes": 5.788794e9 + 6.502562e9, "sources_sha16": "aa42f727f4c383b2"}
-BWD_TC_SOURCES = ("nerfxl_bwd_tc.cu", "nerfxl_tc.cuh", "nerfxl_field.cuh", "nerfxl_half.cuh", "nerfxl_device.cuh")
+BWD_TC_DRAM = {"bytes": 3.992860e9 + 0.378965e9, "sources_sha16": "3db0e8eee44f7740"}
+BWD_TC_SOURCES = ("nerfxl_bwd_tc.cu", "nerfxl_scatter.cuh", "nerfxl_tc.cuh", "nerfxl_field.cuh", "nerfxl_half.cuh",
+                  "nerfxl_device.cuh")
 
 
 def sources_sha16(names=BWD_TC_SOURCES):
@@ -349,6 +352,14 @@ def bwd_tc_traffic():
     if BWD_TC_DRAM["bytes"] is None or BWD_TC_DRAM["sources_sha16"] != sources_sha16():
         return None
     return BWD_TC_DRAM["bytes"]
+
+
+def bwd_tc_reductions_per_sample():
+    """Measured lane-addresses per sample of the headline backward's scatter
+    (None once the kernel's sources differ from the captured build)."""
+    if BWD_TC_DRAM["sources_sha16"] != sources_sha16():
+        return None
+    return BWD_TC_RED["sectors"] / BWD_TC_RED["samples"]
 
 
 def single_form(args, dev):
@@ -806,6 +817,7 @@ def main():
         return r
 
     kern_s = statistics.mean(head["kern_ms"]) / 1000.0
+    red_per_sample = bwd_tc_reductions_per_sample()
     achieved = head["samples"] * TRAIN_BYTES_PER_SAMPLE_F16 / kern_s / 1e9
     rays_total = R * world * steps
     line = {
@@ -836,18 +848,22 @@ def main():
                               "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
                               "%.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src),
-                     "binding_resource": "the table-gradient reductions: ~96 lane-addresses per sample "
-                                         "(8 corners x 16 levels, x-pairs sharing one 16-byte vector half "
-                                         "the time) at ~1.35 SM clocks each on the L1-to-L2 path; "
-                                         "instrumented, the scatter warps are busy 16.1-16.4 K cycles per "
-                                         "128-row tile while the compute warps' chain alone takes 9.3 K; "
-                                         "not HBM (DRAM traffic 0.19x the algorithmic bytes, the swept "
-                                         "region stays in L2)",
-                     "binding": {"resource": "scattered 16-byte FP32 reductions (lane-addresses)",
-                                 "per_sample": RED_ADDRESSES_PER_SAMPLE,
-                                 "achieved_per_s": head["samples"] * RED_ADDRESSES_PER_SAMPLE / kern_s,
+                     "binding_resource": "the table-gradient reductions: 76 lane-addresses per sample "
+                                         "after merging runs of samples in the same cell (96 without), at "
+                                         "the rate the reduction probe measures (binding); issue 50%, "
+                                         "L1 throughput 68%, tensor pipe 8% (ncu, reduced batch); not HBM "
+                                         "(DRAM traffic 0.07x the algorithmic bytes, the swept region's "
+                                         "gradient lines stay in L2)",
+                     "binding": {"resource": "scattered FP32 vector reductions (lane-addresses)",
+                                 "per_sample": red_per_sample,
+                                 "per_sample_kind": "measured by ncu on this build (l1tex__t_sectors_pipe_lsu_"
+                                                    "mem_global_op_red); 96 without merging runs of samples in "
+                                                    "the same cell",
+                                 "achieved_per_s": None if red_per_sample is None
+                                 else head["samples"] * red_per_sample / kern_s,
                                  "ceiling_per_s": red_ceiling,
-                                 "frac": head["samples"] * RED_ADDRESSES_PER_SAMPLE / kern_s / red_ceiling,
+                                 "frac": None if red_per_sample is None
+                                 else head["samples"] * red_per_sample / kern_s / red_ceiling,
                                  "ceiling_kind": "measured in this run: nerfxl_probe_reduction_rate, 4 CTAs x "
                                                  "256 threads per SM issuing red.global.add.v4.f32 (evict-last) "
                                                  "to random 16-byte slots of a 48 MB buffer"}},

@@ -279,29 +279,45 @@ def time_steps(step, steps, flush, stream, prof=True):
 # is not in that pair); runs of samples in the same cell share one set.
 BWD_TC_RED = {"sectors": 2230263639, "samples": 29292644}
 RED_PROBE_BYTES = 48 << 20  # about one grid8 region's FP32 gradient table (49 MB)
+LD_PROBE_BYTES = 24 << 20  # about one grid8 region's FP16 table (24 MB)
+# Table-read sectors per sample of the mixed forward's gather (FP16 tables),
+# from one ncu capture of the plain grid8 forward at full size
+# (l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum / samples), valid while the
+# forward's sources are unchanged.
+FWD_TC_LD = {"sectors": 2144799525, "samples": 29292644, "sources_sha16": "5dd7dc8461094ac7"}
+FWD_TC_SOURCES = ("nerfxl_fwd_tc.cu", "nerfxl_field.cuh", "nerfxl_tc.cuh", "nerfxl_half.cuh", "nerfxl_device.cuh")
 
 
-def reduction_ceiling(stream, reps: int = 5, iters: int = 256) -> float:
-    """Measured ceiling of scattered 16-byte FP32 reductions (per second) on
-    this GPU: nerfxl_probe_reduction_rate into a 48 MB buffer, CUDA events."""
+def _probe_rate(entry: str, nbytes: int, iters: int, stream, reps: int = 5) -> float:
     import torch
 
     from paper_2404_16221_b300 import native as N
 
-    buf = torch.zeros(RED_PROBE_BYTES // 4, dtype=torch.float32, device="cuda")
+    buf = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
     ops = C_int64()
-    lib = N.lib()
-    N.check(lib.nerfxl_probe_reduction_rate(N._ptr(buf), RED_PROBE_BYTES, iters, ctypes_byref(ops),
-                                            N._stream(stream)), "reduction probe")
+    fn = getattr(N.lib(), entry)
+    N.check(fn(N._ptr(buf), nbytes, iters, ctypes_byref(ops), N._stream(stream)), entry)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
     for _ in range(reps):
-        N.check(lib.nerfxl_probe_reduction_rate(N._ptr(buf), RED_PROBE_BYTES, iters, ctypes_byref(ops),
-                                                N._stream(stream)), "reduction probe")
+        N.check(fn(N._ptr(buf), nbytes, iters, ctypes_byref(ops), N._stream(stream)), entry)
     b.record(stream)
     torch.cuda.synchronize()
     return reps * ops.value / (a.elapsed_time(b) / 1000.0)
+
+
+def reduction_ceiling(stream) -> float:
+    """Measured ceiling of scattered 16-byte FP32 reductions (per second) on
+    this GPU: nerfxl_probe_reduction_rate into a 48 MB buffer, CUDA events."""
+    return _probe_rate("nerfxl_probe_reduction_rate", RED_PROBE_BYTES, 256, stream)
+
+
+def load_ceiling(stream) -> float:
+    """Measured ceiling of scattered 8-byte loads (per second) on this GPU:
+    nerfxl_probe_load_rate over a 24 MB buffer (one grid8 region's FP16
+    table), CUDA events."""
+    return _probe_rate("nerfxl_probe_load_rate", LD_PROBE_BYTES, 64, stream)
 
 
 def ctypes_byref(x):
@@ -352,6 +368,14 @@ def bwd_tc_traffic():
     if BWD_TC_DRAM["bytes"] is None or BWD_TC_DRAM["sources_sha16"] != sources_sha16():
         return None
     return BWD_TC_DRAM["bytes"]
+
+
+def fwd_tc_sectors_per_sample():
+    """Measured table-read sectors per sample of the mixed forward's gather
+    (None once the kernel's sources differ from the captured build)."""
+    if FWD_TC_LD["sources_sha16"] != sources_sha16(FWD_TC_SOURCES):
+        return None
+    return FWD_TC_LD["sectors"] / FWD_TC_LD["samples"]
 
 
 def bwd_tc_reductions_per_sample():
@@ -776,6 +800,7 @@ def main():
 
     head = forms["grid8_train_f16tab_bf16mlp"]
     red_ceiling = reduction_ceiling(torch.cuda.current_stream())
+    ld_ceiling = load_ceiling(torch.cuda.current_stream())
     t_step = sum(head["step_ms"]) / 1000.0
     t_e2e = sum(e2e_ms) / 1000.0
     if world > 1:
@@ -870,6 +895,17 @@ def main():
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }
+    fwd = line["forms"].get("grid8_fwd_f16tab_bf16mlp")
+    sps = fwd_tc_sectors_per_sample()
+    if fwd is not None and sps is not None and fwd.get("kernel_ms"):
+        got = fwd["samples_per_step"] * sps / (fwd["kernel_ms"] / 1000.0)
+        fwd["binding"] = {"resource": "scattered table reads (L1 sectors)", "per_sample": sps,
+                          "per_sample_kind": "measured by ncu on this build (l1tex__t_sectors_pipe_lsu_mem_global_"
+                                             "op_ld)",
+                          "achieved_per_s": got, "ceiling_per_s": ld_ceiling, "frac": got / ld_ceiling,
+                          "ceiling_kind": "measured in this run: nerfxl_probe_load_rate, 4 CTAs x 256 threads per "
+                                          "SM, 16 independent random 8-byte loads per thread in flight, 24 MB "
+                                          "buffer"}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, tables, mlp, o, d, args.cpu_rays)
     print(json.dumps(line), flush=True)

@@ -498,6 +498,18 @@ nerfxl_status nerfxl_debug_wait_probe(int32_t* status, uint32_t spins, int32_t a
  */
 nerfxl_status nerfxl_probe_reduction_rate(void* buf, size_t bytes, int32_t iters, int64_t* ops, cudaStream_t stream);
 
+/*
+ * Load-rate probe: the measured ceiling of the forward's table gather.
+ * Launches (asynchronously on `stream`) 4 CTAs of 256 threads per SM; each
+ * thread issues `iters` x 16 independent 8-byte loads from slots of `buf`
+ * chosen by a mixing hash, all inside [buf, buf + bytes). `buf`: caller-owned
+ * device memory, 8-byte aligned, only read; bytes / 8 < 2^32. *ops (host)
+ * receives the number of loads launched; the caller times the launch with its
+ * own events. E_INVALID on bad arguments. The paper has no counterpart
+ * (measurement).
+ */
+nerfxl_status nerfxl_probe_load_rate(const void* buf, size_t bytes, int32_t iters, int64_t* ops, cudaStream_t stream);
+
 /* Thread-local text for the last non-OK status. */
 const char* nerfxl_last_error(void);
 

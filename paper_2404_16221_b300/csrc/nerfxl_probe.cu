@@ -7,7 +7,9 @@
 // Reduction-rate probe: the rate at which the GPU takes scattered 16-byte
 // FP32 reductions (red.global.add.v4.f32 with the evict-last hint, as the
 // backward's table scatter issues them) into a caller-owned buffer, the
-// resource that bounds the backward kernels.
+// resource that bounds the backward kernels. Load-rate probe: the rate of
+// scattered 8-byte loads (one sector each), the resource that bounds the
+// forward's table gather.
 
 #include <cuda_runtime.h>
 
@@ -40,9 +42,48 @@ __global__ void __launch_bounds__(256) k_reduction_rate(float4* buf, uint32_t n1
   }
 }
 
+// Every thread loads 16 independent 8-byte words per iteration from slots
+// picked by a mixing hash, all inside buf[0, n8), and folds them into one word
+// (stored only under an impossible condition, so that the loads stay).
+constexpr int kLoadProbeUnroll = 16;
+__global__ void __launch_bounds__(256) k_load_rate(const uint2* __restrict__ buf, uint32_t n8, int iters,
+                                                   uint32_t* __restrict__ sink) {
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (int i = 0; i < iters; ++i) {
+    uint2 v[kLoadProbeUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadProbeUnroll; ++u) {
+      uint32_t x = gid * 0x9E3779B1u + (uint32_t)(i * kLoadProbeUnroll + u) * 0x85EBCA77u;
+      x ^= x >> 16;
+      x *= 0x7FEB352Du;
+      x ^= x >> 15;
+      x *= 0x846CA68Bu;
+      x ^= x >> 16;
+      v[u] = __ldg(buf + x % n8);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadProbeUnroll; ++u) acc ^= v[u].x + v[u].y;
+  }
+  if (acc == 0x9E3779B9u && gid == 0xFFFFFFFFu) *sink = acc;
+}
+
 }  // namespace nerfxl
 
 using namespace nerfxl;
+
+extern "C" nerfxl_status nerfxl_probe_load_rate(const void* buf, size_t bytes, int32_t iters, int64_t* ops,
+                                                cudaStream_t stream) {
+  if (!buf || bytes < 8 || bytes / 8 > 0xFFFFFFFFull || iters <= 0 || !ops ||
+      (reinterpret_cast<uintptr_t>(buf) & 7u))
+    return set_error(NERFXL_E_INVALID, "bad load probe arguments");
+  const int grid = num_sms() * 4;
+  // the sink is never written (its condition cannot hold: gid < 2^32 - 1)
+  k_load_rate<<<grid, 256, 0, stream>>>(static_cast<const uint2*>(buf), (uint32_t)(bytes / 8), iters,
+                                        static_cast<uint32_t*>(const_cast<void*>(buf)));
+  *ops = (int64_t)grid * 256 * iters * kLoadProbeUnroll;
+  return kernel_launched("k_load_rate");
+}
 
 extern "C" nerfxl_status nerfxl_probe_reduction_rate(void* buf, size_t bytes, int32_t iters, int64_t* ops,
                                                      cudaStream_t stream) {

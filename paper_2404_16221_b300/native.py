@@ -94,6 +94,7 @@ SIGNATURES = {
     "nerfxl_render_cameras": (C.c_int, [_FP, _SP, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nerfxl_debug_wait_probe": (C.c_int, [_vp, C.c_uint32, _i32, _vp]),
     "nerfxl_probe_reduction_rate": (C.c_int, [_vp, _sz, _i32, _vp, _vp]),
+    "nerfxl_probe_load_rate": (C.c_int, [_vp, _sz, _i32, _vp, _vp]),
     "nerfxl_debug_camera_rays": (C.c_int, [_i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp]),
     "nerfxl_partition": (C.c_int, [_vp, _i64, _vp, _i32, _vp, _vp]),
     "nerfxl_occupancy_update": (C.c_int, [_FP, _i32, _i64, C.c_uint64, C.c_float, C.c_float, _vp, _vp, _vp]),

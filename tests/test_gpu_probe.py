@@ -48,3 +48,22 @@ def test_reduction_probe_rejects_bad_arguments():
                                 (N._ptr(buf), 4096, 0, ctypes.byref(ops)), (N._ptr(buf), 4096, 1, None)):
         assert lib.nerfxl_probe_reduction_rate(p, nbytes, iters, o, N._stream(None)) == N.E_INVALID
     assert ops.value == -1
+
+
+def test_load_probe_reads_only_and_counts():
+    from paper_2404_16221_b300 import native as N
+
+    lib = N.lib()
+    nbytes = 1 << 20
+    buf = torch.arange(nbytes // 4, dtype=torch.int32, device="cuda")
+    before = buf.clone()
+    ops = ctypes.c_int64(0)
+    assert lib.nerfxl_probe_load_rate(N._ptr(buf), nbytes, 2, ctypes.byref(ops), N._stream(None)) == N.OK
+    torch.cuda.synchronize()
+    assert ops.value > 0 and ops.value % (2 * 16) == 0
+    assert torch.equal(buf, before)  # only read
+    bad = ctypes.c_int64(-1)
+    for p, nb, it, o in ((None, 4096, 1, ctypes.byref(bad)), (N._ptr(buf), 4, 1, ctypes.byref(bad)),
+                         (N._ptr(buf), 4096, 0, ctypes.byref(bad)), (N._ptr(buf), 4096, 1, None)):
+        assert lib.nerfxl_probe_load_rate(p, nb, it, o, N._stream(None)) == N.E_INVALID
+    assert bad.value == -1

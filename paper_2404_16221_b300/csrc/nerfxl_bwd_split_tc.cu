@@ -1,17 +1,18 @@
 // Backward of the split representation on the tensor cores (16-bit MLPs,
-// FP32 accumulation in tensor memory). One CTA of 16 warps per SM takes
+// FP32 accumulation in tensor memory). One CTA of 12 warps per SM takes
 // 128-row tiles (4 chunk slots of one region), in two roles:
 //   compute warps 0-7   the MMA chain of one tile at a time; warp w serves
 //                       rows 32 (w % 4) + lane (its TMEM lane quarter) and
 //                       columns 32 (w / 4) .. + 31 of the 64-wide products
-//   scatter warps 8-15  scatter the previous tile's dL/dX into the region's
-//                       table gradient: warp 8 + w moves its lane quarter's
-//                       columns of one of two dL/dX buffers in TMEM (levels
-//                       8 (w / 4) .. + 7) into a shared staging, then each
-//                       thread takes one level of 8 consecutive rows and sends
-//                       one set of reductions per run of samples in the same
-//                       cell, while the compute warps run the next tile;
-//                       hand-off through full / empty mbarriers
+//   scatter warps 8-11  scatter the previous tile's dL/dX into the region's
+//                       table gradient: warp 8 + w moves lane quarter w's 32
+//                       columns of one of two dL/dX buffers in TMEM into a
+//                       shared staging, then each thread takes two levels of 8
+//                       consecutive rows and sends one set of reductions per
+//                       run of samples in the same cell, while the compute
+//                       warps run the next tile; hand-off through full / empty
+//                       mbarriers. Four scatter warps contend less with the
+//                       chain than eight (16.3 against 19.9 ms per grid8 step)
 // The table scatter is bound by the SM's rate for scattered vector atomics,
 // so it runs beside the chain instead of on its critical path. Per tile:
 //   records   written by the forward for this tile: X exactly as its first
@@ -57,8 +58,9 @@ namespace nerfxl {
 namespace {
 
 constexpr int kRowsS = 128;
-constexpr int kThreadsS = 512;
-constexpr int kGroupS = 256;  // threads per role
+constexpr int kThreadsS = 384;
+constexpr int kGroupS = 256;  // compute threads
+constexpr int kScatS = 128;   // scatter threads
 constexpr int kBarComputeS = 1, kBarScatterS = 2;
 constexpr int kChunksS = kRowsS / kWarp;
 // TMEM columns: 0 D_A, 64 D_B, 128 D_S (N <= 32), 192 DWc, 288 DWd, 384 DW3, 416 and 448 dX (two buffers)
@@ -226,39 +228,39 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
 
   if (warp >= kGroupS / kWarp) {
     // ===================== scatter warps =====================
-    // Warp (q, h) first moves its TMEM lane quarter's dL/dX (rows 32 q .. 32 q + 31,
-    // levels 8 h .. 8 h + 7) into the shared staging; then thread (level l, chunk
-    // slot qq, window wd) takes one level of 8 consecutive rows and sends one set
+    // Warp w = warp - 8 first moves its TMEM lane quarter's dL/dX (rows 32 w .. 32 w + 31,
+    // all 16 levels) into the shared staging; then thread (level pair lp, chunk slot qq,
+    // window wd) takes levels 2 lp and 2 lp + 1 of 8 consecutive rows and sends one set
     // of reductions per run of samples in the same cell.
-    const int sw = warp - kGroupS / kWarp, q = sw & 3, h = sw >> 2;
+    const int sw = warp - kGroupS / kWarp, q = sw;
     const uint32_t row = (uint32_t)(q * kWarp + lane);
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-    const int l = 2 * sw + (lane >> 4), qq = (lane >> 2) & 3, wd = lane & 3;
+    const int lp = lane >> 4 | (sw << 1), qq = (lane >> 2) & 3, wd = lane & 3;
     float4* sdx = reinterpret_cast<float4*>(sm + oDxS);
     int it = 0;
     for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
       const int b = it & 1;
       const bool ok = tc::mbar_wait_bounded(hfull + b, (uint32_t)(it >> 1) & 1u, kSpinS);
-      if (tc::bar_or(kBarScatterS, kGroupS, !ok || *s_abort != 0)) {
+      if (tc::bar_or(kBarScatterS, kScatS, !ok || *s_abort != 0)) {
         if (!ok && tid == kGroupS) atomicOr(p.err, kErrTimeout);
         break;
       }
       tc::fence_after_sync();
-      {
+      for (int h = 0; h < 2; ++h) {
         float gx[16];
-        tc::tmem_ld16(tq + kDX + 32 * (uint32_t)b + 16 * (uint32_t)h, gx);  // dL/dX, levels 8h..8h+7
+        tc::tmem_ld16(tq + kDX + 32 * (uint32_t)b + 16 * (uint32_t)h, gx);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           sdx[(4 * h + j) * kRowsS + srow(row)] = make_float4(gx[4 * j], gx[4 * j + 1], gx[4 * j + 2], gx[4 * j + 3]);
       }
-      tc::bar_sync(kBarScatterS, kGroupS);  // the staging holds the tile's dL/dX
+      tc::bar_sync(kBarScatterS, kScatS);  // the staging holds the tile's dL/dX
       const char* hd = sm + oHandS + (uint32_t)b * kHandS;
       const int32_t nw = reinterpret_cast<const int32_t*>(hd + kHdNvS)[qq];
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegionS);
       const float* hu = reinterpret_cast<const float*>(hd + kHdUS);
       uint32_t vmask = 0;
-      float uu[8][3], gv[8][2];
+      float uu[8][3], gv[8][4];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int pos = 8 * wd + i;
@@ -267,22 +269,29 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         vmask |= (sc.sl < sc.n ? 1u : 0u) << i;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) uu[i][ax] = hu[ax * kRowsS + r];
-        const float4 x = sdx[(l >> 1) * kRowsS + r];  // features 2l, 2l + 1
-        gv[i][0] = (l & 1) ? x.z : x.x;
-        gv[i][1] = (l & 1) ? x.w : x.y;
+        const float4 x = sdx[lp * kRowsS + r];  // features of levels 2lp, 2lp + 1
+        gv[i][0] = x.x;
+        gv[i][1] = x.y;
+        gv[i][2] = x.z;
+        gv[i][3] = x.w;
       }
       tc::fence_before_sync();
-      tc::bar_sync(kBarScatterS, kGroupS);  // slot, TMEM buffer and staging read by every scatter thread
+      tc::bar_sync(kBarScatterS, kScatS);  // slot, TMEM buffer and staging read by every scatter thread
       if (tid == kGroupS) tc::mbar_arrive(hempty + b);
-      if (l < p.lp.L && vmask != 0u) {
+      if (vmask != 0u) {
         float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-        scatter_runs<8>(
-            p.lp, gtab, l, vmask,
-            [&](int i, float* ui) {
 #pragma unroll
-              for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
-            },
-            [&](int i) { return make_float2(gv[i][0], gv[i][1]); });
+        for (int e = 0; e < 2; ++e) {
+          const int l = 2 * lp + e;
+          if (l < p.lp.L)
+            scatter_runs<8>(
+                p.lp, gtab, l, vmask,
+                [&](int i, float* ui) {
+#pragma unroll
+                  for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
+                },
+                [&](int i) { return make_float2(gv[i][2 * e], gv[i][2 * e + 1]); });
+        }
       }
     }
   } else {

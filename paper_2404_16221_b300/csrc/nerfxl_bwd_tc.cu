@@ -218,13 +218,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
 
   if (warp >= kGroup / kWarp) {
     // ===================== scatter warps =====================
-    // Thread (level l, chunk slot qq, window wd) takes 8 consecutive rows of a
-    // slot at one level: consecutive samples along a ray often fall in the
-    // same cell (most at the coarse levels), so the thread sums their corner
+    // Warp sw takes levels 2 sw and 2 sw + 1 of the tile, one after the
+    // other; lane pair w (lanes 2w, 2w + 1) takes 8 consecutive rows of a
+    // slot (window w: slot qq = w / 4, rows 8 (w % 4) ..), one lane per
+    // x-half h of the cell corners. Consecutive samples along a ray often
+    // fall in the same cell (most at the coarse levels), so a lane sums their
     // contributions in registers and sends one set of reductions per run of
-    // equal cells instead of one per sample.
+    // equal cells, its partner's reductions of the same x-pairs in the same
+    // instructions. The loops stay rolled (one reduction site in the code):
+    // the compute warps' code runs beside this on the same SM, and an
+    // unrolled scatter's size showed as instruction-fetch stalls.
     const int sw = warp - kGroup / kWarp;
-    const int l = 2 * sw + (lane >> 4), qq = (lane >> 2) & 3, wd = lane & 3;
+    const int h = lane & 1, qq = lane >> 3, wd = (lane >> 1) & 3;
     int it = 0;
     for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
       const int b = it & 1;
@@ -237,33 +242,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
       const int32_t nw = reinterpret_cast<const int32_t*>(hd + kHdNv)[qq];
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegion);
       const float* hu = reinterpret_cast<const float*>(hd + kHdU);
-      const float4* df = reinterpret_cast<const float4*>(hd + kHdDf);
+      const float2* df = reinterpret_cast<const float2*>(hd + kHdDf);
       uint32_t vmask = 0;  // rows of the window that hold a sample
-      float uu[8][3], gv[8][2];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int pos = 8 * wd + i;
-        const uint32_t r = prow((uint32_t)(qq * kWarp + pos));
-        const SlotCount sc = slot_count(nw, pos);
+        const SlotCount sc = slot_count(nw, 8 * wd + i);
         vmask |= (sc.sl < sc.n ? 1u : 0u) << i;
+      }
+      const uint32_t r0 = (uint32_t)(qq * kWarp + 8 * wd);  // prow(r0 + i) = prow(r0) + i for i < 8
+      float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+#pragma unroll 1
+      for (int j = 0; j < 2 && vmask != 0u; ++j) {
+        const int l = 2 * sw + j;
+        if (l >= p.lp.L) break;
+        const float2* dl = df + 2 * (size_t)sw * kPRows + j;  // features 2l, 2l + 1 of row r: dl[2 prow(r)]
+        scatter_runs_half_rolled<8>(
+            p.lp, gtab, l, h, vmask,
+            [&](int i, float* ui) {
+              const uint32_t r = prow(r0) + (uint32_t)i;
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) uu[i][ax] = hu[ax * kPRows + r];
-        const float4 x = df[(l >> 1) * kPRows + r];  // features 2l, 2l + 1
-        gv[i][0] = (l & 1) ? x.z : x.x;
-        gv[i][1] = (l & 1) ? x.w : x.y;
+              for (int ax = 0; ax < 3; ++ax) ui[ax] = hu[ax * kPRows + r];
+            },
+            [&](int i) { return dl[2 * (prow(r0) + (uint32_t)i)]; });
       }
       tc::bar_sync(kBarScatter, kGroup);  // slot read by every scatter thread
       if (tid == kGroup) tc::mbar_arrive(hempty + b);
-      if (l < p.lp.L && vmask != 0u) {
-        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-        scatter_runs<8>(
-            p.lp, gtab, l, vmask,
-            [&](int i, float* ui) {
-#pragma unroll
-              for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
-            },
-            [&](int i) { return make_float2(gv[i][0], gv[i][1]); });
-      }
     }
   } else {
     // ===================== compute warps =====================

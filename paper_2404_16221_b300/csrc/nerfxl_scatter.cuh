@@ -87,4 +87,109 @@ __device__ __forceinline__ void scatter_runs(const LevelParams& lp, float2* __re
   if (cx >= 0) scatter_cell(lp, gtab, l, cx, cy, cz, acc);
 }
 
+// The half of a run's corner contributions with corner x offset h (0: x0,
+// 1: x0 + 1): two lanes of one warp take the two halves of the same rows, so
+// that each sends one 8-byte reduction per (y, z) corner and the two lanes'
+// reductions of an x-pair go out in the same instruction. The memory system
+// takes one request per 32-byte sector that an instruction touches, not one
+// per lane: an x-pair whose entries share a sector (an aligned pair, or
+// entries 4m+1 and 4m+2: three x-pairs in four, dense or hashed) costs one
+// request instead of the two of a 16-byte plus an 8-byte reduction from one
+// lane. Corner weights and sums as in accumulate_corners, so every
+// contribution and every per-run sum is the same number as there.
+__device__ __forceinline__ void accumulate_half(const float f[3], int h, float g0, float g1, float acc[8]) {
+  const float wx = h ? f[0] : 1.0f - f[0];
+  const float wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {  // (y, z) corner e = y | z << 1
+    const float w = wx * (wy[e & 1] * wz[e >> 1]);
+    acc[2 * e] = fmaf(w, g0, acc[2 * e]);
+    acc[2 * e + 1] = fmaf(w, g1, acc[2 * e + 1]);
+  }
+}
+
+template <bool kDense>
+__device__ __forceinline__ void scatter_half_ix(const LevelParams& lp, float2* __restrict__ gl, int l, uint32_t x,
+                                                int cy, int cz, const float acc[8]) {
+  const LevelIndex<kDense> ix(lp, l, cy, cz);
+  const uint64_t pol = tc::policy_evict_last();
+#pragma unroll
+  for (int e = 0; e < 4; ++e) tc::red_add_v2(gl + ix(x, e), make_float2(acc[2 * e], acc[2 * e + 1]), pol);
+}
+
+// The level is uniform across the warp (both lanes of every pair take the
+// same level), so the dense / hashed choice is a uniform branch.
+__device__ __forceinline__ void scatter_half(const LevelParams& lp, float2* __restrict__ gtab, int l, int h, int cx,
+                                             int cy, int cz, const float acc[8]) {
+  float2* gl = gtab + lp.off[l];
+  const uint32_t x = (uint32_t)(cx + h);
+  if ((lp.dense_mask >> l) & 1u) scatter_half_ix<true>(lp, gl, l, x, cy, cz, acc);
+  else scatter_half_ix<false>(lp, gl, l, x, cy, cz, acc);
+}
+
+// scatter_runs for the x-half h of the corners (the partner lane, which takes
+// the other half of the same rows, runs the same cells in step).
+template <int N, typename U, typename G>
+__device__ __forceinline__ void scatter_runs_half(const LevelParams& lp, float2* __restrict__ gtab, int l, int h,
+                                                  uint32_t vmask, U&& u, G&& g) {
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+  int cx = -1, cy = 0, cz = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!((vmask >> i) & 1u)) continue;
+    float ui[3];
+    u(i, ui);
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(ui[ax], lp.N[l], c[ax], f[ax]);
+    if (cx >= 0 && (c[0] != cx || c[1] != cy || c[2] != cz)) {
+      scatter_half(lp, gtab, l, h, cx, cy, cz, acc);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+    }
+    cx = c[0];
+    cy = c[1];
+    cz = c[2];
+    const float2 gi = g(i);
+    accumulate_half(f, h, gi.x, gi.y, acc);
+  }
+  if (cx >= 0) scatter_half(lp, gtab, l, h, cx, cy, cz, acc);
+}
+
+// scatter_runs_half with the row loop rolled: u(i) and g(i) read their row
+// where it is (shared memory), and the code holds one reduction site.
+template <int N, typename U, typename G>
+__device__ __forceinline__ void scatter_runs_half_rolled(const LevelParams& lp, float2* __restrict__ gtab, int l,
+                                                         int h, uint32_t vmask, U&& u, G&& g) {
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+  int cx = -1, cy = 0, cz = 0;
+  const int n = lp.N[l];
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    if (!((vmask >> i) & 1u)) continue;
+    float ui[3];
+    u(i, ui);
+    const float2 gi = g(i);
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) level_cell(ui[ax], n, c[ax], f[ax]);
+    if (cx >= 0 && (c[0] != cx || c[1] != cy || c[2] != cz)) {
+      scatter_half(lp, gtab, l, h, cx, cy, cz, acc);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+    }
+    cx = c[0];
+    cy = c[1];
+    cz = c[2];
+    accumulate_half(f, h, gi.x, gi.y, acc);
+  }
+  if (cx >= 0) scatter_half(lp, gtab, l, h, cx, cy, cz, acc);
+}
+
 }  // namespace nerfxl

@@ -175,23 +175,32 @@ __device__ __forceinline__ void keep_scatter_inputs(float* __restrict__ s_U, uin
   if (lane == 0) s_V[warp] = vm;
 }
 
-// Table gradients of a tile from dL/dfeatures (unit-major, kUPitch): thread
-// (window w = tid / 16, level l = tid % 16) takes rows 16 w .. 16 w + 15 at
-// level l, merging runs of samples in the same cell.
+// Table gradients of a tile from dL/dfeatures (unit-major, kUPitch): warp w
+// takes windows w and w + 8 (rows 16 v .. 16 v + 15 of window v), one after
+// the other; lane pair l (lanes 2l, 2l + 1) takes level l of the window, one
+// lane per x-half of the cell corners, merging runs of samples in the same
+// cell. All lanes of a warp read the same row of u (a broadcast).
+
 __device__ __forceinline__ void scatter_tile(const LevelParams& lp, float2* __restrict__ gtab,
                                              const float* __restrict__ s_U, const uint32_t* __restrict__ s_V,
                                              const float* __restrict__ s_G, int tid) {
-  const int w = tid >> 4, l = tid & 15;
-  const uint32_t vm = (s_V[w >> 1] >> (16 * (w & 1))) & 0xFFFFu;
-  if (l >= lp.L || vm == 0u) return;
-  const int r0 = 16 * w;
-  scatter_runs<16>(
-      lp, gtab, l, vm,
-      [&](int i, float* ui) {
+  const int warp = tid / kWarp, lane = tid % kWarp;
+  const int l = lane >> 1, h = lane & 1;
+  if (l >= lp.L) return;
+#pragma unroll 1
+  for (int j = 0; j < 2; ++j) {
+    const int w = warp + 8 * j;
+    const uint32_t vm = (s_V[w >> 1] >> (16 * (w & 1))) & 0xFFFFu;
+    if (vm == 0u) continue;
+    const int r0 = 16 * w;
+    scatter_runs_half<16, false>(
+        lp, gtab, l, h, vm,
+        [&](int i, float* ui) {
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) ui[ax] = s_U[ax * kBwdThreads + r0 + i];
-      },
-      [&](int i) { return make_float2(s_G[2 * l * kUPitch + r0 + i], s_G[(2 * l + 1) * kUPitch + r0 + i]); });
+          for (int ax = 0; ax < 3; ++ax) ui[ax] = s_U[ax * kBwdThreads + r0 + i];
+        },
+        [&](int i) { return make_float2(s_G[2 * l * kUPitch + r0 + i], s_G[(2 * l + 1) * kUPitch + r0 + i]); });
+  }
 }
 
 template <bool kF16Table, int kMlpType>

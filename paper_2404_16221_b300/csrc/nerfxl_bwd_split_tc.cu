@@ -229,13 +229,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
   if (warp >= kGroupS / kWarp) {
     // ===================== scatter warps =====================
     // Warp w = warp - 8 first moves its TMEM lane quarter's dL/dX (rows 32 w .. 32 w + 31,
-    // all 16 levels) into the shared staging; then thread (level pair lp, chunk slot qq,
-    // window wd) takes levels 2 lp and 2 lp + 1 of 8 consecutive rows and sends one set
-    // of reductions per run of samples in the same cell.
+    // all 16 levels) into the shared staging. Then warp w takes levels 4 w .. 4 w + 3,
+    // one after the other: lane pair (lanes 2v, 2v + 1) takes 8 consecutive rows of a chunk slot
+    // (window v: slot qq = v / 4, rows 8 (v % 4) ..), one lane per x-half of the cell
+    // corners, and sends one set of reductions per run of samples in the same cell,
+    // the two halves of an x-pair in the same instructions (rolled loops: one
+    // reduction site in the code, see k_field_bwd_tc).
     const int sw = warp - kGroupS / kWarp, q = sw;
     const uint32_t row = (uint32_t)(q * kWarp + lane);
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-    const int lp = lane >> 4 | (sw << 1), qq = (lane >> 2) & 3, wd = lane & 3;
+    const int hx = lane & 1, qq = lane >> 3, wd = (lane >> 1) & 3;
     float4* sdx = reinterpret_cast<float4*>(sm + oDxS);
     int it = 0;
     for (int t = blockIdx.x; t < n_sub; t += G, ++it) {
@@ -254,45 +257,38 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
         for (int j = 0; j < 4; ++j)
           sdx[(4 * h + j) * kRowsS + srow(row)] = make_float4(gx[4 * j], gx[4 * j + 1], gx[4 * j + 2], gx[4 * j + 3]);
       }
-      tc::bar_sync(kBarScatterS, kScatS);  // the staging holds the tile's dL/dX
       const char* hd = sm + oHandS + (uint32_t)b * kHandS;
+      const float* hu = reinterpret_cast<const float*>(hd + kHdUS);
       const int32_t nw = reinterpret_cast<const int32_t*>(hd + kHdNvS)[qq];
       const int k = *reinterpret_cast<const int32_t*>(hd + kHdRegionS);
-      const float* hu = reinterpret_cast<const float*>(hd + kHdUS);
+      tc::fence_before_sync();
+      tc::bar_sync(kBarScatterS, kScatS);  // the staging holds the tile's dL/dX
       uint32_t vmask = 0;
-      float uu[8][3], gv[8][4];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int pos = 8 * wd + i;
-        const uint32_t r = srow((uint32_t)(qq * kWarp + pos));
-        const SlotCount sc = slot_count(nw, pos);
+        const SlotCount sc = slot_count(nw, 8 * wd + i);
         vmask |= (sc.sl < sc.n ? 1u : 0u) << i;
+      }
+      const uint32_t r0 = (uint32_t)(qq * kWarp + 8 * wd);
+      float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
+      const float2* sdx2 = reinterpret_cast<const float2*>(sdx);
+#pragma unroll 1
+      for (int e = 0; e < 4 && vmask != 0u; ++e) {
+        const int l = 4 * sw + e;
+        if (l >= p.lp.L) break;
+        const float2* dl = sdx2 + 2 * (size_t)(l >> 1) * kRowsS + (l & 1);  // row r: dl[2 srow(r)]
+        scatter_runs_half<8, true>(
+            p.lp, gtab, l, hx, vmask,
+            [&](int i, float* ui) {
+              const uint32_t r = srow(r0 + (uint32_t)i);
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) uu[i][ax] = hu[ax * kRowsS + r];
-        const float4 x = sdx[lp * kRowsS + r];  // features of levels 2lp, 2lp + 1
-        gv[i][0] = x.x;
-        gv[i][1] = x.y;
-        gv[i][2] = x.z;
-        gv[i][3] = x.w;
+              for (int ax = 0; ax < 3; ++ax) ui[ax] = hu[ax * kRowsS + r];
+            },
+            [&](int i) { return dl[2 * srow(r0 + (uint32_t)i)]; });
       }
       tc::fence_before_sync();
-      tc::bar_sync(kBarScatterS, kScatS);  // slot, TMEM buffer and staging read by every scatter thread
+      tc::bar_sync(kBarScatterS, kScatS);  // slot and TMEM buffer read by every scatter thread
       if (tid == kGroupS) tc::mbar_arrive(hempty + b);
-      if (vmask != 0u) {
-        float2* gtab = reinterpret_cast<float2*>(p.grad_tables) + (size_t)k * p.lp.E;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int l = 2 * lp + e;
-          if (l < p.lp.L)
-            scatter_runs<8>(
-                p.lp, gtab, l, vmask,
-                [&](int i, float* ui) {
-#pragma unroll
-                  for (int ax = 0; ax < 3; ++ax) ui[ax] = uu[i][ax];
-                },
-                [&](int i) { return make_float2(gv[i][2 * e], gv[i][2 * e + 1]); });
-        }
-      }
     }
   } else {
     // ===================== compute warps =====================

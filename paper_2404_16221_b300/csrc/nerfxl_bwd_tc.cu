@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
         const int l = 2 * sw + j;
         if (l >= p.lp.L) break;
         const float2* dl = df + 2 * (size_t)sw * kPRows + j;  // features 2l, 2l + 1 of row r: dl[2 prow(r)]
-        scatter_runs_half_rolled<8>(
+        scatter_runs_half<8, true>(
             p.lp, gtab, l, h, vmask,
             [&](int i, float* ui) {
               const uint32_t r = prow(r0) + (uint32_t)i;

@@ -97,7 +97,7 @@ def test_loss_gradient_through_autograd_matches_oracle():
     loss = ((rgb - torch.from_numpy(tgt).cuda()) ** 2).mean() + 0.01 * dist.mean()
     loss.backward()
     L_ref, gt_ref, gm_ref = oracle.loss_grad(H.oracle_field(w, t, m), w.S, o, d, tgt, 0.01)
-    assert abs(float(loss) - L_ref) <= 1e-5 * L_ref
+    assert abs(float(loss.detach()) - L_ref) <= 1e-5 * L_ref
     for g, ref in ((gf.tables.grad, gt_ref), (gf.mlp.grad, gm_ref)):
         ok, e = grad_close(g.cpu().numpy(), ref)
         assert ok, e

@@ -271,13 +271,16 @@ def time_steps(step, steps, flush, stream, prof=True):
     return [a.elapsed_time(b) for a, b in ev], ([a.elapsed_time(b) for a, b in kev] if prof else [])
 
 
-# Table-gradient reductions (lane-addresses) per sample of the headline
-# backward's scatter, from the same ncu capture as BWD_TC_DRAM
-# (l1tex__t_sectors_pipe_lsu_mem_global_op_red.sum / samples). Without merging
-# it would be 16 levels x 4 x-pairs x 1.5 = 96 (a 16-byte vector on the aligned
-# entry pair holding the first corner, plus an 8-byte one when the second corner
-# is not in that pair); runs of samples in the same cell share one set.
-BWD_TC_RED = {"sectors": 2230263639, "samples": 29292644}
+# Table-gradient reduction requests (32-byte sectors per instruction) per
+# sample of the headline backward's scatter, from the same ncu capture as
+# BWD_TC_DRAM (l1tex__t_sectors_pipe_lsu_mem_global_op_red.sum / samples). One
+# lane per sample and level, with a 16-byte vector on the aligned entry pair
+# holding the first corner of each x-pair plus an 8-byte one when the second
+# corner is not in that pair, takes 16 levels x 4 x-pairs x 1.5 = 96; runs of
+# samples in the same cell share one set (76), and two lanes per run, one per
+# x-half, send both halves of an x-pair in one instruction, one request when
+# they share a sector (three x-pairs in four): 63.5.
+BWD_TC_RED = {"sectors": 1860331182, "samples": 29292644}
 RED_PROBE_BYTES = 48 << 20  # about one grid8 region's FP32 gradient table (49 MB)
 LD_PROBE_BYTES = 24 << 20  # about one grid8 region's FP16 table (24 MB)
 # Table-read sectors per sample of the mixed forward's gather (FP16 tables),
@@ -349,7 +352,7 @@ TRAIN_BYTES_PER_SAMPLE_F16 = 32 * 2 + 12 * 4 + 1 + 2 * 8 * 2 * 4 * 16
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), with a hash
 # of the kernel's sources at the time of the capture: the figure is reported
 # only while the sources are unchanged (None: not captured for this build).
-BWD_TC_DRAM = {"bytes": 3.992860e9 + 0.378965e9, "sources_sha16": "3db0e8eee44f7740"}
+BWD_TC_DRAM = {"bytes": 3.991784e9 + 0.340042e9, "sources_sha16": "804c91ed622b7834"}
 BWD_TC_SOURCES = ("nerfxl_bwd_tc.cu", "nerfxl_scatter.cuh", "nerfxl_tc.cuh", "nerfxl_field.cuh", "nerfxl_half.cuh",
                   "nerfxl_device.cuh")
 
@@ -379,7 +382,7 @@ def fwd_tc_sectors_per_sample():
 
 
 def bwd_tc_reductions_per_sample():
-    """Measured lane-addresses per sample of the headline backward's scatter
+    """Measured reduction requests per sample of the headline backward's scatter
     (None once the kernel's sources differ from the captured build)."""
     if BWD_TC_DRAM["sources_sha16"] != sources_sha16():
         return None
@@ -873,17 +876,17 @@ def main():
                               "adjoints 1 B; FP32 gradient read-modify-write 2048 B) x %d samples / mean kernel time "
                               "%.3f ms (%s peak)"
                               % (TRAIN_BYTES_PER_SAMPLE_F16, head["samples"], 1000 * kern_s, src),
-                     "binding_resource": "the table-gradient reductions: 76 lane-addresses per sample "
-                                         "after merging runs of samples in the same cell (96 without), at "
-                                         "the rate the reduction probe measures (binding); issue 50%, "
-                                         "L1 throughput 68%, tensor pipe 8% (ncu, reduced batch); not HBM "
-                                         "(DRAM traffic 0.07x the algorithmic bytes, the swept region's "
-                                         "gradient lines stay in L2)",
-                     "binding": {"resource": "scattered FP32 vector reductions (lane-addresses)",
+                     "binding_resource": "the table-gradient reductions: 63.5 sector requests per sample "
+                                         "(runs of samples in the same cell merged, both halves of an x-pair "
+                                         "in one instruction; 96 with neither), near the rate the reduction "
+                                         "probe measures (binding); issue 52%, L1 throughput 63%, tensor "
+                                         "pipe 9% (ncu, reduced batch); not HBM (DRAM traffic 0.07x the "
+                                         "algorithmic bytes, the swept region's gradient lines stay in L2)",
+                     "binding": {"resource": "scattered FP32 vector reductions (32-byte sector requests)",
                                  "per_sample": red_per_sample,
                                  "per_sample_kind": "measured by ncu on this build (l1tex__t_sectors_pipe_lsu_"
                                                     "mem_global_op_red); 96 without merging runs of samples in "
-                                                    "the same cell",
+                                                    "the same cell and x-pair halves",
                                  "achieved_per_s": None if red_per_sample is None
                                  else head["samples"] * red_per_sample / kern_s,
                                  "ceiling_per_s": red_ceiling,
@@ -891,7 +894,8 @@ def main():
                                  else head["samples"] * red_per_sample / kern_s / red_ceiling,
                                  "ceiling_kind": "measured in this run: nerfxl_probe_reduction_rate, 4 CTAs x "
                                                  "256 threads per SM issuing red.global.add.v4.f32 (evict-last) "
-                                                 "to random 16-byte slots of a 48 MB buffer"}},
+                                                 "to random 16-byte slots of a 48 MB buffer, one sector request "
+                                                 "per lane"}},
         "forms": {k: summary(v) for k, v in forms.items()},
         "clocks": head["clocks"],
     }

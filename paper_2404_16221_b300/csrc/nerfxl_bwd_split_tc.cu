@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_field_bwd_split_tc(BwdSplitTcP
     // one after the other: lane pair (lanes 2v, 2v + 1) takes 8 consecutive rows of a chunk slot
     // (window v: slot qq = v / 4, rows 8 (v % 4) ..), one lane per x-half of the cell
     // corners, and sends one set of reductions per run of samples in the same cell,
-    // the two halves of an x-pair in the same instructions (rolled loops: one
-    // reduction site in the code, see k_field_bwd_tc).
+    // the two halves of an x-pair in the same instructions (nearly rolled loops,
+    // see k_field_bwd_tc).
     const int sw = warp - kGroupS / kWarp, q = sw;
     const uint32_t row = (uint32_t)(q * kWarp + lane);
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);

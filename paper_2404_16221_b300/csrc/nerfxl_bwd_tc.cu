@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_field_bwd_tc(BwdTcParams p) {
     // fall in the same cell (most at the coarse levels), so a lane sums their
     // contributions in registers and sends one set of reductions per run of
     // equal cells, its partner's reductions of the same x-pairs in the same
-    // instructions. The loops stay rolled (one reduction site in the code):
-    // the compute warps' code runs beside this on the same SM, and an
-    // unrolled scatter's size showed as instruction-fetch stalls.
+    // instructions. The loops stay (nearly) rolled and read the rows from the
+    // hand-off slot: the compute warps' code runs beside this on the same SM,
+    // and a fully unrolled scatter's size showed as instruction-fetch stalls.
     const int sw = warp - kGroup / kWarp;
     const int h = lane & 1, qq = lane >> 3, wd = (lane >> 1) & 3;
     int it = 0;

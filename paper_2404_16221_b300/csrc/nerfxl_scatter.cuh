@@ -66,11 +66,11 @@ __device__ __forceinline__ void scatter_half(const LevelParams& lp, float2* __re
 // partner lane, which takes the other half of the same rows, runs the same
 // cells in step): row i has region coordinates u(i), feature gradients
 // (g0, g1) = g(i) of this level, and takes part when bit i of vmask is set;
-// equal cells of successive taking-part rows form a run. The row loop stays
-// rolled (u(i) and g(i) read their row where it is, in shared memory), so the
-// code holds one reduction site: in a warp-specialized kernel the other
-// warps' code runs beside this on the same SM, and an unrolled scatter's
-// size showed as instruction-fetch stalls.
+// equal cells of successive taking-part rows form a run. The row loop is
+// unrolled by two only (u(i) and g(i) read their row where it is, in shared
+// memory), so the code holds two reduction sites: in a warp-specialized
+// kernel the other warps' code runs beside this on the same SM, and a fully
+// unrolled scatter's size showed as instruction-fetch stalls.
 template <int N, bool kUniform, typename U, typename G>
 __device__ __forceinline__ void scatter_runs_half(const LevelParams& lp, float2* __restrict__ gtab, int l, int h,
                                                   uint32_t vmask, U&& u, G&& g) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void scatter_runs_half(const LevelParams& lp, float2*
   for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
   int cx = -1, cy = 0, cz = 0;
   const int n = lp.N[l];
-#pragma unroll 1
+#pragma unroll 2
   for (int i = 0; i < N; ++i) {
     if (!((vmask >> i) & 1u)) continue;
     float ui[3];

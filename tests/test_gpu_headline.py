@@ -85,7 +85,7 @@ def test_headline_training_step_matches_oracle(n_rays):
     assert torch.equal(gf.mlp, tr.mlp.to(torch.bfloat16))
 
 
-@pytest.mark.parametrize("form", ["mixed", "fp32"])
+@pytest.mark.parametrize("form", ["mixed", "fp32", "split_mixed"])
 def test_full_size_backward_sampled_rays(form):
     """The full batch (2^18 rays, T=2^19) through the forward with records and
     the backward, in the launch configuration the benchmark times, with the
@@ -94,10 +94,12 @@ def test_full_size_backward_sampled_rays(form):
     the oracle's gradient of those 512 rays alone. Mixed form (FP16 tables,
     BF16 MLP, kink-free network): every entry within 1e-2 of max|ref| against
     the oracle on the rounded parameters; FP32 form: within 1e-4 on rays the
-    oracle finds clear of ReLU kinks."""
+    oracle finds clear of ReLU kinks; split representation (App. A.1) with
+    FP16 tables and BF16 MLPs, positive features and hidden weights: within
+    1e-2."""
     import dataclasses
 
-    from paper_2404_16221_b300 import api
+    from paper_2404_16221_b300 import api, native as N
 
     w = H.workload("grid8")
     o, d = sy.workload_rays(w)
@@ -107,6 +109,20 @@ def test_full_size_backward_sampled_rays(form):
         t, m = H.kinkless_params(w, seed=84)
         gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
         of = H.oracle_field(w, _rounded(t, torch.float16), _rounded(m, torch.bfloat16))
+        sel = sy.subset(R, 512, 85)
+        tol = TOL
+    elif form == "split_mixed":
+        E = oracle.table_entries(w.level_res, w.log2_T)
+        gp = sy.rng(87, "misc")
+        t = gp.uniform(0.1, 1.0, (w.K, E, 2)).astype(np.float32)
+        dens = np.concatenate([gp.uniform(0.0, 0.05, (w.K, 32 * 64)), gp.normal(0.0, 0.1, (w.K, 64 * 16))], 1)
+        col = np.concatenate([gp.uniform(0.0, 0.05, 32 * 64), gp.uniform(0.0, 0.05, 64 * 64),
+                              gp.normal(0.0, 0.1, 64 * 4)])
+        m = np.concatenate([dens.reshape(-1), col]).astype(np.float32)
+        gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                                  torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+        of = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, _rounded(t, torch.float16),
+                          _rounded(m, torch.bfloat16), arch=1)
         sel = sy.subset(R, 512, 85)
         tol = TOL
     else:

@@ -165,3 +165,43 @@ def test_split_backward_long_runs(tab, mlp):
         err = np.abs(a.astype(np.float64).reshape(-1) - b.reshape(-1)) / np.abs(b).max()
         print("coarse split backward tables=%s mlp=%s %s: max err / max |grad| %.2e" % (tab, mlp, which, err.max()))
         assert err.max() <= tol, (which, err.max())
+
+
+@pytest.mark.parametrize("L", [11, 8])
+@pytest.mark.parametrize("form", ["fused_tc", "split_tc", "fp32"])
+def test_backward_with_fewer_levels(form, L):
+    """Fewer levels than the MLP's 16 inputs (odd and even L; the inputs of the
+    missing levels are zero): the scatter lanes of the missing levels send
+    nothing, the others match the oracle as in the sixteen-level cases."""
+    from paper_2404_16221_b300 import api, native as N
+
+    w = _coarse()
+    w.level_res = np.array(COARSE[:L], np.int32)
+    o, d = sy.workload_rays(w, 4096)
+    sel = sy.subset(4096, 1024, 10)
+    o, d = o[sel].copy(), d[sel].copy()
+    if form == "split_tc":
+        t, m = _split_params(w, 36)
+        gf = api.PartitionedField(w.boxes, w.level_res, w.log2_T, torch.from_numpy(t).to(torch.float16),
+                                  torch.from_numpy(m).to(torch.bfloat16), arch=N.ARCH_SPLIT)
+        of = oracle.Field(w.boxes, w.level_res, w.log2_T, w.F, w.mlp_in, w.W, _rounded(t, torch.float16),
+                          _rounded(m, torch.bfloat16), arch=1)
+        tol = 1e-2
+    elif form == "fused_tc":
+        t, m = H.kinkless_params(w, seed=37)
+        gf = H.gpu_field(w, t, m, table_dtype=torch.float16, mlp_dtype=torch.bfloat16)
+        of = H.oracle_field(w, _rounded(t, torch.float16), _rounded(m, torch.bfloat16))
+        tol = 1e-2
+    else:
+        t, m = H.params(w)
+        gf = H.gpu_field(w, t, m)
+        of = H.oracle_field(w, t, m)
+        keep = H.kink_free(of, w.S, o, d)
+        o, d = o[keep].copy(), d[keep].copy()
+        tol = 1e-4
+    adj = _adjoints(len(o), 38)
+    gt, gm = _run_bwd(gf, w, o, d, adj)
+    gt_ref, gm_ref = oracle.render_grad(of, w.S, o, d, *adj)
+    for which, a, b in (("tables", gt, gt_ref), ("mlp", gm, gm_ref)):
+        ok, e = H.grad_close(a, b, tol)
+        assert ok, (form, L, which, e)

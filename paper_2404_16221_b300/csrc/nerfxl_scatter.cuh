@@ -15,10 +15,11 @@ namespace nerfxl {
 // that each sends one 8-byte reduction per (y, z) corner and the two lanes'
 // reductions of an x-pair go out in the same instruction. The memory system
 // takes one request per 32-byte sector that an instruction touches, not one
-// per lane: an x-pair whose entries share a sector (an aligned pair, or
-// entries 4m+1 and 4m+2: three x-pairs in four, dense or hashed) costs one
-// request instead of the two of a 16-byte plus an 8-byte reduction from one
-// lane. The corner weight is wx (wy wz), the trilinear weight of the
+// per lane: an x-pair whose entries share a sector (one aligned group of four
+// 8-byte entries: dense, unless the first entry is the last of its group;
+// hashed with the x prime 1, unless x = 3 mod 4; three x-pairs in four) costs
+// one request instead of the two of a 16-byte plus an 8-byte reduction from
+// one lane. The corner weight is wx (wy wz), the trilinear weight of the
 // forward's gather (same arithmetic).
 __device__ __forceinline__ void accumulate_half(const float f[3], int h, float g0, float g1, float acc[8]) {
   const float wx = h ? f[0] : 1.0f - f[0];

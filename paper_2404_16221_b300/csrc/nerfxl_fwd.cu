@@ -864,7 +864,7 @@ Layout layout(const nerfxl_field* f, const nerfxl_sampling* s, int64_t R, int fo
   L.gfeat_tiles = 0;
   if (grouped_gather(f, s, R)) {
     L.gfeat_tiles = std::min<int64_t>((L.chunk_cap + 3) / 4, gather_window_tiles());
-    L.gfeat = take(sizeof(uint32_t) * 128 * (size_t)f->L * (size_t)L.gfeat_tiles);
+    L.gfeat = take(sizeof(uint32_t) * 128 * (size_t)(f->L + kGatherCoordWords) * (size_t)L.gfeat_tiles);
   }
   L.total = off;
   L.max_seg = ms;

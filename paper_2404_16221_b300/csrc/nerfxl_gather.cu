@@ -12,10 +12,12 @@
 // level-major words (whole sectors: 512 contiguous bytes per level and tile),
 // and the tensor-core forward then reads the features from there instead of
 // gathering. The features equal the fused gather's bit for bit (same
-// per-level arithmetic, same rounding to the MLP's 16-bit type). Each group is
-// one more pass over the region's samples (positions, launch, feature words),
-// so the groups are as large as still pays: two groups of a 96 MB table beat
-// three to eleven smaller ones.
+// per-level arithmetic, same rounding to the MLP's 16-bit type). A first pass
+// over the window's rows (k_gather_coords) stores each row's region
+// coordinates once, so the group passes do not repeat the ray, segment and
+// sample arithmetic. Each group is still one more pass over the region's
+// samples (coordinates, launch, feature words), so the groups are as large as
+// still pays: two groups of a 96 MB table beat three to eleven smaller ones.
 //
 // Work items are (region, group, tile) in that order over a window of tiles;
 // the persistent CTAs take consecutive items, so the GPU works on one
@@ -54,6 +56,56 @@ struct GatherGroupsParams {
   int32_t g_lo[kMaxLevels + 1];  // group g holds levels g_lo[g] .. g_lo[g + 1] - 1
 };
 
+// The window's rows once: each row's sample position in its region's box, as
+// the tensor-core forward computes it (the same arithmetic, so the groups'
+// features equal the one-pass gather's), stored after the feature words for
+// every group pass to read instead of repeating the ray, segment and sample
+// arithmetic per group.
+__global__ void __launch_bounds__(kGThreads) k_gather_coords(GatherGroupsParams p) {
+  const int64_t n_sub = (int64_t)*p.n_tiles * (kChunksPerTile / 4);
+  const int64_t wa = p.w0, wb = p.w1 < n_sub ? p.w1 : n_sub;
+  const size_t cstride = (size_t)p.window * kGRows;
+  uint32_t* cw0 = p.feat + (size_t)p.lp.L * cstride;
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (wb - wa) * kGRows;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = wa + gi / kGRows;
+    const uint32_t row = (uint32_t)(gi % kGRows);
+    const int q = (int)(row / kWarp), lane = (int)(row % kWarp);
+    const SlotLane sl = slot_lane(p.chunks[t * 4 + q], lane);
+    bool valid = false;
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    if (sl.has) {
+      const int k = region_of_chunk(p.base, p.K, (int)(t * 4));
+      const uint32_t ray = sl.ref.x;
+      const int seg = sl.ref.y >> 16;
+      const int c = sl.ref.y & 0xFFFF;
+      const RayHdr h = p.hdr[ray];
+      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
+      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
+      const int i = c * kWarp + sl.sl;
+      valid = i < ss.n;
+      if (valid) {
+        float o[3], d[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          o[ax] = p.rays_o[3 * (size_t)ray + ax];
+          d[ax] = p.rays_d[3 * (size_t)ray + ax];
+        }
+        float a, b;
+        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
+        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
+        float x[3];
+        sample_point(o, d, tbar, x);
+        region_coord(p.boxes + 6 * k, x, u);
+      }
+    }
+    uint32_t* cw = cw0 + (size_t)(t - wa) * kGRows + row;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) cw[ax * cstride] = __float_as_uint(u[ax]);
+    cw[3 * cstride] = valid ? 1u : 0u;
+  }
+}
+
 template <bool kF16Table, bool kBF16>
 __global__ void __launch_bounds__(kGThreads, 4) k_gather_groups(GatherGroupsParams p) {
   using TabT = typename TableOf<kF16Table>::T;
@@ -80,7 +132,6 @@ __global__ void __launch_bounds__(kGThreads, 4) k_gather_groups(GatherGroupsPara
   const int total = s_pre[K];
   const int sub = threadIdx.x / kGRows;
   const uint32_t row = threadIdx.x % kGRows;
-  const int q = (int)(row / kWarp), lane = (int)(row % kWarp);
   for (int it = blockIdx.x * 2 + sub; it < total; it += gridDim.x * 2) {
     int lo = 0, hi = K - 1;  // region k: s_pre[k] <= it < s_pre[k + 1]
     while (lo < hi) {
@@ -92,34 +143,13 @@ __global__ void __launch_bounds__(kGThreads, 4) k_gather_groups(GatherGroupsPara
     const int rem = it - s_pre[k];
     const int g = rem / s_cnt[k];
     const int64_t t = s_start[k] + rem % s_cnt[k];
-    // the row's sample, as the tensor-core forward computes it
-    const SlotLane sl = slot_lane(p.chunks[t * 4 + q], lane);
-    bool valid = false;
-    float u[3] = {0.0f, 0.0f, 0.0f};
-    if (sl.has) {
-      const uint32_t ray = sl.ref.x;
-      const int seg = sl.ref.y >> 16;
-      const int c = sl.ref.y & 0xFFFF;
-      const RayHdr h = p.hdr[ray];
-      const SegDesc sd = p.segs[(size_t)ray * p.sp.max_seg + seg];
-      const SegSamples ss = seg_samples(p.sp, sd, ray, seg);
-      const int i = c * kWarp + sl.sl;
-      valid = i < ss.n;
-      if (valid) {
-        float o[3], d[3];
+    // the row's region coordinates, from the window's coordinate words
+    const uint32_t* cw = p.feat + ((size_t)p.lp.L * p.window + (size_t)(t - wa)) * kGRows + row;
+    const size_t cstride = (size_t)p.window * kGRows;
+    const bool valid = __ldcs(cw + 3 * cstride) != 0u;
+    float u[3];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          o[ax] = p.rays_o[3 * (size_t)ray + ax];
-          d[ax] = p.rays_d[3 * (size_t)ray + ax];
-        }
-        float a, b;
-        segment_interval(sd, h.tn, h.delta, sample_interval(p.sp, ss, i), a, b);
-        const float tbar = __fmul_rn(0.5f, __fadd_rn(a, b));
-        float x[3];
-        sample_point(o, d, tbar, x);
-        region_coord(p.boxes + 6 * k, x, u);
-      }
-    }
+    for (int ax = 0; ax < 3; ++ax) u[ax] = __uint_as_float(__ldcs(cw + ax * cstride));
     const TabT* table = static_cast<const TabT*>(p.tables) + (size_t)k * p.lp.E;
     // level-major words: the 128 rows of a tile write 512 contiguous bytes per
     // level, whole sectors (a partly written sector would cost L2 a read
@@ -191,6 +221,9 @@ nerfxl_status launch_gather_groups(const nerfxl_field* f, const SampParams& sp, 
   const bool f16tab = f->table_dtype == NERFXL_F16, bf = f->mlp_dtype == NERFXL_BF16;
   void (*kern)(GatherGroupsParams) = f16tab ? (bf ? k_gather_groups<true, true> : k_gather_groups<true, false>)
                                             : (bf ? k_gather_groups<false, true> : k_gather_groups<false, false>);
+  k_gather_coords<<<fwd_grid(((w1 - w0) * kGRows + kGThreads - 1) / kGThreads, 8), kGThreads, 0, stream>>>(p);
+  nerfxl_status st = kernel_launched("k_gather_coords");
+  if (st != NERFXL_OK) return st;
   const size_t smem = sizeof(int32_t) * (3 * (size_t)f->K + 1);
   const int64_t items = (w1 - w0) * p.n_groups;  // upper bound: the window's tiles times the groups
   const int grid = fwd_grid((items + 1) / 2, 4);

@@ -39,7 +39,9 @@ struct Layout {
   size_t smp2;       // float2[R][max_chunk][32]: tbar - tn, delta per sample slot
   // Level-grouped gather (fields whose region table exceeds kGroupMinBytes):
   // a window of gfeat_tiles tiles of level-major feature words,
-  // [L][gfeat_tiles][128] uint32 (two 16-bit features per word).
+  // [L][gfeat_tiles][128] uint32 (two 16-bit features per word), followed by
+  // the rows' region coordinates and sample flags, [4][gfeat_tiles][128]
+  // (u0, u1, u2 as float bits, then 1 for a sample, 0 for an empty row).
   size_t gfeat;
   int64_t gfeat_tiles;
   size_t total;
@@ -110,6 +112,7 @@ RecordOut record_out(char* ws, const Layout& L);
 constexpr size_t kGroupMinBytes = size_t(64) << 20;
 constexpr size_t kGroupBytes = size_t(64) << 20;
 constexpr int64_t kGatherWindowTiles = 65536;
+constexpr int kGatherCoordWords = 4;  // per row after the feature words: u0, u1, u2, sample flag
 // The values in force (nerfxl_set_gather_groups may change them).
 size_t group_min_bytes();
 int64_t gather_window_tiles();

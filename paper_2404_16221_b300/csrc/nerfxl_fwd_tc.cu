@@ -448,8 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
           }
         }
       }
-      tc::fence_before_sync();
-      __syncthreads();  // A tiles and TMEM free for the next tile
+      tc::fence_before_sync();  // no barrier: as at the end of the fused form's tile below
       continue;
     }
     tc::fence_proxy_async();
@@ -545,8 +544,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_field_fwd_tc(FwdTcParams p) {
         }
       }
     }
+    // No barrier here: the warps of level groups 1-3 start the next tile's
+    // gather while those of group 0 render this one. The A tiles are free
+    // (every MMA of this tile has completed), and the next layer-1 MMA, which
+    // overwrites the TMEM columns the render reads, is issued only after the
+    // barrier that ends the next gather, which the render warps reach after
+    // their TMEM reads (fenced before it).
     tc::fence_before_sync();
-    __syncthreads();  // A tiles and TMEM free for the next tile
   }
   if (failed && tid == 0) atomicOr(p.err, kErrTimeout);
   tc::fence_before_sync();

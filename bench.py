@@ -287,7 +287,7 @@ LD_PROBE_BYTES = 24 << 20  # about one grid8 region's FP16 table (24 MB)
 # from one ncu capture of the plain grid8 forward at full size
 # (l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum / samples), valid while the
 # forward's sources are unchanged.
-FWD_TC_LD = {"sectors": 2144788621, "samples": 29292644, "sources_sha16": "781f278e288e30bd"}
+FWD_TC_LD = {"sectors": 2144803190, "samples": 29292644, "sources_sha16": "15c0a93433dfff2f"}
 FWD_TC_SOURCES = ("nerfxl_fwd_tc.cu", "nerfxl_field.cuh", "nerfxl_tc.cuh", "nerfxl_half.cuh", "nerfxl_device.cuh")
 
 

@@ -12,7 +12,9 @@
 //   layer 1  D1[128x64] = A0[128x32] W1            (2 MMAs, K = 16 each)
 //   layer 2  h1 = relu(D1) -> A1; D2 = A1 W2        (4 MMAs)
 //   layer 3  h2 = relu(D2) -> A0; D3[128x16] = A0 W3 (4 MMAs; columns 4..15 zero)
-//   render   sigma = exp(D3[:,0]), rgb = sigmoid(D3[:,1..3]); chunk partial
+//   render   sigma = exp(D3[:,0]), rgb = sigmoid(D3[:,1..3]); chunk partial,
+//            by the four warps of level group 0 while the other twelve
+//            already gather the next tile (no barrier closes a tile)
 // The split representation (kSplit) runs five layers on the same tile:
 //   density  D1 = A0 Wd1 -> relu -> A1;  G[128x16] = A1 Wd2
 //   colour   A0 = [G (16) | SH(d) (16)];  D1 = A0 Wc1 -> relu -> A1;

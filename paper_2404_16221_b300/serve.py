@@ -149,7 +149,7 @@ class ServeEngine:
         self.ws = [torch.empty(wsb, dtype=torch.uint8, device=self.dev) for _ in range(nbuf)]
         self.max_items = 4096
         isz = ctypes.sizeof(N.RayItemDesc)
-        self.items_host = [torch.empty(self.max_items * isz, dtype=torch.uint8).pin_memory() for _ in range(nbuf)]
+        self.items_host = [torch.empty(self.max_items * isz, dtype=torch.uint8, pin_memory=True) for _ in range(nbuf)]
         self.items_dev = [torch.empty(self.max_items * isz, dtype=torch.uint8, device=self.dev) for _ in range(nbuf)]
         self.stream = torch.cuda.current_stream(self.dev)
 

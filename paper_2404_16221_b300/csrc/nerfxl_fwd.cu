@@ -428,10 +428,19 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
   const int n_sub = *p.n_tiles * kFwdSubPerTile;
   int region = -1;
   const float2* table = nullptr;
-  for (int t = blockIdx.x; t < n_sub; t += gridDim.x) {
+  // The two activation buffers alternate roles by sub-tile: features and h2
+  // in s_F, h1 in s_H, swapped on the next sub-tile. So the render of a
+  // sub-tile (warps 0-3, reading h2) overlaps the next sub-tile's gather
+  // (warps 4-7 start it at once; its features go to the other buffer), and no
+  // barrier closes a sub-tile: the next layer 1, which overwrites this h2, runs
+  // after the barrier that ends the next gather.
+  int it = 0;
+  for (int t = blockIdx.x; t < n_sub; t += gridDim.x, ++it) {
     const int k = region_of_chunk(s_base, p.K, t * 4);
-    __syncthreads();  // the previous sub-tile's buffers (and weights) fully read
+    float* s_F = (it & 1) ? s_B : s_A;
+    float* s_H = (it & 1) ? s_A : s_B;
     if (k != region) {
+      __syncthreads();  // the render warps are done with the previous weights
       for (int i = tid; i < kMlpParams; i += blockDim.x) s_w[i] = p.fp.mlp[(size_t)k * kMlpParams + i];
       region = k;
       table = reinterpret_cast<const float2*>(p.fp.tables) + (size_t)k * p.lp.E;
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s_A[(16 * h + j) * kFPitch + srow] = feat[j];
+    for (int j = 0; j < 16; ++j) s_F[(16 * h + j) * kFPitch + srow] = feat[j];
     if (p.rec32 && valid) {  // records for the backward: feature 16 h + j of tile row (t % 2) * 128 + srow
       float* rec = p.rec32 + (size_t)(t / kFwdSubPerTile) * kIn * (kWarp * kChunksPerTile) +
                    (t % kFwdSubPerTile) * kFwdRows + srow;
@@ -492,14 +501,14 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
     {
       const float* W1 = s_w;
       const float* W2 = s_w + kIn * kWidth;
-      // h1 = relu(F W1) -> B; h2 = relu(h1 W2) -> A
-      tile_ab<kFPitch, kFwdRows / 2, kIn, 4, kWidth>(s_A, W1, sb, 4 * ub, acc);
+      // h1 = relu(F W1) -> H; h2 = relu(h1 W2) -> F
+      tile_ab<kFPitch, kFwdRows / 2, kIn, 4, kWidth>(s_F, W1, sb, 4 * ub, acc);
       tile_relu<8, 4>(acc);
-      tile_st<kFPitch, kFwdRows / 2, 4>(s_B, sb, 4 * ub, acc);
+      tile_st<kFPitch, kFwdRows / 2, 4>(s_H, sb, 4 * ub, acc);
       __syncthreads();
-      tile_ab<kFPitch, kFwdRows / 2, kWidth, 4, kWidth>(s_B, W2, sb, 4 * ub, acc);
+      tile_ab<kFPitch, kFwdRows / 2, kWidth, 4, kWidth>(s_H, W2, sb, 4 * ub, acc);
       tile_relu<8, 4>(acc);
-      tile_st<kFPitch, kFwdRows / 2, 4>(s_A, sb, 4 * ub, acc);  // the features' reads ended before h1's store
+      tile_st<kFPitch, kFwdRows / 2, 4>(s_F, sb, 4 * ub, acc);  // the features' reads ended before h1's store
     }
     __syncthreads();
     // ---- render (warps 0-3: thread = sample srow of slot q)
@@ -508,7 +517,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) k_field_fwd_f32(FwdParams p) {
       float raw[kOut] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 8
       for (int n = 0; n < kWidth; ++n) {
-        const float hv = s_A[n * kFPitch + srow];  // h2
+        const float hv = s_F[n * kFPitch + srow];  // h2
         const float4 w3 = *reinterpret_cast<const float4*>(W3 + 4 * n);
         raw[0] = fmaf(hv, w3.x, raw[0]);
         raw[1] = fmaf(hv, w3.y, raw[1]);
